@@ -1,0 +1,196 @@
+/*
+ * poba.h -- C ABI of the GB300 Power Bundle Adjustment library (libpoba.so).
+ *
+ * The library solves bundle-adjustment problems in the BAL camera model (Sec. 4: d_p = 9
+ * camera parameters [w0 w1 w2 t0 t1 t2 f k1 k2], 3 landmark coordinates) with
+ * Levenberg-Marquardt, where each damped normal equation (Sec. 4.1, eq. `normal`) is reduced to
+ * the camera system S dx_p = -b~ (Sec. 4.2, eqs. `Sx`, `Schur`) and solved matrix-free by the
+ * truncated power series x(m) = -sum_{i<=m} (U^-1 W V^-1 W^T)^i U^-1 b~ (Sec. 4.3, eqs.
+ * `S_approx`, `x_approx`) with the stop rule (i+1)||x(i)-x(i-1)|| / ||x(i)|| < eps (eq.
+ * `qcriterion`).  Every step runs in CUDA kernels for sm_103a on one GPU.
+ *
+ * Conventions shared by all entry points
+ *  - Status: every call returns a ba_status; nothing throws across the ABI.  On an error the
+ *    handle stays usable unless the status is BA_ERR_CUDA (a CUDA runtime error other than an
+ *    allocation failure, after which the handle should be destroyed).  ba_last_error() gives a
+ *    one-line description of the most recent failure on the calling thread.
+ *  - Ownership: ba_create copies every input; the library owns all device memory of a handle
+ *    and frees it in ba_destroy.  Output pointers belong to the caller.
+ *  - Pointer kinds: ptr_kind 0 = host memory, 1 = device memory of the handle's GPU.
+ *  - Streams: all GPU work of a handle is ordered on the handle's CUDA stream (the stream given
+ *    at creation, or a stream the library creates when NULL).  Calls that return host scalars
+ *    synchronise that stream before returning; others do not.
+ *  - Threading: a handle must not be used from two threads at once; handles are independent.
+ *  - Layout: cams [n_cams][9], lms [n_lms][3], obs [n_obs][2], row-major float64; index arrays
+ *    int32.  Observations may be given in any order; the library reorders them internally and
+ *    every per-observation output is returned in the caller's original order.
+ */
+#ifndef POBA_H
+#define POBA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ba_handle ba_handle; /* opaque, owned by the library */
+
+typedef enum {
+  BA_OK = 0,
+  BA_ERR_INVALID_ARG = 1,    /* bad size, pointer, index, option, or unsupported shape */
+  BA_ERR_CUDA = 2,           /* CUDA runtime failure (message in ba_last_error) */
+  BA_ERR_OOM = 3,            /* device allocation failed */
+  BA_ERR_NOT_SPD = 4,        /* a damped U or V block had a non-positive Cholesky pivot */
+  BA_ERR_NONFINITE = 5,      /* non-finite input, residual, cost or step */
+  BA_ERR_NOT_LINEARIZED = 6, /* a solve was requested before ba_linearize */
+  BA_ERR_TIMEOUT = 7         /* a bounded device-side wait gave up */
+} ba_status;
+
+typedef enum {
+  BA_FP64 = 0,      /* residuals, Jacobians and series matvecs in float64 */
+  BA_FP32_BULK = 1  /* residuals, Jacobians and series matvecs in float32 with float32 sums
+                       inside a landmark / camera-tile segment and float64 across segments;
+                       block inverses, cost, model decrease and gain ratio stay float64 */
+} ba_precision;
+
+typedef struct {
+  int32_t n_cams, n_lms, n_obs; /* n_cams >= 1, n_lms >= 1, n_obs >= 0 */
+  const double* cams;           /* [n_cams][9] initial cameras */
+  const double* lms;            /* [n_lms][3] initial landmarks */
+  const double* obs;            /* [n_obs][2] pixel observations */
+  const int32_t* cam_idx;       /* [n_obs] camera of each observation, 0 <= . < n_cams */
+  const int32_t* lm_idx;        /* [n_obs] landmark of each observation, 0 <= . < n_lms */
+  const double* weights;        /* [n_obs] observation weights > 0, or NULL for all ones;
+                                   F = 1/2 sum_o w_o ||r_o||^2 */
+  int32_t ptr_kind;             /* 0: all arrays above are host memory, 1: device memory */
+  int32_t precision;            /* ba_precision */
+  void* cuda_stream;            /* cudaStream_t to order work on, or NULL */
+} ba_problem_desc;
+
+typedef struct {
+  double lambda0;       /* initial damping, Sec. 5.1: 1e-4 */
+  double func_tol;      /* relative function tolerance, Sec. 5.1: 1e-6 */
+  double eps;           /* series stop threshold of eq. `qcriterion`, Sec. 5.1: 0.01 */
+  int32_t max_lm;       /* LM iteration cap, Sec. 5.1: 50 */
+  int32_t max_inner;    /* cap on series terms beyond x(0), Sec. 5.1: 20 */
+  int32_t damping_mode; /* 0: D^T D = diag(J^T J) clamped to [1e-6, 1e32]; 1: D = I */
+  int32_t use_graph;    /* 1: replay the series loop as a captured CUDA graph (default) */
+} ba_options;
+
+typedef struct {
+  int32_t inner_iters; /* m: number of applications of U^-1 W V^-1 W^T performed */
+  int32_t stopped;     /* 1 if eq. `qcriterion` fired (or ||x|| = 0), 0 if m hit max_inner */
+  double stop_value;   /* (m+1) ||x(m)-x(m-1)|| / ||x(m)|| at the last term (inf if m = 0) */
+  double x_norm;       /* ||x(m)||_2 */
+  double lambda;       /* damping the blocks were built with */
+} ba_series_info;
+
+typedef struct {
+  double cost_before;     /* F(x) before the step */
+  double cost_after;      /* F(x + dx) of the trial step */
+  double lambda;          /* damping used for this step */
+  double gain_ratio;      /* (F(x) - F(x+dx)) / (L(0) - L(dx)) */
+  double model_decrease;  /* L(0) - L(dx) = 1/2||r||^2 - 1/2||r + J dx||^2 */
+  double stop_value;      /* series stop value (see ba_series_info) */
+  int32_t accepted;       /* 1 if the step was applied */
+  int32_t inner_iters;    /* series terms used */
+  int32_t converged;      /* 1 if accepted with relative decrease < func_tol */
+  int32_t iteration;      /* LM iteration index of this step (0-based) */
+} ba_step_info;
+
+/* Fill *opts with the defaults of Sec. 5.1 (lambda0 1e-4, func_tol 1e-6, eps 0.01, max_lm 50,
+ * max_inner 20, damping_mode 0, use_graph 1).  Returns BA_ERR_INVALID_ARG if opts is NULL. */
+ba_status ba_default_options(ba_options* opts);
+
+/* Create a problem handle (Sec. 4: state x = (x_p, x_l), residuals r(x)).  Copies and
+ * validates the inputs (sizes, index ranges, finiteness, weights > 0), sorts observations by
+ * landmark, orders landmarks for camera locality and builds the tile schedule, then allocates
+ * all device memory once.  opts may be NULL for the defaults.  Errors: BA_ERR_INVALID_ARG (bad
+ * sizes, NULL pointers, out-of-range index, a landmark with more than 256 observations),
+ * BA_ERR_NONFINITE (non-finite input), BA_ERR_OOM, BA_ERR_CUDA.  *out is NULL on error. */
+ba_status ba_create(const ba_problem_desc* desc, const ba_options* opts, ba_handle** out);
+
+/* Replace the options of a handle (takes effect at the next call). */
+ba_status ba_set_options(ba_handle* h, const ba_options* opts);
+
+/* Linearise at the current state (Sec. 4.1): residuals r, Jacobians J_p (2x9) and J_l (2x3)
+ * per observation, and the undamped blocks U = J_p^T J_p, V = J_l^T J_l, b_p = J_p^T r,
+ * b_l = J_l^T r (eq. `normal`).  *cost_out (may be NULL) receives 1/2||r||^2 computed from the
+ * linearisation residuals (in the handle's precision); synchronises only if cost_out != NULL.
+ * Errors: BA_ERR_CUDA. */
+ba_status ba_linearize(ba_handle* h, double* cost_out);
+
+/* Solve the damped normal equation at the current linearisation with damping `lambda`:
+ * U_lambda, V_lambda and their Cholesky inverses (Sec. 4.1), b~ (Sec. 4.2), the power series
+ * x(m) (Sec. 4.3) with the handle's eps / max_inner, and the back-substitution
+ * dx_l = -V_lambda^-1 (b_l + W^T dx_p) (Sec. 4.2; sign derived from eq. `normal`).  The step
+ * stays on the device (read it with ba_get_step).  info may be NULL (then nothing is
+ * synchronised).  Errors: BA_ERR_NOT_LINEARIZED, BA_ERR_INVALID_ARG (lambda <= 0 or not
+ * finite), BA_ERR_NOT_SPD (reported when info != NULL), BA_ERR_CUDA. */
+ba_status ba_solve_schur_power(ba_handle* h, double lambda, ba_series_info* info);
+
+/* One Levenberg-Marquardt iteration (Sec. 5.1 "LM loop"): linearise if the state changed,
+ * damp with the handle's current lambda, solve with the power series, back-substitute,
+ * evaluate F(x + dx) and the model decrease, accept iff F decreased and the model decrease is
+ * positive, update lambda (accept: lambda *= max(1/3, 1 - (2 rho - 1)^3), nu = 2; reject:
+ * lambda *= nu, nu *= 2; clamp to [1e-10, 1e32]) and apply an accepted step.  Synchronises
+ * once.  info may be NULL.  Errors: BA_ERR_NOT_SPD, BA_ERR_NONFINITE (non-finite cost at the
+ * current state), BA_ERR_CUDA. */
+ba_status ba_lm_step(ba_handle* h, ba_step_info* info);
+
+/* Run ba_lm_step until convergence (func_tol) or max_lm iterations.  trace may be NULL or
+ * hold max_lm entries; *n_steps (may be NULL) receives the number of iterations run. */
+ba_status ba_lm_solve(ba_handle* h, ba_step_info* trace, int32_t* n_steps);
+
+/* F(x) = 1/2 sum_o w_o ||r_o(x)||^2 at the current state (Sec. 4), always in float64 with a
+ * fixed-order reduction.  Synchronises.  Errors: BA_ERR_INVALID_ARG (cost_out NULL), CUDA. */
+ba_status ba_cost(ba_handle* h, double* cost_out);
+
+/* Copy the current cameras [n_cams][9] and landmarks [n_lms][3] (caller's landmark order) to
+ * host (ptr_kind 0) or device (1) memory.  Either pointer may be NULL.  Synchronises. */
+ba_status ba_get_params(ba_handle* h, double* cams, double* lms, int32_t ptr_kind);
+
+/* Overwrite the current state (same layout as ba_get_params); marks the linearisation stale
+ * and leaves lambda unchanged.  Errors: BA_ERR_NONFINITE, BA_ERR_INVALID_ARG. */
+ba_status ba_set_params(ba_handle* h, const double* cams, const double* lms, int32_t ptr_kind);
+
+/* Copy the last solve's step dx_p [n_cams][9] and dx_l [n_lms][3] (caller's order).
+ * Synchronises. */
+ba_status ba_get_step(ba_handle* h, double* dx_p, double* dx_l, int32_t ptr_kind);
+
+/* Copy the last linearisation in the caller's observation order, converted to float64:
+ * r [n_obs][2], J_p [n_obs][2][9], J_l [n_obs][2][3] (weights applied as sqrt(w)).  Any pointer
+ * may be NULL.  Errors: BA_ERR_NOT_LINEARIZED. */
+ba_status ba_get_linearization(ba_handle* h, double* r, double* Jp, double* Jl, int32_t ptr_kind);
+
+/* Copy the last linearisation's undamped blocks: U [n_cams][9][9], V [n_lms][3][3] (caller's
+ * landmark order), b_p [n_cams][9], b_l [n_lms][3].  Any pointer may be NULL. */
+ba_status ba_get_blocks(ba_handle* h, double* U, double* V, double* b_p, double* b_l, int32_t ptr_kind);
+
+/* LM state for checkpoint / resume: damping lambda, its growth factor nu, the iteration
+ * counter and the current cost.  ba_set_lm_state marks nothing stale. */
+ba_status ba_get_lm_state(ba_handle* h, double* lambda, double* nu, int32_t* iteration, double* cost);
+ba_status ba_set_lm_state(ba_handle* h, double lambda, double nu, int32_t iteration);
+
+/* Device bytes held by the handle (all buffers of the arena). */
+ba_status ba_memory_footprint(ba_handle* h, uint64_t* bytes);
+
+/* Number of kernel launches the handle has issued since creation (each graph replay counts
+ * its kernel nodes). */
+ba_status ba_kernel_launches(ba_handle* h, uint64_t* count);
+
+/* Free all device memory of the handle (and its own stream, if it created one). NULL is OK. */
+ba_status ba_destroy(ba_handle* h);
+
+/* Static string for a status code. */
+const char* ba_status_string(ba_status s);
+
+/* Description of the most recent error on the calling thread ("" if none). */
+const char* ba_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POBA_H */

@@ -1,0 +1,254 @@
+"""GB300-native Power Bundle Adjustment (Weber et al., "Power Bundle Adjustment for
+Large-Scale 3D Reconstruction").
+
+Python binding of libpoba (include/poba.h).  Each ``ba_*`` function here marshals arguments to
+the C entry point of the same name; every step of the solve runs in the library's CUDA kernels
+(no CPU fallback: the import of the binding fails when libpoba.so is missing).
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA memory); outputs are
+returned as numpy arrays unless a torch CUDA tensor is passed to fill.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import _lib
+from ._lib import BA_FP64, BA_FP32_BULK, Options, ProblemDesc, SeriesInfo, StepInfo
+
+__all__ = ["PobaError", "Handle", "ba_default_options", "ba_create", "ba_set_options",
+           "ba_linearize", "ba_solve_schur_power", "ba_lm_step", "ba_lm_solve", "ba_cost",
+           "ba_get_params", "ba_set_params", "ba_get_step", "ba_get_linearization",
+           "ba_get_blocks", "ba_get_lm_state", "ba_set_lm_state", "ba_memory_footprint",
+           "ba_kernel_launches", "ba_destroy", "BA_FP64", "BA_FP32_BULK", "library"]
+
+
+class PobaError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        self.status_name = _lib.STATUS_NAMES.get(status, str(status))
+        super().__init__(f"{where}: {self.status_name}: {message}")
+
+
+def library() -> C.CDLL:
+    return _lib.load()
+
+
+def _check(status: int, where: str):
+    if status != _lib.BA_OK:
+        msg = library().ba_last_error().decode(errors="replace")
+        raise PobaError(status, where, msg)
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype):
+    """(pointer, ptr_kind, keepalive) for a numpy array or torch tensor of the given dtype."""
+    if a is None:
+        return None, None, None
+    if _is_torch(a):
+        import torch
+        tdt = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        if a.dtype != tdt or not a.is_contiguous():
+            a = a.to(tdt).contiguous()
+        return a.data_ptr(), (1 if a.is_cuda else 0), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, 0, arr
+
+
+@dataclass
+class Handle:
+    ptr: C.c_void_p
+    n_cams: int
+    n_lms: int
+    n_obs: int
+    precision: int
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                library().ba_destroy(self.ptr)
+                self.ptr = None
+        except Exception:
+            pass
+
+
+def ba_default_options(**overrides) -> Options:
+    o = Options()
+    _check(library().ba_default_options(C.byref(o)), "ba_default_options")
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def ba_create(cams, lms, obs, cam_idx, lm_idx, weights=None, precision: int = BA_FP64,
+              options: Optional[Options] = None, stream=None) -> Handle:
+    """Create a problem handle (copies every input)."""
+    n_c = int(cams.shape[0])
+    n_l = int(lms.shape[0])
+    n_o = int(obs.shape[0])
+    keep = []
+    kinds = set()
+    d = ProblemDesc()
+    d.n_cams, d.n_lms, d.n_obs = n_c, n_l, n_o
+    for field, arr, dt in (("cams", cams, np.float64), ("lms", lms, np.float64),
+                           ("obs", obs, np.float64), ("cam_idx", cam_idx, np.int32),
+                           ("lm_idx", lm_idx, np.int32), ("weights", weights, np.float64)):
+        p, kind, k = _ptr(arr, dt)
+        setattr(d, field, p)
+        keep.append(k)
+        if kind is not None:
+            kinds.add(kind)
+    if len(kinds) > 1:
+        raise ValueError("all inputs must live in the same memory (all host or all device)")
+    d.ptr_kind = kinds.pop() if kinds else 0
+    d.precision = int(precision)
+    if stream is not None:
+        d.cuda_stream = int(getattr(stream, "cuda_stream", stream)) or None
+    out = C.c_void_p()
+    opts = options if options is not None else ba_default_options()
+    _check(library().ba_create(C.byref(d), C.byref(opts), C.byref(out)), "ba_create")
+    return Handle(out, n_c, n_l, n_o, int(precision))
+
+
+def ba_set_options(h: Handle, options: Options):
+    _check(library().ba_set_options(h.ptr, C.byref(options)), "ba_set_options")
+
+
+def ba_linearize(h: Handle, want_cost: bool = True):
+    c = C.c_double()
+    _check(library().ba_linearize(h.ptr, C.byref(c) if want_cost else None), "ba_linearize")
+    return c.value if want_cost else None
+
+
+def ba_solve_schur_power(h: Handle, lam: float, want_info: bool = True):
+    info = SeriesInfo()
+    _check(library().ba_solve_schur_power(h.ptr, float(lam), C.byref(info) if want_info else None),
+           "ba_solve_schur_power")
+    if not want_info:
+        return None
+    return dict(inner_iters=info.inner_iters, stopped=info.stopped, stop_value=info.stop_value,
+                x_norm=info.x_norm, lam=info.lambda_)
+
+
+def _step_dict(s: StepInfo) -> dict:
+    return dict(cost_before=s.cost_before, cost_after=s.cost_after, lam=s.lambda_,
+                gain_ratio=s.gain_ratio, model_decrease=s.model_decrease, stop_value=s.stop_value,
+                accepted=bool(s.accepted), inner=s.inner_iters, converged=bool(s.converged),
+                it=s.iteration)
+
+
+def ba_lm_step(h: Handle) -> dict:
+    s = StepInfo()
+    _check(library().ba_lm_step(h.ptr, C.byref(s)), "ba_lm_step")
+    return _step_dict(s)
+
+
+def ba_lm_solve(h: Handle, max_lm: int = 50) -> list:
+    trace = (StepInfo * max(1, max_lm))()
+    n = C.c_int32()
+    _check(library().ba_lm_solve(h.ptr, trace, C.byref(n)), "ba_lm_solve")
+    return [_step_dict(trace[i]) for i in range(n.value)]
+
+
+def ba_cost(h: Handle) -> float:
+    c = C.c_double()
+    _check(library().ba_cost(h.ptr, C.byref(c)), "ba_cost")
+    return c.value
+
+
+def _out(shape, dst):
+    if dst is None:
+        a = np.empty(shape, dtype=np.float64)
+        return a, a.ctypes.data, 0
+    if _is_torch(dst):
+        return dst, dst.data_ptr(), (1 if dst.is_cuda else 0)
+    return dst, dst.ctypes.data, 0
+
+
+def ba_get_params(h: Handle, cams_out=None, lms_out=None):
+    c, cp, k1 = _out((h.n_cams, 9), cams_out)
+    l, lp, k2 = _out((h.n_lms, 3), lms_out)
+    if k1 != k2:
+        raise ValueError("outputs must live in the same memory")
+    _check(library().ba_get_params(h.ptr, cp, lp, k1), "ba_get_params")
+    return c, l
+
+
+def ba_set_params(h: Handle, cams, lms):
+    cp, k1, kc = _ptr(cams, np.float64)
+    lp, k2, kl = _ptr(lms, np.float64)
+    kind = k1 if k1 is not None else (k2 if k2 is not None else 0)
+    _check(library().ba_set_params(h.ptr, cp, lp, kind), "ba_set_params")
+
+
+def ba_get_step(h: Handle, dx_p_out=None, dx_l_out=None):
+    a, ap, k1 = _out((h.n_cams, 9), dx_p_out)
+    b, bp, k2 = _out((h.n_lms, 3), dx_l_out)
+    if k1 != k2:
+        raise ValueError("outputs must live in the same memory")
+    _check(library().ba_get_step(h.ptr, ap, bp, k1), "ba_get_step")
+    return a, b
+
+
+def ba_get_linearization(h: Handle):
+    r = np.empty((h.n_obs, 2))
+    Jp = np.empty((h.n_obs, 2, 9))
+    Jl = np.empty((h.n_obs, 2, 3))
+    _check(library().ba_get_linearization(h.ptr, r.ctypes.data, Jp.ctypes.data, Jl.ctypes.data, 0),
+           "ba_get_linearization")
+    return r, Jp, Jl
+
+
+def ba_get_blocks(h: Handle):
+    U = np.empty((h.n_cams, 9, 9))
+    V = np.empty((h.n_lms, 3, 3))
+    bp = np.empty(h.n_cams * 9)
+    bl = np.empty(h.n_lms * 3)
+    _check(library().ba_get_blocks(h.ptr, U.ctypes.data, V.ctypes.data, bp.ctypes.data,
+                                   bl.ctypes.data, 0), "ba_get_blocks")
+    return U, V, bp, bl
+
+
+def ba_get_lm_state(h: Handle) -> dict:
+    lam, nu, cost = C.c_double(), C.c_double(), C.c_double()
+    it = C.c_int32()
+    _check(library().ba_get_lm_state(h.ptr, C.byref(lam), C.byref(nu), C.byref(it), C.byref(cost)),
+           "ba_get_lm_state")
+    return dict(lam=lam.value, nu=nu.value, iteration=it.value, cost=cost.value)
+
+
+def ba_set_lm_state(h: Handle, lam: float, nu: float, iteration: int):
+    _check(library().ba_set_lm_state(h.ptr, float(lam), float(nu), int(iteration)), "ba_set_lm_state")
+
+
+def ba_memory_footprint(h: Handle) -> int:
+    b = C.c_uint64()
+    _check(library().ba_memory_footprint(h.ptr, C.byref(b)), "ba_memory_footprint")
+    return b.value
+
+
+def ba_kernel_launches(h: Handle) -> int:
+    b = C.c_uint64()
+    _check(library().ba_kernel_launches(h.ptr, C.byref(b)), "ba_kernel_launches")
+    return b.value
+
+
+def ba_destroy(h: Handle):
+    if h.ptr:
+        _check(library().ba_destroy(h.ptr), "ba_destroy")
+        h.ptr = None
+
+
+def from_problem(problem, precision: int = BA_FP64, options: Optional[Options] = None,
+                 stream=None) -> Handle:
+    """ba_create from a bal_synth.Problem-like object (cams0, lms0, obs, indices, weights)."""
+    return ba_create(problem.cams0, problem.lms0, problem.obs, problem.cam_idx, problem.lm_idx,
+                     problem.weights, precision=precision, options=options, stream=stream)

@@ -1,0 +1,88 @@
+"""ctypes declarations for libpoba.so (mirrors include/poba.h)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpoba.so")
+
+BA_OK = 0
+STATUS_NAMES = {0: "BA_OK", 1: "BA_ERR_INVALID_ARG", 2: "BA_ERR_CUDA", 3: "BA_ERR_OOM",
+                4: "BA_ERR_NOT_SPD", 5: "BA_ERR_NONFINITE", 6: "BA_ERR_NOT_LINEARIZED",
+                7: "BA_ERR_TIMEOUT"}
+BA_FP64 = 0
+BA_FP32_BULK = 1
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [("n_cams", C.c_int32), ("n_lms", C.c_int32), ("n_obs", C.c_int32),
+                ("cams", C.c_void_p), ("lms", C.c_void_p), ("obs", C.c_void_p),
+                ("cam_idx", C.c_void_p), ("lm_idx", C.c_void_p), ("weights", C.c_void_p),
+                ("ptr_kind", C.c_int32), ("precision", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
+class Options(C.Structure):
+    _fields_ = [("lambda0", C.c_double), ("func_tol", C.c_double), ("eps", C.c_double),
+                ("max_lm", C.c_int32), ("max_inner", C.c_int32), ("damping_mode", C.c_int32),
+                ("use_graph", C.c_int32)]
+
+
+class SeriesInfo(C.Structure):
+    _fields_ = [("inner_iters", C.c_int32), ("stopped", C.c_int32), ("stop_value", C.c_double),
+                ("x_norm", C.c_double), ("lambda_", C.c_double)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("cost_before", C.c_double), ("cost_after", C.c_double), ("lambda_", C.c_double),
+                ("gain_ratio", C.c_double), ("model_decrease", C.c_double),
+                ("stop_value", C.c_double), ("accepted", C.c_int32), ("inner_iters", C.c_int32),
+                ("converged", C.c_int32), ("iteration", C.c_int32)]
+
+
+# name -> (restype, argtypes); every symbol declared in include/poba.h
+SIGNATURES = {
+    "ba_default_options": (C.c_int, [C.POINTER(Options)]),
+    "ba_create": (C.c_int, [C.POINTER(ProblemDesc), C.POINTER(Options), C.POINTER(C.c_void_p)]),
+    "ba_set_options": (C.c_int, [C.c_void_p, C.POINTER(Options)]),
+    "ba_linearize": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "ba_solve_schur_power": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(SeriesInfo)]),
+    "ba_lm_step": (C.c_int, [C.c_void_p, C.POINTER(StepInfo)]),
+    "ba_lm_solve": (C.c_int, [C.c_void_p, C.POINTER(StepInfo), C.POINTER(C.c_int32)]),
+    "ba_cost": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "ba_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "ba_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "ba_get_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "ba_get_linearization": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "ba_get_blocks": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "ba_get_lm_state": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                  C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+    "ba_set_lm_state": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int32]),
+    "ba_memory_footprint": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
+    "ba_kernel_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
+    "ba_destroy": (C.c_int, [C.c_void_p]),
+    "ba_status_string": (C.c_char_p, [C.c_int]),
+    "ba_last_error": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Load libpoba.so (built in-tree by paper_2204_12834_gb300.build).  Raises when missing:
+    there is no fallback implementation."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libpoba.so not found at {p}; build it with "
+                          "`python -m paper_2204_12834_gb300.build` (needs nvcc)")
+    lib = C.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib

@@ -1,0 +1,761 @@
+// C ABI of libpoba (include/poba.h): handle life cycle, device arena, LM orchestration.
+//
+// One handle owns one problem on one GPU.  All device buffers live in a single arena
+// allocated at creation; every call is ordered on the handle's stream.  The series loop
+// (b~ and x(0), up to max_inner terms, back-substitution) is recorded once as a CUDA graph and
+// replayed; terms after the stop rule fired return at kernel entry.
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/poba.h"
+#include "poba_internal.cuh"
+
+using namespace poba;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ba_status fail(ba_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+ba_status fail_cuda(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky launch error where possible
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? BA_ERR_OOM : BA_ERR_CUDA;
+}
+
+#define CK(call)                                                  \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return fail_cuda(e_, #call);           \
+  } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Device address of one field of the device-resident LM record.
+double* rec_field(LmRecord* rec, size_t offset) { return (double*)((char*)rec + offset); }
+
+}  // namespace
+
+struct ba_handle {
+  int n_c = 0, n_l = 0, n_o = 0, n_o_pad = 0;
+  int precision = BA_FP64;
+  bool weighted = false;
+  ba_options opts{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  Schedule sched;
+  Topology tp{};
+
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+
+  // problem (internal orders)
+  double2* obs = nullptr;
+  double* sqrt_w = nullptr;
+  double* cams = nullptr;
+  double* cams_trial = nullptr;
+  double* lms = nullptr;
+  double* prep = nullptr;
+  double* prep_trial = nullptr;
+  // linearisation (bulk precision)
+  void* J = nullptr;
+  void* r = nullptr;
+  void* partial = nullptr;
+  double* U45 = nullptr;
+  double* b_p = nullptr;
+  double* V = nullptr;
+  double* b_l = nullptr;
+  double* Uinv = nullptr;
+  double* Vinv = nullptr;
+  float* Vinv_f = nullptr;
+  // series
+  double* x = nullptr;
+  double* t = nullptr;
+  double* dx_l = nullptr;
+  double* block_norms = nullptr;
+  double* block_cost = nullptr;
+  double* block_pred = nullptr;
+  double* scalars = nullptr;  // [0] lambda for explicit solves, [1] cost out
+  SeriesState* st = nullptr;
+  LmRecord* rec = nullptr;
+  int32_t* not_spd = nullptr;
+
+  // host staging (pinned)
+  SeriesState* h_st = nullptr;
+  LmRecord* h_rec = nullptr;
+  int32_t* h_flag = nullptr;
+  double* h_scalar = nullptr;
+
+  bool linearized = false;
+  bool cost_valid = false;
+  bool have_step = false;
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_max_inner = -1;
+  double graph_eps = -1.0;
+  int graph_nodes = 0;
+  uint64_t launches = 0;
+
+  bool f32() const { return precision == BA_FP32_BULK; }
+};
+
+namespace {
+
+bool valid_options(const ba_options& o, std::string* why) {
+  if (!(o.lambda0 > 0.0) || !std::isfinite(o.lambda0)) { *why = "lambda0 must be > 0"; return false; }
+  if (!(o.func_tol >= 0.0)) { *why = "func_tol must be >= 0"; return false; }
+  if (!(o.eps >= 0.0)) { *why = "eps must be >= 0"; return false; }
+  if (o.max_lm < 0 || o.max_lm > 100000) { *why = "max_lm out of range"; return false; }
+  if (o.max_inner < 0 || o.max_inner > 10000) { *why = "max_inner out of range [0, 10000]"; return false; }
+  if (o.damping_mode != 0 && o.damping_mode != 1) { *why = "damping_mode must be 0 or 1"; return false; }
+  return true;
+}
+
+template <typename T>
+void copy_in(std::vector<T>& dst, const T* src, size_t n, int ptr_kind) {
+  dst.resize(n);
+  if (n == 0) return;
+  if (ptr_kind == 1) cudaMemcpy(dst.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost);
+  else std::memcpy(dst.data(), src, n * sizeof(T));
+}
+
+// Write a host vector to a caller pointer of the given kind.
+ba_status copy_out(void* dst, const void* src, size_t bytes, int ptr_kind) {
+  if (bytes == 0) return BA_OK;
+  if (ptr_kind == 1) CK(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+  else std::memcpy(dst, src, bytes);
+  return BA_OK;
+}
+
+ba_status check_launch(ba_handle* h, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda(e, what);
+  return BA_OK;
+}
+
+// ---- kernel sequences ------------------------------------------------------------------
+
+void seq_linearize(ba_handle* h) {
+  cudaStream_t s = h->stream;
+  launch_cam_prepare(h->cams, nullptr, h->n_c, h->prep, nullptr, s);
+  if (h->f32()) {
+    launch_linearize<float>(h->tp, h->prep, h->lms, h->obs, h->sqrt_w, (float*)h->J, (float*)h->r,
+                            h->V, h->b_l, (float*)h->partial, h->block_cost, s);
+    launch_lin_camera_reduce<float>(h->tp, (const float*)h->partial, h->U45, h->b_p, s);
+  } else {
+    launch_linearize<double>(h->tp, h->prep, h->lms, h->obs, h->sqrt_w, (double*)h->J,
+                             (double*)h->r, h->V, h->b_l, (double*)h->partial, h->block_cost, s);
+    launch_lin_camera_reduce<double>(h->tp, (const double*)h->partial, h->U45, h->b_p, s);
+  }
+  h->launches += 3;
+}
+
+// series reset, b~ / x(0), max_inner terms, back-substitution with model decrease
+template <typename T>
+void seq_series_body(ba_handle* h, cudaStream_t s) {
+  const Topology& tp = h->tp;
+  const T* J = (const T*)h->J;
+  const T* Vi = h->f32() ? (const T*)(const void*)h->Vinv_f : (const T*)(const void*)h->Vinv;
+  T* part = (T*)h->partial;
+  launch_series_reset(h->st, s);
+  launch_tile_rhs<T>(tp, J, h->b_l, Vi, part, h->st, s);
+  launch_camera_rhs<T>(tp, part, h->b_p, h->Uinv, h->x, h->t, h->block_norms, h->st, s);
+  for (int i = 1; i <= h->opts.max_inner; ++i) {
+    launch_tile_series<T>(tp, J, h->t, Vi, part, h->st, s);
+    launch_camera_series<T>(tp, part, h->Uinv, h->x, h->t, h->block_norms, h->st, i, h->opts.eps, s);
+  }
+  launch_tile_backsub<T>(tp, J, (const T*)h->r, h->x, h->b_l, Vi, h->dx_l, h->block_pred, s);
+}
+
+int series_body_kernels(const ba_handle* h) { return 4 + 2 * h->opts.max_inner; }
+
+ba_status run_series_body(ba_handle* h) {
+  cudaStream_t s = h->stream;
+  if (h->opts.use_graph) {
+    if (!h->graph_exec || h->graph_max_inner != h->opts.max_inner || h->graph_eps != h->opts.eps) {
+      if (h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      if (h->f32()) seq_series_body<float>(h, s);
+      else seq_series_body<double>(h, s);
+      cudaError_t e = cudaStreamEndCapture(s, &g);
+      if (e != cudaSuccess) return fail_cuda(e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+      size_t nn = 0;
+      cudaGraphGetNodes(g, nullptr, &nn);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail_cuda(e, "cudaGraphInstantiate");
+      h->graph_nodes = (int)nn;
+      h->graph_max_inner = h->opts.max_inner;
+      h->graph_eps = h->opts.eps;
+    }
+    CK(cudaGraphLaunch(h->graph_exec, s));
+    h->launches += (uint64_t)h->graph_nodes;
+  } else {
+    if (h->f32()) seq_series_body<float>(h, s);
+    else seq_series_body<double>(h, s);
+    h->launches += (uint64_t)series_body_kernels(h);
+  }
+  return BA_OK;
+}
+
+ba_status run_solve(ba_handle* h, const double* lam_dev) {
+  CK(cudaMemsetAsync(h->not_spd, 0, sizeof(int32_t), h->stream));
+  launch_damp_invert(h->tp, h->U45, h->V, lam_dev, h->opts.damping_mode, h->Uinv, h->Vinv,
+                     h->f32() ? h->Vinv_f : nullptr, h->not_spd, h->stream);
+  h->launches += 1;
+  ba_status st = run_series_body(h);
+  if (st != BA_OK) return st;
+  h->have_step = true;
+  return check_launch(h, "series kernels");
+}
+
+void seq_cost(ba_handle* h, double* out_dev) {
+  launch_cam_prepare(h->cams, nullptr, h->n_c, h->prep, nullptr, h->stream);
+  launch_cost(h->tp, h->prep, h->lms, nullptr, h->obs, h->sqrt_w, h->block_cost, h->stream);
+  launch_reduce_sum(h->block_cost, cost_blocks(h->tp), out_dev, 0.5, h->stream);
+  h->launches += 3;
+}
+
+}  // namespace
+
+extern "C" {
+
+ba_status ba_default_options(ba_options* o) {
+  if (!o) return fail(BA_ERR_INVALID_ARG, "opts is NULL");
+  o->lambda0 = 1e-4;
+  o->func_tol = 1e-6;
+  o->eps = 0.01;
+  o->max_lm = 50;
+  o->max_inner = 20;
+  o->damping_mode = 0;
+  o->use_graph = 1;
+  return BA_OK;
+}
+
+ba_status ba_destroy(ba_handle* h) {
+  if (!h) return BA_OK;
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->arena) cudaFree(h->arena);
+  if (h->h_st) cudaFreeHost(h->h_st);
+  if (h->h_rec) cudaFreeHost(h->h_rec);
+  if (h->h_flag) cudaFreeHost(h->h_flag);
+  if (h->h_scalar) cudaFreeHost(h->h_scalar);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return BA_OK;
+}
+
+ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle** out) {
+  if (!out) return fail(BA_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(BA_ERR_INVALID_ARG, "desc is NULL");
+  if (d->n_cams < 1 || d->n_lms < 1 || d->n_obs < 0)
+    return fail(BA_ERR_INVALID_ARG, "need n_cams >= 1, n_lms >= 1, n_obs >= 0");
+  if (d->ptr_kind != 0 && d->ptr_kind != 1) return fail(BA_ERR_INVALID_ARG, "ptr_kind must be 0 or 1");
+  if (d->precision != BA_FP64 && d->precision != BA_FP32_BULK)
+    return fail(BA_ERR_INVALID_ARG, "precision must be BA_FP64 or BA_FP32_BULK");
+  if (!d->cams || !d->lms) return fail(BA_ERR_INVALID_ARG, "cams / lms is NULL");
+  if (d->n_obs > 0 && (!d->obs || !d->cam_idx || !d->lm_idx))
+    return fail(BA_ERR_INVALID_ARG, "obs / cam_idx / lm_idx is NULL");
+  ba_options o;
+  ba_default_options(&o);
+  if (opts) o = *opts;
+  std::string why;
+  if (!valid_options(o, &why)) return fail(BA_ERR_INVALID_ARG, why);
+
+  const int nc = d->n_cams, nl = d->n_lms, no = d->n_obs;
+  std::vector<double> cams, lms, obs, w;
+  std::vector<int32_t> ci, li;
+  copy_in(cams, d->cams, (size_t)nc * 9, d->ptr_kind);
+  copy_in(lms, d->lms, (size_t)nl * 3, d->ptr_kind);
+  copy_in(obs, d->obs, (size_t)no * 2, d->ptr_kind);
+  copy_in(ci, d->cam_idx, (size_t)no, d->ptr_kind);
+  copy_in(li, d->lm_idx, (size_t)no, d->ptr_kind);
+  if (d->weights) copy_in(w, d->weights, (size_t)no, d->ptr_kind);
+  if (d->ptr_kind == 1) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(e, "copying device inputs");
+  }
+  for (double v : cams) if (!std::isfinite(v)) return fail(BA_ERR_NONFINITE, "non-finite camera parameter");
+  for (double v : lms) if (!std::isfinite(v)) return fail(BA_ERR_NONFINITE, "non-finite landmark");
+  for (double v : obs) if (!std::isfinite(v)) return fail(BA_ERR_NONFINITE, "non-finite observation");
+  for (double v : w) if (!(v > 0.0) || !std::isfinite(v)) return fail(BA_ERR_INVALID_ARG, "weights must be finite and > 0");
+
+  ba_handle* h = new ba_handle();
+  h->n_c = nc;
+  h->n_l = nl;
+  h->n_o = no;
+  h->n_o_pad = (int)align_up((size_t)(no > 0 ? no : 1), 64);
+  h->precision = d->precision;
+  h->weighted = d->weights != nullptr;
+  h->opts = o;
+  why = build_schedule(nc, nl, no, ci.data(), li.data(), &h->sched);
+  if (!why.empty()) {
+    delete h;
+    return fail(BA_ERR_INVALID_ARG, why);
+  }
+  const Schedule& S = h->sched;
+
+  // ---- arena layout
+  const size_t bulk = h->f32() ? sizeof(float) : sizeof(double);
+  struct Item { void** ptr; size_t bytes; };
+  std::vector<Item> items;
+  int32_t *d_lm_seg, *d_cam_of, *d_lm_of, *d_tile_lm0, *d_tile_slot0, *d_slot_cam, *d_cam_slot_ptr, *d_cam_slot_list;
+  uint16_t *d_meta, *d_slot_beg;
+  const size_t slots = (size_t)(S.n_slots > 0 ? S.n_slots : 1);
+  const int nbn = (nc + kCamBlock - 1) / kCamBlock;
+  Topology tmp{};
+  tmp.n_obs = no;
+  const int ncost = cost_blocks(tmp);
+  items.push_back({(void**)&d_lm_seg, sizeof(int32_t) * (nl + 1)});
+  items.push_back({(void**)&d_cam_of, sizeof(int32_t) * (no > 0 ? no : 1)});
+  items.push_back({(void**)&d_lm_of, sizeof(int32_t) * (no > 0 ? no : 1)});
+  items.push_back({(void**)&d_meta, sizeof(uint16_t) * (no > 0 ? no : 1)});
+  items.push_back({(void**)&d_tile_lm0, sizeof(int32_t) * (S.n_tiles + 1)});
+  items.push_back({(void**)&d_tile_slot0, sizeof(int32_t) * (S.n_tiles + 1)});
+  items.push_back({(void**)&d_slot_cam, sizeof(int32_t) * slots});
+  items.push_back({(void**)&d_slot_beg, sizeof(uint16_t) * slots});
+  items.push_back({(void**)&d_cam_slot_ptr, sizeof(int32_t) * (nc + 1)});
+  items.push_back({(void**)&d_cam_slot_list, sizeof(int32_t) * slots});
+  items.push_back({(void**)&h->obs, sizeof(double2) * (no > 0 ? no : 1)});
+  if (h->weighted) items.push_back({(void**)&h->sqrt_w, sizeof(double) * no});
+  items.push_back({(void**)&h->cams, sizeof(double) * nc * 9});
+  items.push_back({(void**)&h->cams_trial, sizeof(double) * nc * 9});
+  items.push_back({(void**)&h->lms, sizeof(double) * nl * 3});
+  items.push_back({(void**)&h->prep, sizeof(double) * nc * kCamPrep});
+  items.push_back({(void**)&h->prep_trial, sizeof(double) * nc * kCamPrep});
+  items.push_back({&h->J, bulk * 24 * h->n_o_pad});
+  items.push_back({&h->r, bulk * 2 * h->n_o_pad});
+  items.push_back({&h->partial, bulk * kLinVals * slots});
+  items.push_back({(void**)&h->U45, sizeof(double) * nc * 45});
+  items.push_back({(void**)&h->b_p, sizeof(double) * nc * 9});
+  items.push_back({(void**)&h->V, sizeof(double) * nl * 6});
+  items.push_back({(void**)&h->b_l, sizeof(double) * nl * 3});
+  items.push_back({(void**)&h->Uinv, sizeof(double) * nc * 81});
+  items.push_back({(void**)&h->Vinv, sizeof(double) * nl * 6});
+  if (h->f32()) items.push_back({(void**)&h->Vinv_f, sizeof(float) * nl * 6});
+  items.push_back({(void**)&h->x, sizeof(double) * nc * 9});
+  items.push_back({(void**)&h->t, sizeof(double) * nc * 9});
+  items.push_back({(void**)&h->dx_l, sizeof(double) * nl * 3});
+  items.push_back({(void**)&h->block_norms, sizeof(double) * 2 * nbn});
+  items.push_back({(void**)&h->block_cost, sizeof(double) * (S.n_tiles > ncost ? S.n_tiles : ncost)});
+  items.push_back({(void**)&h->block_pred, sizeof(double) * S.n_tiles});
+  items.push_back({(void**)&h->scalars, sizeof(double) * 4});
+  items.push_back({(void**)&h->st, sizeof(SeriesState)});
+  items.push_back({(void**)&h->rec, sizeof(LmRecord)});
+  items.push_back({(void**)&h->not_spd, sizeof(int32_t)});
+  size_t total = 0;
+  for (auto& it : items) total = align_up(total, 256) + it.bytes;
+  total = align_up(total, 256);
+
+  auto bail = [&](ba_status s) { ba_destroy(h); return s; };
+  cudaError_t e;
+  if (d->cuda_stream) {
+    h->stream = (cudaStream_t)d->cuda_stream;
+  } else {
+    e = cudaStreamCreate(&h->stream);
+    if (e != cudaSuccess) return bail(fail_cuda(e, "cudaStreamCreate"));
+    h->own_stream = true;
+  }
+  e = cudaMalloc(&h->arena, total);
+  if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(arena)"));
+  h->arena_bytes = total;
+  {
+    size_t off = 0;
+    for (auto& it : items) {
+      off = align_up(off, 256);
+      *it.ptr = (char*)h->arena + off;
+      off += it.bytes;
+    }
+  }
+  e = cudaMemset(h->arena, 0, total);
+  if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMemset(arena)"));
+  if ((e = cudaMallocHost(&h->h_st, sizeof(SeriesState))) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_rec, sizeof(LmRecord))) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_flag, sizeof(int32_t))) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_scalar, sizeof(double) * 4)) != cudaSuccess)
+    return bail(fail_cuda(e, "cudaMallocHost"));
+
+  // ---- upload (sorted / internal orders)
+  std::vector<double> obs_s((size_t)no * 2), sw_s;
+  for (int o = 0; o < no; ++o) {
+    obs_s[2 * o] = obs[2 * S.obs_order[o]];
+    obs_s[2 * o + 1] = obs[2 * S.obs_order[o] + 1];
+  }
+  if (h->weighted) {
+    sw_s.resize(no);
+    for (int o = 0; o < no; ++o) sw_s[o] = std::sqrt(w[S.obs_order[o]]);
+  }
+  std::vector<double> lms_i((size_t)nl * 3);
+  for (int i = 0; i < nl; ++i)
+    for (int k = 0; k < 3; ++k) lms_i[i * 3 + k] = lms[(size_t)S.lm_order[i] * 3 + k];
+  struct Up { void* dst; const void* src; size_t bytes; };
+  std::vector<Up> ups = {
+      {d_lm_seg, S.lm_seg.data(), sizeof(int32_t) * (nl + 1)},
+      {d_cam_of, S.cam_of.data(), sizeof(int32_t) * no},
+      {d_lm_of, S.lm_of.data(), sizeof(int32_t) * no},
+      {d_meta, S.obs_meta.data(), sizeof(uint16_t) * no},
+      {d_tile_lm0, S.tile_lm0.data(), sizeof(int32_t) * (S.n_tiles + 1)},
+      {d_tile_slot0, S.tile_slot0.data(), sizeof(int32_t) * (S.n_tiles + 1)},
+      {d_slot_cam, S.slot_cam.data(), sizeof(int32_t) * S.n_slots},
+      {d_slot_beg, S.slot_beg.data(), sizeof(uint16_t) * S.n_slots},
+      {d_cam_slot_ptr, S.cam_slot_ptr.data(), sizeof(int32_t) * (nc + 1)},
+      {d_cam_slot_list, S.cam_slot_list.data(), sizeof(int32_t) * S.n_slots},
+      {h->obs, obs_s.data(), sizeof(double) * 2 * no},
+      {h->cams, cams.data(), sizeof(double) * nc * 9},
+      {h->lms, lms_i.data(), sizeof(double) * nl * 3},
+  };
+  if (h->weighted) ups.push_back({h->sqrt_w, sw_s.data(), sizeof(double) * no});
+  for (auto& u : ups) {
+    if (u.bytes == 0) continue;
+    e = cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMemcpy(upload)"));
+  }
+  LmRecord r0{};
+  r0.cost = NAN;
+  r0.lambda = o.lambda0;
+  r0.nu = 2.0;
+  e = cudaMemcpy(h->rec, &r0, sizeof(r0), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMemcpy(record)"));
+
+  Topology& tp = h->tp;
+  tp.n_cams = nc;
+  tp.n_lms = nl;
+  tp.n_obs = no;
+  tp.n_obs_pad = h->n_o_pad;
+  tp.n_tiles = S.n_tiles;
+  tp.n_slots = S.n_slots;
+  tp.lm_seg = d_lm_seg;
+  tp.cam_of = d_cam_of;
+  tp.lm_of = d_lm_of;
+  tp.obs_meta = d_meta;
+  tp.tile_lm0 = d_tile_lm0;
+  tp.tile_slot0 = d_tile_slot0;
+  tp.slot_cam = d_slot_cam;
+  tp.slot_beg = d_slot_beg;
+  tp.cam_slot_ptr = d_cam_slot_ptr;
+  tp.cam_slot_list = d_cam_slot_list;
+  *out = h;
+  g_last_error.clear();
+  return BA_OK;
+}
+
+ba_status ba_set_options(ba_handle* h, const ba_options* o) {
+  if (!h || !o) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  std::string why;
+  if (!valid_options(*o, &why)) return fail(BA_ERR_INVALID_ARG, why);
+  const double lam_old = h->opts.lambda0;
+  h->opts = *o;
+  (void)lam_old;
+  return BA_OK;
+}
+
+ba_status ba_linearize(ba_handle* h, double* cost_out) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  seq_linearize(h);
+  ba_status st = check_launch(h, "linearize kernels");
+  if (st != BA_OK) return st;
+  h->linearized = true;
+  if (cost_out) {
+    launch_reduce_sum(h->block_cost, h->tp.n_tiles, h->scalars + 1, 1.0, h->stream);
+    h->launches += 1;
+    CK(cudaMemcpyAsync(h->h_scalar, h->scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *cost_out = h->h_scalar[0];
+  }
+  return BA_OK;
+}
+
+ba_status ba_solve_schur_power(ba_handle* h, double lambda, ba_series_info* info) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->linearized) return fail(BA_ERR_NOT_LINEARIZED, "ba_linearize has not been called");
+  if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(BA_ERR_INVALID_ARG, "lambda must be finite and > 0");
+  launch_set_scalar(h->scalars + 0, lambda, h->stream);
+  h->launches += 1;
+  ba_status st = run_solve(h, h->scalars + 0);
+  if (st != BA_OK) return st;
+  if (!info) return BA_OK;
+  CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SeriesState), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->h_flag, h->not_spd, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  info->inner_iters = h->h_st->m;
+  info->stopped = h->h_st->stopped;
+  info->stop_value = h->h_st->stop_value;
+  info->x_norm = h->h_st->x_norm;
+  info->lambda = lambda;
+  if (*h->h_flag) return fail(BA_ERR_NOT_SPD, "a damped block is not positive definite");
+  return BA_OK;
+}
+
+ba_status ba_lm_step(ba_handle* h, ba_step_info* info) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  cudaStream_t s = h->stream;
+  if (!h->cost_valid) {
+    seq_cost(h, rec_field(h->rec, offsetof(LmRecord, cost)));
+    h->cost_valid = true;
+  }
+  if (!h->linearized) {
+    seq_linearize(h);
+    h->linearized = true;
+  }
+  ba_status st = run_solve(h, rec_field(h->rec, offsetof(LmRecord, lambda)));
+  if (st != BA_OK) return st;
+  launch_cam_prepare(h->cams, h->x, h->n_c, h->prep_trial, h->cams_trial, s);
+  launch_cost(h->tp, h->prep_trial, h->lms, h->dx_l, h->obs, h->sqrt_w, h->block_cost, s);
+  launch_lm_decide(h->block_cost, cost_blocks(h->tp), h->block_pred, h->tp.n_tiles, h->rec, h->st,
+                   h->opts.func_tol, s);
+  launch_apply_step(h->rec, h->cams, h->cams_trial, h->lms, h->dx_l, h->n_c, h->n_l, s);
+  h->launches += 4;
+  st = check_launch(h, "LM step kernels");
+  if (st != BA_OK) return st;
+  CK(cudaMemcpyAsync(h->h_rec, h->rec, sizeof(LmRecord), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SeriesState), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->h_flag, h->not_spd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const LmRecord& R = *h->h_rec;
+  if (R.accepted) h->linearized = false;
+  if (info) {
+    info->cost_before = R.cost_before;
+    info->cost_after = R.cost_trial;
+    info->lambda = R.lambda_used;
+    info->gain_ratio = R.gain_ratio;
+    info->model_decrease = R.model_decrease;
+    info->stop_value = h->h_st->stop_value;
+    info->accepted = R.accepted;
+    info->inner_iters = h->h_st->m;
+    info->converged = R.converged;
+    info->iteration = R.iteration - 1;
+  }
+  if (!std::isfinite(R.cost_before)) return fail(BA_ERR_NONFINITE, "non-finite cost at the current state");
+  if (*h->h_flag) return fail(BA_ERR_NOT_SPD, "a damped block is not positive definite");
+  return BA_OK;
+}
+
+ba_status ba_lm_solve(ba_handle* h, ba_step_info* trace, int32_t* n_steps) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  int n = 0;
+  ba_status st = BA_OK;
+  for (int it = 0; it < h->opts.max_lm; ++it) {
+    ba_step_info si{};
+    st = ba_lm_step(h, &si);
+    if (trace) trace[n] = si;
+    ++n;
+    if (st != BA_OK || si.converged) break;
+  }
+  if (n_steps) *n_steps = n;
+  return st;
+}
+
+ba_status ba_cost(ba_handle* h, double* cost_out) {
+  if (!h || !cost_out) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  seq_cost(h, h->scalars + 1);
+  ba_status st = check_launch(h, "cost kernels");
+  if (st != BA_OK) return st;
+  CK(cudaMemcpyAsync(h->h_scalar, h->scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *cost_out = h->h_scalar[0];
+  return BA_OK;
+}
+
+ba_status ba_get_params(ba_handle* h, double* cams, double* lms, int32_t ptr_kind) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  if (ptr_kind != 0 && ptr_kind != 1) return fail(BA_ERR_INVALID_ARG, "ptr_kind must be 0 or 1");
+  CK(cudaStreamSynchronize(h->stream));
+  if (cams) {
+    if (ptr_kind == 1) CK(cudaMemcpy(cams, h->cams, sizeof(double) * h->n_c * 9, cudaMemcpyDeviceToDevice));
+    else CK(cudaMemcpy(cams, h->cams, sizeof(double) * h->n_c * 9, cudaMemcpyDeviceToHost));
+  }
+  if (lms) {
+    std::vector<double> li((size_t)h->n_l * 3), lo((size_t)h->n_l * 3);
+    CK(cudaMemcpy(li.data(), h->lms, sizeof(double) * li.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < h->n_l; ++i)
+      for (int k = 0; k < 3; ++k) lo[(size_t)h->sched.lm_order[i] * 3 + k] = li[(size_t)i * 3 + k];
+    ba_status st = copy_out(lms, lo.data(), sizeof(double) * lo.size(), ptr_kind);
+    if (st != BA_OK) return st;
+  }
+  return BA_OK;
+}
+
+ba_status ba_set_params(ba_handle* h, const double* cams, const double* lms, int32_t ptr_kind) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  if (ptr_kind != 0 && ptr_kind != 1) return fail(BA_ERR_INVALID_ARG, "ptr_kind must be 0 or 1");
+  std::vector<double> c, l;
+  if (cams) copy_in(c, cams, (size_t)h->n_c * 9, ptr_kind);
+  if (lms) copy_in(l, lms, (size_t)h->n_l * 3, ptr_kind);
+  for (double v : c) if (!std::isfinite(v)) return fail(BA_ERR_NONFINITE, "non-finite camera parameter");
+  for (double v : l) if (!std::isfinite(v)) return fail(BA_ERR_NONFINITE, "non-finite landmark");
+  CK(cudaStreamSynchronize(h->stream));
+  if (cams) CK(cudaMemcpy(h->cams, c.data(), sizeof(double) * c.size(), cudaMemcpyHostToDevice));
+  if (lms) {
+    std::vector<double> li(l.size());
+    for (int i = 0; i < h->n_l; ++i)
+      for (int k = 0; k < 3; ++k) li[(size_t)i * 3 + k] = l[(size_t)h->sched.lm_order[i] * 3 + k];
+    CK(cudaMemcpy(h->lms, li.data(), sizeof(double) * li.size(), cudaMemcpyHostToDevice));
+  }
+  h->linearized = false;
+  h->cost_valid = false;
+  return BA_OK;
+}
+
+ba_status ba_get_step(ba_handle* h, double* dx_p, double* dx_l, int32_t ptr_kind) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  if (ptr_kind != 0 && ptr_kind != 1) return fail(BA_ERR_INVALID_ARG, "ptr_kind must be 0 or 1");
+  CK(cudaStreamSynchronize(h->stream));
+  if (dx_p) {
+    if (ptr_kind == 1) CK(cudaMemcpy(dx_p, h->x, sizeof(double) * h->n_c * 9, cudaMemcpyDeviceToDevice));
+    else CK(cudaMemcpy(dx_p, h->x, sizeof(double) * h->n_c * 9, cudaMemcpyDeviceToHost));
+  }
+  if (dx_l) {
+    std::vector<double> li((size_t)h->n_l * 3), lo((size_t)h->n_l * 3);
+    CK(cudaMemcpy(li.data(), h->dx_l, sizeof(double) * li.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < h->n_l; ++i)
+      for (int k = 0; k < 3; ++k) lo[(size_t)h->sched.lm_order[i] * 3 + k] = li[(size_t)i * 3 + k];
+    ba_status st = copy_out(dx_l, lo.data(), sizeof(double) * lo.size(), ptr_kind);
+    if (st != BA_OK) return st;
+  }
+  return BA_OK;
+}
+
+ba_status ba_get_linearization(ba_handle* h, double* r, double* Jp, double* Jl, int32_t ptr_kind) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->linearized) return fail(BA_ERR_NOT_LINEARIZED, "no current linearisation");
+  if (ptr_kind != 0 && ptr_kind != 1) return fail(BA_ERR_INVALID_ARG, "ptr_kind must be 0 or 1");
+  CK(cudaStreamSynchronize(h->stream));
+  const size_t pad = (size_t)h->n_o_pad, no = (size_t)h->n_o;
+  std::vector<double> Jd(24 * pad), rd(2 * pad);
+  if (h->f32()) {
+    std::vector<float> Jf(24 * pad), rf(2 * pad);
+    CK(cudaMemcpy(Jf.data(), h->J, sizeof(float) * Jf.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(rf.data(), h->r, sizeof(float) * rf.size(), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < Jf.size(); ++i) Jd[i] = Jf[i];
+    for (size_t i = 0; i < rf.size(); ++i) rd[i] = rf[i];
+  } else {
+    CK(cudaMemcpy(Jd.data(), h->J, sizeof(double) * Jd.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(rd.data(), h->r, sizeof(double) * rd.size(), cudaMemcpyDeviceToHost));
+  }
+  std::vector<double> ro(no * 2), jpo(no * 18), jlo(no * 6);
+  for (size_t o = 0; o < no; ++o) {
+    const size_t c = (size_t)h->sched.obs_order[o];
+    for (int i = 0; i < 2; ++i) ro[c * 2 + i] = rd[i * pad + o];
+    for (int p = 0; p < 18; ++p) jpo[c * 18 + p] = Jd[p * pad + o];
+    for (int p = 0; p < 6; ++p) jlo[c * 6 + p] = Jd[(18 + p) * pad + o];
+  }
+  ba_status st;
+  if (r && (st = copy_out(r, ro.data(), sizeof(double) * ro.size(), ptr_kind)) != BA_OK) return st;
+  if (Jp && (st = copy_out(Jp, jpo.data(), sizeof(double) * jpo.size(), ptr_kind)) != BA_OK) return st;
+  if (Jl && (st = copy_out(Jl, jlo.data(), sizeof(double) * jlo.size(), ptr_kind)) != BA_OK) return st;
+  return BA_OK;
+}
+
+ba_status ba_get_blocks(ba_handle* h, double* U, double* V, double* b_p, double* b_l, int32_t ptr_kind) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->linearized) return fail(BA_ERR_NOT_LINEARIZED, "no current linearisation");
+  if (ptr_kind != 0 && ptr_kind != 1) return fail(BA_ERR_INVALID_ARG, "ptr_kind must be 0 or 1");
+  CK(cudaStreamSynchronize(h->stream));
+  const int nc = h->n_c, nl = h->n_l;
+  ba_status st;
+  if (U) {
+    std::vector<double> u45((size_t)nc * 45), u((size_t)nc * 81);
+    CK(cudaMemcpy(u45.data(), h->U45, sizeof(double) * u45.size(), cudaMemcpyDeviceToHost));
+    for (int c = 0; c < nc; ++c) {
+      int idx = 0;
+      for (int i = 0; i < 9; ++i)
+        for (int j = i; j < 9; ++j, ++idx) {
+          u[(size_t)c * 81 + i * 9 + j] = u45[(size_t)c * 45 + idx];
+          u[(size_t)c * 81 + j * 9 + i] = u45[(size_t)c * 45 + idx];
+        }
+    }
+    if ((st = copy_out(U, u.data(), sizeof(double) * u.size(), ptr_kind)) != BA_OK) return st;
+  }
+  if (b_p) {
+    std::vector<double> b((size_t)nc * 9);
+    CK(cudaMemcpy(b.data(), h->b_p, sizeof(double) * b.size(), cudaMemcpyDeviceToHost));
+    if ((st = copy_out(b_p, b.data(), sizeof(double) * b.size(), ptr_kind)) != BA_OK) return st;
+  }
+  if (V) {
+    std::vector<double> v6((size_t)nl * 6), v((size_t)nl * 9);
+    CK(cudaMemcpy(v6.data(), h->V, sizeof(double) * v6.size(), cudaMemcpyDeviceToHost));
+    static const int map[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
+    for (int i = 0; i < nl; ++i) {
+      const size_t c = (size_t)h->sched.lm_order[i];
+      for (int k = 0; k < 9; ++k) v[c * 9 + k] = v6[(size_t)i * 6 + map[k]];
+    }
+    if ((st = copy_out(V, v.data(), sizeof(double) * v.size(), ptr_kind)) != BA_OK) return st;
+  }
+  if (b_l) {
+    std::vector<double> bi((size_t)nl * 3), bo((size_t)nl * 3);
+    CK(cudaMemcpy(bi.data(), h->b_l, sizeof(double) * bi.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < nl; ++i)
+      for (int k = 0; k < 3; ++k) bo[(size_t)h->sched.lm_order[i] * 3 + k] = bi[(size_t)i * 3 + k];
+    if ((st = copy_out(b_l, bo.data(), sizeof(double) * bo.size(), ptr_kind)) != BA_OK) return st;
+  }
+  return BA_OK;
+}
+
+ba_status ba_get_lm_state(ba_handle* h, double* lambda, double* nu, int32_t* iteration, double* cost) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  CK(cudaMemcpyAsync(h->h_rec, h->rec, sizeof(LmRecord), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (lambda) *lambda = h->h_rec->lambda;
+  if (nu) *nu = h->h_rec->nu;
+  if (iteration) *iteration = h->h_rec->iteration;
+  if (cost) *cost = h->cost_valid ? h->h_rec->cost : NAN;
+  return BA_OK;
+}
+
+ba_status ba_set_lm_state(ba_handle* h, double lambda, double nu, int32_t iteration) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  if (!(lambda > 0.0) || !std::isfinite(lambda) || !(nu >= 1.0) || !std::isfinite(nu) || iteration < 0)
+    return fail(BA_ERR_INVALID_ARG, "need lambda > 0, nu >= 1, iteration >= 0");
+  CK(cudaMemcpyAsync(h->h_rec, h->rec, sizeof(LmRecord), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  LmRecord r = *h->h_rec;
+  r.lambda = lambda;
+  r.nu = nu;
+  r.iteration = iteration;
+  *h->h_rec = r;
+  CK(cudaMemcpyAsync(h->rec, h->h_rec, sizeof(LmRecord), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return BA_OK;
+}
+
+ba_status ba_memory_footprint(ba_handle* h, uint64_t* bytes) {
+  if (!h || !bytes) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  *bytes = (uint64_t)h->arena_bytes;
+  return BA_OK;
+}
+
+ba_status ba_kernel_launches(ba_handle* h, uint64_t* count) {
+  if (!h || !count) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  *count = h->launches;
+  return BA_OK;
+}
+
+const char* ba_status_string(ba_status s) {
+  switch (s) {
+    case BA_OK: return "BA_OK";
+    case BA_ERR_INVALID_ARG: return "BA_ERR_INVALID_ARG";
+    case BA_ERR_CUDA: return "BA_ERR_CUDA";
+    case BA_ERR_OOM: return "BA_ERR_OOM";
+    case BA_ERR_NOT_SPD: return "BA_ERR_NOT_SPD";
+    case BA_ERR_NONFINITE: return "BA_ERR_NONFINITE";
+    case BA_ERR_NOT_LINEARIZED: return "BA_ERR_NOT_LINEARIZED";
+    case BA_ERR_TIMEOUT: return "BA_ERR_TIMEOUT";
+  }
+  return "unknown status";
+}
+
+const char* ba_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

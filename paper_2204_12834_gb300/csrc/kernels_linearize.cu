@@ -1,0 +1,466 @@
+// Linearisation-side kernels of libpoba (sm_103a):
+//   cam_prepare      per camera: R(w), the rotation-derivative matrix G, t, f, k1, k2
+//   linearize        per observation: BAL residual r (Sec. 4) and its Jacobians J_p (2x9),
+//                    J_l (2x3) by the analytic chain rule; fused with the landmark blocks
+//                    V = J_l^T J_l, b_l = J_l^T r and the per-tile camera sums of
+//                    J_p^T J_p, J_p^T r (Sec. 4.1, eq. `normal`)
+//   lin_camera_reduce per camera: U = J_p^T J_p (45 packed), b_p = J_p^T r across tiles
+//   damp_invert      U_lambda, V_lambda (Sec. 4.1) and their Cholesky inverses in float64
+//   cost             F(x) = 1/2 sum w ||r||^2 in float64 (Sec. 4), fixed-order block sums
+//
+// Camera model (BAL convention): P = R(w) X + t, p = -P_xy / P_z,
+// pi = f (1 + k1 |p|^2 + k2 |p|^4) p, r = pi - obs.  With the left Jacobian G of SO(3),
+// d(R(w) X)/dw = -[R X]x G; for |w|^2 below machine epsilon R = I + [w]x and
+// d(R X)/dw = -[X]x.
+#include <cfloat>
+#include <cmath>
+
+#include "poba_internal.cuh"
+#include "tile_common.cuh"
+
+namespace poba {
+
+// ---------------------------------------------------------------------------------------
+__global__ void cam_prepare_kernel(const double* __restrict__ cams, const double* __restrict__ dx_p,
+                                   int n_cams, double* __restrict__ prep,
+                                   double* __restrict__ cams_out) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cams) return;
+  double p[9];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) p[j] = cams[c * 9 + j] + (dx_p ? dx_p[c * 9 + j] : 0.0);
+  if (cams_out) {
+#pragma unroll
+    for (int j = 0; j < 9; ++j) cams_out[c * 9 + j] = p[j];
+  }
+  const double w0 = p[0], w1 = p[1], w2 = p[2];
+  const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+  double R[9], G[9], first;
+  if (th2 < DBL_EPSILON) {
+    R[0] = 1.0; R[1] = -w2; R[2] = w1;
+    R[3] = w2;  R[4] = 1.0; R[5] = -w0;
+    R[6] = -w1; R[7] = w0;  R[8] = 1.0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) G[j] = (j % 4 == 0) ? 1.0 : 0.0;
+    first = 1.0;
+  } else {
+    const double th = sqrt(th2);
+    double s, co;
+    sincos(th, &s, &co);
+    const double hs = sin(0.5 * th);
+    const double omc = 2.0 * hs * hs;  // 1 - cos(th) without cancellation
+    const double k0 = w0 / th, k1 = w1 / th, k2 = w2 / th;
+    R[0] = co + omc * k0 * k0;      R[1] = -s * k2 + omc * k0 * k1; R[2] = s * k1 + omc * k0 * k2;
+    R[3] = s * k2 + omc * k0 * k1;  R[4] = co + omc * k1 * k1;      R[5] = -s * k0 + omc * k1 * k2;
+    R[6] = -s * k1 + omc * k0 * k2; R[7] = s * k0 + omc * k1 * k2;  R[8] = co + omc * k2 * k2;
+    // G = I + a [w]x + b [w]x^2, a = (1 - cos th)/th^2, b = (th - sin th)/th^3;
+    // [w]x^2 = w w^T - th^2 I.  b by its Taylor series for small th (cancellation).
+    const double a = omc / th2;
+    const double b = (th < 1e-2) ? (1.0 / 6.0 - th2 / 120.0 + th2 * th2 / 5040.0)
+                                 : (th - s) / (th2 * th);
+    const double W[9] = {0.0, -w2, w1, w2, 0.0, -w0, -w1, w0, 0.0};
+    const double ww[3] = {w0, w1, w2};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        G[i * 3 + j] = (i == j ? 1.0 - b * th2 : 0.0) + a * W[i * 3 + j] + b * ww[i] * ww[j];
+    first = 0.0;
+  }
+  double* q = prep + (size_t)c * kCamPrep;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) q[j] = R[j];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) q[9 + j] = G[j];
+  q[18] = p[3]; q[19] = p[4]; q[20] = p[5];
+  q[21] = p[6]; q[22] = p[7]; q[23] = p[8];
+  q[24] = first;
+}
+
+void launch_cam_prepare(const double* cams, const double* dx_p, int n_cams, double* prep,
+                        double* cams_out, cudaStream_t s) {
+  int threads = 128, blocks = (n_cams + threads - 1) / threads;
+  cam_prepare_kernel<<<blocks, threads, 0, s>>>(cams, dx_p, n_cams, prep, cams_out);
+}
+
+// ---------------------------------------------------------------------------------------
+// Packed index of entry (i, j), i <= j, of a symmetric 9x9 matrix stored row by row.
+__host__ __device__ constexpr int packed9(int i, int j) { return i * 9 - (i * (i - 1)) / 2 + (j - i); }
+__host__ __device__ constexpr int packed_row(int idx) {
+  int i = 0;
+  while (idx >= 9 - i) { idx -= 9 - i; ++i; }
+  return i;
+}
+__host__ __device__ constexpr int packed_col(int idx) {
+  int i = 0;
+  while (idx >= 9 - i) { idx -= 9 - i; ++i; }
+  return i + idx;
+}
+
+// Entry IDX of the per-observation camera contribution: packed (J_p^T J_p)_{ij} for IDX < 45,
+// else (J_p^T r)_j.  Resolved at compile time.
+template <int IDX, typename T>
+__device__ __forceinline__ T lin_entry(const T (&jp)[18], const T (&rr)[2]) {
+  if constexpr (IDX < 45) {
+    constexpr int i = packed_row(IDX), j = packed_col(IDX);
+    return jp[i] * jp[j] + jp[9 + i] * jp[9 + j];
+  } else {
+    constexpr int j = IDX - 45;
+    return jp[j] * rr[0] + jp[9 + j] * rr[1];
+  }
+}
+
+// One round of 9 camera values: stage at the observation's camera-sorted position, then sum
+// per slot into partial[slot * 54 + ROUND * 9 + k].
+template <int ROUND, typename T>
+__device__ __forceinline__ void lin_round(bool active, const T (&jp)[18], const T (&rr)[2], int pos,
+                                          T (*sg)[9], int ns, int n, const uint16_t* sbeg,
+                                          T* partial_tile) {
+  if (active) {
+    sg[pos][0] = lin_entry<ROUND * 9 + 0>(jp, rr);
+    sg[pos][1] = lin_entry<ROUND * 9 + 1>(jp, rr);
+    sg[pos][2] = lin_entry<ROUND * 9 + 2>(jp, rr);
+    sg[pos][3] = lin_entry<ROUND * 9 + 3>(jp, rr);
+    sg[pos][4] = lin_entry<ROUND * 9 + 4>(jp, rr);
+    sg[pos][5] = lin_entry<ROUND * 9 + 5>(jp, rr);
+    sg[pos][6] = lin_entry<ROUND * 9 + 6>(jp, rr);
+    sg[pos][7] = lin_entry<ROUND * 9 + 7>(jp, rr);
+    sg[pos][8] = lin_entry<ROUND * 9 + 8>(jp, rr);
+  }
+  __syncthreads();
+  slot_sums<T, T>(sg, ns, n, sbeg, partial_tile + ROUND * 9, kLinVals);
+  __syncthreads();
+}
+
+// Residual and Jacobians of one observation in precision T.
+template <typename T>
+__device__ __forceinline__ void bal_residual_jacobian(const double* __restrict__ q, const double X0d,
+                                                      const double X1d, const double X2d,
+                                                      const double2 ob, T sw, T (&jp)[18],
+                                                      T (&jl)[6], T (&r)[2]) {
+  const T R[9] = {(T)q[0], (T)q[1], (T)q[2], (T)q[3], (T)q[4], (T)q[5], (T)q[6], (T)q[7], (T)q[8]};
+  const T G[9] = {(T)q[9], (T)q[10], (T)q[11], (T)q[12], (T)q[13], (T)q[14], (T)q[15], (T)q[16], (T)q[17]};
+  const T t0 = (T)q[18], t1 = (T)q[19], t2 = (T)q[20];
+  const T f = (T)q[21], k1 = (T)q[22], k2 = (T)q[23];
+  const bool first = q[24] != 0.0;
+  const T X0 = (T)X0d, X1 = (T)X1d, X2 = (T)X2d;
+  const T RX0 = R[0] * X0 + R[1] * X1 + R[2] * X2;
+  const T RX1 = R[3] * X0 + R[4] * X1 + R[5] * X2;
+  const T RX2 = R[6] * X0 + R[7] * X1 + R[8] * X2;
+  const T P0 = RX0 + t0, P1 = RX1 + t1, P2 = RX2 + t2;
+  const T Y0 = first ? X0 : RX0, Y1 = first ? X1 : RX1, Y2 = first ? X2 : RX2;
+  // D = dP/dw = -[Y]x G
+  T D[9];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    D[0 * 3 + j] = Y2 * G[3 + j] - Y1 * G[6 + j];
+    D[1 * 3 + j] = Y0 * G[6 + j] - Y2 * G[0 + j];
+    D[2 * 3 + j] = Y1 * G[0 + j] - Y0 * G[3 + j];
+  }
+  const T iz = (T)1 / P2;
+  const T px = -P0 * iz, py = -P1 * iz;
+  const T n2 = px * px + py * py;
+  const T rad = (T)1 + n2 * (k1 + k2 * n2);
+  const T drad = k1 + (T)2 * k2 * n2;
+  // M = f (rad I + 2 drad p p^T);  A = dpi/dP = -iz M [I | p]
+  const T m00 = f * (rad + (T)2 * drad * px * px);
+  const T m01 = f * ((T)2 * drad * px * py);
+  const T m11 = f * (rad + (T)2 * drad * py * py);
+  T A[6];
+  A[0] = -iz * m00; A[1] = -iz * m01; A[2] = -iz * (m00 * px + m01 * py);
+  A[3] = -iz * m01; A[4] = -iz * m11; A[5] = -iz * (m01 * px + m11 * py);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      jp[i * 9 + j] = sw * (A[i * 3 + 0] * D[0 + j] + A[i * 3 + 1] * D[3 + j] + A[i * 3 + 2] * D[6 + j]);
+      jp[i * 9 + 3 + j] = sw * A[i * 3 + j];
+      jl[i * 3 + j] = sw * (A[i * 3 + 0] * R[0 + j] + A[i * 3 + 1] * R[3 + j] + A[i * 3 + 2] * R[6 + j]);
+    }
+  }
+  const T pc[2] = {px, py};
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    jp[i * 9 + 6] = sw * rad * pc[i];
+    jp[i * 9 + 7] = sw * f * n2 * pc[i];
+    jp[i * 9 + 8] = sw * f * n2 * n2 * pc[i];
+  }
+  r[0] = sw * (f * rad * px - (T)ob.x);
+  r[1] = sw * (f * rad * py - (T)ob.y);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileObs) linearize_kernel(
+    Topology tp, const double* __restrict__ prep, const double* __restrict__ lms,
+    const double2* __restrict__ obs, const double* __restrict__ sqrt_w, T* __restrict__ J,
+    T* __restrict__ r, double* __restrict__ V, double* __restrict__ b_l, T* __restrict__ partial,
+    double* __restrict__ block_cost) {
+  __shared__ T s9[kTileObs][9];
+  __shared__ T sg[kTileObs][9];
+  __shared__ uint16_t sbeg[kTileObs];
+  __shared__ double sred[kTileObs / 32];
+
+  const int tile = blockIdx.x, tid = threadIdx.x;
+  const int L0 = tp.tile_lm0[tile], L1 = tp.tile_lm0[tile + 1];
+  const int o0 = tp.lm_seg[L0], n = tp.lm_seg[L1] - o0;
+  const int S0 = tp.tile_slot0[tile], ns = tp.tile_slot0[tile + 1] - S0;
+  for (int i = tid; i < ns; i += blockDim.x) sbeg[i] = tp.slot_beg[S0 + i];
+
+  T jp[18], jl[6], rr[2];
+  int pos = 0;
+  double cost = 0.0;
+  const bool active = tid < n;
+  if (active) {
+    const int o = o0 + tid;
+    const int c = tp.cam_of[o], l = tp.lm_of[o];
+    pos = tp.obs_meta[o] & 0xff;
+    const T sw = sqrt_w ? (T)sqrt_w[o] : (T)1;
+    bal_residual_jacobian<T>(prep + (size_t)c * kCamPrep, lms[l * 3 + 0], lms[l * 3 + 1],
+                             lms[l * 3 + 2], obs[o], sw, jp, jl, rr);
+    const size_t pad = (size_t)tp.n_obs_pad;
+#pragma unroll
+    for (int p = 0; p < 18; ++p) J[p * pad + o] = jp[p];
+#pragma unroll
+    for (int p = 0; p < 6; ++p) J[(18 + p) * pad + o] = jl[p];
+    r[o] = rr[0];
+    r[pad + o] = rr[1];
+    cost = 0.5 * ((double)rr[0] * (double)rr[0] + (double)rr[1] * (double)rr[1]);
+    // landmark contributions: J_l^T J_l (6 unique) and J_l^T r (3)
+    s9[tid][0] = jl[0] * jl[0] + jl[3] * jl[3];
+    s9[tid][1] = jl[0] * jl[1] + jl[3] * jl[4];
+    s9[tid][2] = jl[0] * jl[2] + jl[3] * jl[5];
+    s9[tid][3] = jl[1] * jl[1] + jl[4] * jl[4];
+    s9[tid][4] = jl[1] * jl[2] + jl[4] * jl[5];
+    s9[tid][5] = jl[2] * jl[2] + jl[5] * jl[5];
+    s9[tid][6] = jl[0] * rr[0] + jl[3] * rr[1];
+    s9[tid][7] = jl[1] * rr[0] + jl[4] * rr[1];
+    s9[tid][8] = jl[2] * rr[0] + jl[5] * rr[1];
+  }
+  __syncthreads();
+  // per-landmark sums (float32 inside the segment in FP32-bulk mode)
+  if (tid < L1 - L0) {
+    const int l = L0 + tid;
+    const int a = tp.lm_seg[l] - o0, b = tp.lm_seg[l + 1] - o0;
+    T acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = (T)0;
+    for (int q = a; q < b; ++q) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) acc[k] += s9[q][k];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) V[(size_t)l * 6 + k] = (double)acc[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) b_l[(size_t)l * 3 + k] = (double)acc[6 + k];
+  }
+  // camera contributions in 6 rounds of 9 values: 45 packed J_p^T J_p entries, then J_p^T r
+  lin_round<0>(active, jp, rr, pos, sg, ns, n, sbeg, partial + (size_t)S0 * kLinVals);
+  lin_round<1>(active, jp, rr, pos, sg, ns, n, sbeg, partial + (size_t)S0 * kLinVals);
+  lin_round<2>(active, jp, rr, pos, sg, ns, n, sbeg, partial + (size_t)S0 * kLinVals);
+  lin_round<3>(active, jp, rr, pos, sg, ns, n, sbeg, partial + (size_t)S0 * kLinVals);
+  lin_round<4>(active, jp, rr, pos, sg, ns, n, sbeg, partial + (size_t)S0 * kLinVals);
+  lin_round<5>(active, jp, rr, pos, sg, ns, n, sbeg, partial + (size_t)S0 * kLinVals);
+  // block cost (fixed order)
+  const double tot = block_sum_fixed(cost, sred);
+  if (tid == 0 && block_cost) block_cost[tile] = tot;
+}
+
+template <typename T>
+void launch_linearize(const Topology& tp, const double* prep, const double* lms,
+                      const double2* obs, const double* sqrt_w, T* J, T* r, double* V,
+                      double* b_l, T* partial, double* block_cost, cudaStream_t s) {
+  linearize_kernel<T><<<tp.n_tiles, kTileObs, 0, s>>>(tp, prep, lms, obs, sqrt_w, J, r, V, b_l,
+                                                      partial, block_cost);
+}
+template void launch_linearize<double>(const Topology&, const double*, const double*,
+                                       const double2*, const double*, double*, double*, double*,
+                                       double*, double*, double*, cudaStream_t);
+template void launch_linearize<float>(const Topology&, const double*, const double*,
+                                      const double2*, const double*, float*, float*, double*,
+                                      double*, float*, double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------------------
+// Per camera: U (45 packed) and b_p (9) summed over the camera's slots in slot order.
+template <typename PT>
+__global__ void lin_camera_reduce_kernel(Topology tp, const PT* __restrict__ partial,
+                                         double* __restrict__ U45, double* __restrict__ b_p) {
+  const int per = kLinVals;
+  const int c = blockIdx.x * 4 + threadIdx.x / per;
+  const int k = threadIdx.x % per;
+  if (c >= tp.n_cams) return;
+  double acc = 0.0;
+  for (int s = tp.cam_slot_ptr[c]; s < tp.cam_slot_ptr[c + 1]; ++s)
+    acc += (double)partial[(size_t)tp.cam_slot_list[s] * per + k];
+  if (k < 45) U45[(size_t)c * 45 + k] = acc;
+  else b_p[(size_t)c * 9 + (k - 45)] = acc;
+}
+
+template <typename PT>
+void launch_lin_camera_reduce(const Topology& tp, const PT* partial, double* U45, double* b_p,
+                              cudaStream_t s) {
+  const int blocks = (tp.n_cams + 3) / 4;
+  lin_camera_reduce_kernel<PT><<<blocks, 4 * kLinVals, 0, s>>>(tp, partial, U45, b_p);
+}
+template void launch_lin_camera_reduce<double>(const Topology&, const double*, double*, double*, cudaStream_t);
+template void launch_lin_camera_reduce<float>(const Topology&, const float*, double*, double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------------------
+// Damping (reading of D: D^T D = diag(J^T J) clamped to [1e-6, 1e32], or D = I) and block
+// Cholesky inverses A^-1 = L^-T L^-1 in float64.  Blocks [0, cam_blocks) handle cameras, the
+// rest landmarks.
+constexpr double kDampMin = 1e-6, kDampMax = 1e32;
+
+__device__ __forceinline__ double damp_diag(double d, double lam, int mode) {
+  return mode == 0 ? lam * fmin(fmax(d, kDampMin), kDampMax) : lam;
+}
+
+__global__ void damp_invert_kernel(Topology tp, const double* __restrict__ U45,
+                                   const double* __restrict__ V, const double* __restrict__ lambda,
+                                   int mode, int cam_blocks, double* __restrict__ Uinv,
+                                   double* __restrict__ Vinv, float* __restrict__ Vinv_f,
+                                   int32_t* __restrict__ not_spd) {
+  const double lam = *lambda;
+  if ((int)blockIdx.x < cam_blocks) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= tp.n_cams) return;
+    double A[9][9];
+    for (int i = 0; i < 9; ++i)
+      for (int j = i; j < 9; ++j) {
+        const double v = U45[(size_t)c * 45 + packed9(i, j)];
+        A[i][j] = v;
+        A[j][i] = v;
+      }
+    for (int i = 0; i < 9; ++i) A[i][i] += damp_diag(A[i][i], lam, mode);
+    // Cholesky A = L L^T (L in the lower triangle of A)
+    bool ok = true;
+    for (int j = 0; j < 9; ++j) {
+      double d = A[j][j];
+      for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+      if (!(d > 0.0) || !isfinite(d)) { ok = false; d = 1.0; }
+      const double ljj = sqrt(d);
+      A[j][j] = ljj;
+      for (int i = j + 1; i < 9; ++i) {
+        double v = A[i][j];
+        for (int k = 0; k < j; ++k) v -= A[i][k] * A[j][k];
+        A[i][j] = v / ljj;
+      }
+    }
+    if (!ok) atomicOr(not_spd, 1);
+    // M = L^-1 (lower triangular)
+    double M[9][9];
+    for (int j = 0; j < 9; ++j) {
+      for (int i = 0; i < j; ++i) M[i][j] = 0.0;
+      M[j][j] = 1.0 / A[j][j];
+      for (int i = j + 1; i < 9; ++i) {
+        double v = 0.0;
+        for (int k = j; k < i; ++k) v -= A[i][k] * M[k][j];
+        M[i][j] = v / A[i][i];
+      }
+    }
+    // Uinv = M^T M
+    double* out = Uinv + (size_t)c * 81;
+    for (int i = 0; i < 9; ++i)
+      for (int j = i; j < 9; ++j) {
+        double v = 0.0;
+        for (int k = j; k < 9; ++k) v += M[k][i] * M[k][j];
+        out[i * 9 + j] = v;
+        out[j * 9 + i] = v;
+      }
+  } else {
+    const int l = (blockIdx.x - cam_blocks) * blockDim.x + threadIdx.x;
+    if (l >= tp.n_lms) return;
+    const double* v = V + (size_t)l * 6;
+    const double a00 = v[0] + damp_diag(v[0], lam, mode), a01 = v[1], a02 = v[2];
+    const double a11 = v[3] + damp_diag(v[3], lam, mode), a12 = v[4];
+    const double a22 = v[5] + damp_diag(v[5], lam, mode);
+    bool ok = true;
+    double d0 = a00;
+    if (!(d0 > 0.0) || !isfinite(d0)) { ok = false; d0 = 1.0; }
+    const double l00 = sqrt(d0);
+    const double l10 = a01 / l00, l20 = a02 / l00;
+    double d1 = a11 - l10 * l10;
+    if (!(d1 > 0.0) || !isfinite(d1)) { ok = false; d1 = 1.0; }
+    const double l11 = sqrt(d1);
+    const double l21 = (a12 - l20 * l10) / l11;
+    double d2 = a22 - l20 * l20 - l21 * l21;
+    if (!(d2 > 0.0) || !isfinite(d2)) { ok = false; d2 = 1.0; }
+    const double l22 = sqrt(d2);
+    if (!ok) atomicOr(not_spd, 1);
+    // M = L^-1
+    const double m00 = 1.0 / l00, m11 = 1.0 / l11, m22 = 1.0 / l22;
+    const double m10 = -l10 * m00 / l11;
+    const double m21 = -l21 * m11 / l22;
+    const double m20 = -(l20 * m00 + l21 * m10) / l22;
+    // Vinv = M^T M, 6 unique entries [00 01 02 11 12 22]
+    double o[6];
+    o[0] = m00 * m00 + m10 * m10 + m20 * m20;
+    o[1] = m10 * m11 + m20 * m21;
+    o[2] = m20 * m22;
+    o[3] = m11 * m11 + m21 * m21;
+    o[4] = m21 * m22;
+    o[5] = m22 * m22;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Vinv[(size_t)l * 6 + k] = o[k];
+    if (Vinv_f) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) Vinv_f[(size_t)l * 6 + k] = (float)o[k];
+    }
+  }
+}
+
+void launch_damp_invert(const Topology& tp, const double* U45, const double* V,
+                        const double* lambda, int damping_mode, double* Uinv, double* Vinv,
+                        float* Vinv_f, int32_t* not_spd, cudaStream_t s) {
+  const int threads = 128;
+  const int cb = (tp.n_cams + threads - 1) / threads;
+  const int lb = (tp.n_lms + threads - 1) / threads;
+  damp_invert_kernel<<<cb + lb, threads, 0, s>>>(tp, U45, V, lambda, damping_mode, cb, Uinv, Vinv,
+                                                Vinv_f, not_spd);
+}
+
+// ---------------------------------------------------------------------------------------
+// Cost in float64 at (cameras prepared in `prep`, landmarks lms + dx_l).
+constexpr int kCostThreads = 256;
+
+int cost_blocks(const Topology& tp) {
+  int b = (tp.n_obs + kCostThreads - 1) / kCostThreads;
+  return b < 1 ? 1 : (b > 2048 ? 2048 : b);
+}
+
+__global__ void __launch_bounds__(kCostThreads) cost_kernel(
+    Topology tp, const double* __restrict__ prep, const double* __restrict__ lms,
+    const double* __restrict__ dx_l, const double2* __restrict__ obs,
+    const double* __restrict__ sqrt_w, double* __restrict__ block_sums) {
+  __shared__ double sred[kCostThreads / 32];
+  double acc = 0.0;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < tp.n_obs; o += gridDim.x * blockDim.x) {
+    const int c = tp.cam_of[o], l = tp.lm_of[o];
+    const double* q = prep + (size_t)c * kCamPrep;
+    double X0 = lms[l * 3 + 0], X1 = lms[l * 3 + 1], X2 = lms[l * 3 + 2];
+    if (dx_l) {
+      X0 += dx_l[l * 3 + 0];
+      X1 += dx_l[l * 3 + 1];
+      X2 += dx_l[l * 3 + 2];
+    }
+    const double P0 = q[0] * X0 + q[1] * X1 + q[2] * X2 + q[18];
+    const double P1 = q[3] * X0 + q[4] * X1 + q[5] * X2 + q[19];
+    const double P2 = q[6] * X0 + q[7] * X1 + q[8] * X2 + q[20];
+    const double px = -P0 / P2, py = -P1 / P2;
+    const double n2 = px * px + py * py;
+    const double rad = 1.0 + n2 * (q[22] + q[23] * n2);
+    const double2 ob = obs[o];
+    const double r0 = q[21] * rad * px - ob.x, r1 = q[21] * rad * py - ob.y;
+    double e = r0 * r0 + r1 * r1;
+    if (sqrt_w) e *= sqrt_w[o] * sqrt_w[o];
+    acc += e;
+  }
+  const double tot = block_sum_fixed(acc, sred);
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+void launch_cost(const Topology& tp, const double* prep, const double* lms, const double* dx_l,
+                 const double2* obs, const double* sqrt_w, double* block_sums, cudaStream_t s) {
+  cost_kernel<<<cost_blocks(tp), kCostThreads, 0, s>>>(tp, prep, lms, dx_l, obs, sqrt_w, block_sums);
+}
+
+}  // namespace poba

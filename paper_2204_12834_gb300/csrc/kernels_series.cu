@@ -1,0 +1,453 @@
+// Power-series kernels of libpoba (sm_103a), Sec. 4.3.
+//
+// With P = U^-1 W V^-1 W^T, W = J_p^T J_l, one series term t_i = P t_{i-1} is applied
+// matrix-free in two launches:
+//   tile_matvec (per tile of whole landmarks, one observation per thread):
+//     u_o = J_p,o t_c(o)                       (t staged per slot in shared memory)
+//     z_l = V_l^-1 sum_{o in l} J_l,o^T u_o    (landmark-segmented sum in shared memory)
+//     g_o = J_p,o^T (J_l,o z_l(o))             (J still in registers: one J read per term)
+//     partial[slot] = sum_{o in slot} g_o      (per-tile camera sums, fixed order)
+//   camera_step (per camera):
+//     y_c = sum over the camera's slots of partial; t_i = U_c^-1 y_c; x += t_i;
+//     ||t_i||^2, ||x(i)||^2 block sums; the last block applies the stop rule of eq.
+//     `qcriterion` and raises `done`, after which later launches return at once.
+// The same kernels with z_l = V_l^-1 b_l form b~ = b_p - W V^-1 b_l and x(0) = -U^-1 b~
+// (Sec. 4.2, eq. `x_approx` with m = 0); back-substitution (Sec. 4.2) reuses the first half
+// and also accumulates the model decrease 1/2||r||^2 - 1/2||r + J_p dx_p + J_l dx_l||^2.
+#include <cfloat>
+#include <cmath>
+
+#include "poba_internal.cuh"
+#include "tile_common.cuh"
+
+namespace poba {
+
+enum { kModeSeries = 0, kModeRhs = 1 };
+
+template <typename T>
+__device__ __forceinline__ void load_J(const T* __restrict__ J, size_t pad, int o, T (&jp)[18],
+                                       T (&jl)[6]) {
+#pragma unroll
+  for (int p = 0; p < 18; ++p) jp[p] = J[p * pad + o];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) jl[p] = J[(18 + p) * pad + o];
+}
+
+// z = Vinv s with Vinv stored as [00 01 02 11 12 22].
+template <typename T>
+__device__ __forceinline__ void apply_vinv(const T* __restrict__ vi, const T (&s)[3], T (&z)[3]) {
+  const T v0 = vi[0], v1 = vi[1], v2 = vi[2], v3 = vi[3], v4 = vi[4], v5 = vi[5];
+  z[0] = v0 * s[0] + v1 * s[1] + v2 * s[2];
+  z[1] = v1 * s[0] + v3 * s[1] + v4 * s[2];
+  z[2] = v2 * s[0] + v4 * s[1] + v5 * s[2];
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kTileObs) tile_matvec_kernel(
+    Topology tp, const T* __restrict__ J, const double* __restrict__ tvec,
+    const double* __restrict__ b_l, const T* __restrict__ Vinv, T* __restrict__ partial,
+    const SeriesState* __restrict__ st) {
+  if (MODE == kModeSeries && st->done) return;
+  __shared__ T tcam[kTileObs][9];
+  __shared__ T sv[kTileObs][3];
+  __shared__ T sg[kTileObs][9];
+  __shared__ uint16_t sbeg[kTileObs];
+
+  const int tile = blockIdx.x, tid = threadIdx.x;
+  const int L0 = tp.tile_lm0[tile], L1 = tp.tile_lm0[tile + 1];
+  const int o0 = tp.lm_seg[L0], n = tp.lm_seg[L1] - o0;
+  const int S0 = tp.tile_slot0[tile], ns = tp.tile_slot0[tile + 1] - S0;
+  if (MODE == kModeSeries) {
+    for (int i = tid; i < ns * 9; i += blockDim.x) {
+      const int s = i / 9, k = i - s * 9;
+      tcam[s][k] = (T)tvec[(size_t)tp.slot_cam[S0 + s] * 9 + k];
+    }
+  }
+  for (int i = tid; i < ns; i += blockDim.x) sbeg[i] = tp.slot_beg[S0 + i];
+  __syncthreads();
+
+  const bool active = tid < n;
+  const size_t pad = (size_t)tp.n_obs_pad;
+  T jp[18], jl[6];
+  int meta = 0;
+  if (active) {
+    const int o = o0 + tid;
+    meta = tp.obs_meta[o];
+    load_J(J, pad, o, jp, jl);
+    if (MODE == kModeSeries) {
+      const T* tc = tcam[meta >> 8];
+      T u0 = (T)0, u1 = (T)0;
+#pragma unroll
+      for (int j = 0; j < 9; ++j) {
+        u0 += jp[j] * tc[j];
+        u1 += jp[9 + j] * tc[j];
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) sv[tid][k] = jl[k] * u0 + jl[3 + k] * u1;
+    }
+  }
+  __syncthreads();
+  // landmark phase: z_l = V_l^-1 (sum of W^T t contributions, or b_l), written back per obs
+  if (tid < L1 - L0) {
+    const int l = L0 + tid;
+    const int a = tp.lm_seg[l] - o0, b = tp.lm_seg[l + 1] - o0;
+    T s[3];
+    if (MODE == kModeSeries) {
+      s[0] = s[1] = s[2] = (T)0;
+      for (int q = a; q < b; ++q) {
+        s[0] += sv[q][0];
+        s[1] += sv[q][1];
+        s[2] += sv[q][2];
+      }
+    } else {
+      s[0] = (T)b_l[(size_t)l * 3 + 0];
+      s[1] = (T)b_l[(size_t)l * 3 + 1];
+      s[2] = (T)b_l[(size_t)l * 3 + 2];
+    }
+    T z[3];
+    apply_vinv(Vinv + (size_t)l * 6, s, z);
+    for (int q = a; q < b; ++q) {
+      sv[q][0] = z[0];
+      sv[q][1] = z[1];
+      sv[q][2] = z[2];
+    }
+  }
+  __syncthreads();
+  // W z scatter: g_o = J_p^T (J_l z), staged at the camera-sorted position
+  if (active) {
+    const T z0 = sv[tid][0], z1 = sv[tid][1], z2 = sv[tid][2];
+    const T w0 = jl[0] * z0 + jl[1] * z1 + jl[2] * z2;
+    const T w1 = jl[3] * z0 + jl[4] * z1 + jl[5] * z2;
+    T* g = sg[meta & 0xff];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) g[j] = jp[j] * w0 + jp[9 + j] * w1;
+  }
+  __syncthreads();
+  slot_sums<T, T>(sg, ns, n, sbeg, partial + (size_t)S0 * 9, 9);
+}
+
+template <typename T>
+void launch_tile_rhs(const Topology& tp, const T* J, const double* b_l, const T* Vinv, T* partial,
+                     const SeriesState* st, cudaStream_t s) {
+  tile_matvec_kernel<T, kModeRhs><<<tp.n_tiles, kTileObs, 0, s>>>(tp, J, nullptr, b_l, Vinv,
+                                                                  partial, st);
+}
+
+template <typename T>
+void launch_tile_series(const Topology& tp, const T* J, const double* t, const T* Vinv,
+                        T* partial, const SeriesState* st, cudaStream_t s) {
+  tile_matvec_kernel<T, kModeSeries><<<tp.n_tiles, kTileObs, 0, s>>>(tp, J, t, nullptr, Vinv,
+                                                                     partial, st);
+}
+
+// ---------------------------------------------------------------------------------------
+// Back-substitution dx_l = -V^-1 (b_l + W^T dx_p) and the model decrease per tile.
+template <typename T>
+__global__ void __launch_bounds__(kTileObs) tile_backsub_kernel(
+    Topology tp, const T* __restrict__ J, const T* __restrict__ r, const double* __restrict__ x,
+    const double* __restrict__ b_l, const T* __restrict__ Vinv, double* __restrict__ dx_l,
+    double* __restrict__ block_pred) {
+  __shared__ T tcam[kTileObs][9];
+  __shared__ T sv[kTileObs][3];
+  __shared__ double sred[kTileObs / 32];
+
+  const int tile = blockIdx.x, tid = threadIdx.x;
+  const int L0 = tp.tile_lm0[tile], L1 = tp.tile_lm0[tile + 1];
+  const int o0 = tp.lm_seg[L0], n = tp.lm_seg[L1] - o0;
+  const int S0 = tp.tile_slot0[tile], ns = tp.tile_slot0[tile + 1] - S0;
+  for (int i = tid; i < ns * 9; i += blockDim.x) {
+    const int s = i / 9, k = i - s * 9;
+    tcam[s][k] = (T)x[(size_t)tp.slot_cam[S0 + s] * 9 + k];
+  }
+  __syncthreads();
+  const bool active = tid < n;
+  const size_t pad = (size_t)tp.n_obs_pad;
+  T jp[18], jl[6];
+  T u0 = (T)0, u1 = (T)0;
+  if (active) {
+    const int o = o0 + tid;
+    const int meta = tp.obs_meta[o];
+    load_J(J, pad, o, jp, jl);
+    const T* tc = tcam[meta >> 8];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      u0 += jp[j] * tc[j];
+      u1 += jp[9 + j] * tc[j];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sv[tid][k] = jl[k] * u0 + jl[3 + k] * u1;
+  }
+  __syncthreads();
+  if (tid < L1 - L0) {
+    const int l = L0 + tid;
+    const int a = tp.lm_seg[l] - o0, b = tp.lm_seg[l + 1] - o0;
+    T s[3] = {(T)b_l[(size_t)l * 3 + 0], (T)b_l[(size_t)l * 3 + 1], (T)b_l[(size_t)l * 3 + 2]};
+    for (int q = a; q < b; ++q) {
+      s[0] += sv[q][0];
+      s[1] += sv[q][1];
+      s[2] += sv[q][2];
+    }
+    T z[3];
+    apply_vinv(Vinv + (size_t)l * 6, s, z);
+    z[0] = -z[0];
+    z[1] = -z[1];
+    z[2] = -z[2];
+    dx_l[(size_t)l * 3 + 0] = (double)z[0];
+    dx_l[(size_t)l * 3 + 1] = (double)z[1];
+    dx_l[(size_t)l * 3 + 2] = (double)z[2];
+    for (int q = a; q < b; ++q) {
+      sv[q][0] = z[0];
+      sv[q][1] = z[1];
+      sv[q][2] = z[2];
+    }
+  }
+  __syncthreads();
+  double pred = 0.0;
+  if (active) {
+    const int o = o0 + tid;
+    const T z0 = sv[tid][0], z1 = sv[tid][1], z2 = sv[tid][2];
+    const double r0 = (double)r[o], r1 = (double)r[pad + o];
+    const double q0 = r0 + (double)u0 + (double)(jl[0] * z0 + jl[1] * z1 + jl[2] * z2);
+    const double q1 = r1 + (double)u1 + (double)(jl[3] * z0 + jl[4] * z1 + jl[5] * z2);
+    pred = (r0 * r0 + r1 * r1) - (q0 * q0 + q1 * q1);
+  }
+  const double tot = block_sum_fixed(pred, sred);
+  if (tid == 0) block_pred[tile] = tot;
+}
+
+template <typename T>
+void launch_tile_backsub(const Topology& tp, const T* J, const T* r, const double* x,
+                         const double* b_l, const T* Vinv, double* dx_l, double* block_pred,
+                         cudaStream_t s) {
+  tile_backsub_kernel<T><<<tp.n_tiles, kTileObs, 0, s>>>(tp, J, r, x, b_l, Vinv, dx_l, block_pred);
+}
+
+template void launch_tile_rhs<double>(const Topology&, const double*, const double*, const double*, double*, const SeriesState*, cudaStream_t);
+template void launch_tile_rhs<float>(const Topology&, const float*, const double*, const float*, float*, const SeriesState*, cudaStream_t);
+template void launch_tile_series<double>(const Topology&, const double*, const double*, const double*, double*, const SeriesState*, cudaStream_t);
+template void launch_tile_series<float>(const Topology&, const float*, const double*, const float*, float*, const SeriesState*, cudaStream_t);
+template void launch_tile_backsub<double>(const Topology&, const double*, const double*, const double*, const double*, const double*, double*, double*, cudaStream_t);
+template void launch_tile_backsub<float>(const Topology&, const float*, const float*, const double*, const double*, const float*, double*, double*, cudaStream_t);
+
+int tile_blocks(const Topology& tp) { return tp.n_tiles; }
+
+// ---------------------------------------------------------------------------------------
+// Camera step.  Block = kCamBlock cameras x 9 components.
+int camera_blocks(const Topology& tp) { return (tp.n_cams + kCamBlock - 1) / kCamBlock; }
+
+template <typename PT, int MODE>
+__global__ void __launch_bounds__(kCamBlock * 9) camera_step_kernel(
+    Topology tp, const PT* __restrict__ partial, const double* __restrict__ b_p,
+    const double* __restrict__ Uinv, double* __restrict__ x, double* __restrict__ t,
+    double* __restrict__ block_norms, SeriesState* __restrict__ st, int iter, double eps) {
+  if (MODE == kModeSeries && st->done) return;
+  __shared__ double ys[kCamBlock][9];
+  __shared__ double sred[(kCamBlock * 9 + 31) / 32];
+  __shared__ double sfin[2][kCamBlock * 9];
+  __shared__ int is_last;
+  const int tid = threadIdx.x;
+  const int cl = tid / 9, k = tid - cl * 9;
+  const int c = blockIdx.x * kCamBlock + cl;
+  const bool active = c < tp.n_cams;
+  double y = 0.0;
+  if (active) {
+    for (int s = tp.cam_slot_ptr[c]; s < tp.cam_slot_ptr[c + 1]; ++s)
+      y += (double)partial[(size_t)tp.cam_slot_list[s] * 9 + k];
+    if (MODE == kModeRhs) y = b_p[(size_t)c * 9 + k] - y;  // b~ = b_p - W V^-1 b_l
+  }
+  ys[cl][k] = y;
+  __syncthreads();
+  double tn2 = 0.0, xn2 = 0.0;
+  if (active) {
+    const double* ui = Uinv + (size_t)c * 81 + k * 9;
+    double v = 0.0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) v += ui[j] * ys[cl][j];
+    double xv;
+    if (MODE == kModeRhs) {
+      v = -v;  // x(0) = -U^-1 b~
+      xv = v;
+    } else {
+      xv = x[(size_t)c * 9 + k] + v;
+    }
+    x[(size_t)c * 9 + k] = xv;
+    t[(size_t)c * 9 + k] = v;
+    tn2 = v * v;
+    xn2 = xv * xv;
+  }
+  const double bt = block_sum_fixed(tn2, sred);
+  __syncthreads();
+  const double bx = block_sum_fixed(xn2, sred);
+  if (tid == 0) {
+    block_norms[blockIdx.x * 2 + 0] = bt;
+    block_norms[blockIdx.x * 2 + 1] = bx;
+    __threadfence();
+    const unsigned ticket = atomicAdd(&st->counter, 1u);
+    is_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // last block: fixed-order sum of all block norms, then the stop rule
+  double at = 0.0, ax = 0.0;
+  for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+    at += __ldcg(block_norms + b * 2 + 0);
+    ax += __ldcg(block_norms + b * 2 + 1);
+  }
+  sfin[0][tid] = at;
+  sfin[1][tid] = ax;
+  __syncthreads();
+  if (tid == 0) {
+    double T2 = 0.0, X2 = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) {
+      T2 += sfin[0][i];
+      X2 += sfin[1][i];
+    }
+    const double tn = sqrt(T2), xn = sqrt(X2);
+    st->t_norm = tn;
+    st->x_norm = xn;
+    st->m = iter;
+    if (MODE == kModeRhs) {
+      st->stop_value = INFINITY;
+      if (xn == 0.0) {
+        st->done = 1;
+        st->stopped = 1;
+      }
+    } else {
+      if (xn == 0.0) {
+        st->stop_value = 0.0;
+        st->done = 1;
+        st->stopped = 1;
+      } else {
+        const double sv = (double)(iter + 1) * tn / xn;  // eq. `qcriterion`
+        st->stop_value = sv;
+        if (sv < eps) {
+          st->done = 1;
+          st->stopped = 1;
+        }
+      }
+    }
+    st->counter = 0u;
+  }
+}
+
+template <typename PT>
+void launch_camera_rhs(const Topology& tp, const PT* partial, const double* b_p, const double* Uinv,
+                       double* x, double* t, double* block_norms, SeriesState* st, cudaStream_t s) {
+  camera_step_kernel<PT, kModeRhs><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(
+      tp, partial, b_p, Uinv, x, t, block_norms, st, 0, 0.0);
+}
+
+template <typename PT>
+void launch_camera_series(const Topology& tp, const PT* partial, const double* Uinv, double* x,
+                          double* t, double* block_norms, SeriesState* st, int iter, double eps,
+                          cudaStream_t s) {
+  camera_step_kernel<PT, kModeSeries><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(
+      tp, partial, nullptr, Uinv, x, t, block_norms, st, iter, eps);
+}
+
+template void launch_camera_rhs<double>(const Topology&, const double*, const double*, const double*, double*, double*, double*, SeriesState*, cudaStream_t);
+template void launch_camera_rhs<float>(const Topology&, const float*, const double*, const double*, double*, double*, double*, SeriesState*, cudaStream_t);
+template void launch_camera_series<double>(const Topology&, const double*, const double*, double*, double*, double*, SeriesState*, int, double, cudaStream_t);
+template void launch_camera_series<float>(const Topology&, const float*, const double*, double*, double*, double*, SeriesState*, int, double, cudaStream_t);
+
+// ---------------------------------------------------------------------------------------
+__global__ void series_reset_kernel(SeriesState* st) {
+  st->done = 0;
+  st->m = 0;
+  st->stopped = 0;
+  st->stop_value = INFINITY;
+  st->x_norm = 0.0;
+  st->t_norm = 0.0;
+  st->counter = 0u;
+}
+
+void launch_series_reset(SeriesState* st, cudaStream_t s) {
+  series_reset_kernel<<<1, 1, 0, s>>>(st);
+}
+
+__global__ void set_scalar_kernel(double* dst, double v) { *dst = v; }
+
+void launch_set_scalar(double* dst, double v, cudaStream_t s) { set_scalar_kernel<<<1, 1, 0, s>>>(dst, v); }
+
+// Fixed-order sum of n doubles into *out (one block).
+__global__ void __launch_bounds__(kReduceThreads) reduce_sum_kernel(const double* in, int n,
+                                                                     double* out, double scale) {
+  __shared__ double sred[kReduceThreads / 32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += in[i];
+  const double tot = block_sum_fixed(a, sred);
+  if (threadIdx.x == 0) *out = scale * tot;
+}
+
+void launch_reduce_sum(const double* in, int n, double* out, double scale, cudaStream_t s) {
+  reduce_sum_kernel<<<1, kReduceThreads, 0, s>>>(in, n, out, scale);
+}
+
+// ---------------------------------------------------------------------------------------
+// LM decision (Sec. 5.1): F(x + dx) and the model decrease from block sums, gain ratio,
+// accept iff F decreased and the model decrease is positive, lambda / nu update.
+constexpr double kLambdaMin = 1e-10, kLambdaMax = 1e32;
+
+__global__ void __launch_bounds__(kReduceThreads) lm_decide_kernel(
+    const double* block_cost, int n_cost, const double* block_pred, int n_pred, LmRecord* rec,
+    const SeriesState* st, double func_tol) {
+  __shared__ double sred[kReduceThreads / 32];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n_cost; i += blockDim.x) a += block_cost[i];
+  for (int i = threadIdx.x; i < n_pred; i += blockDim.x) b += block_pred[i];
+  const double F_new = 0.5 * block_sum_fixed(a, sred);
+  __syncthreads();
+  const double pred = 0.5 * block_sum_fixed(b, sred);
+  if (threadIdx.x != 0) return;
+  const double F = rec->cost;
+  const double actual = F - F_new;
+  const int accepted = (isfinite(F_new) && actual > 0.0 && pred > 0.0) ? 1 : 0;
+  const double rho = pred != 0.0 ? actual / pred : 0.0;
+  double lam = rec->lambda, nu = rec->nu;
+  rec->lambda_used = lam;
+  if (accepted) {
+    const double q = 2.0 * rho - 1.0;
+    lam *= fmax(1.0 / 3.0, 1.0 - q * q * q);
+    nu = 2.0;
+  } else {
+    lam *= nu;
+    nu *= 2.0;
+  }
+  rec->lambda = fmin(fmax(lam, kLambdaMin), kLambdaMax);
+  rec->nu = nu;
+  rec->cost_before = F;
+  rec->cost_trial = F_new;
+  rec->model_decrease = pred;
+  rec->gain_ratio = rho;
+  rec->accepted = accepted;
+  rec->converged = (accepted && actual / F < func_tol) ? 1 : 0;
+  rec->nonfinite = isfinite(F_new) ? 0 : 1;
+  if (accepted) rec->cost = F_new;
+  rec->iteration += 1;
+}
+
+void launch_lm_decide(const double* block_cost, int n_cost, const double* block_pred, int n_pred,
+                      LmRecord* rec, const SeriesState* st, double func_tol, cudaStream_t s) {
+  lm_decide_kernel<<<1, kReduceThreads, 0, s>>>(block_cost, n_cost, block_pred, n_pred, rec, st,
+                                                func_tol);
+}
+
+// x <- x + dx when the step was accepted (cameras already summed in cams_trial).
+__global__ void apply_step_kernel(const LmRecord* rec, double* cams, const double* cams_trial,
+                                  double* lms, const double* dx_l, int n_cams, int n_lms) {
+  if (!rec->accepted) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_cams * 9) cams[i] = cams_trial[i];
+  if (i < n_lms * 3) lms[i] += dx_l[i];
+}
+
+void launch_apply_step(const LmRecord* rec, double* cams, const double* cams_trial, double* lms,
+                       const double* dx_l, int n_cams, int n_lms, cudaStream_t s) {
+  const int n = n_cams * 9 > n_lms * 3 ? n_cams * 9 : n_lms * 3;
+  const int threads = 256;
+  apply_step_kernel<<<(n + threads - 1) / threads, threads, 0, s>>>(rec, cams, cams_trial, lms,
+                                                                    dx_l, n_cams, n_lms);
+}
+
+}  // namespace poba

@@ -1,0 +1,176 @@
+// Internal declarations of libpoba: device data layout, kernel launchers, host schedule.
+//
+// Data layout in HBM (all per-handle, one arena allocation):
+//   Observations are stored sorted by (internal landmark, camera).  Internal landmark order
+//   groups landmarks by their smallest observing camera so that a run of consecutive
+//   landmarks touches few cameras.  Consecutive landmarks are packed into tiles of at most
+//   kTileObs observations; a landmark never straddles two tiles (its "memory block" in the
+//   sense of Sec. 5, "Efficient storage").  Per tile, the distinct cameras form "slots"; the
+//   camera-keyed reductions (W y scatter and J_p^T J_p) sum per slot inside the tile and then
+//   per camera across the slots that camera owns (CSR cam_slot_ptr / cam_slot_list), so no
+//   global atomics are used and every sum has a fixed order.
+//
+//   Jacobians and residuals are structure-of-arrays planes of length n_obs_pad in the
+//   handle's bulk precision T:
+//     J[p * n_obs_pad + o], p = 0..17: J_p row-major (row i, col j at p = 9 i + j)
+//                           p = 18..23: J_l row-major (row i, col j at p = 18 + 3 i + j)
+//     r[i * n_obs_pad + o], i = 0, 1
+//   obs_meta[o] (uint16) = (position of o in the tile's camera-sorted order) | slot << 8.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace poba {
+
+constexpr int kTileObs = 256;   // observations per tile (= threads of the tile kernels)
+constexpr int kTileLms = 256;   // landmarks per tile
+constexpr int kLinVals = 54;    // 45 packed upper-triangular entries of J_p^T J_p + 9 of J_p^T r
+constexpr int kCamBlock = 32;   // cameras per block in the camera-side kernels
+constexpr int kReduceThreads = 256;
+
+// ---------------------------------------------------------------------------------------
+// Host-side tile schedule (built once in ba_create).
+struct Schedule {
+  int n_cams = 0, n_lms = 0, n_obs = 0;
+  int n_tiles = 0, n_slots = 0, max_slots_per_tile = 0, max_track = 0;
+  std::vector<int32_t> lm_order;     // internal landmark -> caller landmark
+  std::vector<int32_t> lm_rank;      // caller landmark -> internal landmark
+  std::vector<int64_t> obs_order;    // sorted observation -> caller observation
+  std::vector<int32_t> lm_seg;       // [n_lms + 1] observation offsets per internal landmark
+  std::vector<int32_t> cam_of;       // [n_obs] camera of each sorted observation
+  std::vector<int32_t> lm_of;        // [n_obs] internal landmark of each sorted observation
+  std::vector<uint16_t> obs_meta;    // [n_obs] pos | slot << 8
+  std::vector<int32_t> tile_lm0;     // [n_tiles + 1]
+  std::vector<int32_t> tile_slot0;   // [n_tiles + 1]
+  std::vector<int32_t> slot_cam;     // [n_slots]
+  std::vector<uint16_t> slot_beg;    // [n_slots] first camera-sorted position of the slot
+  std::vector<int32_t> cam_slot_ptr; // [n_cams + 1]
+  std::vector<int32_t> cam_slot_list;// [n_slots]
+};
+
+// Returns an empty string on success, else a description of why the inputs are rejected.
+std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_idx,
+                           const int32_t* lm_idx, Schedule* out);
+
+// ---------------------------------------------------------------------------------------
+// Device views passed to kernels by value.
+struct Topology {
+  int n_cams, n_lms, n_obs, n_obs_pad, n_tiles, n_slots;
+  const int32_t* lm_seg;
+  const int32_t* cam_of;
+  const int32_t* lm_of;
+  const uint16_t* obs_meta;
+  const int32_t* tile_lm0;
+  const int32_t* tile_slot0;
+  const int32_t* slot_cam;
+  const uint16_t* slot_beg;
+  const int32_t* cam_slot_ptr;
+  const int32_t* cam_slot_list;
+};
+
+// Per-camera values prepared once per state: rotation R (row-major), the matrix G with
+// dP/dw = -[Y]x G (Y = R X and G = left Jacobian of SO(3) on the regular branch; Y = X and
+// G = I on the first-order branch), translation, intrinsics, and the branch flag.
+constexpr int kCamPrep = 25;  // R[9] G[9] t[3] f k1 k2 first_order
+
+// Series state (device), one per handle.
+struct SeriesState {
+  int32_t done;        // stop rule fired (later iterations skip)
+  int32_t m;           // number of P applications performed
+  int32_t stopped;     // 1 if the stop test fired
+  int32_t pad0;
+  double stop_value;
+  double x_norm;
+  double t_norm;
+  double pad2;
+  uint32_t counter;    // last-block ticket
+  uint32_t pad1;
+};
+
+// LM record (device), written by the decide kernel and read by the host once per iteration.
+struct LmRecord {
+  double cost;          // F(x) (current state)
+  double cost_before;   // F(x) before the last step
+  double cost_trial;    // F(x + dx)
+  double model_decrease;
+  double gain_ratio;
+  double lambda;        // damping for the next solve
+  double nu;
+  double lambda_used;
+  int32_t accepted;
+  int32_t not_spd;      // set by damp/invert
+  int32_t nonfinite;
+  int32_t iteration;
+  int32_t converged;
+  int32_t pad;
+};
+
+// ---------------------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files).  All take the stream last.
+void launch_cam_prepare(const double* cams, const double* dx_p, int n_cams, double* prep,
+                        double* cams_out, cudaStream_t s);
+
+template <typename T>
+void launch_linearize(const Topology& tp, const double* prep, const double* lms,
+                      const double2* obs, const double* sqrt_w, T* J, T* r, double* V,
+                      double* b_l, T* partial, double* block_cost, cudaStream_t s);
+
+template <typename PT>
+void launch_lin_camera_reduce(const Topology& tp, const PT* partial, double* U45, double* b_p,
+                              cudaStream_t s);
+
+void launch_damp_invert(const Topology& tp, const double* U45, const double* V,
+                        const double* lambda, int damping_mode, double* Uinv, double* Vinv,
+                        float* Vinv_f, int32_t* not_spd, cudaStream_t s);
+
+void launch_cost(const Topology& tp, const double* prep, const double* lms, const double* dx_l,
+                 const double2* obs, const double* sqrt_w, double* block_sums, cudaStream_t s);
+
+int cost_blocks(const Topology& tp);
+
+template <typename T>
+void launch_tile_rhs(const Topology& tp, const T* J, const double* b_l, const T* Vinv,
+                     T* partial, const SeriesState* st, cudaStream_t s);
+
+template <typename T>
+void launch_tile_series(const Topology& tp, const T* J, const double* t, const T* Vinv,
+                        T* partial, const SeriesState* st, cudaStream_t s);
+
+template <typename T>
+void launch_tile_backsub(const Topology& tp, const T* J, const T* r, const double* x,
+                         const double* b_l, const T* Vinv, double* dx_l,
+                         double* block_pred, cudaStream_t s);
+
+template <typename PT>
+void launch_camera_rhs(const Topology& tp, const PT* partial, const double* b_p,
+                       const double* Uinv, double* x, double* t, double* block_norms,
+                       SeriesState* st, cudaStream_t s);
+
+template <typename PT>
+void launch_camera_series(const Topology& tp, const PT* partial, const double* Uinv, double* x,
+                          double* t, double* block_norms, SeriesState* st, int iter,
+                          double eps, cudaStream_t s);
+
+int camera_blocks(const Topology& tp);
+int tile_blocks(const Topology& tp);
+
+void launch_series_reset(SeriesState* st, cudaStream_t s);
+
+void launch_reduce_sum(const double* in, int n, double* out, double scale, cudaStream_t s);
+
+void launch_lm_decide(const double* block_cost, int n_cost, const double* block_pred,
+                      int n_pred, LmRecord* rec, const SeriesState* st, double func_tol,
+                      cudaStream_t s);
+
+void launch_apply_step(const LmRecord* rec, double* cams, const double* cams_trial,
+                       double* lms, const double* dx_l, int n_cams, int n_lms, cudaStream_t s);
+
+void launch_set_scalar(double* dst, double v, cudaStream_t s);
+
+
+}  // namespace poba

@@ -1,0 +1,128 @@
+// Host-side tile schedule for libpoba (built once per problem in ba_create).
+//
+// Sec. 5 ("Efficient storage") groups the Jacobians and residuals of each landmark into one
+// dense memory block.  The GPU layout keeps that grouping and adds what the camera-keyed
+// reductions need on a GPU: landmarks are ordered by their smallest observing camera, packed
+// into tiles of at most kTileObs observations, and each tile's distinct cameras become slots
+// whose sums are later combined per camera in a fixed order.
+#include <algorithm>
+#include <numeric>
+#include <string>
+
+#include "poba_internal.cuh"
+
+namespace poba {
+
+std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_idx,
+                           const int32_t* lm_idx, Schedule* S) {
+  if (n_cams < 1 || n_lms < 1 || n_obs < 0) return "n_cams and n_lms must be >= 1, n_obs >= 0";
+  S->n_cams = n_cams;
+  S->n_lms = n_lms;
+  S->n_obs = n_obs;
+
+  std::vector<int32_t> count(n_lms, 0);
+  std::vector<int32_t> key(n_lms, n_cams);  // smallest observing camera (n_cams if unobserved)
+  for (int o = 0; o < n_obs; ++o) {
+    int c = cam_idx[o], l = lm_idx[o];
+    if (c < 0 || c >= n_cams) return "cam_idx[" + std::to_string(o) + "] out of range";
+    if (l < 0 || l >= n_lms) return "lm_idx[" + std::to_string(o) + "] out of range";
+    count[l]++;
+    key[l] = std::min(key[l], c);
+  }
+  int max_track = 0;
+  for (int l = 0; l < n_lms; ++l) max_track = std::max(max_track, count[l]);
+  if (max_track > kTileObs)
+    return "a landmark has " + std::to_string(max_track) + " observations; at most " +
+           std::to_string(kTileObs) + " are supported";
+  S->max_track = max_track;
+
+  // Internal landmark order: by smallest observing camera, then caller index.
+  S->lm_order.resize(n_lms);
+  std::iota(S->lm_order.begin(), S->lm_order.end(), 0);
+  std::stable_sort(S->lm_order.begin(), S->lm_order.end(),
+                   [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+  S->lm_rank.assign(n_lms, 0);
+  for (int i = 0; i < n_lms; ++i) S->lm_rank[S->lm_order[i]] = i;
+
+  S->lm_seg.assign(n_lms + 1, 0);
+  for (int i = 0; i < n_lms; ++i) S->lm_seg[i + 1] = S->lm_seg[i] + count[S->lm_order[i]];
+
+  // Observations sorted by (internal landmark, camera, caller index).
+  S->obs_order.resize(n_obs);
+  std::iota(S->obs_order.begin(), S->obs_order.end(), (int64_t)0);
+  std::sort(S->obs_order.begin(), S->obs_order.end(), [&](int64_t a, int64_t b) {
+    int la = S->lm_rank[lm_idx[a]], lb = S->lm_rank[lm_idx[b]];
+    if (la != lb) return la < lb;
+    if (cam_idx[a] != cam_idx[b]) return cam_idx[a] < cam_idx[b];
+    return a < b;
+  });
+  S->cam_of.resize(n_obs);
+  S->lm_of.resize(n_obs);
+  for (int o = 0; o < n_obs; ++o) {
+    S->cam_of[o] = cam_idx[S->obs_order[o]];
+    S->lm_of[o] = S->lm_rank[lm_idx[S->obs_order[o]]];
+  }
+
+  // Tiles: greedy packing of whole landmarks.
+  S->tile_lm0.clear();
+  S->tile_lm0.push_back(0);
+  {
+    int tile_obs = 0, tile_lms = 0;
+    for (int i = 0; i < n_lms; ++i) {
+      int k = S->lm_seg[i + 1] - S->lm_seg[i];
+      if (tile_lms > 0 && (tile_obs + k > kTileObs || tile_lms + 1 > kTileLms)) {
+        S->tile_lm0.push_back(i);
+        tile_obs = 0;
+        tile_lms = 0;
+      }
+      tile_obs += k;
+      tile_lms += 1;
+    }
+    S->tile_lm0.push_back(n_lms);
+  }
+  S->n_tiles = (int)S->tile_lm0.size() - 1;
+
+  // Slots: distinct cameras per tile, ascending; per observation its slot and its position in
+  // the tile's camera-sorted order (stable in landmark order).
+  S->obs_meta.assign(n_obs, 0);
+  S->tile_slot0.assign(S->n_tiles + 1, 0);
+  S->slot_cam.clear();
+  S->slot_beg.clear();
+  S->max_slots_per_tile = 0;
+  std::vector<int32_t> local;  // observation offsets within the tile
+  for (int t = 0; t < S->n_tiles; ++t) {
+    int o0 = S->lm_seg[S->tile_lm0[t]], o1 = S->lm_seg[S->tile_lm0[t + 1]];
+    int n = o1 - o0;
+    local.resize(n);
+    std::iota(local.begin(), local.end(), 0);
+    std::stable_sort(local.begin(), local.end(),
+                     [&](int32_t a, int32_t b) { return S->cam_of[o0 + a] < S->cam_of[o0 + b]; });
+    int slot = -1, prev_cam = -1;
+    for (int p = 0; p < n; ++p) {
+      int o = o0 + local[p];
+      int c = S->cam_of[o];
+      if (c != prev_cam) {
+        ++slot;
+        prev_cam = c;
+        S->slot_cam.push_back(c);
+        S->slot_beg.push_back((uint16_t)p);
+      }
+      S->obs_meta[o] = (uint16_t)(p | (slot << 8));
+    }
+    int ns = slot + 1;
+    S->max_slots_per_tile = std::max(S->max_slots_per_tile, ns);
+    S->tile_slot0[t + 1] = S->tile_slot0[t] + ns;
+  }
+  S->n_slots = S->tile_slot0[S->n_tiles];
+
+  // Camera -> slots (CSR), slots in tile order.
+  S->cam_slot_ptr.assign(n_cams + 1, 0);
+  for (int s = 0; s < S->n_slots; ++s) S->cam_slot_ptr[S->slot_cam[s] + 1]++;
+  for (int c = 0; c < n_cams; ++c) S->cam_slot_ptr[c + 1] += S->cam_slot_ptr[c];
+  S->cam_slot_list.assign(S->n_slots, 0);
+  std::vector<int32_t> fill(S->cam_slot_ptr.begin(), S->cam_slot_ptr.end() - 1);
+  for (int s = 0; s < S->n_slots; ++s) S->cam_slot_list[fill[S->slot_cam[s]]++] = s;
+  return "";
+}
+
+}  // namespace poba

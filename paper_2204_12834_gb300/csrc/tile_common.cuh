@@ -1,0 +1,58 @@
+// Device helpers shared by the tile kernels of libpoba: fixed-order reductions.
+#pragma once
+
+#include <cstdint>
+
+namespace poba {
+
+// Sum of `val` over the block in a fixed order (warp shuffles, then warps in order).  Must be
+// called by every thread of the block; the total is valid in thread 0.  sred holds one
+// double per warp.
+__device__ __forceinline__ double block_sum_fixed(double val, double* sred) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) val += __shfl_down_sync(0xffffffffu, val, off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sred[warp] = val;
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) tot += sred[w];
+  }
+  return tot;
+}
+
+// Per-slot sums of a tile: rows sg[beg_s .. end_s) of the camera-sorted staging array are
+// summed for each slot s and component k (9 per row) and written to out[s * stride + k].
+// Small tiles split each sum over 2, 4 or 8 lanes (combined by shuffles); the split depends
+// only on the slot count, so the order of every sum is fixed for a given problem.  Must be
+// called by every thread of the block.
+template <typename T, typename PT>
+__device__ __forceinline__ void slot_sums(const T (*sg)[9], int ns, int n, const uint16_t* sbeg,
+                                          PT* out, int stride) {
+  const int pairs = ns * 9;
+  const int nthreads = blockDim.x;
+  int split = 1;
+  if (pairs * 8 <= nthreads) split = 8;
+  else if (pairs * 4 <= nthreads) split = 4;
+  else if (pairs * 2 <= nthreads) split = 2;
+  const int total = pairs * split;
+  const int bound = (total + 31) & ~31;
+  for (int idx = threadIdx.x; idx < bound; idx += nthreads) {
+    const int pair = idx / split, part = idx - pair * split;
+    const bool act = pair < pairs;
+    T acc = (T)0;
+    int s = 0, k = 0;
+    if (act) {
+      s = pair / 9;
+      k = pair - s * 9;
+      const int beg = sbeg[s], end = (s + 1 < ns) ? (int)sbeg[s + 1] : n;
+      for (int q = beg + part; q < end; q += split) acc += sg[q][k];
+    }
+    for (int off = split >> 1; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (act && part == 0) out[(size_t)s * stride + k] = (PT)acc;
+  }
+}
+
+}  // namespace poba

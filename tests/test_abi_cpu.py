@@ -1,0 +1,105 @@
+"""The C-ABI library builds, loads and exports every symbol include/poba.h declares; argument
+validation that runs before any CUDA call is checked here without a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "poba.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2204_12834_gb300 import build as b
+    b.build()
+    import paper_2204_12834_gb300 as poba
+    return poba.library()
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ba_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ("ba_create", "ba_linearize", "ba_solve_schur_power", "ba_lm_step", "ba_cost",
+                 "ba_get_params", "ba_get_step", "ba_destroy", "ba_status_string"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2204_12834_gb300 import _lib
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, name
+
+
+def test_status_strings_and_defaults(lib):
+    assert lib.ba_status_string(0) == b"BA_OK"
+    assert lib.ba_status_string(4) == b"BA_ERR_NOT_SPD"
+    import paper_2204_12834_gb300 as poba
+    o = poba.ba_default_options()
+    # Sec. 5.1: lambda0 1e-4, 50 LM iterations, func tol 1e-6, 20 inner iterations, eps 0.01
+    assert (o.lambda0, o.func_tol, o.eps, o.max_lm, o.max_inner) == (1e-4, 1e-6, 0.01, 50, 20)
+
+
+def _desc(n_c=3, n_l=4, n_o=6, seed=0):
+    rng = np.random.default_rng(seed)
+    cams = rng.normal(size=(n_c, 9))
+    lms = rng.normal(size=(n_l, 3))
+    obs = rng.normal(size=(n_o, 2))
+    ci = rng.integers(0, n_c, n_o).astype(np.int32)
+    li = rng.integers(0, n_l, n_o).astype(np.int32)
+    return cams, lms, obs, ci, li
+
+
+@pytest.mark.parametrize("case", ["bad_cam_index", "bad_lm_index", "zero_cams", "nan_obs",
+                                  "neg_weight", "long_track", "bad_precision"])
+def test_create_rejects_bad_inputs_before_touching_the_gpu(lib, case):
+    import paper_2204_12834_gb300 as poba
+    cams, lms, obs, ci, li = _desc()
+    w = None
+    prec = poba.BA_FP64
+    expect = "BA_ERR_INVALID_ARG"
+    if case == "bad_cam_index":
+        ci[2] = 3
+    elif case == "bad_lm_index":
+        li[0] = -1
+    elif case == "zero_cams":
+        cams = cams[:0]
+    elif case == "nan_obs":
+        obs[1, 0] = np.nan
+        expect = "BA_ERR_NONFINITE"
+    elif case == "neg_weight":
+        w = np.ones(obs.shape[0])
+        w[3] = -1.0
+    elif case == "long_track":
+        n = 300
+        obs = np.zeros((n, 2))
+        ci = np.zeros(n, np.int32)
+        li = np.zeros(n, np.int32)
+    elif case == "bad_precision":
+        prec = 7
+    with pytest.raises(poba.PobaError) as e:
+        poba.ba_create(cams, lms, obs, ci, li, weights=w, precision=prec)
+    assert e.value.status_name == expect, str(e.value)
+
+
+def test_bad_options_rejected(lib):
+    import paper_2204_12834_gb300 as poba
+    cams, lms, obs, ci, li = _desc()
+    for kw in (dict(lambda0=0.0), dict(eps=-1.0), dict(max_inner=-1), dict(damping_mode=3)):
+        with pytest.raises(poba.PobaError) as e:
+            poba.ba_create(cams, lms, obs, ci, li, options=poba.ba_default_options(**kw))
+        assert e.value.status_name == "BA_ERR_INVALID_ARG"
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    assert lib.ba_linearize(None, None) == 1
+    assert lib.ba_lm_step(None, None) == 1
+    assert lib.ba_destroy(None) == 0
