@@ -1,0 +1,554 @@
+#!/usr/bin/env python
+"""Benchmark of GPU Power Bundle Adjustment (LM iterations/s on one GB300).
+
+A step is one Levenberg-Marquardt iteration of the whole hot path: linearise (residuals,
+Jacobians, U / V / b blocks), damp and invert the blocks, form b~ and x(0), run the power
+series with the stop rule (eps 0.01, at most 20 terms), back-substitute, evaluate F(x + dx)
+and the model decrease, accept / reject and update lambda.  Consecutive steps run real LM solves
+from the initial state: a solve runs until the relative function tolerance (1e-6) is met or 50
+iterations have passed, then the state is reset to x0 outside the timed events.  The L2 cache is
+flushed (512 MiB write) before every timed step; each step is timed with CUDA events on the
+library's stream.
+
+Output: one JSON line (rank 0).  `value` is LM iterations/s summed over ranks (each rank solves
+its own replica of the problem; no collective on the data path).  Extra keys report series
+solves/s, time to the tau = 1% cost threshold, the roofline of the dominant kernel, the
+float32-bulk variant, an end-to-end number through the public API with host buffers, and the
+FP64 CPU oracle timed on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl poba|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bal_synth  # noqa: E402
+
+WORKLOAD = "clustered_1200c_160000l"
+METRIC = "LM iterations/s (power-series Schur PoBA, BAL camera model)"
+L2_FLUSH_BYTES = 512 << 20
+FP64_PEAK_TFLOPS_DERIVED = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk/SM x 2 x max clock
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ---------------------------------------------------------------------------------------
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["poba", "reference"], default="poba")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="run only this many untimed FP64 LM steps (for ncu launch lists)")
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling (200 ms) while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="poba_clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peaks() -> tuple[float, str, float, str]:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured", float(d.get("bf16_tflops", 0.0)), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback", 1900.0, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels_series.cu", "tile_common.cuh", "poba_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2204_12834_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(precision: str):
+    """DRAM bytes per series-tile launch from the committed ncu summary, if the kernel source is
+    unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", f"series_tile_{WORKLOAD}.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    if d.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    return d.get(precision, {}).get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------------------
+def series_tile_units(p, sched_slots: int, s: int):
+    """Algorithmic bytes and flops of one series tile launch (one term, tile half):
+    per observation J_p, J_l (24 s) and the 2-byte slot/position code, 48 FMA + 12 adds;
+    per landmark V^-1 (6 s) and its segment offset (4 B), 9 FMA; per slot one 9-vector write."""
+    n_o, n_l = p.n_obs, p.n_lms
+    bytes_ = n_o * (24 * s + 2) + n_l * (6 * s + 4) + sched_slots * 9 * s
+    flops = n_o * (2 * 48 + 12) + n_l * 18
+    return bytes_, flops
+
+
+def explicit_s_bytes(p) -> int:
+    """Block-sparse explicit S (what an explicit-Schur PCG stores): distinct camera pairs that
+    share a landmark (upper triangle incl. diagonal) x 81 doubles."""
+    order = np.argsort(p.lm_idx, kind="stable")
+    li, ci = p.lm_idx[order], p.cam_idx[order].astype(np.int64)
+    starts = np.r_[0, np.nonzero(np.diff(li))[0] + 1, len(li)]
+    pairs = set()
+    nc = p.n_cams
+    for a, b in zip(starts[:-1], starts[1:]):
+        cs = np.unique(ci[a:b])
+        for i in range(len(cs)):
+            for j in range(i, len(cs)):
+                pairs.add(int(cs[i]) * nc + int(cs[j]))
+    return len(pairs) * 81 * 8
+
+
+# ---------------------------------------------------------------------------------------
+def run_poba(args):
+    import torch
+    import paper_2204_12834_gb300 as poba
+    from paper_2204_12834_gb300 import build as pbuild
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    pbuild.build()
+    poba.library()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    p = bal_synth.preset(args.workload)
+    to_dev = lambda a: torch.as_tensor(a).to(dev)
+
+    def make(precision, **opt):
+        with torch.cuda.stream(stream):
+            return poba.ba_create(to_dev(p.cams0), to_dev(p.lms0), to_dev(p.obs), to_dev(p.cam_idx),
+                                  to_dev(p.lm_idx), None if p.weights is None else to_dev(p.weights),
+                                  precision=precision, options=poba.ba_default_options(**opt),
+                                  stream=stream)
+
+    cams0_d, lms0_d = to_dev(p.cams0), to_dev(p.lms0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    if args.profile_steps:
+        h = make(poba.BA_FP64)
+        for _ in range(args.profile_steps):
+            poba.ba_lm_step(h)
+        torch.cuda.synchronize()
+        return
+
+    def reset(h):
+        poba.ba_set_params(h, cams0_d, lms0_d)
+        poba.ba_set_lm_state(h, 1e-4, 2.0, 0)
+
+    def lm_block(h, n_steps, timed):
+        """n_steps LM iterations (restarting from x0 after convergence / 50 iterations)."""
+        evs = []
+        n_lin = 0
+        iters_in_solve = 0
+        with torch.cuda.stream(stream):
+            for _ in range(n_steps):
+                if iters_in_solve >= 50:
+                    reset(h)
+                    iters_in_solve = 0
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s = poba.ba_lm_step(h)
+                e1.record(stream)
+                evs.append((e0, e1))
+                iters_in_solve += 1
+                if s["converged"]:
+                    iters_in_solve = 50
+        stream.synchronize()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return ms
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    clocks = ClockSampler(local)
+    for name, prec in (("fp64", poba.BA_FP64), ("fp32_bulk", poba.BA_FP32_BULK)):
+        h = make(prec)
+        lm_block(h, args.warmup, False)
+        reset(h)
+        poba.ba_set_timing(h, True)
+        launches0 = poba.ba_kernel_launches(h)
+        if name == "fp64":
+            clocks.start()
+        barrier()
+        ms = lm_block(h, args.steps, True)
+        barrier()
+        if name == "fp32_bulk":
+            clk = clocks.stop()
+        launches = poba.ba_kernel_launches(h) - launches0
+        total_ms = max_over_ranks(sum(ms))
+        timing = poba.ba_get_timing(h)
+        poba.ba_set_timing(h, False)
+        results[name] = dict(h=h, ms=ms, total_ms=total_ms, timing=timing, launches=launches)
+
+    # series solves/s at the current linearisation of each handle
+    for name, r in results.items():
+        h = r["h"]
+        poba.ba_linearize(h, want_cost=False)
+        evs = []
+        infos = []
+        n = max(10, min(args.steps, 200))
+        with torch.cuda.stream(stream):
+            for _ in range(n):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                infos.append(poba.ba_solve_schur_power(h, 1e-4))
+                e1.record(stream)
+                evs.append((e0, e1))
+        stream.synchronize()
+        sms = sum(a.elapsed_time(b) for a, b in evs)
+        r["solves_per_s"] = world * n / (max_over_ranks(sms) / 1e3)
+        r["solve_inner_mean"] = float(np.mean([i["inner_iters"] for i in infos]))
+
+    # time to reach f_tau = f* + 0.01 (f0 - f*) in a fresh solve from x0 (per precision)
+    traj = {}
+    for name, prec in (("fp64", poba.BA_FP64), ("fp32_bulk", poba.BA_FP32_BULK)):
+        h = make(prec)
+        f0 = poba.ba_cost(h)
+        t = 0.0
+        pts = []
+        with torch.cuda.stream(stream):
+            for _ in range(50):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s = poba.ba_lm_step(h)
+                e1.record(stream)
+                stream.synchronize()
+                t += e0.elapsed_time(e1) / 1e3
+                pts.append((t, s["cost_after"] if s["accepted"] else s["cost_before"]))
+                if s["converged"]:
+                    break
+        traj[name] = dict(f0=f0, pts=pts, final=pts[-1][1], iters=len(pts))
+    f_star = min(v["final"] for v in traj.values())
+    for name, v in traj.items():
+        f_tau = f_star + 0.01 * (v["f0"] - f_star)
+        v["time_to_tau_s"] = next((t for t, c in v["pts"] if c <= f_tau), None)
+
+    # end-to-end through the public API with host buffers: per step H2D of the state from
+    # pinned host memory, one LM step, D2H of the new state
+    h = make(poba.BA_FP64)
+    cams_h = torch.as_tensor(p.cams0).pin_memory()
+    lms_h = torch.as_tensor(p.lms0).pin_memory()
+    cams_o = torch.empty_like(cams_h).pin_memory()
+    lms_o = torch.empty_like(lms_h).pin_memory()
+    n_e2e = max(5, min(args.steps, 100))
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(n_e2e):
+        if i % 50 == 0:
+            cams_h.copy_(torch.as_tensor(p.cams0))
+            lms_h.copy_(torch.as_tensor(p.lms0))
+            poba.ba_set_lm_state(h, 1e-4, 2.0, 0)
+        poba.ba_set_params(h, cams_h, lms_h)
+        poba.ba_lm_step(h)
+        poba.ba_get_params(h, cams_o.numpy(), lms_o.numpy())
+        cams_h.copy_(cams_o)
+        lms_h.copy_(lms_o)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    state_bytes = (p.n_cams * 9 + p.n_lms * 3) * 8
+
+    # roofline of the dominant kernel class
+    hbm_peak, hbm_kind, _, _ = measured_peaks()
+    r_slots = schedule_slots(p)
+
+    def roofline(name):
+        r = results[name]
+        cls = max(r["timing"], key=lambda k: r["timing"][k][0])
+        ms, cnt = r["timing"]["series_tile"]
+        s = 8 if name == "fp64" else 4
+        nb, nf = series_tile_units(p, r_slots, s)
+        avg_s = ms / 1e3 / max(cnt, 1)
+        traffic = profiled_traffic(name)
+        if name == "fp64":
+            ach = nf / avg_s / 1e12
+            out = {"kernel": "tile_matvec<double> (series term)", "bound": "alu",
+                   "achieved": ach, "peak": FP64_PEAK_TFLOPS_DERIVED, "unit": "TFLOP/s",
+                   "frac": ach / FP64_PEAK_TFLOPS_DERIVED,
+                   "peak_kind": "derived FP64 FMA rate (152 SM x 2 FMA/clk x 2.07 GHz)",
+                   "traffic": traffic, "algorithmic_bytes": nb, "algorithmic_flops": nf,
+                   "avg_launch_us": avg_s * 1e6, "launches": cnt,
+                   "achieved_gbs": nb / avg_s / 1e9, "dominant_class": cls}
+        else:
+            ach = nb / avg_s / 1e9
+            out = {"kernel": "tile_matvec<float> (series term)", "bound": "hbm",
+                   "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                   "peak_kind": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)" if hbm_kind == "measured" else "fallback",
+                   "traffic": traffic, "algorithmic_bytes": nb, "algorithmic_flops": nf,
+                   "avg_launch_us": avg_s * 1e6, "launches": cnt, "dominant_class": cls}
+        return out
+
+    roof64 = roofline("fp64")
+    roof32 = roofline("fp32_bulk")
+    mem_gpu = poba.ba_memory_footprint(results["fp64"]["h"])
+    mem_gpu32 = poba.ba_memory_footprint(results["fp32_bulk"]["h"])
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args)
+
+    if rank != 0:
+        return
+    r64, r32 = results["fp64"], results["fp32_bulk"]
+
+    def kernel_avgs(r):
+        return {k: {"avg_us": (v[0] * 1e3 / v[1]) if v[1] else None, "count": v[1],
+                    "share": v[0] / max(sum(x[0] for x in r["timing"].values()), 1e-12)}
+                for k, v in r["timing"].items()}
+
+    line = {
+        "metric": METRIC,
+        "value": world * args.steps / (r64["total_ms"] / 1e3),
+        "unit": "LM iterations/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": r64["total_ms"] / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded BAL-model problem; stands in for BAL Ladybug-1197)",
+        "config": {"workload": args.workload, "n_cams": p.n_cams, "n_lms": p.n_lms,
+                   "n_obs": p.n_obs, "visibility": "clustered window 8, tracks U{3,4}",
+                   "series": {"eps": 0.01, "max_inner": 20}, "lm": {"lambda0": 1e-4,
+                   "func_tol": 1e-6, "max_lm": 50, "restart_from_x0": True},
+                   "l2": "flushed before every timed step (512 MiB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roof64,
+        "clocks": clk,
+        "gpu_launches": int(r64["launches"]),
+        "e2e": {"value": world * n_e2e / e2e_s, "unit": "LM iterations/s",
+                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+                "steps": n_e2e, "note": "ba_set_params (pinned host) + ba_lm_step + ba_get_params (host)"},
+        "solves_per_s": r64["solves_per_s"],
+        "solve_inner_mean": r64["solve_inner_mean"],
+        "time_to_1pct_cost_s": traj["fp64"]["time_to_tau_s"],
+        "lm_iters_to_converge": traj["fp64"]["iters"],
+        "final_cost": traj["fp64"]["final"],
+        "memory_bytes": mem_gpu,
+        "explicit_S_bytes": explicit_s_bytes(p),
+        "kernels": kernel_avgs(r64),
+        "fp32_bulk": {"value": world * args.steps / (r32["total_ms"] / 1e3), "unit": "LM iterations/s",
+                      "ms_per_step": r32["total_ms"] / args.steps, "roofline": roof32,
+                      "gpu_launches": int(r32["launches"]), "solves_per_s": r32["solves_per_s"],
+                      "solve_inner_mean": r32["solve_inner_mean"],
+                      "time_to_1pct_cost_s": traj["fp32_bulk"]["time_to_tau_s"],
+                      "final_cost": traj["fp32_bulk"]["final"],
+                      "final_cost_rel_to_fp64": traj["fp32_bulk"]["final"] / traj["fp64"]["final"] - 1.0,
+                      "memory_bytes": mem_gpu32, "kernels": kernel_avgs(r32)},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def schedule_slots(p, tile_obs=256, tile_lms=256) -> int:
+    """Number of (tile, camera) slots: landmarks ordered by their smallest observing camera and
+    packed greedily into tiles of whole tracks, as the library's schedule does."""
+    counts = np.bincount(p.lm_idx, minlength=p.n_lms)
+    key = np.full(p.n_lms, p.n_cams, dtype=np.int64)
+    np.minimum.at(key, p.lm_idx, p.cam_idx)
+    lm_order = np.argsort(key, kind="stable")
+    rank = np.empty_like(lm_order)
+    rank[lm_order] = np.arange(p.n_lms)
+    tiles = np.empty(p.n_lms, dtype=np.int64)
+    t = obs = lms = 0
+    for i in lm_order:
+        k = counts[i]
+        if lms > 0 and (obs + k > tile_obs or lms + 1 > tile_lms):
+            t += 1
+            obs = lms = 0
+        obs += k
+        lms += 1
+        tiles[i] = t
+    pair = tiles[p.lm_idx] * p.n_cams + p.cam_idx
+    return int(np.unique(pair).size)
+
+
+# ---------------------------------------------------------------------------------------
+def cpu_baseline(args) -> dict:
+    """The FP64 oracle (as it stands) on the host cores: single-threaded LM iterations on the
+    same workload, run in a subprocess with BLAS / OpenMP threads pinned to 1."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker", "--workload",
+           args.workload, "--cpu-seconds", str(args.cpu_seconds)]
+    try:
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+        d = json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # report, do not hide
+        return {"value": None, "unit": "LM iterations/s", "cores": 1, "kind": "oracle",
+                "sample": f"failed: {e}"}
+    return {"value": d["iters"] / d["seconds"], "unit": "LM iterations/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{d['iters']} oracle LM iterations from x0 on the full {args.workload} problem "
+                      f"({d['seconds']:.1f} s; numpy/scipy, 1 thread)"}
+
+
+def cpu_baseline_worker(args):
+    from oracle import lm as olm
+    p = bal_synth.preset(args.workload)
+    t0 = time.perf_counter()
+    n = 0
+    # one LM iteration at a time, until the time budget is used (at least one iteration)
+    cams, lms = p.cams0, p.lms0
+    lam, nu = 1e-4, 2.0
+    while True:
+        cams, lms, hist = olm.lm_solve(p, olm.Options(max_lm=1, lambda0=lam), cams=cams, lms=lms)
+        lam, nu = olm.lambda_update(lam, nu, hist[-1]["accepted"], hist[-1]["rho"])
+        n += 1
+        if time.perf_counter() - t0 > args.cpu_seconds:
+            break
+    print(json.dumps({"iters": n, "seconds": time.perf_counter() - t0}))
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle timed on the host cores (the paper ships no code)."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import lm as olm
+    p = bal_synth.preset(args.workload)
+    cams, lms = p.cams0, p.lms0
+    lam, nu = 1e-4, 2.0
+    warm = min(args.warmup, 1)
+    for _ in range(warm):
+        olm.lm_solve(p, olm.Options(max_lm=1, lambda0=lam), cams=cams, lms=lms)
+    budget = 120.0
+    t0 = time.perf_counter()
+    n = 0
+    while n < args.steps:
+        cams, lms, hist = olm.lm_solve(p, olm.Options(max_lm=1, lambda0=lam), cams=cams, lms=lms)
+        lam, nu = olm.lambda_update(lam, nu, hist[-1]["accepted"], hist[-1]["rho"])
+        n += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    v = n / dt
+    sample = (f"{n} of {args.steps} requested oracle LM iterations (120 s cap) on the full "
+              f"{args.workload} problem, numpy/scipy FP64")
+    cores = 1
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "LM iterations/s",
+        "n_gpus": world, "steps": n, "warmup": warm, "ms_per_step": 1e3 * dt / n,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded BAL-model problem; stands in for BAL Ladybug-1197)",
+        "config": {"workload": args.workload, "n_cams": p.n_cams, "n_lms": p.n_lms, "n_obs": p.n_obs},
+        "cpu_baseline": {"value": v, "unit": "LM iterations/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "LM iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.cpu_baseline_worker:
+        return cpu_baseline_worker(args)
+    if args.impl == "reference":
+        if os.environ.get("POBA_REFERENCE_CHILD") != "1":
+            # pin BLAS / OpenMP to one thread so the reported core count is exact
+            env = dict(os.environ, POBA_REFERENCE_CHILD="1", OMP_NUM_THREADS="1",
+                       OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+            os.execve(sys.executable, [sys.executable, os.path.abspath(__file__)] + sys.argv[1:], env)
+        return run_reference(args)
+    return run_poba(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -180,6 +180,22 @@ ba_status ba_memory_footprint(ba_handle* h, uint64_t* bytes);
  * its kernel nodes). */
 ba_status ba_kernel_launches(ba_handle* h, uint64_t* count);
 
+/* Kernel timing (CUDA events recorded on the handle's stream around each kernel class, also
+ * inside the replayed series graph).  Classes: 0 linearise (camera prep, residual/Jacobian/
+ * block kernel, camera block reduce), 1 damp and invert, 2 reduced RHS and x(0) (tile + camera
+ * kernel), 3 series tile kernel (one per executed term), 4 series camera kernel (one per
+ * executed term), 5 back-substitution with model decrease, 6 LM evaluation (trial camera prep,
+ * cost, decision, apply).  Times are collected by the calls that synchronise (ba_lm_step,
+ * ba_solve_schur_power with info); series terms skipped after the stop rule fired are not
+ * counted.  Enabling resets the totals; timing adds a few event records per kernel. */
+#define BA_TIMING_CLASSES 7
+typedef struct {
+  double ms[BA_TIMING_CLASSES];      /* summed device time per class */
+  uint64_t count[BA_TIMING_CLASSES]; /* timed launches (or launch groups) per class */
+} ba_timing;
+ba_status ba_set_timing(ba_handle* h, int32_t enable);
+ba_status ba_get_timing(ba_handle* h, ba_timing* out);
+
 /* Free all device memory of the handle (and its own stream, if it created one). NULL is OK. */
 ba_status ba_destroy(ba_handle* h);
 

@@ -23,7 +23,8 @@ __all__ = ["PobaError", "Handle", "ba_default_options", "ba_create", "ba_set_opt
            "ba_linearize", "ba_solve_schur_power", "ba_lm_step", "ba_lm_solve", "ba_cost",
            "ba_get_params", "ba_set_params", "ba_get_step", "ba_get_linearization",
            "ba_get_blocks", "ba_get_lm_state", "ba_set_lm_state", "ba_memory_footprint",
-           "ba_kernel_launches", "ba_destroy", "BA_FP64", "BA_FP32_BULK", "library"]
+           "ba_kernel_launches", "ba_set_timing", "ba_get_timing", "ba_destroy", "BA_FP64",
+           "BA_FP32_BULK", "library", "from_problem"]
 
 
 class PobaError(RuntimeError):
@@ -239,6 +240,17 @@ def ba_kernel_launches(h: Handle) -> int:
     b = C.c_uint64()
     _check(library().ba_kernel_launches(h.ptr, C.byref(b)), "ba_kernel_launches")
     return b.value
+
+
+def ba_set_timing(h: Handle, enable: bool = True):
+    _check(library().ba_set_timing(h.ptr, 1 if enable else 0), "ba_set_timing")
+
+
+def ba_get_timing(h: Handle) -> dict:
+    """{class: (total_ms, count)} for the kernel classes of include/poba.h."""
+    t = _lib.Timing()
+    _check(library().ba_get_timing(h.ptr, C.byref(t)), "ba_get_timing")
+    return {name: (t.ms[i], int(t.count[i])) for i, name in enumerate(_lib.TIMING_CLASSES)}
 
 
 def ba_destroy(h: Handle):

@@ -40,6 +40,14 @@ class StepInfo(C.Structure):
                 ("converged", C.c_int32), ("iteration", C.c_int32)]
 
 
+TIMING_CLASSES = ["linearize", "damp_invert", "rhs", "series_tile", "series_camera", "backsub",
+                  "evaluate"]
+
+
+class Timing(C.Structure):
+    _fields_ = [("ms", C.c_double * 7), ("count", C.c_uint64 * 7)]
+
+
 # name -> (restype, argtypes); every symbol declared in include/poba.h
 SIGNATURES = {
     "ba_default_options": (C.c_int, [C.POINTER(Options)]),
@@ -60,6 +68,8 @@ SIGNATURES = {
     "ba_set_lm_state": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int32]),
     "ba_memory_footprint": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     "ba_kernel_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
+    "ba_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ba_get_timing": (C.c_int, [C.c_void_p, C.POINTER(Timing)]),
     "ba_destroy": (C.c_int, [C.c_void_p]),
     "ba_status_string": (C.c_char_p, [C.c_int]),
     "ba_last_error": (C.c_char_p, []),

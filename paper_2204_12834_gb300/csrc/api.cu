@@ -101,7 +101,17 @@ struct ba_handle {
   int graph_max_inner = -1;
   double graph_eps = -1.0;
   int graph_nodes = 0;
+  bool graph_timing = false;
   uint64_t launches = 0;
+
+  // kernel timing: event pairs per class; series classes have one pair per term
+  bool timing = false;
+  bool capturing = false;
+  int timing_terms = -1;
+  std::vector<cudaEvent_t> ev;  // layout: see ev_index()
+  double t_ms[BA_TIMING_CLASSES] = {0};
+  uint64_t t_count[BA_TIMING_CLASSES] = {0};
+  bool pending[BA_TIMING_CLASSES] = {false};
 
   bool f32() const { return precision == BA_FP32_BULK; }
 };
@@ -140,10 +150,75 @@ ba_status check_launch(ba_handle* h, const char* what) {
   return BA_OK;
 }
 
+// ---- kernel timing --------------------------------------------------------------------
+// Event pair index: classes 0, 1, 2, 5, 6 own one pair; classes 3 and 4 own one pair per term.
+enum { kTLin = 0, kTDamp = 1, kTRhs = 2, kTTile = 3, kTCam = 4, kTBack = 5, kTEval = 6 };
+
+int ev_index(const ba_handle* h, int cls, int term) {
+  const int M = h->timing_terms;
+  switch (cls) {
+    case kTLin: return 0;
+    case kTDamp: return 2;
+    case kTRhs: return 4;
+    case kTBack: return 6;
+    case kTEval: return 8;
+    case kTTile: return 10 + 2 * (term - 1);
+    default: return 10 + 2 * M + 2 * (term - 1);
+  }
+}
+
+ba_status ensure_events(ba_handle* h) {
+  if (h->timing_terms == h->opts.max_inner && !h->ev.empty()) return BA_OK;
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  h->ev.clear();
+  h->timing_terms = h->opts.max_inner;
+  const int n = 10 + 4 * h->opts.max_inner;
+  h->ev.resize(n);
+  for (int i = 0; i < n; ++i) CK(cudaEventCreate(&h->ev[i]));
+  return BA_OK;
+}
+
+// Record the start (which = 0) or end (1) event of a timed class on the handle's stream.
+void tmark(ba_handle* h, int cls, int term, int which) {
+  if (!h->timing) return;
+  cudaEvent_t e = h->ev[ev_index(h, cls, term) + which];
+  if (h->capturing) cudaEventRecordWithFlags(e, h->stream, cudaEventRecordExternal);
+  else cudaEventRecord(e, h->stream);
+  if (which == 1 && cls != kTTile && cls != kTCam) h->pending[cls] = true;
+}
+
+// After a stream synchronisation: add the elapsed time of every pair that ran.
+void collect_timing(ba_handle* h, int terms_run, bool series_ran) {
+  if (!h->timing) return;
+  float ms = 0.f;
+  for (int cls : {kTLin, kTDamp, kTRhs, kTBack, kTEval}) {
+    if (!h->pending[cls]) continue;
+    const int i = ev_index(h, cls, 0);
+    if (cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) == cudaSuccess) {
+      h->t_ms[cls] += ms;
+      h->t_count[cls] += 1;
+    }
+    h->pending[cls] = false;
+  }
+  if (series_ran) {
+    for (int term = 1; term <= terms_run && term <= h->timing_terms; ++term) {
+      for (int cls : {kTTile, kTCam}) {
+        const int i = ev_index(h, cls, term);
+        if (cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) == cudaSuccess) {
+          h->t_ms[cls] += ms;
+          h->t_count[cls] += 1;
+        }
+      }
+    }
+  }
+  cudaGetLastError();
+}
+
 // ---- kernel sequences ------------------------------------------------------------------
 
 void seq_linearize(ba_handle* h) {
   cudaStream_t s = h->stream;
+  tmark(h, kTLin, 0, 0);
   launch_cam_prepare(h->cams, nullptr, h->n_c, h->prep, nullptr, s);
   if (h->f32()) {
     launch_linearize<float>(h->tp, h->prep, h->lms, h->obs, h->sqrt_w, (float*)h->J, (float*)h->r,
@@ -154,6 +229,7 @@ void seq_linearize(ba_handle* h) {
                              (double*)h->r, h->V, h->b_l, (double*)h->partial, h->block_cost, s);
     launch_lin_camera_reduce<double>(h->tp, (const double*)h->partial, h->U45, h->b_p, s);
   }
+  tmark(h, kTLin, 0, 1);
   h->launches += 3;
 }
 
@@ -165,29 +241,44 @@ void seq_series_body(ba_handle* h, cudaStream_t s) {
   const T* Vi = h->f32() ? (const T*)(const void*)h->Vinv_f : (const T*)(const void*)h->Vinv;
   T* part = (T*)h->partial;
   launch_series_reset(h->st, s);
+  tmark(h, kTRhs, 0, 0);
   launch_tile_rhs<T>(tp, J, h->b_l, Vi, part, h->st, s);
   launch_camera_rhs<T>(tp, part, h->b_p, h->Uinv, h->x, h->t, h->block_norms, h->st, s);
+  tmark(h, kTRhs, 0, 1);
   for (int i = 1; i <= h->opts.max_inner; ++i) {
+    tmark(h, kTTile, i, 0);
     launch_tile_series<T>(tp, J, h->t, Vi, part, h->st, s);
+    tmark(h, kTTile, i, 1);
+    tmark(h, kTCam, i, 0);
     launch_camera_series<T>(tp, part, h->Uinv, h->x, h->t, h->block_norms, h->st, i, h->opts.eps, s);
+    tmark(h, kTCam, i, 1);
   }
+  tmark(h, kTBack, 0, 0);
   launch_tile_backsub<T>(tp, J, (const T*)h->r, h->x, h->b_l, Vi, h->dx_l, h->block_pred, s);
+  tmark(h, kTBack, 0, 1);
 }
 
 int series_body_kernels(const ba_handle* h) { return 4 + 2 * h->opts.max_inner; }
 
 ba_status run_series_body(ba_handle* h) {
   cudaStream_t s = h->stream;
+  if (h->timing) {
+    ba_status st = ensure_events(h);
+    if (st != BA_OK) return st;
+  }
   if (h->opts.use_graph) {
-    if (!h->graph_exec || h->graph_max_inner != h->opts.max_inner || h->graph_eps != h->opts.eps) {
+    if (!h->graph_exec || h->graph_max_inner != h->opts.max_inner || h->graph_eps != h->opts.eps ||
+        h->graph_timing != h->timing) {
       if (h->graph_exec) {
         cudaGraphExecDestroy(h->graph_exec);
         h->graph_exec = nullptr;
       }
       cudaGraph_t g = nullptr;
       CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      h->capturing = true;
       if (h->f32()) seq_series_body<float>(h, s);
       else seq_series_body<double>(h, s);
+      h->capturing = false;
       cudaError_t e = cudaStreamEndCapture(s, &g);
       if (e != cudaSuccess) return fail_cuda(e, "cudaStreamEndCapture");
       e = cudaGraphInstantiate(&h->graph_exec, g, 0);
@@ -198,8 +289,13 @@ ba_status run_series_body(ba_handle* h) {
       h->graph_nodes = (int)nn;
       h->graph_max_inner = h->opts.max_inner;
       h->graph_eps = h->opts.eps;
+      h->graph_timing = h->timing;
     }
     CK(cudaGraphLaunch(h->graph_exec, s));
+    if (h->timing) {
+      h->pending[kTRhs] = true;
+      h->pending[kTBack] = true;
+    }
     h->launches += (uint64_t)h->graph_nodes;
   } else {
     if (h->f32()) seq_series_body<float>(h, s);
@@ -211,8 +307,14 @@ ba_status run_series_body(ba_handle* h) {
 
 ba_status run_solve(ba_handle* h, const double* lam_dev) {
   CK(cudaMemsetAsync(h->not_spd, 0, sizeof(int32_t), h->stream));
+  if (h->timing) {
+    ba_status st = ensure_events(h);
+    if (st != BA_OK) return st;
+  }
+  tmark(h, kTDamp, 0, 0);
   launch_damp_invert(h->tp, h->U45, h->V, lam_dev, h->opts.damping_mode, h->Uinv, h->Vinv,
                      h->f32() ? h->Vinv_f : nullptr, h->not_spd, h->stream);
+  tmark(h, kTDamp, 0, 1);
   h->launches += 1;
   ba_status st = run_series_body(h);
   if (st != BA_OK) return st;
@@ -245,7 +347,9 @@ ba_status ba_default_options(ba_options* o) {
 
 ba_status ba_destroy(ba_handle* h) {
   if (!h) return BA_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->arena) cudaFree(h->arena);
   if (h->h_st) cudaFreeHost(h->h_st);
   if (h->h_rec) cudaFreeHost(h->h_rec);
@@ -489,6 +593,7 @@ ba_status ba_solve_schur_power(ba_handle* h, double lambda, ba_series_info* info
   CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SeriesState), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(h->h_flag, h->not_spd, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  collect_timing(h, h->h_st->m, true);
   info->inner_iters = h->h_st->m;
   info->stopped = h->h_st->stopped;
   info->stop_value = h->h_st->stop_value;
@@ -511,11 +616,13 @@ ba_status ba_lm_step(ba_handle* h, ba_step_info* info) {
   }
   ba_status st = run_solve(h, rec_field(h->rec, offsetof(LmRecord, lambda)));
   if (st != BA_OK) return st;
+  tmark(h, kTEval, 0, 0);
   launch_cam_prepare(h->cams, h->x, h->n_c, h->prep_trial, h->cams_trial, s);
   launch_cost(h->tp, h->prep_trial, h->lms, h->dx_l, h->obs, h->sqrt_w, h->block_cost, s);
   launch_lm_decide(h->block_cost, cost_blocks(h->tp), h->block_pred, h->tp.n_tiles, h->rec, h->st,
                    h->opts.func_tol, s);
   launch_apply_step(h->rec, h->cams, h->cams_trial, h->lms, h->dx_l, h->n_c, h->n_l, s);
+  tmark(h, kTEval, 0, 1);
   h->launches += 4;
   st = check_launch(h, "LM step kernels");
   if (st != BA_OK) return st;
@@ -523,6 +630,7 @@ ba_status ba_lm_step(ba_handle* h, ba_step_info* info) {
   CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SeriesState), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h->h_flag, h->not_spd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  collect_timing(h, h->h_st->m, true);
   const LmRecord& R = *h->h_rec;
   if (R.accepted) h->linearized = false;
   if (info) {
@@ -739,6 +847,28 @@ ba_status ba_memory_footprint(ba_handle* h, uint64_t* bytes) {
 ba_status ba_kernel_launches(ba_handle* h, uint64_t* count) {
   if (!h || !count) return fail(BA_ERR_INVALID_ARG, "NULL argument");
   *count = h->launches;
+  return BA_OK;
+}
+
+ba_status ba_set_timing(ba_handle* h, int32_t enable) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  CK(cudaStreamSynchronize(h->stream));
+  h->timing = enable != 0;
+  for (int c = 0; c < BA_TIMING_CLASSES; ++c) {
+    h->t_ms[c] = 0.0;
+    h->t_count[c] = 0;
+    h->pending[c] = false;
+  }
+  if (h->timing) return ensure_events(h);
+  return BA_OK;
+}
+
+ba_status ba_get_timing(ba_handle* h, ba_timing* out) {
+  if (!h || !out) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  for (int c = 0; c < BA_TIMING_CLASSES; ++c) {
+    out->ms[c] = h->t_ms[c];
+    out->count[c] = h->t_count[c];
+  }
   return BA_OK;
 }
 
