@@ -196,6 +196,31 @@ typedef struct {
 ba_status ba_set_timing(ba_handle* h, int32_t enable);
 ba_status ba_get_timing(ba_handle* h, ba_timing* out);
 
+/* Allocation-free cost evaluation.  The paper has no counterpart: this entry point exists for
+ * callers that must not let a library allocate device memory -- cudaMalloc and cudaFree
+ * synchronise the whole device, which latency-bound loops cannot afford, and processes whose
+ * device memory is owned by another allocator (a framework's caching allocator, or a budget
+ * fixed up front) must not take memory behind its back.
+ *
+ * Computes *cost_out = F(x) = 1/2 sum_o w_o ||r_o(x)||^2 in float64, like ba_cost, but without a
+ * handle: every pointer is device memory of the current device (cams [n_cams][9], lms
+ * [n_lms][3], obs [n_obs][2] 16-byte aligned, cam_idx / lm_idx [n_obs], weights [n_obs] or
+ * NULL, cost_out one double).  Work is queued on cuda_stream (NULL: the legacy default stream)
+ * and the call returns without synchronising.  It calls no cudaMalloc / cudaFree: its scratch
+ * (camera rotation records and per-block sums) is one fixed device array of
+ * BA_NOALLOC_MAX_CAMS * 25 + 2048 doubles (about 816 KiB) that every GPU using the library
+ * holds until the process exits.  n_cams above BA_NOALLOC_MAX_CAMS is rejected with
+ * BA_ERR_INVALID_ARG.  The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream capture.  All calls
+ * share the one array and it keeps the last call's contents; every entry a call reads is
+ * written earlier in the same call.  Calls that overlap on the GPU (other streams, other host
+ * threads) race on the array: order them.  An out-of-range index makes *cost_out NaN. */
+#define BA_NOALLOC_MAX_CAMS 4096
+ba_status ba_cost_noalloc(int32_t n_cams, int32_t n_lms, int32_t n_obs, const double* cams,
+                          const double* lms, const double* obs, const int32_t* cam_idx,
+                          const int32_t* lm_idx, const double* weights, double* cost_out,
+                          void* cuda_stream);
+
 /* Free all device memory of the handle (and its own stream, if it created one). NULL is OK. */
 ba_status ba_destroy(ba_handle* h);
 

@@ -24,7 +24,9 @@ __all__ = ["PobaError", "Handle", "ba_default_options", "ba_create", "ba_set_opt
            "ba_get_params", "ba_set_params", "ba_get_step", "ba_get_linearization",
            "ba_get_blocks", "ba_get_lm_state", "ba_set_lm_state", "ba_memory_footprint",
            "ba_kernel_launches", "ba_set_timing", "ba_get_timing", "ba_destroy", "BA_FP64",
-           "BA_FP32_BULK", "library", "from_problem"]
+           "BA_FP32_BULK", "library", "from_problem", "ba_cost_noalloc", "BA_NOALLOC_MAX_CAMS"]
+
+BA_NOALLOC_MAX_CAMS = 4096
 
 
 class PobaError(RuntimeError):
@@ -251,6 +253,29 @@ def ba_get_timing(h: Handle) -> dict:
     t = _lib.Timing()
     _check(library().ba_get_timing(h.ptr, C.byref(t)), "ba_get_timing")
     return {name: (t.ms[i], int(t.count[i])) for i, name in enumerate(_lib.TIMING_CLASSES)}
+
+
+def ba_cost_noalloc(cams, lms, obs, cam_idx, lm_idx, cost_out, weights=None, stream=None):
+    """Allocation-free cost evaluation: every argument is a CUDA tensor on the current device
+    (float64 / int32, contiguous) and the result is written to the one-element CUDA tensor
+    cost_out.  Nothing is allocated and nothing is synchronised."""
+    import torch
+    args = []
+    for a, dt in ((cams, torch.float64), (lms, torch.float64), (obs, torch.float64),
+                  (cam_idx, torch.int32), (lm_idx, torch.int32), (weights, torch.float64),
+                  (cost_out, torch.float64)):
+        if a is None:
+            args.append(None)
+            continue
+        if not (_is_torch(a) and a.is_cuda and a.is_contiguous() and a.dtype == dt):
+            raise ValueError("ba_cost_noalloc takes contiguous CUDA tensors of dtype float64 "
+                             "(indices int32); no conversion is made")
+        args.append(a.data_ptr())
+    st = None
+    if stream is not None:
+        st = int(getattr(stream, "cuda_stream", stream)) or None
+    _check(library().ba_cost_noalloc(int(cams.shape[0]), int(lms.shape[0]), int(obs.shape[0]),
+                                     *args, st), "ba_cost_noalloc")
 
 
 def ba_destroy(h: Handle):

@@ -70,6 +70,9 @@ SIGNATURES = {
     "ba_kernel_launches": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     "ba_set_timing": (C.c_int, [C.c_void_p, C.c_int32]),
     "ba_get_timing": (C.c_int, [C.c_void_p, C.POINTER(Timing)]),
+    "ba_cost_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p]),
     "ba_destroy": (C.c_int, [C.c_void_p]),
     "ba_status_string": (C.c_char_p, [C.c_int]),
     "ba_last_error": (C.c_char_p, []),

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpoba.so")
-SOURCES = ["schedule.cpp", "kernels_linearize.cu", "kernels_series.cu", "api.cu"]
+SOURCES = ["schedule.cpp", "kernels_linearize.cu", "kernels_series.cu", "api.cu", "noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "poba_internal.cuh"), os.path.join(CSRC, "tile_common.cuh"),
            os.path.join(ROOT, "include", "poba.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -44,6 +44,8 @@ double* rec_field(LmRecord* rec, size_t offset) { return (double*)((char*)rec + 
 
 }  // namespace
 
+void poba::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 struct ba_handle {
   int n_c = 0, n_l = 0, n_o = 0, n_o_pad = 0;
   int precision = BA_FP64;

@@ -110,6 +110,9 @@ struct LmRecord {
   int32_t pad;
 };
 
+// Sets the thread's ba_last_error() message (defined with the C ABI).
+void set_last_error(const std::string& msg);
+
 // ---------------------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files).  All take the stream last.
 void launch_cam_prepare(const double* cams, const double* dx_p, int n_cams, double* prep,
