@@ -192,6 +192,10 @@ PRESETS = {
     # Ladybug-1197-sized: 1,200 cameras, 160,000 landmarks, tracks U{3,4}, clustered (~560k obs)
     "clustered_1200c_160000l": dict(n_cams=1200, n_lms=160000, track=("uniform", 3, 4),
                                     visibility="clustered", window=8, seed=1002),
+    # 3,000 cameras, 400,000 landmarks, tracks U{3,4}, clustered (~1.4M obs): Jacobians larger
+    # than the GPU's L2, for profiling the series kernels
+    "clustered_3000c_400000l": dict(n_cams=3000, n_lms=400000, track=("uniform", 3, 4),
+                                    visibility="clustered", window=8, seed=1006),
     # Venice-1778-sized: 10,000 cameras, 1,000,000 landmarks, power-law tracks on [2, 50] (~5M obs)
     "powerlaw_10000c_1000000l": dict(n_cams=10000, n_lms=1000000,
                                      track=("powerlaw", 2.14, 2, 50), visibility="clustered",

@@ -57,7 +57,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--profile-steps", type=int, default=0,
-                    help="run only this many untimed FP64 LM steps (for ncu launch lists)")
+                    help="run only this many untimed LM steps (for ncu captures)")
+    ap.add_argument("--profile-precision", choices=["fp64", "fp32"], default="fp64")
     return ap.parse_args(argv)
 
 
@@ -148,13 +149,17 @@ def profiled_traffic(precision: str):
 
 
 # ---------------------------------------------------------------------------------------
-def series_tile_units(p, sched_slots: int, s: int):
-    """Algorithmic bytes and flops of one series tile launch (one term, tile half):
-    per observation J_p, J_l (24 s) and the 2-byte slot/position code, 48 FMA + 12 adds;
-    per landmark V^-1 (6 s) and its segment offset (4 B), 9 FMA; per slot one 9-vector write."""
-    n_o, n_l = p.n_obs, p.n_lms
-    bytes_ = n_o * (24 * s + 2) + n_l * (6 * s + 4) + sched_slots * 9 * s
-    flops = n_o * (2 * 48 + 12) + n_l * 18
+def series_term_units(p, sched_slots: int, s: int):
+    """Algorithmic bytes and flops of one power-series term t_i = U^-1 W V^-1 W^T t_{i-1}:
+    tile phase -- per observation J_p, J_l (24 s) and the 2-byte slot/position code, 48 FMA +
+    12 adds; per landmark V^-1 (6 s) and its segment offset (4 B), 9 FMA; per slot one 9-vector
+    partial written and the current term read (2 x 9 s);
+    camera phase -- per slot the partial read and the new term written (2 x 9 s), 9 adds; per
+    camera U^-1 (81 x 8 B) and x read / written (2 x 9 x 8 B), 81 FMA + 9 adds."""
+    n_o, n_l, n_c = p.n_obs, p.n_lms, p.n_cams
+    bytes_ = (n_o * (24 * s + 2) + n_l * (6 * s + 4) + sched_slots * 9 * s * 4
+              + n_c * (81 * 8 + 18 * 8))
+    flops = n_o * (2 * 48 + 12) + n_l * 18 + sched_slots * 9 + n_c * (2 * 81 + 9)
     return bytes_, flops
 
 
@@ -203,7 +208,7 @@ def run_poba(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     if args.profile_steps:
-        h = make(poba.BA_FP64)
+        h = make(poba.BA_FP64 if args.profile_precision == "fp64" else poba.BA_FP32_BULK)
         for _ in range(args.profile_steps):
             poba.ba_lm_step(h)
         torch.cuda.synchronize()
@@ -348,30 +353,34 @@ def run_poba(args):
     r_slots = schedule_slots(p)
 
     def roofline(name):
+        """Dominant kernel: the persistent series kernel (tile + camera phases and the two grid
+        barriers of every term).  Its timing class counts executed terms, so ms / count is the
+        average time of one term."""
         r = results[name]
         cls = max(r["timing"], key=lambda k: r["timing"][k][0])
         ms, cnt = r["timing"]["series_tile"]
         s = 8 if name == "fp64" else 4
-        nb, nf = series_tile_units(p, r_slots, s)
+        nb, nf = series_term_units(p, r_slots, s)
         avg_s = ms / 1e3 / max(cnt, 1)
         traffic = profiled_traffic(name)
+        prec = "double" if name == "fp64" else "float"
+        common = {"kernel": f"series_persistent_kernel<{prec}> (one series term: tile phase, "
+                            "camera phase, two grid barriers)",
+                  "traffic": traffic, "algorithmic_bytes_per_term": nb,
+                  "algorithmic_flops_per_term": nf, "avg_term_us": avg_s * 1e6, "terms": cnt,
+                  "dominant_class": cls}
         if name == "fp64":
             ach = nf / avg_s / 1e12
-            out = {"kernel": "tile_matvec<double> (series term)", "bound": "alu",
-                   "achieved": ach, "peak": FP64_PEAK_TFLOPS_DERIVED, "unit": "TFLOP/s",
-                   "frac": ach / FP64_PEAK_TFLOPS_DERIVED,
-                   "peak_kind": "derived FP64 FMA rate (152 SM x 2 FMA/clk x 2.07 GHz)",
-                   "traffic": traffic, "algorithmic_bytes": nb, "algorithmic_flops": nf,
-                   "avg_launch_us": avg_s * 1e6, "launches": cnt,
-                   "achieved_gbs": nb / avg_s / 1e9, "dominant_class": cls}
-        else:
-            ach = nb / avg_s / 1e9
-            out = {"kernel": "tile_matvec<float> (series term)", "bound": "hbm",
-                   "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                   "peak_kind": f"{hbm_kind} (MEASURED_PEAKS.json hbm_gbs)" if hbm_kind == "measured" else "fallback",
-                   "traffic": traffic, "algorithmic_bytes": nb, "algorithmic_flops": nf,
-                   "avg_launch_us": avg_s * 1e6, "launches": cnt, "dominant_class": cls}
-        return out
+            return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS_DERIVED,
+                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS_DERIVED,
+                    "peak_kind": "derived FP64 FMA rate (152 SM x 2 FMA/clk x 2.07 GHz)",
+                    "achieved_gbs": nb / avg_s / 1e9, **common}
+        ach = nb / avg_s / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak,
+                "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm_kind == "measured"
+                else "fallback 6800 GB/s",
+                "achieved_tflops": nf / avg_s / 1e12, **common}
 
     roof64 = roofline("fp64")
     roof32 = roofline("fp32_bulk")

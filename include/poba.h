@@ -44,7 +44,8 @@ typedef enum {
   BA_ERR_NOT_SPD = 4,        /* a damped U or V block had a non-positive Cholesky pivot */
   BA_ERR_NONFINITE = 5,      /* non-finite input, residual, cost or step */
   BA_ERR_NOT_LINEARIZED = 6, /* a solve was requested before ba_linearize */
-  BA_ERR_TIMEOUT = 7         /* a bounded device-side wait gave up */
+  BA_ERR_TIMEOUT = 7         /* a bounded device-side wait gave up (a grid barrier of the
+                                persistent series kernel waited longer than its limit) */
 } ba_status;
 
 typedef enum {
@@ -75,7 +76,10 @@ typedef struct {
   int32_t max_lm;       /* LM iteration cap, Sec. 5.1: 50 */
   int32_t max_inner;    /* cap on series terms beyond x(0), Sec. 5.1: 20 */
   int32_t damping_mode; /* 0: D^T D = diag(J^T J) clamped to [1e-6, 1e32]; 1: D = I */
-  int32_t use_graph;    /* 1: replay the series loop as a captured CUDA graph (default) */
+  int32_t series_exec;  /* how the series loop runs: 0 one launch per kernel, 1 the same launches
+                           replayed as a captured CUDA graph, 2 one persistent cooperative kernel
+                           for all terms with bounded grid barriers (default; falls back to 1
+                           when the device cannot make all its blocks co-resident) */
 } ba_options;
 
 typedef struct {
@@ -100,7 +104,7 @@ typedef struct {
 } ba_step_info;
 
 /* Fill *opts with the defaults of Sec. 5.1 (lambda0 1e-4, func_tol 1e-6, eps 0.01, max_lm 50,
- * max_inner 20, damping_mode 0, use_graph 1).  Returns BA_ERR_INVALID_ARG if opts is NULL. */
+ * max_inner 20, damping_mode 0, series_exec 2).  Returns BA_ERR_INVALID_ARG if opts is NULL. */
 ba_status ba_default_options(ba_options* opts);
 
 /* Create a problem handle (Sec. 4: state x = (x_p, x_l), residuals r(x)).  Copies and
@@ -127,7 +131,7 @@ ba_status ba_linearize(ba_handle* h, double* cost_out);
  * dx_l = -V_lambda^-1 (b_l + W^T dx_p) (Sec. 4.2; sign derived from eq. `normal`).  The step
  * stays on the device (read it with ba_get_step).  info may be NULL (then nothing is
  * synchronised).  Errors: BA_ERR_NOT_LINEARIZED, BA_ERR_INVALID_ARG (lambda <= 0 or not
- * finite), BA_ERR_NOT_SPD (reported when info != NULL), BA_ERR_CUDA. */
+ * finite), BA_ERR_NOT_SPD and BA_ERR_TIMEOUT (reported when info != NULL), BA_ERR_CUDA. */
 ba_status ba_solve_schur_power(ba_handle* h, double lambda, ba_series_info* info);
 
 /* One Levenberg-Marquardt iteration (Sec. 5.1 "LM loop"): linearise if the state changed,
@@ -136,7 +140,7 @@ ba_status ba_solve_schur_power(ba_handle* h, double lambda, ba_series_info* info
  * positive, update lambda (accept: lambda *= max(1/3, 1 - (2 rho - 1)^3), nu = 2; reject:
  * lambda *= nu, nu *= 2; clamp to [1e-10, 1e32]) and apply an accepted step.  Synchronises
  * once.  info may be NULL.  Errors: BA_ERR_NOT_SPD, BA_ERR_NONFINITE (non-finite cost at the
- * current state), BA_ERR_CUDA. */
+ * current state), BA_ERR_TIMEOUT, BA_ERR_CUDA. */
 ba_status ba_lm_step(ba_handle* h, ba_step_info* info);
 
 /* Run ba_lm_step until convergence (func_tol) or max_lm iterations.  trace may be NULL or
@@ -223,6 +227,17 @@ ba_status ba_cost_noalloc(int32_t n_cams, int32_t n_lms, int32_t n_obs, const do
 
 /* Free all device memory of the handle (and its own stream, if it created one). NULL is OK. */
 ba_status ba_destroy(ba_handle* h);
+
+/* Phase timeline of the last persistent series solve (series_exec 2): for each executed term
+ * (at most 64), five %globaltimer readings in ns taken by block 0 -- term start, end of its
+ * tile phase, release of the first grid barrier, end of its camera phase, release of the
+ * second barrier.  Copies min(capacity, 5 * terms) values; *n_terms receives the terms. */
+ba_status ba_get_series_trace(ba_handle* h, int64_t* ns, int32_t capacity, int32_t* n_terms);
+
+/* Test hook for the bounded grid barriers: the limit, in GPU clock cycles, that a block of the
+ * persistent series kernel waits at a barrier before it gives up (default 2^33, several
+ * seconds).  Values < 1 restore the default. */
+ba_status ba_set_barrier_timeout(ba_handle* h, int64_t cycles);
 
 /* Static string for a status code. */
 const char* ba_status_string(ba_status s);

@@ -24,7 +24,8 @@ __all__ = ["PobaError", "Handle", "ba_default_options", "ba_create", "ba_set_opt
            "ba_get_params", "ba_set_params", "ba_get_step", "ba_get_linearization",
            "ba_get_blocks", "ba_get_lm_state", "ba_set_lm_state", "ba_memory_footprint",
            "ba_kernel_launches", "ba_set_timing", "ba_get_timing", "ba_destroy", "BA_FP64",
-           "BA_FP32_BULK", "library", "from_problem", "ba_cost_noalloc", "BA_NOALLOC_MAX_CAMS"]
+           "BA_FP32_BULK", "library", "from_problem", "ba_cost_noalloc", "BA_NOALLOC_MAX_CAMS",
+           "ba_get_series_trace", "ba_set_barrier_timeout"]
 
 BA_NOALLOC_MAX_CAMS = 4096
 
@@ -276,6 +277,19 @@ def ba_cost_noalloc(cams, lms, obs, cam_idx, lm_idx, cost_out, weights=None, str
         st = int(getattr(stream, "cuda_stream", stream)) or None
     _check(library().ba_cost_noalloc(int(cams.shape[0]), int(lms.shape[0]), int(obs.shape[0]),
                                      *args, st), "ba_cost_noalloc")
+
+
+def ba_get_series_trace(h: Handle):
+    """[terms, 5] ns timeline of block 0 in the last persistent series solve (see poba.h)."""
+    buf = np.zeros(64 * 5, dtype=np.int64)
+    n = C.c_int32()
+    _check(library().ba_get_series_trace(h.ptr, buf.ctypes.data, buf.size, C.byref(n)),
+           "ba_get_series_trace")
+    return buf[: 5 * n.value].reshape(n.value, 5)
+
+
+def ba_set_barrier_timeout(h: Handle, cycles: int):
+    _check(library().ba_set_barrier_timeout(h.ptr, int(cycles)), "ba_set_barrier_timeout")
 
 
 def ba_destroy(h: Handle):

@@ -25,7 +25,7 @@ class ProblemDesc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("lambda0", C.c_double), ("func_tol", C.c_double), ("eps", C.c_double),
                 ("max_lm", C.c_int32), ("max_inner", C.c_int32), ("damping_mode", C.c_int32),
-                ("use_graph", C.c_int32)]
+                ("series_exec", C.c_int32)]
 
 
 class SeriesInfo(C.Structure):
@@ -73,6 +73,8 @@ SIGNATURES = {
     "ba_cost_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p]),
+    "ba_set_barrier_timeout": (C.c_int, [C.c_void_p, C.c_int64]),
+    "ba_get_series_trace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     "ba_destroy": (C.c_int, [C.c_void_p]),
     "ba_status_string": (C.c_char_p, [C.c_int]),
     "ba_last_error": (C.c_char_p, []),

@@ -16,8 +16,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpoba.so")
-SOURCES = ["schedule.cpp", "kernels_linearize.cu", "kernels_series.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["schedule.cpp", "kernels_linearize.cu", "kernels_series.cu", "kernels_persistent.cu",
+           "api.cu", "noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "poba_internal.cuh"), os.path.join(CSRC, "tile_common.cuh"),
+           os.path.join(CSRC, "series_body.cuh"),
            os.path.join(ROOT, "include", "poba.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",

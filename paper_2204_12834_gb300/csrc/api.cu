@@ -71,6 +71,7 @@ struct ba_handle {
   void* J = nullptr;
   void* r = nullptr;
   void* partial = nullptr;
+  void* t_cm = nullptr;  // current series term per camera-major slot row (bulk precision)
   double* U45 = nullptr;
   double* b_p = nullptr;
   double* V = nullptr;
@@ -80,18 +81,21 @@ struct ba_handle {
   float* Vinv_f = nullptr;
   // series
   double* x = nullptr;
-  double* t = nullptr;
   double* dx_l = nullptr;
   double* block_norms = nullptr;
   double* block_cost = nullptr;
   double* block_pred = nullptr;
   double* scalars = nullptr;  // [0] lambda for explicit solves, [1] cost out
+  double* group_norms = nullptr;  // persistent kernel: squared norms per camera group
+  GridSync* gs = nullptr;         // persistent kernel: grid-barrier state
+  long long* trace = nullptr;     // persistent kernel: phase timeline of block 0
   SeriesState* st = nullptr;
   LmRecord* rec = nullptr;
   int32_t* not_spd = nullptr;
 
   // host staging (pinned)
   SeriesState* h_st = nullptr;
+  GridSync* h_gs = nullptr;
   LmRecord* h_rec = nullptr;
   int32_t* h_flag = nullptr;
   double* h_scalar = nullptr;
@@ -104,6 +108,9 @@ struct ba_handle {
   double graph_eps = -1.0;
   int graph_nodes = 0;
   bool graph_timing = false;
+  int persist_grid = 0;                  // blocks of the persistent kernel (0: unavailable)
+  long long barrier_timeout = 1LL << 33;  // clock cycles a block waits at a grid barrier
+  int last_exec = -1;                    // series_exec of the last solve
   uint64_t launches = 0;
 
   // kernel timing: event pairs per class; series classes have one pair per term
@@ -127,6 +134,7 @@ bool valid_options(const ba_options& o, std::string* why) {
   if (o.max_lm < 0 || o.max_lm > 100000) { *why = "max_lm out of range"; return false; }
   if (o.max_inner < 0 || o.max_inner > 10000) { *why = "max_inner out of range [0, 10000]"; return false; }
   if (o.damping_mode != 0 && o.damping_mode != 1) { *why = "damping_mode must be 0 or 1"; return false; }
+  if (o.series_exec < 0 || o.series_exec > 2) { *why = "series_exec must be 0, 1 or 2"; return false; }
   return true;
 }
 
@@ -202,7 +210,14 @@ void collect_timing(ba_handle* h, int terms_run, bool series_ran) {
     }
     h->pending[cls] = false;
   }
-  if (series_ran) {
+  if (series_ran && h->last_exec == 2) {
+    // one pair around the persistent kernel, counted once per executed term
+    const int i = ev_index(h, kTTile, 1);
+    if (terms_run >= 1 && cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) == cudaSuccess) {
+      h->t_ms[kTTile] += ms;
+      h->t_count[kTTile] += (uint64_t)terms_run;
+    }
+  } else if (series_ran) {
     for (int term = 1; term <= terms_run && term <= h->timing_terms; ++term) {
       for (int cls : {kTTile, kTCam}) {
         const int i = ev_index(h, cls, term);
@@ -245,14 +260,15 @@ void seq_series_body(ba_handle* h, cudaStream_t s) {
   launch_series_reset(h->st, s);
   tmark(h, kTRhs, 0, 0);
   launch_tile_rhs<T>(tp, J, h->b_l, Vi, part, h->st, s);
-  launch_camera_rhs<T>(tp, part, h->b_p, h->Uinv, h->x, h->t, h->block_norms, h->st, s);
+  launch_camera_rhs<T>(tp, part, h->b_p, h->Uinv, h->x, (T*)h->t_cm, h->block_norms, h->st, s);
   tmark(h, kTRhs, 0, 1);
   for (int i = 1; i <= h->opts.max_inner; ++i) {
     tmark(h, kTTile, i, 0);
-    launch_tile_series<T>(tp, J, h->t, Vi, part, h->st, s);
+    launch_tile_series<T>(tp, J, (const T*)h->t_cm, Vi, part, h->st, s);
     tmark(h, kTTile, i, 1);
     tmark(h, kTCam, i, 0);
-    launch_camera_series<T>(tp, part, h->Uinv, h->x, h->t, h->block_norms, h->st, i, h->opts.eps, s);
+    launch_camera_series<T>(tp, part, h->Uinv, h->x, (T*)h->t_cm, h->block_norms, h->st, i,
+                            h->opts.eps, s);
     tmark(h, kTCam, i, 1);
   }
   tmark(h, kTBack, 0, 0);
@@ -262,13 +278,48 @@ void seq_series_body(ba_handle* h, cudaStream_t s) {
 
 int series_body_kernels(const ba_handle* h) { return 4 + 2 * h->opts.max_inner; }
 
+template <typename T>
+ba_status seq_series_persistent(ba_handle* h, cudaStream_t s) {
+  const Topology& tp = h->tp;
+  const T* J = (const T*)h->J;
+  const T* Vi = h->f32() ? (const T*)(const void*)h->Vinv_f : (const T*)(const void*)h->Vinv;
+  T* part = (T*)h->partial;
+  launch_series_reset(h->st, s);
+  tmark(h, kTRhs, 0, 0);
+  launch_tile_rhs<T>(tp, J, h->b_l, Vi, part, h->st, s);
+  launch_camera_rhs<T>(tp, part, h->b_p, h->Uinv, h->x, (T*)h->t_cm, h->block_norms, h->st, s);
+  tmark(h, kTRhs, 0, 1);
+  CK(cudaMemsetAsync(h->gs, 0, sizeof(GridSync), s));
+  if (h->opts.max_inner > 0) {
+    tmark(h, kTTile, 1, 0);
+    CK(launch_series_persistent<T>(tp, h->persist_grid, J, Vi, h->b_l, h->b_p, h->Uinv, h->x,
+                                   (T*)h->t_cm, part, h->group_norms, h->st, h->gs,
+                                   h->opts.max_inner, h->opts.eps, h->barrier_timeout, h->trace,
+                                   s));
+    tmark(h, kTTile, 1, 1);
+  }
+  tmark(h, kTBack, 0, 0);
+  launch_tile_backsub<T>(tp, J, (const T*)h->r, h->x, h->b_l, Vi, h->dx_l, h->block_pred, s);
+  tmark(h, kTBack, 0, 1);
+  h->launches += 5;
+  return BA_OK;
+}
+
 ba_status run_series_body(ba_handle* h) {
   cudaStream_t s = h->stream;
   if (h->timing) {
     ba_status st = ensure_events(h);
     if (st != BA_OK) return st;
   }
-  if (h->opts.use_graph) {
+  int mode = h->opts.series_exec;
+  if (mode == 2 && h->persist_grid <= 0) mode = 1;
+  h->last_exec = mode;
+  if (mode == 2) {
+    ba_status st = h->f32() ? seq_series_persistent<float>(h, s) : seq_series_persistent<double>(h, s);
+    if (st == BA_OK) h->pending[kTRhs] = h->pending[kTBack] = h->timing;
+    return st;
+  }
+  if (mode == 1) {
     if (!h->graph_exec || h->graph_max_inner != h->opts.max_inner || h->graph_eps != h->opts.eps ||
         h->graph_timing != h->timing) {
       if (h->graph_exec) {
@@ -298,7 +349,7 @@ ba_status run_series_body(ba_handle* h) {
       h->pending[kTRhs] = true;
       h->pending[kTBack] = true;
     }
-    h->launches += (uint64_t)h->graph_nodes;
+    h->launches += (uint64_t)series_body_kernels(h);
   } else {
     if (h->f32()) seq_series_body<float>(h, s);
     else seq_series_body<double>(h, s);
@@ -343,7 +394,7 @@ ba_status ba_default_options(ba_options* o) {
   o->max_lm = 50;
   o->max_inner = 20;
   o->damping_mode = 0;
-  o->use_graph = 1;
+  o->series_exec = 2;
   return BA_OK;
 }
 
@@ -355,6 +406,7 @@ ba_status ba_destroy(ba_handle* h) {
   if (h->arena) cudaFree(h->arena);
   if (h->h_st) cudaFreeHost(h->h_st);
   if (h->h_rec) cudaFreeHost(h->h_rec);
+  if (h->h_gs) cudaFreeHost(h->h_gs);
   if (h->h_flag) cudaFreeHost(h->h_flag);
   if (h->h_scalar) cudaFreeHost(h->h_scalar);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -418,9 +470,11 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
   struct Item { void** ptr; size_t bytes; };
   std::vector<Item> items;
   int32_t *d_lm_seg, *d_cam_of, *d_lm_of, *d_tile_lm0, *d_tile_slot0, *d_slot_cam, *d_cam_slot_ptr, *d_cam_slot_list;
+  int32_t* d_tile_desc;
+  int32_t* d_slot_row;
   uint16_t *d_meta, *d_slot_beg;
   const size_t slots = (size_t)(S.n_slots > 0 ? S.n_slots : 1);
-  const int nbn = (nc + kCamBlock - 1) / kCamBlock;
+  const int nbn = (nc + kCamBlock - 1) / kCamBlock;  // camera-step blocks
   Topology tmp{};
   tmp.n_obs = no;
   const int ncost = cost_blocks(tmp);
@@ -430,10 +484,12 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
   items.push_back({(void**)&d_meta, sizeof(uint16_t) * (no > 0 ? no : 1)});
   items.push_back({(void**)&d_tile_lm0, sizeof(int32_t) * (S.n_tiles + 1)});
   items.push_back({(void**)&d_tile_slot0, sizeof(int32_t) * (S.n_tiles + 1)});
+  items.push_back({(void**)&d_tile_desc, sizeof(int32_t) * 8 * S.n_tiles});
   items.push_back({(void**)&d_slot_cam, sizeof(int32_t) * slots});
   items.push_back({(void**)&d_slot_beg, sizeof(uint16_t) * slots});
   items.push_back({(void**)&d_cam_slot_ptr, sizeof(int32_t) * (nc + 1)});
   items.push_back({(void**)&d_cam_slot_list, sizeof(int32_t) * slots});
+  items.push_back({(void**)&d_slot_row, sizeof(int32_t) * slots});
   items.push_back({(void**)&h->obs, sizeof(double2) * (no > 0 ? no : 1)});
   if (h->weighted) items.push_back({(void**)&h->sqrt_w, sizeof(double) * no});
   items.push_back({(void**)&h->cams, sizeof(double) * nc * 9});
@@ -444,6 +500,7 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
   items.push_back({&h->J, bulk * 24 * h->n_o_pad});
   items.push_back({&h->r, bulk * 2 * h->n_o_pad});
   items.push_back({&h->partial, bulk * kLinVals * slots});
+  items.push_back({&h->t_cm, bulk * 9 * slots});
   items.push_back({(void**)&h->U45, sizeof(double) * nc * 45});
   items.push_back({(void**)&h->b_p, sizeof(double) * nc * 9});
   items.push_back({(void**)&h->V, sizeof(double) * nl * 6});
@@ -452,12 +509,16 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
   items.push_back({(void**)&h->Vinv, sizeof(double) * nl * 6});
   if (h->f32()) items.push_back({(void**)&h->Vinv_f, sizeof(float) * nl * 6});
   items.push_back({(void**)&h->x, sizeof(double) * nc * 9});
-  items.push_back({(void**)&h->t, sizeof(double) * nc * 9});
   items.push_back({(void**)&h->dx_l, sizeof(double) * nl * 3});
   items.push_back({(void**)&h->block_norms, sizeof(double) * 2 * nbn});
   items.push_back({(void**)&h->block_cost, sizeof(double) * (S.n_tiles > ncost ? S.n_tiles : ncost)});
   items.push_back({(void**)&h->block_pred, sizeof(double) * S.n_tiles});
   items.push_back({(void**)&h->scalars, sizeof(double) * 4});
+  // persistent kernel: one (||t||^2, ||x||^2) pair per camera group; a group holds at least one
+  // camera, so there are at most n_cams groups whatever the grid size
+  items.push_back({(void**)&h->group_norms, sizeof(double) * 2 * nc});
+  items.push_back({(void**)&h->gs, sizeof(GridSync)});
+  items.push_back({(void**)&h->trace, sizeof(long long) * kTraceTerms * kTracePoints});
   items.push_back({(void**)&h->st, sizeof(SeriesState)});
   items.push_back({(void**)&h->rec, sizeof(LmRecord)});
   items.push_back({(void**)&h->not_spd, sizeof(int32_t)});
@@ -489,6 +550,7 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
   if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMemset(arena)"));
   if ((e = cudaMallocHost(&h->h_st, sizeof(SeriesState))) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_rec, sizeof(LmRecord))) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_gs, sizeof(GridSync))) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_flag, sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_scalar, sizeof(double) * 4)) != cudaSuccess)
     return bail(fail_cuda(e, "cudaMallocHost"));
@@ -514,10 +576,12 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
       {d_meta, S.obs_meta.data(), sizeof(uint16_t) * no},
       {d_tile_lm0, S.tile_lm0.data(), sizeof(int32_t) * (S.n_tiles + 1)},
       {d_tile_slot0, S.tile_slot0.data(), sizeof(int32_t) * (S.n_tiles + 1)},
+      {d_tile_desc, S.tile_desc.data(), sizeof(int32_t) * 8 * S.n_tiles},
       {d_slot_cam, S.slot_cam.data(), sizeof(int32_t) * S.n_slots},
       {d_slot_beg, S.slot_beg.data(), sizeof(uint16_t) * S.n_slots},
       {d_cam_slot_ptr, S.cam_slot_ptr.data(), sizeof(int32_t) * (nc + 1)},
       {d_cam_slot_list, S.cam_slot_list.data(), sizeof(int32_t) * S.n_slots},
+      {d_slot_row, S.slot_row.data(), sizeof(int32_t) * S.n_slots},
       {h->obs, obs_s.data(), sizeof(double) * 2 * no},
       {h->cams, cams.data(), sizeof(double) * nc * 9},
       {h->lms, lms_i.data(), sizeof(double) * nl * 3},
@@ -527,6 +591,16 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
     if (u.bytes == 0) continue;
     e = cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMemcpy(upload)"));
+  }
+  {
+    // persistent series kernel: all blocks must be co-resident (cooperative launch)
+    int dev = 0, sms = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    const int per_sm = persistent_blocks_per_sm(h->f32());
+    h->persist_grid = (coop && per_sm > 0) ? per_sm * sms : 0;
+    cudaGetLastError();
   }
   LmRecord r0{};
   r0.cost = NAN;
@@ -548,10 +622,12 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
   tp.obs_meta = d_meta;
   tp.tile_lm0 = d_tile_lm0;
   tp.tile_slot0 = d_tile_slot0;
+  tp.tile_desc = (const int4*)d_tile_desc;
   tp.slot_cam = d_slot_cam;
   tp.slot_beg = d_slot_beg;
   tp.cam_slot_ptr = d_cam_slot_ptr;
   tp.cam_slot_list = d_cam_slot_list;
+  tp.slot_row = d_slot_row;
   *out = h;
   g_last_error.clear();
   return BA_OK;
@@ -594,8 +670,11 @@ ba_status ba_solve_schur_power(ba_handle* h, double lambda, ba_series_info* info
   if (!info) return BA_OK;
   CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SeriesState), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(h->h_flag, h->not_spd, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   collect_timing(h, h->h_st->m, true);
+  if (h->last_exec == 2 && h->h_gs->error)
+    return fail(BA_ERR_TIMEOUT, "a grid barrier of the persistent series kernel timed out");
   info->inner_iters = h->h_st->m;
   info->stopped = h->h_st->stopped;
   info->stop_value = h->h_st->stop_value;
@@ -631,8 +710,11 @@ ba_status ba_lm_step(ba_handle* h, ba_step_info* info) {
   CK(cudaMemcpyAsync(h->h_rec, h->rec, sizeof(LmRecord), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SeriesState), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h->h_flag, h->not_spd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   collect_timing(h, h->h_st->m, true);
+  if (h->last_exec == 2 && h->h_gs->error)
+    return fail(BA_ERR_TIMEOUT, "a grid barrier of the persistent series kernel timed out");
   const LmRecord& R = *h->h_rec;
   if (R.accepted) h->linearized = false;
   if (info) {
@@ -837,6 +919,24 @@ ba_status ba_set_lm_state(ba_handle* h, double lambda, double nu, int32_t iterat
   *h->h_rec = r;
   CK(cudaMemcpyAsync(h->rec, h->h_rec, sizeof(LmRecord), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  return BA_OK;
+}
+
+ba_status ba_get_series_trace(ba_handle* h, int64_t* ns, int32_t capacity, int32_t* n_terms) {
+  if (!h || !ns || capacity < 0) return fail(BA_ERR_INVALID_ARG, "bad argument");
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(h->h_st, h->st, sizeof(SeriesState), cudaMemcpyDeviceToHost));
+  int terms = h->last_exec == 2 ? h->h_st->m : 0;
+  if (terms > kTraceTerms) terms = kTraceTerms;
+  const int n = terms * kTracePoints < capacity ? terms * kTracePoints : capacity;
+  if (n > 0) CK(cudaMemcpy(ns, h->trace, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
+  if (n_terms) *n_terms = terms;
+  return BA_OK;
+}
+
+ba_status ba_set_barrier_timeout(ba_handle* h, int64_t cycles) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  h->barrier_timeout = cycles < 1 ? (1LL << 33) : (long long)cycles;
   return BA_OK;
 }
 

@@ -111,11 +111,11 @@ __device__ __forceinline__ T lin_entry(const T (&jp)[18], const T (&rr)[2]) {
 }
 
 // One round of 9 camera values: stage at the observation's camera-sorted position, then sum
-// per slot into partial[slot * 54 + ROUND * 9 + k].
+// per slot into partial[row(slot) * 54 + ROUND * 9 + k].
 template <int ROUND, typename T>
 __device__ __forceinline__ void lin_round(bool active, const T (&jp)[18], const T (&rr)[2], int pos,
                                           T (*sg)[9], int ns, int n, const uint16_t* sbeg,
-                                          T* partial_tile) {
+                                          const int* srow, T* partial) {
   if (active) {
     sg[pos][0] = lin_entry<ROUND * 9 + 0>(jp, rr);
     sg[pos][1] = lin_entry<ROUND * 9 + 1>(jp, rr);
@@ -128,7 +128,7 @@ __device__ __forceinline__ void lin_round(bool active, const T (&jp)[18], const 
     sg[pos][8] = lin_entry<ROUND * 9 + 8>(jp, rr);
   }
   __syncthreads();
-  slot_sums<T, T>(sg, ns, n, sbeg, partial_tile + ROUND * 9, kLinVals);
+  slot_sums<T, T>(sg, ns, n, sbeg, srow, partial + ROUND * 9, kLinVals);
   __syncthreads();
 }
 
@@ -198,13 +198,17 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
   __shared__ T s9[kTileObs][9];
   __shared__ T sg[kTileObs][9];
   __shared__ uint16_t sbeg[kTileObs];
+  __shared__ int srow[kTileObs];
   __shared__ double sred[kTileObs / 32];
 
   const int tile = blockIdx.x, tid = threadIdx.x;
   const int L0 = tp.tile_lm0[tile], L1 = tp.tile_lm0[tile + 1];
   const int o0 = tp.lm_seg[L0], n = tp.lm_seg[L1] - o0;
   const int S0 = tp.tile_slot0[tile], ns = tp.tile_slot0[tile + 1] - S0;
-  for (int i = tid; i < ns; i += blockDim.x) sbeg[i] = tp.slot_beg[S0 + i];
+  for (int i = tid; i < ns; i += blockDim.x) {
+    sbeg[i] = tp.slot_beg[S0 + i];
+    srow[i] = tp.slot_row[S0 + i];
+  }
 
   T jp[18], jl[6], rr[2];
   int pos = 0;
@@ -254,12 +258,12 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
     for (int k = 0; k < 3; ++k) b_l[(size_t)l * 3 + k] = (double)acc[6 + k];
   }
   // camera contributions in 6 rounds of 9 values: 45 packed J_p^T J_p entries, then J_p^T r
-  lin_round<0>(active, jp, rr, pos, sg, ns, n, sbeg, partial + (size_t)S0 * kLinVals);
-  lin_round<1>(active, jp, rr, pos, sg, ns, n, sbeg, partial + (size_t)S0 * kLinVals);
-  lin_round<2>(active, jp, rr, pos, sg, ns, n, sbeg, partial + (size_t)S0 * kLinVals);
-  lin_round<3>(active, jp, rr, pos, sg, ns, n, sbeg, partial + (size_t)S0 * kLinVals);
-  lin_round<4>(active, jp, rr, pos, sg, ns, n, sbeg, partial + (size_t)S0 * kLinVals);
-  lin_round<5>(active, jp, rr, pos, sg, ns, n, sbeg, partial + (size_t)S0 * kLinVals);
+  lin_round<0>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
+  lin_round<1>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
+  lin_round<2>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
+  lin_round<3>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
+  lin_round<4>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
+  lin_round<5>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
   // block cost (fixed order)
   const double tot = block_sum_fixed(cost, sred);
   if (tid == 0 && block_cost) block_cost[tile] = tot;
@@ -288,9 +292,18 @@ __global__ void lin_camera_reduce_kernel(Topology tp, const PT* __restrict__ par
   const int c = blockIdx.x * 4 + threadIdx.x / per;
   const int k = threadIdx.x % per;
   if (c >= tp.n_cams) return;
-  double acc = 0.0;
-  for (int s = tp.cam_slot_ptr[c]; s < tp.cam_slot_ptr[c + 1]; ++s)
-    acc += (double)partial[(size_t)tp.cam_slot_list[s] * per + k];
+  // the camera's slot rows are contiguous (camera-major)
+  const int r0 = tp.cam_slot_ptr[c], r1 = tp.cam_slot_ptr[c + 1];
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int r = r0;
+  for (; r + 4 <= r1; r += 4) {
+    a0 += (double)partial[(size_t)(r + 0) * per + k];
+    a1 += (double)partial[(size_t)(r + 1) * per + k];
+    a2 += (double)partial[(size_t)(r + 2) * per + k];
+    a3 += (double)partial[(size_t)(r + 3) * per + k];
+  }
+  for (; r < r1; ++r) a0 += (double)partial[(size_t)r * per + k];
+  const double acc = (a0 + a1) + (a2 + a3);
   if (k < 45) U45[(size_t)c * 45 + k] = acc;
   else b_p[(size_t)c * 9 + (k - 45)] = acc;
 }
@@ -314,60 +327,82 @@ __device__ __forceinline__ double damp_diag(double d, double lam, int mode) {
   return mode == 0 ? lam * fmin(fmax(d, kDampMin), kDampMax) : lam;
 }
 
-__global__ void damp_invert_kernel(Topology tp, const double* __restrict__ U45,
-                                   const double* __restrict__ V, const double* __restrict__ lambda,
-                                   int mode, int cam_blocks, double* __restrict__ Uinv,
-                                   double* __restrict__ Vinv, float* __restrict__ Vinv_f,
-                                   int32_t* __restrict__ not_spd) {
+// Camera blocks: kCamBlock cameras x 9 threads.  Thread k of a camera loads row k; the 9
+// threads factor A = L L^T column by column (the diagonal keeps 1/L_jj, from rsqrt); thread k
+// then computes column k of M = L^-1 by forward substitution and row k of A^-1 = M^T M.
+// Landmark blocks: one thread per landmark, the same steps for a 3x3 block.
+constexpr int kDampThreads = kCamBlock * 9;
+
+__global__ void __launch_bounds__(kDampThreads) damp_invert_kernel(
+    Topology tp, const double* __restrict__ U45, const double* __restrict__ V,
+    const double* __restrict__ lambda, int mode, int cam_blocks, double* __restrict__ Uinv,
+    double* __restrict__ Vinv, float* __restrict__ Vinv_f, int32_t* __restrict__ not_spd) {
   const double lam = *lambda;
+  const int tid = threadIdx.x;
   if ((int)blockIdx.x < cam_blocks) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= tp.n_cams) return;
-    double A[9][9];
-    for (int i = 0; i < 9; ++i)
-      for (int j = i; j < 9; ++j) {
-        const double v = U45[(size_t)c * 45 + packed9(i, j)];
-        A[i][j] = v;
-        A[j][i] = v;
+    __shared__ double A[kCamBlock][9][10];
+    __shared__ double M[kCamBlock][9][10];
+    const int cl = tid / 9, k = tid - cl * 9;
+    const int c = blockIdx.x * kCamBlock + cl;
+    const bool ok_cam = c < tp.n_cams;
+    if (ok_cam) {
+#pragma unroll
+      for (int j = 0; j < 9; ++j) {
+        const int i0 = k < j ? k : j, j0 = k < j ? j : k;
+        A[cl][k][j] = U45[(size_t)c * 45 + packed9(i0, j0)];
       }
-    for (int i = 0; i < 9; ++i) A[i][i] += damp_diag(A[i][i], lam, mode);
-    // Cholesky A = L L^T (L in the lower triangle of A)
-    bool ok = true;
+      A[cl][k][k] += damp_diag(A[cl][k][k], lam, mode);
+    }
+    __syncthreads();
+    // left-looking Cholesky, one column per step: threads k >= j update row k of column j
+    // in parallel; thread j then takes the reciprocal square root of the pivot.
+    __shared__ int bad[kCamBlock];
+    if (k == 0) bad[cl] = 0;
     for (int j = 0; j < 9; ++j) {
-      double d = A[j][j];
-      for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
-      if (!(d > 0.0) || !isfinite(d)) { ok = false; d = 1.0; }
-      const double ljj = sqrt(d);
-      A[j][j] = ljj;
-      for (int i = j + 1; i < 9; ++i) {
-        double v = A[i][j];
-        for (int k = 0; k < j; ++k) v -= A[i][k] * A[j][k];
-        A[i][j] = v / ljj;
+      if (ok_cam && k >= j) {
+        double v = A[cl][k][j];
+        for (int p = 0; p < j; ++p) v -= A[cl][k][p] * A[cl][j][p];
+        A[cl][k][j] = v;
+      }
+      __syncthreads();
+      if (ok_cam && k == j) {
+        double d = A[cl][j][j];
+        if (!(d > 0.0) || !isfinite(d)) {
+          bad[cl] = 1;
+          d = 1.0;
+        }
+        A[cl][j][j] = rsqrt(d);  // 1 / L_jj
+      }
+      __syncthreads();
+      if (ok_cam && k > j) A[cl][k][j] *= A[cl][j][j];
+      __syncthreads();
+    }
+    if (ok_cam && k == 0 && bad[cl]) atomicOr(not_spd, 1);
+    if (ok_cam) {
+      const double (*a)[10] = A[cl];
+      double m[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) m[i] = 0.0;
+      m[k] = a[k][k];
+      for (int i = k + 1; i < 9; ++i) {
+        double v = 0.0;
+        for (int p = k; p < i; ++p) v -= a[i][p] * m[p];
+        m[i] = v * a[i][i];
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i) M[cl][i][k] = m[i];
+    }
+    __syncthreads();
+    if (ok_cam) {
+      double* out = Uinv + (size_t)c * 81 + k * 9;
+      for (int j = 0; j < 9; ++j) {
+        double v = 0.0;
+        for (int p = (k > j ? k : j); p < 9; ++p) v += M[cl][p][k] * M[cl][p][j];
+        out[j] = v;
       }
     }
-    if (!ok) atomicOr(not_spd, 1);
-    // M = L^-1 (lower triangular)
-    double M[9][9];
-    for (int j = 0; j < 9; ++j) {
-      for (int i = 0; i < j; ++i) M[i][j] = 0.0;
-      M[j][j] = 1.0 / A[j][j];
-      for (int i = j + 1; i < 9; ++i) {
-        double v = 0.0;
-        for (int k = j; k < i; ++k) v -= A[i][k] * M[k][j];
-        M[i][j] = v / A[i][i];
-      }
-    }
-    // Uinv = M^T M
-    double* out = Uinv + (size_t)c * 81;
-    for (int i = 0; i < 9; ++i)
-      for (int j = i; j < 9; ++j) {
-        double v = 0.0;
-        for (int k = j; k < 9; ++k) v += M[k][i] * M[k][j];
-        out[i * 9 + j] = v;
-        out[j * 9 + i] = v;
-      }
   } else {
-    const int l = (blockIdx.x - cam_blocks) * blockDim.x + threadIdx.x;
+    const int l = (blockIdx.x - cam_blocks) * blockDim.x + tid;
     if (l >= tp.n_lms) return;
     const double* v = V + (size_t)l * 6;
     const double a00 = v[0] + damp_diag(v[0], lam, mode), a01 = v[1], a02 = v[2];
@@ -376,21 +411,20 @@ __global__ void damp_invert_kernel(Topology tp, const double* __restrict__ U45,
     bool ok = true;
     double d0 = a00;
     if (!(d0 > 0.0) || !isfinite(d0)) { ok = false; d0 = 1.0; }
-    const double l00 = sqrt(d0);
-    const double l10 = a01 / l00, l20 = a02 / l00;
+    const double m00 = rsqrt(d0);  // 1 / l00
+    const double l10 = a01 * m00, l20 = a02 * m00;
     double d1 = a11 - l10 * l10;
     if (!(d1 > 0.0) || !isfinite(d1)) { ok = false; d1 = 1.0; }
-    const double l11 = sqrt(d1);
-    const double l21 = (a12 - l20 * l10) / l11;
+    const double m11 = rsqrt(d1);
+    const double l21 = (a12 - l20 * l10) * m11;
     double d2 = a22 - l20 * l20 - l21 * l21;
     if (!(d2 > 0.0) || !isfinite(d2)) { ok = false; d2 = 1.0; }
-    const double l22 = sqrt(d2);
+    const double m22 = rsqrt(d2);
     if (!ok) atomicOr(not_spd, 1);
     // M = L^-1
-    const double m00 = 1.0 / l00, m11 = 1.0 / l11, m22 = 1.0 / l22;
-    const double m10 = -l10 * m00 / l11;
-    const double m21 = -l21 * m11 / l22;
-    const double m20 = -(l20 * m00 + l21 * m10) / l22;
+    const double m10 = -l10 * m00 * m11;
+    const double m21 = -l21 * m11 * m22;
+    const double m20 = -(l20 * m00 + l21 * m10) * m22;
     // Vinv = M^T M, 6 unique entries [00 01 02 11 12 22]
     double o[6];
     o[0] = m00 * m00 + m10 * m10 + m20 * m20;
@@ -400,10 +434,10 @@ __global__ void damp_invert_kernel(Topology tp, const double* __restrict__ U45,
     o[4] = m21 * m22;
     o[5] = m22 * m22;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) Vinv[(size_t)l * 6 + k] = o[k];
+    for (int q = 0; q < 6; ++q) Vinv[(size_t)l * 6 + q] = o[q];
     if (Vinv_f) {
 #pragma unroll
-      for (int k = 0; k < 6; ++k) Vinv_f[(size_t)l * 6 + k] = (float)o[k];
+      for (int q = 0; q < 6; ++q) Vinv_f[(size_t)l * 6 + q] = (float)o[q];
     }
   }
 }
@@ -411,11 +445,10 @@ __global__ void damp_invert_kernel(Topology tp, const double* __restrict__ U45,
 void launch_damp_invert(const Topology& tp, const double* U45, const double* V,
                         const double* lambda, int damping_mode, double* Uinv, double* Vinv,
                         float* Vinv_f, int32_t* not_spd, cudaStream_t s) {
-  const int threads = 128;
-  const int cb = (tp.n_cams + threads - 1) / threads;
-  const int lb = (tp.n_lms + threads - 1) / threads;
-  damp_invert_kernel<<<cb + lb, threads, 0, s>>>(tp, U45, V, lambda, damping_mode, cb, Uinv, Vinv,
-                                                Vinv_f, not_spd);
+  const int cb = (tp.n_cams + kCamBlock - 1) / kCamBlock;
+  const int lb = (tp.n_lms + kDampThreads - 1) / kDampThreads;
+  damp_invert_kernel<<<cb + lb, kDampThreads, 0, s>>>(tp, U45, V, lambda, damping_mode, cb, Uinv,
+                                                     Vinv, Vinv_f, not_spd);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -445,7 +478,8 @@ __global__ void __launch_bounds__(kCostThreads) cost_kernel(
     const double P0 = q[0] * X0 + q[1] * X1 + q[2] * X2 + q[18];
     const double P1 = q[3] * X0 + q[4] * X1 + q[5] * X2 + q[19];
     const double P2 = q[6] * X0 + q[7] * X1 + q[8] * X2 + q[20];
-    const double px = -P0 / P2, py = -P1 / P2;
+    const double iz = 1.0 / P2;
+    const double px = -P0 * iz, py = -P1 * iz;
     const double n2 = px * px + py * py;
     const double rad = 1.0 + n2 * (q[22] + q[23] * n2);
     const double2 ob = obs[o];

@@ -1,129 +1,29 @@
-// Power-series kernels of libpoba (sm_103a), Sec. 4.3.
+// Per-term power-series kernels of libpoba (sm_103a), Sec. 4.3, and the LM helper kernels.
 //
-// With P = U^-1 W V^-1 W^T, W = J_p^T J_l, one series term t_i = P t_{i-1} is applied
-// matrix-free in two launches:
-//   tile_matvec (per tile of whole landmarks, one observation per thread):
-//     u_o = J_p,o t_c(o)                       (t staged per slot in shared memory)
-//     z_l = V_l^-1 sum_{o in l} J_l,o^T u_o    (landmark-segmented sum in shared memory)
-//     g_o = J_p,o^T (J_l,o z_l(o))             (J still in registers: one J read per term)
-//     partial[slot] = sum_{o in slot} g_o      (per-tile camera sums, fixed order)
-//   camera_step (per camera):
-//     y_c = sum over the camera's slots of partial; t_i = U_c^-1 y_c; x += t_i;
-//     ||t_i||^2, ||x(i)||^2 block sums; the last block applies the stop rule of eq.
-//     `qcriterion` and raises `done`, after which later launches return at once.
-// The same kernels with z_l = V_l^-1 b_l form b~ = b_p - W V^-1 b_l and x(0) = -U^-1 b~
-// (Sec. 4.2, eq. `x_approx` with m = 0); back-substitution (Sec. 4.2) reuses the first half
-// and also accumulates the model decrease 1/2||r||^2 - 1/2||r + J_p dx_p + J_l dx_l||^2.
+// One series term is two launches: tile_matvec_kernel (the tile body of series_body.cuh over all
+// tiles) and camera_step_kernel (the camera body over all cameras, then the stop rule of eq.
+// `qcriterion` in the last block to finish, which raises `done` so that later launches return at
+// once).  These launches are what the captured-graph path replays; the persistent kernel in
+// kernels_persistent.cu runs the same bodies in one launch.  Back-substitution (Sec. 4.2)
+// reuses the first half of the tile body and also accumulates the model decrease
+// 1/2||r||^2 - 1/2||r + J_p dx_p + J_l dx_l||^2.
 #include <cfloat>
 #include <cmath>
 
 #include "poba_internal.cuh"
+#include "series_body.cuh"
 #include "tile_common.cuh"
 
 namespace poba {
 
-enum { kModeSeries = 0, kModeRhs = 1 };
-
-template <typename T>
-__device__ __forceinline__ void load_J(const T* __restrict__ J, size_t pad, int o, T (&jp)[18],
-                                       T (&jl)[6]) {
-#pragma unroll
-  for (int p = 0; p < 18; ++p) jp[p] = J[p * pad + o];
-#pragma unroll
-  for (int p = 0; p < 6; ++p) jl[p] = J[(18 + p) * pad + o];
-}
-
-// z = Vinv s with Vinv stored as [00 01 02 11 12 22].
-template <typename T>
-__device__ __forceinline__ void apply_vinv(const T* __restrict__ vi, const T (&s)[3], T (&z)[3]) {
-  const T v0 = vi[0], v1 = vi[1], v2 = vi[2], v3 = vi[3], v4 = vi[4], v5 = vi[5];
-  z[0] = v0 * s[0] + v1 * s[1] + v2 * s[2];
-  z[1] = v1 * s[0] + v3 * s[1] + v4 * s[2];
-  z[2] = v2 * s[0] + v4 * s[1] + v5 * s[2];
-}
-
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kTileObs) tile_matvec_kernel(
-    Topology tp, const T* __restrict__ J, const double* __restrict__ tvec,
+    Topology tp, const T* __restrict__ J, const T* __restrict__ t_cm,
     const double* __restrict__ b_l, const T* __restrict__ Vinv, T* __restrict__ partial,
     const SeriesState* __restrict__ st) {
-  if (MODE == kModeSeries && st->done) return;
-  __shared__ T tcam[kTileObs][9];
-  __shared__ T sv[kTileObs][3];
-  __shared__ T sg[kTileObs][9];
-  __shared__ uint16_t sbeg[kTileObs];
-
-  const int tile = blockIdx.x, tid = threadIdx.x;
-  const int L0 = tp.tile_lm0[tile], L1 = tp.tile_lm0[tile + 1];
-  const int o0 = tp.lm_seg[L0], n = tp.lm_seg[L1] - o0;
-  const int S0 = tp.tile_slot0[tile], ns = tp.tile_slot0[tile + 1] - S0;
-  if (MODE == kModeSeries) {
-    for (int i = tid; i < ns * 9; i += blockDim.x) {
-      const int s = i / 9, k = i - s * 9;
-      tcam[s][k] = (T)tvec[(size_t)tp.slot_cam[S0 + s] * 9 + k];
-    }
-  }
-  for (int i = tid; i < ns; i += blockDim.x) sbeg[i] = tp.slot_beg[S0 + i];
-  __syncthreads();
-
-  const bool active = tid < n;
-  const size_t pad = (size_t)tp.n_obs_pad;
-  T jp[18], jl[6];
-  int meta = 0;
-  if (active) {
-    const int o = o0 + tid;
-    meta = tp.obs_meta[o];
-    load_J(J, pad, o, jp, jl);
-    if (MODE == kModeSeries) {
-      const T* tc = tcam[meta >> 8];
-      T u0 = (T)0, u1 = (T)0;
-#pragma unroll
-      for (int j = 0; j < 9; ++j) {
-        u0 += jp[j] * tc[j];
-        u1 += jp[9 + j] * tc[j];
-      }
-#pragma unroll
-      for (int k = 0; k < 3; ++k) sv[tid][k] = jl[k] * u0 + jl[3 + k] * u1;
-    }
-  }
-  __syncthreads();
-  // landmark phase: z_l = V_l^-1 (sum of W^T t contributions, or b_l), written back per obs
-  if (tid < L1 - L0) {
-    const int l = L0 + tid;
-    const int a = tp.lm_seg[l] - o0, b = tp.lm_seg[l + 1] - o0;
-    T s[3];
-    if (MODE == kModeSeries) {
-      s[0] = s[1] = s[2] = (T)0;
-      for (int q = a; q < b; ++q) {
-        s[0] += sv[q][0];
-        s[1] += sv[q][1];
-        s[2] += sv[q][2];
-      }
-    } else {
-      s[0] = (T)b_l[(size_t)l * 3 + 0];
-      s[1] = (T)b_l[(size_t)l * 3 + 1];
-      s[2] = (T)b_l[(size_t)l * 3 + 2];
-    }
-    T z[3];
-    apply_vinv(Vinv + (size_t)l * 6, s, z);
-    for (int q = a; q < b; ++q) {
-      sv[q][0] = z[0];
-      sv[q][1] = z[1];
-      sv[q][2] = z[2];
-    }
-  }
-  __syncthreads();
-  // W z scatter: g_o = J_p^T (J_l z), staged at the camera-sorted position
-  if (active) {
-    const T z0 = sv[tid][0], z1 = sv[tid][1], z2 = sv[tid][2];
-    const T w0 = jl[0] * z0 + jl[1] * z1 + jl[2] * z2;
-    const T w1 = jl[3] * z0 + jl[4] * z1 + jl[5] * z2;
-    T* g = sg[meta & 0xff];
-#pragma unroll
-    for (int j = 0; j < 9; ++j) g[j] = jp[j] * w0 + jp[9 + j] * w1;
-  }
-  __syncthreads();
-  slot_sums<T, T>(sg, ns, n, sbeg, partial + (size_t)S0 * 9, 9);
+  __shared__ TileSmem<T> sm;
+  if (MODE == kModeSeries && st->done) return;  // the stop rule fired in an earlier term
+  tile_matvec_body<T, MODE>(tp, blockIdx.x, J, t_cm, b_l, Vinv, partial, sm);
 }
 
 template <typename T>
@@ -134,9 +34,9 @@ void launch_tile_rhs(const Topology& tp, const T* J, const double* b_l, const T*
 }
 
 template <typename T>
-void launch_tile_series(const Topology& tp, const T* J, const double* t, const T* Vinv,
+void launch_tile_series(const Topology& tp, const T* J, const T* t_cm, const T* Vinv,
                         T* partial, const SeriesState* st, cudaStream_t s) {
-  tile_matvec_kernel<T, kModeSeries><<<tp.n_tiles, kTileObs, 0, s>>>(tp, J, t, nullptr, Vinv,
+  tile_matvec_kernel<T, kModeSeries><<<tp.n_tiles, kTileObs, 0, s>>>(tp, J, t_cm, nullptr, Vinv,
                                                                      partial, st);
 }
 
@@ -152,9 +52,8 @@ __global__ void __launch_bounds__(kTileObs) tile_backsub_kernel(
   __shared__ double sred[kTileObs / 32];
 
   const int tile = blockIdx.x, tid = threadIdx.x;
-  const int L0 = tp.tile_lm0[tile], L1 = tp.tile_lm0[tile + 1];
-  const int o0 = tp.lm_seg[L0], n = tp.lm_seg[L1] - o0;
-  const int S0 = tp.tile_slot0[tile], ns = tp.tile_slot0[tile + 1] - S0;
+  const TileHdr th = load_tile(tp, tile);
+  const int L0 = th.L0, L1 = th.L0 + th.nl, o0 = th.o0, n = th.n, S0 = th.S0, ns = th.ns;
   for (int i = tid; i < ns * 9; i += blockDim.x) {
     const int s = i / 9, k = i - s * 9;
     tcam[s][k] = (T)x[(size_t)tp.slot_cam[S0 + s] * 9 + k];
@@ -225,59 +124,33 @@ void launch_tile_backsub(const Topology& tp, const T* J, const T* r, const doubl
 template void launch_tile_rhs<double>(const Topology&, const double*, const double*, const double*, double*, const SeriesState*, cudaStream_t);
 template void launch_tile_rhs<float>(const Topology&, const float*, const double*, const float*, float*, const SeriesState*, cudaStream_t);
 template void launch_tile_series<double>(const Topology&, const double*, const double*, const double*, double*, const SeriesState*, cudaStream_t);
-template void launch_tile_series<float>(const Topology&, const float*, const double*, const float*, float*, const SeriesState*, cudaStream_t);
+template void launch_tile_series<float>(const Topology&, const float*, const float*, const float*, float*, const SeriesState*, cudaStream_t);
 template void launch_tile_backsub<double>(const Topology&, const double*, const double*, const double*, const double*, const double*, double*, double*, cudaStream_t);
 template void launch_tile_backsub<float>(const Topology&, const float*, const float*, const double*, const double*, const float*, double*, double*, cudaStream_t);
 
 int tile_blocks(const Topology& tp) { return tp.n_tiles; }
 
 // ---------------------------------------------------------------------------------------
-// Camera step.  Block = kCamBlock cameras x 9 components.
+// Camera step: kCamBlock cameras x 9 components per block (camera body), block sums of the
+// squared norms, and the stop rule in the last block to finish (fixed-order sums).
 int camera_blocks(const Topology& tp) { return (tp.n_cams + kCamBlock - 1) / kCamBlock; }
 
 template <typename PT, int MODE>
 __global__ void __launch_bounds__(kCamBlock * 9) camera_step_kernel(
     Topology tp, const PT* __restrict__ partial, const double* __restrict__ b_p,
-    const double* __restrict__ Uinv, double* __restrict__ x, double* __restrict__ t,
+    const double* __restrict__ Uinv, double* __restrict__ x, PT* __restrict__ t_cm,
     double* __restrict__ block_norms, SeriesState* __restrict__ st, int iter, double eps) {
-  if (MODE == kModeSeries && st->done) return;
   __shared__ double ys[kCamBlock][9];
   __shared__ double sred[(kCamBlock * 9 + 31) / 32];
-  __shared__ double sfin[2][kCamBlock * 9];
   __shared__ int is_last;
+  if (MODE == kModeSeries && st->done) return;
   const int tid = threadIdx.x;
-  const int cl = tid / 9, k = tid - cl * 9;
-  const int c = blockIdx.x * kCamBlock + cl;
-  const bool active = c < tp.n_cams;
-  double y = 0.0;
-  if (active) {
-    for (int s = tp.cam_slot_ptr[c]; s < tp.cam_slot_ptr[c + 1]; ++s)
-      y += (double)partial[(size_t)tp.cam_slot_list[s] * 9 + k];
-    if (MODE == kModeRhs) y = b_p[(size_t)c * 9 + k] - y;  // b~ = b_p - W V^-1 b_l
-  }
-  ys[cl][k] = y;
+  double v, xv;
+  camera_body<PT, MODE>(tp, blockIdx.x * kCamBlock, kCamBlock, partial, b_p, Uinv, x, t_cm, ys,
+                        v, xv);
+  const double bt = block_sum_fixed(v * v, sred);
   __syncthreads();
-  double tn2 = 0.0, xn2 = 0.0;
-  if (active) {
-    const double* ui = Uinv + (size_t)c * 81 + k * 9;
-    double v = 0.0;
-#pragma unroll
-    for (int j = 0; j < 9; ++j) v += ui[j] * ys[cl][j];
-    double xv;
-    if (MODE == kModeRhs) {
-      v = -v;  // x(0) = -U^-1 b~
-      xv = v;
-    } else {
-      xv = x[(size_t)c * 9 + k] + v;
-    }
-    x[(size_t)c * 9 + k] = xv;
-    t[(size_t)c * 9 + k] = v;
-    tn2 = v * v;
-    xn2 = xv * xv;
-  }
-  const double bt = block_sum_fixed(tn2, sred);
-  __syncthreads();
-  const double bx = block_sum_fixed(xn2, sred);
+  const double bx = block_sum_fixed(xv * xv, sred);
   if (tid == 0) {
     block_norms[blockIdx.x * 2 + 0] = bt;
     block_norms[blockIdx.x * 2 + 1] = bx;
@@ -288,68 +161,40 @@ __global__ void __launch_bounds__(kCamBlock * 9) camera_step_kernel(
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  // last block: fixed-order sum of all block norms, then the stop rule
+  // last block: fixed-order sum of all block norms (strided per thread, then the block tree)
   double at = 0.0, ax = 0.0;
   for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
     at += __ldcg(block_norms + b * 2 + 0);
     ax += __ldcg(block_norms + b * 2 + 1);
   }
-  sfin[0][tid] = at;
-  sfin[1][tid] = ax;
+  const double T2 = block_sum_fixed(at, sred);
   __syncthreads();
+  const double X2 = block_sum_fixed(ax, sred);
   if (tid == 0) {
-    double T2 = 0.0, X2 = 0.0;
-    for (int i = 0; i < (int)blockDim.x; ++i) {
-      T2 += sfin[0][i];
-      X2 += sfin[1][i];
-    }
-    const double tn = sqrt(T2), xn = sqrt(X2);
-    st->t_norm = tn;
-    st->x_norm = xn;
-    st->m = iter;
-    if (MODE == kModeRhs) {
-      st->stop_value = INFINITY;
-      if (xn == 0.0) {
-        st->done = 1;
-        st->stopped = 1;
-      }
-    } else {
-      if (xn == 0.0) {
-        st->stop_value = 0.0;
-        st->done = 1;
-        st->stopped = 1;
-      } else {
-        const double sv = (double)(iter + 1) * tn / xn;  // eq. `qcriterion`
-        st->stop_value = sv;
-        if (sv < eps) {
-          st->done = 1;
-          st->stopped = 1;
-        }
-      }
-    }
+    series_stop_rule(st, iter, T2, X2, eps);
     st->counter = 0u;
   }
 }
 
 template <typename PT>
 void launch_camera_rhs(const Topology& tp, const PT* partial, const double* b_p, const double* Uinv,
-                       double* x, double* t, double* block_norms, SeriesState* st, cudaStream_t s) {
+                       double* x, PT* t_cm, double* block_norms, SeriesState* st, cudaStream_t s) {
   camera_step_kernel<PT, kModeRhs><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(
-      tp, partial, b_p, Uinv, x, t, block_norms, st, 0, 0.0);
+      tp, partial, b_p, Uinv, x, t_cm, block_norms, st, 0, 0.0);
 }
 
 template <typename PT>
 void launch_camera_series(const Topology& tp, const PT* partial, const double* Uinv, double* x,
-                          double* t, double* block_norms, SeriesState* st, int iter, double eps,
+                          PT* t_cm, double* block_norms, SeriesState* st, int iter, double eps,
                           cudaStream_t s) {
   camera_step_kernel<PT, kModeSeries><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(
-      tp, partial, nullptr, Uinv, x, t, block_norms, st, iter, eps);
+      tp, partial, nullptr, Uinv, x, t_cm, block_norms, st, iter, eps);
 }
 
 template void launch_camera_rhs<double>(const Topology&, const double*, const double*, const double*, double*, double*, double*, SeriesState*, cudaStream_t);
-template void launch_camera_rhs<float>(const Topology&, const float*, const double*, const double*, double*, double*, double*, SeriesState*, cudaStream_t);
+template void launch_camera_rhs<float>(const Topology&, const float*, const double*, const double*, double*, float*, double*, SeriesState*, cudaStream_t);
 template void launch_camera_series<double>(const Topology&, const double*, const double*, double*, double*, double*, SeriesState*, int, double, cudaStream_t);
-template void launch_camera_series<float>(const Topology&, const float*, const double*, double*, double*, double*, SeriesState*, int, double, cudaStream_t);
+template void launch_camera_series<float>(const Topology&, const float*, const double*, double*, float*, double*, SeriesState*, int, double, cudaStream_t);
 
 // ---------------------------------------------------------------------------------------
 __global__ void series_reset_kernel(SeriesState* st) {

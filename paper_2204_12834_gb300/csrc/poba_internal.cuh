@@ -10,6 +10,10 @@
 //   per camera across the slots that camera owns (CSR cam_slot_ptr / cam_slot_list), so no
 //   global atomics are used and every sum has a fixed order.
 //
+//   Per-slot partial sums are written camera-major (row slot_row[s] of slot s), so the rows of
+//   one camera are contiguous for the camera-side kernels; the current series term is kept per
+//   slot row as well (t_cm, camera-major), which a tile gathers through slot_row.
+//
 //   Jacobians and residuals are structure-of-arrays planes of length n_obs_pad in the
 //   handle's bulk precision T:
 //     J[p * n_obs_pad + o], p = 0..17: J_p row-major (row i, col j at p = 9 i + j)
@@ -30,7 +34,7 @@ namespace poba {
 constexpr int kTileObs = 256;   // observations per tile (= threads of the tile kernels)
 constexpr int kTileLms = 256;   // landmarks per tile
 constexpr int kLinVals = 54;    // 45 packed upper-triangular entries of J_p^T J_p + 9 of J_p^T r
-constexpr int kCamBlock = 32;   // cameras per block in the camera-side kernels
+constexpr int kCamBlock = 32;   // cameras per block in the damp / invert kernel
 constexpr int kReduceThreads = 256;
 
 // ---------------------------------------------------------------------------------------
@@ -47,10 +51,12 @@ struct Schedule {
   std::vector<uint16_t> obs_meta;    // [n_obs] pos | slot << 8
   std::vector<int32_t> tile_lm0;     // [n_tiles + 1]
   std::vector<int32_t> tile_slot0;   // [n_tiles + 1]
+  std::vector<int32_t> tile_desc;    // [n_tiles][8]: L0, n_lms, o0, n_obs, S0, n_slots, 0, 0
   std::vector<int32_t> slot_cam;     // [n_slots]
   std::vector<uint16_t> slot_beg;    // [n_slots] first camera-sorted position of the slot
   std::vector<int32_t> cam_slot_ptr; // [n_cams + 1]
-  std::vector<int32_t> cam_slot_list;// [n_slots]
+  std::vector<int32_t> cam_slot_list;// [n_slots] camera-major row -> tile-major slot
+  std::vector<int32_t> slot_row;     // [n_slots] tile-major slot -> camera-major row
 };
 
 // Returns an empty string on success, else a description of why the inputs are rejected.
@@ -67,10 +73,12 @@ struct Topology {
   const uint16_t* obs_meta;
   const int32_t* tile_lm0;
   const int32_t* tile_slot0;
+  const int4* tile_desc;  // two int4 per tile: {L0, nl, o0, n}, {S0, ns, 0, 0}
   const int32_t* slot_cam;
   const uint16_t* slot_beg;
   const int32_t* cam_slot_ptr;
   const int32_t* cam_slot_list;
+  const int32_t* slot_row;  // partial sums are stored camera-major: row slot_row[slot]
 };
 
 // Per-camera values prepared once per state: rotation R (row-major), the matrix G with
@@ -90,6 +98,14 @@ struct SeriesState {
   double pad2;
   uint32_t counter;    // last-block ticket
   uint32_t pad1;
+};
+
+// Grid-barrier state of the persistent series kernel (zeroed before each launch).
+struct GridSync {
+  unsigned count;      // arrivals at the current barrier
+  unsigned gen;        // barrier generation, advanced by the last block to arrive
+  unsigned tile_next;  // dynamic tile counter of the current tile phase
+  int error;           // 1: a barrier wait timed out
 };
 
 // LM record (device), written by the decide kernel and read by the host once per iteration.
@@ -141,7 +157,7 @@ void launch_tile_rhs(const Topology& tp, const T* J, const double* b_l, const T*
                      T* partial, const SeriesState* st, cudaStream_t s);
 
 template <typename T>
-void launch_tile_series(const Topology& tp, const T* J, const double* t, const T* Vinv,
+void launch_tile_series(const Topology& tp, const T* J, const T* t_cm, const T* Vinv,
                         T* partial, const SeriesState* st, cudaStream_t s);
 
 template <typename T>
@@ -149,17 +165,32 @@ void launch_tile_backsub(const Topology& tp, const T* J, const T* r, const doubl
                          const double* b_l, const T* Vinv, double* dx_l,
                          double* block_pred, cudaStream_t s);
 
+// The camera kernels write the new term t into each of the camera's camera-major slot rows
+// (t_cm), which the next tile kernel gathers through slot_row.
 template <typename PT>
 void launch_camera_rhs(const Topology& tp, const PT* partial, const double* b_p,
-                       const double* Uinv, double* x, double* t, double* block_norms,
+                       const double* Uinv, double* x, PT* t_cm, double* block_norms,
                        SeriesState* st, cudaStream_t s);
 
 template <typename PT>
 void launch_camera_series(const Topology& tp, const PT* partial, const double* Uinv, double* x,
-                          double* t, double* block_norms, SeriesState* st, int iter,
+                          PT* t_cm, double* block_norms, SeriesState* st, int iter,
                           double eps, cudaStream_t s);
 
 int camera_blocks(const Topology& tp);
+
+// Persistent series kernel (cooperative launch): up to m_max terms and the stop rule.  Block 0
+// records %globaltimer at 5 points of each of the first kTraceTerms terms (start, end of the
+// tile phase, after the first barrier, end of the camera phase, after the second barrier).
+constexpr int kTraceTerms = 64;
+constexpr int kTracePoints = 5;
+int persistent_blocks_per_sm(bool f32);
+template <typename T>
+cudaError_t launch_series_persistent(const Topology& tp, int grid, const T* J, const T* Vinv,
+                                     const double* b_l, const double* b_p, const double* Uinv,
+                                     double* x, T* t_cm, T* partial, double* group_norms,
+                                     SeriesState* st, GridSync* gs, int m_max, double eps,
+                                     long long timeout, long long* trace, cudaStream_t s);
 int tile_blocks(const Topology& tp);
 
 void launch_series_reset(SeriesState* st, cudaStream_t s);

@@ -114,6 +114,16 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
     S->tile_slot0[t + 1] = S->tile_slot0[t] + ns;
   }
   S->n_slots = S->tile_slot0[S->n_tiles];
+  S->tile_desc.assign((size_t)S->n_tiles * 8, 0);
+  for (int t = 0; t < S->n_tiles; ++t) {
+    int32_t* d = &S->tile_desc[(size_t)t * 8];
+    d[0] = S->tile_lm0[t];
+    d[1] = S->tile_lm0[t + 1] - S->tile_lm0[t];
+    d[2] = S->lm_seg[S->tile_lm0[t]];
+    d[3] = S->lm_seg[S->tile_lm0[t + 1]] - d[2];
+    d[4] = S->tile_slot0[t];
+    d[5] = S->tile_slot0[t + 1] - S->tile_slot0[t];
+  }
 
   // Camera -> slots (CSR), slots in tile order.
   S->cam_slot_ptr.assign(n_cams + 1, 0);
@@ -122,6 +132,8 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
   S->cam_slot_list.assign(S->n_slots, 0);
   std::vector<int32_t> fill(S->cam_slot_ptr.begin(), S->cam_slot_ptr.end() - 1);
   for (int s = 0; s < S->n_slots; ++s) S->cam_slot_list[fill[S->slot_cam[s]]++] = s;
+  S->slot_row.assign(S->n_slots, 0);
+  for (int r = 0; r < S->n_slots; ++r) S->slot_row[S->cam_slot_list[r]] = r;
   return "";
 }
 

@@ -1,0 +1,241 @@
+// Device bodies of one power-series term (Sec. 4.3), shared by the per-term kernels and the
+// persistent series kernel.  Data written by other blocks of the same launch (t_cm, partial,
+// x) is read with __ldcg (L2), since L1 is not coherent across SMs within a launch.
+//
+// With P = U^-1 W V^-1 W^T, W = J_p^T J_l, a term t_i = P t_{i-1} is applied matrix-free:
+//   tile body (per tile of whole landmarks, one observation per thread):
+//     u_o = J_p,o t_c(o)                       (t staged per slot in shared memory)
+//     z_l = V_l^-1 sum_{o in l} J_l,o^T u_o    (landmark-segmented sum in shared memory)
+//     g_o = J_p,o^T (J_l,o z_l(o))             (J still in registers: one J read per term)
+//     partial[row(slot)] = sum_{o in slot} g_o (per-tile camera sums, fixed order)
+//   camera body (9 threads per camera):
+//     y_c = sum of the camera's partial rows; t_i = U_c^-1 y_c; x += t_i; t_cm rows = t_i.
+// With z_l = V_l^-1 b_l (RHS mode) the same bodies form b~ = b_p - W V^-1 b_l and
+// x(0) = -U^-1 b~ (Sec. 4.2 and eq. `x_approx` with m = 0).
+#pragma once
+
+#include <cstdint>
+
+#include "poba_internal.cuh"
+#include "tile_common.cuh"
+
+namespace poba {
+
+enum { kModeSeries = 0, kModeRhs = 1 };
+
+template <typename T>
+__device__ __forceinline__ void load_J(const T* __restrict__ J, size_t pad, int o, T (&jp)[18],
+                                       T (&jl)[6]) {
+#pragma unroll
+  for (int p = 0; p < 18; ++p) jp[p] = J[p * pad + o];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) jl[p] = J[(18 + p) * pad + o];
+}
+
+// z = Vinv s with Vinv stored as [00 01 02 11 12 22].
+template <typename T>
+__device__ __forceinline__ void apply_vinv(const T* __restrict__ vi, const T (&s)[3], T (&z)[3]) {
+  const T v0 = vi[0], v1 = vi[1], v2 = vi[2], v3 = vi[3], v4 = vi[4], v5 = vi[5];
+  z[0] = v0 * s[0] + v1 * s[1] + v2 * s[2];
+  z[1] = v1 * s[0] + v3 * s[1] + v4 * s[2];
+  z[2] = v2 * s[0] + v4 * s[1] + v5 * s[2];
+}
+
+// Tile header: {L0, nl, o0, n} and {S0, ns}.
+struct TileHdr {
+  int L0, nl, o0, n, S0, ns;
+};
+
+__device__ __forceinline__ TileHdr load_tile(const Topology& tp, int tile) {
+  const int4 a = tp.tile_desc[2 * tile], b = tp.tile_desc[2 * tile + 1];
+  return TileHdr{a.x, a.y, a.z, a.w, b.x, b.y};
+}
+
+template <typename T>
+struct TileSmem {
+  T tcam[kTileObs][9];
+  T sv[kTileObs][3];
+  T sg[kTileObs][9];
+  uint16_t sbeg[kTileObs];
+  int srow[kTileObs];
+  int sseg[kTileLms + 1];
+};
+
+// One tile of one term (blockDim.x == kTileObs; every thread must call it).
+template <typename T, int MODE>
+__device__ __forceinline__ void tile_matvec_body(const Topology& tp, int tile,
+                                                 const T* __restrict__ J,
+                                                 const T* __restrict__ t_cm,
+                                                 const double* __restrict__ b_l,
+                                                 const T* __restrict__ Vinv,
+                                                 T* __restrict__ partial, TileSmem<T>& sm) {
+  const int tid = threadIdx.x;
+  const TileHdr th = load_tile(tp, tile);
+  const int o0 = th.o0, n = th.n, ns = th.ns, nl = th.nl;
+  const bool active = tid < n;
+  const size_t pad = (size_t)tp.n_obs_pad;
+  // issue every independent load of the tile before the first barrier
+  T jp[18], jl[6];
+  int meta = 0;
+  if (active) {
+    const int o = o0 + tid;
+    meta = tp.obs_meta[o];
+    load_J(J, pad, o, jp, jl);
+  }
+  T vi[6];
+  double bl[3] = {0.0, 0.0, 0.0};
+  if (tid < nl) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) vi[k] = Vinv[(size_t)(th.L0 + tid) * 6 + k];
+    if (MODE == kModeRhs) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) bl[k] = b_l[(size_t)(th.L0 + tid) * 3 + k];
+    }
+  }
+  for (int i = tid; i < ns; i += blockDim.x) {
+    sm.sbeg[i] = tp.slot_beg[th.S0 + i];
+    sm.srow[i] = tp.slot_row[th.S0 + i];
+  }
+  for (int i = tid; i <= nl; i += blockDim.x) sm.sseg[i] = tp.lm_seg[th.L0 + i] - o0;
+  __syncthreads();
+  if (MODE == kModeSeries) {
+    // the current term is stored camera-major: row srow[s] holds slot s's camera
+    for (int i = tid; i < ns * 9; i += blockDim.x) {
+      const int s = i / 9, k = i - s * 9;
+      sm.tcam[s][k] = __ldcg(t_cm + (size_t)sm.srow[s] * 9 + k);
+    }
+  }
+  __syncthreads();
+
+  if (MODE == kModeSeries && active) {
+    const T* tc = sm.tcam[meta >> 8];
+    T u0 = (T)0, u1 = (T)0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      u0 += jp[j] * tc[j];
+      u1 += jp[9 + j] * tc[j];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sm.sv[tid][k] = jl[k] * u0 + jl[3 + k] * u1;
+  }
+  __syncthreads();
+  // landmark phase: z_l = V_l^-1 (sum of W^T t contributions, or b_l), written back per obs
+  if (tid < nl) {
+    const int a = sm.sseg[tid], b = sm.sseg[tid + 1];
+    T s3[3];
+    if (MODE == kModeSeries) {
+      s3[0] = s3[1] = s3[2] = (T)0;
+      for (int q = a; q < b; ++q) {
+        s3[0] += sm.sv[q][0];
+        s3[1] += sm.sv[q][1];
+        s3[2] += sm.sv[q][2];
+      }
+    } else {
+      s3[0] = (T)bl[0];
+      s3[1] = (T)bl[1];
+      s3[2] = (T)bl[2];
+    }
+    T z[3];
+    z[0] = vi[0] * s3[0] + vi[1] * s3[1] + vi[2] * s3[2];
+    z[1] = vi[1] * s3[0] + vi[3] * s3[1] + vi[4] * s3[2];
+    z[2] = vi[2] * s3[0] + vi[4] * s3[1] + vi[5] * s3[2];
+    for (int q = a; q < b; ++q) {
+      sm.sv[q][0] = z[0];
+      sm.sv[q][1] = z[1];
+      sm.sv[q][2] = z[2];
+    }
+  }
+  __syncthreads();
+  // W z scatter: g_o = J_p^T (J_l z), staged at the camera-sorted position
+  if (active) {
+    const T z0 = sm.sv[tid][0], z1 = sm.sv[tid][1], z2 = sm.sv[tid][2];
+    const T w0 = jl[0] * z0 + jl[1] * z1 + jl[2] * z2;
+    const T w1 = jl[3] * z0 + jl[4] * z1 + jl[5] * z2;
+    T* g = sm.sg[meta & 0xff];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) g[j] = jp[j] * w0 + jp[9 + j] * w1;
+  }
+  __syncthreads();
+  slot_sums<T, T>(sm.sg, ns, n, sm.sbeg, sm.srow, partial, 9);
+}
+
+// Camera body for cameras [cam0, cam0 + per_block): thread (c, k) sums component k of the
+// camera's contiguous slot rows (loads issued 8 at a time, summed in a fixed order), applies
+// row k of U^-1, updates x and writes the new term into the camera's rows of t_cm.  Returns the
+// thread's term and x components (0 for idle threads) for the norms.  FP64 work is one add per
+// slot row and component: every FP64 warp instruction costs 16 pipe cycles on GB300, so no
+// shuffle trees are used for the slot sums.  Every thread of the block must call it.
+template <typename PT, int MODE>
+__device__ __forceinline__ void camera_body(const Topology& tp, int cam0, int per_block,
+                                            const PT* __restrict__ partial,
+                                            const double* __restrict__ b_p,
+                                            const double* __restrict__ Uinv,
+                                            double* __restrict__ x, PT* __restrict__ t_cm,
+                                            double (*ys)[9], double& v_out, double& x_out) {
+  const int tid = threadIdx.x;
+  const int cl = tid / 9, k = tid - cl * 9;
+  const int c = cam0 + cl;
+  const bool cam_ok = cl < per_block && c < tp.n_cams;
+  int r0 = 0, r1 = 0;
+  if (cam_ok) {
+    r0 = tp.cam_slot_ptr[c];
+    r1 = tp.cam_slot_ptr[c + 1];
+  }
+  double y = 0.0;
+  for (int rb = r0; rb < r1; rb += 8) {
+    PT buf[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) buf[j] = (rb + j < r1) ? __ldcg(partial + (size_t)(rb + j) * 9 + k) : (PT)0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) y += (double)buf[j];
+  }
+  if (MODE == kModeRhs && cam_ok) y = b_p[(size_t)c * 9 + k] - y;  // b~ = b_p - W V^-1 b_l
+  if (cl < per_block) ys[cl][k] = y;
+  __syncthreads();
+  double v = 0.0, xv = 0.0;
+  if (cam_ok) {
+    const double* ui = Uinv + (size_t)c * 81 + k * 9;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) v += ui[j] * ys[cl][j];
+    if (MODE == kModeRhs) {
+      v = -v;  // x(0) = -U^-1 b~
+      xv = v;
+    } else {
+      xv = __ldcg(x + (size_t)c * 9 + k) + v;
+    }
+    x[(size_t)c * 9 + k] = xv;
+    const PT tv = (PT)v;
+    for (int q = r0; q < r1; ++q) t_cm[(size_t)q * 9 + k] = tv;
+  }
+  v_out = v;
+  x_out = xv;
+}
+
+// The stop rule of eq. `qcriterion` at term `iter` from the squared norms; updates st.
+__device__ __forceinline__ void series_stop_rule(SeriesState* st, int iter, double T2, double X2,
+                                                 double eps) {
+  const double tn = sqrt(T2), xn = sqrt(X2);
+  st->t_norm = tn;
+  st->x_norm = xn;
+  st->m = iter;
+  if (iter == 0) {
+    st->stop_value = INFINITY;
+    if (xn == 0.0) {
+      st->done = 1;
+      st->stopped = 1;
+    }
+  } else if (xn == 0.0) {
+    st->stop_value = 0.0;
+    st->done = 1;
+    st->stopped = 1;
+  } else {
+    const double sv = (double)(iter + 1) * tn / xn;
+    st->stop_value = sv;
+    if (sv < eps) {
+      st->done = 1;
+      st->stopped = 1;
+    }
+  }
+}
+
+}  // namespace poba

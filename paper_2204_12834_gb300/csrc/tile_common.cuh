@@ -24,13 +24,14 @@ __device__ __forceinline__ double block_sum_fixed(double val, double* sred) {
 }
 
 // Per-slot sums of a tile: rows sg[beg_s .. end_s) of the camera-sorted staging array are
-// summed for each slot s and component k (9 per row) and written to out[s * stride + k].
+// summed for each slot s and component k (9 per row) and written to
+// out[row[s] * stride + k] (row: the slot's camera-major row, staged in shared memory).
 // Small tiles split each sum over 2, 4 or 8 lanes (combined by shuffles); the split depends
 // only on the slot count, so the order of every sum is fixed for a given problem.  Must be
 // called by every thread of the block.
 template <typename T, typename PT>
 __device__ __forceinline__ void slot_sums(const T (*sg)[9], int ns, int n, const uint16_t* sbeg,
-                                          PT* out, int stride) {
+                                          const int* row, PT* out, int stride) {
   const int pairs = ns * 9;
   const int nthreads = blockDim.x;
   int split = 1;
@@ -51,7 +52,7 @@ __device__ __forceinline__ void slot_sums(const T (*sg)[9], int ns, int n, const
       for (int q = beg + part; q < end; q += split) acc += sg[q][k];
     }
     for (int off = split >> 1; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    if (act && part == 0) out[(size_t)s * stride + k] = (PT)acc;
+    if (act && part == 0) out[(size_t)row[s] * stride + k] = (PT)acc;
   }
 }
 

@@ -143,13 +143,16 @@ def test_solve_is_deterministic(poba, case):
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
-def test_graph_and_eager_paths_agree(poba, case):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_series_exec_modes_agree_bitwise(poba, case, precision):
+    """Per-kernel launches, the captured graph and the persistent kernel give the same step."""
     name, p, ref = case
     res = []
-    for g in (0, 1):
-        h = make(poba, p, eps=0.01, max_inner=12, use_graph=g)
+    for mode in (0, 1, 2):
+        h = make(poba, p, precision=precision, eps=0.01, max_inner=12, series_exec=mode)
         poba.ba_linearize(h)
         info = poba.ba_solve_schur_power(h, 1e-2)
         res.append((info["inner_iters"], poba.ba_get_step(h)))
-    assert res[0][0] == res[1][0]
-    assert np.array_equal(res[0][1][0], res[1][1][0])
+    for r in res[1:]:
+        assert r[0] == res[0][0]
+        assert np.array_equal(r[1][0], res[0][1][0]) and np.array_equal(r[1][1], res[0][1][1])
