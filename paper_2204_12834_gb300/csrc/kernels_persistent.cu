@@ -68,16 +68,14 @@ __device__ __forceinline__ bool barrier_wait(GridSync* gs, unsigned gen, long lo
     const long long t0 = clock64();
     unsigned sleep_ns = 32;
     for (unsigned it = 0; ld_volatile(&gs->gen) == gen; ++it) {
-      if ((it & 15u) == 15u) {
-        if (ld_volatile(&gs->error)) {
-          ok = 0;
-          break;
-        }
-        if (clock64() - t0 > timeout) {
-          atomicExch(&gs->error, 1);
-          ok = 0;
-          break;
-        }
+      if (clock64() - t0 > timeout) {
+        atomicExch(&gs->error, 1);
+        ok = 0;
+        break;
+      }
+      if ((it & 15u) == 15u && ld_volatile(&gs->error)) {
+        ok = 0;
+        break;
       }
       __nanosleep(sleep_ns);
       if (sleep_ns < 512) sleep_ns <<= 1;

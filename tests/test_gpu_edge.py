@@ -134,3 +134,28 @@ def test_nonfinite_state_is_reported(poba):
     # the handle stays usable once the state is repaired
     poba.ba_set_params(h, p.cams0, p.lms0)
     assert np.isfinite(poba.ba_cost(h))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_grid_barrier_timeout_is_reported_and_recoverable(poba, precision):
+    """A grid-barrier wait of the persistent series kernel that runs out (limit of one clock
+    cycle) makes the solve return BA_ERR_TIMEOUT; the context stays usable and the next solve
+    with the normal limit gives the usual result."""
+    p = bal_synth.make_problem(40, 2000, track=("uniform", 3, 4), visibility="clustered", seed=119)
+    h = poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, precision=precision,
+                       options=poba.ba_default_options(eps=0.0, max_inner=6, series_exec=2))
+    poba.ba_linearize(h)
+    ref = poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, precision=precision,
+                         options=poba.ba_default_options(eps=0.0, max_inner=6, series_exec=1))
+    poba.ba_linearize(ref)
+    poba.ba_solve_schur_power(ref, 1e-3)
+    want = poba.ba_get_step(ref)
+    poba.ba_set_barrier_timeout(h, 1)
+    with pytest.raises(poba.PobaError) as e:
+        poba.ba_solve_schur_power(h, 1e-3)
+    assert e.value.status_name == "BA_ERR_TIMEOUT"
+    poba.ba_set_barrier_timeout(h, 0)  # back to the default limit
+    info = poba.ba_solve_schur_power(h, 1e-3)
+    assert info["inner_iters"] == 6
+    got = poba.ba_get_step(h)
+    assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
