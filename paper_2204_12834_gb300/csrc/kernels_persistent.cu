@@ -88,7 +88,7 @@ __device__ __forceinline__ bool barrier_wait(GridSync* gs, unsigned gen, long lo
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTileObs, sizeof(T) == 8 ? 2 : 3) series_persistent_kernel(
+__global__ void __launch_bounds__(kTileObs, sizeof(T) == 8 ? 3 : 3) series_persistent_kernel(
     Topology tp, const T* __restrict__ J, const T* __restrict__ Vinv,
     const double* __restrict__ b_l, const double* __restrict__ b_p,
     const double* __restrict__ Uinv, double* __restrict__ x, T* __restrict__ t_cm,
@@ -127,17 +127,24 @@ __global__ void __launch_bounds__(kTileObs, sizeof(T) == 8 ? 2 : 3) series_persi
   const bool tracer = blockIdx.x == 0 && tid == 0 && trace != nullptr;
   for (int i = 1; i <= m_max; ++i) {
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 0] = global_ns();
-    // ---- phase A: tiles
+    // ---- phase A: tiles (the next tile index is fetched while the current one is processed;
+    // a stop decided for the previous term makes the remaining tiles of this one moot)
+    int next = 0;
+    if (tid == 0) next = ld_volatile(&st->done) ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
     for (;;) {
       if (tid == 0) {
-        // a stop decided for the previous term makes the remaining tiles of this one moot
-        s_tile = ld_volatile(&st->done) ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
+        s_tile = next;
+        if (next < tp.n_tiles)
+          next = ld_volatile(&st->done) ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
       }
       __syncthreads();
       const int tile = s_tile;
       __syncthreads();
       if (tile >= tp.n_tiles) break;
-      tile_matvec_body<T, kModeSeries>(tp, tile, J, t_cm, b_l, Vinv, partial, sm);
+      if constexpr (sizeof(T) == 4)
+        tile_matvec_body_f32<kModeSeries>(tp, tile, J, t_cm, b_l, Vinv, partial, sm);
+      else
+        tile_matvec_body<T, kModeSeries>(tp, tile, J, t_cm, b_l, Vinv, partial, sm);
     }
     unsigned gen;
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 1] = global_ns();

@@ -23,7 +23,10 @@ __global__ void __launch_bounds__(kTileObs) tile_matvec_kernel(
     const SeriesState* __restrict__ st) {
   __shared__ TileSmem<T> sm;
   if (MODE == kModeSeries && st->done) return;  // the stop rule fired in an earlier term
-  tile_matvec_body<T, MODE>(tp, blockIdx.x, J, t_cm, b_l, Vinv, partial, sm);
+  if constexpr (sizeof(T) == 4)
+    tile_matvec_body_f32<MODE>(tp, blockIdx.x, J, t_cm, b_l, Vinv, partial, sm);
+  else
+    tile_matvec_body<T, MODE>(tp, blockIdx.x, J, t_cm, b_l, Vinv, partial, sm);
 }
 
 template <typename T>

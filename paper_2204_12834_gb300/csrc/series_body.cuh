@@ -14,6 +14,7 @@
 // x(0) = -U^-1 b~ (Sec. 4.2 and eq. `x_approx` with m = 0).
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 
 #include "poba_internal.cuh"
@@ -51,8 +52,9 @@ __device__ __forceinline__ TileHdr load_tile(const Topology& tp, int tile) {
   return TileHdr{a.x, a.y, a.z, a.w, b.x, b.y};
 }
 
+// 16-byte aligned: the persistent kernel reuses sg as a double array in its camera phase.
 template <typename T>
-struct TileSmem {
+struct __align__(16) TileSmem {
   T tcam[kTileObs][9];
   T sv[kTileObs][3];
   T sg[kTileObs][9];
@@ -60,6 +62,8 @@ struct TileSmem {
   int srow[kTileObs];
   int sseg[kTileLms + 1];
 };
+static_assert(offsetof(TileSmem<float>, sg) % 8 == 0, "sg is reused as double storage");
+static_assert(offsetof(TileSmem<double>, sg) % 8 == 0, "sg is reused as double storage");
 
 // One tile of one term (blockDim.x == kTileObs; every thread must call it).
 template <typename T, int MODE>
@@ -157,6 +161,139 @@ __device__ __forceinline__ void tile_matvec_body(const Topology& tp, int tile,
   }
   __syncthreads();
   slot_sums<T, T>(sm.sg, ns, n, sm.sbeg, sm.srow, partial, 9);
+}
+
+// FP32-bulk tile body (blockDim.x == kTileObs; every thread must call it).  The same sums as
+// tile_matvec_body, arranged for float arithmetic, where redundant FMAs are cheap and barriers
+// are not:
+//   phase 0  J and the observation code into registers; slot threads stage their slot's
+//            first position, camera-major row and current term row; landmark threads stage
+//            their segment, V^-1 and (RHS) b_l and mark their observations' landmark;
+//   phase 1  u = J_p t, v = J_l^T u per observation;
+//   phase 2  every observation thread sums its own landmark's v in segment order and applies
+//            V^-1 (the same sum and the same z in every thread of the landmark), then scatters
+//            g = J_p^T (J_l z) to its camera-sorted position;
+//   phase 3  one warp per slot: lanes take rows beg + lane, beg + lane + 32, ...; a fixed
+//            shuffle tree adds the 9 components; lane 0 writes the slot's row.
+template <int MODE>
+__device__ __forceinline__ void tile_matvec_body_f32(const Topology& tp, int tile,
+                                                     const float* __restrict__ J,
+                                                     const float* __restrict__ t_cm,
+                                                     const double* __restrict__ b_l,
+                                                     const float* __restrict__ Vinv,
+                                                     float* __restrict__ partial,
+                                                     TileSmem<float>& sm) {
+  const int tid = threadIdx.x;
+  const TileHdr th = load_tile(tp, tile);
+  const int o0 = th.o0, n = th.n, ns = th.ns, nl = th.nl;
+  const bool active = tid < n;
+  const size_t pad = (size_t)tp.n_obs_pad;
+  float jp[18], jl[6];
+  int meta = 0;
+  if (active) {
+    const int o = o0 + tid;
+    meta = tp.obs_meta[o];
+    load_J(J, pad, o, jp, jl);
+  }
+  // shared arrays reused here: sbeg / srow per slot, sseg per landmark, tcam per slot,
+  // sv per observation (first the landmark index of each observation, then v);
+  // sg[l][0..5] = V^-1 of landmark l and sg[l][6..8] = b_l (RHS) until phase 2 ends
+  for (int i = tid; i < ns; i += blockDim.x) {
+    const int r = tp.slot_row[th.S0 + i];
+    sm.sbeg[i] = tp.slot_beg[th.S0 + i];
+    sm.srow[i] = r;
+    if (MODE == kModeSeries) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) sm.tcam[i][k] = __ldcg(t_cm + (size_t)r * 9 + k);
+    }
+  }
+  if (tid < nl) {
+    const int a = tp.lm_seg[th.L0 + tid] - o0, b = tp.lm_seg[th.L0 + tid + 1] - o0;
+    sm.sseg[tid] = a;
+    if (tid == nl - 1) sm.sseg[nl] = b;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sm.sg[tid][k] = Vinv[(size_t)(th.L0 + tid) * 6 + k];
+    if (MODE == kModeRhs) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) sm.sg[tid][6 + k] = (float)b_l[(size_t)(th.L0 + tid) * 3 + k];
+    }
+    for (int q = a; q < b; ++q) sm.sv[q][0] = __int_as_float(tid);  // landmark of each obs
+  }
+  __syncthreads();
+  // phase 1
+  int lm = 0;
+  float u0 = 0.f, u1 = 0.f;
+  if (active) {
+    lm = __float_as_int(sm.sv[tid][0]);
+    if (MODE == kModeSeries) {
+      const float* tc = sm.tcam[meta >> 8];
+#pragma unroll
+      for (int j = 0; j < 9; ++j) {
+        u0 += jp[j] * tc[j];
+        u1 += jp[9 + j] * tc[j];
+      }
+    }
+  }
+  __syncthreads();
+  if (MODE == kModeSeries && active) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sm.sv[tid][k] = jl[k] * u0 + jl[3 + k] * u1;
+  }
+  __syncthreads();
+  // phase 2
+  if (active) {
+    float s3[3];
+    const float* vl = sm.sg[lm];
+    if (MODE == kModeSeries) {
+      s3[0] = s3[1] = s3[2] = 0.f;
+      const int a = sm.sseg[lm], b = sm.sseg[lm + 1];
+      for (int q = a; q < b; ++q) {
+        s3[0] += sm.sv[q][0];
+        s3[1] += sm.sv[q][1];
+        s3[2] += sm.sv[q][2];
+      }
+    } else {
+      s3[0] = vl[6];
+      s3[1] = vl[7];
+      s3[2] = vl[8];
+    }
+    const float z0 = vl[0] * s3[0] + vl[1] * s3[1] + vl[2] * s3[2];
+    const float z1 = vl[1] * s3[0] + vl[3] * s3[1] + vl[4] * s3[2];
+    const float z2 = vl[2] * s3[0] + vl[4] * s3[1] + vl[5] * s3[2];
+    const float w0 = jl[0] * z0 + jl[1] * z1 + jl[2] * z2;
+    const float w1 = jl[3] * z0 + jl[4] * z1 + jl[5] * z2;
+    u0 = w0;  // keep g's inputs; the staging array sg still holds V^-1 until the barrier
+    u1 = w1;
+  }
+  __syncthreads();
+  if (active) {
+    float* g = sm.sg[meta & 0xff];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) g[j] = jp[j] * u0 + jp[9 + j] * u1;
+  }
+  __syncthreads();
+  // phase 3: one warp per slot
+  const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  for (int sl = warp; sl < ns; sl += nw) {
+    const int beg = sm.sbeg[sl], end = (sl + 1 < ns) ? (int)sm.sbeg[sl + 1] : n;
+    float acc[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) acc[k] = 0.f;
+    for (int q = beg + lane; q < end; q += 32) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) acc[k] += sm.sg[q][k];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
+    }
+    if (lane == 0) {
+      float* out = partial + (size_t)sm.srow[sl] * 9;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) out[k] = acc[k];
+    }
+  }
 }
 
 // Camera body for cameras [cam0, cam0 + per_block): thread (c, k) sums component k of the
