@@ -130,22 +130,22 @@ def measured_peaks() -> tuple[float, str, float, str]:
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for f in ("kernels_series.cu", "tile_common.cuh", "poba_internal.cuh"):
+    for f in ("kernels_persistent.cu", "series_body.cuh", "tile_common.cuh", "poba_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2204_12834_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic(precision: str):
-    """DRAM bytes per series-tile launch from the committed ncu summary, if the kernel source is
-    unchanged since the capture; else None."""
-    path = os.path.join(ROOT, "profiles", f"series_tile_{WORKLOAD}.json")
+    """DRAM bytes per series term of the persistent kernel from the committed ncu summary, if the
+    kernel source is unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", f"series_persistent_{WORKLOAD}.json")
     try:
         d = json.load(open(path))
     except Exception:
         return None
     if d.get("kernel_source_sha") != kernel_source_sha():
         return None
-    return d.get(precision, {}).get("dram_bytes_per_launch")
+    return d.get(precision, {}).get("dram_bytes_per_term")
 
 
 # ---------------------------------------------------------------------------------------
