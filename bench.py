@@ -69,6 +69,23 @@ def dist_env():
     return rank, world, local
 
 
+def dist_max(v: float, device=None) -> float:
+    """Max of a scalar over all ranks (identity when torch.distributed is not initialised)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(v)
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, slowest_seconds: float) -> float:
+    """Units processed by all ranks / the slowest rank's time (weak scaling: every rank solves
+    its own replica, so the job rate is world x units / max time)."""
+    return world * units_per_rank / slowest_seconds
+
+
 # ---------------------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi clock / throttle sampling (200 ms) while the timed region runs."""
@@ -250,12 +267,7 @@ def run_poba(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return dist_max(v, dev)
 
     results = {}
     clocks = ClockSampler(local)
@@ -402,7 +414,7 @@ def run_poba(args):
 
     line = {
         "metric": METRIC,
-        "value": world * args.steps / (r64["total_ms"] / 1e3),
+        "value": whole_job_rate(args.steps, world, r64["total_ms"] / 1e3),
         "unit": "LM iterations/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -433,7 +445,8 @@ def run_poba(args):
         "memory_bytes": mem_gpu,
         "explicit_S_bytes": explicit_s_bytes(p),
         "kernels": kernel_avgs(r64),
-        "fp32_bulk": {"value": world * args.steps / (r32["total_ms"] / 1e3), "unit": "LM iterations/s",
+        "fp32_bulk": {"value": whole_job_rate(args.steps, world, r32["total_ms"] / 1e3),
+                      "unit": "LM iterations/s",
                       "ms_per_step": r32["total_ms"] / args.steps, "roofline": roof32,
                       "gpu_launches": int(r32["launches"]), "solves_per_s": r32["solves_per_s"],
                       "solve_inner_mean": r32["solve_inner_mean"],
