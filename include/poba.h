@@ -225,6 +225,55 @@ ba_status ba_cost_noalloc(int32_t n_cams, int32_t n_lms, int32_t n_obs, const do
                           const int32_t* lm_idx, const double* weights, double* cost_out,
                           void* cuda_stream);
 
+/* ---- Batches of independent problems ---------------------------------------------------
+ * Sec. 5.3 (Power Stochastic BA, PoST) solves many small, independent sub-problems -- camera clusters
+ * of at most 100 cameras -- each with the power-series solver and the Sec. 5.1 settings.  A
+ * batch handle holds P such problems in one arena; every kernel of a step covers all P at once
+ * (one persistent series launch for the whole batch), while each problem keeps its own LM
+ * record (lambda, nu, cost, gain ratio, accept), its own series stop rule and its own
+ * convergence test.  Results per problem equal those of a handle created for that problem
+ * alone, bit for bit.
+ *
+ * ba_create_batch: descs[0 .. n_problems-1] as for ba_create, each problem's indices local to
+ * that problem (0 <= cam_idx < its n_cams).  All problems need the same precision; weights may
+ * be NULL for some problems (ones) and not others; descs[0].cuda_stream orders the batch.
+ * The batch behaves as one problem whose cameras, landmarks and observations are the
+ * problems' concatenated in order: ba_get_params / ba_set_params / ba_get_step /
+ * ba_get_linearization / ba_get_blocks use that concatenation, ba_get_batch_layout gives its
+ * offsets, ba_cost and ba_linearize's cost return the sum over problems, and
+ * ba_solve_schur_power solves every problem with the one lambda given (its info then holds the
+ * largest m and stop value, stopped = 1 iff every problem stopped, and the norm of the whole
+ * camera step; ba_get_series_state gives each problem's).  ba_lm_step, ba_lm_solve and
+ * ba_get_lm_state reject a handle with more than one problem (BA_ERR_INVALID_ARG);
+ * ba_set_lm_state sets every problem's state and makes every problem active again.
+ * Errors of ba_create_batch: those of ba_create, prefixed "problem p:" in ba_last_error, and
+ * BA_ERR_INVALID_ARG for n_problems < 1 or mixed precisions. */
+ba_status ba_create_batch(const ba_problem_desc* descs, int32_t n_problems, const ba_options* opts,
+                          ba_handle** out);
+
+/* *n_problems = P; cam_off / lm_off (each [P+1], either may be NULL): problem p owns cameras
+ * [cam_off[p], cam_off[p+1]) and landmarks [lm_off[p], lm_off[p+1]) of the concatenation.
+ * A handle from ba_create reports P = 1. */
+ba_status ba_get_batch_layout(ba_handle* h, int32_t* n_problems, int32_t* cam_off, int32_t* lm_off);
+
+/* Series state of the last solve per problem: infos[P] (m, stopped, stop value, ||x(m)|| and
+ * the lambda that problem was damped with).  Synchronises. */
+ba_status ba_get_series_state(ba_handle* h, ba_series_info* infos);
+
+/* One LM iteration (as ba_lm_step) of every active problem of the handle.  A problem that
+ * converges (accepted with relative decrease < func_tol) becomes inactive: later steps leave it
+ * unchanged, its series is skipped, and its info keeps converged = 1 and its own iteration
+ * count with accepted = 0.  infos (may be NULL) receives P entries; *n_active (may be NULL) the
+ * problems still active afterwards.  Synchronises once.  Errors as ba_lm_step (any problem). */
+ba_status ba_lm_step_batch(ba_handle* h, ba_step_info* infos, int32_t* n_active);
+
+/* ba_lm_step_batch until no problem is active or max_lm steps ran; infos (may be NULL, P
+ * entries) receives each problem's last step, *n_steps the steps run. */
+ba_status ba_lm_solve_batch(ba_handle* h, ba_step_info* infos, int32_t* n_steps);
+
+/* F(x) of each problem at the current state: costs[P] (host), float64, fixed order. */
+ba_status ba_cost_batch(ba_handle* h, double* costs);
+
 /* Free all device memory of the handle (and its own stream, if it created one). NULL is OK. */
 ba_status ba_destroy(ba_handle* h);
 

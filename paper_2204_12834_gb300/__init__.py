@@ -25,7 +25,9 @@ __all__ = ["PobaError", "Handle", "ba_default_options", "ba_create", "ba_set_opt
            "ba_get_blocks", "ba_get_lm_state", "ba_set_lm_state", "ba_memory_footprint",
            "ba_kernel_launches", "ba_set_timing", "ba_get_timing", "ba_destroy", "BA_FP64",
            "BA_FP32_BULK", "library", "from_problem", "ba_cost_noalloc", "BA_NOALLOC_MAX_CAMS",
-           "ba_get_series_trace", "ba_set_barrier_timeout"]
+           "ba_get_series_trace", "ba_set_barrier_timeout", "ba_create_batch",
+           "ba_get_batch_layout", "ba_get_series_state", "ba_lm_step_batch", "ba_lm_solve_batch",
+           "ba_cost_batch", "batch_from_problems"]
 
 BA_NOALLOC_MAX_CAMS = 4096
 
@@ -72,6 +74,7 @@ class Handle:
     n_lms: int
     n_obs: int
     precision: int
+    n_problems: int = 1
 
     def __del__(self):
         try:
@@ -92,15 +95,11 @@ def ba_default_options(**overrides) -> Options:
     return o
 
 
-def ba_create(cams, lms, obs, cam_idx, lm_idx, weights=None, precision: int = BA_FP64,
-              options: Optional[Options] = None, stream=None) -> Handle:
-    """Create a problem handle (copies every input)."""
+def _fill_desc(d: ProblemDesc, cams, lms, obs, cam_idx, lm_idx, weights, precision, stream, keep):
     n_c = int(cams.shape[0])
     n_l = int(lms.shape[0])
     n_o = int(obs.shape[0])
-    keep = []
     kinds = set()
-    d = ProblemDesc()
     d.n_cams, d.n_lms, d.n_obs = n_c, n_l, n_o
     for field, arr, dt in (("cams", cams, np.float64), ("lms", lms, np.float64),
                            ("obs", obs, np.float64), ("cam_idx", cam_idx, np.int32),
@@ -116,10 +115,93 @@ def ba_create(cams, lms, obs, cam_idx, lm_idx, weights=None, precision: int = BA
     d.precision = int(precision)
     if stream is not None:
         d.cuda_stream = int(getattr(stream, "cuda_stream", stream)) or None
+    return n_c, n_l, n_o
+
+
+def ba_create(cams, lms, obs, cam_idx, lm_idx, weights=None, precision: int = BA_FP64,
+              options: Optional[Options] = None, stream=None) -> Handle:
+    """Create a problem handle (copies every input)."""
+    keep = []
+    d = ProblemDesc()
+    n_c, n_l, n_o = _fill_desc(d, cams, lms, obs, cam_idx, lm_idx, weights, precision, stream, keep)
     out = C.c_void_p()
     opts = options if options is not None else ba_default_options()
     _check(library().ba_create(C.byref(d), C.byref(opts), C.byref(out)), "ba_create")
     return Handle(out, n_c, n_l, n_o, int(precision))
+
+
+def ba_create_batch(problems, precision: int = BA_FP64, options: Optional[Options] = None,
+                    stream=None) -> Handle:
+    """Create a batch handle from a sequence of (cams, lms, obs, cam_idx, lm_idx, weights)
+    tuples, indices local to each problem.  The handle's arrays are the problems'
+    concatenated in order (offsets: ba_get_batch_layout)."""
+    keep = []
+    descs = (ProblemDesc * len(problems))()
+    tot = [0, 0, 0]
+    for i, pr in enumerate(problems):
+        cams, lms, obs, ci, li = pr[:5]
+        w = pr[5] if len(pr) > 5 else None
+        sizes = _fill_desc(descs[i], cams, lms, obs, ci, li, w, precision,
+                           stream if i == 0 else None, keep)
+        tot = [a + b for a, b in zip(tot, sizes)]
+    out = C.c_void_p()
+    opts = options if options is not None else ba_default_options()
+    _check(library().ba_create_batch(descs, len(problems), C.byref(opts), C.byref(out)),
+           "ba_create_batch")
+    return Handle(out, tot[0], tot[1], tot[2], int(precision), len(problems))
+
+
+def batch_from_problems(problems, precision: int = BA_FP64, options: Optional[Options] = None,
+                        stream=None) -> Handle:
+    """ba_create_batch from bal_synth.Problem-like objects."""
+    return ba_create_batch([(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, p.weights)
+                            for p in problems], precision=precision, options=options,
+                           stream=stream)
+
+
+def ba_get_batch_layout(h: Handle):
+    """(cam_off, lm_off), each [P + 1]: problem p owns cameras cam_off[p]:cam_off[p+1] and
+    landmarks lm_off[p]:lm_off[p+1] of the handle's arrays."""
+    n = C.c_int32()
+    _check(library().ba_get_batch_layout(h.ptr, C.byref(n), None, None), "ba_get_batch_layout")
+    co = np.empty(n.value + 1, dtype=np.int32)
+    lo = np.empty(n.value + 1, dtype=np.int32)
+    _check(library().ba_get_batch_layout(h.ptr, C.byref(n), co.ctypes.data, lo.ctypes.data),
+           "ba_get_batch_layout")
+    return co, lo
+
+
+def _series_dict(info: SeriesInfo) -> dict:
+    return dict(inner_iters=info.inner_iters, stopped=info.stopped, stop_value=info.stop_value,
+                x_norm=info.x_norm, lam=info.lambda_)
+
+
+def ba_get_series_state(h: Handle) -> list:
+    infos = (SeriesInfo * h.n_problems)()
+    _check(library().ba_get_series_state(h.ptr, infos), "ba_get_series_state")
+    return [_series_dict(infos[i]) for i in range(h.n_problems)]
+
+
+def ba_lm_step_batch(h: Handle):
+    """(list of per-problem step dicts, number of problems still active)."""
+    infos = (StepInfo * h.n_problems)()
+    n = C.c_int32()
+    _check(library().ba_lm_step_batch(h.ptr, infos, C.byref(n)), "ba_lm_step_batch")
+    return [_step_dict(infos[i]) for i in range(h.n_problems)], n.value
+
+
+def ba_lm_solve_batch(h: Handle):
+    """(list of each problem's last step dict, number of batch steps run)."""
+    infos = (StepInfo * h.n_problems)()
+    n = C.c_int32()
+    _check(library().ba_lm_solve_batch(h.ptr, infos, C.byref(n)), "ba_lm_solve_batch")
+    return [_step_dict(infos[i]) for i in range(h.n_problems)], n.value
+
+
+def ba_cost_batch(h: Handle) -> np.ndarray:
+    c = np.empty(h.n_problems, dtype=np.float64)
+    _check(library().ba_cost_batch(h.ptr, c.ctypes.data), "ba_cost_batch")
+    return c
 
 
 def ba_set_options(h: Handle, options: Options):
@@ -138,8 +220,7 @@ def ba_solve_schur_power(h: Handle, lam: float, want_info: bool = True):
            "ba_solve_schur_power")
     if not want_info:
         return None
-    return dict(inner_iters=info.inner_iters, stopped=info.stopped, stop_value=info.stop_value,
-                x_norm=info.x_norm, lam=info.lambda_)
+    return _series_dict(info)
 
 
 def _step_dict(s: StepInfo) -> dict:

@@ -75,6 +75,13 @@ SIGNATURES = {
                                   C.c_void_p]),
     "ba_set_barrier_timeout": (C.c_int, [C.c_void_p, C.c_int64]),
     "ba_get_series_trace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    "ba_create_batch": (C.c_int, [C.POINTER(ProblemDesc), C.c_int32, C.POINTER(Options),
+                                  C.POINTER(C.c_void_p)]),
+    "ba_get_batch_layout": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_void_p, C.c_void_p]),
+    "ba_get_series_state": (C.c_int, [C.c_void_p, C.POINTER(SeriesInfo)]),
+    "ba_lm_step_batch": (C.c_int, [C.c_void_p, C.POINTER(StepInfo), C.POINTER(C.c_int32)]),
+    "ba_lm_solve_batch": (C.c_int, [C.c_void_p, C.POINTER(StepInfo), C.POINTER(C.c_int32)]),
+    "ba_cost_batch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ba_destroy": (C.c_int, [C.c_void_p]),
     "ba_status_string": (C.c_char_p, [C.c_int]),
     "ba_last_error": (C.c_char_p, []),

@@ -82,32 +82,40 @@ struct ba_handle {
   // series
   double* x = nullptr;
   double* dx_l = nullptr;
-  double* block_norms = nullptr;
-  double* block_cost = nullptr;
-  double* block_pred = nullptr;
-  double* scalars = nullptr;  // [0] lambda for explicit solves, [1] cost out
-  double* group_norms = nullptr;  // persistent kernel: squared norms per camera group
+  double* cam_norm = nullptr;     // (||t_c||^2, ||x_c||^2) per camera
+  double* block_cost = nullptr;   // per tile: 2 F at the linearisation point
+  double* tile_cost = nullptr;    // per tile: 2 F at a trial point
+  double* block_pred = nullptr;   // per tile: 2 (L(0) - L(dx))
+  double* scalars = nullptr;      // [0] lambda for explicit solves, [1] cost out
+  double* prob_cost = nullptr;    // [n_probs] F per problem (ba_cost_batch)
   GridSync* gs = nullptr;         // persistent kernel: grid-barrier state
   long long* trace = nullptr;     // persistent kernel: phase timeline of block 0
-  SeriesState* st = nullptr;
-  LmRecord* rec = nullptr;
+  SeriesState* st = nullptr;      // [n_probs]
+  SeriesGlobal* sgl = nullptr;
+  LmRecord* rec = nullptr;        // [n_probs]
   int32_t* not_spd = nullptr;
+  int n_probs = 1;
+  std::vector<int32_t> cam_off_h, lm_off_h;  // caller numbering of the problems' cameras / landmarks
 
   // host staging (pinned)
-  SeriesState* h_st = nullptr;
+  SeriesState* h_st = nullptr;   // [n_probs]
+  SeriesGlobal* h_sgl = nullptr;
   GridSync* h_gs = nullptr;
-  LmRecord* h_rec = nullptr;
+  LmRecord* h_rec = nullptr;     // [n_probs]
   int32_t* h_flag = nullptr;
   double* h_scalar = nullptr;
 
   bool linearized = false;
   bool cost_valid = false;
   bool have_step = false;
+  bool last_solve_lm = false;  // the last solve was an LM step (per-problem lambdas)
+  double solve_lambda = 0.0;   // lambda of the last explicit solve
   cudaGraphExec_t graph_exec = nullptr;
   int graph_max_inner = -1;
   double graph_eps = -1.0;
   int graph_nodes = 0;
   bool graph_timing = false;
+  bool graph_active = false;
   int persist_grid = 0;                  // blocks of the persistent kernel (0: unavailable)
   long long barrier_timeout = 1LL << 33;  // clock cycles a block waits at a grid barrier
   int last_exec = -1;                    // series_exec of the last solve
@@ -252,22 +260,22 @@ void seq_linearize(ba_handle* h) {
 
 // series reset, b~ / x(0), max_inner terms, back-substitution with model decrease
 template <typename T>
-void seq_series_body(ba_handle* h, cudaStream_t s) {
+void seq_series_body(ba_handle* h, cudaStream_t s, bool use_active) {
   const Topology& tp = h->tp;
   const T* J = (const T*)h->J;
   const T* Vi = h->f32() ? (const T*)(const void*)h->Vinv_f : (const T*)(const void*)h->Vinv;
   T* part = (T*)h->partial;
-  launch_series_reset(h->st, s);
+  launch_series_reset(h->st, h->sgl, use_active ? h->rec : nullptr, h->n_probs, s);
   tmark(h, kTRhs, 0, 0);
   launch_tile_rhs<T>(tp, J, h->b_l, Vi, part, h->st, s);
-  launch_camera_rhs<T>(tp, part, h->b_p, h->Uinv, h->x, (T*)h->t_cm, h->block_norms, h->st, s);
+  launch_camera_rhs<T>(tp, part, h->b_p, h->Uinv, h->x, (T*)h->t_cm, h->cam_norm, h->st, h->sgl, s);
   tmark(h, kTRhs, 0, 1);
   for (int i = 1; i <= h->opts.max_inner; ++i) {
     tmark(h, kTTile, i, 0);
-    launch_tile_series<T>(tp, J, (const T*)h->t_cm, Vi, part, h->st, s);
+    launch_tile_series<T>(tp, J, (const T*)h->t_cm, Vi, part, h->st, h->sgl, s);
     tmark(h, kTTile, i, 1);
     tmark(h, kTCam, i, 0);
-    launch_camera_series<T>(tp, part, h->Uinv, h->x, (T*)h->t_cm, h->block_norms, h->st, i,
+    launch_camera_series<T>(tp, part, h->Uinv, h->x, (T*)h->t_cm, h->cam_norm, h->st, h->sgl, i,
                             h->opts.eps, s);
     tmark(h, kTCam, i, 1);
   }
@@ -279,23 +287,22 @@ void seq_series_body(ba_handle* h, cudaStream_t s) {
 int series_body_kernels(const ba_handle* h) { return 4 + 2 * h->opts.max_inner; }
 
 template <typename T>
-ba_status seq_series_persistent(ba_handle* h, cudaStream_t s) {
+ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active) {
   const Topology& tp = h->tp;
   const T* J = (const T*)h->J;
   const T* Vi = h->f32() ? (const T*)(const void*)h->Vinv_f : (const T*)(const void*)h->Vinv;
   T* part = (T*)h->partial;
-  launch_series_reset(h->st, s);
+  launch_series_reset(h->st, h->sgl, use_active ? h->rec : nullptr, h->n_probs, s);
   tmark(h, kTRhs, 0, 0);
   launch_tile_rhs<T>(tp, J, h->b_l, Vi, part, h->st, s);
-  launch_camera_rhs<T>(tp, part, h->b_p, h->Uinv, h->x, (T*)h->t_cm, h->block_norms, h->st, s);
+  launch_camera_rhs<T>(tp, part, h->b_p, h->Uinv, h->x, (T*)h->t_cm, h->cam_norm, h->st, h->sgl, s);
   tmark(h, kTRhs, 0, 1);
   CK(cudaMemsetAsync(h->gs, 0, sizeof(GridSync), s));
   if (h->opts.max_inner > 0) {
     tmark(h, kTTile, 1, 0);
-    CK(launch_series_persistent<T>(tp, h->persist_grid, J, Vi, h->b_l, h->b_p, h->Uinv, h->x,
-                                   (T*)h->t_cm, part, h->group_norms, h->st, h->gs,
-                                   h->opts.max_inner, h->opts.eps, h->barrier_timeout, h->trace,
-                                   s));
+    CK(launch_series_persistent<T>(tp, h->persist_grid, J, Vi, h->Uinv, h->x, (T*)h->t_cm, part,
+                                   h->cam_norm, h->st, h->sgl, h->gs, h->opts.max_inner,
+                                   h->opts.eps, h->barrier_timeout, h->trace, s));
     tmark(h, kTTile, 1, 1);
   }
   tmark(h, kTBack, 0, 0);
@@ -305,7 +312,7 @@ ba_status seq_series_persistent(ba_handle* h, cudaStream_t s) {
   return BA_OK;
 }
 
-ba_status run_series_body(ba_handle* h) {
+ba_status run_series_body(ba_handle* h, bool use_active) {
   cudaStream_t s = h->stream;
   if (h->timing) {
     ba_status st = ensure_events(h);
@@ -315,13 +322,14 @@ ba_status run_series_body(ba_handle* h) {
   if (mode == 2 && h->persist_grid <= 0) mode = 1;
   h->last_exec = mode;
   if (mode == 2) {
-    ba_status st = h->f32() ? seq_series_persistent<float>(h, s) : seq_series_persistent<double>(h, s);
+    ba_status st = h->f32() ? seq_series_persistent<float>(h, s, use_active)
+                            : seq_series_persistent<double>(h, s, use_active);
     if (st == BA_OK) h->pending[kTRhs] = h->pending[kTBack] = h->timing;
     return st;
   }
   if (mode == 1) {
     if (!h->graph_exec || h->graph_max_inner != h->opts.max_inner || h->graph_eps != h->opts.eps ||
-        h->graph_timing != h->timing) {
+        h->graph_timing != h->timing || h->graph_active != use_active) {
       if (h->graph_exec) {
         cudaGraphExecDestroy(h->graph_exec);
         h->graph_exec = nullptr;
@@ -329,8 +337,8 @@ ba_status run_series_body(ba_handle* h) {
       cudaGraph_t g = nullptr;
       CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
       h->capturing = true;
-      if (h->f32()) seq_series_body<float>(h, s);
-      else seq_series_body<double>(h, s);
+      if (h->f32()) seq_series_body<float>(h, s, use_active);
+      else seq_series_body<double>(h, s, use_active);
       h->capturing = false;
       cudaError_t e = cudaStreamEndCapture(s, &g);
       if (e != cudaSuccess) return fail_cuda(e, "cudaStreamEndCapture");
@@ -343,6 +351,7 @@ ba_status run_series_body(ba_handle* h) {
       h->graph_max_inner = h->opts.max_inner;
       h->graph_eps = h->opts.eps;
       h->graph_timing = h->timing;
+      h->graph_active = use_active;
     }
     CK(cudaGraphLaunch(h->graph_exec, s));
     if (h->timing) {
@@ -351,36 +360,41 @@ ba_status run_series_body(ba_handle* h) {
     }
     h->launches += (uint64_t)series_body_kernels(h);
   } else {
-    if (h->f32()) seq_series_body<float>(h, s);
-    else seq_series_body<double>(h, s);
+    if (h->f32()) seq_series_body<float>(h, s, use_active);
+    else seq_series_body<double>(h, s, use_active);
     h->launches += (uint64_t)series_body_kernels(h);
   }
   return BA_OK;
 }
 
-ba_status run_solve(ba_handle* h, const double* lam_dev) {
+// lambda of problem p at lam_dev[p * lam_stride]; use_active: problems whose LM record is
+// inactive take no part.
+ba_status run_solve(ba_handle* h, const double* lam_dev, int lam_stride, bool use_active) {
   CK(cudaMemsetAsync(h->not_spd, 0, sizeof(int32_t), h->stream));
   if (h->timing) {
     ba_status st = ensure_events(h);
     if (st != BA_OK) return st;
   }
   tmark(h, kTDamp, 0, 0);
-  launch_damp_invert(h->tp, h->U45, h->V, lam_dev, h->opts.damping_mode, h->Uinv, h->Vinv,
-                     h->f32() ? h->Vinv_f : nullptr, h->not_spd, h->stream);
+  launch_damp_invert(h->tp, h->U45, h->V, lam_dev, lam_stride, h->opts.damping_mode, h->Uinv,
+                     h->Vinv, h->f32() ? h->Vinv_f : nullptr, h->not_spd, h->stream);
   tmark(h, kTDamp, 0, 1);
   h->launches += 1;
-  ba_status st = run_series_body(h);
+  ba_status st = run_series_body(h, use_active);
   if (st != BA_OK) return st;
   h->have_step = true;
   return check_launch(h, "series kernels");
 }
 
-void seq_cost(ba_handle* h, double* out_dev) {
+// F(x) per problem at the current state into out[p * stride] (fixed order).
+void seq_cost(ba_handle* h, double* out, int stride) {
   launch_cam_prepare(h->cams, nullptr, h->n_c, h->prep, nullptr, h->stream);
-  launch_cost(h->tp, h->prep, h->lms, nullptr, h->obs, h->sqrt_w, h->block_cost, h->stream);
-  launch_reduce_sum(h->block_cost, cost_blocks(h->tp), out_dev, 0.5, h->stream);
+  launch_tile_cost(h->tp, h->prep, h->lms, nullptr, h->obs, h->sqrt_w, h->tile_cost, h->stream);
+  launch_reduce_tiles(h->tp, h->tile_cost, out, stride, 0.5, h->stream);
   h->launches += 3;
 }
+
+constexpr int kRecStride = (int)(sizeof(LmRecord) / sizeof(double));
 
 }  // namespace
 
@@ -405,6 +419,7 @@ ba_status ba_destroy(ba_handle* h) {
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->arena) cudaFree(h->arena);
   if (h->h_st) cudaFreeHost(h->h_st);
+  if (h->h_sgl) cudaFreeHost(h->h_sgl);
   if (h->h_rec) cudaFreeHost(h->h_rec);
   if (h->h_gs) cudaFreeHost(h->h_gs);
   if (h->h_flag) cudaFreeHost(h->h_flag);
@@ -414,70 +429,133 @@ ba_status ba_destroy(ba_handle* h) {
   return BA_OK;
 }
 
-ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle** out) {
+}  // extern "C"
+
+namespace {
+
+// ba_create and ba_create_batch: the problems are concatenated (cameras, landmarks and
+// observations of problem p follow those of problem p - 1, with indices offset to match) and
+// scheduled so that no tile holds two problems.
+ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_options* opts,
+                      ba_handle** out) {
   if (!out) return fail(BA_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (!d) return fail(BA_ERR_INVALID_ARG, "desc is NULL");
-  if (d->n_cams < 1 || d->n_lms < 1 || d->n_obs < 0)
-    return fail(BA_ERR_INVALID_ARG, "need n_cams >= 1, n_lms >= 1, n_obs >= 0");
-  if (d->ptr_kind != 0 && d->ptr_kind != 1) return fail(BA_ERR_INVALID_ARG, "ptr_kind must be 0 or 1");
-  if (d->precision != BA_FP64 && d->precision != BA_FP32_BULK)
-    return fail(BA_ERR_INVALID_ARG, "precision must be BA_FP64 or BA_FP32_BULK");
-  if (!d->cams || !d->lms) return fail(BA_ERR_INVALID_ARG, "cams / lms is NULL");
-  if (d->n_obs > 0 && (!d->obs || !d->cam_idx || !d->lm_idx))
-    return fail(BA_ERR_INVALID_ARG, "obs / cam_idx / lm_idx is NULL");
+  if (!descs) return fail(BA_ERR_INVALID_ARG, "desc is NULL");
+  if (n_probs < 1) return fail(BA_ERR_INVALID_ARG, "n_problems must be >= 1");
+  const int precision = descs[0].precision;
+  int64_t tc = 0, tl = 0, to = 0;
+  bool weighted = false;
+  for (int p = 0; p < n_probs; ++p) {
+    const ba_problem_desc* d = &descs[p];
+    const std::string pre = n_probs > 1 ? "problem " + std::to_string(p) + ": " : "";
+    if (d->n_cams < 1 || d->n_lms < 1 || d->n_obs < 0)
+      return fail(BA_ERR_INVALID_ARG, pre + "need n_cams >= 1, n_lms >= 1, n_obs >= 0");
+    if (d->ptr_kind != 0 && d->ptr_kind != 1)
+      return fail(BA_ERR_INVALID_ARG, pre + "ptr_kind must be 0 or 1");
+    if (d->precision != BA_FP64 && d->precision != BA_FP32_BULK)
+      return fail(BA_ERR_INVALID_ARG, pre + "precision must be BA_FP64 or BA_FP32_BULK");
+    if (d->precision != precision)
+      return fail(BA_ERR_INVALID_ARG, pre + "all problems of a batch need the same precision");
+    if (!d->cams || !d->lms) return fail(BA_ERR_INVALID_ARG, pre + "cams / lms is NULL");
+    if (d->n_obs > 0 && (!d->obs || !d->cam_idx || !d->lm_idx))
+      return fail(BA_ERR_INVALID_ARG, pre + "obs / cam_idx / lm_idx is NULL");
+    tc += d->n_cams;
+    tl += d->n_lms;
+    to += d->n_obs;
+    weighted = weighted || d->weights != nullptr;
+  }
+  if (tc > (1 << 28) || tl > (1 << 28) || to > (1LL << 31) - 128)
+    return fail(BA_ERR_INVALID_ARG, "problem too large (cameras, landmarks < 2^28, observations < 2^31)");
   ba_options o;
   ba_default_options(&o);
   if (opts) o = *opts;
   std::string why;
   if (!valid_options(o, &why)) return fail(BA_ERR_INVALID_ARG, why);
 
-  const int nc = d->n_cams, nl = d->n_lms, no = d->n_obs;
+  const int nc = (int)tc, nl = (int)tl, no = (int)to;
   std::vector<double> cams, lms, obs, w;
-  std::vector<int32_t> ci, li;
-  copy_in(cams, d->cams, (size_t)nc * 9, d->ptr_kind);
-  copy_in(lms, d->lms, (size_t)nl * 3, d->ptr_kind);
-  copy_in(obs, d->obs, (size_t)no * 2, d->ptr_kind);
-  copy_in(ci, d->cam_idx, (size_t)no, d->ptr_kind);
-  copy_in(li, d->lm_idx, (size_t)no, d->ptr_kind);
-  if (d->weights) copy_in(w, d->weights, (size_t)no, d->ptr_kind);
-  if (d->ptr_kind == 1) {
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return fail_cuda(e, "copying device inputs");
+  std::vector<int32_t> ci, li, cam_off(n_probs + 1, 0), lm_off(n_probs + 1, 0);
+  cams.reserve((size_t)nc * 9);
+  lms.reserve((size_t)nl * 3);
+  obs.reserve((size_t)no * 2);
+  ci.reserve(no);
+  li.reserve(no);
+  if (weighted) w.reserve(no);
+  for (int p = 0; p < n_probs; ++p) {
+    const ba_problem_desc* d = &descs[p];
+    const std::string pre = n_probs > 1 ? "problem " + std::to_string(p) + ": " : "";
+    std::vector<double> c1, l1, o1, w1;
+    std::vector<int32_t> ci1, li1;
+    copy_in(c1, d->cams, (size_t)d->n_cams * 9, d->ptr_kind);
+    copy_in(l1, d->lms, (size_t)d->n_lms * 3, d->ptr_kind);
+    copy_in(o1, d->obs, (size_t)d->n_obs * 2, d->ptr_kind);
+    copy_in(ci1, d->cam_idx, (size_t)d->n_obs, d->ptr_kind);
+    copy_in(li1, d->lm_idx, (size_t)d->n_obs, d->ptr_kind);
+    if (d->weights) copy_in(w1, d->weights, (size_t)d->n_obs, d->ptr_kind);
+    if (d->ptr_kind == 1) {
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return fail_cuda(e, "copying device inputs");
+    }
+    for (double v : c1) if (!std::isfinite(v)) return fail(BA_ERR_NONFINITE, pre + "non-finite camera parameter");
+    for (double v : l1) if (!std::isfinite(v)) return fail(BA_ERR_NONFINITE, pre + "non-finite landmark");
+    for (double v : o1) if (!std::isfinite(v)) return fail(BA_ERR_NONFINITE, pre + "non-finite observation");
+    for (double v : w1)
+      if (!(v > 0.0) || !std::isfinite(v)) return fail(BA_ERR_INVALID_ARG, pre + "weights must be finite and > 0");
+    if (n_probs > 1) {
+      // index ranges are checked per problem before the offsets are added
+      for (int k = 0; k < d->n_obs; ++k) {
+        if (ci1[k] < 0 || ci1[k] >= d->n_cams)
+          return fail(BA_ERR_INVALID_ARG, pre + "cam_idx[" + std::to_string(k) + "] out of range");
+        if (li1[k] < 0 || li1[k] >= d->n_lms)
+          return fail(BA_ERR_INVALID_ARG, pre + "lm_idx[" + std::to_string(k) + "] out of range");
+      }
+    }
+    const int32_t c0 = cam_off[p], l0 = lm_off[p];
+    cams.insert(cams.end(), c1.begin(), c1.end());
+    lms.insert(lms.end(), l1.begin(), l1.end());
+    obs.insert(obs.end(), o1.begin(), o1.end());
+    for (int k = 0; k < d->n_obs; ++k) {
+      ci.push_back(ci1[k] + c0);
+      li.push_back(li1[k] + l0);
+    }
+    if (weighted) {
+      if (d->weights) w.insert(w.end(), w1.begin(), w1.end());
+      else w.insert(w.end(), (size_t)d->n_obs, 1.0);
+    }
+    cam_off[p + 1] = c0 + d->n_cams;
+    lm_off[p + 1] = l0 + d->n_lms;
   }
-  for (double v : cams) if (!std::isfinite(v)) return fail(BA_ERR_NONFINITE, "non-finite camera parameter");
-  for (double v : lms) if (!std::isfinite(v)) return fail(BA_ERR_NONFINITE, "non-finite landmark");
-  for (double v : obs) if (!std::isfinite(v)) return fail(BA_ERR_NONFINITE, "non-finite observation");
-  for (double v : w) if (!(v > 0.0) || !std::isfinite(v)) return fail(BA_ERR_INVALID_ARG, "weights must be finite and > 0");
 
   ba_handle* h = new ba_handle();
   h->n_c = nc;
   h->n_l = nl;
   h->n_o = no;
   h->n_o_pad = (int)align_up((size_t)(no > 0 ? no : 1), 64);
-  h->precision = d->precision;
-  h->weighted = d->weights != nullptr;
+  h->precision = precision;
+  h->weighted = weighted;
   h->opts = o;
-  why = build_schedule(nc, nl, no, ci.data(), li.data(), &h->sched);
+  h->n_probs = n_probs;
+  h->cam_off_h = cam_off;
+  h->lm_off_h = lm_off;
+  why = build_schedule(nc, nl, no, ci.data(), li.data(), n_probs, cam_off.data(), lm_off.data(),
+                       &h->sched);
   if (!why.empty()) {
     delete h;
     return fail(BA_ERR_INVALID_ARG, why);
   }
   const Schedule& S = h->sched;
+  std::vector<int32_t> tile_prob(S.n_tiles);
+  for (int t = 0; t < S.n_tiles; ++t) tile_prob[t] = S.lm_prob[S.tile_lm0[t]];
 
   // ---- arena layout
   const size_t bulk = h->f32() ? sizeof(float) : sizeof(double);
   struct Item { void** ptr; size_t bytes; };
   std::vector<Item> items;
   int32_t *d_lm_seg, *d_cam_of, *d_lm_of, *d_tile_lm0, *d_tile_slot0, *d_slot_cam, *d_cam_slot_ptr, *d_cam_slot_list;
-  int32_t* d_tile_desc;
-  int32_t* d_slot_row;
+  int32_t *d_tile_desc, *d_slot_row, *d_cam_prob, *d_lm_prob, *d_tile_prob, *d_cam_off, *d_tile_off;
   uint16_t *d_meta, *d_slot_beg;
   const size_t slots = (size_t)(S.n_slots > 0 ? S.n_slots : 1);
-  const int nbn = (nc + kCamBlock - 1) / kCamBlock;  // camera-step blocks
-  Topology tmp{};
-  tmp.n_obs = no;
-  const int ncost = cost_blocks(tmp);
+  const size_t P = (size_t)n_probs;
   items.push_back({(void**)&d_lm_seg, sizeof(int32_t) * (nl + 1)});
   items.push_back({(void**)&d_cam_of, sizeof(int32_t) * (no > 0 ? no : 1)});
   items.push_back({(void**)&d_lm_of, sizeof(int32_t) * (no > 0 ? no : 1)});
@@ -490,8 +568,13 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
   items.push_back({(void**)&d_cam_slot_ptr, sizeof(int32_t) * (nc + 1)});
   items.push_back({(void**)&d_cam_slot_list, sizeof(int32_t) * slots});
   items.push_back({(void**)&d_slot_row, sizeof(int32_t) * slots});
+  items.push_back({(void**)&d_cam_prob, sizeof(int32_t) * nc});
+  items.push_back({(void**)&d_lm_prob, sizeof(int32_t) * nl});
+  items.push_back({(void**)&d_tile_prob, sizeof(int32_t) * S.n_tiles});
+  items.push_back({(void**)&d_cam_off, sizeof(int32_t) * (P + 1)});
+  items.push_back({(void**)&d_tile_off, sizeof(int32_t) * (P + 1)});
   items.push_back({(void**)&h->obs, sizeof(double2) * (no > 0 ? no : 1)});
-  if (h->weighted) items.push_back({(void**)&h->sqrt_w, sizeof(double) * no});
+  if (h->weighted) items.push_back({(void**)&h->sqrt_w, sizeof(double) * (no > 0 ? no : 1)});
   items.push_back({(void**)&h->cams, sizeof(double) * nc * 9});
   items.push_back({(void**)&h->cams_trial, sizeof(double) * nc * 9});
   items.push_back({(void**)&h->lms, sizeof(double) * nl * 3});
@@ -510,17 +593,17 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
   if (h->f32()) items.push_back({(void**)&h->Vinv_f, sizeof(float) * nl * 6});
   items.push_back({(void**)&h->x, sizeof(double) * nc * 9});
   items.push_back({(void**)&h->dx_l, sizeof(double) * nl * 3});
-  items.push_back({(void**)&h->block_norms, sizeof(double) * 2 * nbn});
-  items.push_back({(void**)&h->block_cost, sizeof(double) * (S.n_tiles > ncost ? S.n_tiles : ncost)});
+  items.push_back({(void**)&h->cam_norm, sizeof(double) * 2 * nc});
+  items.push_back({(void**)&h->block_cost, sizeof(double) * S.n_tiles});
+  items.push_back({(void**)&h->tile_cost, sizeof(double) * S.n_tiles});
   items.push_back({(void**)&h->block_pred, sizeof(double) * S.n_tiles});
   items.push_back({(void**)&h->scalars, sizeof(double) * 4});
-  // persistent kernel: one (||t||^2, ||x||^2) pair per camera group; a group holds at least one
-  // camera, so there are at most n_cams groups whatever the grid size
-  items.push_back({(void**)&h->group_norms, sizeof(double) * 2 * nc});
+  items.push_back({(void**)&h->prob_cost, sizeof(double) * P});
   items.push_back({(void**)&h->gs, sizeof(GridSync)});
   items.push_back({(void**)&h->trace, sizeof(long long) * kTraceTerms * kTracePoints});
-  items.push_back({(void**)&h->st, sizeof(SeriesState)});
-  items.push_back({(void**)&h->rec, sizeof(LmRecord)});
+  items.push_back({(void**)&h->st, sizeof(SeriesState) * P});
+  items.push_back({(void**)&h->sgl, sizeof(SeriesGlobal)});
+  items.push_back({(void**)&h->rec, sizeof(LmRecord) * P});
   items.push_back({(void**)&h->not_spd, sizeof(int32_t)});
   size_t total = 0;
   for (auto& it : items) total = align_up(total, 256) + it.bytes;
@@ -528,8 +611,8 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
 
   auto bail = [&](ba_status s) { ba_destroy(h); return s; };
   cudaError_t e;
-  if (d->cuda_stream) {
-    h->stream = (cudaStream_t)d->cuda_stream;
+  if (descs[0].cuda_stream) {
+    h->stream = (cudaStream_t)descs[0].cuda_stream;
   } else {
     e = cudaStreamCreate(&h->stream);
     if (e != cudaSuccess) return bail(fail_cuda(e, "cudaStreamCreate"));
@@ -548,8 +631,9 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
   }
   e = cudaMemset(h->arena, 0, total);
   if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMemset(arena)"));
-  if ((e = cudaMallocHost(&h->h_st, sizeof(SeriesState))) != cudaSuccess ||
-      (e = cudaMallocHost(&h->h_rec, sizeof(LmRecord))) != cudaSuccess ||
+  if ((e = cudaMallocHost(&h->h_st, sizeof(SeriesState) * P)) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_sgl, sizeof(SeriesGlobal))) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_rec, sizeof(LmRecord) * P)) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_gs, sizeof(GridSync))) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_flag, sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_scalar, sizeof(double) * 4)) != cudaSuccess)
@@ -557,13 +641,13 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
 
   // ---- upload (sorted / internal orders)
   std::vector<double> obs_s((size_t)no * 2), sw_s;
-  for (int o = 0; o < no; ++o) {
-    obs_s[2 * o] = obs[2 * S.obs_order[o]];
-    obs_s[2 * o + 1] = obs[2 * S.obs_order[o] + 1];
+  for (int k = 0; k < no; ++k) {
+    obs_s[2 * k] = obs[2 * S.obs_order[k]];
+    obs_s[2 * k + 1] = obs[2 * S.obs_order[k] + 1];
   }
   if (h->weighted) {
     sw_s.resize(no);
-    for (int o = 0; o < no; ++o) sw_s[o] = std::sqrt(w[S.obs_order[o]]);
+    for (int k = 0; k < no; ++k) sw_s[k] = std::sqrt(w[S.obs_order[k]]);
   }
   std::vector<double> lms_i((size_t)nl * 3);
   for (int i = 0; i < nl; ++i)
@@ -582,6 +666,11 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
       {d_cam_slot_ptr, S.cam_slot_ptr.data(), sizeof(int32_t) * (nc + 1)},
       {d_cam_slot_list, S.cam_slot_list.data(), sizeof(int32_t) * S.n_slots},
       {d_slot_row, S.slot_row.data(), sizeof(int32_t) * S.n_slots},
+      {d_cam_prob, S.cam_prob.data(), sizeof(int32_t) * nc},
+      {d_lm_prob, S.lm_prob.data(), sizeof(int32_t) * nl},
+      {d_tile_prob, tile_prob.data(), sizeof(int32_t) * S.n_tiles},
+      {d_cam_off, S.cam_off.data(), sizeof(int32_t) * (P + 1)},
+      {d_tile_off, S.tile_off.data(), sizeof(int32_t) * (P + 1)},
       {h->obs, obs_s.data(), sizeof(double) * 2 * no},
       {h->cams, cams.data(), sizeof(double) * nc * 9},
       {h->lms, lms_i.data(), sizeof(double) * nl * 3},
@@ -602,12 +691,18 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
     h->persist_grid = (coop && per_sm > 0) ? per_sm * sms : 0;
     cudaGetLastError();
   }
-  LmRecord r0{};
-  r0.cost = NAN;
-  r0.lambda = o.lambda0;
-  r0.nu = 2.0;
-  e = cudaMemcpy(h->rec, &r0, sizeof(r0), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMemcpy(record)"));
+  {
+    std::vector<LmRecord> r0(P);
+    for (auto& r : r0) {
+      r = LmRecord{};
+      r.cost = NAN;
+      r.lambda = o.lambda0;
+      r.nu = 2.0;
+      r.active = 1;
+    }
+    e = cudaMemcpy(h->rec, r0.data(), sizeof(LmRecord) * P, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMemcpy(record)"));
+  }
 
   Topology& tp = h->tp;
   tp.n_cams = nc;
@@ -628,8 +723,113 @@ ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle*
   tp.cam_slot_ptr = d_cam_slot_ptr;
   tp.cam_slot_list = d_cam_slot_list;
   tp.slot_row = d_slot_row;
+  tp.n_probs = n_probs;
+  tp.cam_prob = d_cam_prob;
+  tp.lm_prob = d_lm_prob;
+  tp.tile_prob = d_tile_prob;
+  tp.cam_off = d_cam_off;
+  tp.tile_off = d_tile_off;
   *out = h;
   g_last_error.clear();
+  return BA_OK;
+}
+
+// Largest number of series terms any problem of the last solve used.
+int max_terms(const ba_handle* h) {
+  int m = 0;
+  for (int p = 0; p < h->n_probs; ++p) m = h->h_st[p].m > m ? h->h_st[p].m : m;
+  return m;
+}
+
+void fill_series_info(const SeriesState& S, double lambda, ba_series_info* info) {
+  info->inner_iters = S.m;
+  info->stopped = S.stopped;
+  info->stop_value = S.stop_value;
+  info->x_norm = S.x_norm;
+  info->lambda = lambda;
+}
+
+void fill_step_info(const LmRecord& R, const SeriesState& S, ba_step_info* info) {
+  info->cost_before = R.cost_before;
+  info->cost_after = R.cost_trial;
+  info->lambda = R.lambda_used;
+  info->gain_ratio = R.gain_ratio;
+  info->model_decrease = R.model_decrease;
+  info->stop_value = S.stop_value;
+  info->accepted = R.accepted;
+  info->inner_iters = S.m;
+  info->converged = R.converged;
+  info->iteration = R.iteration - 1;
+}
+
+// One LM iteration of every problem of the handle whose record is active; batch: a problem that
+// converges becomes inactive.  Reads the records and series states back (one synchronisation).
+ba_status lm_iteration(ba_handle* h, bool batch) {
+  cudaStream_t s = h->stream;
+  const size_t P = (size_t)h->n_probs;
+  if (!h->cost_valid) {
+    seq_cost(h, rec_field(h->rec, offsetof(LmRecord, cost)), kRecStride);
+    h->cost_valid = true;
+  }
+  if (!h->linearized) {
+    seq_linearize(h);
+    h->linearized = true;
+  }
+  h->last_solve_lm = true;
+  ba_status st = run_solve(h, rec_field(h->rec, offsetof(LmRecord, lambda)), kRecStride, true);
+  if (st != BA_OK) return st;
+  tmark(h, kTEval, 0, 0);
+  launch_cam_prepare(h->cams, h->x, h->n_c, h->prep_trial, h->cams_trial, s);
+  launch_tile_cost(h->tp, h->prep_trial, h->lms, h->dx_l, h->obs, h->sqrt_w, h->tile_cost, s);
+  launch_lm_decide(h->tp, h->tile_cost, h->block_pred, h->rec, h->opts.func_tol, batch ? 1 : 0, s);
+  launch_apply_step(h->tp, h->rec, h->cams, h->cams_trial, h->lms, h->dx_l, s);
+  tmark(h, kTEval, 0, 1);
+  h->launches += 4;
+  st = check_launch(h, "LM step kernels");
+  if (st != BA_OK) return st;
+  CK(cudaMemcpyAsync(h->h_rec, h->rec, sizeof(LmRecord) * P, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SeriesState) * P, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->h_flag, h->not_spd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  collect_timing(h, max_terms(h), true);
+  if (h->last_exec == 2 && h->h_gs->error)
+    return fail(BA_ERR_TIMEOUT, "a grid barrier of the persistent series kernel timed out");
+  // one linearisation covers every problem: it is stale once any problem moved
+  for (size_t p = 0; p < P; ++p)
+    if (h->h_rec[p].accepted) h->linearized = false;
+  return BA_OK;
+}
+
+// Status of an LM iteration after its records were read: non-finite cost, then not-SPD.
+ba_status lm_status(ba_handle* h) {
+  for (int p = 0; p < h->n_probs; ++p)
+    if (!std::isfinite(h->h_rec[p].cost_before))
+      return fail(BA_ERR_NONFINITE, h->n_probs > 1 ? "problem " + std::to_string(p) +
+                                                         ": non-finite cost at the current state"
+                                                   : std::string("non-finite cost at the current state"));
+  if (*h->h_flag) return fail(BA_ERR_NOT_SPD, "a damped block is not positive definite");
+  return BA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ba_status ba_create(const ba_problem_desc* d, const ba_options* opts, ba_handle** out) {
+  return create_impl(d, 1, opts, out);
+}
+
+ba_status ba_create_batch(const ba_problem_desc* descs, int32_t n_problems, const ba_options* opts,
+                          ba_handle** out) {
+  return create_impl(descs, n_problems, opts, out);
+}
+
+ba_status ba_get_batch_layout(ba_handle* h, int32_t* n_problems, int32_t* cam_off, int32_t* lm_off) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  if (n_problems) *n_problems = h->n_probs;
+  if (cam_off) std::memcpy(cam_off, h->cam_off_h.data(), sizeof(int32_t) * (h->n_probs + 1));
+  if (lm_off) std::memcpy(lm_off, h->lm_off_h.data(), sizeof(int32_t) * (h->n_probs + 1));
   return BA_OK;
 }
 
@@ -665,77 +865,66 @@ ba_status ba_solve_schur_power(ba_handle* h, double lambda, ba_series_info* info
   if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(BA_ERR_INVALID_ARG, "lambda must be finite and > 0");
   launch_set_scalar(h->scalars + 0, lambda, h->stream);
   h->launches += 1;
-  ba_status st = run_solve(h, h->scalars + 0);
+  h->solve_lambda = lambda;
+  h->last_solve_lm = false;
+  ba_status st = run_solve(h, h->scalars + 0, 0, false);
   if (st != BA_OK) return st;
   if (!info) return BA_OK;
-  CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SeriesState), cudaMemcpyDeviceToHost, h->stream));
+  const size_t P = (size_t)h->n_probs;
+  CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SeriesState) * P, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(h->h_flag, h->not_spd, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  collect_timing(h, h->h_st->m, true);
+  collect_timing(h, max_terms(h), true);
   if (h->last_exec == 2 && h->h_gs->error)
     return fail(BA_ERR_TIMEOUT, "a grid barrier of the persistent series kernel timed out");
-  info->inner_iters = h->h_st->m;
-  info->stopped = h->h_st->stopped;
-  info->stop_value = h->h_st->stop_value;
-  info->x_norm = h->h_st->x_norm;
-  info->lambda = lambda;
+  if (P == 1) {
+    fill_series_info(h->h_st[0], lambda, info);
+  } else {
+    // a batch: the largest term count and stop value, stopped iff every problem stopped, and
+    // the norm of the whole camera step
+    ba_series_info a{};
+    a.stopped = 1;
+    a.stop_value = -INFINITY;
+    double x2 = 0.0;
+    for (size_t p = 0; p < P; ++p) {
+      const SeriesState& S = h->h_st[p];
+      a.inner_iters = S.m > a.inner_iters ? S.m : a.inner_iters;
+      a.stopped = a.stopped && S.stopped;
+      a.stop_value = S.stop_value > a.stop_value ? S.stop_value : a.stop_value;
+      x2 += S.x_norm * S.x_norm;
+    }
+    a.x_norm = std::sqrt(x2);
+    a.lambda = lambda;
+    *info = a;
+  }
   if (*h->h_flag) return fail(BA_ERR_NOT_SPD, "a damped block is not positive definite");
+  return BA_OK;
+}
+
+ba_status ba_get_series_state(ba_handle* h, ba_series_info* infos) {
+  if (!h || !infos) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  const size_t P = (size_t)h->n_probs;
+  CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SeriesState) * P, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->h_rec, h->rec, sizeof(LmRecord) * P, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (size_t p = 0; p < P; ++p)
+    fill_series_info(h->h_st[p], h->last_solve_lm ? h->h_rec[p].lambda_used : h->solve_lambda, &infos[p]);
   return BA_OK;
 }
 
 ba_status ba_lm_step(ba_handle* h, ba_step_info* info) {
   if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
-  cudaStream_t s = h->stream;
-  if (!h->cost_valid) {
-    seq_cost(h, rec_field(h->rec, offsetof(LmRecord, cost)));
-    h->cost_valid = true;
-  }
-  if (!h->linearized) {
-    seq_linearize(h);
-    h->linearized = true;
-  }
-  ba_status st = run_solve(h, rec_field(h->rec, offsetof(LmRecord, lambda)));
+  if (h->n_probs != 1) return fail(BA_ERR_INVALID_ARG, "a batch handle steps with ba_lm_step_batch");
+  ba_status st = lm_iteration(h, false);
   if (st != BA_OK) return st;
-  tmark(h, kTEval, 0, 0);
-  launch_cam_prepare(h->cams, h->x, h->n_c, h->prep_trial, h->cams_trial, s);
-  launch_cost(h->tp, h->prep_trial, h->lms, h->dx_l, h->obs, h->sqrt_w, h->block_cost, s);
-  launch_lm_decide(h->block_cost, cost_blocks(h->tp), h->block_pred, h->tp.n_tiles, h->rec, h->st,
-                   h->opts.func_tol, s);
-  launch_apply_step(h->rec, h->cams, h->cams_trial, h->lms, h->dx_l, h->n_c, h->n_l, s);
-  tmark(h, kTEval, 0, 1);
-  h->launches += 4;
-  st = check_launch(h, "LM step kernels");
-  if (st != BA_OK) return st;
-  CK(cudaMemcpyAsync(h->h_rec, h->rec, sizeof(LmRecord), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SeriesState), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(h->h_flag, h->not_spd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  collect_timing(h, h->h_st->m, true);
-  if (h->last_exec == 2 && h->h_gs->error)
-    return fail(BA_ERR_TIMEOUT, "a grid barrier of the persistent series kernel timed out");
-  const LmRecord& R = *h->h_rec;
-  if (R.accepted) h->linearized = false;
-  if (info) {
-    info->cost_before = R.cost_before;
-    info->cost_after = R.cost_trial;
-    info->lambda = R.lambda_used;
-    info->gain_ratio = R.gain_ratio;
-    info->model_decrease = R.model_decrease;
-    info->stop_value = h->h_st->stop_value;
-    info->accepted = R.accepted;
-    info->inner_iters = h->h_st->m;
-    info->converged = R.converged;
-    info->iteration = R.iteration - 1;
-  }
-  if (!std::isfinite(R.cost_before)) return fail(BA_ERR_NONFINITE, "non-finite cost at the current state");
-  if (*h->h_flag) return fail(BA_ERR_NOT_SPD, "a damped block is not positive definite");
-  return BA_OK;
+  if (info) fill_step_info(h->h_rec[0], h->h_st[0], info);
+  return lm_status(h);
 }
 
 ba_status ba_lm_solve(ba_handle* h, ba_step_info* trace, int32_t* n_steps) {
   if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  if (h->n_probs != 1) return fail(BA_ERR_INVALID_ARG, "a batch handle solves with ba_lm_solve_batch");
   int n = 0;
   ba_status st = BA_OK;
   for (int it = 0; it < h->opts.max_lm; ++it) {
@@ -749,14 +938,54 @@ ba_status ba_lm_solve(ba_handle* h, ba_step_info* trace, int32_t* n_steps) {
   return st;
 }
 
+ba_status ba_lm_step_batch(ba_handle* h, ba_step_info* infos, int32_t* n_active) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  ba_status st = lm_iteration(h, true);
+  if (st != BA_OK) return st;
+  int active = 0;
+  for (int p = 0; p < h->n_probs; ++p) {
+    if (infos) fill_step_info(h->h_rec[p], h->h_st[p], &infos[p]);
+    active += h->h_rec[p].active ? 1 : 0;
+  }
+  if (n_active) *n_active = active;
+  return lm_status(h);
+}
+
+ba_status ba_lm_solve_batch(ba_handle* h, ba_step_info* infos, int32_t* n_steps) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  int n = 0;
+  ba_status st = BA_OK;
+  for (int it = 0; it < h->opts.max_lm; ++it) {
+    int32_t active = 0;
+    st = ba_lm_step_batch(h, infos, &active);
+    ++n;
+    if (st != BA_OK || active == 0) break;
+  }
+  if (n_steps) *n_steps = n;
+  return st;
+}
+
 ba_status ba_cost(ba_handle* h, double* cost_out) {
   if (!h || !cost_out) return fail(BA_ERR_INVALID_ARG, "NULL argument");
-  seq_cost(h, h->scalars + 1);
+  launch_cam_prepare(h->cams, nullptr, h->n_c, h->prep, nullptr, h->stream);
+  launch_tile_cost(h->tp, h->prep, h->lms, nullptr, h->obs, h->sqrt_w, h->tile_cost, h->stream);
+  launch_reduce_sum(h->tile_cost, h->tp.n_tiles, h->scalars + 1, 0.5, h->stream);
+  h->launches += 3;
   ba_status st = check_launch(h, "cost kernels");
   if (st != BA_OK) return st;
   CK(cudaMemcpyAsync(h->h_scalar, h->scalars + 1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   *cost_out = h->h_scalar[0];
+  return BA_OK;
+}
+
+ba_status ba_cost_batch(ba_handle* h, double* costs) {
+  if (!h || !costs) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  seq_cost(h, h->prob_cost, 1);
+  ba_status st = check_launch(h, "cost kernels");
+  if (st != BA_OK) return st;
+  CK(cudaMemcpyAsync(costs, h->prob_cost, sizeof(double) * h->n_probs, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   return BA_OK;
 }
 
@@ -897,6 +1126,8 @@ ba_status ba_get_blocks(ba_handle* h, double* U, double* V, double* b_p, double*
 
 ba_status ba_get_lm_state(ba_handle* h, double* lambda, double* nu, int32_t* iteration, double* cost) {
   if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  if (h->n_probs != 1)
+    return fail(BA_ERR_INVALID_ARG, "a batch handle reports its LM state per problem (ba_lm_step_batch)");
   CK(cudaMemcpyAsync(h->h_rec, h->rec, sizeof(LmRecord), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (lambda) *lambda = h->h_rec->lambda;
@@ -910,14 +1141,18 @@ ba_status ba_set_lm_state(ba_handle* h, double lambda, double nu, int32_t iterat
   if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
   if (!(lambda > 0.0) || !std::isfinite(lambda) || !(nu >= 1.0) || !std::isfinite(nu) || iteration < 0)
     return fail(BA_ERR_INVALID_ARG, "need lambda > 0, nu >= 1, iteration >= 0");
-  CK(cudaMemcpyAsync(h->h_rec, h->rec, sizeof(LmRecord), cudaMemcpyDeviceToHost, h->stream));
+  const size_t P = (size_t)h->n_probs;
+  CK(cudaMemcpyAsync(h->h_rec, h->rec, sizeof(LmRecord) * P, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  LmRecord r = *h->h_rec;
-  r.lambda = lambda;
-  r.nu = nu;
-  r.iteration = iteration;
-  *h->h_rec = r;
-  CK(cudaMemcpyAsync(h->rec, h->h_rec, sizeof(LmRecord), cudaMemcpyHostToDevice, h->stream));
+  for (size_t p = 0; p < P; ++p) {
+    LmRecord& r = h->h_rec[p];
+    r.lambda = lambda;
+    r.nu = nu;
+    r.iteration = iteration;
+    r.converged = 0;
+    r.active = 1;
+  }
+  CK(cudaMemcpyAsync(h->rec, h->h_rec, sizeof(LmRecord) * P, cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return BA_OK;
 }
@@ -925,8 +1160,8 @@ ba_status ba_set_lm_state(ba_handle* h, double lambda, double nu, int32_t iterat
 ba_status ba_get_series_trace(ba_handle* h, int64_t* ns, int32_t capacity, int32_t* n_terms) {
   if (!h || !ns || capacity < 0) return fail(BA_ERR_INVALID_ARG, "bad argument");
   CK(cudaStreamSynchronize(h->stream));
-  CK(cudaMemcpy(h->h_st, h->st, sizeof(SeriesState), cudaMemcpyDeviceToHost));
-  int terms = h->last_exec == 2 ? h->h_st->m : 0;
+  CK(cudaMemcpy(h->h_st, h->st, sizeof(SeriesState) * h->n_probs, cudaMemcpyDeviceToHost));
+  int terms = h->last_exec == 2 ? max_terms(h) : 0;
   if (terms > kTraceTerms) terms = kTraceTerms;
   const int n = terms * kTracePoints < capacity ? terms * kTracePoints : capacity;
   if (n > 0) CK(cudaMemcpy(ns, h->trace, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));

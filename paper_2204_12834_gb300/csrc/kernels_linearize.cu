@@ -335,9 +335,9 @@ constexpr int kDampThreads = kCamBlock * 9;
 
 __global__ void __launch_bounds__(kDampThreads) damp_invert_kernel(
     Topology tp, const double* __restrict__ U45, const double* __restrict__ V,
-    const double* __restrict__ lambda, int mode, int cam_blocks, double* __restrict__ Uinv,
-    double* __restrict__ Vinv, float* __restrict__ Vinv_f, int32_t* __restrict__ not_spd) {
-  const double lam = *lambda;
+    const double* __restrict__ lambda, int lam_stride, int mode, int cam_blocks,
+    double* __restrict__ Uinv, double* __restrict__ Vinv, float* __restrict__ Vinv_f,
+    int32_t* __restrict__ not_spd) {
   const int tid = threadIdx.x;
   if ((int)blockIdx.x < cam_blocks) {
     __shared__ double A[kCamBlock][9][10];
@@ -346,6 +346,7 @@ __global__ void __launch_bounds__(kDampThreads) damp_invert_kernel(
     const int c = blockIdx.x * kCamBlock + cl;
     const bool ok_cam = c < tp.n_cams;
     if (ok_cam) {
+      const double lam = lambda[(size_t)tp.cam_prob[c] * lam_stride];
 #pragma unroll
       for (int j = 0; j < 9; ++j) {
         const int i0 = k < j ? k : j, j0 = k < j ? j : k;
@@ -404,6 +405,7 @@ __global__ void __launch_bounds__(kDampThreads) damp_invert_kernel(
   } else {
     const int l = (blockIdx.x - cam_blocks) * blockDim.x + tid;
     if (l >= tp.n_lms) return;
+    const double lam = lambda[(size_t)tp.lm_prob[l] * lam_stride];
     const double* v = V + (size_t)l * 6;
     const double a00 = v[0] + damp_diag(v[0], lam, mode), a01 = v[1], a02 = v[2];
     const double a11 = v[3] + damp_diag(v[3], lam, mode), a12 = v[4];
@@ -443,30 +445,27 @@ __global__ void __launch_bounds__(kDampThreads) damp_invert_kernel(
 }
 
 void launch_damp_invert(const Topology& tp, const double* U45, const double* V,
-                        const double* lambda, int damping_mode, double* Uinv, double* Vinv,
-                        float* Vinv_f, int32_t* not_spd, cudaStream_t s) {
+                        const double* lambda, int lam_stride, int damping_mode, double* Uinv,
+                        double* Vinv, float* Vinv_f, int32_t* not_spd, cudaStream_t s) {
   const int cb = (tp.n_cams + kCamBlock - 1) / kCamBlock;
   const int lb = (tp.n_lms + kDampThreads - 1) / kDampThreads;
-  damp_invert_kernel<<<cb + lb, kDampThreads, 0, s>>>(tp, U45, V, lambda, damping_mode, cb, Uinv,
-                                                     Vinv, Vinv_f, not_spd);
+  damp_invert_kernel<<<cb + lb, kDampThreads, 0, s>>>(tp, U45, V, lambda, lam_stride, damping_mode,
+                                                     cb, Uinv, Vinv, Vinv_f, not_spd);
 }
 
 // ---------------------------------------------------------------------------------------
-// Cost in float64 at (cameras prepared in `prep`, landmarks lms + dx_l).
-constexpr int kCostThreads = 256;
-
-int cost_blocks(const Topology& tp) {
-  int b = (tp.n_obs + kCostThreads - 1) / kCostThreads;
-  return b < 1 ? 1 : (b > 2048 ? 2048 : b);
-}
-
-__global__ void __launch_bounds__(kCostThreads) cost_kernel(
+// Cost in float64 at (cameras prepared in `prep`, landmarks lms + dx_l): one block per tile,
+// tile_cost[t] = sum over the tile's observations of w ||r||^2 (fixed order).
+__global__ void __launch_bounds__(kTileObs) tile_cost_kernel(
     Topology tp, const double* __restrict__ prep, const double* __restrict__ lms,
     const double* __restrict__ dx_l, const double2* __restrict__ obs,
-    const double* __restrict__ sqrt_w, double* __restrict__ block_sums) {
-  __shared__ double sred[kCostThreads / 32];
-  double acc = 0.0;
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < tp.n_obs; o += gridDim.x * blockDim.x) {
+    const double* __restrict__ sqrt_w, double* __restrict__ tile_cost) {
+  __shared__ double sred[kTileObs / 32];
+  const int4 d = tp.tile_desc[2 * blockIdx.x];
+  const int o0 = d.z, n = d.w;
+  double e = 0.0;
+  if ((int)threadIdx.x < n) {
+    const int o = o0 + threadIdx.x;
     const int c = tp.cam_of[o], l = tp.lm_of[o];
     const double* q = prep + (size_t)c * kCamPrep;
     double X0 = lms[l * 3 + 0], X1 = lms[l * 3 + 1], X2 = lms[l * 3 + 2];
@@ -484,17 +483,17 @@ __global__ void __launch_bounds__(kCostThreads) cost_kernel(
     const double rad = 1.0 + n2 * (q[22] + q[23] * n2);
     const double2 ob = obs[o];
     const double r0 = q[21] * rad * px - ob.x, r1 = q[21] * rad * py - ob.y;
-    double e = r0 * r0 + r1 * r1;
+    e = r0 * r0 + r1 * r1;
     if (sqrt_w) e *= sqrt_w[o] * sqrt_w[o];
-    acc += e;
   }
-  const double tot = block_sum_fixed(acc, sred);
-  if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+  const double tot = block_sum_fixed(e, sred);
+  if (threadIdx.x == 0) tile_cost[blockIdx.x] = tot;
 }
 
-void launch_cost(const Topology& tp, const double* prep, const double* lms, const double* dx_l,
-                 const double2* obs, const double* sqrt_w, double* block_sums, cudaStream_t s) {
-  cost_kernel<<<cost_blocks(tp), kCostThreads, 0, s>>>(tp, prep, lms, dx_l, obs, sqrt_w, block_sums);
+void launch_tile_cost(const Topology& tp, const double* prep, const double* lms,
+                      const double* dx_l, const double2* obs, const double* sqrt_w,
+                      double* tile_cost, cudaStream_t s) {
+  tile_cost_kernel<<<tp.n_tiles, kTileObs, 0, s>>>(tp, prep, lms, dx_l, obs, sqrt_w, tile_cost);
 }
 
 }  // namespace poba

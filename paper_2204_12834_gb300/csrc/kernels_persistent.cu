@@ -5,12 +5,13 @@
 // Each term is two phases separated by grid barriers:
 //   phase A  every block pulls tiles from a shared counter and runs the tile body (W^T t,
 //            V^-1, W z) -- dynamic scheduling, so no wave tail;
-//   phase B  camera groups (blockDim / 9 cameras each, static round-robin) run the camera body
-//            (U^-1, x accumulation, new term rows) and store per-group squared norms;
-//   barrier  the last block to arrive opens it at once, then sums the group norms in group
-//            order and applies the stop rule; the other blocks see the decision before their
-//            next tile fetch and, at the latest, at the next barrier (a stop skips the camera
-//            phase, so x stays at the term where the rule fired).
+//   phase B  camera groups (spread over all blocks, static) run the camera body (U^-1, x
+//            accumulation, new term rows) and store a squared-norm pair per camera;
+//   barrier  the last block to arrive opens it at once, then sums each running problem's
+//            camera norm pairs in camera order and applies its stop rule; the other blocks see
+//            the decisions before their next tile fetch and, at the latest, at the next
+//            barrier (a stopped problem's tiles and cameras are skipped, so its x stays at the
+//            term where its rule fired).
 // Results are bitwise equal to the per-term launches: every tile and camera computes the same
 // sums in the same order whichever block runs it.
 //
@@ -24,10 +25,6 @@
 
 namespace poba {
 
-__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
-  return *(const volatile unsigned*)p;
-}
-__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
 
 __device__ __forceinline__ long long global_ns() {
   unsigned long long t;
@@ -88,16 +85,14 @@ __device__ __forceinline__ bool barrier_wait(GridSync* gs, unsigned gen, long lo
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTileObs, sizeof(T) == 8 ? 3 : 3) series_persistent_kernel(
+__global__ void __launch_bounds__(kTileObs, 3) series_persistent_kernel(
     Topology tp, const T* __restrict__ J, const T* __restrict__ Vinv,
-    const double* __restrict__ b_l, const double* __restrict__ b_p,
     const double* __restrict__ Uinv, double* __restrict__ x, T* __restrict__ t_cm,
-    T* __restrict__ partial, double* __restrict__ group_norms, SeriesState* __restrict__ st,
-    GridSync* __restrict__ gs, int m_max, double eps, long long timeout,
-    long long* __restrict__ trace) {
+    T* __restrict__ partial, double* __restrict__ cam_norm, SeriesState* __restrict__ st,
+    SeriesGlobal* __restrict__ sgl, GridSync* __restrict__ gs, int m_max, double eps,
+    long long timeout, long long* __restrict__ trace) {
   __shared__ TileSmem<T> sm;
-  __shared__ double sred[kTileObs / 32];
-  __shared__ int s_tile, s_last, s_ok, s_done;
+  __shared__ int s_tile, s_last, s_ok, s_done, s_running;
   __shared__ unsigned s_gen;
   const int tid = threadIdx.x;
   const unsigned G = gridDim.x;
@@ -108,43 +103,50 @@ __global__ void __launch_bounds__(kTileObs, sizeof(T) == 8 ? 3 : 3) series_persi
   per_group = per_group < 1 ? 1 : (per_group > cap ? cap : per_group);
   const int n_groups = (tp.n_cams + per_group - 1) / per_group;
   double (*ys)[9] = reinterpret_cast<double (*)[9]>(&sm.sg[0][0]);  // phase B reuses sg
+  double (*y2)[9] = ys + cap;
 
-  if (tid == 0) s_done = ld_volatile(&st->done);  // x(0) = 0 stops before the first term
+  if (tid == 0) s_done = ld_volatile(&sgl->all_done);  // every x(0) = 0: nothing to do
   __syncthreads();
   if (s_done) return;
   // the block's first camera group is fixed for the whole launch: keep its slot-row range and
   // its components of x in registers (x is written back once at the end)
   const int c_cl = tid / 9, ck = tid - c_cl * 9;
   const int c0 = blockIdx.x * per_group + c_cl;
-  const bool c_ok = (int)blockIdx.x < n_groups && c_cl < per_group && c0 < tp.n_cams;
-  int c_r0 = 0, c_r1 = 0;
+  const bool c_mine = (int)blockIdx.x < n_groups && c_cl < per_group && c0 < tp.n_cams;
+  int c_r0 = 0, c_r1 = 0, c_prob = 0;
   double x_reg = 0.0;
-  if (c_ok) {
+  if (c_mine) {
     c_r0 = tp.cam_slot_ptr[c0];
     c_r1 = tp.cam_slot_ptr[c0 + 1];
+    c_prob = tp.cam_prob[c0];
     x_reg = x[(size_t)c0 * 9 + ck];
   }
   const bool tracer = blockIdx.x == 0 && tid == 0 && trace != nullptr;
   for (int i = 1; i <= m_max; ++i) {
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 0] = global_ns();
     // ---- phase A: tiles (the next tile index is fetched while the current one is processed;
-    // a stop decided for the previous term makes the remaining tiles of this one moot)
+    // once every problem has stopped the remaining tiles are moot; tiles of a problem that
+    // stopped are skipped)
     int next = 0;
-    if (tid == 0) next = ld_volatile(&st->done) ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
+    if (tid == 0)
+      next = ld_volatile(&sgl->all_done) ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
     for (;;) {
       if (tid == 0) {
-        s_tile = next;
-        if (next < tp.n_tiles)
-          next = ld_volatile(&st->done) ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
+        int cur = next;
+        while (cur < tp.n_tiles && ld_volatile(&st[tp.tile_prob[cur]].done))
+          cur = ld_volatile(&sgl->all_done) ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
+        s_tile = cur;
+        if (cur < tp.n_tiles)
+          next = ld_volatile(&sgl->all_done) ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
       }
       __syncthreads();
       const int tile = s_tile;
       __syncthreads();
       if (tile >= tp.n_tiles) break;
       if constexpr (sizeof(T) == 4)
-        tile_matvec_body_f32<kModeSeries>(tp, tile, J, t_cm, b_l, Vinv, partial, sm);
+        tile_matvec_body_f32<kModeSeries>(tp, tile, J, t_cm, nullptr, Vinv, partial, sm);
       else
-        tile_matvec_body<T, kModeSeries>(tp, tile, J, t_cm, b_l, Vinv, partial, sm);
+        tile_matvec_body<T, kModeSeries>(tp, tile, J, t_cm, nullptr, Vinv, partial, sm);
     }
     unsigned gen;
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 1] = global_ns();
@@ -157,76 +159,73 @@ __global__ void __launch_bounds__(kTileObs, sizeof(T) == 8 ? 3 : 3) series_persi
       return;
     }
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 2] = global_ns();
-    if (tid == 0) s_done = ld_volatile(&st->done);
+    if (tid == 0) s_done = ld_volatile(&sgl->all_done);
     __syncthreads();
-    if (s_done) break;  // the rule fired at term i - 1: x stays x(i - 1)
+    if (s_done) break;  // every problem's rule fired at term i - 1 or earlier
     // ---- phase B: cameras (the block's first group uses the cached rows and x)
     for (int g = blockIdx.x; g < n_groups; g += G) {
-      double v, xv;
       if (g == (int)blockIdx.x) {
+        const bool run = c_mine && !ld_volatile(&st[c_prob].done);
         double ui[9];
-        if (c_ok) {
+        if (run) {
 #pragma unroll
           for (int j = 0; j < 9; ++j) ui[j] = Uinv[(size_t)c0 * 81 + ck * 9 + j];
         }
         double y = 0.0;
-        for (int rb = c_r0; rb < c_r1; rb += 8) {
-          T buf[8];
+        if (run) {
+          for (int rb = c_r0; rb < c_r1; rb += 8) {
+            T buf[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) buf[j] = (rb + j < c_r1) ? __ldcg(partial + (size_t)(rb + j) * 9 + ck) : (T)0;
+            for (int j = 0; j < 8; ++j) buf[j] = (rb + j < c_r1) ? __ldcg(partial + (size_t)(rb + j) * 9 + ck) : (T)0;
 #pragma unroll
-          for (int j = 0; j < 8; ++j) y += (double)buf[j];
+            for (int j = 0; j < 8; ++j) y += (double)buf[j];
+          }
         }
         if (c_cl < per_group) ys[c_cl][ck] = y;
         __syncthreads();
-        v = 0.0;
-        xv = 0.0;
-        if (c_ok) {
+        double v = 0.0;
+        if (run) {
 #pragma unroll
           for (int j = 0; j < 9; ++j) v += ui[j] * ys[c_cl][j];
           x_reg += v;
-          xv = x_reg;
           const T tv = (T)v;
           for (int q = c_r0; q < c_r1; ++q) t_cm[(size_t)q * 9 + ck] = tv;
         }
+        __syncthreads();
+        if (c_cl < per_group) {
+          ys[c_cl][ck] = v * v;
+          y2[c_cl][ck] = x_reg * x_reg;
+        }
+        __syncthreads();
+        if (run && ck == 0) {
+          double a = 0.0, b = 0.0;
+#pragma unroll
+          for (int j = 0; j < 9; ++j) {
+            a += ys[c_cl][j];
+            b += y2[c_cl][j];
+          }
+          cam_norm[2 * c0 + 0] = a;
+          cam_norm[2 * c0 + 1] = b;
+        }
+        __syncthreads();
       } else {
-        camera_body<T, kModeSeries>(tp, g * per_group, per_group, partial, b_p, Uinv, x, t_cm,
-                                    ys, v, xv);
+        camera_body<T, kModeSeries>(tp, g * per_group, per_group, partial, nullptr, Uinv, x, t_cm,
+                                    st, cam_norm, ys, y2);
       }
-      const double bt = block_sum_fixed(v * v, sred);
-      __syncthreads();
-      const double bx = block_sum_fixed(xv * xv, sred);
-      if (tid == 0) {
-        group_norms[2 * g + 0] = bt;
-        group_norms[2 * g + 1] = bx;
-      }
-      __syncthreads();
     }
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 3] = global_ns();
     if (barrier_arrive(gs, G, &gen, &s_last, &s_gen)) {
-      // last block: open the barrier, then the norms in group order and the stop rule for
-      // term i (visible to every block before the next barrier)
+      // last block: open the barrier, then every running problem's norms (camera order) and its
+      // stop rule for term i (visible to every block before the next barrier)
       if (tid == 0) barrier_release(gs);
       __threadfence();
-      double at = 0.0, ax = 0.0;
-      for (int g = tid; g < n_groups; g += blockDim.x) {
-        at += __ldcg(group_norms + 2 * g + 0);
-        ax += __ldcg(group_norms + 2 * g + 1);
-      }
-      const double T2 = block_sum_fixed(at, sred);
-      __syncthreads();
-      const double X2 = block_sum_fixed(ax, sred);
-      if (tid == 0) {
-        series_stop_rule(st, i, T2, X2, eps);
-        __threadfence();
-      }
-      __syncthreads();
+      problems_stop_rule(tp, cam_norm, st, sgl, i, eps, &s_running);
     } else if (!barrier_wait(gs, gen, timeout, &s_ok)) {
       return;
     }
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 4] = global_ns();
   }
-  if (c_ok) x[(size_t)c0 * 9 + ck] = x_reg;
+  if (c_mine) x[(size_t)c0 * 9 + ck] = x_reg;
 }
 
 int persistent_blocks_per_sm(bool f32) {
@@ -240,18 +239,18 @@ int persistent_blocks_per_sm(bool f32) {
 
 template <typename T>
 cudaError_t launch_series_persistent(const Topology& tp, int grid, const T* J, const T* Vinv,
-                                     const double* b_l, const double* b_p, const double* Uinv,
-                                     double* x, T* t_cm, T* partial, double* group_norms,
-                                     SeriesState* st, GridSync* gs, int m_max, double eps,
-                                     long long timeout, long long* trace, cudaStream_t s) {
-  void* args[] = {(void*)&tp, (void*)&J, (void*)&Vinv, (void*)&b_l, (void*)&b_p, (void*)&Uinv,
-                  (void*)&x, (void*)&t_cm, (void*)&partial, (void*)&group_norms, (void*)&st,
-                  (void*)&gs, (void*)&m_max, (void*)&eps, (void*)&timeout, (void*)&trace};
+                                     const double* Uinv, double* x, T* t_cm, T* partial,
+                                     double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
+                                     GridSync* gs, int m_max, double eps, long long timeout,
+                                     long long* trace, cudaStream_t s) {
+  void* args[] = {(void*)&tp, (void*)&J, (void*)&Vinv, (void*)&Uinv, (void*)&x, (void*)&t_cm,
+                  (void*)&partial, (void*)&cam_norm, (void*)&st, (void*)&sgl, (void*)&gs,
+                  (void*)&m_max, (void*)&eps, (void*)&timeout, (void*)&trace};
   return cudaLaunchCooperativeKernel((const void*)series_persistent_kernel<T>, dim3(grid),
                                      dim3(kTileObs), args, 0, s);
 }
 
-template cudaError_t launch_series_persistent<double>(const Topology&, int, const double*, const double*, const double*, const double*, const double*, double*, double*, double*, double*, SeriesState*, GridSync*, int, double, long long, long long*, cudaStream_t);
-template cudaError_t launch_series_persistent<float>(const Topology&, int, const float*, const float*, const double*, const double*, const double*, double*, float*, float*, double*, SeriesState*, GridSync*, int, double, long long, long long*, cudaStream_t);
+template cudaError_t launch_series_persistent<double>(const Topology&, int, const double*, const double*, const double*, double*, double*, double*, double*, SeriesState*, SeriesGlobal*, GridSync*, int, double, long long, long long*, cudaStream_t);
+template cudaError_t launch_series_persistent<float>(const Topology&, int, const float*, const float*, const double*, double*, float*, float*, double*, SeriesState*, SeriesGlobal*, GridSync*, int, double, long long, long long*, cudaStream_t);
 
 }  // namespace poba

@@ -20,9 +20,11 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kTileObs) tile_matvec_kernel(
     Topology tp, const T* __restrict__ J, const T* __restrict__ t_cm,
     const double* __restrict__ b_l, const T* __restrict__ Vinv, T* __restrict__ partial,
-    const SeriesState* __restrict__ st) {
+    const SeriesState* __restrict__ st, const SeriesGlobal* __restrict__ sgl) {
   __shared__ TileSmem<T> sm;
-  if (MODE == kModeSeries && st->done) return;  // the stop rule fired in an earlier term
+  // every problem stopped, or this tile's problem stopped in an earlier term (uniform per block)
+  if (MODE == kModeSeries && sgl->all_done) return;
+  if (st[tp.tile_prob[blockIdx.x]].done) return;
   if constexpr (sizeof(T) == 4)
     tile_matvec_body_f32<MODE>(tp, blockIdx.x, J, t_cm, b_l, Vinv, partial, sm);
   else
@@ -33,14 +35,15 @@ template <typename T>
 void launch_tile_rhs(const Topology& tp, const T* J, const double* b_l, const T* Vinv, T* partial,
                      const SeriesState* st, cudaStream_t s) {
   tile_matvec_kernel<T, kModeRhs><<<tp.n_tiles, kTileObs, 0, s>>>(tp, J, nullptr, b_l, Vinv,
-                                                                  partial, st);
+                                                                  partial, st, nullptr);
 }
 
 template <typename T>
 void launch_tile_series(const Topology& tp, const T* J, const T* t_cm, const T* Vinv,
-                        T* partial, const SeriesState* st, cudaStream_t s) {
+                        T* partial, const SeriesState* st, const SeriesGlobal* sgl,
+                        cudaStream_t s) {
   tile_matvec_kernel<T, kModeSeries><<<tp.n_tiles, kTileObs, 0, s>>>(tp, J, t_cm, nullptr, Vinv,
-                                                                     partial, st);
+                                                                     partial, st, sgl);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -126,92 +129,84 @@ void launch_tile_backsub(const Topology& tp, const T* J, const T* r, const doubl
 
 template void launch_tile_rhs<double>(const Topology&, const double*, const double*, const double*, double*, const SeriesState*, cudaStream_t);
 template void launch_tile_rhs<float>(const Topology&, const float*, const double*, const float*, float*, const SeriesState*, cudaStream_t);
-template void launch_tile_series<double>(const Topology&, const double*, const double*, const double*, double*, const SeriesState*, cudaStream_t);
-template void launch_tile_series<float>(const Topology&, const float*, const float*, const float*, float*, const SeriesState*, cudaStream_t);
+template void launch_tile_series<double>(const Topology&, const double*, const double*, const double*, double*, const SeriesState*, const SeriesGlobal*, cudaStream_t);
+template void launch_tile_series<float>(const Topology&, const float*, const float*, const float*, float*, const SeriesState*, const SeriesGlobal*, cudaStream_t);
 template void launch_tile_backsub<double>(const Topology&, const double*, const double*, const double*, const double*, const double*, double*, double*, cudaStream_t);
 template void launch_tile_backsub<float>(const Topology&, const float*, const float*, const double*, const double*, const float*, double*, double*, cudaStream_t);
 
 int tile_blocks(const Topology& tp) { return tp.n_tiles; }
 
 // ---------------------------------------------------------------------------------------
-// Camera step: kCamBlock cameras x 9 components per block (camera body), block sums of the
-// squared norms, and the stop rule in the last block to finish (fixed-order sums).
+// Camera step: kCamBlock cameras x 9 components per block (camera body, norm pair per camera),
+// then the stop rule of every running problem in the last block to finish.
 int camera_blocks(const Topology& tp) { return (tp.n_cams + kCamBlock - 1) / kCamBlock; }
 
 template <typename PT, int MODE>
 __global__ void __launch_bounds__(kCamBlock * 9) camera_step_kernel(
     Topology tp, const PT* __restrict__ partial, const double* __restrict__ b_p,
     const double* __restrict__ Uinv, double* __restrict__ x, PT* __restrict__ t_cm,
-    double* __restrict__ block_norms, SeriesState* __restrict__ st, int iter, double eps) {
+    double* __restrict__ cam_norm, SeriesState* __restrict__ st, SeriesGlobal* __restrict__ sgl,
+    int iter, double eps) {
   __shared__ double ys[kCamBlock][9];
-  __shared__ double sred[(kCamBlock * 9 + 31) / 32];
-  __shared__ int is_last;
-  if (MODE == kModeSeries && st->done) return;
+  __shared__ double y2[kCamBlock][9];
+  __shared__ int is_last, s_running;
+  if (MODE == kModeSeries && sgl->all_done) return;
   const int tid = threadIdx.x;
-  double v, xv;
-  camera_body<PT, MODE>(tp, blockIdx.x * kCamBlock, kCamBlock, partial, b_p, Uinv, x, t_cm, ys,
-                        v, xv);
-  const double bt = block_sum_fixed(v * v, sred);
-  __syncthreads();
-  const double bx = block_sum_fixed(xv * xv, sred);
+  camera_body<PT, MODE>(tp, blockIdx.x * kCamBlock, kCamBlock, partial, b_p, Uinv, x, t_cm, st,
+                        cam_norm, ys, y2);
   if (tid == 0) {
-    block_norms[blockIdx.x * 2 + 0] = bt;
-    block_norms[blockIdx.x * 2 + 1] = bx;
     __threadfence();
-    const unsigned ticket = atomicAdd(&st->counter, 1u);
+    const unsigned ticket = atomicAdd(&sgl->counter, 1u);
     is_last = (ticket == gridDim.x - 1);
   }
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  // last block: fixed-order sum of all block norms (strided per thread, then the block tree)
-  double at = 0.0, ax = 0.0;
-  for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
-    at += __ldcg(block_norms + b * 2 + 0);
-    ax += __ldcg(block_norms + b * 2 + 1);
-  }
-  const double T2 = block_sum_fixed(at, sred);
-  __syncthreads();
-  const double X2 = block_sum_fixed(ax, sred);
-  if (tid == 0) {
-    series_stop_rule(st, iter, T2, X2, eps);
-    st->counter = 0u;
-  }
+  problems_stop_rule(tp, cam_norm, st, sgl, iter, eps, &s_running);
+  if (tid == 0) sgl->counter = 0u;
 }
 
 template <typename PT>
 void launch_camera_rhs(const Topology& tp, const PT* partial, const double* b_p, const double* Uinv,
-                       double* x, PT* t_cm, double* block_norms, SeriesState* st, cudaStream_t s) {
+                       double* x, PT* t_cm, double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
+                       cudaStream_t s) {
   camera_step_kernel<PT, kModeRhs><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(
-      tp, partial, b_p, Uinv, x, t_cm, block_norms, st, 0, 0.0);
+      tp, partial, b_p, Uinv, x, t_cm, cam_norm, st, sgl, 0, 0.0);
 }
 
 template <typename PT>
 void launch_camera_series(const Topology& tp, const PT* partial, const double* Uinv, double* x,
-                          PT* t_cm, double* block_norms, SeriesState* st, int iter, double eps,
-                          cudaStream_t s) {
+                          PT* t_cm, double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
+                          int iter, double eps, cudaStream_t s) {
   camera_step_kernel<PT, kModeSeries><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(
-      tp, partial, nullptr, Uinv, x, t_cm, block_norms, st, iter, eps);
+      tp, partial, nullptr, Uinv, x, t_cm, cam_norm, st, sgl, iter, eps);
 }
 
-template void launch_camera_rhs<double>(const Topology&, const double*, const double*, const double*, double*, double*, double*, SeriesState*, cudaStream_t);
-template void launch_camera_rhs<float>(const Topology&, const float*, const double*, const double*, double*, float*, double*, SeriesState*, cudaStream_t);
-template void launch_camera_series<double>(const Topology&, const double*, const double*, double*, double*, double*, SeriesState*, int, double, cudaStream_t);
-template void launch_camera_series<float>(const Topology&, const float*, const double*, double*, float*, double*, SeriesState*, int, double, cudaStream_t);
+template void launch_camera_rhs<double>(const Topology&, const double*, const double*, const double*, double*, double*, double*, SeriesState*, SeriesGlobal*, cudaStream_t);
+template void launch_camera_rhs<float>(const Topology&, const float*, const double*, const double*, double*, float*, double*, SeriesState*, SeriesGlobal*, cudaStream_t);
+template void launch_camera_series<double>(const Topology&, const double*, const double*, double*, double*, double*, SeriesState*, SeriesGlobal*, int, double, cudaStream_t);
+template void launch_camera_series<float>(const Topology&, const float*, const double*, double*, float*, double*, SeriesState*, SeriesGlobal*, int, double, cudaStream_t);
 
 // ---------------------------------------------------------------------------------------
-__global__ void series_reset_kernel(SeriesState* st) {
-  st->done = 0;
-  st->m = 0;
-  st->stopped = 0;
-  st->stop_value = INFINITY;
-  st->x_norm = 0.0;
-  st->t_norm = 0.0;
-  st->counter = 0u;
+__global__ void series_reset_kernel(SeriesState* st, SeriesGlobal* sgl, const LmRecord* rec,
+                                    int n_probs) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p == 0) {
+    sgl->all_done = 0;
+    sgl->counter = 0u;
+  }
+  if (p >= n_probs) return;
+  st[p].done = (rec && !rec[p].active) ? 1 : 0;
+  st[p].m = 0;
+  st[p].stopped = 0;
+  st[p].stop_value = INFINITY;
+  st[p].x_norm = 0.0;
+  st[p].t_norm = 0.0;
 }
 
-void launch_series_reset(SeriesState* st, cudaStream_t s) {
-  series_reset_kernel<<<1, 1, 0, s>>>(st);
+void launch_series_reset(SeriesState* st, SeriesGlobal* sgl, const LmRecord* rec, int n_probs,
+                         cudaStream_t s) {
+  series_reset_kernel<<<(n_probs + 127) / 128, 128, 0, s>>>(st, sgl, rec, n_probs);
 }
 
 __global__ void set_scalar_kernel(double* dst, double v) { *dst = v; }
@@ -232,22 +227,49 @@ void launch_reduce_sum(const double* in, int n, double* out, double scale, cudaS
   reduce_sum_kernel<<<1, kReduceThreads, 0, s>>>(in, n, out, scale);
 }
 
+// One block per problem: scale * (sum of the problem's tile values), fixed order.
+__global__ void __launch_bounds__(kReduceThreads) reduce_tiles_kernel(Topology tp,
+                                                                       const double* tile_vals,
+                                                                       double* out, int out_stride,
+                                                                       double scale) {
+  __shared__ double sred[kReduceThreads / 32];
+  const int p = blockIdx.x;
+  double a = 0.0;
+  for (int t = tp.tile_off[p] + threadIdx.x; t < tp.tile_off[p + 1]; t += blockDim.x) a += tile_vals[t];
+  const double tot = block_sum_fixed(a, sred);
+  if (threadIdx.x == 0) out[(size_t)p * out_stride] = scale * tot;
+}
+
+void launch_reduce_tiles(const Topology& tp, const double* tile_vals, double* out, int out_stride,
+                         double scale, cudaStream_t s) {
+  reduce_tiles_kernel<<<tp.n_probs, kReduceThreads, 0, s>>>(tp, tile_vals, out, out_stride, scale);
+}
+
 // ---------------------------------------------------------------------------------------
-// LM decision (Sec. 5.1): F(x + dx) and the model decrease from block sums, gain ratio,
-// accept iff F decreased and the model decrease is positive, lambda / nu update.
+// LM decision (Sec. 5.1), one block per problem: F(x + dx) and the model decrease from the
+// problem's tile sums, gain ratio, accept iff F decreased and the model decrease is positive,
+// lambda / nu update.
 constexpr double kLambdaMin = 1e-10, kLambdaMax = 1e32;
 
 __global__ void __launch_bounds__(kReduceThreads) lm_decide_kernel(
-    const double* block_cost, int n_cost, const double* block_pred, int n_pred, LmRecord* rec,
-    const SeriesState* st, double func_tol) {
+    Topology tp, const double* tile_cost, const double* tile_pred, LmRecord* rec_all,
+    double func_tol, int deactivate) {
   __shared__ double sred[kReduceThreads / 32];
+  const int p = blockIdx.x;
+  LmRecord* rec = rec_all + p;
   double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < n_cost; i += blockDim.x) a += block_cost[i];
-  for (int i = threadIdx.x; i < n_pred; i += blockDim.x) b += block_pred[i];
+  for (int t = tp.tile_off[p] + threadIdx.x; t < tp.tile_off[p + 1]; t += blockDim.x) {
+    a += tile_cost[t];
+    b += tile_pred[t];
+  }
   const double F_new = 0.5 * block_sum_fixed(a, sred);
   __syncthreads();
   const double pred = 0.5 * block_sum_fixed(b, sred);
   if (threadIdx.x != 0) return;
+  if (!rec->active) {
+    rec->accepted = 0;
+    return;
+  }
   const double F = rec->cost;
   const double actual = F - F_new;
   const int accepted = (isfinite(F_new) && actual > 0.0 && pred > 0.0) ? 1 : 0;
@@ -273,29 +295,30 @@ __global__ void __launch_bounds__(kReduceThreads) lm_decide_kernel(
   rec->nonfinite = isfinite(F_new) ? 0 : 1;
   if (accepted) rec->cost = F_new;
   rec->iteration += 1;
+  if (deactivate && rec->converged) rec->active = 0;
 }
 
-void launch_lm_decide(const double* block_cost, int n_cost, const double* block_pred, int n_pred,
-                      LmRecord* rec, const SeriesState* st, double func_tol, cudaStream_t s) {
-  lm_decide_kernel<<<1, kReduceThreads, 0, s>>>(block_cost, n_cost, block_pred, n_pred, rec, st,
-                                                func_tol);
+void launch_lm_decide(const Topology& tp, const double* tile_cost, const double* tile_pred,
+                      LmRecord* rec, double func_tol, int deactivate, cudaStream_t s) {
+  lm_decide_kernel<<<tp.n_probs, kReduceThreads, 0, s>>>(tp, tile_cost, tile_pred, rec, func_tol,
+                                                         deactivate);
 }
 
-// x <- x + dx when the step was accepted (cameras already summed in cams_trial).
-__global__ void apply_step_kernel(const LmRecord* rec, double* cams, const double* cams_trial,
-                                  double* lms, const double* dx_l, int n_cams, int n_lms) {
-  if (!rec->accepted) return;
+// x <- x + dx for the problems whose step was accepted (cameras already summed in cams_trial).
+__global__ void apply_step_kernel(Topology tp, const LmRecord* rec, double* cams,
+                                  const double* cams_trial, double* lms, const double* dx_l) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n_cams * 9) cams[i] = cams_trial[i];
-  if (i < n_lms * 3) lms[i] += dx_l[i];
+  if (i < tp.n_cams * 9 && rec[tp.cam_prob[i / 9]].accepted) cams[i] = cams_trial[i];
+  if (i < tp.n_lms * 3 && rec[tp.lm_prob[i / 3]].accepted) lms[i] += dx_l[i];
 }
 
-void launch_apply_step(const LmRecord* rec, double* cams, const double* cams_trial, double* lms,
-                       const double* dx_l, int n_cams, int n_lms, cudaStream_t s) {
-  const int n = n_cams * 9 > n_lms * 3 ? n_cams * 9 : n_lms * 3;
+void launch_apply_step(const Topology& tp, const LmRecord* rec, double* cams,
+                       const double* cams_trial, double* lms, const double* dx_l,
+                       cudaStream_t s) {
+  const int n = tp.n_cams * 9 > tp.n_lms * 3 ? tp.n_cams * 9 : tp.n_lms * 3;
   const int threads = 256;
-  apply_step_kernel<<<(n + threads - 1) / threads, threads, 0, s>>>(rec, cams, cams_trial, lms,
-                                                                    dx_l, n_cams, n_lms);
+  apply_step_kernel<<<(n + threads - 1) / threads, threads, 0, s>>>(tp, rec, cams, cams_trial, lms,
+                                                                    dx_l);
 }
 
 }  // namespace poba

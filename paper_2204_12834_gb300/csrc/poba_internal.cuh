@@ -40,7 +40,7 @@ constexpr int kReduceThreads = 256;
 // ---------------------------------------------------------------------------------------
 // Host-side tile schedule (built once in ba_create).
 struct Schedule {
-  int n_cams = 0, n_lms = 0, n_obs = 0;
+  int n_cams = 0, n_lms = 0, n_obs = 0, n_probs = 1;
   int n_tiles = 0, n_slots = 0, max_slots_per_tile = 0, max_track = 0;
   std::vector<int32_t> lm_order;     // internal landmark -> caller landmark
   std::vector<int32_t> lm_rank;      // caller landmark -> internal landmark
@@ -57,11 +57,22 @@ struct Schedule {
   std::vector<int32_t> cam_slot_ptr; // [n_cams + 1]
   std::vector<int32_t> cam_slot_list;// [n_slots] camera-major row -> tile-major slot
   std::vector<int32_t> slot_row;     // [n_slots] tile-major slot -> camera-major row
+  // independent problems (a batch): cameras [cam_off[p], cam_off[p+1]) and caller landmarks
+  // [lm_off[p], lm_off[p+1]) form problem p; internal landmarks and tiles are contiguous per
+  // problem and no tile holds two problems
+  std::vector<int32_t> cam_off;      // [n_probs + 1]
+  std::vector<int32_t> lm_off_int;   // [n_probs + 1] internal landmark ranges
+  std::vector<int32_t> tile_off;     // [n_probs + 1] tile ranges
+  std::vector<int32_t> cam_prob;     // [n_cams]
+  std::vector<int32_t> lm_prob;      // [n_lms] problem of each internal landmark
 };
 
 // Returns an empty string on success, else a description of why the inputs are rejected.
+// cam_off / lm_off ([n_probs + 1]) split cameras and landmarks into independent problems; every
+// observation must join a camera and a landmark of the same problem.  NULL means one problem.
 std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_idx,
-                           const int32_t* lm_idx, Schedule* out);
+                           const int32_t* lm_idx, int n_probs, const int32_t* cam_off,
+                           const int32_t* lm_off, Schedule* out);
 
 // ---------------------------------------------------------------------------------------
 // Device views passed to kernels by value.
@@ -79,6 +90,13 @@ struct Topology {
   const int32_t* cam_slot_ptr;
   const int32_t* cam_slot_list;
   const int32_t* slot_row;  // partial sums are stored camera-major: row slot_row[slot]
+  // independent problems (P = 1 for a single problem)
+  int n_probs;
+  const int32_t* cam_prob;  // [n_cams]
+  const int32_t* lm_prob;   // [n_lms] (internal landmark order)
+  const int32_t* tile_prob; // [n_tiles]
+  const int32_t* cam_off;   // [n_probs + 1]
+  const int32_t* tile_off;  // [n_probs + 1]
 };
 
 // Per-camera values prepared once per state: rotation R (row-major), the matrix G with
@@ -86,18 +104,23 @@ struct Topology {
 // G = I on the first-order branch), translation, intrinsics, and the branch flag.
 constexpr int kCamPrep = 25;  // R[9] G[9] t[3] f k1 k2 first_order
 
-// Series state (device), one per handle.
+// Series state (device), one per problem.
 struct SeriesState {
-  int32_t done;        // stop rule fired (later iterations skip)
+  int32_t done;        // stop rule fired, or the problem takes no part in this solve
   int32_t m;           // number of P applications performed
   int32_t stopped;     // 1 if the stop test fired
   int32_t pad0;
   double stop_value;
   double x_norm;
   double t_norm;
-  double pad2;
-  uint32_t counter;    // last-block ticket
-  uint32_t pad1;
+  double pad1;
+};
+
+// Series state shared by all problems of a handle.
+struct SeriesGlobal {
+  int32_t all_done;    // every problem has stopped (later terms return at once)
+  uint32_t counter;    // last-block ticket of the per-term camera kernel
+  int32_t pad[2];
 };
 
 // Grid-barrier state of the persistent series kernel (zeroed before each launch).
@@ -123,7 +146,7 @@ struct LmRecord {
   int32_t nonfinite;
   int32_t iteration;
   int32_t converged;
-  int32_t pad;
+  int32_t active;       // 0: the problem has converged and is frozen (batches only)
 };
 
 // Sets the thread's ba_last_error() message (defined with the C ABI).
@@ -143,14 +166,16 @@ template <typename PT>
 void launch_lin_camera_reduce(const Topology& tp, const PT* partial, double* U45, double* b_p,
                               cudaStream_t s);
 
+// lambda of problem p is lam[p * lam_stride] (lam_stride 0: one lambda for all problems).
 void launch_damp_invert(const Topology& tp, const double* U45, const double* V,
-                        const double* lambda, int damping_mode, double* Uinv, double* Vinv,
-                        float* Vinv_f, int32_t* not_spd, cudaStream_t s);
+                        const double* lambda, int lam_stride, int damping_mode, double* Uinv,
+                        double* Vinv, float* Vinv_f, int32_t* not_spd, cudaStream_t s);
 
-void launch_cost(const Topology& tp, const double* prep, const double* lms, const double* dx_l,
-                 const double2* obs, const double* sqrt_w, double* block_sums, cudaStream_t s);
-
-int cost_blocks(const Topology& tp);
+// 2 F per tile (sum of w ||r||^2 over the tile's observations) at (cameras in prep, landmarks
+// lms + dx_l), float64.
+void launch_tile_cost(const Topology& tp, const double* prep, const double* lms,
+                      const double* dx_l, const double2* obs, const double* sqrt_w,
+                      double* tile_cost, cudaStream_t s);
 
 template <typename T>
 void launch_tile_rhs(const Topology& tp, const T* J, const double* b_l, const T* Vinv,
@@ -158,7 +183,8 @@ void launch_tile_rhs(const Topology& tp, const T* J, const double* b_l, const T*
 
 template <typename T>
 void launch_tile_series(const Topology& tp, const T* J, const T* t_cm, const T* Vinv,
-                        T* partial, const SeriesState* st, cudaStream_t s);
+                        T* partial, const SeriesState* st, const SeriesGlobal* sgl,
+                        cudaStream_t s);
 
 template <typename T>
 void launch_tile_backsub(const Topology& tp, const T* J, const T* r, const double* x,
@@ -166,18 +192,44 @@ void launch_tile_backsub(const Topology& tp, const T* J, const T* r, const doubl
                          double* block_pred, cudaStream_t s);
 
 // The camera kernels write the new term t into each of the camera's camera-major slot rows
-// (t_cm), which the next tile kernel gathers through slot_row.
+// (t_cm), which the next tile kernel gathers through slot_row, and a (||t_c||^2, ||x_c||^2)
+// pair per camera (cam_norm); the last block to finish reduces the pairs per problem and
+// applies the stop rule of each problem.
 template <typename PT>
 void launch_camera_rhs(const Topology& tp, const PT* partial, const double* b_p,
-                       const double* Uinv, double* x, PT* t_cm, double* block_norms,
-                       SeriesState* st, cudaStream_t s);
+                       const double* Uinv, double* x, PT* t_cm, double* cam_norm,
+                       SeriesState* st, SeriesGlobal* sgl, cudaStream_t s);
 
 template <typename PT>
 void launch_camera_series(const Topology& tp, const PT* partial, const double* Uinv, double* x,
-                          PT* t_cm, double* block_norms, SeriesState* st, int iter,
-                          double eps, cudaStream_t s);
+                          PT* t_cm, double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
+                          int iter, double eps, cudaStream_t s);
 
 int camera_blocks(const Topology& tp);
+int tile_blocks(const Topology& tp);
+
+// done[p] = 1 for problems that take no part (rec[p].active == 0; rec may be NULL).
+void launch_series_reset(SeriesState* st, SeriesGlobal* sgl, const LmRecord* rec, int n_probs,
+                         cudaStream_t s);
+
+// out[p * out_stride] = scale * (sum of tile_vals over the tiles of problem p), fixed order.
+void launch_reduce_tiles(const Topology& tp, const double* tile_vals, double* out,
+                         int out_stride, double scale, cudaStream_t s);
+
+// Per problem: F(x + dx) and the model decrease from tile sums, gain ratio, accept, lambda / nu
+// update; inactive problems are left as they are.  deactivate: a converged problem becomes
+// inactive.
+void launch_lm_decide(const Topology& tp, const double* tile_cost, const double* tile_pred,
+                      LmRecord* rec, double func_tol, int deactivate, cudaStream_t s);
+
+void launch_apply_step(const Topology& tp, const LmRecord* rec, double* cams,
+                       const double* cams_trial, double* lms, const double* dx_l,
+                       cudaStream_t s);
+
+void launch_set_scalar(double* dst, double v, cudaStream_t s);
+
+// Fixed-order sum of n doubles into *out = scale * sum (one block).
+void launch_reduce_sum(const double* in, int n, double* out, double scale, cudaStream_t s);
 
 // Persistent series kernel (cooperative launch): up to m_max terms and the stop rule.  Block 0
 // records %globaltimer at 5 points of each of the first kTraceTerms terms (start, end of the
@@ -187,24 +239,9 @@ constexpr int kTracePoints = 5;
 int persistent_blocks_per_sm(bool f32);
 template <typename T>
 cudaError_t launch_series_persistent(const Topology& tp, int grid, const T* J, const T* Vinv,
-                                     const double* b_l, const double* b_p, const double* Uinv,
-                                     double* x, T* t_cm, T* partial, double* group_norms,
-                                     SeriesState* st, GridSync* gs, int m_max, double eps,
-                                     long long timeout, long long* trace, cudaStream_t s);
-int tile_blocks(const Topology& tp);
-
-void launch_series_reset(SeriesState* st, cudaStream_t s);
-
-void launch_reduce_sum(const double* in, int n, double* out, double scale, cudaStream_t s);
-
-void launch_lm_decide(const double* block_cost, int n_cost, const double* block_pred,
-                      int n_pred, LmRecord* rec, const SeriesState* st, double func_tol,
-                      cudaStream_t s);
-
-void launch_apply_step(const LmRecord* rec, double* cams, const double* cams_trial,
-                       double* lms, const double* dx_l, int n_cams, int n_lms, cudaStream_t s);
-
-void launch_set_scalar(double* dst, double v, cudaStream_t s);
-
+                                     const double* Uinv, double* x, T* t_cm, T* partial,
+                                     double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
+                                     GridSync* gs, int m_max, double eps, long long timeout,
+                                     long long* trace, cudaStream_t s);
 
 }  // namespace poba

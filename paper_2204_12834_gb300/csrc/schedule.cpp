@@ -14,11 +14,37 @@
 namespace poba {
 
 std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_idx,
-                           const int32_t* lm_idx, Schedule* S) {
+                           const int32_t* lm_idx, int n_probs, const int32_t* cam_off,
+                           const int32_t* lm_off, Schedule* S) {
   if (n_cams < 1 || n_lms < 1 || n_obs < 0) return "n_cams and n_lms must be >= 1, n_obs >= 0";
+  if (n_probs < 1) return "need at least one problem";
   S->n_cams = n_cams;
   S->n_lms = n_lms;
   S->n_obs = n_obs;
+  S->n_probs = n_probs;
+  S->cam_off.assign(n_probs + 1, 0);
+  std::vector<int32_t> loff(n_probs + 1, 0);
+  if (cam_off && lm_off) {
+    for (int p = 0; p <= n_probs; ++p) {
+      S->cam_off[p] = cam_off[p];
+      loff[p] = lm_off[p];
+    }
+  } else {
+    if (n_probs != 1) return "problem offsets missing";
+    S->cam_off[1] = n_cams;
+    loff[1] = n_lms;
+  }
+  if (S->cam_off[0] != 0 || S->cam_off[n_probs] != n_cams || loff[0] != 0 || loff[n_probs] != n_lms)
+    return "problem offsets must start at 0 and end at n_cams / n_lms";
+  for (int p = 0; p < n_probs; ++p)
+    if (S->cam_off[p + 1] <= S->cam_off[p] || loff[p + 1] <= loff[p])
+      return "every problem needs at least one camera and one landmark";
+  S->cam_prob.assign(n_cams, 0);
+  for (int p = 0; p < n_probs; ++p)
+    for (int c = S->cam_off[p]; c < S->cam_off[p + 1]; ++c) S->cam_prob[c] = p;
+  std::vector<int32_t> lprob(n_lms, 0);
+  for (int p = 0; p < n_probs; ++p)
+    for (int l = loff[p]; l < loff[p + 1]; ++l) lprob[l] = p;
 
   std::vector<int32_t> count(n_lms, 0);
   std::vector<int32_t> key(n_lms, n_cams);  // smallest observing camera (n_cams if unobserved)
@@ -26,6 +52,8 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
     int c = cam_idx[o], l = lm_idx[o];
     if (c < 0 || c >= n_cams) return "cam_idx[" + std::to_string(o) + "] out of range";
     if (l < 0 || l >= n_lms) return "lm_idx[" + std::to_string(o) + "] out of range";
+    if (S->cam_prob[c] != lprob[l])
+      return "observation " + std::to_string(o) + " joins a camera and a landmark of different problems";
     count[l]++;
     key[l] = std::min(key[l], c);
   }
@@ -36,11 +64,21 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
            std::to_string(kTileObs) + " are supported";
   S->max_track = max_track;
 
-  // Internal landmark order: by smallest observing camera, then caller index.
+  // Internal landmark order: by problem, then smallest observing camera (unobserved landmarks
+  // last within their problem), then caller index.
   S->lm_order.resize(n_lms);
   std::iota(S->lm_order.begin(), S->lm_order.end(), 0);
-  std::stable_sort(S->lm_order.begin(), S->lm_order.end(),
-                   [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+  std::stable_sort(S->lm_order.begin(), S->lm_order.end(), [&](int32_t a, int32_t b) {
+    if (lprob[a] != lprob[b]) return lprob[a] < lprob[b];
+    return key[a] < key[b];
+  });
+  S->lm_prob.resize(n_lms);
+  S->lm_off_int.assign(n_probs + 1, 0);
+  for (int i = 0; i < n_lms; ++i) {
+    S->lm_prob[i] = lprob[S->lm_order[i]];
+    S->lm_off_int[S->lm_prob[i] + 1]++;
+  }
+  for (int p = 0; p < n_probs; ++p) S->lm_off_int[p + 1] += S->lm_off_int[p];
   S->lm_rank.assign(n_lms, 0);
   for (int i = 0; i < n_lms; ++i) S->lm_rank[S->lm_order[i]] = i;
 
@@ -63,14 +101,15 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
     S->lm_of[o] = S->lm_rank[lm_idx[S->obs_order[o]]];
   }
 
-  // Tiles: greedy packing of whole landmarks.
+  // Tiles: greedy packing of whole landmarks of one problem.
   S->tile_lm0.clear();
   S->tile_lm0.push_back(0);
   {
     int tile_obs = 0, tile_lms = 0;
     for (int i = 0; i < n_lms; ++i) {
       int k = S->lm_seg[i + 1] - S->lm_seg[i];
-      if (tile_lms > 0 && (tile_obs + k > kTileObs || tile_lms + 1 > kTileLms)) {
+      const bool new_prob = i > 0 && S->lm_prob[i] != S->lm_prob[i - 1];
+      if (tile_lms > 0 && (new_prob || tile_obs + k > kTileObs || tile_lms + 1 > kTileLms)) {
         S->tile_lm0.push_back(i);
         tile_obs = 0;
         tile_lms = 0;
@@ -81,6 +120,9 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
     S->tile_lm0.push_back(n_lms);
   }
   S->n_tiles = (int)S->tile_lm0.size() - 1;
+  S->tile_off.assign(n_probs + 1, 0);
+  for (int t = 0; t < S->n_tiles; ++t) S->tile_off[S->lm_prob[S->tile_lm0[t]] + 1]++;
+  for (int p = 0; p < n_probs; ++p) S->tile_off[p + 1] += S->tile_off[p];
 
   // Slots: distinct cameras per tile, ascending; per observation its slot and its position in
   // the tile's camera-sorted order (stable in landmark order).

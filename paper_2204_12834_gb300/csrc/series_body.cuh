@@ -296,23 +296,31 @@ __device__ __forceinline__ void tile_matvec_body_f32(const Topology& tp, int til
   }
 }
 
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
+  return *(const volatile unsigned*)p;
+}
+
 // Camera body for cameras [cam0, cam0 + per_block): thread (c, k) sums component k of the
 // camera's contiguous slot rows (loads issued 8 at a time, summed in a fixed order), applies
-// row k of U^-1, updates x and writes the new term into the camera's rows of t_cm.  Returns the
-// thread's term and x components (0 for idle threads) for the norms.  FP64 work is one add per
-// slot row and component: every FP64 warp instruction costs 16 pipe cycles on GB300, so no
-// shuffle trees are used for the slot sums.  Every thread of the block must call it.
+// row k of U^-1, updates x and writes the new term into the camera's rows of t_cm; then the 9
+// threads of the camera add their squared term and x components (in component order) into the
+// camera's pair cam_norm[c] = (||t_c||^2, ||x_c||^2).  Cameras of problems whose series has
+// stopped are left as they are.  FP64 work is one add per slot row and component: every FP64
+// warp instruction costs 16 pipe cycles on GB300, so no shuffle trees are used for the slot
+// sums.  ys and y2 are shared [per_block][9] arrays.  Every thread of the block must call it.
 template <typename PT, int MODE>
 __device__ __forceinline__ void camera_body(const Topology& tp, int cam0, int per_block,
                                             const PT* __restrict__ partial,
                                             const double* __restrict__ b_p,
                                             const double* __restrict__ Uinv,
                                             double* __restrict__ x, PT* __restrict__ t_cm,
-                                            double (*ys)[9], double& v_out, double& x_out) {
+                                            const SeriesState* st, double* __restrict__ cam_norm,
+                                            double (*ys)[9], double (*y2)[9]) {
   const int tid = threadIdx.x;
   const int cl = tid / 9, k = tid - cl * 9;
   const int c = cam0 + cl;
-  const bool cam_ok = cl < per_block && c < tp.n_cams;
+  const bool cam_ok = cl < per_block && c < tp.n_cams && !ld_volatile(&st[tp.cam_prob[c]].done);
   int r0 = 0, r1 = 0;
   if (cam_ok) {
     r0 = tp.cam_slot_ptr[c];
@@ -344,11 +352,27 @@ __device__ __forceinline__ void camera_body(const Topology& tp, int cam0, int pe
     const PT tv = (PT)v;
     for (int q = r0; q < r1; ++q) t_cm[(size_t)q * 9 + k] = tv;
   }
-  v_out = v;
-  x_out = xv;
+  __syncthreads();
+  if (cl < per_block) {
+    ys[cl][k] = v * v;
+    y2[cl][k] = xv * xv;
+  }
+  __syncthreads();
+  if (cam_ok && k == 0) {
+    double a = 0.0, b = 0.0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      a += ys[cl][j];
+      b += y2[cl][j];
+    }
+    cam_norm[2 * c + 0] = a;
+    cam_norm[2 * c + 1] = b;
+  }
+  __syncthreads();
 }
 
-// The stop rule of eq. `qcriterion` at term `iter` from the squared norms; updates st.
+// The stop rule of eq. `qcriterion` at term `iter` from the squared norms; updates one
+// problem's state.
 __device__ __forceinline__ void series_stop_rule(SeriesState* st, int iter, double T2, double X2,
                                                  double eps) {
   const double tn = sqrt(T2), xn = sqrt(X2);
@@ -373,6 +397,41 @@ __device__ __forceinline__ void series_stop_rule(SeriesState* st, int iter, doub
       st->stopped = 1;
     }
   }
+}
+
+// Every problem still running: sum its cameras' norm pairs (one warp per problem, lanes strided
+// over the cameras, then a fixed shuffle tree) and apply its stop rule for term `iter`; raise
+// all_done when no problem is left.  Every thread of one block must call it.
+__device__ __forceinline__ void problems_stop_rule(const Topology& tp,
+                                                   const double* __restrict__ cam_norm,
+                                                   SeriesState* st, SeriesGlobal* sgl, int iter,
+                                                   double eps, int* s_running) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) *s_running = 0;
+  __syncthreads();
+  for (int p = warp; p < tp.n_probs; p += nw) {
+    if (ld_volatile(&st[p].done)) continue;  // warp-uniform
+    double a = 0.0, b = 0.0;
+    for (int c = tp.cam_off[p] + lane; c < tp.cam_off[p + 1]; c += 32) {
+      a += __ldcg(cam_norm + 2 * c + 0);
+      b += __ldcg(cam_norm + 2 * c + 1);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, off);
+      b += __shfl_down_sync(0xffffffffu, b, off);
+    }
+    if (lane == 0) {
+      series_stop_rule(&st[p], iter, a, b, eps);
+      if (!st[p].done) atomicAdd(s_running, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (*s_running == 0) sgl->all_done = 1;
+  }
+  __syncthreads();
 }
 
 }  // namespace poba

@@ -1,0 +1,219 @@
+"""Batches of independent problems (the PoST sub-problem solve, Sec. 5.3): one handle holds P
+problems of uneven sizes and steps them together.  Every problem's tiles, slot rows and
+fixed-order sums are the ones a handle created for it alone would use, so results must be equal
+bit for bit to per-problem handles; the series and the LM loop must also match the FP64 oracle
+per problem (series <= 1e-10 relative in FP64 at equal lambda and stop rule, <= 1e-4 in
+FP32-bulk; LM: same accept sequence, cost within 1e-6)."""
+import numpy as np
+import pytest
+
+import bal_synth
+from gpu_helpers import OracleRef, rel
+from oracle import camera_model as cm
+from oracle import lm as olm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def poba():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2204_12834_gb300 import build as b
+    b.build()
+    import paper_2204_12834_gb300 as m
+    m.library()
+    return m
+
+
+@pytest.fixture(scope="module")
+def small():
+    """Seven problems of 4 to 33 cameras and 30 to 600 landmarks, tracks of 2 to 8."""
+    return bal_synth.make_batch(7, seed=5, cams=(3, 40), lms=(30, 600), track=(2, 8))
+
+
+def single(poba, p, precision=0, **opt):
+    return poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, p.weights,
+                          precision=precision, options=poba.ba_default_options(**opt))
+
+
+def batch(poba, probs, precision=0, **opt):
+    return poba.batch_from_problems(probs, precision=precision,
+                                    options=poba.ba_default_options(**opt))
+
+
+def test_layout_params_and_costs(poba, small):
+    h = batch(poba, small)
+    co, lo = poba.ba_get_batch_layout(h)
+    assert list(co) == list(np.cumsum([0] + [p.n_cams for p in small]))
+    assert list(lo) == list(np.cumsum([0] + [p.n_lms for p in small]))
+    c, l = poba.ba_get_params(h)
+    assert np.array_equal(c, np.concatenate([p.cams0 for p in small]))
+    assert np.array_equal(l, np.concatenate([p.lms0 for p in small]))
+    costs = poba.ba_cost_batch(h)
+    for p, f in zip(small, costs):
+        fo = cm.cost(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, p.weights)
+        assert abs(f - fo) <= 1e-12 * fo
+    assert abs(poba.ba_cost(h) - costs.sum()) <= 1e-12 * costs.sum()
+
+
+@pytest.mark.parametrize("lam", [0.3, 1.0])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-4)])
+def test_series_per_problem_matches_oracle(poba, small, precision, tol, lam):
+    """One lambda for the whole batch; each problem runs its own stop rule (eps = 0.01) and
+    stops at its own term (lambda = 1: 6 to 9 terms)."""
+    h = batch(poba, small, precision=precision, eps=0.01, max_inner=20)
+    poba.ba_linearize(h)
+    info = poba.ba_solve_schur_power(h, lam)
+    states = poba.ba_get_series_state(h)
+    dxp, dxl = poba.ba_get_step(h)
+    co, lo = poba.ba_get_batch_layout(h)
+    ms = []
+    for i, p in enumerate(small):
+        o = OracleRef(p).solve(lam, 0.01, 20)
+        if precision == 0:
+            assert states[i]["inner_iters"] == o["m"]
+            assert abs(states[i]["stop_value"] - o["sv"]) <= 1e-8 * o["sv"] or o["m"] == 0
+        assert states[i]["lam"] == lam
+        assert rel(dxp[co[i]:co[i + 1]], o["x"]) < tol
+        assert rel(dxl[lo[i]:lo[i + 1]], o["xl"]) < tol
+        ms.append(states[i]["inner_iters"])
+    assert info["inner_iters"] == max(ms)
+    if precision == 0:
+        assert len(set(ms)) > 1  # the problems stop at different terms
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("series_exec", [0, 2])
+def test_lm_equals_individual_handles_bitwise(poba, small, precision, series_exec):
+    opt = dict(max_lm=12, series_exec=series_exec)
+    hb = batch(poba, small, precision=precision, **opt)
+    last, n_steps = poba.ba_lm_solve_batch(hb)
+    cb, lb = poba.ba_get_params(hb)
+    co, lo = poba.ba_get_batch_layout(hb)
+    longest = 0
+    for i, p in enumerate(small):
+        h = single(poba, p, precision=precision, **opt)
+        trace = poba.ba_lm_solve(h, max_lm=12)
+        c, l = poba.ba_get_params(h)
+        assert np.array_equal(cb[co[i]:co[i + 1]], c), i
+        assert np.array_equal(lb[lo[i]:lo[i + 1]], l), i
+        assert last[i]["it"] == trace[-1]["it"]
+        assert last[i]["converged"] == trace[-1]["converged"]
+        assert last[i]["cost_after"] == trace[-1]["cost_after"]
+        longest = max(longest, len(trace))
+    assert n_steps == longest
+
+
+def test_lm_per_problem_matches_oracle(poba, small):
+    """FP64: each problem's own accept / reject sequence and final cost follow the oracle's LM
+    loop (Sec. 5.1 settings) although the problems converge at different iterations."""
+    hb = batch(poba, small, max_lm=15)
+    steps = []
+    for _ in range(15):
+        infos, active = poba.ba_lm_step_batch(hb)
+        steps.append(infos)
+        if active == 0:
+            break
+    costs = poba.ba_cost_batch(hb)
+    n_conv = []
+    for i, p in enumerate(small):
+        _, _, hist = olm.lm_solve(p, olm.Options(max_lm=15))
+        mine = []
+        for s in steps:
+            if not mine or not mine[-1]["converged"]:
+                mine.append(s[i])
+        assert len(mine) == len(hist), i
+        for s, o in zip(mine, hist):
+            assert s["accepted"] == o["accepted"]
+            assert s["inner"] == o["inner"]
+            assert abs(s["cost_after"] - o["cost_after"]) <= 1e-6 * o["cost_after"]
+        f_orc = min([e["cost_after"] for e in hist if e["accepted"]] + [hist[0]["cost_before"]])
+        assert abs(costs[i] - f_orc) <= 1e-6 * f_orc
+        n_conv.append(len(hist))
+    assert len(set(n_conv)) > 1  # the problems converge at different iterations
+
+
+def test_single_problem_batch_equals_plain_handle(poba, small):
+    p = small[0]
+    ha = single(poba, p, max_lm=5)
+    hb = batch(poba, [p], max_lm=5)
+    for _ in range(5):
+        a = poba.ba_lm_step(ha)
+        (b,), _ = poba.ba_lm_step_batch(hb)
+        assert a == b
+    assert all(np.array_equal(x, y) for x, y in zip(poba.ba_get_params(ha), poba.ba_get_params(hb)))
+
+
+def test_batch_edge_cases(poba, small):
+    from paper_2204_12834_gb300 import PobaError
+    empty = bal_synth.make_problem(5, 40, track=("uniform", 2, 3), seed=11)
+    probs = [small[0], empty, small[5]]
+    tup = [(q.cams0, q.lms0, q.obs, q.cam_idx, q.lm_idx) for q in probs]
+    tup[1] = (empty.cams0, empty.lms0, np.zeros((0, 2)), np.zeros(0, np.int32), np.zeros(0, np.int32))
+    h = poba.ba_create_batch(tup, options=poba.ba_default_options(max_lm=6))
+    costs = poba.ba_cost_batch(h)
+    assert costs[1] == 0.0
+    with pytest.raises(PobaError) as e:
+        poba.ba_lm_step(h)
+    assert e.value.status_name == "BA_ERR_INVALID_ARG"
+    with pytest.raises(PobaError):
+        poba.ba_get_lm_state(h)
+    last, n = poba.ba_lm_solve_batch(h)
+    assert not last[1]["accepted"] and np.isfinite(last[0]["cost_after"])
+    # after ba_set_lm_state every problem is active again and steps
+    poba.ba_set_lm_state(h, 1e-4, 2.0, 0)
+    infos, active = poba.ba_lm_step_batch(h)
+    assert infos[0]["it"] == 0 and infos[2]["it"] == 0
+    # bad batches are rejected with the problem named
+    bad = list(tup)
+    bad[2] = (small[5].cams0, small[5].lms0, small[5].obs, small[5].cam_idx + 100, small[5].lm_idx)
+    with pytest.raises(PobaError) as e:
+        poba.ba_create_batch(bad)
+    assert e.value.status_name == "BA_ERR_INVALID_ARG" and "problem 2" in str(e.value)
+
+
+@pytest.fixture(scope="module")
+def full_batch():
+    """256 problems: cameras U{8..200}, landmarks U{500..20000}, tracks U{2..8} (about 12.7M
+    observations): the batched workload of the benchmark."""
+    return bal_synth.make_batch(256)
+
+
+def test_full_size_batch_fp32(poba, full_batch):
+    """The benchmark's batch in its launch configuration (FP32 bulk, persistent series): two LM
+    steps of the batch equal those of per-problem handles on sampled problems bit for bit, the
+    sampled problems' first series matches the FP64 oracle within 1e-4, and every problem's
+    accepted steps decrease its own cost."""
+    hb = batch(poba, full_batch, precision=1)
+    f0 = poba.ba_cost_batch(hb)
+    steps = [poba.ba_lm_step_batch(hb)[0] for _ in range(2)]
+    f2 = poba.ba_cost_batch(hb)
+    for i in range(len(full_batch)):
+        a = [s[i] for s in steps]
+        assert np.isfinite(f2[i]) and f2[i] <= f0[i]
+        if a[0]["accepted"]:
+            assert a[0]["cost_after"] < a[0]["cost_before"]
+        assert (f2[i] < f0[i]) == any(s["accepted"] for s in a)
+    co, lo = poba.ba_get_batch_layout(hb)
+    cb, lb = poba.ba_get_params(hb)
+    rng = np.random.default_rng(3)
+    sizes = np.array([p.n_obs for p in full_batch])
+    sample = list(rng.choice(len(full_batch), 3, replace=False)) + [int(sizes.argmin())]
+    for i in sample:
+        p = full_batch[i]
+        h = single(poba, p, precision=1)
+        s0 = poba.ba_lm_step(h)
+        s1 = poba.ba_lm_step(h)
+        assert s0 == steps[0][i] and s1 == steps[1][i]
+        c, l = poba.ba_get_params(h)
+        assert np.array_equal(cb[co[i]:co[i + 1]], c) and np.array_equal(lb[lo[i]:lo[i + 1]], l)
+    # the series of the smallest problem at the first step against the FP64 oracle
+    i = int(sizes.argmin())
+    p = full_batch[i]
+    h = single(poba, p, precision=1)
+    poba.ba_linearize(h)
+    info = poba.ba_solve_schur_power(h, 1e-4)
+    dxp, dxl = poba.ba_get_step(h)
+    o = OracleRef(p).solve(1e-4, 0.0, info["inner_iters"])
+    assert rel(dxp, o["x"]) < 1e-4 and rel(dxl, o["xl"]) < 1e-4
