@@ -101,6 +101,8 @@ typedef struct {
   int32_t inner_iters;    /* series terms used */
   int32_t converged;      /* 1 if accepted with relative decrease < func_tol */
   int32_t iteration;      /* LM iteration index of this step (0-based) */
+  int32_t not_spd;        /* 1 if a damped block failed its Cholesky factorisation: the
+                             iteration had no step and was rejected (cost_after is NaN) */
 } ba_step_info;
 
 /* Fill *opts with the defaults of Sec. 5.1 (lambda0 1e-4, func_tol 1e-6, eps 0.01, max_lm 50,
@@ -138,9 +140,12 @@ ba_status ba_solve_schur_power(ba_handle* h, double lambda, ba_series_info* info
  * damp with the handle's current lambda, solve with the power series, back-substitute,
  * evaluate F(x + dx) and the model decrease, accept iff F decreased and the model decrease is
  * positive, update lambda (accept: lambda *= max(1/3, 1 - (2 rho - 1)^3), nu = 2; reject:
- * lambda *= nu, nu *= 2; clamp to [1e-10, 1e32]) and apply an accepted step.  Synchronises
- * once.  info may be NULL.  Errors: BA_ERR_NOT_SPD, BA_ERR_NONFINITE (non-finite cost at the
- * current state), BA_ERR_TIMEOUT, BA_ERR_CUDA. */
+ * lambda *= nu, nu *= 2; clamp to [1e-10, 1e32]) and apply an accepted step.  Sec. 4.1 takes
+ * the damped blocks to be positive definite; when one still fails its Cholesky factorisation
+ * in floating point (damping that underflows, a nearly singular block), the iteration has no
+ * step: it is rejected like a step that did not decrease F, lambda grows, and info->not_spd = 1
+ * -- this is not an error.  Synchronises once.  info may be NULL.  Errors: BA_ERR_NONFINITE
+ * (non-finite cost at the current state), BA_ERR_TIMEOUT, BA_ERR_CUDA. */
 ba_status ba_lm_step(ba_handle* h, ba_step_info* info);
 
 /* Run ba_lm_step until convergence (func_tol) or max_lm iterations.  trace may be NULL or

@@ -11,8 +11,12 @@ family): gain ratio rho = (F(x) - F(x + dx)) / (L(0) - L(dx)) with the model dec
 directly from r and J; the step is accepted iff F decreased and L(0) - L(dx) > 0; on accept
 lambda <- lambda max(1/3, 1 - (2 rho - 1)^3), nu <- 2; on reject lambda <- lambda nu,
 nu <- 2 nu; lambda is clamped to [1e-10, 1e32].  Rejected steps re-solve with the new lambda at
-the same linearisation.  The run stops after an accepted step whose relative decrease
-(F_old - F_new) / F_old is below func_tol, or after max_lm iterations.
+the same linearisation.  Sec. 4.1 takes the damped blocks to be positive definite; in floating
+point a block can still fail its Cholesky factorisation (lambda so small that the damping
+underflows, or a nearly singular block).  Reading: such an iteration has no step -- it is
+rejected like a step that did not decrease F (state unchanged, lambda <- lambda nu), and its
+history entry has not_spd = True and cost_after = NaN.  The run stops after an accepted step
+whose relative decrease (F_old - F_new) / F_old is below func_tol, or after max_lm iterations.
 """
 from __future__ import annotations
 
@@ -78,7 +82,13 @@ def lm_solve(problem, opts: Options | None = None, solver="power", cams=None, lm
         if ne is None:
             r, Jp, Jl = cm.linearize(cams, lms, *args)
             ne = NormalEquation(r, Jp, Jl, problem.cam_idx, problem.lm_idx, nc, nl)
-        dx_p, dx_l, m, sv = solve_step(ne, lam, opts, solver)
+        try:
+            dx_p, dx_l, m, sv = solve_step(ne, lam, opts, solver)
+        except np.linalg.LinAlgError:
+            history.append(dict(it=it, cost_before=F, cost_after=np.nan, lam=lam, accepted=False,
+                                rho=0.0, inner=0, stop_value=np.inf, pred=0.0, not_spd=True))
+            lam, nu = lambda_update(lam, nu, False, 0.0)
+            continue
         cams_new = cams + dx_p.reshape(nc, 9)
         lms_new = lms + dx_l.reshape(nl, 3)
         F_new = cm.cost(cams_new, lms_new, *args)
@@ -87,7 +97,7 @@ def lm_solve(problem, opts: Options | None = None, solver="power", cams=None, lm
         accepted = bool(np.isfinite(F_new) and actual > 0.0 and pred > 0.0)
         rho = actual / pred if pred != 0.0 else 0.0
         history.append(dict(it=it, cost_before=F, cost_after=F_new, lam=lam, accepted=accepted,
-                            rho=rho, inner=m, stop_value=sv, pred=pred))
+                            rho=rho, inner=m, stop_value=sv, pred=pred, not_spd=False))
         lam, nu = lambda_update(lam, nu, accepted, rho)
         if accepted:
             cams, lms = cams_new, lms_new

@@ -227,7 +227,7 @@ def _step_dict(s: StepInfo) -> dict:
     return dict(cost_before=s.cost_before, cost_after=s.cost_after, lam=s.lambda_,
                 gain_ratio=s.gain_ratio, model_decrease=s.model_decrease, stop_value=s.stop_value,
                 accepted=bool(s.accepted), inner=s.inner_iters, converged=bool(s.converged),
-                it=s.iteration)
+                it=s.iteration, not_spd=bool(s.not_spd))
 
 
 def ba_lm_step(h: Handle) -> dict:

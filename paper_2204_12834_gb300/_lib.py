@@ -37,7 +37,7 @@ class StepInfo(C.Structure):
     _fields_ = [("cost_before", C.c_double), ("cost_after", C.c_double), ("lambda_", C.c_double),
                 ("gain_ratio", C.c_double), ("model_decrease", C.c_double),
                 ("stop_value", C.c_double), ("accepted", C.c_int32), ("inner_iters", C.c_int32),
-                ("converged", C.c_int32), ("iteration", C.c_int32)]
+                ("converged", C.c_int32), ("iteration", C.c_int32), ("not_spd", C.c_int32)]
 
 
 TIMING_CLASSES = ["linearize", "damp_invert", "rhs", "series_tile", "series_camera", "backsub",

@@ -370,7 +370,7 @@ ba_status run_series_body(ba_handle* h, bool use_active) {
 // lambda of problem p at lam_dev[p * lam_stride]; use_active: problems whose LM record is
 // inactive take no part.
 ba_status run_solve(ba_handle* h, const double* lam_dev, int lam_stride, bool use_active) {
-  CK(cudaMemsetAsync(h->not_spd, 0, sizeof(int32_t), h->stream));
+  CK(cudaMemsetAsync(h->not_spd, 0, sizeof(int32_t) * h->n_probs, h->stream));
   if (h->timing) {
     ba_status st = ensure_events(h);
     if (st != BA_OK) return st;
@@ -604,7 +604,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   items.push_back({(void**)&h->st, sizeof(SeriesState) * P});
   items.push_back({(void**)&h->sgl, sizeof(SeriesGlobal)});
   items.push_back({(void**)&h->rec, sizeof(LmRecord) * P});
-  items.push_back({(void**)&h->not_spd, sizeof(int32_t)});
+  items.push_back({(void**)&h->not_spd, sizeof(int32_t) * P});
   size_t total = 0;
   for (auto& it : items) total = align_up(total, 256) + it.bytes;
   total = align_up(total, 256);
@@ -635,7 +635,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
       (e = cudaMallocHost(&h->h_sgl, sizeof(SeriesGlobal))) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_rec, sizeof(LmRecord) * P)) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_gs, sizeof(GridSync))) != cudaSuccess ||
-      (e = cudaMallocHost(&h->h_flag, sizeof(int32_t))) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_flag, sizeof(int32_t) * P)) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_scalar, sizeof(double) * 4)) != cudaSuccess)
     return bail(fail_cuda(e, "cudaMallocHost"));
 
@@ -760,6 +760,7 @@ void fill_step_info(const LmRecord& R, const SeriesState& S, ba_step_info* info)
   info->inner_iters = S.m;
   info->converged = R.converged;
   info->iteration = R.iteration - 1;
+  info->not_spd = R.not_spd;
 }
 
 // One LM iteration of every problem of the handle whose record is active; batch: a problem that
@@ -781,7 +782,8 @@ ba_status lm_iteration(ba_handle* h, bool batch) {
   tmark(h, kTEval, 0, 0);
   launch_cam_prepare(h->cams, h->x, h->n_c, h->prep_trial, h->cams_trial, s);
   launch_tile_cost(h->tp, h->prep_trial, h->lms, h->dx_l, h->obs, h->sqrt_w, h->tile_cost, s);
-  launch_lm_decide(h->tp, h->tile_cost, h->block_pred, h->rec, h->opts.func_tol, batch ? 1 : 0, s);
+  launch_lm_decide(h->tp, h->tile_cost, h->block_pred, h->not_spd, h->rec, h->opts.func_tol,
+                   batch ? 1 : 0, s);
   launch_apply_step(h->tp, h->rec, h->cams, h->cams_trial, h->lms, h->dx_l, s);
   tmark(h, kTEval, 0, 1);
   h->launches += 4;
@@ -789,7 +791,6 @@ ba_status lm_iteration(ba_handle* h, bool batch) {
   if (st != BA_OK) return st;
   CK(cudaMemcpyAsync(h->h_rec, h->rec, sizeof(LmRecord) * P, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SeriesState) * P, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(h->h_flag, h->not_spd, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   collect_timing(h, max_terms(h), true);
@@ -801,14 +802,15 @@ ba_status lm_iteration(ba_handle* h, bool batch) {
   return BA_OK;
 }
 
-// Status of an LM iteration after its records were read: non-finite cost, then not-SPD.
+// Status of an LM iteration after its records were read: a non-finite cost at the current state
+// of an active problem.  (Blocks that were not positive definite made that problem's step a
+// rejected one; its step info says so.)
 ba_status lm_status(ba_handle* h) {
   for (int p = 0; p < h->n_probs; ++p)
     if (!std::isfinite(h->h_rec[p].cost_before))
       return fail(BA_ERR_NONFINITE, h->n_probs > 1 ? "problem " + std::to_string(p) +
                                                          ": non-finite cost at the current state"
                                                    : std::string("non-finite cost at the current state"));
-  if (*h->h_flag) return fail(BA_ERR_NOT_SPD, "a damped block is not positive definite");
   return BA_OK;
 }
 
@@ -872,7 +874,7 @@ ba_status ba_solve_schur_power(ba_handle* h, double lambda, ba_series_info* info
   if (!info) return BA_OK;
   const size_t P = (size_t)h->n_probs;
   CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SeriesState) * P, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaMemcpyAsync(h->h_flag, h->not_spd, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->h_flag, h->not_spd, sizeof(int32_t) * P, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   collect_timing(h, max_terms(h), true);
@@ -898,7 +900,11 @@ ba_status ba_solve_schur_power(ba_handle* h, double lambda, ba_series_info* info
     a.lambda = lambda;
     *info = a;
   }
-  if (*h->h_flag) return fail(BA_ERR_NOT_SPD, "a damped block is not positive definite");
+  for (size_t p = 0; p < P; ++p)
+    if (h->h_flag[p])
+      return fail(BA_ERR_NOT_SPD, P > 1 ? "problem " + std::to_string(p) +
+                                              ": a damped block is not positive definite"
+                                        : std::string("a damped block is not positive definite"));
   return BA_OK;
 }
 

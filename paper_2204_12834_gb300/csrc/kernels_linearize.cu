@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kDampThreads) damp_invert_kernel(
       if (ok_cam && k > j) A[cl][k][j] *= A[cl][j][j];
       __syncthreads();
     }
-    if (ok_cam && k == 0 && bad[cl]) atomicOr(not_spd, 1);
+    if (ok_cam && k == 0 && bad[cl]) atomicOr(not_spd + tp.cam_prob[c], 1);
     if (ok_cam) {
       const double (*a)[10] = A[cl];
       double m[9];
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(kDampThreads) damp_invert_kernel(
     double d2 = a22 - l20 * l20 - l21 * l21;
     if (!(d2 > 0.0) || !isfinite(d2)) { ok = false; d2 = 1.0; }
     const double m22 = rsqrt(d2);
-    if (!ok) atomicOr(not_spd, 1);
+    if (!ok) atomicOr(not_spd + tp.lm_prob[l], 1);
     // M = L^-1
     const double m10 = -l10 * m00 * m11;
     const double m21 = -l21 * m11 * m22;

@@ -248,12 +248,13 @@ void launch_reduce_tiles(const Topology& tp, const double* tile_vals, double* ou
 // ---------------------------------------------------------------------------------------
 // LM decision (Sec. 5.1), one block per problem: F(x + dx) and the model decrease from the
 // problem's tile sums, gain ratio, accept iff F decreased and the model decrease is positive,
-// lambda / nu update.
+// lambda / nu update.  An iteration whose damped blocks were not positive definite has no step
+// and counts as rejected (its trial cost is reported as NaN).
 constexpr double kLambdaMin = 1e-10, kLambdaMax = 1e32;
 
 __global__ void __launch_bounds__(kReduceThreads) lm_decide_kernel(
-    Topology tp, const double* tile_cost, const double* tile_pred, LmRecord* rec_all,
-    double func_tol, int deactivate) {
+    Topology tp, const double* tile_cost, const double* tile_pred, const int32_t* not_spd,
+    LmRecord* rec_all, double func_tol, int deactivate) {
   __shared__ double sred[kReduceThreads / 32];
   const int p = blockIdx.x;
   LmRecord* rec = rec_all + p;
@@ -262,18 +263,23 @@ __global__ void __launch_bounds__(kReduceThreads) lm_decide_kernel(
     a += tile_cost[t];
     b += tile_pred[t];
   }
-  const double F_new = 0.5 * block_sum_fixed(a, sred);
+  double F_new = 0.5 * block_sum_fixed(a, sred);
   __syncthreads();
-  const double pred = 0.5 * block_sum_fixed(b, sred);
+  double pred = 0.5 * block_sum_fixed(b, sred);
   if (threadIdx.x != 0) return;
   if (!rec->active) {
     rec->accepted = 0;
     return;
   }
+  const int bad = not_spd[p] != 0;
+  if (bad) {
+    F_new = NAN;
+    pred = 0.0;
+  }
   const double F = rec->cost;
   const double actual = F - F_new;
-  const int accepted = (isfinite(F_new) && actual > 0.0 && pred > 0.0) ? 1 : 0;
-  const double rho = pred != 0.0 ? actual / pred : 0.0;
+  const int accepted = (!bad && isfinite(F_new) && actual > 0.0 && pred > 0.0) ? 1 : 0;
+  const double rho = (!bad && pred != 0.0) ? actual / pred : 0.0;
   double lam = rec->lambda, nu = rec->nu;
   rec->lambda_used = lam;
   if (accepted) {
@@ -291,17 +297,19 @@ __global__ void __launch_bounds__(kReduceThreads) lm_decide_kernel(
   rec->model_decrease = pred;
   rec->gain_ratio = rho;
   rec->accepted = accepted;
+  rec->not_spd = bad;
   rec->converged = (accepted && actual / F < func_tol) ? 1 : 0;
-  rec->nonfinite = isfinite(F_new) ? 0 : 1;
+  rec->nonfinite = (bad || isfinite(F_new)) ? 0 : 1;
   if (accepted) rec->cost = F_new;
   rec->iteration += 1;
   if (deactivate && rec->converged) rec->active = 0;
 }
 
 void launch_lm_decide(const Topology& tp, const double* tile_cost, const double* tile_pred,
-                      LmRecord* rec, double func_tol, int deactivate, cudaStream_t s) {
-  lm_decide_kernel<<<tp.n_probs, kReduceThreads, 0, s>>>(tp, tile_cost, tile_pred, rec, func_tol,
-                                                         deactivate);
+                      const int32_t* not_spd, LmRecord* rec, double func_tol, int deactivate,
+                      cudaStream_t s) {
+  lm_decide_kernel<<<tp.n_probs, kReduceThreads, 0, s>>>(tp, tile_cost, tile_pred, not_spd, rec,
+                                                         func_tol, deactivate);
 }
 
 // x <- x + dx for the problems whose step was accepted (cameras already summed in cams_trial).

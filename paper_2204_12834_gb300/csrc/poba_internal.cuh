@@ -142,7 +142,7 @@ struct LmRecord {
   double nu;
   double lambda_used;
   int32_t accepted;
-  int32_t not_spd;      // set by damp/invert
+  int32_t not_spd;      // the last iteration's damped blocks were not positive definite
   int32_t nonfinite;
   int32_t iteration;
   int32_t converged;
@@ -166,7 +166,9 @@ template <typename PT>
 void launch_lin_camera_reduce(const Topology& tp, const PT* partial, double* U45, double* b_p,
                               cudaStream_t s);
 
-// lambda of problem p is lam[p * lam_stride] (lam_stride 0: one lambda for all problems).
+// lambda of problem p is lam[p * lam_stride] (lam_stride 0: one lambda for all problems);
+// not_spd[p] is set to 1 when a damped block of problem p fails its Cholesky factorisation (the
+// failed pivot is replaced by 1 so that the inverse stays finite).
 void launch_damp_invert(const Topology& tp, const double* U45, const double* V,
                         const double* lambda, int lam_stride, int damping_mode, double* Uinv,
                         double* Vinv, float* Vinv_f, int32_t* not_spd, cudaStream_t s);
@@ -217,10 +219,12 @@ void launch_reduce_tiles(const Topology& tp, const double* tile_vals, double* ou
                          int out_stride, double scale, cudaStream_t s);
 
 // Per problem: F(x + dx) and the model decrease from tile sums, gain ratio, accept, lambda / nu
-// update; inactive problems are left as they are.  deactivate: a converged problem becomes
-// inactive.
+// update; inactive problems are left as they are.  A problem whose damped blocks were not
+// positive definite (not_spd[p]) has no step: it is rejected.  deactivate: a converged problem
+// becomes inactive.
 void launch_lm_decide(const Topology& tp, const double* tile_cost, const double* tile_pred,
-                      LmRecord* rec, double func_tol, int deactivate, cudaStream_t s);
+                      const int32_t* not_spd, LmRecord* rec, double func_tol, int deactivate,
+                      cudaStream_t s);
 
 void launch_apply_step(const Topology& tp, const LmRecord* rec, double* cams,
                        const double* cams_trial, double* lms, const double* dx_l,

@@ -114,6 +114,30 @@ def test_not_spd_is_reported(poba):
     assert info["inner_iters"] >= 0
 
 
+def test_not_spd_lm_iteration_is_rejected_like_the_oracle(poba):
+    """In the LM loop a damped block that fails Cholesky is not an error: the iteration has no
+    step, is rejected (state unchanged, lambda raised, here to the 1e-10 clamp) and reports
+    not_spd; the following iterations match the oracle's LM loop, which does the same."""
+    from oracle import lm as olm
+    p = bal_synth.make_problem(4, 60, track=("uniform", 2, 4), seed=113)
+    p.cams0 = np.vstack([p.cams0, p.cams0[:1]])  # camera 4: no observations -> U = 0
+    _, _, hist = olm.lm_solve(p, olm.Options(lambda0=1e-320, max_lm=6))
+    h = poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx,
+                       options=poba.ba_default_options(lambda0=1e-320, max_lm=6))
+    steps = poba.ba_lm_solve(h, max_lm=6)
+    assert len(steps) == len(hist)
+    s0, o0 = steps[0], hist[0]
+    assert s0["not_spd"] and o0["not_spd"] and not s0["accepted"]
+    assert np.isnan(s0["cost_after"])
+    assert abs(s0["cost_before"] - o0["cost_before"]) <= 1e-12 * o0["cost_before"]
+    for s, o in zip(steps[1:], hist[1:]):
+        assert not s["not_spd"] and s["accepted"] == o["accepted"] and s["inner"] == o["inner"]
+        assert abs(s["lam"] - o["lam"]) <= 1e-12 * o["lam"]
+        assert abs(s["cost_after"] - o["cost_after"]) <= 1e-6 * o["cost_after"]
+    c, _ = poba.ba_get_params(h)
+    assert np.array_equal(c[4], p.cams0[4])
+
+
 def test_solve_before_linearize(poba):
     p = bal_synth.make_problem(4, 50, seed=115)
     h = poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx)

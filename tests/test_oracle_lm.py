@@ -55,3 +55,21 @@ def test_func_tol_stops_early():
     assert len(h) < 50
     last = h[-1]
     assert last["accepted"] and (last["cost_before"] - last["cost_after"]) / last["cost_before"] < 1e-3
+
+
+def test_not_spd_iteration_is_a_rejected_step():
+    """A camera nothing observes has U = 0; with lambda0 = 1e-320 its damping lambda * 1e-6
+    underflows to 0, the block fails Cholesky, and the iteration is rejected with the state
+    unchanged and lambda raised (then clamped to 1e-10); the solve then proceeds normally."""
+    p = bal_synth.make_problem(4, 60, track=("uniform", 2, 4), seed=113)
+    p.cams0 = np.vstack([p.cams0, p.cams0[:1]])  # camera 4: no observations
+    # the underflow the test relies on
+    assert 1e-320 * 1e-6 == 0.0
+    cams, lms, hist = lm.lm_solve(p, lm.Options(lambda0=1e-320, max_lm=6))
+    h0 = hist[0]
+    assert h0["not_spd"] and not h0["accepted"] and np.isnan(h0["cost_after"])
+    assert hist[1]["lam"] == lm.LAMBDA_MIN and not hist[1]["not_spd"]
+    assert hist[1]["cost_before"] == h0["cost_before"]
+    assert any(h["accepted"] for h in hist[1:])
+    # the unobserved camera never moves: its damped block is lambda * 1e-6 * I, its rhs 0
+    assert np.array_equal(cams[4], p.cams0[4])
