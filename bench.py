@@ -62,6 +62,8 @@ def parse_args(argv=None):
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run only this many untimed LM steps (for ncu captures)")
     ap.add_argument("--profile-precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="profile mode on the 256-problem batch instead of the single problem")
     return ap.parse_args(argv)
 
 
@@ -228,9 +230,15 @@ def run_poba(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     if args.profile_steps:
-        h = make(poba.BA_FP64 if args.profile_precision == "fp64" else poba.BA_FP32_BULK)
-        for _ in range(args.profile_steps):
-            poba.ba_lm_step(h)
+        prec = poba.BA_FP64 if args.profile_precision == "fp64" else poba.BA_FP32_BULK
+        if args.profile_batch:
+            hb = poba.batch_from_problems(bal_synth.make_batch(256), precision=prec, stream=stream)
+            for _ in range(args.profile_steps):
+                poba.ba_lm_step_batch(hb)
+        else:
+            h = make(prec)
+            for _ in range(args.profile_steps):
+                poba.ba_lm_step(h)
         torch.cuda.synchronize()
         return
 
