@@ -79,7 +79,11 @@ typedef struct {
   int32_t series_exec;  /* how the series loop runs: 0 one launch per kernel, 1 the same launches
                            replayed as a captured CUDA graph, 2 one persistent cooperative kernel
                            for all terms with bounded grid barriers (default; falls back to 1
-                           when the device cannot make all its blocks co-resident) */
+                           when the device cannot make all its blocks co-resident); in
+                           BA_FP32_BULK mode it stages each tile's inputs with asynchronous
+                           bulk copies issued ahead of the tile (when every tile has at most
+                           128 distinct cameras), 3 the persistent kernel without that
+                           pipeline.  All modes give bitwise-equal results. */
 } ba_options;
 
 typedef struct {
@@ -282,10 +286,11 @@ ba_status ba_cost_batch(ba_handle* h, double* costs);
 /* Free all device memory of the handle (and its own stream, if it created one). NULL is OK. */
 ba_status ba_destroy(ba_handle* h);
 
-/* Phase timeline of the last persistent series solve (series_exec 2): for each executed term
- * (at most 64), five %globaltimer readings in ns taken by block 0 -- term start, end of its
- * tile phase, release of the first grid barrier, end of its camera phase, release of the
- * second barrier.  Copies min(capacity, 5 * terms) values; *n_terms receives the terms. */
+/* Phase timeline of the last persistent series solve (series_exec 2 or 3): for each executed term
+ * (at most 64), five %globaltimer readings in ns taken by the last block of the grid (a block
+ * that always has camera work) -- term start, end of its tile phase, release of the first grid
+ * barrier, end of its camera phase, release of the second barrier.  Copies min(capacity,
+ * 5 * terms) values; *n_terms receives the terms. */
 ba_status ba_get_series_trace(ba_handle* h, int64_t* ns, int32_t capacity, int32_t* n_terms);
 
 /* Test hook for the bounded grid barriers: the limit, in GPU clock cycles, that a block of the

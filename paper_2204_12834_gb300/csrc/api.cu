@@ -71,7 +71,7 @@ struct ba_handle {
   void* J = nullptr;
   void* r = nullptr;
   void* partial = nullptr;
-  void* t_cm = nullptr;  // current series term per camera-major slot row (bulk precision)
+  void* t_cam = nullptr;  // current series term per camera-major slot row (bulk precision)
   double* U45 = nullptr;
   double* b_p = nullptr;
   double* V = nullptr;
@@ -89,7 +89,10 @@ struct ba_handle {
   double* scalars = nullptr;      // [0] lambda for explicit solves, [1] cost out
   double* prob_cost = nullptr;    // [n_probs] F per problem (ba_cost_batch)
   GridSync* gs = nullptr;         // persistent kernel: grid-barrier state
-  long long* trace = nullptr;     // persistent kernel: phase timeline of block 0
+  int4* tile_list = nullptr;      // batches: descriptors of the tiles taking part in a solve
+  int32_t* list_off = nullptr;    // batches: [n_probs] scratch of the tile-list scan
+  int32_t* n_tiles_dev = nullptr; // one int: n_tiles (the tile list of a single problem)
+  long long* trace = nullptr;     // persistent kernel: phase timeline of its last block
   SeriesState* st = nullptr;      // [n_probs]
   SeriesGlobal* sgl = nullptr;
   LmRecord* rec = nullptr;        // [n_probs]
@@ -117,6 +120,8 @@ struct ba_handle {
   bool graph_timing = false;
   bool graph_active = false;
   int persist_grid = 0;                  // blocks of the persistent kernel (0: unavailable)
+  int pipe_grid = 0;                     // blocks of the pipelined FP32 kernel (0: not used)
+  CamRounds persist_rounds{}, pipe_rounds{};  // camera schedules for those grids
   long long barrier_timeout = 1LL << 33;  // clock cycles a block waits at a grid barrier
   int last_exec = -1;                    // series_exec of the last solve
   uint64_t launches = 0;
@@ -142,7 +147,7 @@ bool valid_options(const ba_options& o, std::string* why) {
   if (o.max_lm < 0 || o.max_lm > 100000) { *why = "max_lm out of range"; return false; }
   if (o.max_inner < 0 || o.max_inner > 10000) { *why = "max_inner out of range [0, 10000]"; return false; }
   if (o.damping_mode != 0 && o.damping_mode != 1) { *why = "damping_mode must be 0 or 1"; return false; }
-  if (o.series_exec < 0 || o.series_exec > 2) { *why = "series_exec must be 0, 1 or 2"; return false; }
+  if (o.series_exec < 0 || o.series_exec > 3) { *why = "series_exec must be 0, 1, 2 or 3"; return false; }
   return true;
 }
 
@@ -218,7 +223,7 @@ void collect_timing(ba_handle* h, int terms_run, bool series_ran) {
     }
     h->pending[cls] = false;
   }
-  if (series_ran && h->last_exec == 2) {
+  if (series_ran && h->last_exec >= 2) {
     // one pair around the persistent kernel, counted once per executed term
     const int i = ev_index(h, kTTile, 1);
     if (terms_run >= 1 && cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) == cudaSuccess) {
@@ -268,14 +273,14 @@ void seq_series_body(ba_handle* h, cudaStream_t s, bool use_active) {
   launch_series_reset(h->st, h->sgl, use_active ? h->rec : nullptr, h->n_probs, s);
   tmark(h, kTRhs, 0, 0);
   launch_tile_rhs<T>(tp, J, h->b_l, Vi, part, h->st, s);
-  launch_camera_rhs<T>(tp, part, h->b_p, h->Uinv, h->x, (T*)h->t_cm, h->cam_norm, h->st, h->sgl, s);
+  launch_camera_rhs<T>(tp, part, h->b_p, h->Uinv, h->x, (T*)h->t_cam, h->cam_norm, h->st, h->sgl, s);
   tmark(h, kTRhs, 0, 1);
   for (int i = 1; i <= h->opts.max_inner; ++i) {
     tmark(h, kTTile, i, 0);
-    launch_tile_series<T>(tp, J, (const T*)h->t_cm, Vi, part, h->st, h->sgl, s);
+    launch_tile_series<T>(tp, J, (const T*)h->t_cam, Vi, part, h->st, h->sgl, s);
     tmark(h, kTTile, i, 1);
     tmark(h, kTCam, i, 0);
-    launch_camera_series<T>(tp, part, h->Uinv, h->x, (T*)h->t_cm, h->cam_norm, h->st, h->sgl, i,
+    launch_camera_series<T>(tp, part, h->Uinv, h->x, (T*)h->t_cam, h->cam_norm, h->st, h->sgl, i,
                             h->opts.eps, s);
     tmark(h, kTCam, i, 1);
   }
@@ -287,7 +292,7 @@ void seq_series_body(ba_handle* h, cudaStream_t s, bool use_active) {
 int series_body_kernels(const ba_handle* h) { return 4 + 2 * h->opts.max_inner; }
 
 template <typename T>
-ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active) {
+ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active, bool pipelined) {
   const Topology& tp = h->tp;
   const T* J = (const T*)h->J;
   const T* Vi = h->f32() ? (const T*)(const void*)h->Vinv_f : (const T*)(const void*)h->Vinv;
@@ -295,20 +300,43 @@ ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active) {
   launch_series_reset(h->st, h->sgl, use_active ? h->rec : nullptr, h->n_probs, s);
   tmark(h, kTRhs, 0, 0);
   launch_tile_rhs<T>(tp, J, h->b_l, Vi, part, h->st, s);
-  launch_camera_rhs<T>(tp, part, h->b_p, h->Uinv, h->x, (T*)h->t_cm, h->cam_norm, h->st, h->sgl, s);
+  launch_camera_rhs<T>(tp, part, h->b_p, h->Uinv, h->x, (T*)h->t_cam, h->cam_norm, h->st, h->sgl, s);
   tmark(h, kTRhs, 0, 1);
+  h->launches += 4;  // reset, the two RHS kernels, back-substitution
   CK(cudaMemsetAsync(h->gs, 0, sizeof(GridSync), s));
   if (h->opts.max_inner > 0) {
-    tmark(h, kTTile, 1, 0);
-    CK(launch_series_persistent<T>(tp, h->persist_grid, J, Vi, h->Uinv, h->x, (T*)h->t_cm, part,
-                                   h->cam_norm, h->st, h->sgl, h->gs, h->opts.max_inner,
-                                   h->opts.eps, h->barrier_timeout, h->trace, s));
-    tmark(h, kTTile, 1, 1);
+    if constexpr (sizeof(T) == 4) {
+      if (pipelined) {
+        const int4* list = tp.tile_desc;
+        const int* n_list = h->n_tiles_dev;
+        if (h->n_probs > 1) {
+          launch_active_tiles(tp, h->st, h->list_off, h->tile_list, h->sgl, s);
+          h->launches += 2;
+          list = h->tile_list;
+          n_list = &h->sgl->n_list;
+        }
+        tmark(h, kTTile, 1, 0);
+        CK(launch_series_pipelined(tp, h->pipe_rounds, h->pipe_grid, list, n_list, J, Vi, h->Uinv, h->x,
+                                   (float*)h->t_cam, part, h->cam_norm, h->st, h->sgl, h->gs,
+                                   h->opts.max_inner, h->opts.eps, h->barrier_timeout, h->trace,
+                                   s));
+        tmark(h, kTTile, 1, 1);
+        h->launches += 1;
+      }
+    }
+    if (!pipelined) {
+      tmark(h, kTTile, 1, 0);
+      CK(launch_series_persistent<T>(tp, h->persist_rounds, h->persist_grid, J, Vi, h->Uinv, h->x,
+                                     (T*)h->t_cam, part,
+                                     h->cam_norm, h->st, h->sgl, h->gs, h->opts.max_inner,
+                                     h->opts.eps, h->barrier_timeout, h->trace, s));
+      tmark(h, kTTile, 1, 1);
+      h->launches += 1;
+    }
   }
   tmark(h, kTBack, 0, 0);
   launch_tile_backsub<T>(tp, J, (const T*)h->r, h->x, h->b_l, Vi, h->dx_l, h->block_pred, s);
   tmark(h, kTBack, 0, 1);
-  h->launches += 5;
   return BA_OK;
 }
 
@@ -319,11 +347,13 @@ ba_status run_series_body(ba_handle* h, bool use_active) {
     if (st != BA_OK) return st;
   }
   int mode = h->opts.series_exec;
-  if (mode == 2 && h->persist_grid <= 0) mode = 1;
+  if (mode >= 2 && h->persist_grid <= 0) mode = 1;
   h->last_exec = mode;
-  if (mode == 2) {
-    ba_status st = h->f32() ? seq_series_persistent<float>(h, s, use_active)
-                            : seq_series_persistent<double>(h, s, use_active);
+  if (mode >= 2) {
+    // series_exec 2: FP32-bulk takes the pipelined kernel where it applies; 3: never
+    const bool pipelined = mode == 2 && h->f32() && h->pipe_grid > 0;
+    ba_status st = h->f32() ? seq_series_persistent<float>(h, s, use_active, pipelined)
+                            : seq_series_persistent<double>(h, s, use_active, false);
     if (st == BA_OK) h->pending[kTRhs] = h->pending[kTBack] = h->timing;
     return st;
   }
@@ -547,6 +577,27 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   std::vector<int32_t> tile_prob(S.n_tiles);
   for (int t = 0; t < S.n_tiles; ++t) tile_prob[t] = S.lm_prob[S.tile_lm0[t]];
 
+  {
+    // persistent series kernels: all blocks must be co-resident (cooperative launch)
+    int dev = 0, sms = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    const int per_sm = persistent_blocks_per_sm(h->f32());
+    h->persist_grid = (coop && per_sm > 0) ? per_sm * sms : 0;
+    if (h->f32() && h->persist_grid > 0 && S.max_slots_per_tile <= kTileSlots) {
+      const int pipe_per_sm = pipelined_blocks_per_sm();
+      h->pipe_grid = pipe_per_sm > 0 ? pipe_per_sm * sms : 0;
+    }
+    cudaGetLastError();
+  }
+  // camera schedule of the persistent kernels (rounds per grid size)
+  CamSchedule cs;
+  build_cam_schedule(S, &cs);
+  CamRoundList rl_p, rl_q;
+  if (h->persist_grid > 0) build_cam_rounds(cs, nc, h->persist_grid, &rl_p);
+  if (h->pipe_grid > 0) build_cam_rounds(cs, nc, h->pipe_grid, &rl_q);
+
   // ---- arena layout
   const size_t bulk = h->f32() ? sizeof(float) : sizeof(double);
   struct Item { void** ptr; size_t bytes; };
@@ -583,7 +634,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   items.push_back({&h->J, bulk * 24 * h->n_o_pad});
   items.push_back({&h->r, bulk * 2 * h->n_o_pad});
   items.push_back({&h->partial, bulk * kLinVals * slots});
-  items.push_back({&h->t_cm, bulk * 9 * slots});
+  items.push_back({&h->t_cam, bulk * kTStride * nc});
   items.push_back({(void**)&h->U45, sizeof(double) * nc * 45});
   items.push_back({(void**)&h->b_p, sizeof(double) * nc * 9});
   items.push_back({(void**)&h->V, sizeof(double) * nl * 6});
@@ -600,6 +651,24 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   items.push_back({(void**)&h->scalars, sizeof(double) * 4});
   items.push_back({(void**)&h->prob_cost, sizeof(double) * P});
   items.push_back({(void**)&h->gs, sizeof(GridSync)});
+  uint8_t* d_tile_rec = nullptr;
+  items.push_back({(void**)&d_tile_rec, S.tile_rec.size() > 0 ? S.tile_rec.size() : 16});
+  items.push_back({(void**)&h->n_tiles_dev, sizeof(int32_t)});
+  int32_t *d_cam_item, *d_item_q;
+  int32_t* d_rl[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  const CamRoundList* rls[2] = {&rl_p, &rl_q};
+  items.push_back({(void**)&d_cam_item, sizeof(int32_t) * cs.cam_item.size()});
+  items.push_back({(void**)&d_item_q, sizeof(int32_t) * (cs.item_q.size() > 0 ? cs.item_q.size() : 1)});
+  for (int g = 0; g < 2; ++g) {
+    if (rls[g]->round_cam.empty()) continue;
+    items.push_back({(void**)&d_rl[g][0], sizeof(int32_t) * rls[g]->round_cam.size()});
+    items.push_back({(void**)&d_rl[g][1], sizeof(int32_t) * rls[g]->round_item.size()});
+    items.push_back({(void**)&d_rl[g][2], sizeof(int32_t) * rls[g]->block_round.size()});
+  }
+  if (n_probs > 1) {
+    items.push_back({(void**)&h->tile_list, sizeof(int4) * 2 * (size_t)S.n_tiles});
+    items.push_back({(void**)&h->list_off, sizeof(int32_t) * P});
+  }
   items.push_back({(void**)&h->trace, sizeof(long long) * kTraceTerms * kTracePoints});
   items.push_back({(void**)&h->st, sizeof(SeriesState) * P});
   items.push_back({(void**)&h->sgl, sizeof(SeriesGlobal)});
@@ -671,6 +740,16 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
       {d_tile_prob, tile_prob.data(), sizeof(int32_t) * S.n_tiles},
       {d_cam_off, S.cam_off.data(), sizeof(int32_t) * (P + 1)},
       {d_tile_off, S.tile_off.data(), sizeof(int32_t) * (P + 1)},
+      {d_tile_rec, S.tile_rec.data(), S.tile_rec.size()},
+      {h->n_tiles_dev, &S.n_tiles, sizeof(int32_t)},
+      {d_cam_item, cs.cam_item.data(), sizeof(int32_t) * cs.cam_item.size()},
+      {d_item_q, cs.item_q.data(), sizeof(int32_t) * cs.item_q.size()},
+      {d_rl[0][0], rl_p.round_cam.data(), sizeof(int32_t) * rl_p.round_cam.size()},
+      {d_rl[0][1], rl_p.round_item.data(), sizeof(int32_t) * rl_p.round_item.size()},
+      {d_rl[0][2], rl_p.block_round.data(), sizeof(int32_t) * rl_p.block_round.size()},
+      {d_rl[1][0], rl_q.round_cam.data(), sizeof(int32_t) * rl_q.round_cam.size()},
+      {d_rl[1][1], rl_q.round_item.data(), sizeof(int32_t) * rl_q.round_item.size()},
+      {d_rl[1][2], rl_q.block_round.data(), sizeof(int32_t) * rl_q.block_round.size()},
       {h->obs, obs_s.data(), sizeof(double) * 2 * no},
       {h->cams, cams.data(), sizeof(double) * nc * 9},
       {h->lms, lms_i.data(), sizeof(double) * nl * 3},
@@ -680,16 +759,6 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
     if (u.bytes == 0) continue;
     e = cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMemcpy(upload)"));
-  }
-  {
-    // persistent series kernel: all blocks must be co-resident (cooperative launch)
-    int dev = 0, sms = 0, coop = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    const int per_sm = persistent_blocks_per_sm(h->f32());
-    h->persist_grid = (coop && per_sm > 0) ? per_sm * sms : 0;
-    cudaGetLastError();
   }
   {
     std::vector<LmRecord> r0(P);
@@ -729,6 +798,9 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   tp.tile_prob = d_tile_prob;
   tp.cam_off = d_cam_off;
   tp.tile_off = d_tile_off;
+  tp.tile_rec = d_tile_rec;
+  h->persist_rounds = CamRounds{d_cam_item, d_item_q, d_rl[0][0], d_rl[0][1], d_rl[0][2]};
+  h->pipe_rounds = CamRounds{d_cam_item, d_item_q, d_rl[1][0], d_rl[1][1], d_rl[1][2]};
   *out = h;
   g_last_error.clear();
   return BA_OK;
@@ -794,7 +866,7 @@ ba_status lm_iteration(ba_handle* h, bool batch) {
   CK(cudaMemcpyAsync(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   collect_timing(h, max_terms(h), true);
-  if (h->last_exec == 2 && h->h_gs->error)
+  if (h->last_exec >= 2 && h->h_gs->error)
     return fail(BA_ERR_TIMEOUT, "a grid barrier of the persistent series kernel timed out");
   // one linearisation covers every problem: it is stale once any problem moved
   for (size_t p = 0; p < P; ++p)
@@ -878,7 +950,7 @@ ba_status ba_solve_schur_power(ba_handle* h, double lambda, ba_series_info* info
   CK(cudaMemcpyAsync(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   collect_timing(h, max_terms(h), true);
-  if (h->last_exec == 2 && h->h_gs->error)
+  if (h->last_exec >= 2 && h->h_gs->error)
     return fail(BA_ERR_TIMEOUT, "a grid barrier of the persistent series kernel timed out");
   if (P == 1) {
     fill_series_info(h->h_st[0], lambda, info);
@@ -1167,7 +1239,7 @@ ba_status ba_get_series_trace(ba_handle* h, int64_t* ns, int32_t capacity, int32
   if (!h || !ns || capacity < 0) return fail(BA_ERR_INVALID_ARG, "bad argument");
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(h->h_st, h->st, sizeof(SeriesState) * h->n_probs, cudaMemcpyDeviceToHost));
-  int terms = h->last_exec == 2 ? max_terms(h) : 0;
+  int terms = h->last_exec >= 2 ? max_terms(h) : 0;
   if (terms > kTraceTerms) terms = kTraceTerms;
   const int n = terms * kTracePoints < capacity ? terms * kTracePoints : capacity;
   if (n > 0) CK(cudaMemcpy(ns, h->trace, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));

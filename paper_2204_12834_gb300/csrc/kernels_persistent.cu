@@ -84,44 +84,216 @@ __device__ __forceinline__ bool barrier_wait(GridSync* gs, unsigned gen, long lo
   return *s_ok != 0;
 }
 
+// Phase B of a term: block b runs the rounds [block_round[b], block_round[b + 1]) of the camera
+// schedule.  In a round, thread (item, k) sums component k of one chunk of slot rows; then
+// thread (camera, k) adds its camera's chunk sums in chunk order, applies row k of U^-1, updates
+// x and writes the new term t_cam[c] and the camera's norm pair -- the same sums in the same
+// order as camera_body.  The block's first round is fixed for the whole launch: its item
+// bounds, cameras and the cameras' x stay in registers (x is written back at the end), so a
+// term's chain of dependent loads there is the chunk rows and the done flag.  Later rounds (a
+// block has several when cameras outnumber the grid) load their indices each term; every load
+// that does not depend on the chunk sums is issued at the start of the round.  Shared scratch
+// (doubles): pc[kRoundItems][9], ys[kRoundItems][9], y2[kRoundItems][9].
+constexpr int kCamScratchBytes = 3 * kRoundItems * 9 * 8;
+
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Row k of camera c's U^-1 (read-only during the launch) toward L1 ahead of its use.
+__device__ __forceinline__ void prefetch_uinv_row(const double* __restrict__ Uinv, int c, int k) {
+  const double* r = Uinv + (size_t)c * 81 + k * 9;
+  prefetch_l1(r);
+  prefetch_l1(r + 8);
+}
+
+struct RoundCache {  // in shared memory
+  int rd, nc, ni;                 // the block's first round (rd = -1: none), its cameras, items
+  int q[kRoundItems][2];          // item rows
+  int cam[kRoundItems][4];        // camera, its items (round-relative), problem
+  double x[kRoundItems][9];       // the cameras' x
+};
+
+__device__ __forceinline__ void round_cache(const Topology& tp, const CamRounds& cr,
+                                            const double* __restrict__ x, RoundCache& rc) {
+  const int it = threadIdx.x / 9, k = threadIdx.x - it * 9;
+  const int rd = cr.block_round[blockIdx.x] < cr.block_round[blockIdx.x + 1]
+                     ? cr.block_round[blockIdx.x] : -1;
+  if (threadIdx.x == 0) rc.rd = rd;
+  if (rd >= 0) {
+    const int c0 = cr.round_cam[rd], i0 = cr.round_item[rd];
+    const int nc = cr.round_cam[rd + 1] - c0, ni = cr.round_item[rd + 1] - i0;
+    if (threadIdx.x == 0) {
+      rc.nc = nc;
+      rc.ni = ni;
+    }
+    if (it < ni && k < 2) rc.q[it][k] = cr.item_q[2 * (i0 + it) + k];
+    if (it < nc) {
+      const int c = c0 + it;
+      if (k == 0) rc.cam[it][0] = c;
+      if (k == 1) rc.cam[it][1] = cr.cam_item[c] - i0;
+      if (k == 2) rc.cam[it][2] = cr.cam_item[c + 1] - i0;
+      if (k == 3) rc.cam[it][3] = tp.cam_prob[c];
+      rc.x[it][k] = x[(size_t)c * 9 + k];
+    }
+  }
+  __syncthreads();
+}
+
+// Combination, U^-1 and norms of one round (after the chunk sums are in pc).
+template <typename T>
+__device__ __forceinline__ double round_finish(bool cam, bool run, int c, int ia, int ib,
+                                               const double* __restrict__ Uinv, double xo,
+                                               T* __restrict__ t_cam,
+                                               double* __restrict__ cam_norm, double (*pc)[9],
+                                               double (*ys)[9], double (*y2)[9]) {
+  const int it = threadIdx.x / 9, k = threadIdx.x - it * 9;
+  double y = 0.0;
+  if (run)
+    for (int j = ia; j < ib; ++j) y += pc[j][k];
+  if (cam) ys[it][k] = y;
+  __syncthreads();
+  double v = 0.0, xv = 0.0;
+  if (run) {
+    const double* ui = Uinv + (size_t)c * 81 + k * 9;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) v += __ldg(ui + j) * ys[it][j];
+    xv = xo + v;
+    t_cam[(size_t)c * kTStride + k] = (T)v;
+  }
+  __syncthreads();
+  if (cam) {
+    ys[it][k] = v * v;
+    y2[it][k] = xv * xv;
+  }
+  __syncthreads();
+  if (run && k == 0) {
+    double a = 0.0, b = 0.0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      a += ys[it][j];
+      b += y2[it][j];
+    }
+    cam_norm[2 * c + 0] = a;
+    cam_norm[2 * c + 1] = b;
+  }
+  __syncthreads();
+  return run ? xv : xo;
+}
+
+template <typename T>
+__device__ __forceinline__ void camera_phase(const Topology& tp, const CamRounds& cr,
+                                             RoundCache& rc, const T* __restrict__ partial,
+                                             const double* __restrict__ Uinv,
+                                             double* __restrict__ x, T* __restrict__ t_cam,
+                                             double* __restrict__ cam_norm,
+                                             const SeriesState* st, double* scratch) {
+  double (*pc)[9] = reinterpret_cast<double (*)[9]>(scratch);
+  double (*ys)[9] = pc + kRoundItems;
+  double (*y2)[9] = ys + kRoundItems;
+  const int tid = threadIdx.x;
+  const int it = tid / 9, k = tid - it * 9;
+  if (rc.rd < 0) return;
+  {
+    // the cached first round
+    const bool cam = it < rc.nc;
+    int c = 0, done = 1;
+    if (cam) {
+      c = rc.cam[it][0];
+      prefetch_uinv_row(Uinv, c, k);
+      done = ld_volatile(&st[rc.cam[it][3]].done);
+    }
+    if (it < rc.ni) pc[it][k] = cam_chunk_sum(partial, rc.q[it][0], rc.q[it][1], k);
+    __syncthreads();
+    const double xo = cam ? rc.x[it][k] : 0.0;
+    const double xv = round_finish<T>(cam, cam && !done, c, cam ? rc.cam[it][1] : 0,
+                                      cam ? rc.cam[it][2] : 0, Uinv, xo, t_cam, cam_norm, pc,
+                                      ys, y2);
+    if (cam) rc.x[it][k] = xv;
+  }
+  for (int rd = rc.rd + 1; rd < cr.block_round[blockIdx.x + 1]; ++rd) {
+    const int c0 = cr.round_cam[rd], nc = cr.round_cam[rd + 1] - c0;
+    const int i0 = cr.round_item[rd], ni = cr.round_item[rd + 1] - i0;
+    const int c = c0 + it;
+    const bool cam = it < nc;
+    double xo = 0.0;
+    int ia = 0, ib = 0, done = 1;
+    if (cam) {
+      prefetch_uinv_row(Uinv, c, k);
+      xo = __ldcg(x + (size_t)c * 9 + k);
+      ia = cr.cam_item[c] - i0;
+      ib = cr.cam_item[c + 1] - i0;
+      done = ld_volatile(&st[tp.cam_prob[c]].done);
+    }
+    if (it < ni) {
+      const int q0 = cr.item_q[2 * (i0 + it)], q1 = cr.item_q[2 * (i0 + it) + 1];
+      pc[it][k] = cam_chunk_sum(partial, q0, q1, k);
+    }
+    __syncthreads();
+    const bool run = cam && !done;
+    const double xv = round_finish<T>(cam, run, c, ia, ib, Uinv, xo, t_cam, cam_norm, pc, ys, y2);
+    if (run) x[(size_t)c * 9 + k] = xv;
+  }
+}
+
+// The cached first round's x back to memory (end of the launch).
+__device__ __forceinline__ void round_writeback(const RoundCache& rc, double* __restrict__ x) {
+  const int it = threadIdx.x / 9, k = threadIdx.x - it * 9;
+  if (rc.rd >= 0 && it < rc.nc) x[(size_t)rc.cam[it][0] * 9 + k] = rc.x[it][k];
+}
+
+// Barrier 2 of a term: the last block opens it, then applies every running problem's stop rule
+// for term i (visible to every block before the next barrier).  False: this block must leave
+// (a wait timed out or another block failed).
+__device__ __forceinline__ bool term_end_barrier(const Topology& tp, GridSync* gs,
+                                                 const double* cam_norm, SeriesState* st,
+                                                 SeriesGlobal* sgl, int i, double eps,
+                                                 long long timeout, int* s_last, unsigned* s_gen,
+                                                 int* s_ok, int* s_running) {
+  unsigned gen;
+  if (barrier_arrive(gs, gridDim.x, &gen, s_last, s_gen)) {
+    if (threadIdx.x == 0) barrier_release(gs);
+    __threadfence();
+    problems_stop_rule(tp, cam_norm, st, sgl, i, eps, s_running);
+    return true;
+  }
+  return barrier_wait(gs, gen, timeout, s_ok);
+}
+
+// Barrier 1 of a term (after the tile phase): the last block resets the tile counter.
+__device__ __forceinline__ bool tile_end_barrier(GridSync* gs, long long timeout, int* s_last,
+                                                 unsigned* s_gen, int* s_ok) {
+  unsigned gen;
+  if (barrier_arrive(gs, gridDim.x, &gen, s_last, s_gen)) {
+    if (threadIdx.x == 0) {
+      gs->tile_next = 0u;
+      barrier_release(gs);
+    }
+    return true;
+  }
+  return barrier_wait(gs, gen, timeout, s_ok);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kTileObs, 3) series_persistent_kernel(
-    Topology tp, const T* __restrict__ J, const T* __restrict__ Vinv,
-    const double* __restrict__ Uinv, double* __restrict__ x, T* __restrict__ t_cm,
+    Topology tp, CamRounds cr, const T* __restrict__ J, const T* __restrict__ Vinv,
+    const double* __restrict__ Uinv, double* __restrict__ x, T* __restrict__ t_cam,
     T* __restrict__ partial, double* __restrict__ cam_norm, SeriesState* __restrict__ st,
     SeriesGlobal* __restrict__ sgl, GridSync* __restrict__ gs, int m_max, double eps,
     long long timeout, long long* __restrict__ trace) {
   __shared__ TileSmem<T> sm;
   __shared__ int s_tile, s_last, s_ok, s_done, s_running;
   __shared__ unsigned s_gen;
+  static_assert(kCamScratchBytes <= sizeof(sm.sg), "phase B scratch fits in sg");
   const int tid = threadIdx.x;
-  const unsigned G = gridDim.x;
-  // camera groups: spread over every block (cameras per group = ceil(n_cams / blocks), at most
-  // blockDim / 9), so the FP64 camera work of a term runs on all SMs at once
-  const int cap = kTileObs / 9;
-  int per_group = (tp.n_cams + (int)G - 1) / (int)G;
-  per_group = per_group < 1 ? 1 : (per_group > cap ? cap : per_group);
-  const int n_groups = (tp.n_cams + per_group - 1) / per_group;
-  double (*ys)[9] = reinterpret_cast<double (*)[9]>(&sm.sg[0][0]);  // phase B reuses sg
-  double (*y2)[9] = ys + cap;
+  double* scratch = reinterpret_cast<double*>(&sm.sg[0][0]);  // phase B reuses sg
 
   if (tid == 0) s_done = ld_volatile(&sgl->all_done);  // every x(0) = 0: nothing to do
   __syncthreads();
   if (s_done) return;
-  // the block's first camera group is fixed for the whole launch: keep its slot-row range and
-  // its components of x in registers (x is written back once at the end)
-  const int c_cl = tid / 9, ck = tid - c_cl * 9;
-  const int c0 = blockIdx.x * per_group + c_cl;
-  const bool c_mine = (int)blockIdx.x < n_groups && c_cl < per_group && c0 < tp.n_cams;
-  int c_r0 = 0, c_r1 = 0, c_prob = 0;
-  double x_reg = 0.0;
-  if (c_mine) {
-    c_r0 = tp.cam_slot_ptr[c0];
-    c_r1 = tp.cam_slot_ptr[c0 + 1];
-    c_prob = tp.cam_prob[c0];
-    x_reg = x[(size_t)c0 * 9 + ck];
-  }
-  const bool tracer = blockIdx.x == 0 && tid == 0 && trace != nullptr;
+  __shared__ RoundCache rc;
+  round_cache(tp, cr, x, rc);
+  const bool tracer = blockIdx.x == gridDim.x - 1 && tid == 0 && trace != nullptr;
   for (int i = 1; i <= m_max; ++i) {
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 0] = global_ns();
     // ---- phase A: tiles (the next tile index is fetched while the current one is processed;
@@ -144,88 +316,336 @@ __global__ void __launch_bounds__(kTileObs, 3) series_persistent_kernel(
       __syncthreads();
       if (tile >= tp.n_tiles) break;
       if constexpr (sizeof(T) == 4)
-        tile_matvec_body_f32<kModeSeries>(tp, tile, J, t_cm, nullptr, Vinv, partial, sm);
+        tile_matvec_body_f32<kModeSeries>(tp, tile, J, t_cam, nullptr, Vinv, partial, sm);
       else
-        tile_matvec_body<T, kModeSeries>(tp, tile, J, t_cm, nullptr, Vinv, partial, sm);
+        tile_matvec_body<T, kModeSeries>(tp, tile, J, t_cam, nullptr, Vinv, partial, sm);
     }
-    unsigned gen;
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 1] = global_ns();
-    if (barrier_arrive(gs, G, &gen, &s_last, &s_gen)) {
-      if (tid == 0) {
-        gs->tile_next = 0u;
-        barrier_release(gs);
-      }
-    } else if (!barrier_wait(gs, gen, timeout, &s_ok)) {
-      return;
-    }
+    if (!tile_end_barrier(gs, timeout, &s_last, &s_gen, &s_ok)) return;
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 2] = global_ns();
     if (tid == 0) s_done = ld_volatile(&sgl->all_done);
     __syncthreads();
     if (s_done) break;  // every problem's rule fired at term i - 1 or earlier
-    // ---- phase B: cameras (the block's first group uses the cached rows and x)
-    for (int g = blockIdx.x; g < n_groups; g += G) {
-      if (g == (int)blockIdx.x) {
-        const bool run = c_mine && !ld_volatile(&st[c_prob].done);
-        double ui[9];
-        if (run) {
-#pragma unroll
-          for (int j = 0; j < 9; ++j) ui[j] = Uinv[(size_t)c0 * 81 + ck * 9 + j];
-        }
-        double y = 0.0;
-        if (run) {
-          for (int rb = c_r0; rb < c_r1; rb += 8) {
-            T buf[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) buf[j] = (rb + j < c_r1) ? __ldcg(partial + (size_t)(rb + j) * 9 + ck) : (T)0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) y += (double)buf[j];
-          }
-        }
-        if (c_cl < per_group) ys[c_cl][ck] = y;
-        __syncthreads();
-        double v = 0.0;
-        if (run) {
-#pragma unroll
-          for (int j = 0; j < 9; ++j) v += ui[j] * ys[c_cl][j];
-          x_reg += v;
-          const T tv = (T)v;
-          for (int q = c_r0; q < c_r1; ++q) t_cm[(size_t)q * 9 + ck] = tv;
-        }
-        __syncthreads();
-        if (c_cl < per_group) {
-          ys[c_cl][ck] = v * v;
-          y2[c_cl][ck] = x_reg * x_reg;
-        }
-        __syncthreads();
-        if (run && ck == 0) {
-          double a = 0.0, b = 0.0;
-#pragma unroll
-          for (int j = 0; j < 9; ++j) {
-            a += ys[c_cl][j];
-            b += y2[c_cl][j];
-          }
-          cam_norm[2 * c0 + 0] = a;
-          cam_norm[2 * c0 + 1] = b;
-        }
-        __syncthreads();
-      } else {
-        camera_body<T, kModeSeries>(tp, g * per_group, per_group, partial, nullptr, Uinv, x, t_cm,
-                                    st, cam_norm, ys, y2);
-      }
-    }
+    // ---- phase B: cameras
+    camera_phase<T>(tp, cr, rc, partial, Uinv, x, t_cam, cam_norm, st, scratch);
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 3] = global_ns();
-    if (barrier_arrive(gs, G, &gen, &s_last, &s_gen)) {
-      // last block: open the barrier, then every running problem's norms (camera order) and its
-      // stop rule for term i (visible to every block before the next barrier)
-      if (tid == 0) barrier_release(gs);
-      __threadfence();
-      problems_stop_rule(tp, cam_norm, st, sgl, i, eps, &s_running);
-    } else if (!barrier_wait(gs, gen, timeout, &s_ok)) {
+    if (!term_end_barrier(tp, gs, cam_norm, st, sgl, i, eps, timeout, &s_last, &s_gen, &s_ok,
+                          &s_running))
       return;
-    }
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 4] = global_ns();
   }
-  if (c_mine) x[(size_t)c0 * 9 + ck] = x_reg;
+  round_writeback(rc, x);
+}
+
+// ---------------------------------------------------------------------------------------
+// FP32-bulk persistent kernel with a software-pipelined tile phase.  The tile body is the one
+// of the per-term kernel (f32_tile_core: the same sums in the same order); what changes is how
+// a tile's inputs reach shared memory.  A block's tiles are claimed ahead and their inputs
+// arrive while earlier tiles compute:
+//   descriptor    32-byte asynchronous copy, three tiles ahead;
+//   index record  one bulk copy (cp.async.bulk, completion on an mbarrier), two tiles ahead;
+//   Jacobians     24 bulk copies (one per plane, the tile's range rounded out to 16 bytes), one
+//                 tile ahead, issued as soon as the current tile's J has moved to registers;
+//   t rows, V^-1  asynchronous copies issued in the middle of the previous tile, once its
+//                 index record (slot rows) has arrived.
+// The tiles come from a list of descriptors (the handle's tiles, or for a batch the tiles of
+// the problems taking part in the solve); any block may take any tile (one atomic ticket per
+// tile).  A block that finds no tile leaves the phase with nothing in flight.  Every mbarrier
+// wait is bounded (kCopyWaitCycles); a block that gives up sets the error flag, waits (bounded)
+// for the copies it started, and leaves; the others leave at their next grid barrier.
+constexpr int kJStage = kTileObs + 4;  // floats per staged plane: the tile range rounded out
+
+struct __align__(16) F32Pipe {
+  float sJ[24][kJStage];
+  uint8_t rec[3][kTileRecMax];
+  float tc[2][kTileSlots][kTStride];
+  float vi[2][kTileLms][6];
+  float sg[kTileObs][9];  // phase 1-2 v (as [.][3]), then the scatter; doubles in phase B
+  int4 desc[4][2];
+  unsigned long long mbJ;
+  unsigned long long mbR[3];
+};
+static_assert(offsetof(F32Pipe, rec) % 16 == 0 && offsetof(F32Pipe, tc) % 16 == 0 &&
+                  offsetof(F32Pipe, vi) % 16 == 0 && offsetof(F32Pipe, sg) % 16 == 0 &&
+                  offsetof(F32Pipe, desc) % 16 == 0 && offsetof(F32Pipe, mbJ) % 8 == 0,
+              "bulk-copy destinations must be 16-byte aligned");
+static_assert((kJStage * 4) % 16 == 0 && kTileRecMax % 16 == 0, "16-byte rows");
+static_assert(kCamScratchBytes <= sizeof(float) * kTileObs * 9, "phase B scratch fits in sg");
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* mb) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mb)) : "memory");
+}
+__device__ __forceinline__ void mbar_arm(unsigned long long* mb, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned long long* mb, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(mb)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bound on a wait for this block's own copies (about 4 s at 2 GHz).  Independent of the grid
+// barrier limit: a copy that was started is always waited for.
+constexpr long long kCopyWaitCycles = 1LL << 33;
+
+// Bounded wait for the phase with the given parity; false after `timeout` cycles.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* mb, unsigned parity,
+                                          long long timeout) {
+  const long long t0 = clock64();
+  while (!mbar_try(mb, parity))
+    if (clock64() - t0 > timeout) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* mb) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(mb))
+      : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Thread 0: bulk copies of the 24 Jacobian planes of the tile {o0, n} into sJ.
+__device__ __forceinline__ void issue_J(F32Pipe& S, const float* __restrict__ J, size_t pad,
+                                        int o0, int n) {
+  const int a0 = o0 & ~3, e = (o0 + n + 3) & ~3;
+  const unsigned bytes = (unsigned)(e - a0) * 4u;
+  mbar_arm(&S.mbJ, n > 0 ? 24u * bytes : 0u);
+  if (n > 0) {
+#pragma unroll 1
+    for (int p = 0; p < 24; ++p) bulk_g2s(&S.sJ[p][0], J + (size_t)p * pad + a0, bytes, &S.mbJ);
+  }
+}
+
+// Thread 0: bulk copy of a tile's index record into ring slot r.
+__device__ __forceinline__ void issue_rec(F32Pipe& S, const uint8_t* __restrict__ recs, int r,
+                                          const int4 (&d)[2]) {
+  const unsigned bytes = (unsigned)tile_rec_layout(d[0].w, d[1].y, d[0].y).bytes;
+  mbar_arm(&S.mbR[r], bytes);
+  bulk_g2s(&S.rec[r][0], recs + (size_t)d[1].z * 16, bytes, &S.mbR[r]);
+}
+
+__global__ void __launch_bounds__(kTileObs, 3) series_persistent_f32_kernel(
+    Topology tp, CamRounds cr, const int4* __restrict__ list, const int* __restrict__ n_list_p,
+    const float* __restrict__ J, const float* __restrict__ Vinv, const double* __restrict__ Uinv,
+    double* __restrict__ x, float* __restrict__ t_cam, float* __restrict__ partial,
+    double* __restrict__ cam_norm, SeriesState* __restrict__ st, SeriesGlobal* __restrict__ sgl,
+    GridSync* __restrict__ gs, int m_max, double eps, long long timeout,
+    long long* __restrict__ trace) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  F32Pipe& S = *reinterpret_cast<F32Pipe*>(dyn_smem);
+  __shared__ int s_last, s_ok, s_done, s_running, s_fail;
+  __shared__ int s_tk[4];  // tickets of the tiles in desc[] (>= n_list: none)
+  __shared__ unsigned s_gen;
+  const int tid = threadIdx.x;
+  const size_t pad = (size_t)tp.n_obs_pad;
+  double* scratch = reinterpret_cast<double*>(&S.sg[0][0]);  // phase B reuses sg
+  float (*sv)[3] = reinterpret_cast<float (*)[3]>(&S.sg[0][0]);
+
+  if (tid == 0) {
+    s_done = ld_volatile(&sgl->all_done);
+    s_fail = 0;
+    mbar_init(&S.mbJ);
+    for (int r = 0; r < 3; ++r) mbar_init(&S.mbR[r]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (s_done) return;
+  const int n_list = *n_list_p;
+  __shared__ RoundCache rc;
+  round_cache(tp, cr, x, rc);
+  unsigned parJ = 0u, parR = 0u;  // phase parity of mbJ and of mbR[0..2] (bit r)
+  unsigned pend = 0u;  // armed barriers not yet waited for (bit r: mbR[r], bit 3: mbJ)
+  const bool tracer = blockIdx.x == gridDim.x - 1 && tid == 0 && trace != nullptr;
+
+  for (int i = 1; i <= m_max; ++i) {
+    if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 0] = global_ns();
+    // ---- phase A, prologue: claim three tiles, fetch their descriptors, start the first
+    // two records and the first Jacobians
+    int tk_next = n_list;  // thread 0: ticket claimed for the slot after the last filled one
+    if (tid == 0) {
+      int t0 = n_list;
+      if (!ld_volatile(&sgl->all_done)) t0 = (int)atomicAdd(&gs->tile_next, 3u);
+      for (int q = 0; q < 3; ++q) {
+        const int tk = t0 + q < n_list ? t0 + q : n_list;
+        s_tk[q] = tk;
+        if (tk < n_list) {
+          cp_async16(&S.desc[q][0], list + 2 * (size_t)tk);
+          cp_async16(&S.desc[q][1], list + 2 * (size_t)tk + 1);
+        }
+      }
+      cp_async_wait_all();
+      if (t0 + 2 < n_list) tk_next = (int)atomicAdd(&gs->tile_next, 1u);
+      if (s_tk[0] < n_list) {
+        issue_rec(S, tp.tile_rec, 0, S.desc[0]);
+        issue_J(S, J, pad, S.desc[0][0].z, S.desc[0][0].w);
+        pend |= 9u;
+      }
+      if (s_tk[1] < n_list) {
+        issue_rec(S, tp.tile_rec, 1, S.desc[1]);
+        pend |= 2u;
+      }
+    }
+    __syncthreads();
+    if (s_tk[0] < n_list) {
+      // t rows and V^-1 of the first tile
+      const bool ok = mbar_wait(&S.mbR[0], parR & 1u, kCopyWaitCycles);
+      if (ok) {
+        parR ^= 1u;
+        pend &= ~1u;
+      } else {
+        s_fail = 1;
+      }
+      const int4 d0 = S.desc[0][0], d1 = S.desc[0][1];
+      const TileRecLayout g = tile_rec_layout(d0.w, d1.y, d0.y);
+      const int* scam = reinterpret_cast<const int*>(&S.rec[0][g.scam]);
+      if (ok && tid < d1.y) {  // the record's slot cameras are valid only once it has arrived
+        const float* src = t_cam + (size_t)scam[tid] * kTStride;
+        cp_async16(&S.tc[0][tid][0], src);
+        cp_async16(&S.tc[0][tid][4], src + 4);
+        cp_async16(&S.tc[0][tid][8], src + 8);
+      }
+      if (tid < d0.y) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) cp_async4(&S.vi[0][tid][k], Vinv + (size_t)(d0.x + tid) * 6 + k);
+      }
+      cp_async_commit();
+    }
+    // ---- phase A, steady state: tile k uses desc[k % 4], rec[k % 3], tc / vi[k % 2]
+    for (int k = 0;; ++k) {
+      const int dk = k & 3, rk = k % 3, bk = k & 1;
+      if (s_tk[dk] >= n_list || s_fail) break;
+      if (mbar_wait(&S.mbJ, parJ, kCopyWaitCycles)) {
+        parJ ^= 1u;
+        pend &= ~8u;
+      } else {
+        s_fail = 1;
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      if (s_fail) break;
+      const int4 d0 = S.desc[dk][0], d1 = S.desc[dk][1];
+      const int L0 = d0.x, nl = d0.y, o0 = d0.z, n = d0.w, ns = d1.y;
+      const TileRecLayout g = tile_rec_layout(n, ns, nl);
+      const uint8_t* rec = S.rec[rk];
+      const bool active = tid < n;
+      float jp[18], jl[6];
+      int meta = 0, lm = 0;
+      if (active) {
+        const int sh = (o0 & 3) + tid;
+#pragma unroll
+        for (int p = 0; p < 18; ++p) jp[p] = S.sJ[p][sh];
+#pragma unroll
+        for (int p = 0; p < 6; ++p) jl[p] = S.sJ[18 + p][sh];
+        meta = reinterpret_cast<const uint16_t*>(rec + g.meta)[tid];
+        lm = rec[g.olm + tid];
+      }
+      (void)L0;
+      __syncthreads();  // sJ and desc[(k + 3) % 4] are free
+      const int k1 = (k + 1) & 3, k2 = (k + 2) & 3, k3 = (k + 3) & 3;
+      if (tid == 0) {
+        if (s_tk[k1] < n_list) {
+          issue_J(S, J, pad, S.desc[k1][0].z, S.desc[k1][0].w);
+          pend |= 8u;
+        }
+        if (s_tk[k2] < n_list) {
+          issue_rec(S, tp.tile_rec, (k + 2) % 3, S.desc[k2]);
+          pend |= 1u << ((k + 2) % 3);
+        }
+        const int tk = tk_next;
+        s_tk[k3] = tk;
+        tk_next = n_list;
+        if (tk < n_list) {
+          cp_async16(&S.desc[k3][0], list + 2 * (size_t)tk);
+          cp_async16(&S.desc[k3][1], list + 2 * (size_t)tk + 1);
+          cp_async_commit();
+          if (!ld_volatile(&sgl->all_done)) {
+            tk_next = (int)atomicAdd(&gs->tile_next, 1u);
+            if (tk_next > n_list) tk_next = n_list;
+          }
+        }
+      }
+      // the next tile's t rows and V^-1, once its record has arrived (mid-tile)
+      auto mid = [&]() {
+        if (s_tk[k1] >= n_list) return;
+        const int r1 = (k + 1) % 3;
+        const bool ok = mbar_wait(&S.mbR[r1], (parR >> r1) & 1u, kCopyWaitCycles);
+        if (ok) {
+          parR ^= 1u << r1;
+          pend &= ~(1u << r1);
+        } else {
+          s_fail = 1;
+        }
+        const int4 e0 = S.desc[k1][0], e1 = S.desc[k1][1];
+        const TileRecLayout h = tile_rec_layout(e0.w, e1.y, e0.y);
+        const int* scam1 = reinterpret_cast<const int*>(&S.rec[r1][h.scam]);
+        if (ok && tid < e1.y) {
+          const float* src = t_cam + (size_t)scam1[tid] * kTStride;
+          cp_async16(&S.tc[bk ^ 1][tid][0], src);
+          cp_async16(&S.tc[bk ^ 1][tid][4], src + 4);
+          cp_async16(&S.tc[bk ^ 1][tid][8], src + 8);
+        }
+        if (tid < e0.y) {
+#pragma unroll
+          for (int q = 0; q < 6; ++q)
+            cp_async4(&S.vi[bk ^ 1][tid][q], Vinv + (size_t)(e0.x + tid) * 6 + q);
+        }
+        cp_async_commit();
+      };
+      f32_tile_core<kModeSeries>(active, n, ns, lm, meta, jp, jl, &S.tc[bk][0][0], kTStride,
+                                 &S.vi[bk][0][0], 6,
+                                 reinterpret_cast<const uint16_t*>(rec + g.sseg),
+                                 reinterpret_cast<const uint16_t*>(rec + g.sbeg),
+                                 reinterpret_cast<const int*>(rec + g.srow), sv, S.sg, partial,
+                                 mid);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (s_fail) {
+      // let the bulk copies this block started finish (each wait bounded) before it leaves
+      if (tid == 0) {
+        atomicExch(&gs->error, 1);
+        if (pend & 8u) mbar_wait(&S.mbJ, parJ, kCopyWaitCycles);
+        for (int r = 0; r < 3; ++r)
+          if (pend & (1u << r)) mbar_wait(&S.mbR[r], (parR >> r) & 1u, kCopyWaitCycles);
+      }
+      __syncthreads();
+      return;
+    }
+    if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 1] = global_ns();
+    if (!tile_end_barrier(gs, timeout, &s_last, &s_gen, &s_ok)) return;
+    if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 2] = global_ns();
+    if (tid == 0) s_done = ld_volatile(&sgl->all_done);
+    __syncthreads();
+    if (s_done) break;
+    // ---- phase B: cameras
+    camera_phase<float>(tp, cr, rc, partial, Uinv, x, t_cam, cam_norm, st, scratch);
+    if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 3] = global_ns();
+    if (!term_end_barrier(tp, gs, cam_norm, st, sgl, i, eps, timeout, &s_last, &s_gen, &s_ok,
+                          &s_running))
+      return;
+    if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 4] = global_ns();
+  }
+  round_writeback(rc, x);
 }
 
 int persistent_blocks_per_sm(bool f32) {
@@ -237,20 +657,52 @@ int persistent_blocks_per_sm(bool f32) {
   return nb;
 }
 
+size_t pipelined_smem_bytes() { return sizeof(F32Pipe); }
+
+int pipelined_blocks_per_sm() {
+  if (cudaFuncSetAttribute(series_persistent_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(F32Pipe)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, series_persistent_f32_kernel, kTileObs,
+                                                    sizeof(F32Pipe)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
 template <typename T>
-cudaError_t launch_series_persistent(const Topology& tp, int grid, const T* J, const T* Vinv,
-                                     const double* Uinv, double* x, T* t_cm, T* partial,
+cudaError_t launch_series_persistent(const Topology& tp, const CamRounds& cr, int grid, const T* J, const T* Vinv,
+                                     const double* Uinv, double* x, T* t_cam, T* partial,
                                      double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
                                      GridSync* gs, int m_max, double eps, long long timeout,
                                      long long* trace, cudaStream_t s) {
-  void* args[] = {(void*)&tp, (void*)&J, (void*)&Vinv, (void*)&Uinv, (void*)&x, (void*)&t_cm,
-                  (void*)&partial, (void*)&cam_norm, (void*)&st, (void*)&sgl, (void*)&gs,
-                  (void*)&m_max, (void*)&eps, (void*)&timeout, (void*)&trace};
+  void* args[] = {(void*)&tp, (void*)&cr, (void*)&J, (void*)&Vinv, (void*)&Uinv, (void*)&x,
+                  (void*)&t_cam, (void*)&partial, (void*)&cam_norm, (void*)&st, (void*)&sgl,
+                  (void*)&gs, (void*)&m_max, (void*)&eps, (void*)&timeout, (void*)&trace};
   return cudaLaunchCooperativeKernel((const void*)series_persistent_kernel<T>, dim3(grid),
                                      dim3(kTileObs), args, 0, s);
 }
 
-template cudaError_t launch_series_persistent<double>(const Topology&, int, const double*, const double*, const double*, double*, double*, double*, double*, SeriesState*, SeriesGlobal*, GridSync*, int, double, long long, long long*, cudaStream_t);
-template cudaError_t launch_series_persistent<float>(const Topology&, int, const float*, const float*, const double*, double*, float*, float*, double*, SeriesState*, SeriesGlobal*, GridSync*, int, double, long long, long long*, cudaStream_t);
+cudaError_t launch_series_pipelined(const Topology& tp, const CamRounds& cr, int grid,
+                                    const int4* list,
+                                    const int* n_list, const float* J, const float* Vinv,
+                                    const double* Uinv, double* x, float* t_cam, float* partial,
+                                    double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
+                                    GridSync* gs, int m_max, double eps, long long timeout,
+                                    long long* trace, cudaStream_t s) {
+  void* args[] = {(void*)&tp, (void*)&cr, (void*)&list, (void*)&n_list, (void*)&J, (void*)&Vinv,
+                  (void*)&Uinv, (void*)&x, (void*)&t_cam, (void*)&partial, (void*)&cam_norm,
+                  (void*)&st, (void*)&sgl, (void*)&gs, (void*)&m_max, (void*)&eps,
+                  (void*)&timeout, (void*)&trace};
+  return cudaLaunchCooperativeKernel((const void*)series_persistent_f32_kernel, dim3(grid),
+                                     dim3(kTileObs), args, sizeof(F32Pipe), s);
+}
+
+template cudaError_t launch_series_persistent<double>(const Topology&, const CamRounds&, int, const double*, const double*, const double*, double*, double*, double*, double*, SeriesState*, SeriesGlobal*, GridSync*, int, double, long long, long long*, cudaStream_t);
+template cudaError_t launch_series_persistent<float>(const Topology&, const CamRounds&, int, const float*, const float*, const double*, double*, float*, float*, double*, SeriesState*, SeriesGlobal*, GridSync*, int, double, long long, long long*, cudaStream_t);
 
 }  // namespace poba

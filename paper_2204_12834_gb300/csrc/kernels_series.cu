@@ -18,7 +18,7 @@ namespace poba {
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kTileObs) tile_matvec_kernel(
-    Topology tp, const T* __restrict__ J, const T* __restrict__ t_cm,
+    Topology tp, const T* __restrict__ J, const T* __restrict__ t_cam,
     const double* __restrict__ b_l, const T* __restrict__ Vinv, T* __restrict__ partial,
     const SeriesState* __restrict__ st, const SeriesGlobal* __restrict__ sgl) {
   __shared__ TileSmem<T> sm;
@@ -26,9 +26,9 @@ __global__ void __launch_bounds__(kTileObs) tile_matvec_kernel(
   if (MODE == kModeSeries && sgl->all_done) return;
   if (st[tp.tile_prob[blockIdx.x]].done) return;
   if constexpr (sizeof(T) == 4)
-    tile_matvec_body_f32<MODE>(tp, blockIdx.x, J, t_cm, b_l, Vinv, partial, sm);
+    tile_matvec_body_f32<MODE>(tp, blockIdx.x, J, t_cam, b_l, Vinv, partial, sm);
   else
-    tile_matvec_body<T, MODE>(tp, blockIdx.x, J, t_cm, b_l, Vinv, partial, sm);
+    tile_matvec_body<T, MODE>(tp, blockIdx.x, J, t_cam, b_l, Vinv, partial, sm);
 }
 
 template <typename T>
@@ -39,10 +39,10 @@ void launch_tile_rhs(const Topology& tp, const T* J, const double* b_l, const T*
 }
 
 template <typename T>
-void launch_tile_series(const Topology& tp, const T* J, const T* t_cm, const T* Vinv,
+void launch_tile_series(const Topology& tp, const T* J, const T* t_cam, const T* Vinv,
                         T* partial, const SeriesState* st, const SeriesGlobal* sgl,
                         cudaStream_t s) {
-  tile_matvec_kernel<T, kModeSeries><<<tp.n_tiles, kTileObs, 0, s>>>(tp, J, t_cm, nullptr, Vinv,
+  tile_matvec_kernel<T, kModeSeries><<<tp.n_tiles, kTileObs, 0, s>>>(tp, J, t_cam, nullptr, Vinv,
                                                                      partial, st, sgl);
 }
 
@@ -144,7 +144,7 @@ int camera_blocks(const Topology& tp) { return (tp.n_cams + kCamBlock - 1) / kCa
 template <typename PT, int MODE>
 __global__ void __launch_bounds__(kCamBlock * 9) camera_step_kernel(
     Topology tp, const PT* __restrict__ partial, const double* __restrict__ b_p,
-    const double* __restrict__ Uinv, double* __restrict__ x, PT* __restrict__ t_cm,
+    const double* __restrict__ Uinv, double* __restrict__ x, PT* __restrict__ t_cam,
     double* __restrict__ cam_norm, SeriesState* __restrict__ st, SeriesGlobal* __restrict__ sgl,
     int iter, double eps) {
   __shared__ double ys[kCamBlock][9];
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kCamBlock * 9) camera_step_kernel(
   __shared__ int is_last, s_running;
   if (MODE == kModeSeries && sgl->all_done) return;
   const int tid = threadIdx.x;
-  camera_body<PT, MODE>(tp, blockIdx.x * kCamBlock, kCamBlock, partial, b_p, Uinv, x, t_cm, st,
+  camera_body<PT, MODE>(tp, blockIdx.x * kCamBlock, kCamBlock, partial, b_p, Uinv, x, t_cam, st,
                         cam_norm, ys, y2);
   if (tid == 0) {
     __threadfence();
@@ -168,18 +168,18 @@ __global__ void __launch_bounds__(kCamBlock * 9) camera_step_kernel(
 
 template <typename PT>
 void launch_camera_rhs(const Topology& tp, const PT* partial, const double* b_p, const double* Uinv,
-                       double* x, PT* t_cm, double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
+                       double* x, PT* t_cam, double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
                        cudaStream_t s) {
   camera_step_kernel<PT, kModeRhs><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(
-      tp, partial, b_p, Uinv, x, t_cm, cam_norm, st, sgl, 0, 0.0);
+      tp, partial, b_p, Uinv, x, t_cam, cam_norm, st, sgl, 0, 0.0);
 }
 
 template <typename PT>
 void launch_camera_series(const Topology& tp, const PT* partial, const double* Uinv, double* x,
-                          PT* t_cm, double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
+                          PT* t_cam, double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
                           int iter, double eps, cudaStream_t s) {
   camera_step_kernel<PT, kModeSeries><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(
-      tp, partial, nullptr, Uinv, x, t_cm, cam_norm, st, sgl, iter, eps);
+      tp, partial, nullptr, Uinv, x, t_cam, cam_norm, st, sgl, iter, eps);
 }
 
 template void launch_camera_rhs<double>(const Topology&, const double*, const double*, const double*, double*, double*, double*, SeriesState*, SeriesGlobal*, cudaStream_t);
@@ -207,6 +207,64 @@ __global__ void series_reset_kernel(SeriesState* st, SeriesGlobal* sgl, const Lm
 void launch_series_reset(SeriesState* st, SeriesGlobal* sgl, const LmRecord* rec, int n_probs,
                          cudaStream_t s) {
   series_reset_kernel<<<(n_probs + 127) / 128, 128, 0, s>>>(st, sgl, rec, n_probs);
+}
+
+// Active tile list of a batch: an exclusive scan of the tile counts of the problems still
+// taking part (one block, problems in chunks of blockDim), then a copy of their descriptors.
+__global__ void __launch_bounds__(1024) active_tiles_scan_kernel(Topology tp,
+                                                                  const SeriesState* st,
+                                                                  int32_t* list_off,
+                                                                  SeriesGlobal* sgl) {
+  __shared__ int s_warp[32];
+  __shared__ int s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) s_base = 0;
+  __syncthreads();
+  for (int p0 = 0; p0 < tp.n_probs; p0 += blockDim.x) {
+    const int p = p0 + threadIdx.x;
+    const int c = (p < tp.n_probs && !st[p].done) ? tp.tile_off[p + 1] - tp.tile_off[p] : 0;
+    int v = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, v, off);
+      if (lane >= off) v += y;
+    }
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+      int w = lane < nw ? s_warp[lane] : 0;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, off);
+        if (lane >= off) w += y;
+      }
+      s_warp[lane] = w;
+    }
+    __syncthreads();
+    const int excl = s_base + (warp > 0 ? s_warp[warp - 1] : 0) + v - c;
+    if (p < tp.n_probs) list_off[p] = excl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) s_base = excl + c;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sgl->n_list = s_base;
+}
+
+__global__ void active_tiles_fill_kernel(Topology tp, const SeriesState* st,
+                                         const int32_t* list_off, int4* list) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tp.n_tiles) return;
+  const int p = tp.tile_prob[t];
+  if (st[p].done) return;
+  const int k = list_off[p] + (t - tp.tile_off[p]);
+  list[2 * (size_t)k] = tp.tile_desc[2 * (size_t)t];
+  list[2 * (size_t)k + 1] = tp.tile_desc[2 * (size_t)t + 1];
+}
+
+void launch_active_tiles(const Topology& tp, const SeriesState* st, int32_t* list_off,
+                         int4* list, SeriesGlobal* sgl, cudaStream_t s) {
+  active_tiles_scan_kernel<<<1, 1024, 0, s>>>(tp, st, list_off, sgl);
+  active_tiles_fill_kernel<<<(tp.n_tiles + 255) / 256, 256, 0, s>>>(tp, st, list_off, list);
 }
 
 __global__ void set_scalar_kernel(double* dst, double v) { *dst = v; }

@@ -11,8 +11,12 @@
 //   global atomics are used and every sum has a fixed order.
 //
 //   Per-slot partial sums are written camera-major (row slot_row[s] of slot s), so the rows of
-//   one camera are contiguous for the camera-side kernels; the current series term is kept per
-//   slot row as well (t_cm, camera-major), which a tile gathers through slot_row.
+//   one camera are contiguous for the camera-side kernels.  A camera's rows are summed in
+//   chunks of cam_chunk_rows(rows) rows (each chunk in row order, then the chunks in order), in
+//   every kernel, so that the persistent kernels can spread a camera's chunks over threads and
+//   still produce the same sums.  The current series term is kept per camera (t_cam, rows of
+//   kTStride elements), which a tile gathers through its slots' cameras.  A tile holds at most
+//   kTileSlots slots.
 //
 //   Jacobians and residuals are structure-of-arrays planes of length n_obs_pad in the
 //   handle's bulk precision T:
@@ -33,6 +37,22 @@ namespace poba {
 
 constexpr int kTileObs = 256;   // observations per tile (= threads of the tile kernels)
 constexpr int kTileLms = 256;   // landmarks per tile
+constexpr int kTileSlots = 128; // distinct cameras (slots) per tile
+constexpr int kTStride = 12;    // elements per camera row of the current term (9 used; 16-byte
+                                // aligned rows for asynchronous copies)
+constexpr int kCamChunkMin = 16;  // rows per chunk of a camera's row sum (at least)
+constexpr int kRoundItems = 28;   // camera chunks per round of the persistent camera phase
+
+// Rows per chunk of a camera with `rows` slot rows: at least kCamChunkMin, and few enough
+// chunks to fit one round.
+__host__ __device__ constexpr int cam_chunk_rows(int rows) {
+  return (rows + kRoundItems - 1) / kRoundItems > kCamChunkMin
+             ? (rows + kRoundItems - 1) / kRoundItems
+             : kCamChunkMin;
+}
+__host__ __device__ constexpr int cam_chunks(int rows) {
+  return rows > 0 ? (rows + cam_chunk_rows(rows) - 1) / cam_chunk_rows(rows) : 1;
+}
 constexpr int kLinVals = 54;    // 45 packed upper-triangular entries of J_p^T J_p + 9 of J_p^T r
 constexpr int kCamBlock = 32;   // cameras per block in the damp / invert kernel
 constexpr int kReduceThreads = 256;
@@ -51,7 +71,8 @@ struct Schedule {
   std::vector<uint16_t> obs_meta;    // [n_obs] pos | slot << 8
   std::vector<int32_t> tile_lm0;     // [n_tiles + 1]
   std::vector<int32_t> tile_slot0;   // [n_tiles + 1]
-  std::vector<int32_t> tile_desc;    // [n_tiles][8]: L0, n_lms, o0, n_obs, S0, n_slots, 0, 0
+  std::vector<int32_t> tile_desc;    // [n_tiles][8]: L0, n_lms, o0, n_obs, S0, n_slots, rec, prob
+  std::vector<uint8_t> tile_rec;     // per-tile records (see tile_rec_layout), 16-byte aligned
   std::vector<int32_t> slot_cam;     // [n_slots]
   std::vector<uint16_t> slot_beg;    // [n_slots] first camera-sorted position of the slot
   std::vector<int32_t> cam_slot_ptr; // [n_cams + 1]
@@ -67,12 +88,54 @@ struct Schedule {
   std::vector<int32_t> lm_prob;      // [n_lms] problem of each internal landmark
 };
 
+// Per-tile record, one contiguous 16-byte aligned block per tile, so that one bulk copy brings
+// a tile's index data into shared memory: the observations' codes (pos | slot << 8), their
+// landmark within the tile, the slots' first positions, the landmark segment offsets (tile-
+// relative), the slots' camera-major rows and the slots' cameras.  Each array is padded to a multiple of 16 bytes.
+// tile_desc[t][6] is the record's offset in 16-byte units.
+struct TileRecLayout {
+  int meta, olm, sbeg, sseg, srow, scam, bytes;  // byte offsets of the arrays and the total
+};
+__host__ __device__ constexpr TileRecLayout tile_rec_layout(int n, int ns, int nl) {
+  const int n8 = (n + 7) & ~7, n16 = (n + 15) & ~15, ns8 = (ns + 7) & ~7;
+  const int nl8 = (nl + 1 + 7) & ~7, ns4 = (ns + 3) & ~3;
+  const int meta = 0, olm = meta + 2 * n8, sbeg = olm + n16, sseg = sbeg + 2 * ns8;
+  const int srow = sseg + 2 * nl8, scam = srow + 4 * ns4, bytes = scam + 4 * ns4;
+  return TileRecLayout{meta, olm, sbeg, sseg, srow, scam, bytes};
+}
+constexpr int kTileRecMax = tile_rec_layout(kTileObs, kTileSlots, kTileLms).bytes;
+
 // Returns an empty string on success, else a description of why the inputs are rejected.
 // cam_off / lm_off ([n_probs + 1]) split cameras and landmarks into independent problems; every
 // observation must join a camera and a landmark of the same problem.  NULL means one problem.
 std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_idx,
                            const int32_t* lm_idx, int n_probs, const int32_t* cam_off,
                            const int32_t* lm_off, Schedule* out);
+
+// Camera schedule of the persistent camera phase.  Items are the chunks of every camera's slot
+// rows (cam_chunks per camera, in camera order): camera c owns items [cam_item[c],
+// cam_item[c + 1]) and item i covers rows [item_q[2 i], item_q[2 i + 1]).  Rounds pack whole
+// cameras in order with at most max_items items (at most kRoundItems, at least the largest
+// camera's chunk count): round r holds cameras [round_cam[r], round_cam[r + 1]) and items
+// [round_item[r], round_item[r + 1]).  For a grid of G blocks, block b runs rounds
+// [block_round[b], block_round[b + 1]).
+struct CamSchedule {
+  std::vector<int32_t> cam_item, item_q;
+};
+struct CamRoundList {
+  std::vector<int32_t> round_cam, round_item, block_round;
+};
+void build_cam_schedule(const Schedule& S, CamSchedule* out);
+// Rounds sized for a grid of G blocks: as few items per round as spread the items over the grid.
+void build_cam_rounds(const CamSchedule& cs, int n_cams, int G, CamRoundList* out);
+
+struct CamRounds {
+  const int32_t* cam_item;
+  const int32_t* item_q;
+  const int32_t* round_cam;
+  const int32_t* round_item;
+  const int32_t* block_round;  // [G + 1]
+};
 
 // ---------------------------------------------------------------------------------------
 // Device views passed to kernels by value.
@@ -84,7 +147,8 @@ struct Topology {
   const uint16_t* obs_meta;
   const int32_t* tile_lm0;
   const int32_t* tile_slot0;
-  const int4* tile_desc;  // two int4 per tile: {L0, nl, o0, n}, {S0, ns, 0, 0}
+  const int4* tile_desc;  // two int4 per tile: {L0, nl, o0, n}, {S0, ns, rec16, problem}
+  const uint8_t* tile_rec;  // per-tile records (tile_rec_layout)
   const int32_t* slot_cam;
   const uint16_t* slot_beg;
   const int32_t* cam_slot_ptr;
@@ -120,7 +184,8 @@ struct SeriesState {
 struct SeriesGlobal {
   int32_t all_done;    // every problem has stopped (later terms return at once)
   uint32_t counter;    // last-block ticket of the per-term camera kernel
-  int32_t pad[2];
+  int32_t n_list;      // tiles in the active tile list (batches)
+  int32_t pad;
 };
 
 // Grid-barrier state of the persistent series kernel (zeroed before each launch).
@@ -184,7 +249,7 @@ void launch_tile_rhs(const Topology& tp, const T* J, const double* b_l, const T*
                      T* partial, const SeriesState* st, cudaStream_t s);
 
 template <typename T>
-void launch_tile_series(const Topology& tp, const T* J, const T* t_cm, const T* Vinv,
+void launch_tile_series(const Topology& tp, const T* J, const T* t_cam, const T* Vinv,
                         T* partial, const SeriesState* st, const SeriesGlobal* sgl,
                         cudaStream_t s);
 
@@ -194,17 +259,17 @@ void launch_tile_backsub(const Topology& tp, const T* J, const T* r, const doubl
                          double* block_pred, cudaStream_t s);
 
 // The camera kernels write the new term t into each of the camera's camera-major slot rows
-// (t_cm), which the next tile kernel gathers through slot_row, and a (||t_c||^2, ||x_c||^2)
+// (t_cam), which the next tile kernel gathers through slot_row, and a (||t_c||^2, ||x_c||^2)
 // pair per camera (cam_norm); the last block to finish reduces the pairs per problem and
 // applies the stop rule of each problem.
 template <typename PT>
 void launch_camera_rhs(const Topology& tp, const PT* partial, const double* b_p,
-                       const double* Uinv, double* x, PT* t_cm, double* cam_norm,
+                       const double* Uinv, double* x, PT* t_cam, double* cam_norm,
                        SeriesState* st, SeriesGlobal* sgl, cudaStream_t s);
 
 template <typename PT>
 void launch_camera_series(const Topology& tp, const PT* partial, const double* Uinv, double* x,
-                          PT* t_cm, double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
+                          PT* t_cam, double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
                           int iter, double eps, cudaStream_t s);
 
 int camera_blocks(const Topology& tp);
@@ -235,15 +300,33 @@ void launch_set_scalar(double* dst, double v, cudaStream_t s);
 // Fixed-order sum of n doubles into *out = scale * sum (one block).
 void launch_reduce_sum(const double* in, int n, double* out, double scale, cudaStream_t s);
 
-// Persistent series kernel (cooperative launch): up to m_max terms and the stop rule.  Block 0
-// records %globaltimer at 5 points of each of the first kTraceTerms terms (start, end of the
-// tile phase, after the first barrier, end of the camera phase, after the second barrier).
+// Persistent series kernel (cooperative launch): up to m_max terms and the stop rule.  The last
+// block records %globaltimer at 5 points of each of the first kTraceTerms terms (start, end of
+// the tile phase, after the first barrier, end of the camera phase, after the second barrier).
 constexpr int kTraceTerms = 64;
 constexpr int kTracePoints = 5;
 int persistent_blocks_per_sm(bool f32);
+
+// FP32-bulk persistent kernel with the software-pipelined tile phase (bulk copies of each
+// tile's Jacobians and index record, issued ahead).  Needs every tile to hold at most
+// kTileSlots slots.  Tiles come from `list` (descriptor pairs as tile_desc), *n_list of them.
+int pipelined_blocks_per_sm();  // 0: the kernel cannot be launched on this device
+cudaError_t launch_series_pipelined(const Topology& tp, const CamRounds& cr, int grid,
+                                    const int4* list,
+                                    const int* n_list, const float* J, const float* Vinv,
+                                    const double* Uinv, double* x, float* t_cam, float* partial,
+                                    double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
+                                    GridSync* gs, int m_max, double eps, long long timeout,
+                                    long long* trace, cudaStream_t s);
+
+// Batches: the descriptors of the tiles of every problem still taking part (st[p].done == 0),
+// in tile order, into list; their number into sgl->n_list.  list_off: [n_probs] scratch.
+void launch_active_tiles(const Topology& tp, const SeriesState* st, int32_t* list_off,
+                         int4* list, SeriesGlobal* sgl, cudaStream_t s);
 template <typename T>
-cudaError_t launch_series_persistent(const Topology& tp, int grid, const T* J, const T* Vinv,
-                                     const double* Uinv, double* x, T* t_cm, T* partial,
+cudaError_t launch_series_persistent(const Topology& tp, const CamRounds& cr, int grid, const T* J,
+                                     const T* Vinv,
+                                     const double* Uinv, double* x, T* t_cam, T* partial,
                                      double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
                                      GridSync* gs, int m_max, double eps, long long timeout,
                                      long long* trace, cudaStream_t s);

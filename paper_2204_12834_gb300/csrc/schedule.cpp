@@ -6,6 +6,7 @@
 // into tiles of at most kTileObs observations, and each tile's distinct cameras become slots
 // whose sums are later combined per camera in a fixed order.
 #include <algorithm>
+#include <climits>
 #include <numeric>
 #include <string>
 
@@ -101,21 +102,31 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
     S->lm_of[o] = S->lm_rank[lm_idx[S->obs_order[o]]];
   }
 
-  // Tiles: greedy packing of whole landmarks of one problem.
+  // Tiles: greedy packing of whole landmarks of one problem, at most kTileObs observations,
+  // kTileLms landmarks and kTileSlots distinct cameras per tile.
   S->tile_lm0.clear();
   S->tile_lm0.push_back(0);
   {
-    int tile_obs = 0, tile_lms = 0;
+    int tile_obs = 0, tile_lms = 0, tile_cams = 0, tile_id = 0;
+    std::vector<int32_t> stamp(n_cams, -1);  // tile that last counted the camera
     for (int i = 0; i < n_lms; ++i) {
-      int k = S->lm_seg[i + 1] - S->lm_seg[i];
+      const int k = S->lm_seg[i + 1] - S->lm_seg[i];
+      int fresh = 0;  // cameras of landmark i not yet in the tile (a track has distinct cameras)
+      for (int o = S->lm_seg[i]; o < S->lm_seg[i + 1]; ++o) fresh += stamp[S->cam_of[o]] != tile_id;
       const bool new_prob = i > 0 && S->lm_prob[i] != S->lm_prob[i - 1];
-      if (tile_lms > 0 && (new_prob || tile_obs + k > kTileObs || tile_lms + 1 > kTileLms)) {
+      if (tile_lms > 0 && (new_prob || tile_obs + k > kTileObs || tile_lms + 1 > kTileLms ||
+                           tile_cams + fresh > kTileSlots)) {
         S->tile_lm0.push_back(i);
         tile_obs = 0;
         tile_lms = 0;
+        tile_cams = 0;
+        ++tile_id;
+        fresh = k;
       }
+      for (int o = S->lm_seg[i]; o < S->lm_seg[i + 1]; ++o) stamp[S->cam_of[o]] = tile_id;
       tile_obs += k;
       tile_lms += 1;
+      tile_cams += fresh;
     }
     S->tile_lm0.push_back(n_lms);
   }
@@ -157,6 +168,7 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
   }
   S->n_slots = S->tile_slot0[S->n_tiles];
   S->tile_desc.assign((size_t)S->n_tiles * 8, 0);
+  size_t rec_bytes = 0;
   for (int t = 0; t < S->n_tiles; ++t) {
     int32_t* d = &S->tile_desc[(size_t)t * 8];
     d[0] = S->tile_lm0[t];
@@ -165,7 +177,11 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
     d[3] = S->lm_seg[S->tile_lm0[t + 1]] - d[2];
     d[4] = S->tile_slot0[t];
     d[5] = S->tile_slot0[t + 1] - S->tile_slot0[t];
+    d[6] = (int32_t)(rec_bytes / 16);
+    d[7] = S->lm_prob[S->tile_lm0[t]];
+    rec_bytes += (size_t)tile_rec_layout(d[3], d[5], d[1]).bytes;
   }
+  if (rec_bytes / 16 > (size_t)INT32_MAX) return "too many tiles for the tile records";
 
   // Camera -> slots (CSR), slots in tile order.
   S->cam_slot_ptr.assign(n_cams + 1, 0);
@@ -176,7 +192,70 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
   for (int s = 0; s < S->n_slots; ++s) S->cam_slot_list[fill[S->slot_cam[s]]++] = s;
   S->slot_row.assign(S->n_slots, 0);
   for (int r = 0; r < S->n_slots; ++r) S->slot_row[S->cam_slot_list[r]] = r;
+
+  // Per-tile records (copies of the index data above, grouped per tile).
+  S->tile_rec.assign(rec_bytes, 0);
+  for (int t = 0; t < S->n_tiles; ++t) {
+    const int32_t* d = &S->tile_desc[(size_t)t * 8];
+    const int L0 = d[0], nl = d[1], o0 = d[2], n = d[3], S0 = d[4], ns = d[5];
+    const TileRecLayout g = tile_rec_layout(n, ns, nl);
+    uint8_t* base = &S->tile_rec[(size_t)d[6] * 16];
+    uint16_t* meta = reinterpret_cast<uint16_t*>(base + g.meta);
+    uint8_t* olm = base + g.olm;
+    uint16_t* sbeg = reinterpret_cast<uint16_t*>(base + g.sbeg);
+    uint16_t* sseg = reinterpret_cast<uint16_t*>(base + g.sseg);
+    int32_t* srow = reinterpret_cast<int32_t*>(base + g.srow);
+    int32_t* scam = reinterpret_cast<int32_t*>(base + g.scam);
+    for (int i = 0; i < n; ++i) meta[i] = S->obs_meta[o0 + i];
+    for (int l = 0; l < nl; ++l)
+      for (int o = S->lm_seg[L0 + l]; o < S->lm_seg[L0 + l + 1]; ++o) olm[o - o0] = (uint8_t)l;
+    for (int s = 0; s < ns; ++s) {
+      sbeg[s] = S->slot_beg[S0 + s];
+      srow[s] = S->slot_row[S0 + s];
+      scam[s] = S->slot_cam[S0 + s];
+    }
+    for (int l = 0; l <= nl; ++l) sseg[l] = (uint16_t)(S->lm_seg[L0 + l] - o0);
+  }
   return "";
+}
+
+void build_cam_schedule(const Schedule& S, CamSchedule* cs) {
+  cs->cam_item.assign(S.n_cams + 1, 0);
+  cs->item_q.clear();
+  for (int c = 0; c < S.n_cams; ++c) {
+    const int r0 = S.cam_slot_ptr[c], r1 = S.cam_slot_ptr[c + 1];
+    const int k = cam_chunks(r1 - r0), C = cam_chunk_rows(r1 - r0);
+    for (int j = 0; j < k; ++j) {
+      cs->item_q.push_back(std::min(r0 + j * C, r1));
+      cs->item_q.push_back(std::min(r0 + (j + 1) * C, r1));
+    }
+    cs->cam_item[c + 1] = cs->cam_item[c] + k;
+  }
+}
+
+void build_cam_rounds(const CamSchedule& cs, int n_cams, int G, CamRoundList* out) {
+  const int total = cs.cam_item[n_cams];
+  int biggest = 1;
+  for (int c = 0; c < n_cams; ++c) biggest = std::max(biggest, cs.cam_item[c + 1] - cs.cam_item[c]);
+  int max_items = (total + G - 1) / G;
+  max_items = std::min(kRoundItems, std::max(max_items, biggest));
+  out->round_cam.assign(1, 0);
+  out->round_item.assign(1, 0);
+  int in_round = 0;
+  for (int c = 0; c < n_cams; ++c) {
+    const int k = cs.cam_item[c + 1] - cs.cam_item[c];
+    if (c > out->round_cam.back() && in_round + k > max_items) {
+      out->round_cam.push_back(c);
+      out->round_item.push_back(cs.cam_item[c]);
+      in_round = 0;
+    }
+    in_round += k;
+  }
+  out->round_cam.push_back(n_cams);
+  out->round_item.push_back(total);
+  const int R = (int)out->round_cam.size() - 1;
+  out->block_round.assign(G + 1, 0);
+  for (int b = 0; b <= G; ++b) out->block_round[b] = (int)(((int64_t)b * R) / G);
 }
 
 }  // namespace poba

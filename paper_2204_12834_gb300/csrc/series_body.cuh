@@ -1,5 +1,5 @@
 // Device bodies of one power-series term (Sec. 4.3), shared by the per-term kernels and the
-// persistent series kernel.  Data written by other blocks of the same launch (t_cm, partial,
+// persistent series kernel.  Data written by other blocks of the same launch (t_cam, partial,
 // x) is read with __ldcg (L2), since L1 is not coherent across SMs within a launch.
 //
 // With P = U^-1 W V^-1 W^T, W = J_p^T J_l, a term t_i = P t_{i-1} is applied matrix-free:
@@ -9,7 +9,7 @@
 //     g_o = J_p,o^T (J_l,o z_l(o))             (J still in registers: one J read per term)
 //     partial[row(slot)] = sum_{o in slot} g_o (per-tile camera sums, fixed order)
 //   camera body (9 threads per camera):
-//     y_c = sum of the camera's partial rows; t_i = U_c^-1 y_c; x += t_i; t_cm rows = t_i.
+//     y_c = sum of the camera's partial rows; t_i = U_c^-1 y_c; x += t_i; t_cam[c] = t_i.
 // With z_l = V_l^-1 b_l (RHS mode) the same bodies form b~ = b_p - W V^-1 b_l and
 // x(0) = -U^-1 b~ (Sec. 4.2 and eq. `x_approx` with m = 0).
 #pragma once
@@ -69,7 +69,7 @@ static_assert(offsetof(TileSmem<double>, sg) % 8 == 0, "sg is reused as double s
 template <typename T, int MODE>
 __device__ __forceinline__ void tile_matvec_body(const Topology& tp, int tile,
                                                  const T* __restrict__ J,
-                                                 const T* __restrict__ t_cm,
+                                                 const T* __restrict__ t_cam,
                                                  const double* __restrict__ b_l,
                                                  const T* __restrict__ Vinv,
                                                  T* __restrict__ partial, TileSmem<T>& sm) {
@@ -103,10 +103,10 @@ __device__ __forceinline__ void tile_matvec_body(const Topology& tp, int tile,
   for (int i = tid; i <= nl; i += blockDim.x) sm.sseg[i] = tp.lm_seg[th.L0 + i] - o0;
   __syncthreads();
   if (MODE == kModeSeries) {
-    // the current term is stored camera-major: row srow[s] holds slot s's camera
+    // the current term of each slot's camera
     for (int i = tid; i < ns * 9; i += blockDim.x) {
       const int s = i / 9, k = i - s * 9;
-      sm.tcam[s][k] = __ldcg(t_cm + (size_t)sm.srow[s] * 9 + k);
+      sm.tcam[s][k] = __ldcg(t_cam + (size_t)tp.slot_cam[th.S0 + s] * kTStride + k);
     }
   }
   __syncthreads();
@@ -163,6 +163,88 @@ __device__ __forceinline__ void tile_matvec_body(const Topology& tp, int tile,
   slot_sums<T, T>(sm.sg, ns, n, sm.sbeg, sm.srow, partial, 9);
 }
 
+// Phases 1-3 of the FP32-bulk tile (below), shared by the per-term tile kernel and the
+// pipelined persistent kernel so that both compute the same sums in the same order.  The caller
+// stages: tcam[slot * tstride .. + 9) = current term of the slot's camera; V^-1 of tile landmark l at
+// vinv[l * vstride .. + 6) (RHS mode: b_l at + 6 .. + 9); sseg[l] = tile-relative segment
+// offsets (nl + 1 entries); sbeg[s] = first camera-sorted position of slot s; srow[s] = its
+// camera-major row.  lm = the observation's landmark within the tile, meta = pos | slot << 8.
+// mid() runs between the two barriers of phase 1.  sv and sg may share storage.  Every thread of
+// the block must call it.
+template <int MODE, typename SegT, typename BegT, typename Mid>
+__device__ __forceinline__ void f32_tile_core(bool active, int n, int ns, int lm, int meta,
+                                              const float (&jp)[18], const float (&jl)[6],
+                                              const float* tcam, int tstride, const float* vinv,
+                                              int vstride, const SegT* sseg, const BegT* sbeg,
+                                              const int* srow, float (*sv)[3], float (*sg)[9],
+                                              float* __restrict__ partial, Mid&& mid) {
+  const int tid = threadIdx.x;
+  // phase 1: u = J_p t, v = J_l^T u
+  float u0 = 0.f, u1 = 0.f;
+  if (MODE == kModeSeries && active) {
+    const float* tc = tcam + (size_t)(meta >> 8) * tstride;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      u0 += jp[j] * tc[j];
+      u1 += jp[9 + j] * tc[j];
+    }
+  }
+  __syncthreads();
+  mid();
+  if (MODE == kModeSeries && active) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sv[tid][k] = jl[k] * u0 + jl[3 + k] * u1;
+  }
+  __syncthreads();
+  // phase 2: each observation thread sums its landmark's v in segment order, applies V^-1 and
+  // forms J_l z
+  if (active) {
+    float s3[3];
+    const float* vl = vinv + (size_t)lm * vstride;
+    if (MODE == kModeSeries) {
+      s3[0] = s3[1] = s3[2] = 0.f;
+      const int a = sseg[lm], b = sseg[lm + 1];
+      for (int q = a; q < b; ++q) {
+        s3[0] += sv[q][0];
+        s3[1] += sv[q][1];
+        s3[2] += sv[q][2];
+      }
+    } else {
+      s3[0] = vl[6];
+      s3[1] = vl[7];
+      s3[2] = vl[8];
+    }
+    const float z0 = vl[0] * s3[0] + vl[1] * s3[1] + vl[2] * s3[2];
+    const float z1 = vl[1] * s3[0] + vl[3] * s3[1] + vl[4] * s3[2];
+    const float z2 = vl[2] * s3[0] + vl[4] * s3[1] + vl[5] * s3[2];
+    u0 = jl[0] * z0 + jl[1] * z1 + jl[2] * z2;
+    u1 = jl[3] * z0 + jl[4] * z1 + jl[5] * z2;
+  }
+  __syncthreads();  // sv and the V^-1 staging may alias sg
+  if (active) {
+    float* g = sg[meta & 0xff];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) g[j] = jp[j] * u0 + jp[9 + j] * u1;
+  }
+  __syncthreads();
+  // phase 3: one warp per slot; lane 3 k + c sums component k over the c-th third of the
+  // slot's rows in row order, and the three thirds are added in chunk order
+  const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  const int kc = lane / 3, cc = lane - 3 * kc;
+  for (int sl = warp; sl < ns; sl += nw) {
+    const int beg = sbeg[sl], end = (sl + 1 < ns) ? (int)sbeg[sl + 1] : n;
+    const int chunk = (end - beg + 2) / 3;
+    float acc = 0.f;
+    if (lane < 27) {
+      const int q0 = beg + cc * chunk, q1 = min(q0 + chunk, end);
+      for (int q = q0; q < q1; ++q) acc += sg[q][kc];
+    }
+    const float a1 = __shfl_down_sync(0xffffffffu, acc, 1);
+    const float a2 = __shfl_down_sync(0xffffffffu, acc, 2);
+    if (lane < 27 && cc == 0) partial[(size_t)srow[sl] * 9 + kc] = (acc + a1) + a2;
+  }
+}
+
 // FP32-bulk tile body (blockDim.x == kTileObs; every thread must call it).  The same sums as
 // tile_matvec_body, arranged for float arithmetic, where redundant FMAs are cheap and barriers
 // are not:
@@ -173,12 +255,12 @@ __device__ __forceinline__ void tile_matvec_body(const Topology& tp, int tile,
 //   phase 2  every observation thread sums its own landmark's v in segment order and applies
 //            V^-1 (the same sum and the same z in every thread of the landmark), then scatters
 //            g = J_p^T (J_l z) to its camera-sorted position;
-//   phase 3  one warp per slot: lanes take rows beg + lane, beg + lane + 32, ...; a fixed
-//            shuffle tree adds the 9 components; lane 0 writes the slot's row.
+//   phase 3  one warp per slot: 27 lanes, one per (component, third of the slot's rows), sum
+//            their rows in order; the thirds are added in order and written to the slot's row.
 template <int MODE>
 __device__ __forceinline__ void tile_matvec_body_f32(const Topology& tp, int tile,
                                                      const float* __restrict__ J,
-                                                     const float* __restrict__ t_cm,
+                                                     const float* __restrict__ t_cam,
                                                      const double* __restrict__ b_l,
                                                      const float* __restrict__ Vinv,
                                                      float* __restrict__ partial,
@@ -203,8 +285,9 @@ __device__ __forceinline__ void tile_matvec_body_f32(const Topology& tp, int til
     sm.sbeg[i] = tp.slot_beg[th.S0 + i];
     sm.srow[i] = r;
     if (MODE == kModeSeries) {
+      const int c = tp.slot_cam[th.S0 + i];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) sm.tcam[i][k] = __ldcg(t_cm + (size_t)r * 9 + k);
+      for (int k = 0; k < 9; ++k) sm.tcam[i][k] = __ldcg(t_cam + (size_t)c * kTStride + k);
     }
   }
   if (tid < nl) {
@@ -220,80 +303,9 @@ __device__ __forceinline__ void tile_matvec_body_f32(const Topology& tp, int til
     for (int q = a; q < b; ++q) sm.sv[q][0] = __int_as_float(tid);  // landmark of each obs
   }
   __syncthreads();
-  // phase 1
-  int lm = 0;
-  float u0 = 0.f, u1 = 0.f;
-  if (active) {
-    lm = __float_as_int(sm.sv[tid][0]);
-    if (MODE == kModeSeries) {
-      const float* tc = sm.tcam[meta >> 8];
-#pragma unroll
-      for (int j = 0; j < 9; ++j) {
-        u0 += jp[j] * tc[j];
-        u1 += jp[9 + j] * tc[j];
-      }
-    }
-  }
-  __syncthreads();
-  if (MODE == kModeSeries && active) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) sm.sv[tid][k] = jl[k] * u0 + jl[3 + k] * u1;
-  }
-  __syncthreads();
-  // phase 2
-  if (active) {
-    float s3[3];
-    const float* vl = sm.sg[lm];
-    if (MODE == kModeSeries) {
-      s3[0] = s3[1] = s3[2] = 0.f;
-      const int a = sm.sseg[lm], b = sm.sseg[lm + 1];
-      for (int q = a; q < b; ++q) {
-        s3[0] += sm.sv[q][0];
-        s3[1] += sm.sv[q][1];
-        s3[2] += sm.sv[q][2];
-      }
-    } else {
-      s3[0] = vl[6];
-      s3[1] = vl[7];
-      s3[2] = vl[8];
-    }
-    const float z0 = vl[0] * s3[0] + vl[1] * s3[1] + vl[2] * s3[2];
-    const float z1 = vl[1] * s3[0] + vl[3] * s3[1] + vl[4] * s3[2];
-    const float z2 = vl[2] * s3[0] + vl[4] * s3[1] + vl[5] * s3[2];
-    const float w0 = jl[0] * z0 + jl[1] * z1 + jl[2] * z2;
-    const float w1 = jl[3] * z0 + jl[4] * z1 + jl[5] * z2;
-    u0 = w0;  // keep g's inputs; the staging array sg still holds V^-1 until the barrier
-    u1 = w1;
-  }
-  __syncthreads();
-  if (active) {
-    float* g = sm.sg[meta & 0xff];
-#pragma unroll
-    for (int j = 0; j < 9; ++j) g[j] = jp[j] * u0 + jp[9 + j] * u1;
-  }
-  __syncthreads();
-  // phase 3: one warp per slot
-  const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-  for (int sl = warp; sl < ns; sl += nw) {
-    const int beg = sm.sbeg[sl], end = (sl + 1 < ns) ? (int)sm.sbeg[sl + 1] : n;
-    float acc[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) acc[k] = 0.f;
-    for (int q = beg + lane; q < end; q += 32) {
-#pragma unroll
-      for (int k = 0; k < 9; ++k) acc[k] += sm.sg[q][k];
-    }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
-    }
-    if (lane == 0) {
-      float* out = partial + (size_t)sm.srow[sl] * 9;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) out[k] = acc[k];
-    }
-  }
+  const int lm = active ? __float_as_int(sm.sv[tid][0]) : 0;
+  f32_tile_core<MODE>(active, n, ns, lm, meta, jp, jl, &sm.tcam[0][0], 9, &sm.sg[0][0], 9, sm.sseg,
+                      sm.sbeg, sm.srow, sm.sv, sm.sg, partial, [] {});
 }
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
@@ -301,38 +313,49 @@ __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
   return *(const volatile unsigned*)p;
 }
 
+// Sum of one chunk of a camera's slot rows, component k: rows [q0, q1) in row order (loads are
+// issued 16 floats or 8 doubles at a time; the additions are in row order either way).
+template <typename PT>
+__device__ __forceinline__ double cam_chunk_sum(const PT* __restrict__ partial, int q0, int q1,
+                                                int k) {
+  constexpr int B = sizeof(PT) == 4 ? 16 : 8;
+  double pc = 0.0;
+  for (int rb = q0; rb < q1; rb += B) {
+    PT buf[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+      buf[j] = (rb + j < q1) ? __ldcg(partial + (size_t)(rb + j) * 9 + k) : (PT)0;
+#pragma unroll
+    for (int j = 0; j < B; ++j) pc += (double)buf[j];
+  }
+  return pc;
+}
+
 // Camera body for cameras [cam0, cam0 + per_block): thread (c, k) sums component k of the
-// camera's contiguous slot rows (loads issued 8 at a time, summed in a fixed order), applies
-// row k of U^-1, updates x and writes the new term into the camera's rows of t_cm; then the 9
-// threads of the camera add their squared term and x components (in component order) into the
-// camera's pair cam_norm[c] = (||t_c||^2, ||x_c||^2).  Cameras of problems whose series has
-// stopped are left as they are.  FP64 work is one add per slot row and component: every FP64
-// warp instruction costs 16 pipe cycles on GB300, so no shuffle trees are used for the slot
-// sums.  ys and y2 are shared [per_block][9] arrays.  Every thread of the block must call it.
+// camera's contiguous slot rows (chunk by chunk, cam_chunk_rows rows per chunk, the chunks in
+// order), applies row k of U^-1, updates x and writes the new term t_cam[c]; then the 9 threads
+// of the camera add their squared term and x components (in component order) into the camera's
+// pair cam_norm[c] = (||t_c||^2, ||x_c||^2).  Cameras of problems whose series has stopped are
+// left as they are.  FP64 work is one add per slot row and component: every FP64 warp
+// instruction costs 16 pipe cycles on GB300, so no shuffle trees are used for the slot sums.
+// ys and y2 are shared [per_block][9] arrays.  Every thread of the block must call it.
 template <typename PT, int MODE>
 __device__ __forceinline__ void camera_body(const Topology& tp, int cam0, int per_block,
                                             const PT* __restrict__ partial,
                                             const double* __restrict__ b_p,
                                             const double* __restrict__ Uinv,
-                                            double* __restrict__ x, PT* __restrict__ t_cm,
+                                            double* __restrict__ x, PT* __restrict__ t_cam,
                                             const SeriesState* st, double* __restrict__ cam_norm,
                                             double (*ys)[9], double (*y2)[9]) {
   const int tid = threadIdx.x;
   const int cl = tid / 9, k = tid - cl * 9;
   const int c = cam0 + cl;
   const bool cam_ok = cl < per_block && c < tp.n_cams && !ld_volatile(&st[tp.cam_prob[c]].done);
-  int r0 = 0, r1 = 0;
-  if (cam_ok) {
-    r0 = tp.cam_slot_ptr[c];
-    r1 = tp.cam_slot_ptr[c + 1];
-  }
   double y = 0.0;
-  for (int rb = r0; rb < r1; rb += 8) {
-    PT buf[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) buf[j] = (rb + j < r1) ? __ldcg(partial + (size_t)(rb + j) * 9 + k) : (PT)0;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) y += (double)buf[j];
+  if (cam_ok) {
+    const int r0 = tp.cam_slot_ptr[c], r1 = tp.cam_slot_ptr[c + 1];
+    const int C = cam_chunk_rows(r1 - r0);
+    for (int q0 = r0; q0 < r1; q0 += C) y += cam_chunk_sum(partial, q0, min(q0 + C, r1), k);
   }
   if (MODE == kModeRhs && cam_ok) y = b_p[(size_t)c * 9 + k] - y;  // b~ = b_p - W V^-1 b_l
   if (cl < per_block) ys[cl][k] = y;
@@ -349,8 +372,7 @@ __device__ __forceinline__ void camera_body(const Topology& tp, int cam0, int pe
       xv = __ldcg(x + (size_t)c * 9 + k) + v;
     }
     x[(size_t)c * 9 + k] = xv;
-    const PT tv = (PT)v;
-    for (int q = r0; q < r1; ++q) t_cm[(size_t)q * 9 + k] = tv;
+    t_cam[(size_t)c * kTStride + k] = (PT)v;
   }
   __syncthreads();
   if (cl < per_block) {

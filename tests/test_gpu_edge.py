@@ -18,10 +18,10 @@ def poba():
     return m
 
 
-def check_series(poba, p, lam=1e-3, m=6, tol=1e-10):
+def check_series(poba, p, lam=1e-3, m=6, tol=1e-10, precision=0):
     ref = OracleRef(p)
     h = poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, p.weights,
-                       options=poba.ba_default_options(eps=0.0, max_inner=m))
+                       precision=precision, options=poba.ba_default_options(eps=0.0, max_inner=m))
     poba.ba_linearize(h)
     poba.ba_solve_schur_power(h, lam)
     dxp, dxl = poba.ba_get_step(h)
@@ -55,6 +55,18 @@ def test_longest_track_and_wide_tiles(poba):
     p.lm_idx = np.concatenate([p.lm_idx, add_l])
     assert np.sum(p.lm_idx == 0) == 256
     check_series(poba, p)
+    # FP32-bulk: a tile with more than 128 distinct cameras takes the persistent kernel without
+    # the copy pipeline; both persistent forms and the per-term launches agree bit for bit
+    h32 = check_series(poba, p, tol=1e-4, precision=1)
+    steps = []
+    for mode in (1, 2, 3):
+        h = poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, precision=1,
+                           options=poba.ba_default_options(eps=0.0, max_inner=6, series_exec=mode))
+        poba.ba_linearize(h)
+        poba.ba_solve_schur_power(h, 1e-3)
+        steps.append(poba.ba_get_step(h))
+    for st in steps[1:]:
+        assert np.array_equal(st[0], steps[0][0]) and np.array_equal(st[1], steps[0][1])
 
 
 def test_no_observations(poba):
@@ -160,14 +172,14 @@ def test_nonfinite_state_is_reported(poba):
     assert np.isfinite(poba.ba_cost(h))
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_grid_barrier_timeout_is_reported_and_recoverable(poba, precision):
+@pytest.mark.parametrize("precision,mode", [(0, 2), (1, 2), (1, 3)])
+def test_grid_barrier_timeout_is_reported_and_recoverable(poba, precision, mode):
     """A grid-barrier wait of the persistent series kernel that runs out (limit of one clock
     cycle) makes the solve return BA_ERR_TIMEOUT; the context stays usable and the next solve
     with the normal limit gives the usual result."""
     p = bal_synth.make_problem(40, 2000, track=("uniform", 3, 4), visibility="clustered", seed=119)
     h = poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, precision=precision,
-                       options=poba.ba_default_options(eps=0.0, max_inner=6, series_exec=2))
+                       options=poba.ba_default_options(eps=0.0, max_inner=6, series_exec=mode))
     poba.ba_linearize(h)
     ref = poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, precision=precision,
                          options=poba.ba_default_options(eps=0.0, max_inner=6, series_exec=1))

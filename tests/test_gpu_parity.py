@@ -145,10 +145,11 @@ def test_solve_is_deterministic(poba, case):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_series_exec_modes_agree_bitwise(poba, case, precision):
-    """Per-kernel launches, the captured graph and the persistent kernel give the same step."""
+    """Per-kernel launches, the captured graph and the persistent kernel (with and without the
+    FP32 copy pipeline) give the same step."""
     name, p, ref = case
     res = []
-    for mode in (0, 1, 2):
+    for mode in (0, 1, 2, 3):
         h = make(poba, p, precision=precision, eps=0.01, max_inner=12, series_exec=mode)
         poba.ba_linearize(h)
         info = poba.ba_solve_schur_power(h, 1e-2)
