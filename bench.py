@@ -157,9 +157,10 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(precision: str):
-    """DRAM bytes per series term of the persistent kernel from the committed ncu summary, if the
-    kernel source is unchanged since the capture; else None."""
+def profiled_traffic(precision: str, form: int):
+    """DRAM bytes per series term of the persistent kernel in the given form (3 plain, 4 with the
+    copy pipeline) from the committed ncu summary, if the kernel source is unchanged since the
+    capture; else None."""
     path = os.path.join(ROOT, "profiles", f"series_persistent_{WORKLOAD}.json")
     try:
         d = json.load(open(path))
@@ -167,7 +168,10 @@ def profiled_traffic(precision: str):
         return None
     if d.get("kernel_source_sha") != kernel_source_sha():
         return None
-    return d.get(precision, {}).get("dram_bytes_per_term")
+    e = d.get(precision, {})
+    if e.get("form") not in (None, form):
+        return None
+    return e.get("dram_bytes_per_term")
 
 
 # ---------------------------------------------------------------------------------------
@@ -285,6 +289,7 @@ def run_poba(args):
     for name, prec in (("fp64", poba.BA_FP64), ("fp32_bulk", poba.BA_FP32_BULK)):
         h = make(prec)
         lm_block(h, args.warmup, False)
+        tuned = poba.ba_autotune(h, trials=3)  # picks the series execution form (untimed)
         reset(h)
         poba.ba_set_timing(h, True)
         launches0 = poba.ba_kernel_launches(h)
@@ -299,7 +304,8 @@ def run_poba(args):
         total_ms = max_over_ranks(sum(ms))
         timing = poba.ba_get_timing(h)
         poba.ba_set_timing(h, False)
-        results[name] = dict(h=h, ms=ms, total_ms=total_ms, timing=timing, launches=launches)
+        results[name] = dict(h=h, ms=ms, total_ms=total_ms, timing=timing, launches=launches,
+                             tuned=tuned)
 
     # series solves/s at the current linearisation of each handle
     for name, r in results.items():
@@ -376,19 +382,26 @@ def run_poba(args):
     r_slots = schedule_slots(p)
 
     def roofline(name):
-        """Dominant kernel: the persistent series kernel (tile + camera phases and the two grid
-        barriers of every term).  Its timing class counts executed terms, so ms / count is the
-        average time of one term."""
+        """Dominant kernel: the series (one term = tile phase and camera phase, plus the two
+        grid barriers in a persistent form).  The timing classes count executed terms, so
+        ms / count is the average time of one term."""
         r = results[name]
         cls = max(r["timing"], key=lambda k: r["timing"][k][0])
-        ms, cnt = r["timing"]["series_tile"]
+        ms_t, cnt = r["timing"]["series_tile"]
+        ms_c, _ = r["timing"]["series_camera"]
         s = 8 if name == "fp64" else 4
         nb, nf = series_term_units(p, r_slots, s)
-        avg_s = ms / 1e3 / max(cnt, 1)
-        traffic = profiled_traffic(name)
+        avg_s = (ms_t + ms_c) / 1e3 / max(cnt, 1)
+        form = r["tuned"]["exec"]
         prec = "double" if name == "fp64" else "float"
-        common = {"kernel": f"series_persistent_kernel<{prec}> (one series term: tile phase, "
-                            "camera phase, two grid barriers)",
+        kernel = {1: f"tile_matvec_kernel<{prec}, 0> + camera_step_kernel<{prec}, 0> "
+                     "(replayed CUDA graph, one pair of launches per term)",
+                  3: f"series_persistent_kernel<{prec}> (one series term: tile phase, camera "
+                     "phase, two grid barriers)",
+                  4: "series_persistent_f32_kernel (one series term: pipelined tile phase, "
+                     "camera phase, two grid barriers)"}[form]
+        traffic = profiled_traffic(name, form)
+        common = {"kernel": kernel, "series_form": r["tuned"],
                   "traffic": traffic, "algorithmic_bytes_per_term": nb,
                   "algorithmic_flops_per_term": nf, "avg_term_us": avg_s * 1e6, "terms": cnt,
                   "dominant_class": cls}
@@ -459,6 +472,7 @@ def run_poba(args):
         "memory_bytes": mem_gpu,
         "explicit_S_bytes": explicit_s_bytes(p),
         "kernels": kernel_avgs(r64),
+        "series_form": r64["tuned"],
         "fp32_bulk": {"value": whole_job_rate(args.steps, world, r32["total_ms"] / 1e3),
                       "unit": "LM iterations/s",
                       "ms_per_step": r32["total_ms"] / args.steps, "roofline": roof32,
@@ -467,7 +481,8 @@ def run_poba(args):
                       "time_to_1pct_cost_s": traj["fp32_bulk"]["time_to_tau_s"],
                       "final_cost": traj["fp32_bulk"]["final"],
                       "final_cost_rel_to_fp64": traj["fp32_bulk"]["final"] / traj["fp64"]["final"] - 1.0,
-                      "memory_bytes": mem_gpu32, "kernels": kernel_avgs(r32)},
+                      "memory_bytes": mem_gpu32, "kernels": kernel_avgs(r32),
+                      "series_form": r32["tuned"]},
         "batched": batched,
         "cpu_baseline": cpu,
     }
@@ -517,6 +532,7 @@ def batched_section(args, poba, torch, stream, dev, max_over_ranks, barrier):
                 n_not_spd)
 
     solve()  # warm-up solve
+    tuned = poba.ba_autotune(hb, trials=2)  # picks the series execution form (untimed)
     launches0 = poba.ba_kernel_launches(hb)
     barrier()
     runs = [solve() for _ in range(max(1, args.batch_solves))]
@@ -537,6 +553,7 @@ def batched_section(args, poba, torch, stream, dev, max_over_ranks, barrier):
         "lm_steps_per_solve": runs[-1][3],
         "converged": runs[-1][4],
         "not_spd_iterations": runs[-1][5],
+        "series_form": tuned,
         "gpu_launches": int(launches),
         "solves": n_solves,
         "memory_bytes": poba.ba_memory_footprint(hb),

@@ -77,13 +77,15 @@ typedef struct {
   int32_t max_inner;    /* cap on series terms beyond x(0), Sec. 5.1: 20 */
   int32_t damping_mode; /* 0: D^T D = diag(J^T J) clamped to [1e-6, 1e32]; 1: D = I */
   int32_t series_exec;  /* how the series loop runs: 0 one launch per kernel, 1 the same launches
-                           replayed as a captured CUDA graph, 2 one persistent cooperative kernel
-                           for all terms with bounded grid barriers (default; falls back to 1
-                           when the device cannot make all its blocks co-resident); in
-                           BA_FP32_BULK mode it stages each tile's inputs with asynchronous
-                           bulk copies issued ahead of the tile (when every tile has at most
-                           128 distinct cameras), 3 the persistent kernel without that
-                           pipeline.  All modes give bitwise-equal results. */
+                           replayed as a captured CUDA graph, 3 one persistent cooperative kernel
+                           for all terms with bounded grid barriers, 4 (BA_FP32_BULK) the
+                           persistent kernel staging each tile's inputs with asynchronous bulk
+                           copies issued ahead of the tile (needs at most 128 distinct cameras
+                           per tile, else as 3), 2 (default) the handle's choice: 4 when the
+                           float Jacobians exceed half the L2 cache, else 3, or what
+                           ba_autotune measured.  Forms a device cannot run fall back (4 to 3,
+                           3 to 1: all blocks of a persistent kernel must be co-resident).  All
+                           forms give bitwise-equal results. */
 } ba_options;
 
 typedef struct {
@@ -283,10 +285,23 @@ ba_status ba_lm_solve_batch(ba_handle* h, ba_step_info* infos, int32_t* n_steps)
 /* F(x) of each problem at the current state: costs[P] (host), float64, fixed order. */
 ba_status ba_cost_batch(ba_handle* h, double* costs);
 
+/* Autotuner of the series execution (no counterpart in the paper; the schedule choice of the
+ * batched form).  On the handle's current linearisation (linearising first if needed) it times
+ * `trials` series solves (damp, invert, max_inner terms, back-substitution; after one warm-up)
+ * at lambda0 in each form the device can run -- the replayed CUDA graph of per-term launches,
+ * the persistent kernel at 1, 2 or 3 blocks per SM, and in BA_FP32_BULK mode the persistent
+ * kernel with the copy pipeline at 1, 2 or 3 blocks per SM -- and makes the fastest the form
+ * that series_exec 2 uses.  All forms give bitwise-equal results, so tuning changes only
+ * speed.  Overwrites the last step (as ba_solve_schur_power does).  *exec_out (may be NULL)
+ * receives the chosen form (1, 3 or 4), *blocks_per_sm_out (may be NULL) its blocks per SM (0
+ * for the graph).  Synchronises.  Errors: BA_ERR_INVALID_ARG (trials < 1), and those of
+ * ba_solve_schur_power. */
+ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* blocks_per_sm_out);
+
 /* Free all device memory of the handle (and its own stream, if it created one). NULL is OK. */
 ba_status ba_destroy(ba_handle* h);
 
-/* Phase timeline of the last persistent series solve (series_exec 2 or 3): for each executed term
+/* Phase timeline of the last persistent series solve: for each executed term
  * (at most 64), five %globaltimer readings in ns taken by the last block of the grid (a block
  * that always has camera work) -- term start, end of its tile phase, release of the first grid
  * barrier, end of its camera phase, release of the second barrier.  Copies min(capacity,

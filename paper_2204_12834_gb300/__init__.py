@@ -27,7 +27,7 @@ __all__ = ["PobaError", "Handle", "ba_default_options", "ba_create", "ba_set_opt
            "BA_FP32_BULK", "library", "from_problem", "ba_cost_noalloc", "BA_NOALLOC_MAX_CAMS",
            "ba_get_series_trace", "ba_set_barrier_timeout", "ba_create_batch",
            "ba_get_batch_layout", "ba_get_series_state", "ba_lm_step_batch", "ba_lm_solve_batch",
-           "ba_cost_batch", "batch_from_problems"]
+           "ba_cost_batch", "batch_from_problems", "ba_autotune"]
 
 BA_NOALLOC_MAX_CAMS = 4096
 
@@ -371,6 +371,14 @@ def ba_get_series_trace(h: Handle):
 
 def ba_set_barrier_timeout(h: Handle, cycles: int):
     _check(library().ba_set_barrier_timeout(h.ptr, int(cycles)), "ba_set_barrier_timeout")
+
+
+def ba_autotune(h: Handle, trials: int = 3) -> dict:
+    """Time the series execution forms on the current linearisation and keep the fastest for
+    series_exec 2.  Returns {"exec": 1 | 3 | 4, "blocks_per_sm": k}."""
+    e, k = C.c_int32(), C.c_int32()
+    _check(library().ba_autotune(h.ptr, int(trials), C.byref(e), C.byref(k)), "ba_autotune")
+    return {"exec": e.value, "blocks_per_sm": k.value}
 
 
 def ba_destroy(h: Handle):

@@ -119,11 +119,14 @@ struct ba_handle {
   int graph_nodes = 0;
   bool graph_timing = false;
   bool graph_active = false;
-  int persist_grid = 0;                  // blocks of the persistent kernel (0: unavailable)
-  int pipe_grid = 0;                     // blocks of the pipelined FP32 kernel (0: not used)
-  CamRounds persist_rounds{}, pipe_rounds{};  // camera schedules for those grids
+  // persistent kernels: grid = blocks per SM x SMs; camera schedules for 1..3 blocks per SM
+  int sms = 0;
+  int plain_max = 0, pipe_max = 0;       // occupancy limits (0: kernel unavailable)
+  int plain_k = 0, pipe_k = 0;           // blocks per SM in use
+  CamRounds plain_rounds[3]{}, pipe_rounds[3]{};
+  int auto_exec = 1;                     // form used for series_exec 2: 1, 3 or 4
   long long barrier_timeout = 1LL << 33;  // clock cycles a block waits at a grid barrier
-  int last_exec = -1;                    // series_exec of the last solve
+  int last_exec = -1;                    // execution form of the last solve (1, 0, 3 or 4)
   uint64_t launches = 0;
 
   // kernel timing: event pairs per class; series classes have one pair per term
@@ -147,7 +150,7 @@ bool valid_options(const ba_options& o, std::string* why) {
   if (o.max_lm < 0 || o.max_lm > 100000) { *why = "max_lm out of range"; return false; }
   if (o.max_inner < 0 || o.max_inner > 10000) { *why = "max_inner out of range [0, 10000]"; return false; }
   if (o.damping_mode != 0 && o.damping_mode != 1) { *why = "damping_mode must be 0 or 1"; return false; }
-  if (o.series_exec < 0 || o.series_exec > 3) { *why = "series_exec must be 0, 1, 2 or 3"; return false; }
+  if (o.series_exec < 0 || o.series_exec > 4) { *why = "series_exec must be in [0, 4]"; return false; }
   return true;
 }
 
@@ -223,7 +226,7 @@ void collect_timing(ba_handle* h, int terms_run, bool series_ran) {
     }
     h->pending[cls] = false;
   }
-  if (series_ran && h->last_exec >= 2) {
+  if (series_ran && h->last_exec >= 3) {
     // one pair around the persistent kernel, counted once per executed term
     const int i = ev_index(h, kTTile, 1);
     if (terms_run >= 1 && cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) == cudaSuccess) {
@@ -316,7 +319,8 @@ ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active, b
           n_list = &h->sgl->n_list;
         }
         tmark(h, kTTile, 1, 0);
-        CK(launch_series_pipelined(tp, h->pipe_rounds, h->pipe_grid, list, n_list, J, Vi, h->Uinv, h->x,
+        CK(launch_series_pipelined(tp, h->pipe_rounds[h->pipe_k - 1], h->pipe_k * h->sms, list,
+                                   n_list, J, Vi, h->Uinv, h->x,
                                    (float*)h->t_cam, part, h->cam_norm, h->st, h->sgl, h->gs,
                                    h->opts.max_inner, h->opts.eps, h->barrier_timeout, h->trace,
                                    s));
@@ -326,7 +330,8 @@ ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active, b
     }
     if (!pipelined) {
       tmark(h, kTTile, 1, 0);
-      CK(launch_series_persistent<T>(tp, h->persist_rounds, h->persist_grid, J, Vi, h->Uinv, h->x,
+      CK(launch_series_persistent<T>(tp, h->plain_rounds[h->plain_k - 1], h->plain_k * h->sms, J,
+                                     Vi, h->Uinv, h->x,
                                      (T*)h->t_cam, part,
                                      h->cam_norm, h->st, h->sgl, h->gs, h->opts.max_inner,
                                      h->opts.eps, h->barrier_timeout, h->trace, s));
@@ -346,12 +351,14 @@ ba_status run_series_body(ba_handle* h, bool use_active) {
     ba_status st = ensure_events(h);
     if (st != BA_OK) return st;
   }
-  int mode = h->opts.series_exec;
-  if (mode >= 2 && h->persist_grid <= 0) mode = 1;
+  // execution form: 0 per-term launches, 1 graph replay, 3 persistent, 4 persistent with the
+  // FP32 copy pipeline; series_exec 2 takes the handle's choice (heuristic or ba_autotune)
+  int mode = h->opts.series_exec == 2 ? h->auto_exec : h->opts.series_exec;
+  if (mode == 4 && h->pipe_k <= 0) mode = 3;
+  if (mode == 3 && h->plain_k <= 0) mode = 1;
   h->last_exec = mode;
-  if (mode >= 2) {
-    // series_exec 2: FP32-bulk takes the pipelined kernel where it applies; 3: never
-    const bool pipelined = mode == 2 && h->f32() && h->pipe_grid > 0;
+  if (mode >= 3) {
+    const bool pipelined = mode == 4;
     ba_status st = h->f32() ? seq_series_persistent<float>(h, s, use_active, pipelined)
                             : seq_series_persistent<double>(h, s, use_active, false);
     if (st == BA_OK) h->pending[kTRhs] = h->pending[kTBack] = h->timing;
@@ -584,19 +591,29 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     const int per_sm = persistent_blocks_per_sm(h->f32());
-    h->persist_grid = (coop && per_sm > 0) ? per_sm * sms : 0;
-    if (h->f32() && h->persist_grid > 0 && S.max_slots_per_tile <= kTileSlots) {
+    h->sms = sms;
+    h->plain_max = (coop && per_sm > 0) ? (per_sm < 3 ? per_sm : 3) : 0;
+    if (h->f32() && h->plain_max > 0 && S.max_slots_per_tile <= kTileSlots) {
       const int pipe_per_sm = pipelined_blocks_per_sm();
-      h->pipe_grid = pipe_per_sm > 0 ? pipe_per_sm * sms : 0;
+      h->pipe_max = pipe_per_sm > 0 ? (pipe_per_sm < 3 ? pipe_per_sm : 3) : 0;
     }
+    h->plain_k = h->plain_max;
+    h->pipe_k = h->pipe_max;
+    // default form: persistent; FP32-bulk Jacobians that do not fit in half the L2 cache take
+    // the copy pipeline (ba_autotune measures instead)
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    const double j_bytes = 24.0 * (h->f32() ? 4.0 : 8.0) * (double)no;
+    h->auto_exec = h->plain_k > 0 ? 3 : 1;
+    if (h->pipe_k > 0 && j_bytes > 0.5 * (double)l2) h->auto_exec = 4;
     cudaGetLastError();
   }
-  // camera schedule of the persistent kernels (rounds per grid size)
+  // camera schedules of the persistent kernels (rounds per grid size)
   CamSchedule cs;
   build_cam_schedule(S, &cs);
-  CamRoundList rl_p, rl_q;
-  if (h->persist_grid > 0) build_cam_rounds(cs, nc, h->persist_grid, &rl_p);
-  if (h->pipe_grid > 0) build_cam_rounds(cs, nc, h->pipe_grid, &rl_q);
+  CamRoundList rl[2][3];
+  for (int k = 1; k <= h->plain_max; ++k) build_cam_rounds(cs, nc, k * h->sms, &rl[0][k - 1]);
+  for (int k = 1; k <= h->pipe_max; ++k) build_cam_rounds(cs, nc, k * h->sms, &rl[1][k - 1]);
 
   // ---- arena layout
   const size_t bulk = h->f32() ? sizeof(float) : sizeof(double);
@@ -655,16 +672,16 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   items.push_back({(void**)&d_tile_rec, S.tile_rec.size() > 0 ? S.tile_rec.size() : 16});
   items.push_back({(void**)&h->n_tiles_dev, sizeof(int32_t)});
   int32_t *d_cam_item, *d_item_q;
-  int32_t* d_rl[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
-  const CamRoundList* rls[2] = {&rl_p, &rl_q};
+  int32_t* d_rl[2][3][3] = {};
   items.push_back({(void**)&d_cam_item, sizeof(int32_t) * cs.cam_item.size()});
   items.push_back({(void**)&d_item_q, sizeof(int32_t) * (cs.item_q.size() > 0 ? cs.item_q.size() : 1)});
-  for (int g = 0; g < 2; ++g) {
-    if (rls[g]->round_cam.empty()) continue;
-    items.push_back({(void**)&d_rl[g][0], sizeof(int32_t) * rls[g]->round_cam.size()});
-    items.push_back({(void**)&d_rl[g][1], sizeof(int32_t) * rls[g]->round_item.size()});
-    items.push_back({(void**)&d_rl[g][2], sizeof(int32_t) * rls[g]->block_round.size()});
-  }
+  for (int f = 0; f < 2; ++f)
+    for (int k = 0; k < 3; ++k) {
+      if (rl[f][k].round_cam.empty()) continue;
+      items.push_back({(void**)&d_rl[f][k][0], sizeof(int32_t) * rl[f][k].round_cam.size()});
+      items.push_back({(void**)&d_rl[f][k][1], sizeof(int32_t) * rl[f][k].round_item.size()});
+      items.push_back({(void**)&d_rl[f][k][2], sizeof(int32_t) * rl[f][k].block_round.size()});
+    }
   if (n_probs > 1) {
     items.push_back({(void**)&h->tile_list, sizeof(int4) * 2 * (size_t)S.n_tiles});
     items.push_back({(void**)&h->list_off, sizeof(int32_t) * P});
@@ -744,17 +761,18 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
       {h->n_tiles_dev, &S.n_tiles, sizeof(int32_t)},
       {d_cam_item, cs.cam_item.data(), sizeof(int32_t) * cs.cam_item.size()},
       {d_item_q, cs.item_q.data(), sizeof(int32_t) * cs.item_q.size()},
-      {d_rl[0][0], rl_p.round_cam.data(), sizeof(int32_t) * rl_p.round_cam.size()},
-      {d_rl[0][1], rl_p.round_item.data(), sizeof(int32_t) * rl_p.round_item.size()},
-      {d_rl[0][2], rl_p.block_round.data(), sizeof(int32_t) * rl_p.block_round.size()},
-      {d_rl[1][0], rl_q.round_cam.data(), sizeof(int32_t) * rl_q.round_cam.size()},
-      {d_rl[1][1], rl_q.round_item.data(), sizeof(int32_t) * rl_q.round_item.size()},
-      {d_rl[1][2], rl_q.block_round.data(), sizeof(int32_t) * rl_q.block_round.size()},
       {h->obs, obs_s.data(), sizeof(double) * 2 * no},
       {h->cams, cams.data(), sizeof(double) * nc * 9},
       {h->lms, lms_i.data(), sizeof(double) * nl * 3},
   };
   if (h->weighted) ups.push_back({h->sqrt_w, sw_s.data(), sizeof(double) * no});
+  for (int f = 0; f < 2; ++f)
+    for (int k = 0; k < 3; ++k) {
+      if (rl[f][k].round_cam.empty()) continue;
+      ups.push_back({d_rl[f][k][0], rl[f][k].round_cam.data(), sizeof(int32_t) * rl[f][k].round_cam.size()});
+      ups.push_back({d_rl[f][k][1], rl[f][k].round_item.data(), sizeof(int32_t) * rl[f][k].round_item.size()});
+      ups.push_back({d_rl[f][k][2], rl[f][k].block_round.data(), sizeof(int32_t) * rl[f][k].block_round.size()});
+    }
   for (auto& u : ups) {
     if (u.bytes == 0) continue;
     e = cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
@@ -799,8 +817,10 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   tp.cam_off = d_cam_off;
   tp.tile_off = d_tile_off;
   tp.tile_rec = d_tile_rec;
-  h->persist_rounds = CamRounds{d_cam_item, d_item_q, d_rl[0][0], d_rl[0][1], d_rl[0][2]};
-  h->pipe_rounds = CamRounds{d_cam_item, d_item_q, d_rl[1][0], d_rl[1][1], d_rl[1][2]};
+  for (int k = 0; k < 3; ++k) {
+    h->plain_rounds[k] = CamRounds{d_cam_item, d_item_q, d_rl[0][k][0], d_rl[0][k][1], d_rl[0][k][2]};
+    h->pipe_rounds[k] = CamRounds{d_cam_item, d_item_q, d_rl[1][k][0], d_rl[1][k][1], d_rl[1][k][2]};
+  }
   *out = h;
   g_last_error.clear();
   return BA_OK;
@@ -866,7 +886,7 @@ ba_status lm_iteration(ba_handle* h, bool batch) {
   CK(cudaMemcpyAsync(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   collect_timing(h, max_terms(h), true);
-  if (h->last_exec >= 2 && h->h_gs->error)
+  if (h->last_exec >= 3 && h->h_gs->error)
     return fail(BA_ERR_TIMEOUT, "a grid barrier of the persistent series kernel timed out");
   // one linearisation covers every problem: it is stale once any problem moved
   for (size_t p = 0; p < P; ++p)
@@ -950,7 +970,7 @@ ba_status ba_solve_schur_power(ba_handle* h, double lambda, ba_series_info* info
   CK(cudaMemcpyAsync(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   collect_timing(h, max_terms(h), true);
-  if (h->last_exec >= 2 && h->h_gs->error)
+  if (h->last_exec >= 3 && h->h_gs->error)
     return fail(BA_ERR_TIMEOUT, "a grid barrier of the persistent series kernel timed out");
   if (P == 1) {
     fill_series_info(h->h_st[0], lambda, info);
@@ -977,6 +997,79 @@ ba_status ba_solve_schur_power(ba_handle* h, double lambda, ba_series_info* info
       return fail(BA_ERR_NOT_SPD, P > 1 ? "problem " + std::to_string(p) +
                                               ": a damped block is not positive definite"
                                         : std::string("a damped block is not positive definite"));
+  return BA_OK;
+}
+
+ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* bps_out) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  if (trials < 1) return fail(BA_ERR_INVALID_ARG, "trials must be >= 1");
+  if (!h->linearized) {
+    seq_linearize(h);
+    ba_status st = check_launch(h, "linearize kernels");
+    if (st != BA_OK) return st;
+    h->linearized = true;
+  }
+  struct Cand {
+    int exec, k;
+  };
+  std::vector<Cand> cands = {{1, 0}};
+  for (int k = 1; k <= h->plain_max; ++k) cands.push_back({3, k});
+  for (int k = 1; k <= h->pipe_max; ++k) cands.push_back({4, k});
+  const ba_options saved = h->opts;
+  const bool saved_timing = h->timing;
+  const int saved_plain = h->plain_k, saved_pipe = h->pipe_k;
+  h->opts.eps = 0.0;  // every form runs max_inner terms
+  h->timing = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ba_status st = BA_OK;
+  float best_ms = 0.f;
+  Cand best{-1, 0};
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    st = fail_cuda(cudaGetLastError(), "cudaEventCreate");
+  launch_set_scalar(h->scalars + 0, h->opts.lambda0, h->stream);
+  h->launches += 1;
+  h->last_solve_lm = false;
+  h->solve_lambda = h->opts.lambda0;
+  for (const Cand& c : cands) {
+    if (st != BA_OK) break;
+    h->opts.series_exec = c.exec;
+    if (c.exec == 3) h->plain_k = c.k;
+    if (c.exec == 4) h->pipe_k = c.k;
+    st = run_solve(h, h->scalars + 0, 0, false);  // warm-up (and graph capture)
+    if (st != BA_OK) break;
+    cudaEventRecord(e0, h->stream);
+    for (int t = 0; t < trials && st == BA_OK; ++t) st = run_solve(h, h->scalars + 0, 0, false);
+    cudaEventRecord(e1, h->stream);
+    if (st != BA_OK) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      st = fail_cuda(e, "autotune");
+      break;
+    }
+    CK(cudaMemcpy(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost));
+    if (c.exec >= 3 && h->h_gs->error) {
+      st = fail(BA_ERR_TIMEOUT, "a grid barrier of the persistent series kernel timed out");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best.exec < 0 || ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  h->opts = saved;
+  h->timing = saved_timing;
+  h->plain_k = saved_plain;
+  h->pipe_k = saved_pipe;
+  if (st != BA_OK) return st;
+  h->auto_exec = best.exec;
+  if (best.exec == 3) h->plain_k = best.k;
+  if (best.exec == 4) h->pipe_k = best.k;
+  if (exec_out) *exec_out = best.exec;
+  if (bps_out) *bps_out = best.k;
   return BA_OK;
 }
 
@@ -1239,7 +1332,7 @@ ba_status ba_get_series_trace(ba_handle* h, int64_t* ns, int32_t capacity, int32
   if (!h || !ns || capacity < 0) return fail(BA_ERR_INVALID_ARG, "bad argument");
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(h->h_st, h->st, sizeof(SeriesState) * h->n_probs, cudaMemcpyDeviceToHost));
-  int terms = h->last_exec >= 2 ? max_terms(h) : 0;
+  int terms = h->last_exec >= 3 ? max_terms(h) : 0;
   if (terms > kTraceTerms) terms = kTraceTerms;
   const int n = terms * kTracePoints < capacity ? terms * kTracePoints : capacity;
   if (n > 0) CK(cudaMemcpy(ns, h->trace, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));

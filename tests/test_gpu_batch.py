@@ -84,7 +84,7 @@ def test_series_per_problem_matches_oracle(poba, small, precision, tol, lam):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("series_exec", [0, 2, 3])
+@pytest.mark.parametrize("series_exec", [0, 2, 3, 4])
 def test_lm_equals_individual_handles_bitwise(poba, small, precision, series_exec):
     opt = dict(max_lm=12, series_exec=series_exec)
     hb = batch(poba, small, precision=precision, **opt)

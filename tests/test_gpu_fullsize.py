@@ -80,18 +80,20 @@ def test_full_series_fp64_and_fp32(poba, problem, oracle_ref, eps, m):
 
 
 def test_fp32_persistent_forms_agree_bitwise(poba, problem):
-    """FP32-bulk at full size: the pipelined persistent kernel (series_exec 2) and the plain
-    persistent kernel (3) give the same step bit for bit, with the stop rule on."""
+    """FP32-bulk at full size: the pipelined persistent kernel (series_exec 4), the plain
+    persistent kernel (3) and the handle's choice (2) give the same step bit for bit, with the
+    stop rule on."""
     p = problem
     out = []
-    for mode in (2, 3):
+    for mode in (2, 3, 4):
         h = poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, precision=1,
                            options=poba.ba_default_options(series_exec=mode))
         poba.ba_linearize(h)
         info = poba.ba_solve_schur_power(h, 1e-2)
         out.append((info["inner_iters"], poba.ba_get_step(h)))
-    assert out[0][0] == out[1][0]
-    assert np.array_equal(out[0][1][0], out[1][1][0]) and np.array_equal(out[0][1][1], out[1][1][1])
+    for o in out[1:]:
+        assert o[0] == out[0][0]
+        assert np.array_equal(o[1][0], out[0][1][0]) and np.array_equal(o[1][1], out[0][1][1])
 
 
 def test_two_lm_iterations(poba, problem):

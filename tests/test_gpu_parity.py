@@ -145,11 +145,11 @@ def test_solve_is_deterministic(poba, case):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_series_exec_modes_agree_bitwise(poba, case, precision):
-    """Per-kernel launches, the captured graph and the persistent kernel (with and without the
-    FP32 copy pipeline) give the same step."""
+    """Per-kernel launches, the captured graph, the persistent kernel with and without the FP32
+    copy pipeline, and the handle's own choice give the same step."""
     name, p, ref = case
     res = []
-    for mode in (0, 1, 2, 3):
+    for mode in (0, 1, 2, 3, 4):
         h = make(poba, p, precision=precision, eps=0.01, max_inner=12, series_exec=mode)
         poba.ba_linearize(h)
         info = poba.ba_solve_schur_power(h, 1e-2)
@@ -157,3 +157,22 @@ def test_series_exec_modes_agree_bitwise(poba, case, precision):
     for r in res[1:]:
         assert r[0] == res[0][0]
         assert np.array_equal(r[1][0], res[0][1][0]) and np.array_equal(r[1][1], res[0][1][1])
+
+
+def test_autotune_keeps_results(poba, case):
+    """ba_autotune times the execution forms and picks one; the options are unchanged and the
+    tuned handle's step equals the graph-replay step bit for bit."""
+    name, p, ref = case
+    for precision in (0, 1):
+        h = make(poba, p, precision=precision, eps=0.01, max_inner=12)
+        poba.ba_linearize(h)
+        choice = poba.ba_autotune(h, trials=2)
+        assert choice["exec"] in (1, 3, 4)
+        assert choice["exec"] != 4 or precision == 1
+        info = poba.ba_solve_schur_power(h, 1e-2)
+        g = make(poba, p, precision=precision, eps=0.01, max_inner=12, series_exec=1)
+        poba.ba_linearize(g)
+        info_g = poba.ba_solve_schur_power(g, 1e-2)
+        assert info["inner_iters"] == info_g["inner_iters"]
+        a, b = poba.ba_get_step(h), poba.ba_get_step(g)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
