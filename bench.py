@@ -57,6 +57,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-sub-problems section (256 problems, FP32 bulk)")
     ap.add_argument("--batch-solves", type=int, default=3)
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint section (200 cameras, 20,000 landmarks, weighted)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--profile-steps", type=int, default=0,
@@ -421,6 +423,8 @@ def run_poba(args):
     batched = None if args.no_batch else batched_section(args, poba, torch, stream, dev,
                                                            max_over_ranks, barrier)
 
+    adjoint = None if args.no_adjoint else adjoint_section(args, poba, torch, stream, dev)
+
     roof64 = roofline("fp64")
     roof32 = roofline("fp32_bulk")
     mem_gpu = poba.ba_memory_footprint(results["fp64"]["h"])
@@ -484,9 +488,56 @@ def run_poba(args):
                       "memory_bytes": mem_gpu32, "kernels": kernel_avgs(r32),
                       "series_form": r32["tuned"]},
         "batched": batched,
+        "adjoint": adjoint,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
+
+
+def adjoint_section(args, poba, torch, stream, dev):
+    """Differentiable BA: 200 cameras, 20,000 landmarks (about 80,000 observations), weights
+    U(0.5, 1.5), FP64.  Forward: LM from x0 to func_tol (or 50 iterations).  Backward: the
+    implicit-differentiation adjoint (damp, invert, the series with the default eps 0.01 and at
+    most 20 terms, back-substitution, per-observation gradients) at the LM's final lambda, for a
+    random dL/dx, with device inputs and outputs.  Both timed with CUDA events; the backward is
+    repeated and the median reported."""
+    p = bal_synth.preset("weighted_200c_20000l")
+    to = lambda a: torch.as_tensor(a).to(dev)
+    with torch.cuda.stream(stream):
+        h = poba.ba_create(to(p.cams0), to(p.lms0), to(p.obs), to(p.cam_idx), to(p.lm_idx),
+                           to(p.weights), options=poba.ba_default_options(), stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        steps = poba.ba_lm_solve(h)
+        e1.record(stream)
+        stream.synchronize()
+        fwd_ms = e0.elapsed_time(e1)
+        lam = poba.ba_get_lm_state(h)["lam"]
+        rng = np.random.default_rng(0)
+        g_c = to(rng.normal(size=(p.n_cams, 9)))
+        g_l = to(rng.normal(size=(p.n_lms, 3)))
+        d_obs = torch.empty((p.n_obs, 2), dtype=torch.float64, device=dev)
+        d_w = torch.empty(p.n_obs, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            poba.ba_adjoint(h, lam, g_c, g_l, d_obs, d_w)
+        ms = []
+        info = None
+        for _ in range(20):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, _, info = poba.ba_adjoint(h, lam, g_c, g_l, d_obs, d_w)
+            b.record(stream)
+            stream.synchronize()
+            ms.append(a.elapsed_time(b))
+    bwd = float(np.median(ms))
+    return {"metric": "adjoint backward passes/s (implicit differentiation, FP64)",
+            "value": 1e3 / bwd, "unit": "backward/s", "backward_ms": bwd,
+            "forward_ms": fwd_ms, "forward_lm_iterations": len(steps),
+            "adjoint_lambda": lam, "adjoint_terms": info["inner_iters"],
+            "config": {"workload": "weighted_200c_20000l", "n_cams": p.n_cams,
+                       "n_lms": p.n_lms, "n_obs": p.n_obs, "weights": "U(0.5, 1.5)"}}
 
 
 def batched_section(args, poba, torch, stream, dev, max_over_ranks, barrier):

@@ -298,6 +298,29 @@ ba_status ba_cost_batch(ba_handle* h, double* costs);
  * ba_solve_schur_power. */
 ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* blocks_per_sm_out);
 
+/* Implicit-differentiation adjoint (no counterpart in the paper; the differentiable form built
+ * around its solver).  At the current state x (normally a converged solution, where
+ * g = sum_o w_o J_o^T r_o = 0), and for a scalar L(x) whose gradient the caller passes as
+ * g_cams = dL/dx_p [n_cams][9] and g_lms = dL/dx_l [n_lms][3] (caller's landmark order), it
+ * solves the adjoint system H_lam a = (g_cams; g_lms) with the damped Gauss-Newton matrix of eq.
+ * `normal` (Sec. 4.1) -- the same damping as an LM step at `lambda`, which also removes the
+ * gauge freedom -- through the Schur complement and the power series of Sec. 4.3 (the
+ * handle's eps, max_inner and series_exec; the reduced right-hand side is g_p - W V^-1 g_l),
+ * then writes per observation (caller's order)
+ *   d_obs [n_obs][2]   = dL/dobs_o = w_o J_o a_o,
+ *   d_weights [n_obs]  = dL/dw_o   = -r_o^T J_o a_o   (may be NULL),
+ * i.e. the implicit-function-theorem gradients with H_lam in place of dg/dx (exact for a
+ * Gauss-Newton step at a fixed point, and at zero residuals for the minimiser of F plus the
+ * prior lambda/2 ||D (x - x*)||^2).  The series converges more slowly as lambda decreases
+ * (its ratio approaches 1 along the gauge directions): pass a larger max_inner or a larger
+ * lambda where the LM's final lambda is tiny.  Linearises first if the state changed;
+ * overwrites the last step (the step buffers hold a).  All four arrays are host (ptr_kind 0)
+ * or device (1) memory.  info (may be NULL) receives the series state as for
+ * ba_solve_schur_power.  Synchronises.  Errors: BA_ERR_INVALID_ARG, BA_ERR_NOT_SPD,
+ * BA_ERR_TIMEOUT, BA_ERR_CUDA, BA_ERR_OOM. */
+ba_status ba_adjoint(ba_handle* h, double lambda, const double* g_cams, const double* g_lms,
+                     double* d_obs, double* d_weights, int32_t ptr_kind, ba_series_info* info);
+
 /* Free all device memory of the handle (and its own stream, if it created one). NULL is OK. */
 ba_status ba_destroy(ba_handle* h);
 

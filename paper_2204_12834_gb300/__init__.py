@@ -27,7 +27,7 @@ __all__ = ["PobaError", "Handle", "ba_default_options", "ba_create", "ba_set_opt
            "BA_FP32_BULK", "library", "from_problem", "ba_cost_noalloc", "BA_NOALLOC_MAX_CAMS",
            "ba_get_series_trace", "ba_set_barrier_timeout", "ba_create_batch",
            "ba_get_batch_layout", "ba_get_series_state", "ba_lm_step_batch", "ba_lm_solve_batch",
-           "ba_cost_batch", "batch_from_problems", "ba_autotune"]
+           "ba_cost_batch", "batch_from_problems", "ba_autotune", "ba_adjoint"]
 
 BA_NOALLOC_MAX_CAMS = 4096
 
@@ -379,6 +379,36 @@ def ba_autotune(h: Handle, trials: int = 3) -> dict:
     e, k = C.c_int32(), C.c_int32()
     _check(library().ba_autotune(h.ptr, int(trials), C.byref(e), C.byref(k)), "ba_autotune")
     return {"exec": e.value, "blocks_per_sm": k.value}
+
+
+def ba_adjoint(h: Handle, lam: float, g_cams, g_lms, d_obs=None, d_weights=None,
+               want_weights: bool = True):
+    """Implicit-differentiation adjoint at the current state (see include/poba.h): returns
+    (d_obs [n_obs, 2], d_weights [n_obs] or None, series info).  g_cams / g_lms are numpy arrays
+    or torch tensors; with CUDA tensors the outputs are CUDA tensors (pass d_obs / d_weights to
+    fill preallocated ones)."""
+    gp, k1, kg = _ptr(g_cams, np.float64)
+    gl, k2, kl = _ptr(g_lms, np.float64)
+    if k1 != k2:
+        raise ValueError("g_cams and g_lms must live in the same memory")
+    if k1 == 1:
+        import torch
+        dev = kg.device
+        if d_obs is None:
+            d_obs = torch.empty((h.n_obs, 2), dtype=torch.float64, device=dev)
+        if d_weights is None and want_weights:
+            d_weights = torch.empty(h.n_obs, dtype=torch.float64, device=dev)
+        po, pw = d_obs.data_ptr(), (d_weights.data_ptr() if d_weights is not None else None)
+    else:
+        if d_obs is None:
+            d_obs = np.empty((h.n_obs, 2))
+        if d_weights is None and want_weights:
+            d_weights = np.empty(h.n_obs)
+        po, pw = d_obs.ctypes.data, (d_weights.ctypes.data if d_weights is not None else None)
+    info = SeriesInfo()
+    _check(library().ba_adjoint(h.ptr, float(lam), gp, gl, po, pw, k1, C.byref(info)),
+           "ba_adjoint")
+    return d_obs, d_weights, _series_dict(info)
 
 
 def ba_destroy(h: Handle):

@@ -83,6 +83,8 @@ SIGNATURES = {
     "ba_lm_solve_batch": (C.c_int, [C.c_void_p, C.POINTER(StepInfo), C.POINTER(C.c_int32)]),
     "ba_cost_batch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ba_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "ba_adjoint": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                             C.c_void_p, C.c_int32, C.POINTER(SeriesInfo)]),
     "ba_destroy": (C.c_int, [C.c_void_p]),
     "ba_status_string": (C.c_char_p, [C.c_int]),
     "ba_last_error": (C.c_char_p, []),

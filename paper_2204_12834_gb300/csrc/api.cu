@@ -76,6 +76,15 @@ struct ba_handle {
   double* b_p = nullptr;
   double* V = nullptr;
   double* b_l = nullptr;
+  // right-hand side the series solves with: (b_p, b_l) for a step of eq. `normal`, the adjoint
+  // buffers (adj_p, adj_l) = -(dL/dx_p, dL/dx_l) for ba_adjoint
+  const double* rhs_p = nullptr;
+  const double* rhs_l = nullptr;
+  double* adj_p = nullptr;
+  double* adj_l = nullptr;
+  int32_t* obs_caller = nullptr;   // [n_obs] caller index of each sorted observation
+  int32_t* lm_order_dev = nullptr; // [n_lms] caller index of each internal landmark
+  double* grad_out = nullptr;      // ba_adjoint host-output scratch [3 n_obs] (allocated on use)
   double* Uinv = nullptr;
   double* Vinv = nullptr;
   float* Vinv_f = nullptr;
@@ -119,6 +128,7 @@ struct ba_handle {
   int graph_nodes = 0;
   bool graph_timing = false;
   bool graph_active = false;
+  const double* graph_rhs = nullptr;
   // persistent kernels: grid = blocks per SM x SMs; camera schedules for 1..3 blocks per SM
   int sms = 0;
   int plain_max = 0, pipe_max = 0;       // occupancy limits (0: kernel unavailable)
@@ -275,8 +285,8 @@ void seq_series_body(ba_handle* h, cudaStream_t s, bool use_active) {
   T* part = (T*)h->partial;
   launch_series_reset(h->st, h->sgl, use_active ? h->rec : nullptr, h->n_probs, s);
   tmark(h, kTRhs, 0, 0);
-  launch_tile_rhs<T>(tp, J, h->b_l, Vi, part, h->st, s);
-  launch_camera_rhs<T>(tp, part, h->b_p, h->Uinv, h->x, (T*)h->t_cam, h->cam_norm, h->st, h->sgl, s);
+  launch_tile_rhs<T>(tp, J, h->rhs_l, Vi, part, h->st, s);
+  launch_camera_rhs<T>(tp, part, h->rhs_p, h->Uinv, h->x, (T*)h->t_cam, h->cam_norm, h->st, h->sgl, s);
   tmark(h, kTRhs, 0, 1);
   for (int i = 1; i <= h->opts.max_inner; ++i) {
     tmark(h, kTTile, i, 0);
@@ -288,7 +298,7 @@ void seq_series_body(ba_handle* h, cudaStream_t s, bool use_active) {
     tmark(h, kTCam, i, 1);
   }
   tmark(h, kTBack, 0, 0);
-  launch_tile_backsub<T>(tp, J, (const T*)h->r, h->x, h->b_l, Vi, h->dx_l, h->block_pred, s);
+  launch_tile_backsub<T>(tp, J, (const T*)h->r, h->x, h->rhs_l, Vi, h->dx_l, h->block_pred, s);
   tmark(h, kTBack, 0, 1);
 }
 
@@ -302,8 +312,8 @@ ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active, b
   T* part = (T*)h->partial;
   launch_series_reset(h->st, h->sgl, use_active ? h->rec : nullptr, h->n_probs, s);
   tmark(h, kTRhs, 0, 0);
-  launch_tile_rhs<T>(tp, J, h->b_l, Vi, part, h->st, s);
-  launch_camera_rhs<T>(tp, part, h->b_p, h->Uinv, h->x, (T*)h->t_cam, h->cam_norm, h->st, h->sgl, s);
+  launch_tile_rhs<T>(tp, J, h->rhs_l, Vi, part, h->st, s);
+  launch_camera_rhs<T>(tp, part, h->rhs_p, h->Uinv, h->x, (T*)h->t_cam, h->cam_norm, h->st, h->sgl, s);
   tmark(h, kTRhs, 0, 1);
   h->launches += 4;  // reset, the two RHS kernels, back-substitution
   CK(cudaMemsetAsync(h->gs, 0, sizeof(GridSync), s));
@@ -340,7 +350,7 @@ ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active, b
     }
   }
   tmark(h, kTBack, 0, 0);
-  launch_tile_backsub<T>(tp, J, (const T*)h->r, h->x, h->b_l, Vi, h->dx_l, h->block_pred, s);
+  launch_tile_backsub<T>(tp, J, (const T*)h->r, h->x, h->rhs_l, Vi, h->dx_l, h->block_pred, s);
   tmark(h, kTBack, 0, 1);
   return BA_OK;
 }
@@ -366,7 +376,8 @@ ba_status run_series_body(ba_handle* h, bool use_active) {
   }
   if (mode == 1) {
     if (!h->graph_exec || h->graph_max_inner != h->opts.max_inner || h->graph_eps != h->opts.eps ||
-        h->graph_timing != h->timing || h->graph_active != use_active) {
+        h->graph_timing != h->timing || h->graph_active != use_active ||
+        h->graph_rhs != h->rhs_p) {
       if (h->graph_exec) {
         cudaGraphExecDestroy(h->graph_exec);
         h->graph_exec = nullptr;
@@ -389,6 +400,7 @@ ba_status run_series_body(ba_handle* h, bool use_active) {
       h->graph_eps = h->opts.eps;
       h->graph_timing = h->timing;
       h->graph_active = use_active;
+      h->graph_rhs = h->rhs_p;
     }
     CK(cudaGraphLaunch(h->graph_exec, s));
     if (h->timing) {
@@ -455,6 +467,7 @@ ba_status ba_destroy(ba_handle* h) {
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->arena) cudaFree(h->arena);
+  if (h->grad_out) cudaFree(h->grad_out);
   if (h->h_st) cudaFreeHost(h->h_st);
   if (h->h_sgl) cudaFreeHost(h->h_sgl);
   if (h->h_rec) cudaFreeHost(h->h_rec);
@@ -656,6 +669,10 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   items.push_back({(void**)&h->b_p, sizeof(double) * nc * 9});
   items.push_back({(void**)&h->V, sizeof(double) * nl * 6});
   items.push_back({(void**)&h->b_l, sizeof(double) * nl * 3});
+  items.push_back({(void**)&h->adj_p, sizeof(double) * nc * 9});
+  items.push_back({(void**)&h->adj_l, sizeof(double) * nl * 3});
+  items.push_back({(void**)&h->obs_caller, sizeof(int32_t) * (no > 0 ? no : 1)});
+  items.push_back({(void**)&h->lm_order_dev, sizeof(int32_t) * nl});
   items.push_back({(void**)&h->Uinv, sizeof(double) * nc * 81});
   items.push_back({(void**)&h->Vinv, sizeof(double) * nl * 6});
   if (h->f32()) items.push_back({(void**)&h->Vinv_f, sizeof(float) * nl * 6});
@@ -735,6 +752,8 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
     sw_s.resize(no);
     for (int k = 0; k < no; ++k) sw_s[k] = std::sqrt(w[S.obs_order[k]]);
   }
+  std::vector<int32_t> obs_caller((size_t)no);
+  for (int k = 0; k < no; ++k) obs_caller[k] = (int32_t)S.obs_order[k];
   std::vector<double> lms_i((size_t)nl * 3);
   for (int i = 0; i < nl; ++i)
     for (int k = 0; k < 3; ++k) lms_i[i * 3 + k] = lms[(size_t)S.lm_order[i] * 3 + k];
@@ -762,6 +781,8 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
       {d_cam_item, cs.cam_item.data(), sizeof(int32_t) * cs.cam_item.size()},
       {d_item_q, cs.item_q.data(), sizeof(int32_t) * cs.item_q.size()},
       {h->obs, obs_s.data(), sizeof(double) * 2 * no},
+      {h->obs_caller, obs_caller.data(), sizeof(int32_t) * no},
+      {h->lm_order_dev, S.lm_order.data(), sizeof(int32_t) * nl},
       {h->cams, cams.data(), sizeof(double) * nc * 9},
       {h->lms, lms_i.data(), sizeof(double) * nl * 3},
   };
@@ -817,6 +838,8 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   tp.cam_off = d_cam_off;
   tp.tile_off = d_tile_off;
   tp.tile_rec = d_tile_rec;
+  h->rhs_p = h->b_p;
+  h->rhs_l = h->b_l;
   for (int k = 0; k < 3; ++k) {
     h->plain_rounds[k] = CamRounds{d_cam_item, d_item_q, d_rl[0][k][0], d_rl[0][k][1], d_rl[0][k][2]};
     h->pipe_rounds[k] = CamRounds{d_cam_item, d_item_q, d_rl[1][k][0], d_rl[1][k][1], d_rl[1][k][2]};
@@ -1070,6 +1093,94 @@ ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* 
   if (best.exec == 4) h->pipe_k = best.k;
   if (exec_out) *exec_out = best.exec;
   if (bps_out) *bps_out = best.k;
+  return BA_OK;
+}
+
+ba_status ba_adjoint(ba_handle* h, double lambda, const double* g_cams, const double* g_lms,
+                     double* d_obs, double* d_weights, int32_t ptr_kind, ba_series_info* info) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(BA_ERR_INVALID_ARG, "lambda must be finite and > 0");
+  if (!g_cams || !g_lms || !d_obs) return fail(BA_ERR_INVALID_ARG, "g_cams / g_lms / d_obs is NULL");
+  if (ptr_kind != 0 && ptr_kind != 1) return fail(BA_ERR_INVALID_ARG, "ptr_kind must be 0 or 1");
+  cudaStream_t s = h->stream;
+  const size_t nc9 = (size_t)h->n_c * 9, nl3 = (size_t)h->n_l * 3, no = (size_t)h->n_o;
+  if (!h->linearized) {
+    seq_linearize(h);
+    ba_status st = check_launch(h, "linearize kernels");
+    if (st != BA_OK) return st;
+    h->linearized = true;
+  }
+  // the incoming gradient: device inputs are read in place, host inputs are staged in the
+  // step buffers (which the solve overwrites)
+  const double* gp = g_cams;
+  const double* gl = g_lms;
+  if (ptr_kind == 0) {
+    CK(cudaMemcpyAsync(h->x, g_cams, sizeof(double) * nc9, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(h->dx_l, g_lms, sizeof(double) * nl3, cudaMemcpyHostToDevice, s));
+    gp = h->x;
+    gl = h->dx_l;
+  }
+  launch_adjoint_rhs(h->n_c, h->n_l, h->lm_order_dev, gp, gl, h->adj_p, h->adj_l, s);
+  launch_set_scalar(h->scalars + 0, lambda, s);
+  h->launches += 2;
+  h->solve_lambda = lambda;
+  h->last_solve_lm = false;
+  h->rhs_p = h->adj_p;
+  h->rhs_l = h->adj_l;
+  ba_status st = run_solve(h, h->scalars + 0, 0, false);
+  h->rhs_p = h->b_p;
+  h->rhs_l = h->b_l;
+  if (st != BA_OK) return st;
+  // a = (x, dx_l); per-observation gradients in the caller's order
+  double* out_obs = d_obs;
+  double* out_w = d_weights;
+  if (ptr_kind == 0) {
+    if (!h->grad_out) {
+      cudaError_t e = cudaMalloc(&h->grad_out, sizeof(double) * 3 * (no > 0 ? no : 1));
+      if (e != cudaSuccess) return fail_cuda(e, "cudaMalloc(adjoint outputs)");
+    }
+    out_obs = h->grad_out;
+    out_w = d_weights ? h->grad_out + 2 * no : nullptr;
+  }
+  if (h->f32())
+    launch_obs_gradient<float>(h->tp, (const float*)h->J, (const float*)h->r, h->sqrt_w, h->x,
+                               h->dx_l, h->obs_caller, out_obs, out_w, s);
+  else
+    launch_obs_gradient<double>(h->tp, (const double*)h->J, (const double*)h->r, h->sqrt_w,
+                                h->x, h->dx_l, h->obs_caller, out_obs, out_w, s);
+  h->launches += no > 0 ? 1 : 0;
+  st = check_launch(h, "adjoint gradient kernel");
+  if (st != BA_OK) return st;
+  if (ptr_kind == 0 && no > 0) {
+    CK(cudaMemcpyAsync(d_obs, out_obs, sizeof(double) * 2 * no, cudaMemcpyDeviceToHost, s));
+    if (d_weights) CK(cudaMemcpyAsync(d_weights, out_w, sizeof(double) * no, cudaMemcpyDeviceToHost, s));
+  }
+  const size_t P = (size_t)h->n_probs;
+  CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SeriesState) * P, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->h_flag, h->not_spd, sizeof(int32_t) * P, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  collect_timing(h, max_terms(h), true);
+  if (h->last_exec >= 3 && h->h_gs->error)
+    return fail(BA_ERR_TIMEOUT, "a grid barrier of the persistent series kernel timed out");
+  if (info) {
+    int m = 0, stopped = 1;
+    double sv = -INFINITY, x2 = 0.0;
+    for (size_t p = 0; p < P; ++p) {
+      const SeriesState& S = h->h_st[p];
+      m = S.m > m ? S.m : m;
+      stopped = stopped && S.stopped;
+      sv = S.stop_value > sv ? S.stop_value : sv;
+      x2 += S.x_norm * S.x_norm;
+    }
+    info->inner_iters = m;
+    info->stopped = stopped;
+    info->stop_value = P == 1 ? h->h_st[0].stop_value : sv;
+    info->x_norm = P == 1 ? h->h_st[0].x_norm : std::sqrt(x2);
+    info->lambda = lambda;
+  }
+  for (size_t p = 0; p < P; ++p)
+    if (h->h_flag[p]) return fail(BA_ERR_NOT_SPD, "a damped block is not positive definite");
   return BA_OK;
 }
 

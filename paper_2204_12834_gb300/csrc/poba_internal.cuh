@@ -297,6 +297,17 @@ void launch_apply_step(const Topology& tp, const LmRecord* rec, double* cams,
 
 void launch_set_scalar(double* dst, double v, cudaStream_t s);
 
+// Adjoint (kernels_adjoint.cu): the right-hand side -(dL/dx) in internal order, and the
+// per-observation gradients dL/dobs (d_obs [n_obs][2]) and dL/dw (d_w [n_obs], may be NULL) in
+// the caller's observation order from the adjoint vector (a_p per camera, a_l per internal
+// landmark).
+void launch_adjoint_rhs(int n_cams, int n_lms, const int32_t* lm_order, const double* g_p,
+                        const double* g_l, double* adj_p, double* adj_l, cudaStream_t s);
+template <typename T>
+void launch_obs_gradient(const Topology& tp, const T* J, const T* r, const double* sqrt_w,
+                         const double* a_p, const double* a_l, const int32_t* obs_caller,
+                         double* d_obs, double* d_w, cudaStream_t s);
+
 // Fixed-order sum of n doubles into *out = scale * sum (one block).
 void launch_reduce_sum(const double* in, int n, double* out, double scale, cudaStream_t s);
 
