@@ -57,6 +57,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-sub-problems section (256 problems, FP32 bulk)")
     ap.add_argument("--batch-solves", type=int, default=3)
+    ap.add_argument("--no-pcg", action="store_true",
+                    help="skip the PCG comparison (Schur-Jacobi and power-series preconditioners)")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the adjoint section (200 cameras, 20,000 landmarks, weighted)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
@@ -424,6 +426,7 @@ def run_poba(args):
                                                            max_over_ranks, barrier)
 
     adjoint = None if args.no_adjoint else adjoint_section(args, poba, torch, stream, dev)
+    pcg = None if args.no_pcg else pcg_section(poba, torch, stream, results)
 
     roof64 = roofline("fp64")
     roof32 = roofline("fp32_bulk")
@@ -489,9 +492,50 @@ def run_poba(args):
                       "series_form": r32["tuned"]},
         "batched": batched,
         "adjoint": adjoint,
+        "pcg": pcg,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
+
+
+def pcg_section(poba, torch, stream, results):
+    """The comparison solvers on the benchmark workload (FP64 and FP32-bulk handles at their
+    current linearisation, lambda = 1e-4): PCG on the reduced camera system with the
+    Schur-Jacobi preconditioner and with the order-2 power series (PoCG), to relative residuals
+    1e-2 and 1e-4, against the power-series solve (20 terms).  Times are CUDA events around one
+    solve (median of 3); PCG synchronises once per iteration."""
+    out = {}
+    for name in ("fp64", "fp32_bulk"):
+        h = results[name]["h"]
+        poba.ba_linearize(h, want_cost=False)
+        rows = []
+        for precond, m in (("jacobi", 0), ("power", 2)):
+            for rtol in (1e-2, 1e-4):
+                ms, it = [], 0
+                for _ in range(3):
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    info = poba.ba_solve_schur_pcg(h, 1e-4, precond, m, rtol=rtol, max_iter=500)
+                    b.record(stream)
+                    stream.synchronize()
+                    ms.append(a.elapsed_time(b))
+                    it = info["iterations"]
+                rows.append({"precond": precond, "m": m, "rtol": rtol, "iterations": it,
+                             "ms": float(np.median(ms))})
+        ms = []
+        for _ in range(3):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            info = poba.ba_solve_schur_power(h, 1e-4)
+            b.record(stream)
+            stream.synchronize()
+            ms.append(a.elapsed_time(b))
+        out[name] = {"pcg": rows, "power_series": {"terms": info["inner_iters"],
+                                                    "ms": float(np.median(ms))}}
+    out["config"] = {"workload": WORKLOAD, "lambda": 1e-4, "max_iter": 500}
+    return out
 
 
 def adjoint_section(args, poba, torch, stream, dev):

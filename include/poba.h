@@ -285,6 +285,27 @@ ba_status ba_lm_solve_batch(ba_handle* h, ba_step_info* infos, int32_t* n_steps)
 /* F(x) of each problem at the current state: costs[P] (host), float64, fixed order. */
 ba_status ba_cost_batch(ba_handle* h, double* costs);
 
+/* Preconditioned conjugate gradients on the reduced camera system S dx_p = -b~ (Sec. 4.2,
+ * eqs. `Sx`, `Schur`): the comparison solvers of the paper, built from the same kernels.  S is
+ * applied matrix-free (S p = U_lam p - W V_lam^-1 W^T p, the series tile kernel plus a camera
+ * kernel).  precond 0: Schur-Jacobi -- the inverses of the 9x9 diagonal blocks of S, the
+ * preconditioner of Ceres-explicit / Ceres-implicit (Sec. 5); precond 1: the order-m_precond
+ * power series sum_{i<=m} (U^-1 W V^-1 W^T)^i U^-1 (eq. `S_approx`) as M^-1, the Neumann-series
+ * preconditioner of Fig. 2 ("PoCG"; each application is a series solve of m_precond terms in
+ * the handle's series_exec form).  Hestenes-Stiefel CG from dx_p = 0 until ||r|| <= rtol ||b~||
+ * or max_iter iterations; then dx_l by back-substitution.  The step is read with ba_get_step.
+ * Vector reductions have a fixed order.  Synchronises once per iteration.  Errors:
+ * BA_ERR_NOT_LINEARIZED, BA_ERR_INVALID_ARG, BA_ERR_NOT_SPD, BA_ERR_NONFINITE, BA_ERR_CUDA,
+ * BA_ERR_OOM (the PCG vectors are allocated on the first call). */
+typedef struct {
+  int32_t iterations;  /* CG iterations performed */
+  int32_t converged;   /* 1 if the relative residual reached rtol */
+  double rel_residual; /* ||r|| / ||b~|| at the end */
+  double lambda;       /* damping the blocks were built with */
+} ba_pcg_info;
+ba_status ba_solve_schur_pcg(ba_handle* h, double lambda, int32_t precond, int32_t m_precond,
+                             double rtol, int32_t max_iter, ba_pcg_info* info);
+
 /* Autotuner of the series execution (no counterpart in the paper; the schedule choice of the
  * batched form).  On the handle's current linearisation (linearising first if needed) it times
  * `trials` series solves (damp, invert, max_inner terms, back-substitution; after one warm-up)

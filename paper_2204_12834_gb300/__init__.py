@@ -27,7 +27,8 @@ __all__ = ["PobaError", "Handle", "ba_default_options", "ba_create", "ba_set_opt
            "BA_FP32_BULK", "library", "from_problem", "ba_cost_noalloc", "BA_NOALLOC_MAX_CAMS",
            "ba_get_series_trace", "ba_set_barrier_timeout", "ba_create_batch",
            "ba_get_batch_layout", "ba_get_series_state", "ba_lm_step_batch", "ba_lm_solve_batch",
-           "ba_cost_batch", "batch_from_problems", "ba_autotune", "ba_adjoint"]
+           "ba_cost_batch", "batch_from_problems", "ba_autotune", "ba_adjoint",
+           "ba_solve_schur_pcg"]
 
 BA_NOALLOC_MAX_CAMS = 4096
 
@@ -409,6 +410,18 @@ def ba_adjoint(h: Handle, lam: float, g_cams, g_lms, d_obs=None, d_weights=None,
     _check(library().ba_adjoint(h.ptr, float(lam), gp, gl, po, pw, k1, C.byref(info)),
            "ba_adjoint")
     return d_obs, d_weights, _series_dict(info)
+
+
+def ba_solve_schur_pcg(h: Handle, lam: float, precond: str = "jacobi", m: int = 2,
+                       rtol: float = 1e-10, max_iter: int = 500) -> dict:
+    """PCG on the reduced camera system; precond "jacobi" (Schur-Jacobi) or "power" (order-m
+    series, PoCG).  The step is read with ba_get_step."""
+    info = _lib.PcgInfo()
+    code = {"jacobi": 0, "power": 1}[precond]
+    _check(library().ba_solve_schur_pcg(h.ptr, float(lam), code, int(m), float(rtol),
+                                        int(max_iter), C.byref(info)), "ba_solve_schur_pcg")
+    return dict(iterations=info.iterations, converged=bool(info.converged),
+                rel_residual=info.rel_residual, lam=info.lambda_)
 
 
 def ba_destroy(h: Handle):

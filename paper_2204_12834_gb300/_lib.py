@@ -40,6 +40,11 @@ class StepInfo(C.Structure):
                 ("converged", C.c_int32), ("iteration", C.c_int32), ("not_spd", C.c_int32)]
 
 
+class PcgInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32),
+                ("rel_residual", C.c_double), ("lambda_", C.c_double)]
+
+
 TIMING_CLASSES = ["linearize", "damp_invert", "rhs", "series_tile", "series_camera", "backsub",
                   "evaluate"]
 
@@ -85,6 +90,8 @@ SIGNATURES = {
     "ba_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "ba_adjoint": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_void_p, C.c_int32, C.POINTER(SeriesInfo)]),
+    "ba_solve_schur_pcg": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_double,
+                                     C.c_int32, C.POINTER(PcgInfo)]),
     "ba_destroy": (C.c_int, [C.c_void_p]),
     "ba_status_string": (C.c_char_p, [C.c_int]),
     "ba_last_error": (C.c_char_p, []),

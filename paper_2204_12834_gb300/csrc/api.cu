@@ -85,6 +85,12 @@ struct ba_handle {
   int32_t* obs_caller = nullptr;   // [n_obs] caller index of each sorted observation
   int32_t* lm_order_dev = nullptr; // [n_lms] caller index of each internal landmark
   double* grad_out = nullptr;      // ba_adjoint host-output scratch [3 n_obs] (allocated on use)
+  // PCG buffers (allocated on first use): y r z p q rhs [9 n_c], scalars, dot partials,
+  // Schur-Jacobi blocks (sums, assembled, inverted)
+  double* pcg = nullptr;
+  double *pcg_y = nullptr, *pcg_r = nullptr, *pcg_z = nullptr, *pcg_p = nullptr, *pcg_q = nullptr,
+         *pcg_rhs = nullptr, *pcg_sc = nullptr, *pcg_part = nullptr, *pcg_sj = nullptr,
+         *pcg_s45 = nullptr, *pcg_minv = nullptr;
   double* Uinv = nullptr;
   double* Vinv = nullptr;
   float* Vinv_f = nullptr;
@@ -468,6 +474,7 @@ ba_status ba_destroy(ba_handle* h) {
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->arena) cudaFree(h->arena);
   if (h->grad_out) cudaFree(h->grad_out);
+  if (h->pcg) cudaFree(h->pcg);
   if (h->h_st) cudaFreeHost(h->h_st);
   if (h->h_sgl) cudaFreeHost(h->h_sgl);
   if (h->h_rec) cudaFreeHost(h->h_rec);
@@ -1182,6 +1189,191 @@ ba_status ba_adjoint(ba_handle* h, double lambda, const double* g_cams, const do
   for (size_t p = 0; p < P; ++p)
     if (h->h_flag[p]) return fail(BA_ERR_NOT_SPD, "a damped block is not positive definite");
   return BA_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+ba_status ensure_pcg(ba_handle* h) {
+  if (h->pcg) return BA_OK;
+  const size_t n9 = (size_t)h->n_c * 9, n45 = (size_t)h->n_c * 45, n81 = (size_t)h->n_c * 81;
+  const size_t total = 6 * n9 + kPcgCount + kPcgDotBlocks + 2 * n45 + n81;
+  CK(cudaMalloc(&h->pcg, sizeof(double) * total));
+  double* q = h->pcg;
+  double** bufs[] = {&h->pcg_y, &h->pcg_r, &h->pcg_z, &h->pcg_p, &h->pcg_q, &h->pcg_rhs};
+  for (double** b : bufs) {
+    *b = q;
+    q += n9;
+  }
+  h->pcg_sc = q;
+  q += kPcgCount;
+  h->pcg_part = q;
+  q += kPcgDotBlocks;
+  h->pcg_sj = q;
+  q += n45;
+  h->pcg_s45 = q;
+  q += n45;
+  h->pcg_minv = q;
+  CK(cudaMemsetAsync(h->pcg_sc, 0, sizeof(double) * kPcgCount, h->stream));
+  return BA_OK;
+}
+
+// S p (float64 p, q): stage p as the series term, W V^-1 W^T p in the tiles, U_lam p - y per
+// camera.
+template <typename T>
+void seq_schur_apply(ba_handle* h, double lambda, const double* p, double* q) {
+  cudaStream_t s = h->stream;
+  const T* Vi = h->f32() ? (const T*)(const void*)h->Vinv_f : (const T*)(const void*)h->Vinv;
+  launch_stage_term<T>(h->n_c, p, (T*)h->t_cam, s);
+  launch_series_reset(h->st, h->sgl, nullptr, h->n_probs, s);
+  launch_tile_series<T>(h->tp, (const T*)h->J, (const T*)h->t_cam, Vi, (T*)h->partial, h->st,
+                        h->sgl, s);
+  launch_schur_camera<T>(h->tp, (const T*)h->partial, h->U45, lambda, h->opts.damping_mode, p, q,
+                         s);
+  h->launches += 4;
+}
+
+// The reduced right-hand side -b~ = W V^-1 b_l - b_p.
+template <typename T>
+void seq_schur_rhs(ba_handle* h, double* out) {
+  cudaStream_t s = h->stream;
+  const T* Vi = h->f32() ? (const T*)(const void*)h->Vinv_f : (const T*)(const void*)h->Vinv;
+  launch_series_reset(h->st, h->sgl, nullptr, h->n_probs, s);
+  launch_tile_rhs<T>(h->tp, (const T*)h->J, h->b_l, Vi, (T*)h->partial, h->st, s);
+  launch_schur_rhs_camera<T>(h->tp, (const T*)h->partial, h->b_p, out, s);
+  h->launches += 3;
+}
+
+// Schur-Jacobi blocks S_cc and their inverses.
+template <typename T>
+void seq_schur_jacobi(ba_handle* h, double lambda) {
+  cudaStream_t s = h->stream;
+  launch_schur_jacobi_tiles<T>(h->tp, (const T*)h->J, h->Vinv, (T*)h->partial, s);
+  launch_lin_camera_reduce<T>(h->tp, (const T*)h->partial, h->pcg_sj, h->pcg_z, s);
+  launch_schur_diag(h->n_c, h->U45, h->pcg_sj, lambda, h->opts.damping_mode, h->pcg_s45, s);
+  launch_invert_camera_blocks(h->tp, h->pcg_s45, h->pcg_sc + kPcgZero, h->opts.damping_mode,
+                              h->pcg_minv, h->not_spd, s);
+  h->launches += 4;
+}
+
+// z = M^-1 r.  Power series: the series solve with the right-hand side (b_p, b_l) = (-r, 0),
+// i.e. x(m) = sum_{i<=m} P^i U^-1 r.
+ba_status precondition(ba_handle* h, int precond, int m, const double* r, double* z) {
+  cudaStream_t s = h->stream;
+  if (precond == 0) {
+    launch_block_apply(h->n_c, h->pcg_minv, r, z, s);
+    h->launches += 1;
+    return BA_OK;
+  }
+  launch_negate(h->n_c * 9, r, h->adj_p, s);
+  CK(cudaMemsetAsync(h->adj_l, 0, sizeof(double) * (size_t)h->n_l * 3, s));
+  const ba_options saved = h->opts;
+  h->opts.eps = 0.0;
+  h->opts.max_inner = m;
+  h->rhs_p = h->adj_p;
+  h->rhs_l = h->adj_l;
+  ba_status st = run_series_body(h, false);
+  h->rhs_p = h->b_p;
+  h->rhs_l = h->b_l;
+  h->opts = saved;
+  if (st != BA_OK) return st;
+  CK(cudaMemcpyAsync(z, h->x, sizeof(double) * (size_t)h->n_c * 9, cudaMemcpyDeviceToDevice, s));
+  h->launches += 1;
+  return BA_OK;
+}
+
+template <typename T>
+ba_status pcg_solve(ba_handle* h, double lambda, int precond, int m, double rtol, int max_iter,
+                    ba_pcg_info* info) {
+  cudaStream_t s = h->stream;
+  const int n = h->n_c * 9;
+  seq_schur_rhs<T>(h, h->pcg_rhs);
+  if (precond == 0) seq_schur_jacobi<T>(h, lambda);
+  CK(cudaMemsetAsync(h->pcg_y, 0, sizeof(double) * n, s));
+  CK(cudaMemcpyAsync(h->pcg_r, h->pcg_rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  launch_dot(n, h->pcg_rhs, h->pcg_rhs, h->pcg_part, h->pcg_sc + kPcgBb, s);
+  ba_status st = precondition(h, precond, m, h->pcg_r, h->pcg_z);
+  if (st != BA_OK) return st;
+  launch_dot(n, h->pcg_r, h->pcg_z, h->pcg_part, h->pcg_sc + kPcgRzNew, s);
+  launch_cg_direction(n, h->pcg_sc, h->pcg_z, h->pcg_p, 1, s);
+  h->launches += 6;
+  int it = 0;
+  double rel = 1.0, bb = 0.0;
+  bool conv = false;
+  for (it = 1; it <= max_iter; ++it) {
+    seq_schur_apply<T>(h, lambda, h->pcg_p, h->pcg_q);
+    launch_dot(n, h->pcg_p, h->pcg_q, h->pcg_part, h->pcg_sc + kPcgPq, s);
+    launch_cg_update(n, h->pcg_sc, h->pcg_p, h->pcg_q, h->pcg_y, h->pcg_r, s);
+    launch_dot(n, h->pcg_r, h->pcg_r, h->pcg_part, h->pcg_sc + kPcgRr, s);
+    h->launches += 5;
+    CK(cudaMemcpyAsync(h->h_scalar, h->pcg_sc + kPcgRr, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    st = check_launch(h, "PCG kernels");
+    if (st != BA_OK) return st;
+    bb = h->h_scalar[1];
+    rel = bb > 0.0 ? std::sqrt(h->h_scalar[0] / bb) : 0.0;
+    if (!std::isfinite(rel)) return fail(BA_ERR_NONFINITE, "non-finite PCG residual");
+    if (rel <= rtol) {
+      conv = true;
+      break;
+    }
+    if (it == max_iter) break;
+    st = precondition(h, precond, m, h->pcg_r, h->pcg_z);
+    if (st != BA_OK) return st;
+    launch_dot(n, h->pcg_r, h->pcg_z, h->pcg_part, h->pcg_sc + kPcgRzNew, s);
+    launch_cg_direction(n, h->pcg_sc, h->pcg_z, h->pcg_p, 0, s);
+    h->launches += 4;
+  }
+  if (bb == 0.0) {
+    rel = 0.0;
+    conv = true;
+  }
+  // dx_p = y, dx_l by back-substitution
+  CK(cudaMemcpyAsync(h->x, h->pcg_y, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  const T* Vi = h->f32() ? (const T*)(const void*)h->Vinv_f : (const T*)(const void*)h->Vinv;
+  launch_tile_backsub<T>(h->tp, (const T*)h->J, (const T*)h->r, h->x, h->b_l, Vi, h->dx_l,
+                         h->block_pred, s);
+  h->launches += 1;
+  CK(cudaMemcpyAsync(h->h_flag, h->not_spd, sizeof(int32_t) * h->n_probs, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  st = check_launch(h, "PCG back-substitution");
+  if (st != BA_OK) return st;
+  h->have_step = true;
+  if (info) {
+    info->iterations = it > max_iter ? max_iter : it;
+    info->converged = conv ? 1 : 0;
+    info->rel_residual = rel;
+    info->lambda = lambda;
+  }
+  for (int p = 0; p < h->n_probs; ++p)
+    if (h->h_flag[p]) return fail(BA_ERR_NOT_SPD, "a damped block is not positive definite");
+  return BA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ba_status ba_solve_schur_pcg(ba_handle* h, double lambda, int32_t precond, int32_t m_precond,
+                             double rtol, int32_t max_iter, ba_pcg_info* info) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  if (!h->linearized) return fail(BA_ERR_NOT_LINEARIZED, "ba_linearize has not been called");
+  if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(BA_ERR_INVALID_ARG, "lambda must be finite and > 0");
+  if (precond != 0 && precond != 1) return fail(BA_ERR_INVALID_ARG, "precond must be 0 (Schur-Jacobi) or 1 (power series)");
+  if (m_precond < 0 || m_precond > 10000) return fail(BA_ERR_INVALID_ARG, "m_precond out of range [0, 10000]");
+  if (!(rtol >= 0.0) || max_iter < 1) return fail(BA_ERR_INVALID_ARG, "need rtol >= 0 and max_iter >= 1");
+  ba_status st = ensure_pcg(h);
+  if (st != BA_OK) return st;
+  CK(cudaMemsetAsync(h->not_spd, 0, sizeof(int32_t) * h->n_probs, h->stream));
+  launch_set_scalar(h->scalars + 0, lambda, h->stream);
+  launch_damp_invert(h->tp, h->U45, h->V, h->scalars + 0, 0, h->opts.damping_mode, h->Uinv,
+                     h->Vinv, h->f32() ? h->Vinv_f : nullptr, h->not_spd, h->stream);
+  h->launches += 2;
+  h->solve_lambda = lambda;
+  h->last_solve_lm = false;
+  return h->f32() ? pcg_solve<float>(h, lambda, precond, m_precond, rtol, max_iter, info)
+                  : pcg_solve<double>(h, lambda, precond, m_precond, rtol, max_iter, info);
 }
 
 ba_status ba_get_series_state(ba_handle* h, ba_series_info* infos) {

@@ -84,19 +84,6 @@ void launch_cam_prepare(const double* cams, const double* dx_p, int n_cams, doub
 }
 
 // ---------------------------------------------------------------------------------------
-// Packed index of entry (i, j), i <= j, of a symmetric 9x9 matrix stored row by row.
-__host__ __device__ constexpr int packed9(int i, int j) { return i * 9 - (i * (i - 1)) / 2 + (j - i); }
-__host__ __device__ constexpr int packed_row(int idx) {
-  int i = 0;
-  while (idx >= 9 - i) { idx -= 9 - i; ++i; }
-  return i;
-}
-__host__ __device__ constexpr int packed_col(int idx) {
-  int i = 0;
-  while (idx >= 9 - i) { idx -= 9 - i; ++i; }
-  return i + idx;
-}
-
 // Entry IDX of the per-observation camera contribution: packed (J_p^T J_p)_{ij} for IDX < 45,
 // else (J_p^T r)_j.  Resolved at compile time.
 template <int IDX, typename T>
@@ -321,11 +308,6 @@ template void launch_lin_camera_reduce<float>(const Topology&, const float*, dou
 // Damping (reading of D: D^T D = diag(J^T J) clamped to [1e-6, 1e32], or D = I) and block
 // Cholesky inverses A^-1 = L^-T L^-1 in float64.  Blocks [0, cam_blocks) handle cameras, the
 // rest landmarks.
-constexpr double kDampMin = 1e-6, kDampMax = 1e32;
-
-__device__ __forceinline__ double damp_diag(double d, double lam, int mode) {
-  return mode == 0 ? lam * fmin(fmax(d, kDampMin), kDampMax) : lam;
-}
 
 // Camera blocks: kCamBlock cameras x 9 threads.  Thread k of a camera loads row k; the 9
 // threads factor A = L L^T column by column (the diagonal keeps 1/L_jj, from rsqrt); thread k
@@ -451,6 +433,15 @@ void launch_damp_invert(const Topology& tp, const double* U45, const double* V,
   const int lb = (tp.n_lms + kDampThreads - 1) / kDampThreads;
   damp_invert_kernel<<<cb + lb, kDampThreads, 0, s>>>(tp, U45, V, lambda, lam_stride, damping_mode,
                                                      cb, Uinv, Vinv, Vinv_f, not_spd);
+}
+
+// Cameras only: out81[c] = (A45[c] + damping at lambda)^-1 (the same factorisation as above).
+void launch_invert_camera_blocks(const Topology& tp, const double* A45, const double* lambda,
+                                 int damping_mode, double* out81, int32_t* not_spd,
+                                 cudaStream_t s) {
+  const int cb = (tp.n_cams + kCamBlock - 1) / kCamBlock;
+  damp_invert_kernel<<<cb, kDampThreads, 0, s>>>(tp, A45, nullptr, lambda, 0, damping_mode, cb,
+                                                 out81, nullptr, nullptr, not_spd);
 }
 
 // ---------------------------------------------------------------------------------------

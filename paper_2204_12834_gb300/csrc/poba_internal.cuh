@@ -297,6 +297,35 @@ void launch_apply_step(const Topology& tp, const LmRecord* rec, double* cams,
 
 void launch_set_scalar(double* dst, double v, cudaStream_t s);
 
+// PCG on the reduced camera system (kernels_pcg.cu).  Scalars of the recursion, in sc[]:
+enum { kPcgRz = 0, kPcgPq = 1, kPcgRzNew = 2, kPcgRr = 3, kPcgBb = 4, kPcgZero = 5, kPcgCount = 8 };
+constexpr int kPcgDotBlocks = 128;
+template <typename T>
+void launch_schur_jacobi_tiles(const Topology& tp, const T* J, const double* Vinv, T* partial,
+                               cudaStream_t s);
+void launch_schur_diag(int n_cams, const double* U45, const double* SJ45, double lam, int mode,
+                       double* S45, cudaStream_t s);
+void launch_invert_camera_blocks(const Topology& tp, const double* A45, const double* lambda,
+                                 int damping_mode, double* out81, int32_t* not_spd,
+                                 cudaStream_t s);
+template <typename PT>
+void launch_schur_camera(const Topology& tp, const PT* partial, const double* U45, double lam,
+                         int mode, const double* p, double* q, cudaStream_t s);
+template <typename PT>
+void launch_schur_rhs_camera(const Topology& tp, const PT* partial, const double* b_p,
+                             double* out, cudaStream_t s);
+template <typename PT>
+void launch_stage_term(int n_cams, const double* p, PT* t_cam, cudaStream_t s);
+void launch_dot(int n, const double* a, const double* b, double* part, double* out,
+                cudaStream_t s);
+void launch_cg_update(int n, const double* sc, const double* p, const double* q, double* y,
+                      double* r, cudaStream_t s);
+void launch_cg_direction(int n, double* sc, const double* z, double* p, int first,
+                         cudaStream_t s);
+void launch_block_apply(int n_cams, const double* M81, const double* r, double* z,
+                        cudaStream_t s);
+void launch_negate(int n, const double* src, double* dst, cudaStream_t s);
+
 // Adjoint (kernels_adjoint.cu): the right-hand side -(dL/dx) in internal order, and the
 // per-observation gradients dL/dobs (d_obs [n_obs][2]) and dL/dw (d_w [n_obs], may be NULL) in
 // the caller's observation order from the adjoint vector (a_p per camera, a_l per internal

@@ -5,6 +5,27 @@
 
 namespace poba {
 
+// Packed index of entry (i, j), i <= j, of a symmetric 9x9 matrix stored row by row.
+__host__ __device__ constexpr int packed9(int i, int j) { return i * 9 - (i * (i - 1)) / 2 + (j - i); }
+__host__ __device__ constexpr int packed_row(int idx) {
+  int i = 0;
+  while (idx >= 9 - i) { idx -= 9 - i; ++i; }
+  return i;
+}
+__host__ __device__ constexpr int packed_col(int idx) {
+  int i = 0;
+  while (idx >= 9 - i) { idx -= 9 - i; ++i; }
+  return i + idx;
+}
+
+// Damping of a diagonal entry d (reading of D: D^T D = diag(J^T J) clamped to [1e-6, 1e32] in
+// mode 0, D = I in mode 1).
+constexpr double kDampMin = 1e-6, kDampMax = 1e32;
+
+__device__ __forceinline__ double damp_diag(double d, double lam, int mode) {
+  return mode == 0 ? lam * fmin(fmax(d, kDampMin), kDampMax) : lam;
+}
+
 // Sum of `val` over the block in a fixed order (warp shuffles, then warps in order).  Must be
 // called by every thread of the block; the total is valid in thread 0.  sred holds one
 // double per warp.
