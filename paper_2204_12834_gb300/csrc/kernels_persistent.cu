@@ -360,13 +360,15 @@ struct __align__(16) F32Pipe {
   uint8_t rec[3][kTileRecMax];
   float tc[2][kTileSlots][kTStride];
   float vi[2][kTileLms][6];
-  float sg[kTileObs][9];  // phase 1-2 v (as [.][3]), then the scatter; doubles in phase B
+  float sv[kTileObs][3];
+  float sg[kTileObs][9];  // the scatter; phase B's doubles
   int4 desc[4][2];
   unsigned long long mbJ;
   unsigned long long mbR[3];
 };
 static_assert(offsetof(F32Pipe, rec) % 16 == 0 && offsetof(F32Pipe, tc) % 16 == 0 &&
                   offsetof(F32Pipe, vi) % 16 == 0 && offsetof(F32Pipe, sg) % 16 == 0 &&
+                  offsetof(F32Pipe, sv) % 16 == 0 &&
                   offsetof(F32Pipe, desc) % 16 == 0 && offsetof(F32Pipe, mbJ) % 8 == 0,
               "bulk-copy destinations must be 16-byte aligned");
 static_assert((kJStage * 4) % 16 == 0 && kTileRecMax % 16 == 0, "16-byte rows");
@@ -459,7 +461,6 @@ __global__ void __launch_bounds__(kTileObs, 3) series_persistent_f32_kernel(
   const int tid = threadIdx.x;
   const size_t pad = (size_t)tp.n_obs_pad;
   double* scratch = reinterpret_cast<double*>(&S.sg[0][0]);  // phase B reuses sg
-  float (*sv)[3] = reinterpret_cast<float (*)[3]>(&S.sg[0][0]);
 
   if (tid == 0) {
     s_done = ld_volatile(&sgl->all_done);
@@ -560,33 +561,36 @@ __global__ void __launch_bounds__(kTileObs, 3) series_persistent_f32_kernel(
         lm = rec[g.olm + tid];
       }
       (void)L0;
-      __syncthreads();  // sJ and desc[(k + 3) % 4] are free
       const int k1 = (k + 1) & 3, k2 = (k + 2) & 3, k3 = (k + 3) & 3;
-      if (tid == 0) {
-        if (s_tk[k1] < n_list) {
-          issue_J(S, J, pad, S.desc[k1][0].z, S.desc[k1][0].w);
-          pend |= 8u;
-        }
-        if (s_tk[k2] < n_list) {
-          issue_rec(S, tp.tile_rec, (k + 2) % 3, S.desc[k2]);
-          pend |= 1u << ((k + 2) % 3);
-        }
-        const int tk = tk_next;
-        s_tk[k3] = tk;
-        tk_next = n_list;
-        if (tk < n_list) {
-          cp_async16(&S.desc[k3][0], list + 2 * (size_t)tk);
-          cp_async16(&S.desc[k3][1], list + 2 * (size_t)tk + 1);
-          cp_async_commit();
-          if (!ld_volatile(&sgl->all_done)) {
-            tk_next = (int)atomicAdd(&gs->tile_next, 1u);
-            if (tk_next > n_list) tk_next = n_list;
+      // after the core's first barrier every thread holds its J in registers and is past the
+      // start of this tile: refill sJ, the record ring and the descriptor ring for the tiles
+      // ahead, and fetch the next tile's t rows and V^-1 once its record has arrived
+      auto ahead = [&]() {
+        if (tid == 0) {
+          if (s_tk[k1] < n_list) {
+            issue_J(S, J, pad, S.desc[k1][0].z, S.desc[k1][0].w);
+            pend |= 8u;
+          }
+          if (s_tk[k2] < n_list) {
+            issue_rec(S, tp.tile_rec, (k + 2) % 3, S.desc[k2]);
+            pend |= 1u << ((k + 2) % 3);
+          }
+          const int tk = tk_next;
+          s_tk[k3] = tk;
+          tk_next = n_list;
+          if (tk < n_list) {
+            cp_async16(&S.desc[k3][0], list + 2 * (size_t)tk);
+            cp_async16(&S.desc[k3][1], list + 2 * (size_t)tk + 1);
+            if (!ld_volatile(&sgl->all_done)) {
+              tk_next = (int)atomicAdd(&gs->tile_next, 1u);
+              if (tk_next > n_list) tk_next = n_list;
+            }
           }
         }
-      }
-      // the next tile's t rows and V^-1, once its record has arrived (mid-tile)
-      auto mid = [&]() {
-        if (s_tk[k1] >= n_list) return;
+        if (s_tk[k1] >= n_list) {
+          cp_async_commit();
+          return;
+        }
         const int r1 = (k + 1) % 3;
         const bool ok = mbar_wait(&S.mbR[r1], (parR >> r1) & 1u, kCopyWaitCycles);
         if (ok) {
@@ -611,12 +615,12 @@ __global__ void __launch_bounds__(kTileObs, 3) series_persistent_f32_kernel(
         }
         cp_async_commit();
       };
-      f32_tile_core<kModeSeries>(active, n, ns, lm, meta, jp, jl, &S.tc[bk][0][0], kTStride,
-                                 &S.vi[bk][0][0], 6,
-                                 reinterpret_cast<const uint16_t*>(rec + g.sseg),
-                                 reinterpret_cast<const uint16_t*>(rec + g.sbeg),
-                                 reinterpret_cast<const int*>(rec + g.srow), sv, S.sg, partial,
-                                 mid);
+      f32_tile_core<kModeSeries, false>(active, n, ns, lm, meta, jp, jl, &S.tc[bk][0][0],
+                                        kTStride, &S.vi[bk][0][0], 6,
+                                        reinterpret_cast<const uint16_t*>(rec + g.sseg),
+                                        reinterpret_cast<const uint16_t*>(rec + g.sbeg),
+                                        reinterpret_cast<const int*>(rec + g.srow), S.sv, S.sg,
+                                        partial, ahead);
     }
     cp_async_wait_all();
     __syncthreads();

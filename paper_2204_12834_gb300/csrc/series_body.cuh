@@ -169,15 +169,17 @@ __device__ __forceinline__ void tile_matvec_body(const Topology& tp, int tile,
 // vinv[l * vstride .. + 6) (RHS mode: b_l at + 6 .. + 9); sseg[l] = tile-relative segment
 // offsets (nl + 1 entries); sbeg[s] = first camera-sorted position of slot s; srow[s] = its
 // camera-major row.  lm = the observation's landmark within the tile, meta = pos | slot << 8.
-// mid() runs between the two barriers of phase 1.  sv and sg may share storage.  Every thread of
-// the block must call it.
-template <int MODE, typename SegT, typename BegT, typename Mid>
+// kShared: the caller's staging shares storage (landmark marks in sv, V^-1 in sg), which costs
+// two more barriers; otherwise sv, sg, tcam and vinv must be separate.  hook() runs after the
+// barrier that follows the v writes (every thread has passed the start of the tile).  Every
+// thread of the block must call it.
+template <int MODE, bool kShared, typename SegT, typename BegT, typename Hook>
 __device__ __forceinline__ void f32_tile_core(bool active, int n, int ns, int lm, int meta,
                                               const float (&jp)[18], const float (&jl)[6],
                                               const float* tcam, int tstride, const float* vinv,
                                               int vstride, const SegT* sseg, const BegT* sbeg,
                                               const int* srow, float (*sv)[3], float (*sg)[9],
-                                              float* __restrict__ partial, Mid&& mid) {
+                                              float* __restrict__ partial, Hook&& hook) {
   const int tid = threadIdx.x;
   // phase 1: u = J_p t, v = J_l^T u
   float u0 = 0.f, u1 = 0.f;
@@ -189,13 +191,13 @@ __device__ __forceinline__ void f32_tile_core(bool active, int n, int ns, int lm
       u1 += jp[9 + j] * tc[j];
     }
   }
-  __syncthreads();
-  mid();
+  if (kShared) __syncthreads();  // sv still holds the landmark marks read before the call
   if (MODE == kModeSeries && active) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) sv[tid][k] = jl[k] * u0 + jl[3 + k] * u1;
   }
   __syncthreads();
+  hook();
   // phase 2: each observation thread sums its landmark's v in segment order, applies V^-1 and
   // forms J_l z
   if (active) {
@@ -220,7 +222,7 @@ __device__ __forceinline__ void f32_tile_core(bool active, int n, int ns, int lm
     u0 = jl[0] * z0 + jl[1] * z1 + jl[2] * z2;
     u1 = jl[3] * z0 + jl[4] * z1 + jl[5] * z2;
   }
-  __syncthreads();  // sv and the V^-1 staging may alias sg
+  if (kShared) __syncthreads();  // the V^-1 staging shares sg with the scatter below
   if (active) {
     float* g = sg[meta & 0xff];
 #pragma unroll
@@ -304,8 +306,8 @@ __device__ __forceinline__ void tile_matvec_body_f32(const Topology& tp, int til
   }
   __syncthreads();
   const int lm = active ? __float_as_int(sm.sv[tid][0]) : 0;
-  f32_tile_core<MODE>(active, n, ns, lm, meta, jp, jl, &sm.tcam[0][0], 9, &sm.sg[0][0], 9, sm.sseg,
-                      sm.sbeg, sm.srow, sm.sv, sm.sg, partial, [] {});
+  f32_tile_core<MODE, true>(active, n, ns, lm, meta, jp, jl, &sm.tcam[0][0], 9, &sm.sg[0][0], 9,
+                            sm.sseg, sm.sbeg, sm.srow, sm.sv, sm.sg, partial, [] {});
 }
 
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
