@@ -426,16 +426,15 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Thread 0: bulk copies of the 24 Jacobian planes of the tile {o0, n} into sJ.
+// Warp 0: bulk copies of the 24 Jacobian planes of the tile {o0, n} into sJ, one plane per lane
+// (lane 0 arms the barrier first).
 __device__ __forceinline__ void issue_J(F32Pipe& S, const float* __restrict__ J, size_t pad,
-                                        int o0, int n) {
+                                        int o0, int n, int lane) {
   const int a0 = o0 & ~3, e = (o0 + n + 3) & ~3;
   const unsigned bytes = (unsigned)(e - a0) * 4u;
-  mbar_arm(&S.mbJ, n > 0 ? 24u * bytes : 0u);
-  if (n > 0) {
-#pragma unroll 1
-    for (int p = 0; p < 24; ++p) bulk_g2s(&S.sJ[p][0], J + (size_t)p * pad + a0, bytes, &S.mbJ);
-  }
+  if (lane == 0) mbar_arm(&S.mbJ, n > 0 ? 24u * bytes : 0u);
+  __syncwarp();
+  if (n > 0 && lane < 24) bulk_g2s(&S.sJ[lane][0], J + (size_t)lane * pad + a0, bytes, &S.mbJ);
 }
 
 // Thread 0: bulk copy of a tile's index record into ring slot r.
@@ -483,28 +482,31 @@ __global__ void __launch_bounds__(kTileObs, 3) series_persistent_f32_kernel(
     // ---- phase A, prologue: claim three tiles, fetch their descriptors, start the first
     // two records and the first Jacobians
     int tk_next = n_list;  // thread 0: ticket claimed for the slot after the last filled one
-    if (tid == 0) {
-      int t0 = n_list;
-      if (!ld_volatile(&sgl->all_done)) t0 = (int)atomicAdd(&gs->tile_next, 3u);
-      for (int q = 0; q < 3; ++q) {
-        const int tk = t0 + q < n_list ? t0 + q : n_list;
-        s_tk[q] = tk;
-        if (tk < n_list) {
-          cp_async16(&S.desc[q][0], list + 2 * (size_t)tk);
-          cp_async16(&S.desc[q][1], list + 2 * (size_t)tk + 1);
+    if (tid < 32) {
+      if (tid == 0) {
+        int t0 = n_list;
+        if (!ld_volatile(&sgl->all_done)) t0 = (int)atomicAdd(&gs->tile_next, 3u);
+        for (int q = 0; q < 3; ++q) {
+          const int tk = t0 + q < n_list ? t0 + q : n_list;
+          s_tk[q] = tk;
+          if (tk < n_list) {
+            cp_async16(&S.desc[q][0], list + 2 * (size_t)tk);
+            cp_async16(&S.desc[q][1], list + 2 * (size_t)tk + 1);
+          }
+        }
+        cp_async_wait_all();
+        if (t0 + 2 < n_list) tk_next = (int)atomicAdd(&gs->tile_next, 1u);
+        if (s_tk[0] < n_list) {
+          issue_rec(S, tp.tile_rec, 0, S.desc[0]);
+          pend |= 9u;
+        }
+        if (s_tk[1] < n_list) {
+          issue_rec(S, tp.tile_rec, 1, S.desc[1]);
+          pend |= 2u;
         }
       }
-      cp_async_wait_all();
-      if (t0 + 2 < n_list) tk_next = (int)atomicAdd(&gs->tile_next, 1u);
-      if (s_tk[0] < n_list) {
-        issue_rec(S, tp.tile_rec, 0, S.desc[0]);
-        issue_J(S, J, pad, S.desc[0][0].z, S.desc[0][0].w);
-        pend |= 9u;
-      }
-      if (s_tk[1] < n_list) {
-        issue_rec(S, tp.tile_rec, 1, S.desc[1]);
-        pend |= 2u;
-      }
+      __syncwarp();
+      if (s_tk[0] < n_list) issue_J(S, J, pad, S.desc[0][0].z, S.desc[0][0].w, tid);
     }
     __syncthreads();
     if (s_tk[0] < n_list) {
@@ -566,24 +568,26 @@ __global__ void __launch_bounds__(kTileObs, 3) series_persistent_f32_kernel(
       // start of this tile: refill sJ, the record ring and the descriptor ring for the tiles
       // ahead, and fetch the next tile's t rows and V^-1 once its record has arrived
       auto ahead = [&]() {
-        if (tid == 0) {
+        if (tid < 32) {
           if (s_tk[k1] < n_list) {
-            issue_J(S, J, pad, S.desc[k1][0].z, S.desc[k1][0].w);
-            pend |= 8u;
+            issue_J(S, J, pad, S.desc[k1][0].z, S.desc[k1][0].w, tid);
+            if (tid == 0) pend |= 8u;
           }
-          if (s_tk[k2] < n_list) {
-            issue_rec(S, tp.tile_rec, (k + 2) % 3, S.desc[k2]);
-            pend |= 1u << ((k + 2) % 3);
-          }
-          const int tk = tk_next;
-          s_tk[k3] = tk;
-          tk_next = n_list;
-          if (tk < n_list) {
-            cp_async16(&S.desc[k3][0], list + 2 * (size_t)tk);
-            cp_async16(&S.desc[k3][1], list + 2 * (size_t)tk + 1);
-            if (!ld_volatile(&sgl->all_done)) {
-              tk_next = (int)atomicAdd(&gs->tile_next, 1u);
-              if (tk_next > n_list) tk_next = n_list;
+          if (tid == 0) {
+            if (s_tk[k2] < n_list) {
+              issue_rec(S, tp.tile_rec, (k + 2) % 3, S.desc[k2]);
+              pend |= 1u << ((k + 2) % 3);
+            }
+            const int tk = tk_next;
+            s_tk[k3] = tk;
+            tk_next = n_list;
+            if (tk < n_list) {
+              cp_async16(&S.desc[k3][0], list + 2 * (size_t)tk);
+              cp_async16(&S.desc[k3][1], list + 2 * (size_t)tk + 1);
+              if (!ld_volatile(&sgl->all_done)) {
+                tk_next = (int)atomicAdd(&gs->tile_next, 1u);
+                if (tk_next > n_list) tk_next = n_list;
+              }
             }
           }
         }
