@@ -316,21 +316,22 @@ __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
 }
 
 // Sum of one chunk of a camera's slot rows, component k: rows [q0, q1) in row order (loads are
-// issued 16 floats or 8 doubles at a time; the additions are in row order either way).
+// issued 16 floats or 8 doubles at a time).  A chunk is a segment: FP32-bulk rows are added in
+// float inside it and the chunks in double (camera_body), FP64 rows in double throughout.
 template <typename PT>
 __device__ __forceinline__ double cam_chunk_sum(const PT* __restrict__ partial, int q0, int q1,
                                                 int k) {
   constexpr int B = sizeof(PT) == 4 ? 16 : 8;
-  double pc = 0.0;
+  PT pc = (PT)0;
   for (int rb = q0; rb < q1; rb += B) {
     PT buf[B];
 #pragma unroll
     for (int j = 0; j < B; ++j)
       buf[j] = (rb + j < q1) ? __ldcg(partial + (size_t)(rb + j) * 9 + k) : (PT)0;
 #pragma unroll
-    for (int j = 0; j < B; ++j) pc += (double)buf[j];
+    for (int j = 0; j < B; ++j) pc += buf[j];
   }
-  return pc;
+  return (double)pc;
 }
 
 // Camera body for cameras [cam0, cam0 + per_block): thread (c, k) sums component k of the
