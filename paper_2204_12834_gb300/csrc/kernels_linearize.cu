@@ -84,6 +84,26 @@ void launch_cam_prepare(const double* cams, const double* dx_p, int n_cams, doub
 }
 
 // ---------------------------------------------------------------------------------------
+// Entry e of a slot's camera contribution as two products of staged values (J_p row 0 at 0..8,
+// row 1 at 9..17, r at 18, 19): packed (J_p^T J_p)_{ab} for e < 45, (J_p^T r)_j for e >= 45.
+struct LinPairTable {
+  uchar4 v[kLinVals];
+};
+__host__ __device__ constexpr LinPairTable make_lin_pairs() {
+  LinPairTable t{};
+  for (int e = 0; e < kLinVals; ++e) {
+    if (e < 45) {
+      const int a = packed_row(e), b = packed_col(e);
+      t.v[e] = uchar4{(unsigned char)a, (unsigned char)b, (unsigned char)(9 + a), (unsigned char)(9 + b)};
+    } else {
+      const int j = e - 45;
+      t.v[e] = uchar4{(unsigned char)j, 18, (unsigned char)(9 + j), 19};
+    }
+  }
+  return t;
+}
+__constant__ LinPairTable kLinPairs = make_lin_pairs();
+
 // Entry IDX of the per-observation camera contribution: packed (J_p^T J_p)_{ij} for IDX < 45,
 // else (J_p^T r)_j.  Resolved at compile time.
 template <int IDX, typename T>
@@ -183,7 +203,8 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
     T* __restrict__ r, double* __restrict__ V, double* __restrict__ b_l, T* __restrict__ partial,
     double* __restrict__ block_cost) {
   __shared__ T s9[kTileObs][9];
-  __shared__ T sg[kTileObs][9];
+  __shared__ T sg[sizeof(T) == 4 ? 1 : kTileObs][9];
+  __shared__ float sj[sizeof(T) == 4 ? kTileObs : 1][20];
   __shared__ uint16_t sbeg[kTileObs];
   __shared__ int srow[kTileObs];
   __shared__ double sred[kTileObs / 32];
@@ -244,13 +265,34 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
 #pragma unroll
     for (int k = 0; k < 3; ++k) b_l[(size_t)l * 3 + k] = (double)acc[6 + k];
   }
-  // camera contributions in 6 rounds of 9 values: 45 packed J_p^T J_p entries, then J_p^T r
-  lin_round<0>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
-  lin_round<1>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
-  lin_round<2>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
-  lin_round<3>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
-  lin_round<4>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
-  lin_round<5>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
+  if constexpr (sizeof(T) == 4) {
+    // FP32-bulk: J_p and r of each observation staged once at its camera-sorted position; then
+    // thread (slot, entry) sums entry `entry` of the slot's J_p^T J_p / J_p^T r over the slot's
+    // rows in row order (float inside the slot segment)
+    if (active) {
+#pragma unroll
+      for (int e = 0; e < 18; ++e) sj[pos][e] = jp[e];
+      sj[pos][18] = rr[0];
+      sj[pos][19] = rr[1];
+    }
+    __syncthreads();
+    for (int pr = tid; pr < ns * kLinVals; pr += blockDim.x) {
+      const int sl = pr / kLinVals, e = pr - sl * kLinVals;
+      const int beg = sbeg[sl], end = (sl + 1 < ns) ? (int)sbeg[sl + 1] : n;
+      const uchar4 ix = kLinPairs.v[e];
+      float acc = 0.f;
+      for (int q = beg; q < end; ++q) acc += sj[q][ix.x] * sj[q][ix.y] + sj[q][ix.z] * sj[q][ix.w];
+      partial[(size_t)srow[sl] * kLinVals + e] = acc;
+    }
+  } else {
+    // camera contributions in 6 rounds of 9 values: 45 packed J_p^T J_p entries, then J_p^T r
+    lin_round<0>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
+    lin_round<1>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
+    lin_round<2>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
+    lin_round<3>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
+    lin_round<4>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
+    lin_round<5>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
+  }
   // block cost (fixed order)
   const double tot = block_sum_fixed(cost, sred);
   if (tid == 0 && block_cost) block_cost[tile] = tot;
