@@ -112,6 +112,7 @@ struct ba_handle {
   SeriesGlobal* sgl = nullptr;
   LmRecord* rec = nullptr;        // [n_probs]
   int32_t* not_spd = nullptr;
+  int32_t* io_bad = nullptr;      // [2] non-finite flags of ba_set_params
   int n_probs = 1;
   std::vector<int32_t> cam_off_h, lm_off_h;  // caller numbering of the problems' cameras / landmarks
 
@@ -121,6 +122,7 @@ struct ba_handle {
   GridSync* h_gs = nullptr;
   LmRecord* h_rec = nullptr;     // [n_probs]
   int32_t* h_flag = nullptr;
+  int32_t* h_io = nullptr;       // [2]
   double* h_scalar = nullptr;
 
   bool linearized = false;
@@ -480,6 +482,7 @@ ba_status ba_destroy(ba_handle* h) {
   if (h->h_rec) cudaFreeHost(h->h_rec);
   if (h->h_gs) cudaFreeHost(h->h_gs);
   if (h->h_flag) cudaFreeHost(h->h_flag);
+  if (h->h_io) cudaFreeHost(h->h_io);
   if (h->h_scalar) cudaFreeHost(h->h_scalar);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -715,6 +718,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   items.push_back({(void**)&h->sgl, sizeof(SeriesGlobal)});
   items.push_back({(void**)&h->rec, sizeof(LmRecord) * P});
   items.push_back({(void**)&h->not_spd, sizeof(int32_t) * P});
+  items.push_back({(void**)&h->io_bad, sizeof(int32_t) * 2});
   size_t total = 0;
   for (auto& it : items) total = align_up(total, 256) + it.bytes;
   total = align_up(total, 256);
@@ -746,6 +750,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
       (e = cudaMallocHost(&h->h_rec, sizeof(LmRecord) * P)) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_gs, sizeof(GridSync))) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_flag, sizeof(int32_t) * P)) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_io, sizeof(int32_t) * 2)) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_scalar, sizeof(double) * 4)) != cudaSuccess)
     return bail(fail_cuda(e, "cudaMallocHost"));
 
@@ -1463,63 +1468,71 @@ ba_status ba_cost_batch(ba_handle* h, double* costs) {
   return BA_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Camera [n_c][9] and landmark [n_l][3] arrays out in the caller's order (landmarks permuted on
+// the device through the staging buffer adj_l); one synchronisation.
+ba_status state_out(ba_handle* h, const double* cams_dev, const double* lms_dev, double* cams,
+                    double* lms, int32_t ptr_kind) {
+  if (ptr_kind != 0 && ptr_kind != 1) return fail(BA_ERR_INVALID_ARG, "ptr_kind must be 0 or 1");
+  cudaStream_t s = h->stream;
+  const cudaMemcpyKind kind = ptr_kind == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (cams) CK(cudaMemcpyAsync(cams, cams_dev, sizeof(double) * (size_t)h->n_c * 9, kind, s));
+  if (lms) {
+    launch_scatter_rows3(lms_dev, h->lm_order_dev, h->n_l, h->adj_l, s);
+    h->launches += 1;
+    CK(cudaMemcpyAsync(lms, h->adj_l, sizeof(double) * (size_t)h->n_l * 3, kind, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  return check_launch(h, "state output");
+}
+
+}  // namespace
+
+extern "C" {
+
 ba_status ba_get_params(ba_handle* h, double* cams, double* lms, int32_t ptr_kind) {
   if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
-  if (ptr_kind != 0 && ptr_kind != 1) return fail(BA_ERR_INVALID_ARG, "ptr_kind must be 0 or 1");
-  CK(cudaStreamSynchronize(h->stream));
-  if (cams) {
-    if (ptr_kind == 1) CK(cudaMemcpy(cams, h->cams, sizeof(double) * h->n_c * 9, cudaMemcpyDeviceToDevice));
-    else CK(cudaMemcpy(cams, h->cams, sizeof(double) * h->n_c * 9, cudaMemcpyDeviceToHost));
-  }
-  if (lms) {
-    std::vector<double> li((size_t)h->n_l * 3), lo((size_t)h->n_l * 3);
-    CK(cudaMemcpy(li.data(), h->lms, sizeof(double) * li.size(), cudaMemcpyDeviceToHost));
-    for (int i = 0; i < h->n_l; ++i)
-      for (int k = 0; k < 3; ++k) lo[(size_t)h->sched.lm_order[i] * 3 + k] = li[(size_t)i * 3 + k];
-    ba_status st = copy_out(lms, lo.data(), sizeof(double) * lo.size(), ptr_kind);
-    if (st != BA_OK) return st;
-  }
-  return BA_OK;
+  return state_out(h, h->cams, h->lms, cams, lms, ptr_kind);
 }
 
 ba_status ba_set_params(ba_handle* h, const double* cams, const double* lms, int32_t ptr_kind) {
   if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
   if (ptr_kind != 0 && ptr_kind != 1) return fail(BA_ERR_INVALID_ARG, "ptr_kind must be 0 or 1");
-  std::vector<double> c, l;
-  if (cams) copy_in(c, cams, (size_t)h->n_c * 9, ptr_kind);
-  if (lms) copy_in(l, lms, (size_t)h->n_l * 3, ptr_kind);
-  for (double v : c) if (!std::isfinite(v)) return fail(BA_ERR_NONFINITE, "non-finite camera parameter");
-  for (double v : l) if (!std::isfinite(v)) return fail(BA_ERR_NONFINITE, "non-finite landmark");
-  CK(cudaStreamSynchronize(h->stream));
-  if (cams) CK(cudaMemcpy(h->cams, c.data(), sizeof(double) * c.size(), cudaMemcpyHostToDevice));
-  if (lms) {
-    std::vector<double> li(l.size());
-    for (int i = 0; i < h->n_l; ++i)
-      for (int k = 0; k < 3; ++k) li[(size_t)i * 3 + k] = l[(size_t)h->sched.lm_order[i] * 3 + k];
-    CK(cudaMemcpy(h->lms, li.data(), sizeof(double) * li.size(), cudaMemcpyHostToDevice));
+  cudaStream_t s = h->stream;
+  const size_t nc9 = (size_t)h->n_c * 9, nl3 = (size_t)h->n_l * 3;
+  // host inputs are copied into the staging buffers first; the state changes only once every
+  // value is known to be finite
+  const double* c_src = cams;
+  const double* l_src = lms;
+  if (ptr_kind == 0) {
+    if (cams) CK(cudaMemcpyAsync(h->adj_p, cams, sizeof(double) * nc9, cudaMemcpyHostToDevice, s));
+    if (lms) CK(cudaMemcpyAsync(h->adj_l, lms, sizeof(double) * nl3, cudaMemcpyHostToDevice, s));
+    c_src = h->adj_p;
+    l_src = h->adj_l;
   }
+  CK(cudaMemsetAsync(h->io_bad, 0, sizeof(int32_t) * 2, s));
+  if (cams) launch_check_finite(c_src, (int)nc9, h->io_bad + 0, s);
+  if (lms) launch_check_finite(l_src, (int)nl3, h->io_bad + 1, s);
+  CK(cudaMemcpyAsync(h->h_io, h->io_bad, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  ba_status st = check_launch(h, "state input");
+  if (st != BA_OK) return st;
+  if (h->h_io[0]) return fail(BA_ERR_NONFINITE, "non-finite camera parameter");
+  if (h->h_io[1]) return fail(BA_ERR_NONFINITE, "non-finite landmark");
+  if (cams) CK(cudaMemcpyAsync(h->cams, c_src, sizeof(double) * nc9, cudaMemcpyDeviceToDevice, s));
+  if (lms) launch_gather_rows3(l_src, h->lm_order_dev, h->n_l, h->lms, s);
+  h->launches += (cams ? 1 : 0) + (lms ? 2 : 0);
   h->linearized = false;
   h->cost_valid = false;
-  return BA_OK;
+  return check_launch(h, "state input");
 }
 
 ba_status ba_get_step(ba_handle* h, double* dx_p, double* dx_l, int32_t ptr_kind) {
   if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
-  if (ptr_kind != 0 && ptr_kind != 1) return fail(BA_ERR_INVALID_ARG, "ptr_kind must be 0 or 1");
-  CK(cudaStreamSynchronize(h->stream));
-  if (dx_p) {
-    if (ptr_kind == 1) CK(cudaMemcpy(dx_p, h->x, sizeof(double) * h->n_c * 9, cudaMemcpyDeviceToDevice));
-    else CK(cudaMemcpy(dx_p, h->x, sizeof(double) * h->n_c * 9, cudaMemcpyDeviceToHost));
-  }
-  if (dx_l) {
-    std::vector<double> li((size_t)h->n_l * 3), lo((size_t)h->n_l * 3);
-    CK(cudaMemcpy(li.data(), h->dx_l, sizeof(double) * li.size(), cudaMemcpyDeviceToHost));
-    for (int i = 0; i < h->n_l; ++i)
-      for (int k = 0; k < 3; ++k) lo[(size_t)h->sched.lm_order[i] * 3 + k] = li[(size_t)i * 3 + k];
-    ba_status st = copy_out(dx_l, lo.data(), sizeof(double) * lo.size(), ptr_kind);
-    if (st != BA_OK) return st;
-  }
-  return BA_OK;
+  return state_out(h, h->x, h->dx_l, dx_p, dx_l, ptr_kind);
 }
 
 ba_status ba_get_linearization(ba_handle* h, double* r, double* Jp, double* Jl, int32_t ptr_kind) {

@@ -267,6 +267,35 @@ void launch_active_tiles(const Topology& tp, const SeriesState* st, int32_t* lis
   active_tiles_fill_kernel<<<(tp.n_tiles + 255) / 256, 256, 0, s>>>(tp, st, list_off, list);
 }
 
+// ---------------------------------------------------------------------------------------
+// State input / output between the caller's landmark order and the internal order.
+__global__ void check_finite_kernel(const double* __restrict__ src, int n, int32_t* bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && !isfinite(src[i])) atomicOr(bad, 1);
+}
+
+__global__ void gather_rows3_kernel(const double* __restrict__ src, const int32_t* __restrict__ order,
+                                    int n, double* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 3 * n) dst[i] = src[(size_t)order[i / 3] * 3 + i % 3];
+}
+
+__global__ void scatter_rows3_kernel(const double* __restrict__ src, const int32_t* __restrict__ order,
+                                     int n, double* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 3 * n) dst[(size_t)order[i / 3] * 3 + i % 3] = src[i];
+}
+
+void launch_check_finite(const double* src, int n, int32_t* bad, cudaStream_t s) {
+  if (n > 0) check_finite_kernel<<<(n + 255) / 256, 256, 0, s>>>(src, n, bad);
+}
+void launch_gather_rows3(const double* src, const int32_t* order, int n, double* dst, cudaStream_t s) {
+  if (n > 0) gather_rows3_kernel<<<(3 * n + 255) / 256, 256, 0, s>>>(src, order, n, dst);
+}
+void launch_scatter_rows3(const double* src, const int32_t* order, int n, double* dst, cudaStream_t s) {
+  if (n > 0) scatter_rows3_kernel<<<(3 * n + 255) / 256, 256, 0, s>>>(src, order, n, dst);
+}
+
 __global__ void set_scalar_kernel(double* dst, double v) { *dst = v; }
 
 void launch_set_scalar(double* dst, double v, cudaStream_t s) { set_scalar_kernel<<<1, 1, 0, s>>>(dst, v); }

@@ -297,6 +297,12 @@ void launch_apply_step(const Topology& tp, const LmRecord* rec, double* cams,
 
 void launch_set_scalar(double* dst, double v, cudaStream_t s);
 
+// State input / output: *bad |= 1 if any of src[0..n) is not finite; dst[i] (internal order)
+// = src[order[i]] (rows of 3); dst[order[i]] = src[i].
+void launch_check_finite(const double* src, int n, int32_t* bad, cudaStream_t s);
+void launch_gather_rows3(const double* src, const int32_t* order, int n, double* dst, cudaStream_t s);
+void launch_scatter_rows3(const double* src, const int32_t* order, int n, double* dst, cudaStream_t s);
+
 // PCG on the reduced camera system (kernels_pcg.cu).  Scalars of the recursion, in sc[]:
 enum { kPcgRz = 0, kPcgPq = 1, kPcgRzNew = 2, kPcgRr = 3, kPcgBb = 4, kPcgZero = 5, kPcgCount = 8 };
 constexpr int kPcgDotBlocks = 128;
