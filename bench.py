@@ -637,6 +637,17 @@ def batched_section(args, poba, torch, stream, dev, max_over_ranks, barrier):
     wall_s = max_over_ranks(sum(r[1] for r in runs))
     per = np.array(runs[-1][2])
     n_solves = len(runs)
+    f32_costs = poba.ba_cost_batch(hb)
+    # the plain FP64 path on the same batch: one solve, its time and the final costs
+    del hb
+    h64 = poba.batch_from_problems(probs, precision=poba.BA_FP64, stream=stream)
+    poba.ba_autotune(h64, trials=1)
+    poba.ba_set_params(h64, cams0, lms0)
+    poba.ba_set_lm_state(h64, 1e-4, 2.0, 0)
+    hb = h64
+    r64 = solve()
+    f64_costs = poba.ba_cost_batch(h64)
+    ratio = f32_costs / f64_costs - 1.0
     return {
         "metric": "problems/s (batched sub-problems solved to func_tol, FP32 bulk)",
         "value": P * n_solves / (dev_ms / 1e3),
@@ -649,6 +660,12 @@ def batched_section(args, poba, torch, stream, dev, max_over_ranks, barrier):
         "converged": runs[-1][4],
         "not_spd_iterations": runs[-1][5],
         "series_form": tuned,
+        "fp64_batch": {"problems_per_s": P / (r64[0] / 1e3), "batch_solve_ms": r64[0],
+                       "p50_solve_ms": float(np.percentile(r64[2], 50)),
+                       "p99_solve_ms": float(np.percentile(r64[2], 99)),
+                       "converged": r64[4], "lm_steps_per_solve": r64[3]},
+        "final_cost_fp32_vs_fp64": {"median_rel": float(np.median(ratio)),
+                                    "max_abs_rel": float(np.abs(ratio).max())},
         "gpu_launches": int(launches),
         "solves": n_solves,
         "memory_bytes": poba.ba_memory_footprint(hb),
