@@ -82,18 +82,33 @@ def test_schur_jacobi_one_iteration_for_single_observation_tracks(poba):
     assert rel(dxp, x) < 1e-10 and rel(dxl, xl) < 1e-10
 
 
+def schur_cancellation(ne, lam):
+    """||(|U_lam| + |W| |V_lam^-1| |W|^T) t|| / ||S t|| at t = 1: how many digits the float
+    products lose when S t = U_lam t - W V_lam^-1 W^T t cancels."""
+    Ul, Vl = ne.damped(lam)
+    Vi = neq.chol_inverse(Vl)
+    t = np.ones(9 * ne.n_cams)
+    aW = abs(ne.W)
+    mag = neq.apply_blocks(np.abs(Ul), t) + aW @ neq.apply_blocks(np.abs(Vi), aW.T @ t)
+    return float(np.linalg.norm(mag) / np.linalg.norm(opcg.schur_apply(ne, Ul, Vi, t)))
+
+
 def test_pcg_fp32_bulk(poba, case):
-    """FP32-bulk: the same iterates as the oracle's FP64 PCG within 1e-4 for a fixed number of
-    iterations; a converged solve takes about as many iterations as in FP64.  (The converged
-    FP32 step solves the float system: its FP64 residual is bounded by cond(S) times the float
-    rounding of J, not by rtol.)"""
+    """FP32-bulk: the same iterates as the oracle's FP64 PCG for a fixed number of iterations;
+    a converged solve takes about as many iterations as in FP64.  The bound follows from the
+    arithmetic: a float S p carries about one float rounding (2^-24) times the cancellation
+    ratio of U_lam - W V^-1 W^T (about 8e3 here at lambda = 1e-2) and CG passes it on to the
+    iterate, so the test allows twice that.  (The converged FP32 step solves the float system:
+    its FP64 residual is bounded by cond(S) times the float rounding of J, not by rtol.)"""
     p, ref = case
+    tol = 2.0 * schur_cancellation(ref.ne, 1e-2) * 2.0 ** -24
+    assert 1e-4 < tol < 2e-3
     for precond, m in (("jacobi", 0), ("power", 2)):
         h = handle(poba, p, precision=1)
         poba.ba_solve_schur_pcg(h, 1e-2, precond, m, rtol=0.0, max_iter=6)
         dxp, _ = poba.ba_get_step(h)
         xo, _, _, _ = opcg.pcg_solve(ref.ne, 1e-2, precond, m, rtol=0.0, max_iter=6)
-        assert rel(dxp, xo) < 1e-4
+        assert rel(dxp, xo) < tol, (precond, rel(dxp, xo), tol)
     h = handle(poba, p, precision=1)
     info = poba.ba_solve_schur_pcg(h, 1e-3, "jacobi", rtol=1e-6, max_iter=1000)
     h64 = handle(poba, p)
