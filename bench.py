@@ -59,6 +59,8 @@ def parse_args(argv=None):
     ap.add_argument("--batch-solves", type=int, default=3)
     ap.add_argument("--no-pcg", action="store_true",
                     help="skip the PCG comparison (Schur-Jacobi and power-series preconditioners)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large single-problem section (10,000 cameras, 5M observations)")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the adjoint section (200 cameras, 20,000 landmarks, weighted)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
@@ -195,18 +197,22 @@ def series_term_units(p, sched_slots: int, s: int):
 
 def explicit_s_bytes(p) -> int:
     """Block-sparse explicit S (what an explicit-Schur PCG stores): distinct camera pairs that
-    share a landmark (upper triangle incl. diagonal) x 81 doubles."""
-    order = np.argsort(p.lm_idx, kind="stable")
-    li, ci = p.lm_idx[order], p.cam_idx[order].astype(np.int64)
-    starts = np.r_[0, np.nonzero(np.diff(li))[0] + 1, len(li)]
-    pairs = set()
+    share a landmark (upper triangle incl. diagonal) x 81 doubles.  Landmarks are grouped by
+    track length so that each group's pairs come from one index table."""
+    order = np.lexsort((p.cam_idx, p.lm_idx))
+    cams = p.cam_idx[order].astype(np.int64)
+    counts = np.bincount(p.lm_idx, minlength=p.n_lms)
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
     nc = p.n_cams
-    for a, b in zip(starts[:-1], starts[1:]):
-        cs = np.unique(ci[a:b])
-        for i in range(len(cs)):
-            for j in range(i, len(cs)):
-                pairs.add(int(cs[i]) * nc + int(cs[j]))
-    return len(pairs) * 81 * 8
+    codes = []
+    for k in np.unique(counts[counts > 0]):
+        ls = starts[counts == k]
+        tracks = cams[ls[:, None] + np.arange(k)[None, :]]  # [n_k, k] sorted cameras
+        i, j = np.triu_indices(int(k))
+        codes.append((tracks[:, i] * nc + tracks[:, j]).ravel())
+    if not codes:
+        return 0
+    return int(np.unique(np.concatenate(codes)).size) * 81 * 8
 
 
 # ---------------------------------------------------------------------------------------
@@ -426,6 +432,8 @@ def run_poba(args):
                                                            max_over_ranks, barrier)
 
     adjoint = None if args.no_adjoint else adjoint_section(args, poba, torch, stream, dev)
+    large = None if args.no_large else large_section(args, poba, torch, stream, dev,
+                                                     max_over_ranks, barrier)
     pcg = None if args.no_pcg else pcg_section(poba, torch, stream, results)
 
     roof64 = roofline("fp64")
@@ -493,6 +501,7 @@ def run_poba(args):
         "batched": batched,
         "adjoint": adjoint,
         "pcg": pcg,
+        "large": large,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
@@ -582,6 +591,96 @@ def adjoint_section(args, poba, torch, stream, dev):
             "adjoint_lambda": lam, "adjoint_terms": info["inner_iters"],
             "config": {"workload": "weighted_200c_20000l", "n_cams": p.n_cams,
                        "n_lms": p.n_lms, "n_obs": p.n_obs, "weights": "U(0.5, 1.5)"}}
+
+
+LARGE_WORKLOAD = "powerlaw_10000c_1000000l"
+
+
+def large_section(args, poba, torch, stream, dev, max_over_ranks, barrier):
+    """The large single problem (10,000 cameras, 1,000,000 landmarks, about 5.0M observations,
+    power-law tracks on [2, 50]) in FP32 bulk: LM iterations/s from x0, series solves/s, the
+    series term against the HBM roofline (its Jacobians, 0.48 GB, are well beyond L2, so no
+    flush is needed) and the memory footprint next to an explicit block-sparse S."""
+    p = bal_synth.preset(LARGE_WORKLOAD)
+    to_dev = lambda a: torch.as_tensor(a).to(dev)
+    cams0_d, lms0_d = to_dev(p.cams0), to_dev(p.lms0)
+    with torch.cuda.stream(stream):
+        h = poba.ba_create(cams0_d, lms0_d, to_dev(p.obs), to_dev(p.cam_idx), to_dev(p.lm_idx),
+                           precision=poba.BA_FP32_BULK, stream=stream)
+    tuned = poba.ba_autotune(h, trials=2)
+    n_steps = max(3, min(args.steps, 20))
+
+    def lm_steps(n):
+        poba.ba_set_params(h, cams0_d, lms0_d)
+        poba.ba_set_lm_state(h, 1e-4, 2.0, 0)
+        evs = []
+        with torch.cuda.stream(stream):
+            for _ in range(n):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                poba.ba_lm_step(h)
+                e1.record(stream)
+                evs.append((e0, e1))
+        stream.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    lm_steps(max(3, args.warmup))
+    poba.ba_set_timing(h, True)
+    launches0 = poba.ba_kernel_launches(h)
+    barrier()
+    ms = lm_steps(n_steps)
+    barrier()
+    launches = poba.ba_kernel_launches(h) - launches0
+    timing = poba.ba_get_timing(h)
+    poba.ba_set_timing(h, False)
+    total_ms = max_over_ranks(sum(ms))
+    poba.ba_linearize(h, want_cost=False)
+    evs = []
+    n_solves = 10
+    with torch.cuda.stream(stream):
+        for _ in range(n_solves):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = poba.ba_solve_schur_power(h, 1e-4)
+            e1.record(stream)
+            evs.append((e0, e1))
+    stream.synchronize()
+    solve_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs))
+    ms_t, cnt = timing["series_tile"]
+    ms_c, _ = timing["series_camera"]
+    avg_s = (ms_t + ms_c) / 1e3 / max(cnt, 1)
+    nb, nf = series_term_units(p, schedule_slots(p), 4)
+    hbm_peak, hbm_kind, _, _ = measured_peaks()
+    ach = nb / avg_s / 1e9
+    out = {
+        "metric": "LM iterations/s (large single problem, FP32 bulk)",
+        "value": n_steps / (total_ms / 1e3),
+        "unit": "LM iterations/s",
+        "ms_per_step": total_ms / n_steps,
+        "solves_per_s": n_solves / (solve_ms / 1e3),
+        "solve_inner_iters": info["inner_iters"],
+        "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": ach / hbm_peak,
+                     "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)"
+                     if hbm_kind == "measured" else "fallback 6800 GB/s",
+                     "kernel": "series term (tile phase, camera phase, two grid barriers)",
+                     "series_form": tuned, "algorithmic_bytes_per_term": nb,
+                     "algorithmic_flops_per_term": nf, "avg_term_us": avg_s * 1e6, "terms": cnt,
+                     "achieved_tflops": nf / avg_s / 1e12, "traffic": None},
+        "kernels": {k: {"avg_us": (v[0] * 1e3 / v[1]) if v[1] else None, "count": v[1]}
+                    for k, v in timing.items()},
+        "gpu_launches": int(launches),
+        "memory_bytes": poba.ba_memory_footprint(h),
+        "explicit_S_bytes": explicit_s_bytes(p),
+        "config": {"workload": LARGE_WORKLOAD, "n_cams": p.n_cams, "n_lms": p.n_lms,
+                   "n_obs": p.n_obs, "tracks": "power law k^-2.14 on [2, 50], window max(2k, 64)",
+                   "series": {"eps": 0.01, "max_inner": 20}, "lm": {"lambda0": 1e-4},
+                   "steps": n_steps, "l2": "inputs larger than L2 (no flush)"},
+    }
+    poba.ba_destroy(h)
+    return out
 
 
 def batched_section(args, poba, torch, stream, dev, max_over_ranks, barrier):

@@ -966,9 +966,7 @@ ba_status ba_set_options(ba_handle* h, const ba_options* o) {
   if (!h || !o) return fail(BA_ERR_INVALID_ARG, "NULL argument");
   std::string why;
   if (!valid_options(*o, &why)) return fail(BA_ERR_INVALID_ARG, why);
-  const double lam_old = h->opts.lambda0;
   h->opts = *o;
-  (void)lam_old;
   return BA_OK;
 }
 

@@ -24,6 +24,10 @@ namespace poba {
 
 enum { kModeSeries = 0, kModeRhs = 1 };
 
+// FP32 tiles whose slots hold fewer rows than this on average sum each (slot, component) in one
+// thread; longer slots are split over a warp.
+constexpr int kShortSlotRows = 6;
+
 template <typename T>
 __device__ __forceinline__ void load_J(const T* __restrict__ J, size_t pad, int o, T (&jp)[18],
                                        T (&jl)[6]) {
@@ -229,8 +233,21 @@ __device__ __forceinline__ void f32_tile_core(bool active, int n, int ns, int lm
     for (int j = 0; j < 9; ++j) g[j] = jp[j] * u0 + jp[9 + j] * u1;
   }
   __syncthreads();
-  // phase 3: one warp per slot; lane 3 k + c sums component k over the c-th third of the
-  // slot's rows in row order, and the three thirds are added in chunk order
+  // phase 3, chosen by the tile's shape (the same choice in every form):
+  //  * short slots (fewer than kShortSlotRows rows on average): one thread per (slot, component)
+  //    sums the slot's rows in row order;
+  //  * otherwise one warp per slot: lane 3 k + c sums component k over the c-th third of the
+  //    slot's rows in row order, and the three thirds are added in chunk order.
+  if (n < kShortSlotRows * ns) {
+    for (int k = tid; k < ns * 9; k += blockDim.x) {
+      const int sl = k / 9, kc = k - 9 * sl;
+      const int beg = sbeg[sl], end = (sl + 1 < ns) ? (int)sbeg[sl + 1] : n;
+      float acc = 0.f;
+      for (int q = beg; q < end; ++q) acc += sg[q][kc];
+      partial[(size_t)srow[sl] * 9 + kc] = acc;
+    }
+    return;
+  }
   const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
   const int kc = lane / 3, cc = lane - 3 * kc;
   for (int sl = warp; sl < ns; sl += nw) {
@@ -257,8 +274,10 @@ __device__ __forceinline__ void f32_tile_core(bool active, int n, int ns, int lm
 //   phase 2  every observation thread sums its own landmark's v in segment order and applies
 //            V^-1 (the same sum and the same z in every thread of the landmark), then scatters
 //            g = J_p^T (J_l z) to its camera-sorted position;
-//   phase 3  one warp per slot: 27 lanes, one per (component, third of the slot's rows), sum
-//            their rows in order; the thirds are added in order and written to the slot's row.
+//   phase 3  tiles of short slots: one thread per (slot, component) sums the slot's rows in
+//            order; otherwise one warp per slot: 27 lanes, one per (component, third of the
+//            slot's rows), sum their rows in order, the thirds are added in order; either way
+//            the sum is written to the slot's camera-major row.
 template <int MODE>
 __device__ __forceinline__ void tile_matvec_body_f32(const Topology& tp, int tile,
                                                      const float* __restrict__ J,
