@@ -40,7 +40,8 @@ constexpr int kTileLms = 256;   // landmarks per tile
 constexpr int kTileSlots = 128; // distinct cameras (slots) per tile
 constexpr int kTStride = 12;    // elements per camera row of the current term (9 used; 16-byte
                                 // aligned rows for asynchronous copies)
-constexpr int kCamChunkMin = 16;  // rows per chunk of a camera's row sum (at least)
+constexpr int kCamChunkMin = 64;  // rows per chunk of a camera's row sum (at least): few
+                                  // rounds for cameras with many slot rows
 constexpr int kRoundItems = 28;   // camera chunks per round of the persistent camera phase
 
 // Rows per chunk of a camera with `rows` slot rows: at least kCamChunkMin, and few enough
