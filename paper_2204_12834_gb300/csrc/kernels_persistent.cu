@@ -296,20 +296,28 @@ __global__ void __launch_bounds__(kTileObs, 3) series_persistent_kernel(
   const bool tracer = blockIdx.x == gridDim.x - 1 && tid == 0 && trace != nullptr;
   for (int i = 1; i <= m_max; ++i) {
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 0] = global_ns();
-    // ---- phase A: tiles (the next tile index is fetched while the current one is processed;
-    // once every problem has stopped the remaining tiles are moot; tiles of a problem that
-    // stopped are skipped)
-    int next = 0;
-    if (tid == 0)
-      next = ld_volatile(&sgl->all_done) ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
+    // ---- phase A: tiles.  Thread 0 claims the next ticket while the current tile is
+    // processed and reads the all-stopped flag for the claim after that, so neither round trip
+    // holds the block (tickets at or past n_tiles mean none).  Once every problem has stopped
+    // the remaining tiles are moot (a block may still take one); in a batch, tiles of a problem
+    // that stopped are skipped.
+    int next = 0, stop_seen = 0;
+    if (tid == 0) {
+      stop_seen = ld_volatile(&sgl->all_done) || (tp.n_probs == 1 && ld_volatile(&st[0].done));
+      next = stop_seen ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
+    }
     for (;;) {
       if (tid == 0) {
-        int cur = next;
-        while (cur < tp.n_tiles && ld_volatile(&st[tp.tile_prob[cur]].done))
-          cur = ld_volatile(&sgl->all_done) ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
+        int cur = next < tp.n_tiles ? next : tp.n_tiles;
+        if (tp.n_probs > 1) {
+          while (cur < tp.n_tiles && ld_volatile(&st[tp.tile_prob[cur]].done)) {
+            cur = ld_volatile(&sgl->all_done) ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
+            if (cur > tp.n_tiles) cur = tp.n_tiles;
+          }
+        }
         s_tile = cur;
-        if (cur < tp.n_tiles)
-          next = ld_volatile(&sgl->all_done) ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
+        if (cur < tp.n_tiles) next = stop_seen ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
+        stop_seen = ld_volatile(&sgl->all_done);  // used by the next claim
       }
       __syncthreads();
       const int tile = s_tile;
@@ -482,6 +490,7 @@ __global__ void __launch_bounds__(kTileObs, 3) series_persistent_f32_kernel(
     // ---- phase A, prologue: claim three tiles, fetch their descriptors, start the first
     // two records and the first Jacobians
     int tk_next = n_list;  // thread 0: ticket claimed for the slot after the last filled one
+    int stop_seen = 0;     // thread 0: the all-stopped flag as of the previous claim
     if (tid < 32) {
       if (tid == 0) {
         int t0 = n_list;
@@ -578,17 +587,17 @@ __global__ void __launch_bounds__(kTileObs, 3) series_persistent_f32_kernel(
               issue_rec(S, tp.tile_rec, (k + 2) % 3, S.desc[k2]);
               pend |= 1u << ((k + 2) % 3);
             }
+            // the ticket claimed one tile ago (at or past n_list: none) and the all-stopped
+            // flag read then: neither round trip is waited for in the tile that starts it
             const int tk = tk_next;
             s_tk[k3] = tk;
             tk_next = n_list;
             if (tk < n_list) {
               cp_async16(&S.desc[k3][0], list + 2 * (size_t)tk);
               cp_async16(&S.desc[k3][1], list + 2 * (size_t)tk + 1);
-              if (!ld_volatile(&sgl->all_done)) {
-                tk_next = (int)atomicAdd(&gs->tile_next, 1u);
-                if (tk_next > n_list) tk_next = n_list;
-              }
+              if (!stop_seen) tk_next = (int)atomicAdd(&gs->tile_next, 1u);
             }
+            stop_seen = ld_volatile(&sgl->all_done);
           }
         }
         if (s_tk[k1] >= n_list) {
