@@ -163,11 +163,11 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(precision: str, form: int):
+def profiled_traffic(precision: str, form: int, workload: str = WORKLOAD):
     """DRAM bytes per series term of the persistent kernel in the given form (3 plain, 4 with the
-    copy pipeline) from the committed ncu summary, if the kernel source is unchanged since the
-    capture; else None."""
-    path = os.path.join(ROOT, "profiles", f"series_persistent_{WORKLOAD}.json")
+    copy pipeline) on `workload`, from the committed ncu summary, if the kernel source is
+    unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", f"series_persistent_{workload}.json")
     try:
         d = json.load(open(path))
     except Exception:
@@ -181,18 +181,25 @@ def profiled_traffic(precision: str, form: int):
 
 
 # ---------------------------------------------------------------------------------------
-def series_term_units(p, sched_slots: int, s: int):
-    """Algorithmic bytes and flops of one power-series term t_i = U^-1 W V^-1 W^T t_{i-1}:
-    tile phase -- per observation J_p, J_l (24 s) and the 2-byte slot/position code, 48 FMA +
-    12 adds; per landmark V^-1 (6 s) and its segment offset (4 B), 9 FMA; per slot one 9-vector
-    partial written and the current term read (2 x 9 s);
-    camera phase -- per slot the partial read and the new term written (2 x 9 s), 9 adds; per
-    camera U^-1 (81 x 8 B) and x read / written (2 x 9 x 8 B), 81 FMA + 9 adds."""
+def series_term_units(p, s: int):
+    """Algorithmic (minimal) bytes and flops of one power-series term
+    t_i = U^-1 W V^-1 W^T t_{i-1} applied matrix-free, per Sec. 4.3: per observation J_p and
+    J_l (24 s) and its camera index (4 B), 48 FMA (J_p t 18, J_l^T u 6, J_l z 6, J_p^T w 18);
+    per landmark V^-1 (6 s) and its segment offset (4 B), 9 FMA; per camera U^-1 (45 x 8 B)
+    and t, x read and written (27 x 8 B), 81 FMA."""
     n_o, n_l, n_c = p.n_obs, p.n_lms, p.n_cams
-    bytes_ = (n_o * (24 * s + 2) + n_l * (6 * s + 4) + sched_slots * 9 * s * 4
-              + n_c * (81 * 8 + 18 * 8))
-    flops = n_o * (2 * 48 + 12) + n_l * 18 + sched_slots * 9 + n_c * (2 * 81 + 9)
+    bytes_ = n_o * (24 * s + 4) + n_l * (6 * s + 4) + n_c * (45 * 8 + 27 * 8)
+    flops = n_o * 2 * 48 + n_l * 2 * 9 + n_c * 2 * 81
     return bytes_, flops
+
+
+def series_term_design_bytes(p, sched_slots: int, s: int) -> int:
+    """Bytes one term moves in this design: the observation term with the 2-byte slot code,
+    V^-1, per (tile, camera) slot a 9-vector partial written and read back and the current term
+    gathered and the new one written (4 x 9 s), and per camera U^-1 (81 x 8 B) and x."""
+    n_o, n_l, n_c = p.n_obs, p.n_lms, p.n_cams
+    return (n_o * (24 * s + 2) + n_l * (6 * s + 4) + sched_slots * 9 * s * 4
+            + n_c * (81 * 8 + 18 * 8))
 
 
 def explicit_s_bytes(p) -> int:
@@ -400,7 +407,8 @@ def run_poba(args):
         ms_t, cnt = r["timing"]["series_tile"]
         ms_c, _ = r["timing"]["series_camera"]
         s = 8 if name == "fp64" else 4
-        nb, nf = series_term_units(p, r_slots, s)
+        nb, nf = series_term_units(p, s)
+        nd = series_term_design_bytes(p, r_slots, s)
         avg_s = (ms_t + ms_c) / 1e3 / max(cnt, 1)
         form = r["tuned"]["exec"]
         prec = "double" if name == "fp64" else "float"
@@ -413,7 +421,8 @@ def run_poba(args):
         traffic = profiled_traffic(name, form)
         common = {"kernel": kernel, "series_form": r["tuned"],
                   "traffic": traffic, "algorithmic_bytes_per_term": nb,
-                  "algorithmic_flops_per_term": nf, "avg_term_us": avg_s * 1e6, "terms": cnt,
+                  "algorithmic_flops_per_term": nf, "design_bytes_per_term": nd,
+                  "design_gbs": nd / avg_s / 1e9, "avg_term_us": avg_s * 1e6, "terms": cnt,
                   "dominant_class": cls}
         if name == "fp64":
             ach = nf / avg_s / 1e12
@@ -651,7 +660,8 @@ def large_section(args, poba, torch, stream, dev, max_over_ranks, barrier):
     ms_t, cnt = timing["series_tile"]
     ms_c, _ = timing["series_camera"]
     avg_s = (ms_t + ms_c) / 1e3 / max(cnt, 1)
-    nb, nf = series_term_units(p, schedule_slots(p), 4)
+    nb, nf = series_term_units(p, 4)
+    nd = series_term_design_bytes(p, schedule_slots(p), 4)
     hbm_peak, hbm_kind, _, _ = measured_peaks()
     ach = nb / avg_s / 1e9
     out = {
@@ -667,8 +677,10 @@ def large_section(args, poba, torch, stream, dev, max_over_ranks, barrier):
                      if hbm_kind == "measured" else "fallback 6800 GB/s",
                      "kernel": "series term (tile phase, camera phase, two grid barriers)",
                      "series_form": tuned, "algorithmic_bytes_per_term": nb,
-                     "algorithmic_flops_per_term": nf, "avg_term_us": avg_s * 1e6, "terms": cnt,
-                     "achieved_tflops": nf / avg_s / 1e12, "traffic": None},
+                     "algorithmic_flops_per_term": nf, "design_bytes_per_term": nd,
+                     "design_gbs": nd / avg_s / 1e9, "avg_term_us": avg_s * 1e6, "terms": cnt,
+                     "achieved_tflops": nf / avg_s / 1e12,
+                     "traffic": profiled_traffic("fp32_bulk", tuned["exec"], LARGE_WORKLOAD)},
         "kernels": {k: {"avg_us": (v[0] * 1e3 / v[1]) if v[1] else None, "count": v[1]}
                     for k, v in timing.items()},
         "gpu_launches": int(launches),
@@ -778,27 +790,34 @@ def batched_section(args, poba, torch, stream, dev, max_over_ranks, barrier):
     }
 
 
-def schedule_slots(p, tile_obs=256, tile_lms=256) -> int:
-    """Number of (tile, camera) slots: landmarks ordered by their smallest observing camera and
-    packed greedily into tiles of whole tracks, as the library's schedule does."""
-    counts = np.bincount(p.lm_idx, minlength=p.n_lms)
+def schedule_slots(p, tile_obs=256, tile_lms=256, tile_cams=128) -> int:
+    """Number of (tile, camera) slots of the library's schedule: landmarks ordered by their
+    smallest observing camera, packed greedily into tiles of whole tracks (at most tile_obs
+    observations, tile_lms landmarks, tile_cams distinct cameras)."""
     key = np.full(p.n_lms, p.n_cams, dtype=np.int64)
     np.minimum.at(key, p.lm_idx, p.cam_idx)
     lm_order = np.argsort(key, kind="stable")
     rank = np.empty_like(lm_order)
     rank[lm_order] = np.arange(p.n_lms)
-    tiles = np.empty(p.n_lms, dtype=np.int64)
-    t = obs = lms = 0
-    for i in lm_order:
-        k = counts[i]
-        if lms > 0 and (obs + k > tile_obs or lms + 1 > tile_lms):
-            t += 1
-            obs = lms = 0
-        obs += k
+    order = np.lexsort((p.cam_idx, rank[p.lm_idx]))
+    cams = p.cam_idx[order].tolist()
+    seg = np.concatenate([[0], np.cumsum(np.bincount(rank[p.lm_idx], minlength=p.n_lms))]).tolist()
+    stamp = [-1] * p.n_cams
+    tile = obs = lms = ncam = slots = 0
+    for i in range(p.n_lms):
+        a, b = seg[i], seg[i + 1]
+        fresh = sum(1 for c in cams[a:b] if stamp[c] != tile)
+        if lms > 0 and (obs + b - a > tile_obs or lms + 1 > tile_lms or ncam + fresh > tile_cams):
+            slots += ncam
+            tile += 1
+            obs = lms = ncam = 0
+            fresh = b - a
+        for c in cams[a:b]:
+            stamp[c] = tile
+        obs += b - a
         lms += 1
-        tiles[i] = t
-    pair = tiles[p.lm_idx] * p.n_cams + p.cam_idx
-    return int(np.unique(pair).size)
+        ncam += fresh
+    return slots + ncam
 
 
 # ---------------------------------------------------------------------------------------
