@@ -104,41 +104,6 @@ __host__ __device__ constexpr LinPairTable make_lin_pairs() {
 }
 __constant__ LinPairTable kLinPairs = make_lin_pairs();
 
-// Entry IDX of the per-observation camera contribution: packed (J_p^T J_p)_{ij} for IDX < 45,
-// else (J_p^T r)_j.  Resolved at compile time.
-template <int IDX, typename T>
-__device__ __forceinline__ T lin_entry(const T (&jp)[18], const T (&rr)[2]) {
-  if constexpr (IDX < 45) {
-    constexpr int i = packed_row(IDX), j = packed_col(IDX);
-    return jp[i] * jp[j] + jp[9 + i] * jp[9 + j];
-  } else {
-    constexpr int j = IDX - 45;
-    return jp[j] * rr[0] + jp[9 + j] * rr[1];
-  }
-}
-
-// One round of 9 camera values: stage at the observation's camera-sorted position, then sum
-// per slot into partial[row(slot) * 54 + ROUND * 9 + k].
-template <int ROUND, typename T>
-__device__ __forceinline__ void lin_round(bool active, const T (&jp)[18], const T (&rr)[2], int pos,
-                                          T (*sg)[9], int ns, int n, const uint16_t* sbeg,
-                                          const int* srow, T* partial) {
-  if (active) {
-    sg[pos][0] = lin_entry<ROUND * 9 + 0>(jp, rr);
-    sg[pos][1] = lin_entry<ROUND * 9 + 1>(jp, rr);
-    sg[pos][2] = lin_entry<ROUND * 9 + 2>(jp, rr);
-    sg[pos][3] = lin_entry<ROUND * 9 + 3>(jp, rr);
-    sg[pos][4] = lin_entry<ROUND * 9 + 4>(jp, rr);
-    sg[pos][5] = lin_entry<ROUND * 9 + 5>(jp, rr);
-    sg[pos][6] = lin_entry<ROUND * 9 + 6>(jp, rr);
-    sg[pos][7] = lin_entry<ROUND * 9 + 7>(jp, rr);
-    sg[pos][8] = lin_entry<ROUND * 9 + 8>(jp, rr);
-  }
-  __syncthreads();
-  slot_sums<T, T>(sg, ns, n, sbeg, srow, partial + ROUND * 9, kLinVals);
-  __syncthreads();
-}
-
 // Residual and Jacobians of one observation in precision T.
 template <typename T>
 __device__ __forceinline__ void bal_residual_jacobian(const double* __restrict__ q, const double X0d,
@@ -202,9 +167,15 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
     const double2* __restrict__ obs, const double* __restrict__ sqrt_w, T* __restrict__ J,
     T* __restrict__ r, double* __restrict__ V, double* __restrict__ b_l, T* __restrict__ partial,
     double* __restrict__ block_cost) {
-  __shared__ T s9[kTileObs][9];
-  __shared__ T sg[sizeof(T) == 4 ? 1 : kTileObs][9];
-  __shared__ float sj[sizeof(T) == 4 ? kTileObs : 1][20];
+  // sj: J_p and r of each observation at its camera-sorted position; s9: the landmark
+  // contributions.  In FP64 the two share storage (the static limit is 48 KB), with a barrier
+  // between the landmark sums and the staging.
+  constexpr bool kAlias = sizeof(T) == 8;
+  constexpr int kSjBytes = kTileObs * 20 * (int)sizeof(T);
+  constexpr int kS9Bytes = kTileObs * 9 * (int)sizeof(T);
+  __shared__ __align__(16) unsigned char lin_smem[kAlias ? kSjBytes : kSjBytes + kS9Bytes];
+  T (*sj)[20] = reinterpret_cast<T (*)[20]>(lin_smem);
+  T (*s9)[9] = reinterpret_cast<T (*)[9]>(lin_smem + (kAlias ? 0 : kSjBytes));
   __shared__ uint16_t sbeg[kTileObs];
   __shared__ int srow[kTileObs];
   __shared__ double sred[kTileObs / 32];
@@ -265,33 +236,29 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
 #pragma unroll
     for (int k = 0; k < 3; ++k) b_l[(size_t)l * 3 + k] = (double)acc[6 + k];
   }
-  if constexpr (sizeof(T) == 4) {
-    // FP32-bulk: J_p and r of each observation staged once at its camera-sorted position; then
-    // thread (slot, entry) sums entry `entry` of the slot's J_p^T J_p / J_p^T r over the slot's
-    // rows in row order (float inside the slot segment)
-    if (active) {
+  // J_p and r of each observation staged once at its camera-sorted position; then thread
+  // (slot, entry) sums entry `entry` of the slot's J_p^T J_p / J_p^T r over the slot's rows in
+  // row order (FP32-bulk: in float inside the slot segment; FP64: two FMAs per row)
+  if constexpr (kAlias) __syncthreads();  // the landmark sums above have read s9
+  if (active) {
 #pragma unroll
-      for (int e = 0; e < 18; ++e) sj[pos][e] = jp[e];
-      sj[pos][18] = rr[0];
-      sj[pos][19] = rr[1];
+    for (int e = 0; e < 18; ++e) sj[pos][e] = jp[e];
+    sj[pos][18] = rr[0];
+    sj[pos][19] = rr[1];
+  }
+  __syncthreads();
+  for (int pr = tid; pr < ns * kLinVals; pr += blockDim.x) {
+    const int sl = pr / kLinVals, e = pr - sl * kLinVals;
+    const int beg = sbeg[sl], end = (sl + 1 < ns) ? (int)sbeg[sl + 1] : n;
+    const uchar4 ix = kLinPairs.v[e];
+    T acc = (T)0;
+    for (int q = beg; q < end; ++q) {
+      if constexpr (sizeof(T) == 8)
+        acc = fma(sj[q][ix.x], sj[q][ix.y], fma(sj[q][ix.z], sj[q][ix.w], acc));
+      else
+        acc += sj[q][ix.x] * sj[q][ix.y] + sj[q][ix.z] * sj[q][ix.w];
     }
-    __syncthreads();
-    for (int pr = tid; pr < ns * kLinVals; pr += blockDim.x) {
-      const int sl = pr / kLinVals, e = pr - sl * kLinVals;
-      const int beg = sbeg[sl], end = (sl + 1 < ns) ? (int)sbeg[sl + 1] : n;
-      const uchar4 ix = kLinPairs.v[e];
-      float acc = 0.f;
-      for (int q = beg; q < end; ++q) acc += sj[q][ix.x] * sj[q][ix.y] + sj[q][ix.z] * sj[q][ix.w];
-      partial[(size_t)srow[sl] * kLinVals + e] = acc;
-    }
-  } else {
-    // camera contributions in 6 rounds of 9 values: 45 packed J_p^T J_p entries, then J_p^T r
-    lin_round<0>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
-    lin_round<1>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
-    lin_round<2>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
-    lin_round<3>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
-    lin_round<4>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
-    lin_round<5>(active, jp, rr, pos, sg, ns, n, sbeg, srow, partial);
+    partial[(size_t)srow[sl] * kLinVals + e] = acc;
   }
   // block cost (fixed order)
   const double tot = block_sum_fixed(cost, sred);
