@@ -137,23 +137,25 @@ template void launch_tile_backsub<float>(const Topology&, const float*, const fl
 int tile_blocks(const Topology& tp) { return tp.n_tiles; }
 
 // ---------------------------------------------------------------------------------------
-// Camera step: kCamBlock cameras x 9 components per block (camera body, norm pair per camera),
-// then the stop rule of every running problem in the last block to finish.
 int camera_blocks(const Topology& tp) { return (tp.n_cams + kCamBlock - 1) / kCamBlock; }
 
-template <typename PT, int MODE>
-__global__ void __launch_bounds__(kCamBlock * 9) camera_step_kernel(
+// Camera step: CS cameras x 9 components per block (camera body, norm pair per camera), then
+// the stop rule of every running problem in the last block to finish.  A handle with one or two
+// problems takes 8-camera blocks, which spread the latency-bound row sums over many SMs; a batch
+// takes kCamBlock cameras (9 warps), so that the last block has warps for its many problems.
+template <typename PT, int MODE, int CS>
+__global__ void __launch_bounds__(CS * 9) camera_step_kernel(
     Topology tp, const PT* __restrict__ partial, const double* __restrict__ b_p,
     const double* __restrict__ Uinv, double* __restrict__ x, PT* __restrict__ t_cam,
     double* __restrict__ cam_norm, SeriesState* __restrict__ st, SeriesGlobal* __restrict__ sgl,
     int iter, double eps) {
-  __shared__ double ys[kCamBlock][9];
-  __shared__ double y2[kCamBlock][9];
+  __shared__ double ys[CS][9];
+  __shared__ double y2[CS][9];
   __shared__ int is_last, s_running;
   if (MODE == kModeSeries && sgl->all_done) return;
   const int tid = threadIdx.x;
-  camera_body<PT, MODE>(tp, blockIdx.x * kCamBlock, kCamBlock, partial, b_p, Uinv, x, t_cam, st,
-                        cam_norm, ys, y2);
+  camera_body<PT, MODE>(tp, blockIdx.x * CS, CS, partial, b_p, Uinv, x, t_cam, st, cam_norm, ys,
+                        y2);
   if (tid == 0) {
     __threadfence();
     const unsigned ticket = atomicAdd(&sgl->counter, 1u);
@@ -166,20 +168,32 @@ __global__ void __launch_bounds__(kCamBlock * 9) camera_step_kernel(
   if (tid == 0) sgl->counter = 0u;
 }
 
+template <typename PT, int MODE>
+void launch_camera_step(const Topology& tp, const PT* partial, const double* b_p,
+                        const double* Uinv, double* x, PT* t_cam, double* cam_norm,
+                        SeriesState* st, SeriesGlobal* sgl, int iter, double eps, cudaStream_t s) {
+  constexpr int kSmall = 8;
+  if (tp.n_probs <= 2)
+    camera_step_kernel<PT, MODE, kSmall><<<(tp.n_cams + kSmall - 1) / kSmall, kSmall * 9, 0, s>>>(
+        tp, partial, b_p, Uinv, x, t_cam, cam_norm, st, sgl, iter, eps);
+  else
+    camera_step_kernel<PT, MODE, kCamBlock><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(
+        tp, partial, b_p, Uinv, x, t_cam, cam_norm, st, sgl, iter, eps);
+}
+
 template <typename PT>
 void launch_camera_rhs(const Topology& tp, const PT* partial, const double* b_p, const double* Uinv,
                        double* x, PT* t_cam, double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
                        cudaStream_t s) {
-  camera_step_kernel<PT, kModeRhs><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(
-      tp, partial, b_p, Uinv, x, t_cam, cam_norm, st, sgl, 0, 0.0);
+  launch_camera_step<PT, kModeRhs>(tp, partial, b_p, Uinv, x, t_cam, cam_norm, st, sgl, 0, 0.0, s);
 }
 
 template <typename PT>
 void launch_camera_series(const Topology& tp, const PT* partial, const double* Uinv, double* x,
                           PT* t_cam, double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
                           int iter, double eps, cudaStream_t s) {
-  camera_step_kernel<PT, kModeSeries><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(
-      tp, partial, nullptr, Uinv, x, t_cam, cam_norm, st, sgl, iter, eps);
+  launch_camera_step<PT, kModeSeries>(tp, partial, nullptr, Uinv, x, t_cam, cam_norm, st, sgl,
+                                      iter, eps, s);
 }
 
 template void launch_camera_rhs<double>(const Topology&, const double*, const double*, const double*, double*, double*, double*, SeriesState*, SeriesGlobal*, cudaStream_t);

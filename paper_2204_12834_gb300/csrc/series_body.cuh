@@ -445,20 +445,33 @@ __device__ __forceinline__ void series_stop_rule(SeriesState* st, int iter, doub
 
 // Every problem still running: sum its cameras' norm pairs (one warp per problem, lanes strided
 // over the cameras, then a fixed shuffle tree) and apply its stop rule for term `iter`; raise
-// all_done when no problem is left.  Every thread of one block must call it.
+// all_done when no problem is left.  Every thread of one block (at least one full warp) must
+// call it.
 __device__ __forceinline__ void problems_stop_rule(const Topology& tp,
                                                    const double* __restrict__ cam_norm,
                                                    SeriesState* st, SeriesGlobal* sgl, int iter,
                                                    double eps, int* s_running) {
+  // only full warps take problems (the shuffles below use every lane of a warp)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   if (threadIdx.x == 0) *s_running = 0;
   __syncthreads();
-  for (int p = warp; p < tp.n_probs; p += nw) {
+  for (int p = warp; warp < nw && p < tp.n_probs; p += nw) {
     if (ld_volatile(&st[p].done)) continue;  // warp-uniform
+    // lane j adds the pairs of cameras j, j + 32, j + 64, ... in that order; the loads go out
+    // eight at a time so that the sum waits for one round trip per eight cameras
     double a = 0.0, b = 0.0;
-    for (int c = tp.cam_off[p] + lane; c < tp.cam_off[p + 1]; c += 32) {
-      a += __ldcg(cam_norm + 2 * c + 0);
-      b += __ldcg(cam_norm + 2 * c + 1);
+    const int c1 = tp.cam_off[p + 1];
+    const double2* cn = reinterpret_cast<const double2*>(cam_norm);
+    for (int cb = tp.cam_off[p] + lane; cb < c1; cb += 32 * 8) {
+      double2 v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        v[j] = cb + 32 * j < c1 ? __ldcg(cn + cb + 32 * j) : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        a += v[j].x;
+        b += v[j].y;
+      }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
