@@ -7,7 +7,7 @@
 //            V^-1, W z) -- dynamic scheduling, so no wave tail;
 //   phase B  camera groups (spread over all blocks, static) run the camera body (U^-1, x
 //            accumulation, new term rows) and store a squared-norm pair per camera;
-//   barrier  the last block to arrive opens it at once, then sums each running problem's
+//   barrier  the last block to arrive opens it by arriving, then sums each running problem's
 //            camera norm pairs in camera order and applies its stop rule; the other blocks see
 //            the decisions before their next tile fetch and, at the latest, at the next
 //            barrier (a stopped problem's tiles and cameras are skipped, so its x stays at the
@@ -32,39 +32,34 @@ __device__ __forceinline__ long long global_ns() {
   return (long long)t;
 }
 
-// Arrive at the barrier.  Returns (in every thread) whether this block arrived last; the
-// generation seen before arriving is stored in *gen.
-__device__ __forceinline__ int barrier_arrive(GridSync* gs, unsigned G, unsigned* gen, int* s_last,
-                                              unsigned* s_gen) {
+// Grid barrier on a monotonic arrival counter: barrier n of a launch completes when the counter
+// reaches (n + 1) G, so the last block to arrive opens it by its own arrival (no release step)
+// and the others poll the counter.  Arrive: the block's writes are made visible (barrier, then
+// a fence by the arriving thread), then one atomic.  Returns (in every thread) whether this block
+// arrived last; the count that completes the barrier is stored in *target.
+__device__ __forceinline__ int barrier_arrive(GridSync* gs, unsigned G, unsigned* target,
+                                              int* s_last, unsigned* s_target) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned g = ld_volatile(&gs->gen);
     __threadfence();
-    const unsigned ticket = atomicAdd(&gs->count, 1u);
-    *s_last = ticket == G - 1;
-    *s_gen = g;
+    const unsigned ticket = atomicAdd(&gs->arrive, 1u);
+    *s_last = ticket % G == G - 1;
+    *s_target = (ticket / G + 1) * G;
   }
   __syncthreads();
-  *gen = *s_gen;
+  *target = *s_target;
   return *s_last;
 }
 
-// Last block: open the barrier (after its own work).  Thread 0 only.
-__device__ __forceinline__ void barrier_release(GridSync* gs) {
-  gs->count = 0u;
-  __threadfence();
-  atomicAdd(&gs->gen, 1u);
-}
-
-// Wait until the generation moves past `gen`; false on timeout or when another block failed.
-// Polls with an exponential back-off (32 ns .. 512 ns) to keep the hot word quiet.
-__device__ __forceinline__ bool barrier_wait(GridSync* gs, unsigned gen, long long timeout,
+// Wait until the arrival count reaches `target`; false on timeout or when another block failed.
+// Polls with an exponential back-off (32 ns .. 256 ns) to keep the hot word quiet.
+__device__ __forceinline__ bool barrier_wait(GridSync* gs, unsigned target, long long timeout,
                                              int* s_ok) {
   if (threadIdx.x == 0) {
     int ok = 1;
     const long long t0 = clock64();
     unsigned sleep_ns = 32;
-    for (unsigned it = 0; ld_volatile(&gs->gen) == gen; ++it) {
+    for (unsigned it = 0; ld_volatile(&gs->arrive) < target; ++it) {
       if (clock64() - t0 > timeout) {
         atomicExch(&gs->error, 1);
         ok = 0;
@@ -75,7 +70,7 @@ __device__ __forceinline__ bool barrier_wait(GridSync* gs, unsigned gen, long lo
         break;
       }
       __nanosleep(sleep_ns);
-      if (sleep_ns < 512) sleep_ns <<= 1;
+      if (sleep_ns < 256) sleep_ns <<= 1;
     }
     __threadfence();
     *s_ok = ok;
@@ -250,28 +245,26 @@ __device__ __forceinline__ bool term_end_barrier(const Topology& tp, GridSync* g
                                                  SeriesGlobal* sgl, int i, double eps,
                                                  long long timeout, int* s_last, unsigned* s_gen,
                                                  int* s_ok, int* s_running) {
-  unsigned gen;
-  if (barrier_arrive(gs, gridDim.x, &gen, s_last, s_gen)) {
-    if (threadIdx.x == 0) barrier_release(gs);
+  unsigned target;
+  if (barrier_arrive(gs, gridDim.x, &target, s_last, s_gen)) {
     __threadfence();
     problems_stop_rule(tp, cam_norm, st, sgl, i, eps, s_running);
     return true;
   }
-  return barrier_wait(gs, gen, timeout, s_ok);
+  return barrier_wait(gs, target, timeout, s_ok);
 }
 
 // Barrier 1 of a term (after the tile phase): the last block resets the tile counter.
 __device__ __forceinline__ bool tile_end_barrier(GridSync* gs, long long timeout, int* s_last,
                                                  unsigned* s_gen, int* s_ok) {
-  unsigned gen;
-  if (barrier_arrive(gs, gridDim.x, &gen, s_last, s_gen)) {
-    if (threadIdx.x == 0) {
-      gs->tile_next = 0u;
-      barrier_release(gs);
-    }
+  unsigned target;
+  if (barrier_arrive(gs, gridDim.x, &target, s_last, s_gen)) {
+    // no block claims tiles again before the term's second barrier, which this block reaches
+    // after the reset (its arrival there publishes it)
+    if (threadIdx.x == 0) atomicExch(&gs->tile_next, 0u);
     return true;
   }
-  return barrier_wait(gs, gen, timeout, s_ok);
+  return barrier_wait(gs, target, timeout, s_ok);
 }
 
 template <typename T>
@@ -556,7 +549,7 @@ __global__ void __launch_bounds__(kTileObs, 3) series_persistent_f32_kernel(
       __syncthreads();
       if (s_fail) break;
       const int4 d0 = S.desc[dk][0], d1 = S.desc[dk][1];
-      const int L0 = d0.x, nl = d0.y, o0 = d0.z, n = d0.w, ns = d1.y;
+      const int nl = d0.y, o0 = d0.z, n = d0.w, ns = d1.y;
       const TileRecLayout g = tile_rec_layout(n, ns, nl);
       const uint8_t* rec = S.rec[rk];
       const bool active = tid < n;
@@ -571,7 +564,6 @@ __global__ void __launch_bounds__(kTileObs, 3) series_persistent_f32_kernel(
         meta = reinterpret_cast<const uint16_t*>(rec + g.meta)[tid];
         lm = rec[g.olm + tid];
       }
-      (void)L0;
       const int k1 = (k + 1) & 3, k2 = (k + 2) & 3, k3 = (k + 3) & 3;
       // after the core's first barrier every thread holds its J in registers and is past the
       // start of this tile: refill sJ, the record ring and the descriptor ring for the tiles
@@ -673,8 +665,6 @@ int persistent_blocks_per_sm(bool f32) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, series_persistent_kernel<double>, kTileObs, 0);
   return nb;
 }
-
-size_t pipelined_smem_bytes() { return sizeof(F32Pipe); }
 
 int pipelined_blocks_per_sm() {
   if (cudaFuncSetAttribute(series_persistent_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

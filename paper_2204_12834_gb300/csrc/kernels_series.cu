@@ -134,8 +134,6 @@ template void launch_tile_series<float>(const Topology&, const float*, const flo
 template void launch_tile_backsub<double>(const Topology&, const double*, const double*, const double*, const double*, const double*, double*, double*, cudaStream_t);
 template void launch_tile_backsub<float>(const Topology&, const float*, const float*, const double*, const double*, const float*, double*, double*, cudaStream_t);
 
-int tile_blocks(const Topology& tp) { return tp.n_tiles; }
-
 // ---------------------------------------------------------------------------------------
 int camera_blocks(const Topology& tp) { return (tp.n_cams + kCamBlock - 1) / kCamBlock; }
 

@@ -191,10 +191,11 @@ struct SeriesGlobal {
 
 // Grid-barrier state of the persistent series kernel (zeroed before each launch).
 struct GridSync {
-  unsigned count;      // arrivals at the current barrier
-  unsigned gen;        // barrier generation, advanced by the last block to arrive
+  unsigned arrive;     // grid-barrier arrivals since the launch (barrier n completes at (n+1) G)
+  int error;           // 1: a barrier wait timed out or a block failed
+  unsigned pad0[30];   // the tile counter lives on its own 128-byte line
   unsigned tile_next;  // dynamic tile counter of the current tile phase
-  int error;           // 1: a barrier wait timed out
+  unsigned pad1[31];
 };
 
 // LM record (device), written by the decide kernel and read by the host once per iteration.
@@ -274,7 +275,6 @@ void launch_camera_series(const Topology& tp, const PT* partial, const double* U
                           int iter, double eps, cudaStream_t s);
 
 int camera_blocks(const Topology& tp);
-int tile_blocks(const Topology& tp);
 
 // done[p] = 1 for problems that take no part (rec[p].active == 0; rec may be NULL).
 void launch_series_reset(SeriesState* st, SeriesGlobal* sgl, const LmRecord* rec, int n_probs,
