@@ -362,7 +362,7 @@ def ba_cost_noalloc(cams, lms, obs, cam_idx, lm_idx, cost_out, weights=None, str
 
 
 def ba_get_series_trace(h: Handle):
-    """[terms, 5] ns timeline of block 0 in the last persistent series solve (see poba.h)."""
+    """[terms, 5] ns timeline of the last block in the last persistent series solve (see poba.h)."""
     buf = np.zeros(64 * 5, dtype=np.int64)
     n = C.c_int32()
     _check(library().ba_get_series_trace(h.ptr, buf.ctypes.data, buf.size, C.byref(n)),
