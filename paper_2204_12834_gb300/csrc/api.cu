@@ -62,6 +62,9 @@ struct ba_handle {
   // problem (internal orders)
   double2* obs = nullptr;
   double* sqrt_w = nullptr;
+  float2* obs32 = nullptr;     // FP32 bulk: float copies of obs and sqrt_w (linearisation)
+  float* sqrt_w32 = nullptr;
+  float* prep32 = nullptr;     // FP32 bulk: float copy of the prepared camera records
   double* cams = nullptr;
   double* cams_trial = nullptr;
   double* lms = nullptr;
@@ -270,10 +273,10 @@ void collect_timing(ba_handle* h, int terms_run, bool series_ran) {
 void seq_linearize(ba_handle* h) {
   cudaStream_t s = h->stream;
   tmark(h, kTLin, 0, 0);
-  launch_cam_prepare(h->cams, nullptr, h->n_c, h->prep, nullptr, s);
+  launch_cam_prepare(h->cams, nullptr, h->n_c, h->prep, nullptr, s, h->prep32);
   if (h->f32()) {
-    launch_linearize<float>(h->tp, h->prep, h->lms, h->obs, h->sqrt_w, (float*)h->J, (float*)h->r,
-                            h->V, h->b_l, (float*)h->partial, h->block_cost, s);
+    launch_linearize<float>(h->tp, h->prep32, h->lms, h->obs32, h->sqrt_w32, (float*)h->J,
+                            (float*)h->r, h->V, h->b_l, (float*)h->partial, h->block_cost, s);
     launch_lin_camera_reduce<float>(h->tp, (const float*)h->partial, h->U45, h->b_p, s);
   } else {
     launch_linearize<double>(h->tp, h->prep, h->lms, h->obs, h->sqrt_w, (double*)h->J,
@@ -670,6 +673,11 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   items.push_back({(void**)&h->cams_trial, sizeof(double) * nc * 9});
   items.push_back({(void**)&h->lms, sizeof(double) * nl * 3});
   items.push_back({(void**)&h->prep, sizeof(double) * nc * kCamPrep});
+  if (h->f32()) {
+    items.push_back({(void**)&h->prep32, sizeof(float) * nc * kCamPrep});
+    items.push_back({(void**)&h->obs32, sizeof(float2) * (no > 0 ? no : 1)});
+    if (h->weighted) items.push_back({(void**)&h->sqrt_w32, sizeof(float) * (no > 0 ? no : 1)});
+  }
   items.push_back({(void**)&h->prep_trial, sizeof(double) * nc * kCamPrep});
   items.push_back({&h->J, bulk * 24 * h->n_o_pad});
   items.push_back({&h->r, bulk * 2 * h->n_o_pad});
@@ -799,6 +807,18 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
       {h->lms, lms_i.data(), sizeof(double) * nl * 3},
   };
   if (h->weighted) ups.push_back({h->sqrt_w, sw_s.data(), sizeof(double) * no});
+  // FP32 bulk: the observations and weights in float, rounded once here as the kernels would
+  std::vector<float> obs32_s, sw32_s;
+  if (h->f32()) {
+    obs32_s.resize((size_t)no * 2);
+    for (size_t k = 0; k < obs32_s.size(); ++k) obs32_s[k] = (float)obs_s[k];
+    ups.push_back({h->obs32, obs32_s.data(), sizeof(float) * 2 * no});
+    if (h->weighted) {
+      sw32_s.resize(no);
+      for (int k = 0; k < no; ++k) sw32_s[k] = (float)sw_s[k];
+      ups.push_back({h->sqrt_w32, sw32_s.data(), sizeof(float) * no});
+    }
+  }
   for (int f = 0; f < 2; ++f)
     for (int k = 0; k < 3; ++k) {
       if (rl[f][k].round_cam.empty()) continue;

@@ -23,7 +23,7 @@ namespace poba {
 // ---------------------------------------------------------------------------------------
 __global__ void cam_prepare_kernel(const double* __restrict__ cams, const double* __restrict__ dx_p,
                                    int n_cams, double* __restrict__ prep,
-                                   double* __restrict__ cams_out) {
+                                   double* __restrict__ cams_out, float* __restrict__ prep32) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_cams) return;
   double p[9];
@@ -75,12 +75,16 @@ __global__ void cam_prepare_kernel(const double* __restrict__ cams, const double
   q[18] = p[3]; q[19] = p[4]; q[20] = p[5];
   q[21] = p[6]; q[22] = p[7]; q[23] = p[8];
   q[24] = first;
+  if (prep32) {  // the FP32-bulk linearisation reads the record in float, converted once here
+#pragma unroll
+    for (int j = 0; j < kCamPrep; ++j) prep32[(size_t)c * kCamPrep + j] = (float)q[j];
+  }
 }
 
 void launch_cam_prepare(const double* cams, const double* dx_p, int n_cams, double* prep,
-                        double* cams_out, cudaStream_t s) {
+                        double* cams_out, cudaStream_t s, float* prep32) {
   int threads = 128, blocks = (n_cams + threads - 1) / threads;
-  cam_prepare_kernel<<<blocks, threads, 0, s>>>(cams, dx_p, n_cams, prep, cams_out);
+  cam_prepare_kernel<<<blocks, threads, 0, s>>>(cams, dx_p, n_cams, prep, cams_out, prep32);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -106,15 +110,15 @@ __constant__ LinPairTable kLinPairs = make_lin_pairs();
 
 // Residual and Jacobians of one observation in precision T.
 template <typename T>
-__device__ __forceinline__ void bal_residual_jacobian(const double* __restrict__ q, const double X0d,
+__device__ __forceinline__ void bal_residual_jacobian(const T* __restrict__ q, const double X0d,
                                                       const double X1d, const double X2d,
-                                                      const double2 ob, T sw, T (&jp)[18],
+                                                      const vec2<T> ob, T sw, T (&jp)[18],
                                                       T (&jl)[6], T (&r)[2]) {
   const T R[9] = {(T)q[0], (T)q[1], (T)q[2], (T)q[3], (T)q[4], (T)q[5], (T)q[6], (T)q[7], (T)q[8]};
   const T G[9] = {(T)q[9], (T)q[10], (T)q[11], (T)q[12], (T)q[13], (T)q[14], (T)q[15], (T)q[16], (T)q[17]};
   const T t0 = (T)q[18], t1 = (T)q[19], t2 = (T)q[20];
   const T f = (T)q[21], k1 = (T)q[22], k2 = (T)q[23];
-  const bool first = q[24] != 0.0;
+  const bool first = q[24] != (T)0;
   const T X0 = (T)X0d, X1 = (T)X1d, X2 = (T)X2d;
   const T RX0 = R[0] * X0 + R[1] * X1 + R[2] * X2;
   const T RX1 = R[3] * X0 + R[4] * X1 + R[5] * X2;
@@ -163,8 +167,8 @@ __device__ __forceinline__ void bal_residual_jacobian(const double* __restrict__
 
 template <typename T>
 __global__ void __launch_bounds__(kTileObs) linearize_kernel(
-    Topology tp, const double* __restrict__ prep, const double* __restrict__ lms,
-    const double2* __restrict__ obs, const double* __restrict__ sqrt_w, T* __restrict__ J,
+    Topology tp, const T* __restrict__ prep, const double* __restrict__ lms,
+    const vec2<T>* __restrict__ obs, const T* __restrict__ sqrt_w, T* __restrict__ J,
     T* __restrict__ r, double* __restrict__ V, double* __restrict__ b_l, T* __restrict__ partial,
     double* __restrict__ block_cost) {
   // sj: J_p and r of each observation at its camera-sorted position; s9: the landmark
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
     const int o = o0 + tid;
     const int c = tp.cam_of[o], l = tp.lm_of[o];
     pos = tp.obs_meta[o] & 0xff;
-    const T sw = sqrt_w ? (T)sqrt_w[o] : (T)1;
+    const T sw = sqrt_w ? sqrt_w[o] : (T)1;
     bal_residual_jacobian<T>(prep + (size_t)c * kCamPrep, lms[l * 3 + 0], lms[l * 3 + 1],
                              lms[l * 3 + 2], obs[o], sw, jp, jl, rr);
     const size_t pad = (size_t)tp.n_obs_pad;
@@ -266,17 +270,17 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
 }
 
 template <typename T>
-void launch_linearize(const Topology& tp, const double* prep, const double* lms,
-                      const double2* obs, const double* sqrt_w, T* J, T* r, double* V,
-                      double* b_l, T* partial, double* block_cost, cudaStream_t s) {
+void launch_linearize(const Topology& tp, const T* prep, const double* lms, const vec2<T>* obs,
+                      const T* sqrt_w, T* J, T* r, double* V, double* b_l, T* partial,
+                      double* block_cost, cudaStream_t s) {
   linearize_kernel<T><<<tp.n_tiles, kTileObs, 0, s>>>(tp, prep, lms, obs, sqrt_w, J, r, V, b_l,
                                                       partial, block_cost);
 }
 template void launch_linearize<double>(const Topology&, const double*, const double*,
                                        const double2*, const double*, double*, double*, double*,
                                        double*, double*, double*, cudaStream_t);
-template void launch_linearize<float>(const Topology&, const double*, const double*,
-                                      const double2*, const double*, float*, float*, double*,
+template void launch_linearize<float>(const Topology&, const float*, const double*,
+                                      const float2*, const float*, float*, float*, double*,
                                       double*, float*, double*, cudaStream_t);
 
 // ---------------------------------------------------------------------------------------

@@ -221,13 +221,23 @@ void set_last_error(const std::string& msg);
 
 // ---------------------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files).  All take the stream last.
+// prep32 (optional): a float copy of the records for the FP32-bulk linearisation.
 void launch_cam_prepare(const double* cams, const double* dx_p, int n_cams, double* prep,
-                        double* cams_out, cudaStream_t s);
+                        double* cams_out, cudaStream_t s, float* prep32 = nullptr);
 
+// Pair type of the observations in a precision: double2 / float2.
+template <typename T> struct Vec2Of;
+template <> struct Vec2Of<double> { using type = double2; };
+template <> struct Vec2Of<float> { using type = float2; };
+template <typename T> using vec2 = typename Vec2Of<T>::type;
+
+// Inputs in the working precision T: the prepared camera records, the observations and the
+// square-root weights (FP32 bulk passes float copies made once, so that no observation pays a
+// double-to-float conversion, which GB300 runs on its FP64 pipe).
 template <typename T>
-void launch_linearize(const Topology& tp, const double* prep, const double* lms,
-                      const double2* obs, const double* sqrt_w, T* J, T* r, double* V,
-                      double* b_l, T* partial, double* block_cost, cudaStream_t s);
+void launch_linearize(const Topology& tp, const T* prep, const double* lms, const vec2<T>* obs,
+                      const T* sqrt_w, T* J, T* r, double* V, double* b_l, T* partial,
+                      double* block_cost, cudaStream_t s);
 
 template <typename PT>
 void launch_lin_camera_reduce(const Topology& tp, const PT* partial, double* U45, double* b_p,
