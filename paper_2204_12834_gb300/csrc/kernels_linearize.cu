@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
   T (*s9)[9] = reinterpret_cast<T (*)[9]>(lin_smem + (kAlias ? 0 : kSjBytes));
   __shared__ uint16_t sbeg[kTileObs];
   __shared__ int srow[kTileObs];
-  __shared__ double sred[kTileObs / 32];
+  __shared__ double sred[kTileObs];
 
   const int tile = blockIdx.x, tid = threadIdx.x;
   const int L0 = tp.tile_lm0[tile], L1 = tp.tile_lm0[tile + 1];
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
     partial[(size_t)srow[sl] * kLinVals + e] = acc;
   }
   // block cost (fixed order)
-  const double tot = block_sum_fixed(cost, sred);
+  const double tot = block_sum_tile(cost, sred);
   if (tid == 0 && block_cost) block_cost[tile] = tot;
 }
 
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kTileObs) tile_cost_kernel(
     Topology tp, const double* __restrict__ prep, const double* __restrict__ lms,
     const double* __restrict__ dx_l, const double2* __restrict__ obs,
     const double* __restrict__ sqrt_w, double* __restrict__ tile_cost) {
-  __shared__ double sred[kTileObs / 32];
+  __shared__ double sred[kTileObs];
   const int4 d = tp.tile_desc[2 * blockIdx.x];
   const int o0 = d.z, n = d.w;
   double e = 0.0;
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(kTileObs) tile_cost_kernel(
     e = r0 * r0 + r1 * r1;
     if (sqrt_w) e *= sqrt_w[o] * sqrt_w[o];
   }
-  const double tot = block_sum_fixed(e, sred);
+  const double tot = block_sum_tile(e, sred);
   if (threadIdx.x == 0) tile_cost[blockIdx.x] = tot;
 }
 

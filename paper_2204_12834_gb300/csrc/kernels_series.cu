@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kTileObs) tile_backsub_kernel(
     double* __restrict__ block_pred) {
   __shared__ T tcam[kTileObs][9];
   __shared__ T sv[kTileObs][3];
-  __shared__ double sred[kTileObs / 32];
+  __shared__ double sred[kTileObs];
 
   const int tile = blockIdx.x, tid = threadIdx.x;
   const TileHdr th = load_tile(tp, tile);
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kTileObs) tile_backsub_kernel(
     const double q1 = r1 + (double)u1 + (double)(jl[3] * z0 + jl[4] * z1 + jl[5] * z2);
     pred = (r0 * r0 + r1 * r1) - (q0 * q0 + q1 * q1);
   }
-  const double tot = block_sum_fixed(pred, sred);
+  const double tot = block_sum_tile(pred, sred);
   if (tid == 0) block_pred[tile] = tot;
 }
 

@@ -44,6 +44,24 @@ __device__ __forceinline__ double block_sum_fixed(double val, double* sred) {
   return tot;
 }
 
+// Sum of `val` over a tile block in a fixed order with few FP64 instructions: the values are
+// staged in sbuf ([blockDim.x] doubles), lane j of warp 0 adds values j, j + 32, j + 64, ... in
+// that order, then a shuffle tree adds the lanes.  About 12 FP64 warp instructions instead of a
+// shuffle tree in every warp.  Must be called by every thread of the block; the total is valid
+// in thread 0.
+__device__ __forceinline__ double block_sum_tile(double val, double* sbuf) {
+  sbuf[threadIdx.x] = val;
+  __syncthreads();
+  double a = 0.0;
+  if (threadIdx.x < 32) {
+    a = sbuf[threadIdx.x];
+    for (int j = threadIdx.x + 32; j < (int)blockDim.x; j += 32) a += sbuf[j];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
+  }
+  return a;
+}
+
 // Per-slot sums of a tile: rows sg[beg_s .. end_s) of the camera-sorted staging array are
 // summed for each slot s and component k (9 per row) and written to
 // out[row[s] * stride + k] (row: the slot's camera-major row, staged in shared memory).
