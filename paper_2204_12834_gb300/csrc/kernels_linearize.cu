@@ -83,7 +83,8 @@ __global__ void cam_prepare_kernel(const double* __restrict__ cams, const double
 
 void launch_cam_prepare(const double* cams, const double* dx_p, int n_cams, double* prep,
                         double* cams_out, cudaStream_t s, float* prep32) {
-  int threads = 128, blocks = (n_cams + threads - 1) / threads;
+  // one warp per block: the FP64 rotation work (sin, cos, sqrt) spreads over many SMs
+  int threads = 32, blocks = (n_cams + threads - 1) / threads;
   cam_prepare_kernel<<<blocks, threads, 0, s>>>(cams, dx_p, n_cams, prep, cams_out, prep32);
 }
 

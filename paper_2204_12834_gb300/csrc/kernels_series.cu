@@ -327,14 +327,30 @@ void launch_reduce_sum(const double* in, int n, double* out, double scale, cudaS
 }
 
 // One block per problem: scale * (sum of the problem's tile values), fixed order.
+// v[t0] + v[t0 + stride] + ... (t < t1) added in that order, with the loads issued eight at a
+// time so that the sum waits for one round trip per eight values.
+__device__ __forceinline__ double strided_sum(const double* __restrict__ v, int t0, int t1,
+                                              int stride) {
+  double a = 0.0;
+  for (int t = t0; t < t1; t += 8 * stride) {
+    double buf[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) buf[j] = t + j * stride < t1 ? v[t + j * stride] : 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (t + j * stride < t1) a += buf[j];
+  }
+  return a;
+}
+
 __global__ void __launch_bounds__(kReduceThreads) reduce_tiles_kernel(Topology tp,
                                                                        const double* tile_vals,
                                                                        double* out, int out_stride,
                                                                        double scale) {
   __shared__ double sred[kReduceThreads / 32];
   const int p = blockIdx.x;
-  double a = 0.0;
-  for (int t = tp.tile_off[p] + threadIdx.x; t < tp.tile_off[p + 1]; t += blockDim.x) a += tile_vals[t];
+  const double a = strided_sum(tile_vals, tp.tile_off[p] + threadIdx.x, tp.tile_off[p + 1],
+                               blockDim.x);
   const double tot = block_sum_fixed(a, sred);
   if (threadIdx.x == 0) out[(size_t)p * out_stride] = scale * tot;
 }
@@ -357,11 +373,9 @@ __global__ void __launch_bounds__(kReduceThreads) lm_decide_kernel(
   __shared__ double sred[kReduceThreads / 32];
   const int p = blockIdx.x;
   LmRecord* rec = rec_all + p;
-  double a = 0.0, b = 0.0;
-  for (int t = tp.tile_off[p] + threadIdx.x; t < tp.tile_off[p + 1]; t += blockDim.x) {
-    a += tile_cost[t];
-    b += tile_pred[t];
-  }
+  const int t0 = tp.tile_off[p] + threadIdx.x, t1 = tp.tile_off[p + 1];
+  const double a = strided_sum(tile_cost, t0, t1, blockDim.x);
+  const double b = strided_sum(tile_pred, t0, t1, blockDim.x);
   double F_new = 0.5 * block_sum_fixed(a, sred);
   __syncthreads();
   double pred = 0.5 * block_sum_fixed(b, sred);
