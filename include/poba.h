@@ -81,9 +81,9 @@ typedef struct {
                            for all terms with bounded grid barriers, 4 (BA_FP32_BULK) the
                            persistent kernel staging each tile's inputs with asynchronous bulk
                            copies issued ahead of the tile (needs at most 128 distinct cameras
-                           per tile, else as 3), 2 (default) the handle's choice: 4 when the
-                           float Jacobians exceed half the L2 cache, else 3, or what
-                           ba_autotune measured.  Forms a device cannot run fall back (4 to 3,
+                           per tile, else as 3), 2 (default) the handle's choice: 3 at the
+                           largest residency (4 blocks per SM in BA_FP32_BULK, 3 in BA_FP64),
+                           or what ba_autotune measured.  Forms a device cannot run fall back (4 to 3,
                            3 to 1: all blocks of a persistent kernel must be co-resident).  All
                            forms give bitwise-equal results. */
 } ba_options;
@@ -310,8 +310,9 @@ ba_status ba_solve_schur_pcg(ba_handle* h, double lambda, int32_t precond, int32
  * batched form).  On the handle's current linearisation (linearising first if needed) it times
  * `trials` series solves (damp, invert, max_inner terms, back-substitution; after one warm-up)
  * at lambda0 in each form the device can run -- the replayed CUDA graph of per-term launches,
- * the persistent kernel at 1, 2 or 3 blocks per SM, and in BA_FP32_BULK mode the persistent
- * kernel with the copy pipeline at 1, 2 or 3 blocks per SM -- and makes the fastest the form
+ * the persistent kernel at 1 to 3 blocks per SM (1 to 4 in BA_FP32_BULK mode), and in
+ * BA_FP32_BULK mode the persistent kernel with the copy pipeline at 1 to 3 blocks per SM --
+ * and makes the fastest the form
  * that series_exec 2 uses.  All forms give bitwise-equal results, so tuning changes only
  * speed.  Overwrites the last step (as ba_solve_schur_power does).  *exec_out (may be NULL)
  * receives the chosen form (1, 3 or 4), *blocks_per_sm_out (may be NULL) its blocks per SM (0

@@ -144,7 +144,7 @@ struct ba_handle {
   int sms = 0;
   int plain_max = 0, pipe_max = 0;       // occupancy limits (0: kernel unavailable)
   int plain_k = 0, pipe_k = 0;           // blocks per SM in use
-  CamRounds plain_rounds[3]{}, pipe_rounds[3]{};
+  CamRounds plain_rounds[4]{}, pipe_rounds[4]{};  // per blocks-per-SM setting (1..4)
   int auto_exec = 1;                     // form used for series_exec 2: 1, 3 or 4
   long long barrier_timeout = 1LL << 33;  // clock cycles a block waits at a grid barrier
   int last_exec = -1;                    // execution form of the last solve (1, 0, 3 or 4)
@@ -618,26 +618,25 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     const int per_sm = persistent_blocks_per_sm(h->f32());
     h->sms = sms;
-    h->plain_max = (coop && per_sm > 0) ? (per_sm < 3 ? per_sm : 3) : 0;
+    // FP32 bulk: the plain persistent kernel fits 4 blocks of 256 threads per SM
+    const int cap = h->f32() ? 4 : 3;
+    h->plain_max = (coop && per_sm > 0) ? (per_sm < cap ? per_sm : cap) : 0;
     if (h->f32() && h->plain_max > 0 && S.max_slots_per_tile <= kTileSlots) {
       const int pipe_per_sm = pipelined_blocks_per_sm();
       h->pipe_max = pipe_per_sm > 0 ? (pipe_per_sm < 3 ? pipe_per_sm : 3) : 0;
     }
     h->plain_k = h->plain_max;
     h->pipe_k = h->pipe_max;
-    // default form: persistent; FP32-bulk Jacobians that do not fit in half the L2 cache take
-    // the copy pipeline (ba_autotune measures instead)
-    int l2 = 0;
-    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
-    const double j_bytes = 24.0 * (h->f32() ? 4.0 : 8.0) * (double)no;
+    // default form: the plain persistent kernel at its largest residency (in FP32 bulk at 4
+    // blocks per SM it is at least as fast as the copy pipeline on every workload measured);
+    // ba_autotune measures every form instead
     h->auto_exec = h->plain_k > 0 ? 3 : 1;
-    if (h->pipe_k > 0 && j_bytes > 0.5 * (double)l2) h->auto_exec = 4;
     cudaGetLastError();
   }
   // camera schedules of the persistent kernels (rounds per grid size)
   CamSchedule cs;
   build_cam_schedule(S, &cs);
-  CamRoundList rl[2][3];
+  CamRoundList rl[2][4];
   for (int k = 1; k <= h->plain_max; ++k) build_cam_rounds(cs, nc, k * h->sms, &rl[0][k - 1]);
   for (int k = 1; k <= h->pipe_max; ++k) build_cam_rounds(cs, nc, k * h->sms, &rl[1][k - 1]);
 
@@ -707,11 +706,11 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   items.push_back({(void**)&d_tile_rec, S.tile_rec.size() > 0 ? S.tile_rec.size() : 16});
   items.push_back({(void**)&h->n_tiles_dev, sizeof(int32_t)});
   int32_t *d_cam_item, *d_item_q;
-  int32_t* d_rl[2][3][3] = {};
+  int32_t* d_rl[2][4][3] = {};
   items.push_back({(void**)&d_cam_item, sizeof(int32_t) * cs.cam_item.size()});
   items.push_back({(void**)&d_item_q, sizeof(int32_t) * (cs.item_q.size() > 0 ? cs.item_q.size() : 1)});
   for (int f = 0; f < 2; ++f)
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
       if (rl[f][k].round_cam.empty()) continue;
       items.push_back({(void**)&d_rl[f][k][0], sizeof(int32_t) * rl[f][k].round_cam.size()});
       items.push_back({(void**)&d_rl[f][k][1], sizeof(int32_t) * rl[f][k].round_item.size()});
@@ -820,7 +819,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
     }
   }
   for (int f = 0; f < 2; ++f)
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
       if (rl[f][k].round_cam.empty()) continue;
       ups.push_back({d_rl[f][k][0], rl[f][k].round_cam.data(), sizeof(int32_t) * rl[f][k].round_cam.size()});
       ups.push_back({d_rl[f][k][1], rl[f][k].round_item.data(), sizeof(int32_t) * rl[f][k].round_item.size()});
@@ -872,7 +871,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   tp.tile_rec = d_tile_rec;
   h->rhs_p = h->b_p;
   h->rhs_l = h->b_l;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4; ++k) {
     h->plain_rounds[k] = CamRounds{d_cam_item, d_item_q, d_rl[0][k][0], d_rl[0][k][1], d_rl[0][k][2]};
     h->pipe_rounds[k] = CamRounds{d_cam_item, d_item_q, d_rl[1][k][0], d_rl[1][k][1], d_rl[1][k][2]};
   }

@@ -268,7 +268,7 @@ __device__ __forceinline__ bool tile_end_barrier(GridSync* gs, long long timeout
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTileObs, 3) series_persistent_kernel(
+__global__ void __launch_bounds__(kTileObs, sizeof(T) == 4 ? 4 : 3) series_persistent_kernel(
     Topology tp, CamRounds cr, const T* __restrict__ J, const T* __restrict__ Vinv,
     const double* __restrict__ Uinv, double* __restrict__ x, T* __restrict__ t_cam,
     T* __restrict__ partial, double* __restrict__ cam_norm, SeriesState* __restrict__ st,
