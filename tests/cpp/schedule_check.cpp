@@ -1,0 +1,166 @@
+// Host check of the library's tile schedule (no GPU; test infrastructure for
+// tests/test_schedule_cpu.py).  Reads one problem's (or one batch's) observation indices from a
+// file, builds the schedule and the camera rounds for a grid of G blocks, and verifies the
+// properties the kernels rely on.  Prints "ok ..." or the first violated property.
+//
+// Input (little-endian int32): P, n_cams, n_lms, n_obs, G, cam_off[P + 1], lm_off[P + 1],
+// cam_idx[n_obs], lm_idx[n_obs].
+#include <cstdio>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "poba_internal.cuh"
+
+using namespace poba;
+
+#define CHECK(cond, ...)                 \
+  do {                                   \
+    if (!(cond)) {                       \
+      std::printf("FAIL: " __VA_ARGS__); \
+      std::printf("\n");                 \
+      return 1;                          \
+    }                                    \
+  } while (0)
+
+static bool read_ints(FILE* f, int32_t* p, size_t n) { return std::fread(p, 4, n, f) == n; }
+
+int main(int argc, char** argv) {
+  if (argc < 2) return 2;
+  FILE* f = std::fopen(argv[1], "rb");
+  if (!f) return 2;
+  int32_t hdr[5];
+  if (!read_ints(f, hdr, 5)) return 2;
+  const int P = hdr[0], nc = hdr[1], nl = hdr[2], no = hdr[3], G = hdr[4];
+  std::vector<int32_t> cam_off(P + 1), lm_off(P + 1), cam(no), lm(no);
+  if (!read_ints(f, cam_off.data(), P + 1) || !read_ints(f, lm_off.data(), P + 1) ||
+      !read_ints(f, cam.data(), no) || !read_ints(f, lm.data(), no))
+    return 2;
+  std::fclose(f);
+
+  Schedule S;
+  const std::string why = build_schedule(nc, nl, no, cam.data(), lm.data(), P,
+                                         P > 1 ? cam_off.data() : nullptr,
+                                         P > 1 ? lm_off.data() : nullptr, &S);
+  CHECK(why.empty(), "build_schedule rejected the input: %s", why.c_str());
+
+  // observations: a permutation of the caller's, sorted by (internal landmark, camera)
+  std::vector<char> seen(no, 0);
+  for (int o = 0; o < no; ++o) {
+    const int64_t q = S.obs_order[o];
+    CHECK(q >= 0 && q < no && !seen[q], "obs_order is not a permutation at %d", o);
+    seen[q] = 1;
+    CHECK(S.cam_of[o] == cam[q], "cam_of[%d] is not the caller's camera", o);
+    CHECK(S.lm_of[o] == S.lm_rank[lm[q]], "lm_of[%d] is not the internal landmark", o);
+    if (o > 0) {
+      CHECK(S.lm_of[o] > S.lm_of[o - 1] ||
+                (S.lm_of[o] == S.lm_of[o - 1] && S.cam_of[o] >= S.cam_of[o - 1]),
+            "observations %d, %d out of (landmark, camera) order", o - 1, o);
+    }
+  }
+  for (int l = 0; l < nl; ++l)
+    for (int o = S.lm_seg[l]; o < S.lm_seg[l + 1]; ++o)
+      CHECK(S.lm_of[o] == l, "lm_seg of landmark %d holds observation %d of another", l, o);
+  CHECK(S.lm_seg[0] == 0 && S.lm_seg[nl] == no, "lm_seg does not cover the observations");
+
+  // tiles: whole landmarks of one problem within the caps; slots = the tile's cameras ascending
+  CHECK(S.tile_lm0.front() == 0 && S.tile_lm0.back() == nl, "tiles do not cover the landmarks");
+  std::vector<int> slot_count_of_cam(nc, 0);
+  for (int t = 0; t < S.n_tiles; ++t) {
+    const int L0 = S.tile_lm0[t], L1 = S.tile_lm0[t + 1];
+    CHECK(L1 > L0, "tile %d is empty", t);
+    const int o0 = S.lm_seg[L0], n = S.lm_seg[L1] - o0;
+    const int nlt = L1 - L0;
+    std::set<int> cams;
+    for (int o = o0; o < o0 + n; ++o) cams.insert(S.cam_of[o]);
+    CHECK(nlt <= kTileLms, "tile %d holds %d landmarks", t, nlt);
+    CHECK(n <= kTileObs, "tile %d holds %d observations", t, n);
+    CHECK((int)cams.size() <= kTileSlots || nlt == 1, "tile %d holds %d cameras", t,
+          (int)cams.size());
+    for (int l = L0 + 1; l < L1; ++l)
+      CHECK(S.lm_prob[l] == S.lm_prob[L0], "tile %d holds two problems", t);
+    const int s0 = S.tile_slot0[t], ns = S.tile_slot0[t + 1] - s0;
+    CHECK(ns == (int)cams.size(), "tile %d has %d slots for %d cameras", t, ns, (int)cams.size());
+    int s = 0;
+    for (int c : cams) {
+      CHECK(S.slot_cam[s0 + s] == c, "tile %d slot %d is not its %d-th camera", t, s, s);
+      ++slot_count_of_cam[c];
+      ++s;
+    }
+    // observation codes: the slot of its camera, and positions that sort the tile by
+    // (camera, landmark order)
+    std::vector<int> at(n, -1);
+    for (int o = o0; o < o0 + n; ++o) {
+      const int pos = S.obs_meta[o] & 0xff, sl = S.obs_meta[o] >> 8;
+      CHECK(sl < ns && S.slot_cam[s0 + sl] == S.cam_of[o], "observation %d has a wrong slot", o);
+      CHECK(pos < n && at[pos] < 0, "observation %d has a repeated position", o);
+      at[pos] = o;
+    }
+    for (int p = 1; p < n; ++p) {
+      const int a = at[p - 1], b = at[p];
+      CHECK(S.cam_of[a] < S.cam_of[b] || (S.cam_of[a] == S.cam_of[b] && a < b),
+            "tile %d positions %d, %d are not in (camera, landmark) order", t, p - 1, p);
+    }
+    for (int sl = 0; sl < ns; ++sl) {
+      const int p = S.slot_beg[s0 + sl];
+      CHECK(p < n && S.cam_of[at[p]] == S.slot_cam[s0 + sl] &&
+                (p == 0 || S.cam_of[at[p - 1]] != S.slot_cam[s0 + sl]),
+            "tile %d slot %d does not start at its camera's first position", t, sl);
+    }
+  }
+
+  // camera-major rows: each camera's slots are contiguous rows, in tile order
+  CHECK(S.cam_slot_ptr[0] == 0 && S.cam_slot_ptr[nc] == S.n_slots, "camera rows do not cover slots");
+  std::vector<char> row_seen(S.n_slots, 0);
+  for (int s = 0; s < S.n_slots; ++s) {
+    const int r = S.slot_row[s];
+    CHECK(r >= 0 && r < S.n_slots && !row_seen[r], "slot_row is not a permutation at %d", s);
+    row_seen[r] = 1;
+    CHECK(S.cam_slot_list[r] == s, "cam_slot_list is not the inverse of slot_row at %d", r);
+    const int c = S.slot_cam[s];
+    CHECK(r >= S.cam_slot_ptr[c] && r < S.cam_slot_ptr[c + 1], "slot %d's row is not its camera's", s);
+  }
+  for (int c = 0; c < nc; ++c) {
+    CHECK(S.cam_slot_ptr[c + 1] - S.cam_slot_ptr[c] == slot_count_of_cam[c],
+          "camera %d has a wrong row count", c);
+    for (int r = S.cam_slot_ptr[c] + 1; r < S.cam_slot_ptr[c + 1]; ++r)
+      CHECK(S.cam_slot_list[r] > S.cam_slot_list[r - 1], "camera %d's rows are not in tile order", c);
+  }
+
+  // camera rounds for a grid of G blocks
+  CamSchedule cs;
+  build_cam_schedule(S, &cs);
+  for (int c = 0; c < nc; ++c) {
+    const int r0 = S.cam_slot_ptr[c], r1 = S.cam_slot_ptr[c + 1];
+    const int i0 = cs.cam_item[c], i1 = cs.cam_item[c + 1];
+    CHECK(i1 - i0 == cam_chunks(r1 - r0) && i1 - i0 <= kRoundItems, "camera %d's chunk count", c);
+    int q = r0;
+    for (int i = i0; i < i1; ++i) {
+      CHECK(cs.item_q[2 * i] == q && cs.item_q[2 * i + 1] >= q &&
+                cs.item_q[2 * i + 1] - q <= cam_chunk_rows(r1 - r0),
+            "camera %d's chunks do not tile its rows", c);
+      q = cs.item_q[2 * i + 1];
+    }
+    CHECK(q == r1, "camera %d's chunks end at %d, not %d", c, q, r1);
+  }
+  CamRoundList rl;
+  build_cam_rounds(cs, nc, G, &rl);
+  const int R = (int)rl.round_cam.size() - 1;
+  CHECK(rl.round_cam.front() == 0 && rl.round_cam.back() == nc, "rounds do not cover the cameras");
+  for (int r = 0; r < R; ++r) {
+    const int c0 = rl.round_cam[r], c1 = rl.round_cam[r + 1];
+    CHECK(c1 > c0, "round %d is empty", r);
+    CHECK(rl.round_item[r] == cs.cam_item[c0] && rl.round_item[r + 1] == cs.cam_item[c1],
+          "round %d's items are not its cameras'", r);
+    CHECK(c1 - c0 <= kRoundItems && rl.round_item[r + 1] - rl.round_item[r] <= kRoundItems,
+          "round %d holds %d cameras and %d items", r, c1 - c0,
+          rl.round_item[r + 1] - rl.round_item[r]);
+  }
+  CHECK((int)rl.block_round.size() == G + 1 && rl.block_round[0] == 0 && rl.block_round[G] == R,
+        "block_round does not split the rounds over the grid");
+  for (int b = 0; b < G; ++b)
+    CHECK(rl.block_round[b + 1] >= rl.block_round[b], "block_round decreases at %d", b);
+
+  std::printf("ok tiles=%d slots=%d rounds=%d\n", S.n_tiles, S.n_slots, R);
+  return 0;
+}
