@@ -72,7 +72,13 @@ CASES = {
 
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_schedule_properties(checker, tmp_path, name):
-    run(checker, tmp_path, [CASES[name]()])
+    """... and bench.py's mirror of the packer (the slot count behind its design bytes)
+    counts the library's slots."""
+    import bench
+    p = CASES[name]()
+    out = run(checker, tmp_path, [p])
+    slots = int(out.split("slots=")[1].split()[0])
+    assert bench.schedule_slots(p) == slots
 
 
 def test_schedule_with_a_256_camera_track(checker, tmp_path):
