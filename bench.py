@@ -65,6 +65,10 @@ def parse_args(argv=None):
                     help="skip the adjoint section (200 cameras, 20,000 landmarks, weighted)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-solver", choices=["power", "direct"], default="power",
+                    help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-sync-dir", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-sync-n", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run only this many untimed LM steps (for ncu captures)")
     ap.add_argument("--profile-precision", choices=["fp64", "fp32"], default="fp64")
@@ -820,41 +824,126 @@ def schedule_slots(p, tile_obs=256, tile_lms=256, tile_cams=128) -> int:
 
 
 # ---------------------------------------------------------------------------------------
-def cpu_baseline(args) -> dict:
-    """The FP64 oracle (as it stands) on the host cores: single-threaded LM iterations on the
-    same workload, run in a subprocess with BLAS / OpenMP threads pinned to 1."""
+ORACLE_ENV_1T = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+def run_oracle_workers(args, solver: str, seconds: float, n: int) -> list[dict]:
+    """Run n oracle LM workers (each single-threaded, in its own process) on the workload for
+    about `seconds` each, started together, and return their reports."""
     env = dict(os.environ)
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    for k in ORACLE_ENV_1T:
         env[k] = "1"
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker", "--workload",
-           args.workload, "--cpu-seconds", str(args.cpu_seconds)]
+    with tempfile.TemporaryDirectory(prefix="poba_oracle_") as sync:
+        cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker", "--workload",
+               args.workload, "--cpu-seconds", str(seconds), "--cpu-solver", solver,
+               "--cpu-sync-dir", sync, "--cpu-sync-n", str(n)]
+        procs = [subprocess.Popen(cmd, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                  text=True) for _ in range(n)]
+        reports = []
+        try:
+            for pr in procs:
+                out, err = pr.communicate(timeout=600 + 4 * seconds)
+                if pr.returncode != 0:
+                    raise RuntimeError(f"oracle worker exited {pr.returncode}: {err[-300:]}")
+                reports.append(json.loads(out.strip().splitlines()[-1]))
+        finally:
+            for pr in procs:
+                if pr.poll() is None:
+                    pr.kill()
+                    pr.wait()
+    return reports
+
+
+def host_cores() -> int:
     try:
-        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
-        d = json.loads(out.stdout.strip().splitlines()[-1])
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def host_free_bytes() -> int | None:
+    try:
+        return os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError, AttributeError):
+        return None
+
+
+def cpu_baseline(args) -> dict:
+    """The FP64 oracle (as it stands) on the host cores, on the same workload:
+      * the reported value: single-threaded LM iterations with the power-series solve
+        (BLAS / OpenMP threads pinned to 1, in a subprocess), with its peak RSS;
+      * `direct`: the same LM with the oracle's exact solve of the reduced system (explicit
+        block-sparse S, Schur-Jacobi PCG to 1e-12), single-threaded;
+      * `all_cores`: independent single-threaded power-series LM replicas, one per host core
+        (capped so their resident sets fit in half the free host memory), started together;
+        value = all replicas' iterations / the span from the first start to the last end."""
+    unit = "LM iterations/s"
+    try:
+        (d,) = run_oracle_workers(args, "power", args.cpu_seconds, 1)
     except Exception as e:  # report, do not hide
-        return {"value": None, "unit": "LM iterations/s", "cores": 1, "kind": "oracle",
+        return {"value": None, "unit": unit, "cores": 1, "kind": "oracle",
                 "sample": f"failed: {e}"}
-    return {"value": d["iters"] / d["seconds"], "unit": "LM iterations/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"{d['iters']} oracle LM iterations from x0 on the full {args.workload} problem "
-                      f"({d['seconds']:.1f} s; numpy/scipy, 1 thread)"}
+    line = {"value": d["iters"] / d["seconds"], "unit": unit, "cores": 1, "kind": "oracle",
+            "sample": f"{d['iters']} oracle LM iterations from x0 on the full {args.workload} "
+                      f"problem ({d['seconds']:.1f} s; numpy/scipy, 1 thread)",
+            "peak_rss_bytes": d["peak_rss_bytes"]}
+    side = max(args.cpu_seconds / 2, 0.1)
+    try:
+        (e,) = run_oracle_workers(args, "direct", side, 1)
+        line["direct"] = {
+            "value": e["iters"] / e["seconds"], "unit": unit, "cores": 1,
+            "solver": "explicit block-sparse S, Schur-Jacobi PCG to 1e-12",
+            "sample": f"{e['iters']} oracle LM iterations from x0 ({e['seconds']:.1f} s)",
+            "peak_rss_bytes": e["peak_rss_bytes"]}
+    except Exception as ex:
+        line["direct"] = {"value": None, "unit": unit, "sample": f"failed: {ex}"}
+    cores = host_cores()
+    free = host_free_bytes()
+    n = cores
+    if free is not None:
+        n = max(1, min(cores, int(0.5 * free // max(d["peak_rss_bytes"], 1))))
+    try:
+        reps = run_oracle_workers(args, "power", side, n)
+        span = max(r["end"] for r in reps) - min(r["start"] for r in reps)
+        iters = sum(r["iters"] for r in reps)
+        line["all_cores"] = {
+            "value": iters / span, "unit": unit, "cores": n, "host_cores": cores,
+            "sample": f"{n} independent single-threaded oracle LM replicas, {iters} iterations "
+                      f"in {span:.1f} s",
+            "peak_rss_bytes_per_replica": max(r["peak_rss_bytes"] for r in reps)}
+    except Exception as ex:
+        line["all_cores"] = {"value": None, "unit": unit, "sample": f"failed: {ex}"}
+    return line
 
 
 def cpu_baseline_worker(args):
+    import resource
     from oracle import lm as olm
     p = bal_synth.preset(args.workload)
+    if args.cpu_sync_dir:
+        # start together: announce readiness, then wait (bounded) for the others
+        open(os.path.join(args.cpu_sync_dir, f"ready.{os.getpid()}"), "w").close()
+        t_wait = time.monotonic()
+        while (len(os.listdir(args.cpu_sync_dir)) < args.cpu_sync_n
+               and time.monotonic() - t_wait < 300):
+            time.sleep(0.01)
+    start = time.time()
     t0 = time.perf_counter()
     n = 0
     # one LM iteration at a time, until the time budget is used (at least one iteration)
     cams, lms = p.cams0, p.lms0
     lam, nu = 1e-4, 2.0
     while True:
-        cams, lms, hist = olm.lm_solve(p, olm.Options(max_lm=1, lambda0=lam), cams=cams, lms=lms)
+        cams, lms, hist = olm.lm_solve(p, olm.Options(max_lm=1, lambda0=lam),
+                                       solver=args.cpu_solver, cams=cams, lms=lms)
         lam, nu = olm.lambda_update(lam, nu, hist[-1]["accepted"], hist[-1]["rho"])
         n += 1
         if time.perf_counter() - t0 > args.cpu_seconds:
             break
-    print(json.dumps({"iters": n, "seconds": time.perf_counter() - t0}))
+    seconds = time.perf_counter() - t0
+    rss = resource.getrusage(resource.RUSAGE_SELF).ru_maxrss * 1024  # KiB on Linux
+    print(json.dumps({"iters": n, "seconds": seconds, "start": start, "end": start + seconds,
+                      "peak_rss_bytes": rss}))
 
 
 def run_reference(args):
