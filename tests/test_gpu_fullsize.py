@@ -43,21 +43,21 @@ def test_sampled_linearization_and_blocks(poba, problem):
     rng = np.random.default_rng(0)
     obs_s = rng.choice(p.n_obs, 3000, replace=False)
     ro, Jpo, Jlo = cm.linearize(p.cams0, p.lms0, p.obs[obs_s], p.cam_idx[obs_s], p.lm_idx[obs_s])
-    assert np.abs(r[obs_s] - ro).max() <= 1e-11 * max(1.0, np.abs(ro).max())
-    assert np.abs(Jp[obs_s] - Jpo).max() <= 1e-11 * np.abs(Jpo).max()
-    assert np.abs(Jl[obs_s] - Jlo).max() <= 1e-11 * np.abs(Jlo).max()
+    assert np.abs(r[obs_s] - ro).max() <= 1e-12 * max(1.0, np.abs(ro).max())
+    assert np.abs(Jp[obs_s] - Jpo).max() <= 1e-12 * np.abs(Jpo).max()
+    assert np.abs(Jl[obs_s] - Jlo).max() <= 1e-12 * np.abs(Jlo).max()
     for c in rng.choice(p.n_cams, 8, replace=False):
         sel = np.nonzero(p.cam_idx == c)[0]
         rc, Jpc, _ = cm.linearize(p.cams0, p.lms0, p.obs[sel], p.cam_idx[sel], p.lm_idx[sel])
         Uc = np.einsum("oij,oik->jk", Jpc, Jpc)
         bc = np.einsum("oij,oi->j", Jpc, rc)
-        assert np.abs(U[c] - Uc).max() <= 1e-11 * np.abs(Uc).max()
+        assert np.abs(U[c] - Uc).max() <= 1e-12 * np.abs(Uc).max()
         assert np.abs(bp[9 * c:9 * c + 9] - bc).max() <= 1e-10 * max(np.abs(bc).max(), 1e-300)
     for l in rng.choice(p.n_lms, 64, replace=False):
         sel = np.nonzero(p.lm_idx == l)[0]
         rl, _, Jll = cm.linearize(p.cams0, p.lms0, p.obs[sel], p.cam_idx[sel], p.lm_idx[sel])
         Vl = np.einsum("oij,oik->jk", Jll, Jll)
-        assert np.abs(V[l] - Vl).max() <= 1e-11 * np.abs(Vl).max()
+        assert np.abs(V[l] - Vl).max() <= 1e-12 * np.abs(Vl).max()
         bll = np.einsum("oij,oi->j", Jll, rl)
         assert np.abs(bl[3 * l:3 * l + 3] - bll).max() <= 1e-10 * max(np.abs(bll).max(), 1e-12)
 

@@ -1,7 +1,9 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on the same seeded
 problems.  Tolerances: FP64 mode -- series / step relative difference <= 1e-10 at equal
-(lambda, m), Jacobians and blocks <= 1e-11 relative; FP32-bulk mode -- series relative difference
-<= 1e-4; LM final cost within 1e-6 relative."""
+(lambda, m), residuals, Jacobians and blocks <= 1e-12 relative (measured <= 1e-14: FP64 rounding
+of the projection and its chain rule, with r = pi - obs cancelling against pixel-sized
+observations); FP32-bulk mode -- series relative difference <= 1e-4; LM final cost within 1e-6
+relative."""
 import numpy as np
 import pytest
 
@@ -12,6 +14,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_SERIES_TOL = 1e-10
 FP32_SERIES_TOL = 1e-4
+LIN_TOL = 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -52,9 +55,9 @@ def test_linearization_fp64(poba, case):
     h = make(poba, p)
     cost = poba.ba_linearize(h)
     r, Jp, Jl = poba.ba_get_linearization(h)
-    assert rel(r, ref.r) < 1e-11
-    assert np.abs(Jp - ref.Jp).max() / np.abs(ref.Jp).max() < 1e-11
-    assert np.abs(Jl - ref.Jl).max() / np.abs(ref.Jl).max() < 1e-11
+    assert rel(r, ref.r) < LIN_TOL
+    assert np.abs(Jp - ref.Jp).max() / np.abs(ref.Jp).max() < LIN_TOL
+    assert np.abs(Jl - ref.Jl).max() / np.abs(ref.Jl).max() < LIN_TOL
     assert abs(cost - 0.5 * np.sum(ref.r ** 2)) / cost < 1e-12
 
 
@@ -63,10 +66,10 @@ def test_blocks_fp64(poba, case):
     h = make(poba, p)
     poba.ba_linearize(h)
     U, V, bp, bl = poba.ba_get_blocks(h)
-    assert np.abs(U - ref.ne.U).max() / np.abs(ref.ne.U).max() < 1e-11
-    assert np.abs(V - ref.ne.V).max() / np.abs(ref.ne.V).max() < 1e-11
-    assert rel(bp, ref.ne.b_p) < 1e-11
-    assert rel(bl, ref.ne.b_l) < 1e-11
+    assert np.abs(U - ref.ne.U).max() / np.abs(ref.ne.U).max() < LIN_TOL
+    assert np.abs(V - ref.ne.V).max() / np.abs(ref.ne.V).max() < LIN_TOL
+    assert rel(bp, ref.ne.b_p) < LIN_TOL
+    assert rel(bl, ref.ne.b_l) < LIN_TOL
 
 
 @pytest.mark.parametrize("lam,m", [(1e-4, 20), (1e-2, 5), (1.0, 0), (1e-3, 1)])
