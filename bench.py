@@ -184,6 +184,16 @@ def profiled_traffic(precision: str, form: int, workload: str = WORKLOAD):
     return e.get("dram_bytes_per_term")
 
 
+def step_stats(ms) -> dict:
+    """Median and spread of the per-step CUDA-event times (steps differ: a rejected step skips
+    the linearisation, and the series stops after a varying number of terms)."""
+    a = np.asarray(ms, dtype=np.float64)
+    if a.size == 0:
+        return {"median": None, "p10": None, "p90": None, "n": 0}
+    return {"median": float(np.median(a)), "p10": float(np.percentile(a, 10)),
+            "p90": float(np.percentile(a, 90)), "n": int(a.size)}
+
+
 def oracle_direct_final(workload: str, p, f0_gpu: float):
     """Final cost of the oracle's LM with the exact reduced solve, run to convergence from x0
     (stored by tests/golden/make_lm_direct_reference.py), if it was made for this problem: the
@@ -497,6 +507,7 @@ def run_poba(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": r64["total_ms"] / args.steps,
+        "step_ms": step_stats(r64["ms"]),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -526,7 +537,8 @@ def run_poba(args):
         "series_form": r64["tuned"],
         "fp32_bulk": {"value": whole_job_rate(args.steps, world, r32["total_ms"] / 1e3),
                       "unit": "LM iterations/s",
-                      "ms_per_step": r32["total_ms"] / args.steps, "roofline": roof32,
+                      "ms_per_step": r32["total_ms"] / args.steps,
+                      "step_ms": step_stats(r32["ms"]), "roofline": roof32,
                       "gpu_launches": int(r32["launches"]), "solves_per_s": r32["solves_per_s"],
                       "solve_inner_mean": r32["solve_inner_mean"],
                       "time_to_1pct_cost_s": traj["fp32_bulk"]["time_to_tau_s"],

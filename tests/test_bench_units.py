@@ -75,3 +75,9 @@ def test_minimal_series_units_per_observation():
     b4, _ = bench.series_term_units(p, 4)
     assert b8 - b4 == p.n_obs * 24 * 4 + p.n_lms * 6 * 4
     assert f == 96 * p.n_obs + 18 * p.n_lms + 162 * p.n_cams
+
+
+def test_step_stats():
+    s = bench.step_stats([3.0, 1.0, 2.0, 10.0, 2.0])
+    assert s["median"] == 2.0 and s["n"] == 5 and s["p10"] <= s["median"] <= s["p90"] <= 10.0
+    assert bench.step_stats([])["median"] is None
