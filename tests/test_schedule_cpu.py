@@ -106,3 +106,15 @@ def test_batch_schedule_properties(checker, tmp_path):
                                        track=("uniform", 2, 8), visibility="clustered",
                                        seed=int(rng.integers(1 << 30))) for _ in range(8)]
     run(checker, tmp_path, problems, grid=152)
+
+
+@pytest.mark.parametrize("workload", ["clustered_1200c_160000l", "powerlaw_10000c_1000000l"])
+def test_full_size_schedules(checker, tmp_path, workload):
+    """The two full-size single problems the benchmark times, at the grids of the persistent
+    kernel (3 and 4 blocks per SM on 152 SMs); bench.py's slot mirror counts the same slots."""
+    import bench
+    p = bal_synth.preset(workload)
+    for grid in (456, 608):
+        out = run(checker, tmp_path, [p], grid=grid)
+        slots = int(out.split("slots=")[1].split()[0])
+    assert bench.schedule_slots(p) == slots
