@@ -47,11 +47,6 @@ def block_diagonal(M, n_blocks, d):
     return out
 
 
-def block_diag_sparse(blocks):
-    n, d, _ = blocks.shape
-    return sp.block_diag(list(blocks), format="csr") if n < 64 else _bd_fast(blocks)
-
-
 def _bd_fast(blocks):
     n, d, _ = blocks.shape
     b = np.arange(n)[:, None, None]

@@ -127,3 +127,20 @@ def test_model_decrease_closed_form():
     b = J.T @ r.ravel()
     ref = -(b @ dx) - 0.5 * dx @ (J.T @ J) @ dx
     np.testing.assert_allclose(neq.model_decrease(ne, dxp, dxl), ref, rtol=1e-8)
+
+
+def test_solve_reduced_takes_pcg_above_the_dense_limit():
+    """Above 9 n_c = DENSE_LIMIT the exact reduced solve switches from dense Cholesky to PCG on
+    the explicit block-sparse S; its dx_p solves S dx_p = -b~ like the dense route."""
+    p = bal_synth.make_problem(240, 3000, track=("uniform", 3, 5), visibility="clustered", seed=23)
+    assert 9 * p.n_cams > direct.DENSE_LIMIT
+    r, Jp, Jl = cm.linearize(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx)
+    ne = neq.NormalEquation(r, Jp, Jl, p.cam_idx, p.lm_idx, p.n_cams, p.n_lms)
+    Ul, Vl = ne.damped(1e-3)
+    Vi = neq.chol_inverse(Vl)
+    bt = neq.schur_rhs(ne, Vi)
+    dx = direct.solve_reduced(ne, Ul, Vi, bt)
+    S = neq.explicit_schur(ne, Ul, Vi, dense=True)
+    x_dense = direct.solve_dense(S, bt)
+    assert np.linalg.norm(S @ dx + bt) / np.linalg.norm(bt) < 1e-11
+    assert np.linalg.norm(dx - x_dense) / np.linalg.norm(x_dense) < 1e-8
