@@ -33,11 +33,11 @@ def test_rotation_preserves_norm_and_inverts():
     RX = np.stack(RX, 1)
     np.testing.assert_allclose(np.linalg.norm(RX, axis=1), np.linalg.norm(X, axis=1), rtol=1e-13)
     back = np.stack(cm.rotate([-w[:, i] for i in range(3)], [RX[:, i] for i in range(3)]), 1)
-    np.testing.assert_allclose(back, X, atol=1e-12)
+    np.testing.assert_allclose(back, X, rtol=0, atol=1e-12)
     # rotation by theta about z is the planar rotation of (x, y)
     th = 0.7
     r = np.stack(cm.rotate([np.zeros(1), np.zeros(1), np.full(1, th)], [np.ones(1), np.full(1, 2.0), np.full(1, -3.0)]), 1)[0]
-    np.testing.assert_allclose(r, [np.cos(th) - 2 * np.sin(th), np.sin(th) + 2 * np.cos(th), -3.0], atol=1e-14)
+    np.testing.assert_allclose(r, [np.cos(th) - 2 * np.sin(th), np.sin(th) + 2 * np.cos(th), -3.0], rtol=0, atol=1e-14)
 
 
 def test_small_angle_branch_is_continuous():
@@ -48,7 +48,7 @@ def test_small_angle_branch_is_continuous():
         w = [np.array([th]), np.array([0.0]), np.array([0.0])]
         RX = np.array([v[0] for v in cm.rotate(w, X)])
         exact = np.array([1.0, -2.0 * np.cos(th) + 7.0 * np.sin(th), -2.0 * np.sin(th) - 7.0 * np.cos(th)])
-        np.testing.assert_allclose(RX, exact, atol=1e-14)
+        np.testing.assert_allclose(RX, exact, rtol=0, atol=1e-14)
 
 
 def test_jacobians_match_central_differences():
@@ -102,7 +102,7 @@ def test_generator_noise_is_the_residual_at_ground_truth():
     # oracle's residual at the ground truth must give back exactly the injected noise.
     p = bal_synth.make_problem(12, 300, seed=3)
     rg = cm.residuals(p.cams_gt, p.lms_gt, p.obs, p.cam_idx, p.lm_idx)
-    np.testing.assert_allclose(rg, -p.noise, atol=1e-9)
+    np.testing.assert_allclose(rg, -p.noise, rtol=0, atol=1e-9)
 
 
 def test_weighted_cost():

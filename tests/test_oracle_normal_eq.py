@@ -54,9 +54,9 @@ def test_blocks_equal_dense_normal_matrix():
 def test_damping_modes():
     A = np.array([[[4.0, 1.0], [1.0, 0.0]]])
     D0 = neq.damp(A, 0.5, 0)
-    np.testing.assert_allclose(D0[0], [[4.0 + 2.0, 1.0], [1.0, 0.5 * neq.DAMP_MIN]])
+    np.testing.assert_allclose(D0[0], [[4.0 + 2.0, 1.0], [1.0, 0.5 * neq.DAMP_MIN]], rtol=1e-15, atol=0)
     D1 = neq.damp(A, 0.5, 1)
-    np.testing.assert_allclose(D1[0], [[4.5, 1.0], [1.0, 0.5]])
+    np.testing.assert_allclose(D1[0], [[4.5, 1.0], [1.0, 0.5]], rtol=0, atol=0)
 
 
 def test_block_cholesky_inverse():
@@ -65,9 +65,9 @@ def test_block_cholesky_inverse():
     Ul, Vl = ne.damped(1e-4)
     Ui, Vi = neq.chol_inverse(Ul), neq.chol_inverse(Vl)
     for c in range(p.n_cams):
-        np.testing.assert_allclose(Ui[c] @ Ul[c], np.eye(9), atol=1e-9)
+        np.testing.assert_allclose(Ui[c] @ Ul[c], np.eye(9), rtol=0, atol=1e-9)
     for l in range(p.n_lms):
-        np.testing.assert_allclose(Vi[l] @ Vl[l], np.eye(3), atol=1e-10)
+        np.testing.assert_allclose(Vi[l] @ Vl[l], np.eye(3), rtol=0, atol=1e-10)
     # an undamped zero block is not positive definite
     with pytest.raises(np.linalg.LinAlgError):
         neq.chol_inverse(np.zeros((1, 3, 3)))
@@ -97,7 +97,7 @@ def test_schur_route_equals_full_dense_solve(lam, mode):
     S_ref = H[:npp, :npp] - H[:npp, npp:] @ np.linalg.solve(H[npp:, npp:], H[npp:, :npp])
     np.testing.assert_allclose(S, S_ref, rtol=1e-9, atol=1e-6 * np.abs(S_ref).max())
     # S is symmetric positive definite (Sec. 4.1, lambda > 0)
-    np.testing.assert_allclose(S, S.T, atol=1e-9 * np.abs(S).max())
+    np.testing.assert_allclose(S, S.T, rtol=0, atol=1e-9 * np.abs(S).max())
     assert np.linalg.eigvalsh(S).min() > 0
 
 

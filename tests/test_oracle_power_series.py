@@ -42,7 +42,7 @@ def test_lemma1_eigenvalues_in_unit_interval(lam):
 
 def test_factorisation_S_equals_U_times_I_minus_P():
     _, _, _, _, Ud, P, S, _ = _setup()
-    np.testing.assert_allclose(Ud @ (np.eye(P.shape[0]) - P), S, atol=1e-8 * np.abs(S).max())
+    np.testing.assert_allclose(Ud @ (np.eye(P.shape[0]) - P), S, rtol=0, atol=1e-8 * np.abs(S).max())
 
 
 @pytest.mark.parametrize("m", [0, 1, 2, 5, 12])
@@ -102,6 +102,9 @@ def test_stop_index_matches_dense_partial_sums():
                 break
         assert m == expect, (eps, m, expect)
         assert np.linalg.norm(x - xs[expect]) / np.linalg.norm(xs[expect]) < 1e-12
+        # the returned stop value is the left-hand side of eq. `qcriterion` at the stop index
+        sv_ref = (expect + 1) * np.linalg.norm(xs[expect] - xs[expect - 1]) / np.linalg.norm(xs[expect])
+        assert abs(sv - sv_ref) <= 1e-9 * sv_ref, (eps, sv, sv_ref)
 
 
 def test_stop_rule_scripted_sequences():
@@ -111,6 +114,8 @@ def test_stop_rule_scripted_sequences():
     assert ps.run_stop_rule([9, 0.004, 1, 1, 1, 1], x, 0.01, 20) == 1      # 2 * 0.004 = 0.008
     assert ps.run_stop_rule([9, 0.005, 1, 1, 1, 1], x, 0.01, 5) == 5       # 0.010 is not < 0.01
     assert ps.run_stop_rule([9, 1, 1, 1, 1, 1], [1, 1, 0.0, 1, 1, 1], 0.01, 5) == 2  # ||x|| = 0
+    # the test starts at i = 1: a small ratio at i = 0 (1 * 0.001) does not stop the series
+    assert ps.run_stop_rule([0.001, 1, 0.001, 1, 1, 1], x, 0.01, 20) == 2  # 2.0, 0.003
     assert ps.stop_test(3, 0.0024, 1.0, 0.01)                                # 4 * 0.0024 = 0.0096
     assert not ps.stop_test(3, 0.0025, 1.0, 0.01)                            # 0.0100
 
