@@ -115,3 +115,20 @@ def test_weighted_cost():
     sw = np.sqrt(p.weights)
     np.testing.assert_allclose(rw, r1 * sw[:, None], rtol=1e-14)
     np.testing.assert_allclose(Jpw, Jp1 * sw[:, None, None], rtol=1e-14)
+
+
+def test_rotation_matches_the_matrix_exponential():
+    """R(w) = exp([w]_x): Rodrigues' formula (and the first-order branch below THETA2_SMALL)
+    agrees with scipy's matrix exponential of the skew matrix at angles from 1e-9 to 3 rad, so
+    the small-angle branch cannot be taken where its error would show."""
+    import scipy.linalg as sla
+    rng = np.random.default_rng(9)
+    for th in (1e-9, 1e-7, 1e-5, 1e-3, 0.1, 1.0, 3.0):
+        k = rng.normal(size=3)
+        k /= np.linalg.norm(k)
+        w = th * k
+        X = rng.normal(0, 5.0, size=3)
+        K = np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+        ref = sla.expm(K) @ X
+        RX = np.array([v[0] for v in cm.rotate([np.array([wi]) for wi in w], [np.array([xi]) for xi in X])])
+        np.testing.assert_allclose(RX, ref, rtol=0, atol=1e-14 * np.linalg.norm(X), err_msg=f"theta={th}")
