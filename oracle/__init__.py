@@ -17,11 +17,18 @@ Layout (each function cites the passage it restates):
                     the stop rule (eq. `qcriterion`), plus the operator P = U^-1 W V^-1 W^T
   direct         -- exact solves of S dx_p = -b~: dense Cholesky, Schur-Jacobi PCG
   lm             -- Levenberg-Marquardt outer loop with the settings of Sec. 5.1 ("LM loop")
+  pcg            -- conjugate gradients on the reduced system, matrix-free, with the Schur-Jacobi
+                    (Sec. 5) or the truncated power-series (eq. `S_approx`) preconditioner
+  adjoint        -- implicit-differentiation adjoint of the solution (no paper counterpart):
+                    H_lam a = dL/dx through the Schur complement, gradients w.r.t. observations
+                    and weights
 
 Parity status: every function above is pinned by ``tests/test_oracle_*.py`` against closed
-forms, finite differences, brute-force dense solves, Lemma 1 / Prop. 1 / Prop. 2 identities or
-scripted sequences.  The one exception is the LM trajectory itself (the lambda-update rule is
+forms, finite differences, brute-force dense solves, Lemma 1 / Prop. 1 / Prop. 2 identities,
+library routines (matrix exponential, dense Cholesky) or scripted sequences, and
+``tests/test_oracle_planted_mistakes.py`` checks that one-line mistakes planted in each function
+make those pins fail.  The one exception is the LM trajectory itself (the lambda-update rule is
 not printed in the paper): "parity unpinned" against the paper, pinned only by invariants
 (cost never increases on accepted steps, convergence to the noise floor).
 """
-from . import camera_model, normal_eq, power_series, direct, lm  # noqa: F401
+from . import camera_model, normal_eq, power_series, direct, lm, pcg, adjoint  # noqa: F401
