@@ -26,8 +26,8 @@ Layout (each function cites the passage it restates):
 Parity status: every function above is pinned by ``tests/test_oracle_*.py`` against closed
 forms, finite differences, brute-force dense solves, Lemma 1 / Prop. 1 / Prop. 2 identities,
 library routines (matrix exponential, dense Cholesky) or scripted sequences, and
-``tests/test_oracle_planted_mistakes.py`` checks that one-line mistakes planted in each function
-make those pins fail.  The one exception is the LM trajectory itself (the lambda-update rule is
+``tests/test_oracle_planted_mistakes.py`` checks that one-line mistakes planted in every function
+that computes a step of the method make those pins fail.  The one exception is the LM trajectory itself (the lambda-update rule is
 not printed in the paper): "parity unpinned" against the paper, pinned only by invariants
 (cost never increases on accepted steps, convergence to the noise floor).
 """

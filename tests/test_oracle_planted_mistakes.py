@@ -108,6 +108,10 @@ CASES = [
     Case("cross_product_index", o_cm, "_cross", "a[2] * b[0] - a[0] * b[2]", "a[2] * b[0] - a[0] * b[1]",
          (ROTATION, GOLDEN)),
     Case("dual_cos_derivative_sign", o_cm, "_cos", "-x.d * np.sin(x.v)", "x.d * np.sin(x.v)", (FD_JAC,)),
+    Case("dual_sin_derivative", o_cm, "_sin", "x.d * np.cos(x.v)", "x.d * np.sin(x.v)", (FD_JAC,)),
+    Case("dual_sqrt_derivative_half_dropped", o_cm, "_sqrt", "(0.5 / s)", "(1.0 / s)", (FD_JAC,)),
+    Case("dual_select_derivative_from_other_branch", o_cm, "_where",
+         "np.where(mask[..., None], ad, bd)", "np.where(mask[..., None], bd, ad)", (FD_JAC,)),
     Case("dual_product_rule_term_dropped", o_cm, "Dual",
          "self.d * ov[..., None] + od * self.v[..., None]", "self.d * ov[..., None]", (FD_JAC,)),
     Case("dual_quotient_rule_sign", o_cm, "Dual",
@@ -141,6 +145,8 @@ CASES = [
     Case("damping_lambda_dropped", o_neq, "damp", "out[:, idx, idx] += lam * diag", "out[:, idx, idx] += diag",
          (DAMPING, SCHUR_ROUTE)),
     Case("damping_mode_ignored", o_neq, "damp", "if damping_mode == 0:", "if True:", (DAMPING, SCHUR_ROUTE_M1)),
+    Case("landmark_blocks_undamped", o_neq, "NormalEquation",
+         "damp(self.V, lam, damping_mode)", "damp(self.V, 0.0, damping_mode)", (SCHUR_ROUTE,)),
     Case("cholesky_inverse_factor_order", o_neq, "chol_inverse",
          '"nji,njk->nik"', '"nij,nkj->nik"', (CHOL,)),
     Case("cholesky_inverse_transpose_dropped", o_neq, "chol_inverse",
@@ -188,6 +194,7 @@ CASES = [
     Case("schur_jacobi_from_U_blocks", o_pcg, "schur_jacobi_blocks",
          "S = explicit_schur(ne, Ulam, Vinv, dense=False)\n    return block_diagonal(S, ne.n_cams, 9)",
          "return Ulam.copy()", (SJ_EXACT,)),
+    Case("pcg_solve_rhs_sign", o_pcg, "pcg_solve", "t), -bt, apply_Minv", "t), bt, apply_Minv", (PCG_EXACT,)),
     Case("power_preconditioner_without_U_inverse_term", o_pcg, "power_series_preconditioner",
          "        z = t.copy()\n", "        z = 0 * t\n", (PCG_ORDER0,)),
     Case("power_preconditioner_one_term_short", o_pcg, "power_series_preconditioner",
@@ -210,6 +217,8 @@ CASES = [
     Case("adjoint_rhs_sign", o_adj, "adjoint_solve", "rhs = g_p - ne.W @", "rhs = g_p + ne.W @", (ADJ_OBS,)),
     Case("adjoint_landmark_back_substitution_sign", o_adj, "adjoint_solve",
          "g_l - ne.W.T @ a_p", "g_l + ne.W.T @ a_p", (ADJ_OBS,)),
+    Case("adjoint_weights_not_passed", o_adj, "gradients",
+         "observation_gradients(r, Jp, Jl, p.weights,", "observation_gradients(r, Jp, Jl, None,", (ADJ_OBS,)),
     Case("adjoint_damping_mode_flipped", o_adj, "adjoint_solve",
          "ne.damped(lam, damping_mode)", "ne.damped(lam, 1 - damping_mode)", (ADJ_OBS, ADJ_W)),
     Case("adjoint_landmark_part_dropped", o_adj, "observation_gradients",
