@@ -45,6 +45,19 @@ FP64_PEAK_TFLOPS_DERIVED = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk/SM 
 FALLBACK_HBM_GBS = 6800.0
 
 
+# the BAL problem each seeded synthetic workload stands in for (sizes only; no BAL data is read)
+STANDS_IN_FOR = {
+    "clustered_1200c_160000l": "BAL Ladybug-1197",
+    "powerlaw_10000c_1000000l": "BAL Venice-1778",
+}
+
+
+def data_note(workload: str) -> str:
+    what = STANDS_IN_FOR.get(workload)
+    tail = f"stands in for {what}" if what else "no BAL counterpart"
+    return f"synthetic (seeded BAL-model problem; {tail})"
+
+
 # ---------------------------------------------------------------------------------------
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
@@ -512,7 +525,7 @@ def run_poba(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
-        "data": "synthetic (seeded BAL-model problem; stands in for BAL Ladybug-1197)",
+        "data": data_note(args.workload),
         "config": {"workload": args.workload, "n_cams": p.n_cams, "n_lms": p.n_lms,
                    "n_obs": p.n_obs, "visibility": "clustered window 8, tracks U{3,4}",
                    "series": {"eps": 0.01, "max_inner": 20}, "lm": {"lambda0": 1e-4,
@@ -1012,7 +1025,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "LM iterations/s",
         "n_gpus": world, "steps": n, "warmup": warm, "ms_per_step": 1e3 * dt / n,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded BAL-model problem; stands in for BAL Ladybug-1197)",
+        "data": data_note(args.workload),
         "config": {"workload": args.workload, "n_cams": p.n_cams, "n_lms": p.n_lms, "n_obs": p.n_obs},
         "cpu_baseline": {"value": v, "unit": "LM iterations/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
