@@ -103,3 +103,26 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.ba_linearize(None, None) == 1
     assert lib.ba_lm_step(None, None) == 1
     assert lib.ba_destroy(None) == 0
+
+
+def test_noalloc_cost_rejects_bad_arguments_before_any_cuda_call(lib):
+    """ba_cost_noalloc checks sizes, its scratch limit, NULL pointers and the 16-byte alignment
+    of obs on the host, before it asks CUDA for anything; the pointers here are never read."""
+    import ctypes as C
+    from paper_2204_12834_gb300 import BA_NOALLOC_MAX_CAMS
+    fake = C.c_void_p(0x10000)            # aligned, never dereferenced
+    odd = C.c_void_p(0x10008)             # 8 mod 16
+    cases = [
+        ((0, 1, 0, fake, fake, fake, fake, fake, None, fake), "n_cams >= 1"),
+        ((1, 0, 0, fake, fake, fake, fake, fake, None, fake), "n_lms >= 1"),
+        ((1, 1, -1, fake, fake, fake, fake, fake, None, fake), "n_obs >= 0"),
+        ((BA_NOALLOC_MAX_CAMS + 1, 1, 0, fake, fake, fake, fake, fake, None, fake),
+         str(BA_NOALLOC_MAX_CAMS)),
+        ((1, 1, 0, None, fake, fake, fake, fake, None, fake), "NULL"),
+        ((1, 1, 0, fake, fake, fake, fake, fake, None, None), "NULL"),
+        ((1, 1, 4, fake, fake, None, fake, fake, None, fake), "NULL observation"),
+        ((1, 1, 4, fake, fake, odd, fake, fake, None, fake), "16-byte aligned"),
+    ]
+    for args, words in cases:
+        assert lib.ba_cost_noalloc(*args, None) == 1, args  # BA_ERR_INVALID_ARG
+        assert words in lib.ba_last_error().decode(), (args, lib.ba_last_error())
