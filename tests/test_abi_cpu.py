@@ -126,3 +126,31 @@ def test_noalloc_cost_rejects_bad_arguments_before_any_cuda_call(lib):
     for args, words in cases:
         assert lib.ba_cost_noalloc(*args, None) == 1, args  # BA_ERR_INVALID_ARG
         assert words in lib.ba_last_error().decode(), (args, lib.ba_last_error())
+
+
+def test_create_batch_rejects_bad_problems_before_touching_the_gpu(lib):
+    """ba_create_batch validates every problem on the host: an empty batch, mixed precisions
+    and a bad index in one problem are rejected, the last naming the problem."""
+    import ctypes as C
+    import paper_2204_12834_gb300 as poba
+    from paper_2204_12834_gb300._lib import ProblemDesc
+    ok = _desc(seed=1)
+    bad = list(_desc(seed=2))
+    bad[3] = bad[3].copy()
+    bad[3][4] = 3  # camera index == n_cams
+    with pytest.raises(poba.PobaError) as e:
+        poba.ba_create_batch([ok, tuple(bad)])
+    assert e.value.status_name == "BA_ERR_INVALID_ARG"
+    assert "problem 1: cam_idx[4] out of range" in str(e.value)
+
+    keep = []
+    descs = (ProblemDesc * 2)()
+    for i, (pr, prec) in enumerate(((ok, poba.BA_FP64), (_desc(seed=3), poba.BA_FP32_BULK))):
+        poba._fill_desc(descs[i], *pr, None, prec, None, keep)
+    out = C.c_void_p()
+    opts = poba.ba_default_options()
+    assert lib.ba_create_batch(descs, 2, C.byref(opts), C.byref(out)) == 1
+    assert "same precision" in lib.ba_last_error().decode()
+    assert not out.value
+    assert lib.ba_create_batch(descs, 0, C.byref(opts), C.byref(out)) == 1
+    assert "n_problems must be >= 1" in lib.ba_last_error().decode()
