@@ -105,3 +105,36 @@ def test_gradient_vanishes_at_convergence():
         return np.linalg.norm(np.concatenate([ne.b_p, ne.b_l]))
 
     assert grad_norm(cams, lms) < 1e-9 * grad_norm(p.cams0, p.lms0)
+
+
+def test_failed_factorisations_raise_lambda_like_rejections(monkeypatch):
+    """A failed Cholesky factorisation (made here on the host: the first three solves raise
+    LinAlgError) gives an iteration without a step, handled like a rejected step: the state is
+    unchanged and lambda grows by nu = 2, 4, 8 (not by an accept rule), then the solve goes on."""
+    p = bal_synth.make_problem(6, 120, track=("uniform", 2, 5), seed=45)
+    real = lm.solve_step
+    calls = []
+
+    def failing(*args, **kw):
+        calls.append(1)
+        if len(calls) <= 3:
+            raise np.linalg.LinAlgError("planted: not positive definite")
+        return real(*args, **kw)
+
+    monkeypatch.setattr(lm, "solve_step", failing)
+    _, _, hist = lm.lm_solve(p, lm.Options(max_lm=5), solver="direct")
+    assert [h["not_spd"] for h in hist[:4]] == [True, True, True, False]
+    assert [h["lam"] for h in hist[:4]] == [1e-4, 2e-4, 8e-4, 6.4e-3]
+    assert all(h["cost_before"] == hist[0]["cost_before"] for h in hist[:4])
+    assert hist[3]["accepted"]
+
+
+def test_power_solver_passes_eps_to_the_series():
+    """The LM loop hands its eps to the series (eq. `qcriterion`): every iteration either stops
+    at a stop value below eps or runs max_inner terms, and with eps = 0.5 the first iteration,
+    far from the solution, stops after a few terms."""
+    p = bal_synth.make_problem(8, 200, track=("uniform", 2, 5), seed=41)
+    _, _, hist = lm.lm_solve(p, lm.Options(max_lm=4, eps=0.5, max_inner=20), solver="power")
+    for h in hist:
+        assert h["inner"] == 20 or h["stop_value"] < 0.5, h
+    assert 1 <= hist[0]["inner"] < 20

@@ -48,6 +48,18 @@ def _pin(fn, *args):
     return run
 
 
+def _pin_mp(fn):
+    """A pin that takes pytest's monkeypatch fixture: run it with its own MonkeyPatch."""
+    def run():
+        mp = pytest.MonkeyPatch()
+        try:
+            fn(mp)
+        finally:
+            mp.undo()
+    run.__name__ = fn.__name__
+    return run
+
+
 # pins by part
 GOLDEN = _pin(pin_cm.test_golden_projections)
 ROTATION = _pin(pin_cm.test_rotation_preserves_norm_and_inverts)
@@ -73,6 +85,8 @@ LM_FLOOR = _pin(pin_lm.test_lm_decreases_cost_and_reaches_noise_floor, "direct")
 FUNC_TOL = _pin(pin_lm.test_func_tol_stops_early)
 LM_REJECT = _pin(pin_lm.test_cost_increasing_trial_steps_are_rejected)
 LM_GRAD = _pin(pin_lm.test_gradient_vanishes_at_convergence)
+LM_NOT_SPD = _pin_mp(pin_lm.test_failed_factorisations_raise_lambda_like_rejections)
+LM_EPS = _pin(pin_lm.test_power_solver_passes_eps_to_the_series)
 PCG_EXACT = _pin(pin_pcg.test_pcg_converges_to_the_exact_reduced_solve, "jacobi", 0)
 PCG_ORDER0 = _pin(pin_pcg.test_order_zero_power_series_is_the_U_block_preconditioner)
 SJ_EXACT = _pin(pin_pcg.test_schur_jacobi_is_exact_for_single_observation_tracks)
@@ -207,6 +221,11 @@ CASES = [
          (LAMBDA_RULE,)),
     Case("lm_accepts_cost_increase", o_lm, "lm_solve",
          "actual > 0.0 and pred > 0.0", "pred > 0.0", (LM_REJECT,)),
+    Case("lm_not_spd_handled_as_accept", o_lm, "lm_solve",
+         "lam, nu = lambda_update(lam, nu, False, 0.0)", "lam, nu = lambda_update(lam, nu, True, 0.0)",
+         (LM_NOT_SPD,)),
+    Case("lm_series_eps_dropped", o_lm, "solve_step",
+         "bt, opts.eps, opts.max_inner)", "bt, 0.0, opts.max_inner)", (LM_EPS,)),
     Case("lm_keeps_stale_linearisation", o_lm, "lm_solve",
          "            ne = None\n            if (F_old", "            if (F_old", (LM_GRAD,)),
     Case("lm_step_subtracted", o_lm, "lm_solve",
@@ -237,11 +256,14 @@ def _plant(case, monkeypatch):
     src = textwrap.dedent(inspect.getsource(orig))
     n = src.count(case.old)
     assert n == 1, f"{case.module.__name__}.{case.name}: edit site {case.old!r} occurs {n} times"
-    ns = dict(vars(case.module))
     code = compile(src.replace(case.old, case.new), f"<planted {case.id}>", "exec",
                    flags=__future__.annotations.compiler_flag, dont_inherit=True)
-    exec(code, ns)
-    mutant = ns[case.name]
+    # Define the edited version in the module's own namespace, so that it sees the module's
+    # globals as they are at call time (including any a pin patches), then put the original
+    # back and install the edit through monkeypatch, which undoes it after the test.
+    exec(code, vars(case.module))
+    mutant = getattr(case.module, case.name)
+    setattr(case.module, case.name, orig)
     for mod in ORACLE_MODULES + PIN_MODULES:
         if getattr(mod, case.name, None) is orig:
             monkeypatch.setattr(mod, case.name, mutant)
