@@ -92,6 +92,7 @@ PCG_ORDER0 = _pin(pin_pcg.test_order_zero_power_series_is_the_U_block_preconditi
 SJ_EXACT = _pin(pin_pcg.test_schur_jacobi_is_exact_for_single_observation_tracks)
 ADJ_OBS = _pin(pin_adj.test_obs_gradient_is_the_derivative_of_a_damped_step)
 ADJ_W = _pin(pin_adj.test_weight_gradient_at_the_optimum)
+ADJ_POWER = _pin(pin_adj.test_power_series_adjoint_converges_to_the_direct_one, 1.0)
 
 
 @dataclass
@@ -209,6 +210,10 @@ CASES = [
          "S = explicit_schur(ne, Ulam, Vinv, dense=False)\n    return block_diagonal(S, ne.n_cams, 9)",
          "return Ulam.copy()", (SJ_EXACT,)),
     Case("pcg_solve_rhs_sign", o_pcg, "pcg_solve", "t), -bt, apply_Minv", "t), bt, apply_Minv", (PCG_EXACT,)),
+    Case("pcg_solve_back_substitution_sign", o_pcg, "pcg_solve",
+         "back_substitute(ne, Vi, y)", "back_substitute(ne, Vi, -y)", (PCG_EXACT,)),
+    Case("power_preconditioner_first_term_without_U_inverse", o_pcg, "power_series_preconditioner",
+         "t = apply_blocks(Uinv, r)", "t = r.copy()", (PCG_ORDER0,)),
     Case("power_preconditioner_without_U_inverse_term", o_pcg, "power_series_preconditioner",
          "        z = t.copy()\n", "        z = 0 * t\n", (PCG_ORDER0,)),
     Case("power_preconditioner_one_term_short", o_pcg, "power_series_preconditioner",
@@ -226,6 +231,11 @@ CASES = [
          (LM_NOT_SPD,)),
     Case("lm_series_eps_dropped", o_lm, "solve_step",
          "bt, opts.eps, opts.max_inner)", "bt, 0.0, opts.max_inner)", (LM_EPS,)),
+    Case("lm_state_not_moved_on_accept", o_lm, "lm_solve",
+         "            cams, lms = cams_new, lms_new\n", "", (LM_FLOOR, LM_GRAD)),
+    Case("lm_lambda_update_with_inverted_accept", o_lm, "lm_solve",
+         "lam, nu = lambda_update(lam, nu, accepted, rho)", "lam, nu = lambda_update(lam, nu, not accepted, rho)",
+         (LM_GRAD,)),
     Case("lm_keeps_stale_linearisation", o_lm, "lm_solve",
          "            ne = None\n            if (F_old", "            if (F_old", (LM_GRAD,)),
     Case("lm_step_subtracted", o_lm, "lm_solve",
@@ -238,6 +248,10 @@ CASES = [
          "g_l - ne.W.T @ a_p", "g_l + ne.W.T @ a_p", (ADJ_OBS,)),
     Case("adjoint_weights_not_passed", o_adj, "gradients",
          "observation_gradients(r, Jp, Jl, p.weights,", "observation_gradients(r, Jp, Jl, None,", (ADJ_OBS,)),
+    Case("adjoint_series_rhs_sign", o_adj, "adjoint_solve",
+         "power_series_solve(ne, Ui, Vi, -rhs,", "power_series_solve(ne, Ui, Vi, rhs,", (ADJ_POWER,)),
+    Case("adjoint_obs_gradient_sign", o_adj, "observation_gradients",
+         "d_obs = np.sqrt(w)[:, None] * u", "d_obs = -np.sqrt(w)[:, None] * u", (ADJ_OBS,)),
     Case("adjoint_damping_mode_flipped", o_adj, "adjoint_solve",
          "ne.damped(lam, damping_mode)", "ne.damped(lam, 1 - damping_mode)", (ADJ_OBS, ADJ_W)),
     Case("adjoint_landmark_part_dropped", o_adj, "observation_gradients",
