@@ -1,13 +1,15 @@
 """Planted mistakes in the oracle (CPU only).
 
-Each case below edits one line of one oracle function in memory -- a dropped term, a flipped
-sign, a swapped index or operand, an off-by-one bound -- compiles the edited function in its
-module's namespace, puts it in place of the original (also in every oracle or pin module that
-imported it by name) and runs the pins named for it.  The case passes when every one of those pins fails with
-an AssertionError.  This shows that the pins of tests/test_oracle_*.py constrain each part of the
-oracle (camera model, Jacobians, normal equation, damping, inverses, Schur complement,
-back-substitution, power series, stop rule, exact solves, PCG, LM loop, adjoint) through facts
-fixed by the paper and the mathematics, not by re-running the oracle against itself.
+Each case below makes one small edit to one oracle function in memory: a dropped term or line,
+a flipped sign, a swapped index or operand, an off-by-one bound, a wrong update rule.  The
+edited function is compiled in its module's namespace and put in place of the original (also in
+every oracle or pin module that imported it by name); then the pins named for the case run.
+The case passes when every one of those pins fails with an AssertionError.
+
+This shows that the pins of tests/test_oracle_*.py constrain each part of the oracle (camera
+model, Jacobians, normal equation, damping, inverses, Schur complement, back-substitution,
+power series, stop rule, exact solves, PCG, LM loop, adjoint) through facts fixed by the paper,
+the mathematics or a stated reading of the paper, not by re-running the oracle against itself.
 
 An edit whose text no longer occurs exactly once in the oracle fails loudly, so a later change
 to the oracle cannot turn a case into a silent no-op.  A control test runs every pin used here
