@@ -138,3 +138,14 @@ def test_power_solver_passes_eps_to_the_series():
     for h in hist:
         assert h["inner"] == 20 or h["stop_value"] < 0.5, h
     assert 1 <= hist[0]["inner"] < 20
+
+
+def test_default_settings_are_the_papers():
+    """Sec. 5.1 prints the settings: initial damping 1e-4, at most 50 LM iterations, relative
+    function tolerance 1e-6, series threshold eps = 0.01 and at most 20 inner iterations."""
+    import inspect
+    from oracle import power_series as ps
+    o = lm.Options()
+    assert (o.lambda0, o.max_lm, o.func_tol, o.eps, o.max_inner) == (1e-4, 50, 1e-6, 0.01, 20)
+    sig = inspect.signature(ps.power_series_solve)
+    assert sig.parameters["eps"].default == 0.01 and sig.parameters["m_max"].default == 20
