@@ -76,18 +76,21 @@ class Dual:
 
 
 def _sin(x):
+    """sin of an array or Dual (derivative cos x)."""
     if isinstance(x, Dual):
         return Dual(np.sin(x.v), x.d * np.cos(x.v)[..., None])
     return np.sin(x)
 
 
 def _cos(x):
+    """cos of an array or Dual (derivative -sin x)."""
     if isinstance(x, Dual):
         return Dual(np.cos(x.v), -x.d * np.sin(x.v)[..., None])
     return np.cos(x)
 
 
 def _sqrt(x):
+    """sqrt of an array or Dual (derivative 1 / (2 sqrt x))."""
     if isinstance(x, Dual):
         s = np.sqrt(x.v)
         return Dual(s, x.d * (0.5 / s)[..., None])
@@ -104,10 +107,12 @@ def _where(mask, a, b):
 
 
 def _value(x):
+    """The value part of a Dual, or the array itself."""
     return x.v if isinstance(x, Dual) else x
 
 
 def _cross(a, b):
+    """Cross product a x b of two 3-component lists (arrays or Duals)."""
     return [a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]]
 
 

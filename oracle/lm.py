@@ -35,6 +35,7 @@ LAMBDA_MAX = 1e32
 
 @dataclasses.dataclass
 class Options:
+    """The LM and series settings; the defaults are those of Sec. 5.1."""
     lambda0: float = 1e-4
     func_tol: float = 1e-6
     eps: float = 0.01

@@ -48,6 +48,7 @@ def block_diagonal(M, n_blocks, d):
 
 
 def _bd_fast(blocks):
+    """Sparse CSR block-diagonal matrix from dense blocks [n, d, d]."""
     n, d, _ = blocks.shape
     b = np.arange(n)[:, None, None]
     rows = d * b + np.arange(d)[None, :, None] + np.zeros((1, 1, d), dtype=np.int64)
