@@ -41,6 +41,9 @@ import test_oracle_power_series as pin_ps
 ORACLE_MODULES = (o_cm, o_neq, o_ps, o_direct, o_lm, o_pcg, o_adj)
 # the pins' own modules, some of which import oracle functions by name
 PIN_MODULES = (pin_adj, pin_cm, pin_lm, pin_neq, pin_pcg, pin_ps)
+# every function and class of those modules as imported, to check that each edit is undone
+ORIGINALS = {(m.__name__, k): v for m in ORACLE_MODULES + PIN_MODULES for k, v in vars(m).items()
+             if inspect.isfunction(v) or inspect.isclass(v)}
 
 
 def _pin(fn, *args):
@@ -303,3 +306,10 @@ def test_pins_pass_without_a_planted_mistake():
     pins = {p.__name__: p for c in CASES for p in c.pins}
     for name, pin in sorted(pins.items()):
         pin()
+
+
+def test_every_edit_was_undone():
+    """Runs after the cases above: each module again holds the objects it was imported with."""
+    mods = {m.__name__: m for m in ORACLE_MODULES + PIN_MODULES}
+    changed = [key for key, v in ORIGINALS.items() if vars(mods[key[0]]).get(key[1]) is not v]
+    assert not changed, changed
