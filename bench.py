@@ -175,7 +175,8 @@ def measured_peaks() -> tuple[float, str, float, str]:
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for f in ("kernels_persistent.cu", "series_body.cuh", "tile_common.cuh", "poba_internal.cuh"):
+    for f in ("kernels_persistent.cu", "series_body.cuh", "tile_common.cuh", "poba_internal.cuh",
+              "jacobian_io.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2204_12834_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -238,13 +239,15 @@ def series_term_units(p, s: int):
     return bytes_, flops
 
 
-def series_term_design_bytes(p, sched_slots: int, s: int) -> int:
-    """Bytes one term moves in this design: the observation term with the 2-byte slot code,
-    V^-1, per (tile, camera) slot a 9-vector partial written and read back and the current term
-    gathered and the new one written (4 x 9 s), and per camera U^-1 (81 x 8 B) and x."""
+def series_term_design_bytes(p, group_slots: int, s: int) -> int:
+    """Bytes one term moves in this design: per observation J (24 s) and its 4-byte chunk code;
+    per landmark V^-1 (6 s) and its 2-byte segment offset; per group slot (one per group and
+    camera it touches, ba_get_schedule's n_group_slots) the current term gathered (12 s), the
+    9-vector partial written and read back (2 x 9 s); per camera U^-1 (81 x 8 B), x read and
+    written and the new term (12 s)."""
     n_o, n_l, n_c = p.n_obs, p.n_lms, p.n_cams
-    return (n_o * (24 * s + 2) + n_l * (6 * s + 4) + sched_slots * 9 * s * 4
-            + n_c * (81 * 8 + 18 * 8))
+    return (n_o * (24 * s + 4) + n_l * (6 * s + 2) + group_slots * 30 * s
+            + n_c * (81 * 8 + 18 * 8 + 12 * s))
 
 
 def explicit_s_bytes(p) -> int:
@@ -445,7 +448,6 @@ def run_poba(args):
 
     # roofline of the dominant kernel class
     hbm_peak, hbm_kind, _, _ = measured_peaks()
-    r_slots = schedule_slots(p)
 
     def roofline(name):
         """Dominant kernel: the series (one term = tile phase and camera phase, plus the two
@@ -457,18 +459,17 @@ def run_poba(args):
         ms_c, _ = r["timing"]["series_camera"]
         s = 8 if name == "fp64" else 4
         nb, nf = series_term_units(p, s)
-        nd = series_term_design_bytes(p, r_slots, s)
+        sched = poba.ba_get_schedule(r["h"])
+        nd = series_term_design_bytes(p, sched["n_group_slots"], s)
         avg_s = (ms_t + ms_c) / 1e3 / max(cnt, 1)
         form = r["tuned"]["exec"]
         prec = "double" if name == "fp64" else "float"
-        kernel = {1: f"tile_matvec_kernel<{prec}, 0> + camera_step_kernel<{prec}, 0> "
+        kernel = {1: f"series_group_kernel<{prec}, 0> + camera_step_kernel<{prec}, 0> "
                      "(replayed CUDA graph, one pair of launches per term)",
-                  3: f"series_persistent_kernel<{prec}> (one series term: tile phase, camera "
-                     "phase, two grid barriers)",
-                  4: "series_persistent_f32_kernel (one series term: pipelined tile phase, "
-                     "camera phase, two grid barriers)"}[form]
+                  3: f"series_persistent_kernel<{prec}> (one series term: group phase, camera "
+                     "phase, two grid barriers)"}[form]
         traffic = profiled_traffic(name, form)
-        common = {"kernel": kernel, "series_form": r["tuned"],
+        common = {"kernel": kernel, "series_form": r["tuned"], "schedule": sched,
                   "traffic": traffic, "algorithmic_bytes_per_term": nb,
                   "algorithmic_flops_per_term": nf, "design_bytes_per_term": nd,
                   "design_gbs": nd / avg_s / 1e9, "avg_term_us": avg_s * 1e6, "terms": cnt,
@@ -713,7 +714,8 @@ def large_section(args, poba, torch, stream, dev, max_over_ranks, barrier):
     ms_c, _ = timing["series_camera"]
     avg_s = (ms_t + ms_c) / 1e3 / max(cnt, 1)
     nb, nf = series_term_units(p, 4)
-    nd = series_term_design_bytes(p, schedule_slots(p), 4)
+    sched = poba.ba_get_schedule(h)
+    nd = series_term_design_bytes(p, sched["n_group_slots"], 4)
     hbm_peak, hbm_kind, _, _ = measured_peaks()
     ach = nb / avg_s / 1e9
     out = {
@@ -728,7 +730,8 @@ def large_section(args, poba, torch, stream, dev, max_over_ranks, barrier):
                      "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)"
                      if hbm_kind == "measured" else "fallback 6800 GB/s",
                      "kernel": "series term (tile phase, camera phase, two grid barriers)",
-                     "series_form": tuned, "algorithmic_bytes_per_term": nb,
+                     "series_form": tuned, "schedule": sched,
+                     "algorithmic_bytes_per_term": nb,
                      "algorithmic_flops_per_term": nf, "design_bytes_per_term": nd,
                      "design_gbs": nd / avg_s / 1e9, "avg_term_us": avg_s * 1e6, "terms": cnt,
                      "achieved_tflops": nf / avg_s / 1e12,

@@ -78,14 +78,14 @@ typedef struct {
   int32_t damping_mode; /* 0: D^T D = diag(J^T J) clamped to [1e-6, 1e32]; 1: D = I */
   int32_t series_exec;  /* how the series loop runs: 0 one launch per kernel, 1 the same launches
                            replayed as a captured CUDA graph, 3 one persistent cooperative kernel
-                           for all terms with bounded grid barriers, 4 (BA_FP32_BULK) the
-                           persistent kernel staging each tile's inputs with asynchronous bulk
-                           copies issued ahead of the tile (needs at most 128 distinct cameras
-                           per tile, else as 3), 2 (default) the handle's choice: 3 at the
-                           largest residency (4 blocks per SM in BA_FP32_BULK, 3 in BA_FP64),
-                           or what ba_autotune measured.  Forms a device cannot run fall back (4 to 3,
-                           3 to 1: all blocks of a persistent kernel must be co-resident).  All
-                           forms give bitwise-equal results. */
+                           for all terms with bounded grid barriers, 4 (BA_FP32_BULK; else as 3)
+                           the persistent kernel with each chunk's inputs staged in shared
+                           memory by bulk asynchronous copies issued one chunk ahead, 2
+                           (default) the handle's schedule (ba_set_schedule / ba_autotune; at
+                           creation 3 at the largest residency, 4 blocks per SM in BA_FP32_BULK,
+                           3 in BA_FP64).  A device that cannot run a persistent form falls back
+                           (4 to 3, 3 to 1: all blocks must be co-resident).  All forms give
+                           bitwise-equal results for the handle's series schedule. */
 } ba_options;
 
 typedef struct {
@@ -306,18 +306,54 @@ typedef struct {
 ba_status ba_solve_schur_pcg(ba_handle* h, double lambda, int32_t precond, int32_t m_precond,
                              double rtol, int32_t max_iter, ba_pcg_info* info);
 
-/* Autotuner of the series execution (no counterpart in the paper; the schedule choice of the
+/* Series schedule (no counterpart in the paper; the GPU form of the paper's per-landmark memory
+ * blocks, Sec. 5 "Efficient storage").  The power-series kernels cut each problem's observed
+ * landmarks into groups of consecutive landmarks of about group_obs observations (boundaries
+ * at whole landmarks, balanced by observation count, at most 256 distinct cameras per group),
+ * and each group into chunks of at most 256 observations.  One thread block runs one group and
+ * keeps one camera-keyed accumulator per distinct camera of the group, written once per group:
+ * larger groups mean fewer partial rows for the camera step, smaller ones finer load balance.
+ * The sums of a step depend on the group boundaries, so two handles give bitwise-equal results
+ * when their group sizes agree (a batch and handles made for its problems alone included).
+ *   group_obs      observations per group; 0: automatic, n_obs / (the blocks of the
+ *                  persistent kernel at its largest residency that run groups: SMs x residency
+ *                  - 1), i.e. one group per block (at least 256);
+ *   tail_parts     each group of at least 512 observations gives its last eighth to
+ *                  tail_parts smaller groups, which blocks take after the large ones (groups go
+ *                  out largest first), so that the blocks that finish early even out the end of
+ *                  the phase; 0: no split (the default at creation);
+ *   series_exec    the form series_exec 2 runs: 1 (graph of per-term launches), 3 (persistent
+ *                  kernel) or 4 (persistent kernel with staged chunks, BA_FP32_BULK);
+ *   blocks_per_sm  the persistent kernel's residency (1 .. its occupancy limit on the device:
+ *                  on GB300 4 for form 3 in BA_FP32_BULK, 3 in BA_FP64, 3 for form 4);
+ *   n_groups, n_chunks, n_group_slots (ba_get_schedule only): the resulting schedule; the
+ *                  camera step sums n_group_slots partial rows of 9 values per term.
+ * ba_set_schedule rebuilds the schedule on the host when the group size changes (it waits for
+ * the handle's stream and replaces the schedule's device allocation).  Errors:
+ * BA_ERR_INVALID_ARG (negative group_obs, tail_parts outside [0, 64], a form other than 1, 3 or
+ * 4, form 4 in BA_FP64, a residency out of range),
+ * BA_ERR_OOM, BA_ERR_CUDA. */
+typedef struct {
+  int32_t group_obs;
+  int32_t tail_parts;
+  int32_t series_exec;
+  int32_t blocks_per_sm;
+  int32_t n_groups, n_chunks, n_group_slots;
+} ba_schedule;
+ba_status ba_get_schedule(ba_handle* h, ba_schedule* out);
+ba_status ba_set_schedule(ba_handle* h, const ba_schedule* in);
+
+/* Autotuner of the series schedule (no counterpart in the paper; the schedule choice of the
  * batched form).  On the handle's current linearisation (linearising first if needed) it times
  * `trials` series solves (damp, invert, max_inner terms, back-substitution; after one warm-up)
- * at lambda0 in each form the device can run -- the replayed CUDA graph of per-term launches,
- * the persistent kernel at 1 to 3 blocks per SM (1 to 4 in BA_FP32_BULK mode), and in
- * BA_FP32_BULK mode the persistent kernel with the copy pipeline at 1 to 3 blocks per SM --
- * and makes the fastest the form
- * that series_exec 2 uses.  All forms give bitwise-equal results, so tuning changes only
- * speed.  Overwrites the last step (as ba_solve_schur_power does).  *exec_out (may be NULL)
- * receives the chosen form (1, 3 or 4), *blocks_per_sm_out (may be NULL) its blocks per SM (0
- * for the graph).  Synchronises.  Errors: BA_ERR_INVALID_ARG (trials < 1), and those of
- * ba_solve_schur_power. */
+ * at lambda0 for: each persistent form (3, and 4 in BA_FP32_BULK) at each residency the device
+ * allows with one group per block (group_obs = n_obs / (grid - 1)) and a tail split of 2; at the
+ * fastest of those, tail splits of 0 and 4 and half the group size; and the replayed CUDA graph
+ * of per-term launches on the fastest schedule.  The fastest becomes the handle's schedule
+ * (ba_get_schedule reports it) and the form series_exec 2 runs.  Overwrites the last step (as
+ * ba_solve_schur_power does).  *exec_out (may be NULL) receives the chosen form (1, 3 or 4),
+ * *blocks_per_sm_out (may be NULL) its blocks per SM (0 for the graph).  Synchronises.
+ * Errors: BA_ERR_INVALID_ARG (trials < 1), and those of ba_solve_schur_power. */
 ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* blocks_per_sm_out);
 
 /* Implicit-differentiation adjoint (no counterpart in the paper; the differentiable form built
@@ -346,9 +382,9 @@ ba_status ba_adjoint(ba_handle* h, double lambda, const double* g_cams, const do
 /* Free all device memory of the handle (and its own stream, if it created one). NULL is OK. */
 ba_status ba_destroy(ba_handle* h);
 
-/* Phase timeline of the last persistent series solve: for each executed term
- * (at most 64), five %globaltimer readings in ns taken by the last block of the grid (a block
- * that always has camera work) -- term start, end of its tile phase, release of the first grid
+/* Phase timeline of the last persistent series solve: for each executed term (at most 64),
+ * five %globaltimer readings in ns taken by the grid's first block (a block that always has
+ * group and camera work) -- term start, end of its group phase, release of the first grid
  * barrier, end of its camera phase, release of the second barrier.  Copies min(capacity,
  * 5 * terms) values; *n_terms receives the terms. */
 ba_status ba_get_series_trace(ba_handle* h, int64_t* ns, int32_t capacity, int32_t* n_terms);

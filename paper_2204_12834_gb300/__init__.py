@@ -28,7 +28,7 @@ __all__ = ["PobaError", "Handle", "ba_default_options", "ba_create", "ba_set_opt
            "ba_get_series_trace", "ba_set_barrier_timeout", "ba_create_batch",
            "ba_get_batch_layout", "ba_get_series_state", "ba_lm_step_batch", "ba_lm_solve_batch",
            "ba_cost_batch", "batch_from_problems", "ba_autotune", "ba_adjoint",
-           "ba_solve_schur_pcg"]
+           "ba_solve_schur_pcg", "ba_get_schedule", "ba_set_schedule"]
 
 BA_NOALLOC_MAX_CAMS = 4096
 
@@ -375,11 +375,31 @@ def ba_set_barrier_timeout(h: Handle, cycles: int):
 
 
 def ba_autotune(h: Handle, trials: int = 3) -> dict:
-    """Time the series execution forms on the current linearisation and keep the fastest for
-    series_exec 2.  Returns {"exec": 1 | 3 | 4, "blocks_per_sm": k}."""
+    """Time the series schedules (form, residency, group size) on the current linearisation and
+    keep the fastest for series_exec 2.  Returns {"exec": 1 | 3 | 4, "blocks_per_sm": k}."""
     e, k = C.c_int32(), C.c_int32()
     _check(library().ba_autotune(h.ptr, int(trials), C.byref(e), C.byref(k)), "ba_autotune")
     return {"exec": e.value, "blocks_per_sm": k.value}
+
+
+def ba_get_schedule(h: Handle) -> dict:
+    """The handle's series schedule: group_obs, tail_parts, series_exec, blocks_per_sm,
+    n_groups, n_chunks, n_group_slots."""
+    s = _lib.Schedule()
+    _check(library().ba_get_schedule(h.ptr, C.byref(s)), "ba_get_schedule")
+    return {name: getattr(s, name) for name, _ in _lib.Schedule._fields_}
+
+
+def ba_set_schedule(h: Handle, group_obs: Optional[int] = None, series_exec: Optional[int] = None,
+                    blocks_per_sm: Optional[int] = None, tail_parts: Optional[int] = None):
+    """Change the series schedule; arguments left as None keep their current value."""
+    cur = ba_get_schedule(h)
+    s = _lib.Schedule()
+    s.group_obs = int(cur["group_obs"] if group_obs is None else group_obs)
+    s.tail_parts = int(cur["tail_parts"] if tail_parts is None else tail_parts)
+    s.series_exec = int(cur["series_exec"] if series_exec is None else series_exec)
+    s.blocks_per_sm = int(cur["blocks_per_sm"] if blocks_per_sm is None else blocks_per_sm)
+    _check(library().ba_set_schedule(h.ptr, C.byref(s)), "ba_set_schedule")
 
 
 def ba_adjoint(h: Handle, lam: float, g_cams, g_lms, d_obs=None, d_weights=None,

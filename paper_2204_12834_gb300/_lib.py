@@ -45,6 +45,12 @@ class PcgInfo(C.Structure):
                 ("rel_residual", C.c_double), ("lambda_", C.c_double)]
 
 
+class Schedule(C.Structure):
+    _fields_ = [("group_obs", C.c_int32), ("tail_parts", C.c_int32), ("series_exec", C.c_int32),
+                ("blocks_per_sm", C.c_int32),
+                ("n_groups", C.c_int32), ("n_chunks", C.c_int32), ("n_group_slots", C.c_int32)]
+
+
 TIMING_CLASSES = ["linearize", "damp_invert", "rhs", "series_tile", "series_camera", "backsub",
                   "evaluate"]
 
@@ -88,6 +94,8 @@ SIGNATURES = {
     "ba_lm_solve_batch": (C.c_int, [C.c_void_p, C.POINTER(StepInfo), C.POINTER(C.c_int32)]),
     "ba_cost_batch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ba_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "ba_get_schedule": (C.c_int, [C.c_void_p, C.POINTER(Schedule)]),
+    "ba_set_schedule": (C.c_int, [C.c_void_p, C.POINTER(Schedule)]),
     "ba_adjoint": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_void_p, C.c_int32, C.POINTER(SeriesInfo)]),
     "ba_solve_schur_pcg": (C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_int32, C.c_double,

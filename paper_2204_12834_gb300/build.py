@@ -20,6 +20,7 @@ SOURCES = ["schedule.cpp", "kernels_linearize.cu", "kernels_series.cu", "kernels
            "kernels_adjoint.cu", "kernels_pcg.cu",
            "api.cu", "noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "poba_internal.cuh"), os.path.join(CSRC, "tile_common.cuh"),
+           os.path.join(CSRC, "jacobian_io.cuh"),
            os.path.join(CSRC, "series_body.cuh"),
            os.path.join(ROOT, "include", "poba.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

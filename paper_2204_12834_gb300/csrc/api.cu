@@ -107,9 +107,6 @@ struct ba_handle {
   double* scalars = nullptr;      // [0] lambda for explicit solves, [1] cost out
   double* prob_cost = nullptr;    // [n_probs] F per problem (ba_cost_batch)
   GridSync* gs = nullptr;         // persistent kernel: grid-barrier state
-  int4* tile_list = nullptr;      // batches: descriptors of the tiles taking part in a solve
-  int32_t* list_off = nullptr;    // batches: [n_probs] scratch of the tile-list scan
-  int32_t* n_tiles_dev = nullptr; // one int: n_tiles (the tile list of a single problem)
   long long* trace = nullptr;     // persistent kernel: phase timeline of its last block
   SeriesState* st = nullptr;      // [n_probs]
   SeriesGlobal* sgl = nullptr;
@@ -140,11 +137,22 @@ struct ba_handle {
   bool graph_timing = false;
   bool graph_active = false;
   const double* graph_rhs = nullptr;
-  // persistent kernels: grid = blocks per SM x SMs; camera schedules for 1..3 blocks per SM
+  // series schedule (groups of chunks) and what depends on it, in a device allocation of its
+  // own that is rebuilt when the group size changes: descriptors, records, group slots, the
+  // series partial rows and the camera rounds of the persistent kernel for 1..plain_max blocks
+  // per SM
+  SerSchedule ser;
+  SerTopo sp{};
+  void* ser_arena = nullptr;
+  size_t ser_bytes = 0;
+  void* ser_partial = nullptr;           // [n_gslots][9] partial rows (bulk precision)
+  int group_obs = 0;                     // requested group size (0: automatic)
+  // persistent kernel: grid = blocks per SM x SMs
   int sms = 0;
-  int plain_max = 0, pipe_max = 0;       // occupancy limits (0: kernel unavailable)
-  int plain_k = 0, pipe_k = 0;           // blocks per SM in use
-  CamRounds plain_rounds[4]{}, pipe_rounds[4]{};  // per blocks-per-SM setting (1..4)
+  int plain_max = 0;                     // occupancy limit (0: kernel unavailable)
+  int plain_k = 0;                       // blocks per SM in use
+  int stage_max = 0, stage_k = 0;        // FP32 staged persistent kernel: limit, in use
+  CamRounds plain_rounds[4]{};           // per blocks-per-SM setting (1..4; any persistent form)
   int auto_exec = 1;                     // form used for series_exec 2: 1, 3 or 4
   long long barrier_timeout = 1LL << 33;  // clock cycles a block waits at a grid barrier
   int last_exec = -1;                    // execution form of the last solve (1, 0, 3 or 4)
@@ -291,21 +299,23 @@ void seq_linearize(ba_handle* h) {
 template <typename T>
 void seq_series_body(ba_handle* h, cudaStream_t s, bool use_active) {
   const Topology& tp = h->tp;
+  const SerTopo& sp = h->sp;
   const T* J = (const T*)h->J;
   const T* Vi = h->f32() ? (const T*)(const void*)h->Vinv_f : (const T*)(const void*)h->Vinv;
-  T* part = (T*)h->partial;
+  T* part = (T*)h->ser_partial;
   launch_series_reset(h->st, h->sgl, use_active ? h->rec : nullptr, h->n_probs, s);
   tmark(h, kTRhs, 0, 0);
-  launch_tile_rhs<T>(tp, J, h->rhs_l, Vi, part, h->st, s);
-  launch_camera_rhs<T>(tp, part, h->rhs_p, h->Uinv, h->x, (T*)h->t_cam, h->cam_norm, h->st, h->sgl, s);
+  launch_tile_rhs<T>(tp, sp, J, h->rhs_l, Vi, part, h->st, s);
+  launch_camera_rhs<T>(tp, sp, part, h->rhs_p, h->Uinv, h->x, (T*)h->t_cam, h->cam_norm, h->st,
+                       h->sgl, s);
   tmark(h, kTRhs, 0, 1);
   for (int i = 1; i <= h->opts.max_inner; ++i) {
     tmark(h, kTTile, i, 0);
-    launch_tile_series<T>(tp, J, (const T*)h->t_cam, Vi, part, h->st, h->sgl, s);
+    launch_tile_series<T>(tp, sp, J, (const T*)h->t_cam, Vi, part, h->st, h->sgl, s);
     tmark(h, kTTile, i, 1);
     tmark(h, kTCam, i, 0);
-    launch_camera_series<T>(tp, part, h->Uinv, h->x, (T*)h->t_cam, h->cam_norm, h->st, h->sgl, i,
-                            h->opts.eps, s);
+    launch_camera_series<T>(tp, sp, part, h->Uinv, h->x, (T*)h->t_cam, h->cam_norm, h->st,
+                            h->sgl, i, h->opts.eps, s);
     tmark(h, kTCam, i, 1);
   }
   tmark(h, kTBack, 0, 0);
@@ -313,52 +323,46 @@ void seq_series_body(ba_handle* h, cudaStream_t s, bool use_active) {
   tmark(h, kTBack, 0, 1);
 }
 
-int series_body_kernels(const ba_handle* h) { return 4 + 2 * h->opts.max_inner; }
+// Kernels of one series solve in the per-term forms (the group kernel is skipped when the
+// schedule has no group).
+int series_body_kernels(const ba_handle* h) {
+  const int group = h->sp.n_groups > 0 ? 1 : 0;
+  return 3 + group + (1 + group) * h->opts.max_inner;
+}
 
 template <typename T>
-ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active, bool pipelined) {
+ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active, bool staged) {
   const Topology& tp = h->tp;
+  const SerTopo& sp = h->sp;
   const T* J = (const T*)h->J;
   const T* Vi = h->f32() ? (const T*)(const void*)h->Vinv_f : (const T*)(const void*)h->Vinv;
-  T* part = (T*)h->partial;
+  T* part = (T*)h->ser_partial;
   launch_series_reset(h->st, h->sgl, use_active ? h->rec : nullptr, h->n_probs, s);
   tmark(h, kTRhs, 0, 0);
-  launch_tile_rhs<T>(tp, J, h->rhs_l, Vi, part, h->st, s);
-  launch_camera_rhs<T>(tp, part, h->rhs_p, h->Uinv, h->x, (T*)h->t_cam, h->cam_norm, h->st, h->sgl, s);
+  launch_tile_rhs<T>(tp, sp, J, h->rhs_l, Vi, part, h->st, s);
+  launch_camera_rhs<T>(tp, sp, part, h->rhs_p, h->Uinv, h->x, (T*)h->t_cam, h->cam_norm, h->st,
+                       h->sgl, s);
   tmark(h, kTRhs, 0, 1);
-  h->launches += 4;  // reset, the two RHS kernels, back-substitution
+  h->launches += 3 + (sp.n_groups > 0 ? 1 : 0);  // reset, the RHS kernels, back-substitution
   CK(cudaMemsetAsync(h->gs, 0, sizeof(GridSync), s));
   if (h->opts.max_inner > 0) {
+    tmark(h, kTTile, 1, 0);
     if constexpr (sizeof(T) == 4) {
-      if (pipelined) {
-        const int4* list = tp.tile_desc;
-        const int* n_list = h->n_tiles_dev;
-        if (h->n_probs > 1) {
-          launch_active_tiles(tp, h->st, h->list_off, h->tile_list, h->sgl, s);
-          h->launches += 2;
-          list = h->tile_list;
-          n_list = &h->sgl->n_list;
-        }
-        tmark(h, kTTile, 1, 0);
-        CK(launch_series_pipelined(tp, h->pipe_rounds[h->pipe_k - 1], h->pipe_k * h->sms, list,
-                                   n_list, J, Vi, h->Uinv, h->x,
-                                   (float*)h->t_cam, part, h->cam_norm, h->st, h->sgl, h->gs,
-                                   h->opts.max_inner, h->opts.eps, h->barrier_timeout, h->trace,
-                                   s));
-        tmark(h, kTTile, 1, 1);
-        h->launches += 1;
+      if (staged) {
+        CK(launch_series_staged(tp, sp, h->plain_rounds[h->stage_k - 1], h->stage_k * h->sms, J,
+                                Vi, h->Uinv, h->x, (T*)h->t_cam, part, h->cam_norm, h->st,
+                                h->sgl, h->gs, h->opts.max_inner, h->opts.eps,
+                                h->barrier_timeout, h->trace, s));
       }
     }
-    if (!pipelined) {
-      tmark(h, kTTile, 1, 0);
-      CK(launch_series_persistent<T>(tp, h->plain_rounds[h->plain_k - 1], h->plain_k * h->sms, J,
-                                     Vi, h->Uinv, h->x,
-                                     (T*)h->t_cam, part,
-                                     h->cam_norm, h->st, h->sgl, h->gs, h->opts.max_inner,
+    if (!staged) {
+      CK(launch_series_persistent<T>(tp, sp, h->plain_rounds[h->plain_k - 1],
+                                     h->plain_k * h->sms, J, Vi, h->Uinv, h->x, (T*)h->t_cam,
+                                     part, h->cam_norm, h->st, h->sgl, h->gs, h->opts.max_inner,
                                      h->opts.eps, h->barrier_timeout, h->trace, s));
-      tmark(h, kTTile, 1, 1);
-      h->launches += 1;
     }
+    tmark(h, kTTile, 1, 1);
+    h->launches += 1;
   }
   tmark(h, kTBack, 0, 0);
   launch_tile_backsub<T>(tp, J, (const T*)h->r, h->x, h->rhs_l, Vi, h->dx_l, h->block_pred, s);
@@ -372,15 +376,14 @@ ba_status run_series_body(ba_handle* h, bool use_active) {
     ba_status st = ensure_events(h);
     if (st != BA_OK) return st;
   }
-  // execution form: 0 per-term launches, 1 graph replay, 3 persistent, 4 persistent with the
-  // FP32 copy pipeline; series_exec 2 takes the handle's choice (heuristic or ba_autotune)
+  // execution form: 0 per-term launches, 1 graph replay, 3 persistent, 4 persistent with staged
+  // chunks (FP32 bulk); series_exec 2 takes the handle's schedule (default or ba_autotune)
   int mode = h->opts.series_exec == 2 ? h->auto_exec : h->opts.series_exec;
-  if (mode == 4 && h->pipe_k <= 0) mode = 3;
+  if (mode == 4 && h->stage_k <= 0) mode = 3;
   if (mode == 3 && h->plain_k <= 0) mode = 1;
   h->last_exec = mode;
   if (mode >= 3) {
-    const bool pipelined = mode == 4;
-    ba_status st = h->f32() ? seq_series_persistent<float>(h, s, use_active, pipelined)
+    ba_status st = h->f32() ? seq_series_persistent<float>(h, s, use_active, mode == 4)
                             : seq_series_persistent<double>(h, s, use_active, false);
     if (st == BA_OK) h->pending[kTRhs] = h->pending[kTBack] = h->timing;
     return st;
@@ -478,6 +481,7 @@ ba_status ba_destroy(ba_handle* h) {
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->arena) cudaFree(h->arena);
+  if (h->ser_arena) cudaFree(h->ser_arena);
   if (h->grad_out) cudaFree(h->grad_out);
   if (h->pcg) cudaFree(h->pcg);
   if (h->h_st) cudaFreeHost(h->h_st);
@@ -495,6 +499,91 @@ ba_status ba_destroy(ba_handle* h) {
 }  // extern "C"
 
 namespace {
+
+// The blocks that run groups in the persistent kernel at its largest residency (the grid's last
+// block applies the stop rule and takes no groups): the automatic group size is cut for them.
+int auto_workers(const ba_handle* h) { return (h->plain_max > 0 ? h->plain_max : 2) * h->sms - 1; }
+
+// Default tail split of the series groups: none (ba_autotune tries splits).
+constexpr int kDefaultTail = 0;
+
+// (Re)builds the series schedule for a group size (0: automatic, n_obs / grid) and its device
+// allocation: descriptors, chunk records, group slots, partial rows, and the camera rounds of
+// the persistent kernel for each residency.  The old allocation is freed after the handle's
+// stream drains, and the captured graph (which holds its pointers) is dropped.
+ba_status rebuild_series(ba_handle* h, int group_obs, int tail) {
+  const Schedule& S = h->sched;
+  const int target = group_obs > 0 ? group_obs : series_auto_target(h->n_o, auto_workers(h));
+  SerSchedule Q;
+  const std::string why = build_series_schedule(S, target, tail, &Q);
+  if (!why.empty()) return fail(BA_ERR_INVALID_ARG, why);
+  CamSchedule cs;
+  build_cam_schedule(Q.cam_ptr, h->n_c, &cs);
+  CamRoundList rl[4];
+  for (int k = 1; k <= h->plain_max && k <= 4; ++k) build_cam_rounds(cs, h->n_c, k * h->sms, &rl[k - 1]);
+  const size_t bulk = h->f32() ? sizeof(float) : sizeof(double);
+  struct Item { void** ptr; const void* src; size_t bytes; };
+  int32_t *d_group = nullptr, *d_chunk = nullptr, *d_gcam = nullptr, *d_grow = nullptr,
+          *d_cptr = nullptr, *d_item = nullptr, *d_q = nullptr, *d_rl[4][3] = {};
+  uint8_t* d_rec = nullptr;
+  void* d_part = nullptr;
+  auto nz = [](size_t b) { return b > 0 ? b : (size_t)16; };
+  std::vector<Item> items = {
+      {(void**)&d_group, Q.group.data(), sizeof(int32_t) * Q.group.size()},
+      {(void**)&d_chunk, Q.chunk.data(), sizeof(int32_t) * Q.chunk.size()},
+      {(void**)&d_rec, Q.rec.data(), Q.rec.size()},
+      {(void**)&d_gcam, Q.gslot_cam.data(), sizeof(int32_t) * Q.gslot_cam.size()},
+      {(void**)&d_grow, Q.gslot_row.data(), sizeof(int32_t) * Q.gslot_row.size()},
+      {(void**)&d_cptr, Q.cam_ptr.data(), sizeof(int32_t) * Q.cam_ptr.size()},
+      {&d_part, nullptr, bulk * 9 * (size_t)Q.n_gslots},
+      {(void**)&d_item, cs.cam_item.data(), sizeof(int32_t) * cs.cam_item.size()},
+      {(void**)&d_q, cs.item_q.data(), sizeof(int32_t) * cs.item_q.size()},
+  };
+  for (int k = 0; k < 4; ++k) {
+    if (rl[k].round_cam.empty()) continue;
+    items.push_back({(void**)&d_rl[k][0], rl[k].round_cam.data(), sizeof(int32_t) * rl[k].round_cam.size()});
+    items.push_back({(void**)&d_rl[k][1], rl[k].round_item.data(), sizeof(int32_t) * rl[k].round_item.size()});
+    items.push_back({(void**)&d_rl[k][2], rl[k].block_round.data(), sizeof(int32_t) * rl[k].block_round.size()});
+  }
+  size_t total = 0;
+  for (auto& it : items) total = align_up(total, 256) + nz(it.bytes);
+  total = align_up(total, 256);
+  void* arena = nullptr;
+  cudaError_t e = cudaMalloc(&arena, total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(BA_ERR_OOM, "cudaMalloc(series schedule) failed");
+  }
+  size_t off = 0;
+  for (auto& it : items) {
+    off = align_up(off, 256);
+    *it.ptr = (char*)arena + off;
+    off += nz(it.bytes);
+  }
+  // the old schedule may still be in use by queued work of the handle's stream
+  e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaMemset(arena, 0, total);
+  for (auto& it : items)
+    if (e == cudaSuccess && it.src && it.bytes) e = cudaMemcpy(*it.ptr, it.src, it.bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(arena);
+    return fail_cuda(e, "uploading the series schedule");
+  }
+  if (h->ser_arena) cudaFree(h->ser_arena);
+  if (h->graph_exec) {
+    cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+  }
+  h->ser_arena = arena;
+  h->ser_bytes = total;
+  h->ser_partial = d_part;
+  h->group_obs = group_obs;
+  h->sp = SerTopo{Q.n_groups, Q.n_chunks, Q.n_gslots, (const int4*)d_group, (const int4*)d_chunk,
+                  d_rec, d_gcam, d_grow, d_cptr};
+  for (int k = 0; k < 4; ++k) h->plain_rounds[k] = CamRounds{d_item, d_q, d_rl[k][0], d_rl[k][1], d_rl[k][2]};
+  h->ser = std::move(Q);
+  return BA_OK;
+}
 
 // ba_create and ba_create_batch: the problems are concatenated (cameras, landmarks and
 // observations of problem p follow those of problem p - 1, with indices offset to match) and
@@ -611,34 +700,32 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   for (int t = 0; t < S.n_tiles; ++t) tile_prob[t] = S.lm_prob[S.tile_lm0[t]];
 
   {
-    // persistent series kernels: all blocks must be co-resident (cooperative launch)
+    // persistent series kernel: all blocks must be co-resident (cooperative launch)
     int dev = 0, sms = 0, coop = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     const int per_sm = persistent_blocks_per_sm(h->f32());
     h->sms = sms;
-    // FP32 bulk: the plain persistent kernel fits 4 blocks of 256 threads per SM
+    // FP32 bulk: up to 4 blocks of 256 threads per SM, FP64: up to 3
     const int cap = h->f32() ? 4 : 3;
     h->plain_max = (coop && per_sm > 0) ? (per_sm < cap ? per_sm : cap) : 0;
-    if (h->f32() && h->plain_max > 0 && S.max_slots_per_tile <= kTileSlots) {
-      const int pipe_per_sm = pipelined_blocks_per_sm();
-      h->pipe_max = pipe_per_sm > 0 ? (pipe_per_sm < 3 ? pipe_per_sm : 3) : 0;
-    }
     h->plain_k = h->plain_max;
-    h->pipe_k = h->pipe_max;
-    // default form: the plain persistent kernel at its largest residency (in FP32 bulk at 4
-    // blocks per SM it is at least as fast as the copy pipeline on every workload measured);
-    // ba_autotune measures every form instead
+    if (h->f32() && h->plain_max > 0) {
+      const int st = staged_blocks_per_sm();
+      h->stage_max = st < 3 ? st : 3;
+      h->stage_k = h->stage_max;
+    }
+    // default form: the persistent kernel at its largest residency; ba_autotune measures the
+    // forms instead
     h->auto_exec = h->plain_k > 0 ? 3 : 1;
+    cudaError_t ie = h->f32() ? series_group_kernels_init<float>() : series_group_kernels_init<double>();
+    if (ie != cudaSuccess) {
+      delete h;
+      return fail_cuda(ie, "series kernel attributes");
+    }
     cudaGetLastError();
   }
-  // camera schedules of the persistent kernels (rounds per grid size)
-  CamSchedule cs;
-  build_cam_schedule(S, &cs);
-  CamRoundList rl[2][4];
-  for (int k = 1; k <= h->plain_max; ++k) build_cam_rounds(cs, nc, k * h->sms, &rl[0][k - 1]);
-  for (int k = 1; k <= h->pipe_max; ++k) build_cam_rounds(cs, nc, k * h->sms, &rl[1][k - 1]);
 
   // ---- arena layout
   const size_t bulk = h->f32() ? sizeof(float) : sizeof(double);
@@ -692,7 +779,8 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   items.push_back({(void**)&h->lm_order_dev, sizeof(int32_t) * nl});
   items.push_back({(void**)&h->Uinv, sizeof(double) * nc * 81});
   items.push_back({(void**)&h->Vinv, sizeof(double) * nl * 6});
-  if (h->f32()) items.push_back({(void**)&h->Vinv_f, sizeof(float) * nl * 6});
+  // (4 floats of slack: the staged kernel copies V^-1 ranges rounded out to 16 bytes)
+  if (h->f32()) items.push_back({(void**)&h->Vinv_f, sizeof(float) * ((size_t)nl * 6 + 4)});
   items.push_back({(void**)&h->x, sizeof(double) * nc * 9});
   items.push_back({(void**)&h->dx_l, sizeof(double) * nl * 3});
   items.push_back({(void**)&h->cam_norm, sizeof(double) * 2 * nc});
@@ -704,22 +792,6 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   items.push_back({(void**)&h->gs, sizeof(GridSync)});
   uint8_t* d_tile_rec = nullptr;
   items.push_back({(void**)&d_tile_rec, S.tile_rec.size() > 0 ? S.tile_rec.size() : 16});
-  items.push_back({(void**)&h->n_tiles_dev, sizeof(int32_t)});
-  int32_t *d_cam_item, *d_item_q;
-  int32_t* d_rl[2][4][3] = {};
-  items.push_back({(void**)&d_cam_item, sizeof(int32_t) * cs.cam_item.size()});
-  items.push_back({(void**)&d_item_q, sizeof(int32_t) * (cs.item_q.size() > 0 ? cs.item_q.size() : 1)});
-  for (int f = 0; f < 2; ++f)
-    for (int k = 0; k < 4; ++k) {
-      if (rl[f][k].round_cam.empty()) continue;
-      items.push_back({(void**)&d_rl[f][k][0], sizeof(int32_t) * rl[f][k].round_cam.size()});
-      items.push_back({(void**)&d_rl[f][k][1], sizeof(int32_t) * rl[f][k].round_item.size()});
-      items.push_back({(void**)&d_rl[f][k][2], sizeof(int32_t) * rl[f][k].block_round.size()});
-    }
-  if (n_probs > 1) {
-    items.push_back({(void**)&h->tile_list, sizeof(int4) * 2 * (size_t)S.n_tiles});
-    items.push_back({(void**)&h->list_off, sizeof(int32_t) * P});
-  }
   items.push_back({(void**)&h->trace, sizeof(long long) * kTraceTerms * kTracePoints});
   items.push_back({(void**)&h->st, sizeof(SeriesState) * P});
   items.push_back({(void**)&h->sgl, sizeof(SeriesGlobal)});
@@ -796,9 +868,6 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
       {d_cam_off, S.cam_off.data(), sizeof(int32_t) * (P + 1)},
       {d_tile_off, S.tile_off.data(), sizeof(int32_t) * (P + 1)},
       {d_tile_rec, S.tile_rec.data(), S.tile_rec.size()},
-      {h->n_tiles_dev, &S.n_tiles, sizeof(int32_t)},
-      {d_cam_item, cs.cam_item.data(), sizeof(int32_t) * cs.cam_item.size()},
-      {d_item_q, cs.item_q.data(), sizeof(int32_t) * cs.item_q.size()},
       {h->obs, obs_s.data(), sizeof(double) * 2 * no},
       {h->obs_caller, obs_caller.data(), sizeof(int32_t) * no},
       {h->lm_order_dev, S.lm_order.data(), sizeof(int32_t) * nl},
@@ -818,13 +887,6 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
       ups.push_back({h->sqrt_w32, sw32_s.data(), sizeof(float) * no});
     }
   }
-  for (int f = 0; f < 2; ++f)
-    for (int k = 0; k < 4; ++k) {
-      if (rl[f][k].round_cam.empty()) continue;
-      ups.push_back({d_rl[f][k][0], rl[f][k].round_cam.data(), sizeof(int32_t) * rl[f][k].round_cam.size()});
-      ups.push_back({d_rl[f][k][1], rl[f][k].round_item.data(), sizeof(int32_t) * rl[f][k].round_item.size()});
-      ups.push_back({d_rl[f][k][2], rl[f][k].block_round.data(), sizeof(int32_t) * rl[f][k].block_round.size()});
-    }
   for (auto& u : ups) {
     if (u.bytes == 0) continue;
     e = cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice);
@@ -871,9 +933,9 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   tp.tile_rec = d_tile_rec;
   h->rhs_p = h->b_p;
   h->rhs_l = h->b_l;
-  for (int k = 0; k < 4; ++k) {
-    h->plain_rounds[k] = CamRounds{d_cam_item, d_item_q, d_rl[0][k][0], d_rl[0][k][1], d_rl[0][k][2]};
-    h->pipe_rounds[k] = CamRounds{d_cam_item, d_item_q, d_rl[1][k][0], d_rl[1][k][1], d_rl[1][k][2]};
+  {
+    ba_status st = rebuild_series(h, 0, kDefaultTail);
+    if (st != BA_OK) return bail(st);
   }
   *out = h;
   g_last_error.clear();
@@ -1061,47 +1123,53 @@ ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* 
     if (st != BA_OK) return st;
     h->linearized = true;
   }
+  // a candidate: execution form, blocks per SM, group size
   struct Cand {
-    int exec, k;
+    int exec, k, target, tail;
   };
-  std::vector<Cand> cands = {{1, 0}};
-  for (int k = 1; k <= h->plain_max; ++k) cands.push_back({3, k});
-  for (int k = 1; k <= h->pipe_max; ++k) cands.push_back({4, k});
   const ba_options saved = h->opts;
   const bool saved_timing = h->timing;
-  const int saved_plain = h->plain_k, saved_pipe = h->pipe_k;
-  h->opts.eps = 0.0;  // every form runs max_inner terms
+  const int saved_k = h->plain_k, saved_sk = h->stage_k, saved_target = h->ser.target,
+            saved_req = h->group_obs, saved_tail = h->ser.tail;
+  h->opts.eps = 0.0;  // every candidate runs max_inner terms
   h->timing = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   ba_status st = BA_OK;
-  float best_ms = 0.f;
-  Cand best{-1, 0};
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     st = fail_cuda(cudaGetLastError(), "cudaEventCreate");
   launch_set_scalar(h->scalars + 0, h->opts.lambda0, h->stream);
   h->launches += 1;
   h->last_solve_lm = false;
   h->solve_lambda = h->opts.lambda0;
-  for (const Cand& c : cands) {
-    if (st != BA_OK) break;
+  float best_ms = 0.f;
+  Cand best{-1, 0, 0, 0};
+  auto trial = [&](const Cand& c) {
+    if (st != BA_OK) return;
+    if ((c.target != h->ser.target || c.tail != h->ser.tail) &&
+        (st = rebuild_series(h, c.target, c.tail)) != BA_OK)
+      return;
     h->opts.series_exec = c.exec;
     if (c.exec == 3) h->plain_k = c.k;
-    if (c.exec == 4) h->pipe_k = c.k;
+    if (c.exec == 4) h->stage_k = c.k;
     st = run_solve(h, h->scalars + 0, 0, false);  // warm-up (and graph capture)
-    if (st != BA_OK) break;
+    if (st != BA_OK) return;
     cudaEventRecord(e0, h->stream);
     for (int t = 0; t < trials && st == BA_OK; ++t) st = run_solve(h, h->scalars + 0, 0, false);
     cudaEventRecord(e1, h->stream);
-    if (st != BA_OK) break;
+    if (st != BA_OK) return;
     cudaError_t e = cudaEventSynchronize(e1);
     if (e != cudaSuccess) {
       st = fail_cuda(e, "autotune");
-      break;
+      return;
     }
-    CK(cudaMemcpy(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost));
+    e = cudaMemcpy(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      st = fail_cuda(e, "autotune");
+      return;
+    }
     if (c.exec >= 3 && h->h_gs->error) {
       st = fail(BA_ERR_TIMEOUT, "a grid barrier of the persistent series kernel timed out");
-      break;
+      return;
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
@@ -1109,19 +1177,79 @@ ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* 
       best_ms = ms;
       best = c;
     }
+  };
+  // the persistent kernel at each residency with one group per block; then two groups per
+  // block at the best residency (finer load balance, more partial rows); then the per-term
+  // launches replayed as a graph on the best schedule
+  for (int k = 1; k <= h->plain_max; ++k)
+    trial({3, k, series_auto_target(h->n_o, k * h->sms - 1), kDefaultTail});
+  for (int k = 1; k <= h->stage_max; ++k)
+    trial({4, k, series_auto_target(h->n_o, k * h->sms - 1), kDefaultTail});
+  if (best.exec >= 3) {
+    const Cand b = best;
+    trial({b.exec, b.k, b.target, 0});
+    trial({b.exec, b.k, b.target, 4});
+    if (b.target > kChunkObs) trial({b.exec, b.k, (b.target + 1) / 2, b.tail});
   }
+  trial({1, 0, best.exec < 0 ? h->ser.target : best.target, best.exec < 0 ? h->ser.tail : best.tail});
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   h->opts = saved;
   h->timing = saved_timing;
-  h->plain_k = saved_plain;
-  h->pipe_k = saved_pipe;
-  if (st != BA_OK) return st;
+  h->plain_k = saved_k;
+  h->stage_k = saved_sk;
+  if (st != BA_OK) {
+    if (h->ser.target != saved_target || h->ser.tail != saved_tail)
+      rebuild_series(h, saved_req, saved_tail);
+    return st;
+  }
+  if (best.target != h->ser.target || best.tail != h->ser.tail) {
+    st = rebuild_series(h, best.target, best.tail);
+    if (st != BA_OK) return st;
+  }
+  h->group_obs = best.target;
   h->auto_exec = best.exec;
   if (best.exec == 3) h->plain_k = best.k;
-  if (best.exec == 4) h->pipe_k = best.k;
+  if (best.exec == 4) h->stage_k = best.k;
   if (exec_out) *exec_out = best.exec;
-  if (bps_out) *bps_out = best.k;
+  if (bps_out) *bps_out = best.exec >= 3 ? best.k : 0;
+  return BA_OK;
+}
+
+ba_status ba_get_schedule(ba_handle* h, ba_schedule* out) {
+  if (!h || !out) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  out->group_obs = h->ser.target;
+  out->tail_parts = h->ser.tail;
+  out->series_exec = h->auto_exec;
+  out->blocks_per_sm = h->auto_exec == 4 ? h->stage_k : h->plain_k;
+  out->n_groups = h->ser.n_groups;
+  out->n_chunks = h->ser.n_chunks;
+  out->n_group_slots = h->ser.n_gslots;
+  return BA_OK;
+}
+
+ba_status ba_set_schedule(ba_handle* h, const ba_schedule* in) {
+  if (!h || !in) return fail(BA_ERR_INVALID_ARG, "NULL argument");
+  if (in->group_obs < 0) return fail(BA_ERR_INVALID_ARG, "group_obs must be >= 0");
+  if (in->tail_parts < 0 || in->tail_parts > 64)
+    return fail(BA_ERR_INVALID_ARG, "tail_parts must be in [0, 64]");
+  if (in->series_exec != 1 && in->series_exec != 3 && in->series_exec != 4)
+    return fail(BA_ERR_INVALID_ARG, "series_exec must be 1, 3 or 4");
+  if (in->series_exec == 4 && h->stage_max <= 0)
+    return fail(BA_ERR_INVALID_ARG, "series_exec 4 needs BA_FP32_BULK and the staged kernel");
+  const int kmax = in->series_exec == 4 ? h->stage_max : h->plain_max;
+  if (in->series_exec >= 3 && (in->blocks_per_sm < 1 || in->blocks_per_sm > kmax))
+    return fail(BA_ERR_INVALID_ARG, "blocks_per_sm must be in [1, " + std::to_string(kmax) +
+                                        "] (the persistent kernel's residency on this device)");
+  const int target = in->group_obs > 0 ? in->group_obs : series_auto_target(h->n_o, auto_workers(h));
+  if (target != h->ser.target || in->tail_parts != h->ser.tail) {
+    ba_status st = rebuild_series(h, in->group_obs, in->tail_parts);
+    if (st != BA_OK) return st;
+  }
+  h->group_obs = in->group_obs;
+  h->auto_exec = in->series_exec;
+  if (in->series_exec == 3) h->plain_k = in->blocks_per_sm;
+  if (in->series_exec == 4) h->stage_k = in->blocks_per_sm;
   return BA_OK;
 }
 
@@ -1249,11 +1377,11 @@ void seq_schur_apply(ba_handle* h, double lambda, const double* p, double* q) {
   const T* Vi = h->f32() ? (const T*)(const void*)h->Vinv_f : (const T*)(const void*)h->Vinv;
   launch_stage_term<T>(h->n_c, p, (T*)h->t_cam, s);
   launch_series_reset(h->st, h->sgl, nullptr, h->n_probs, s);
-  launch_tile_series<T>(h->tp, (const T*)h->J, (const T*)h->t_cam, Vi, (T*)h->partial, h->st,
-                        h->sgl, s);
-  launch_schur_camera<T>(h->tp, (const T*)h->partial, h->U45, lambda, h->opts.damping_mode, p, q,
-                         s);
-  h->launches += 4;
+  launch_tile_series<T>(h->tp, h->sp, (const T*)h->J, (const T*)h->t_cam, Vi,
+                        (T*)h->ser_partial, h->st, h->sgl, s);
+  launch_schur_camera<T>(h->tp, h->sp, (const T*)h->ser_partial, h->U45, lambda,
+                         h->opts.damping_mode, p, q, s);
+  h->launches += 3 + (h->sp.n_groups > 0 ? 1 : 0);
 }
 
 // The reduced right-hand side -b~ = W V^-1 b_l - b_p.
@@ -1262,9 +1390,9 @@ void seq_schur_rhs(ba_handle* h, double* out) {
   cudaStream_t s = h->stream;
   const T* Vi = h->f32() ? (const T*)(const void*)h->Vinv_f : (const T*)(const void*)h->Vinv;
   launch_series_reset(h->st, h->sgl, nullptr, h->n_probs, s);
-  launch_tile_rhs<T>(h->tp, (const T*)h->J, h->b_l, Vi, (T*)h->partial, h->st, s);
-  launch_schur_rhs_camera<T>(h->tp, (const T*)h->partial, h->b_p, out, s);
-  h->launches += 3;
+  launch_tile_rhs<T>(h->tp, h->sp, (const T*)h->J, h->b_l, Vi, (T*)h->ser_partial, h->st, s);
+  launch_schur_rhs_camera<T>(h->tp, h->sp, (const T*)h->ser_partial, h->b_p, out, s);
+  h->launches += 2 + (h->sp.n_groups > 0 ? 1 : 0);
 }
 
 // Schur-Jacobi blocks S_cc and their inverses.
@@ -1573,8 +1701,11 @@ ba_status ba_get_linearization(ba_handle* h, double* r, double* Jp, double* Jl, 
   for (size_t o = 0; o < no; ++o) {
     const size_t c = (size_t)h->sched.obs_order[o];
     for (int i = 0; i < 2; ++i) ro[c * 2 + i] = rd[i * pad + o];
-    for (int p = 0; p < 18; ++p) jpo[c * 18 + p] = Jd[p * pad + o];
-    for (int p = 0; p < 6; ++p) jlo[c * 6 + p] = Jd[(18 + p) * pad + o];
+    const bool f32 = h->f32();
+    for (int p = 0; p < 18; ++p)
+      jpo[c * 18 + p] = Jd[f32 ? jidx<float>(p, o, pad) : jidx<double>(p, o, pad)];
+    for (int p = 0; p < 6; ++p)
+      jlo[c * 6 + p] = Jd[f32 ? jidx<float>(18 + p, o, pad) : jidx<double>(18 + p, o, pad)];
   }
   ba_status st;
   if (r && (st = copy_out(r, ro.data(), sizeof(double) * ro.size(), ptr_kind)) != BA_OK) return st;
@@ -1681,7 +1812,7 @@ ba_status ba_set_barrier_timeout(ba_handle* h, int64_t cycles) {
 
 ba_status ba_memory_footprint(ba_handle* h, uint64_t* bytes) {
   if (!h || !bytes) return fail(BA_ERR_INVALID_ARG, "NULL argument");
-  *bytes = (uint64_t)h->arena_bytes;
+  *bytes = (uint64_t)(h->arena_bytes + h->ser_bytes);
   return BA_OK;
 }
 

@@ -51,9 +51,9 @@ __global__ void obs_gradient_kernel(Topology tp, const T* __restrict__ J, const 
   for (int i = 0; i < 2; ++i) {
     double v = 0.0;
 #pragma unroll
-    for (int j = 0; j < 9; ++j) v += (double)J[(size_t)(9 * i + j) * pad + o] * ap[j];
+    for (int j = 0; j < 9; ++j) v += (double)J[jidx<T>(9 * i + j, o, pad)] * ap[j];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) v += (double)J[(size_t)(18 + 3 * i + j) * pad + o] * al[j];
+    for (int j = 0; j < 3; ++j) v += (double)J[jidx<T>(18 + 3 * i + j, o, pad)] * al[j];
     u[i] = v;
   }
   const double sw = sqrt_w ? sqrt_w[o] : 1.0;

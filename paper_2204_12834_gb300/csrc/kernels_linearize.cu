@@ -15,6 +15,7 @@
 #include <cfloat>
 #include <cmath>
 
+#include "jacobian_io.cuh"
 #include "poba_internal.cuh"
 #include "tile_common.cuh"
 
@@ -208,10 +209,7 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
     bal_residual_jacobian<T>(prep + (size_t)c * kCamPrep, lms[l * 3 + 0], lms[l * 3 + 1],
                              lms[l * 3 + 2], obs[o], sw, jp, jl, rr);
     const size_t pad = (size_t)tp.n_obs_pad;
-#pragma unroll
-    for (int p = 0; p < 18; ++p) J[p * pad + o] = jp[p];
-#pragma unroll
-    for (int p = 0; p < 6; ++p) J[(18 + p) * pad + o] = jl[p];
+    store_J(J, pad, o, jp, jl);
     r[o] = rr[0];
     r[pad + o] = rr[1];
     cost = 0.5 * ((double)rr[0] * (double)rr[0] + (double)rr[1] * (double)rr[1]);

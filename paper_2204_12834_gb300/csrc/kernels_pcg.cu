@@ -1,6 +1,6 @@
 // Preconditioned conjugate gradients on the reduced camera system (Sec. 4.2, eqs. `Sx`,
 // `Schur`) -- the solvers the paper compares against -- built from the same matvec kernels:
-//   S p = U_lam p - W V_lam^-1 W^T p   (the series tile kernel for W V^-1 W^T p, then
+//   S p = U_lam p - W V_lam^-1 W^T p   (the series group kernel for W V^-1 W^T p, then
 //                                       schur_camera_kernel for U_lam p - y);
 //   Schur-Jacobi preconditioner (Sec. 5, Ceres' choice): the inverses of the 9x9 diagonal
 //       blocks S_cc = U_lam,c - sum_l W_cl V_l^-1 W_cl^T, whose second term is summed per
@@ -77,9 +77,9 @@ __global__ void __launch_bounds__(kTileObs) schur_jacobi_tile_kernel(
       for (int q = o; q < o0 + n && tp.cam_of[q] == c && tp.lm_of[q] == l; ++q) {
         double jp[18], jl[6];
 #pragma unroll
-        for (int e = 0; e < 18; ++e) jp[e] = (double)J[(size_t)e * pad + q];
+        for (int e = 0; e < 18; ++e) jp[e] = (double)J[jidx<T>(e, q, pad)];
 #pragma unroll
-        for (int e = 0; e < 6; ++e) jl[e] = (double)J[(size_t)(18 + e) * pad + q];
+        for (int e = 0; e < 6; ++e) jl[e] = (double)J[jidx<T>(18 + e, q, pad)];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
@@ -135,16 +135,16 @@ void launch_schur_diag(int n_cams, const double* U45, const double* SJ45, double
 }
 
 // ---------------------------------------------------------------------------------------
-// S p, camera side: q_c = U_lam,c p_c - (sum of the camera's partial rows, chunked as in
+// S p, camera side: q_c = U_lam,c p_c - (sum of the camera's series partial rows, chunked as in
 // camera_body).  9 threads per camera.
 template <typename PT>
 __global__ void __launch_bounds__(kCamBlock * 9) schur_camera_kernel(
-    Topology tp, const PT* __restrict__ partial, const double* __restrict__ U45, double lam,
+    Topology tp, const int32_t* __restrict__ cam_ptr, const PT* __restrict__ partial, const double* __restrict__ U45, double lam,
     int mode, const double* __restrict__ p, double* __restrict__ q) {
   const int cl = threadIdx.x / 9, k = threadIdx.x - 9 * (threadIdx.x / 9);
   const int c = blockIdx.x * kCamBlock + cl;
   if (c >= tp.n_cams) return;
-  const int r0 = tp.cam_slot_ptr[c], r1 = tp.cam_slot_ptr[c + 1];
+  const int r0 = cam_ptr[c], r1 = cam_ptr[c + 1];
   const int C = cam_chunk_rows(r1 - r0);
   double y = 0.0;
   for (int q0 = r0; q0 < r1; q0 += C) y += cam_chunk_sum(partial, q0, min(q0 + C, r1), k);
@@ -159,24 +159,25 @@ __global__ void __launch_bounds__(kCamBlock * 9) schur_camera_kernel(
 }
 
 template <typename PT>
-void launch_schur_camera(const Topology& tp, const PT* partial, const double* U45, double lam,
-                         int mode, const double* p, double* q, cudaStream_t s) {
-  schur_camera_kernel<PT><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(tp, partial, U45, lam, mode,
-                                                                      p, q);
+void launch_schur_camera(const Topology& tp, const SerTopo& sp, const PT* partial,
+                         const double* U45, double lam, int mode, const double* p, double* q,
+                         cudaStream_t s) {
+  schur_camera_kernel<PT><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(tp, sp.cam_ptr, partial, U45,
+                                                                      lam, mode, p, q);
 }
-template void launch_schur_camera<double>(const Topology&, const double*, const double*, double, int, const double*, double*, cudaStream_t);
-template void launch_schur_camera<float>(const Topology&, const float*, const double*, double, int, const double*, double*, cudaStream_t);
+template void launch_schur_camera<double>(const Topology&, const SerTopo&, const double*, const double*, double, int, const double*, double*, cudaStream_t);
+template void launch_schur_camera<float>(const Topology&, const SerTopo&, const float*, const double*, double, int, const double*, double*, cudaStream_t);
 
 // Reduced right-hand side of S y = -b~: out_c = (sum of the camera's partial rows, W V^-1 b_l)
 // - b_p,c.  9 threads per camera.
 template <typename PT>
 __global__ void __launch_bounds__(kCamBlock * 9) schur_rhs_camera_kernel(
-    Topology tp, const PT* __restrict__ partial, const double* __restrict__ b_p,
+    Topology tp, const int32_t* __restrict__ cam_ptr, const PT* __restrict__ partial, const double* __restrict__ b_p,
     double* __restrict__ out) {
   const int cl = threadIdx.x / 9, k = threadIdx.x - 9 * (threadIdx.x / 9);
   const int c = blockIdx.x * kCamBlock + cl;
   if (c >= tp.n_cams) return;
-  const int r0 = tp.cam_slot_ptr[c], r1 = tp.cam_slot_ptr[c + 1];
+  const int r0 = cam_ptr[c], r1 = cam_ptr[c + 1];
   const int C = cam_chunk_rows(r1 - r0);
   double y = 0.0;
   for (int q0 = r0; q0 < r1; q0 += C) y += cam_chunk_sum(partial, q0, min(q0 + C, r1), k);
@@ -184,12 +185,13 @@ __global__ void __launch_bounds__(kCamBlock * 9) schur_rhs_camera_kernel(
 }
 
 template <typename PT>
-void launch_schur_rhs_camera(const Topology& tp, const PT* partial, const double* b_p,
-                             double* out, cudaStream_t s) {
-  schur_rhs_camera_kernel<PT><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(tp, partial, b_p, out);
+void launch_schur_rhs_camera(const Topology& tp, const SerTopo& sp, const PT* partial,
+                             const double* b_p, double* out, cudaStream_t s) {
+  schur_rhs_camera_kernel<PT><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(tp, sp.cam_ptr, partial,
+                                                                          b_p, out);
 }
-template void launch_schur_rhs_camera<double>(const Topology&, const double*, const double*, double*, cudaStream_t);
-template void launch_schur_rhs_camera<float>(const Topology&, const float*, const double*, double*, cudaStream_t);
+template void launch_schur_rhs_camera<double>(const Topology&, const SerTopo&, const double*, const double*, double*, cudaStream_t);
+template void launch_schur_rhs_camera<float>(const Topology&, const SerTopo&, const float*, const double*, double*, cudaStream_t);
 
 // The current term rows the tile kernel gathers: t_cam[c] = p_c (bulk precision).
 template <typename PT>

@@ -3,16 +3,17 @@
 // rule of Sec. 4.3 (eqs. `S_approx`, `x_approx`, `qcriterion`).
 //
 // Each term is two phases separated by grid barriers:
-//   phase A  every block pulls tiles from a shared counter and runs the tile body (W^T t,
-//            V^-1, W z) -- dynamic scheduling, so no wave tail;
+//   phase A  every block but the last takes groups of the series schedule by ticket (largest
+//            first) and runs the group body (W^T t, V^-1, W z, one partial row per group slot);
 //   phase B  camera groups (spread over all blocks, static) run the camera body (U^-1, x
 //            accumulation, new term rows) and store a squared-norm pair per camera;
-//   barrier  the last block to arrive opens it by arriving, then sums each running problem's
-//            camera norm pairs in camera order and applies its stop rule; the other blocks see
-//            the decisions before their next tile fetch and, at the latest, at the next
-//            barrier (a stopped problem's tiles and cameras are skipped, so its x stays at the
-//            term where its rule fired).
-// Results are bitwise equal to the per-term launches: every tile and camera computes the same
+//   barrier  the last block to arrive opens it by arriving; the grid's last block (the stop-rule
+//            block, which takes no groups) waits for it, sums each running problem's camera norm
+//            pairs in camera order and applies its stop rule while the others run the next
+//            term's groups; every block sees the decisions before the next camera phase (a
+//            stopped problem's groups and cameras are skipped, so its x stays at the term where
+//            its rule fired).
+// Results are bitwise equal to the per-term launches: every group and camera computes the same
 // sums in the same order whichever block runs it.
 //
 // Every barrier wait is bounded: after `timeout` clock cycles a block sets the error flag and
@@ -237,29 +238,37 @@ __device__ __forceinline__ void round_writeback(const RoundCache& rc, double* __
   if (rc.rd >= 0 && it < rc.nc) x[(size_t)rc.cam[it][0] * 9 + k] = rc.x[it][k];
 }
 
-// Barrier 2 of a term: the last block opens it, then applies every running problem's stop rule
-// for term i (visible to every block before the next barrier).  False: this block must leave
-// (a wait timed out or another block failed).
+// The stop-rule block of a persistent launch: the grid's last block.  It takes no groups; at the
+// end of each term it waits for every camera of the term, then applies every running problem's
+// stop rule while the other blocks already run the next term's groups, and only then arrives
+// at that term's first barrier -- so every block sees the decisions before the next camera
+// phase, and the reduction of the camera norms (thousands of cameras for a large problem) is
+// off the critical path.
+__device__ __forceinline__ bool stop_block() { return blockIdx.x == gridDim.x - 1; }
+
+// Barrier 2 of a term.  False: this block must leave (a wait timed out or another block
+// failed).  The stop-rule block waits for the barrier and then applies the stop rule of term i;
+// every other block leaves as soon as the barrier is complete.
 __device__ __forceinline__ bool term_end_barrier(const Topology& tp, GridSync* gs,
                                                  const double* cam_norm, SeriesState* st,
                                                  SeriesGlobal* sgl, int i, double eps,
                                                  long long timeout, int* s_last, unsigned* s_gen,
                                                  int* s_ok, int* s_running) {
   unsigned target;
-  if (barrier_arrive(gs, gridDim.x, &target, s_last, s_gen)) {
-    __threadfence();
-    problems_stop_rule(tp, cam_norm, st, sgl, i, eps, s_running);
-    return true;
-  }
-  return barrier_wait(gs, target, timeout, s_ok);
+  const bool last = barrier_arrive(gs, gridDim.x, &target, s_last, s_gen);
+  if (!stop_block()) return last || barrier_wait(gs, target, timeout, s_ok);
+  if (!last && !barrier_wait(gs, target, timeout, s_ok)) return false;
+  __threadfence();
+  problems_stop_rule(tp, cam_norm, st, sgl, i, eps, s_running);
+  return true;
 }
 
-// Barrier 1 of a term (after the tile phase): the last block resets the tile counter.
+// Barrier 1 of a term (after the group phase): the last block resets the ticket counter.
 __device__ __forceinline__ bool tile_end_barrier(GridSync* gs, long long timeout, int* s_last,
                                                  unsigned* s_gen, int* s_ok) {
   unsigned target;
   if (barrier_arrive(gs, gridDim.x, &target, s_last, s_gen)) {
-    // no block claims tiles again before the term's second barrier, which this block reaches
+    // no block claims groups again before the term's second barrier, which this block reaches
     // after the reset (its arrival there publishes it)
     if (threadIdx.x == 0) atomicExch(&gs->tile_next, 0u);
     return true;
@@ -268,14 +277,15 @@ __device__ __forceinline__ bool tile_end_barrier(GridSync* gs, long long timeout
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTileObs, sizeof(T) == 4 ? 4 : 3) series_persistent_kernel(
-    Topology tp, CamRounds cr, const T* __restrict__ J, const T* __restrict__ Vinv,
+__global__ void __launch_bounds__(kChunkObs, sizeof(T) == 4 ? 4 : 3) series_persistent_kernel(
+    Topology tp, SerTopo sp, CamRounds cr, const T* __restrict__ J, const T* __restrict__ Vinv,
     const double* __restrict__ Uinv, double* __restrict__ x, T* __restrict__ t_cam,
     T* __restrict__ partial, double* __restrict__ cam_norm, SeriesState* __restrict__ st,
     SeriesGlobal* __restrict__ sgl, GridSync* __restrict__ gs, int m_max, double eps,
     long long timeout, long long* __restrict__ trace) {
-  __shared__ TileSmem<T> sm;
-  __shared__ int s_tile, s_last, s_ok, s_done, s_running;
+  extern __shared__ __align__(16) unsigned char group_smem[];
+  GroupSmem<T>& sm = *reinterpret_cast<GroupSmem<T>*>(group_smem);
+  __shared__ int s_group, s_last, s_ok, s_done, s_running;
   __shared__ unsigned s_gen;
   static_assert(kCamScratchBytes <= sizeof(sm.sg), "phase B scratch fits in sg");
   const int tid = threadIdx.x;
@@ -286,40 +296,23 @@ __global__ void __launch_bounds__(kTileObs, sizeof(T) == 4 ? 4 : 3) series_persi
   if (s_done) return;
   __shared__ RoundCache rc;
   round_cache(tp, cr, x, rc);
-  const bool tracer = blockIdx.x == gridDim.x - 1 && tid == 0 && trace != nullptr;
+  const bool tracer = blockIdx.x == 0 && tid == 0 && trace != nullptr;
   for (int i = 1; i <= m_max; ++i) {
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 0] = global_ns();
-    // ---- phase A: tiles.  Thread 0 claims the next ticket while the current tile is
-    // processed and reads the all-stopped flag for the claim after that, so neither round trip
-    // holds the block (tickets at or past n_tiles mean none).  Once every problem has stopped
-    // the remaining tiles are moot (a block may still take one); in a batch, tiles of a problem
-    // that stopped are skipped.
-    int next = 0, stop_seen = 0;
-    if (tid == 0) {
-      stop_seen = ld_volatile(&sgl->all_done) || (tp.n_probs == 1 && ld_volatile(&st[0].done));
-      next = stop_seen ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
-    }
+    // ---- phase A: groups by ticket (not the stop-rule block).  Once every problem has stopped
+    // the remaining groups are moot; in a batch, groups of a problem that stopped are skipped.
     for (;;) {
+      if (stop_block()) break;
       if (tid == 0) {
-        int cur = next < tp.n_tiles ? next : tp.n_tiles;
-        if (tp.n_probs > 1) {
-          while (cur < tp.n_tiles && ld_volatile(&st[tp.tile_prob[cur]].done)) {
-            cur = ld_volatile(&sgl->all_done) ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
-            if (cur > tp.n_tiles) cur = tp.n_tiles;
-          }
-        }
-        s_tile = cur;
-        if (cur < tp.n_tiles) next = stop_seen ? tp.n_tiles : (int)atomicAdd(&gs->tile_next, 1u);
-        stop_seen = ld_volatile(&sgl->all_done);  // used by the next claim
+        int g = ld_volatile(&sgl->all_done) ? sp.n_groups : (int)atomicAdd(&gs->tile_next, 1u);
+        while (g < sp.n_groups && ld_volatile(&st[__ldg(sp.group + 2 * g + 1).y].done))
+          g = ld_volatile(&sgl->all_done) ? sp.n_groups : (int)atomicAdd(&gs->tile_next, 1u);
+        s_group = g < sp.n_groups ? g : sp.n_groups;
       }
-      __syncthreads();
-      const int tile = s_tile;
-      __syncthreads();
-      if (tile >= tp.n_tiles) break;
-      if constexpr (sizeof(T) == 4)
-        tile_matvec_body_f32<kModeSeries>(tp, tile, J, t_cam, nullptr, Vinv, partial, sm);
-      else
-        tile_matvec_body<T, kModeSeries>(tp, tile, J, t_cam, nullptr, Vinv, partial, sm);
+      __syncthreads();  // also: every thread is done with the previous group's shared memory
+      const int g = s_group;
+      if (g >= sp.n_groups) break;
+      group_body<T, kModeSeries>(tp, sp, g, J, t_cam, nullptr, Vinv, partial, sm);
     }
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 1] = global_ns();
     if (!tile_end_barrier(gs, timeout, &s_last, &s_gen, &s_ok)) return;
@@ -339,47 +332,40 @@ __global__ void __launch_bounds__(kTileObs, sizeof(T) == 4 ? 4 : 3) series_persi
 }
 
 // ---------------------------------------------------------------------------------------
-// FP32-bulk persistent kernel with a software-pipelined tile phase.  The tile body is the one
-// of the per-term kernel (f32_tile_core: the same sums in the same order); what changes is how
-// a tile's inputs reach shared memory.  A block's tiles are claimed ahead and their inputs
-// arrive while earlier tiles compute:
-//   descriptor    32-byte asynchronous copy, three tiles ahead;
-//   index record  one bulk copy (cp.async.bulk, completion on an mbarrier), two tiles ahead;
-//   Jacobians     24 bulk copies (one per plane, the tile's range rounded out to 16 bytes), one
-//                 tile ahead, issued as soon as the current tile's J has moved to registers;
-//   t rows, V^-1  asynchronous copies issued in the middle of the previous tile, once its
-//                 index record (slot rows) has arrived.
-// The tiles come from a list of descriptors (the handle's tiles, or for a batch the tiles of
-// the problems taking part in the solve); any block may take any tile (one atomic ticket per
-// tile).  A block that finds no tile leaves the phase with nothing in flight.  Every mbarrier
-// wait is bounded (kCopyWaitCycles); a block that gives up sets the error flag, waits (bounded)
-// for the copies it started, and leaves; the others leave at their next grid barrier.
-constexpr int kJStage = kTileObs + 4;  // floats per staged plane: the tile range rounded out
-
-struct __align__(16) F32Pipe {
-  float sJ[24][kJStage];
-  uint8_t rec[3][kTileRecMax];
-  float tc[2][kTileSlots][kTStride];
-  float vi[2][kTileLms][6];
-  float sv[kTileObs][3];
-  float sg[kTileObs][9];  // the scatter; phase B's doubles
-  int4 desc[4][2];
-  unsigned long long mbJ;
-  unsigned long long mbR[3];
+// FP32-bulk persistent kernel with staged chunks (series_exec 4).  The arithmetic is the group
+// body's (chunk_f32_core: the same sums in the same order as every other form); what changes is
+// how a chunk's inputs reach the threads.  One thread copies each chunk -- its six Jacobian
+// plane groups, its record and its landmarks' V^-1 rows -- into shared memory with bulk
+// asynchronous copies (cp.async.bulk, completion counted on an mbarrier), one chunk ahead: the
+// copies of chunk k + 1 go out once every thread holds chunk k's inputs in registers (the first
+// barrier of chunk k), so they arrive while chunk k computes.  The next group is claimed one
+// group ahead, so the stream of copies runs across group boundaries.  Every mbarrier wait is
+// bounded (kCopyWaitCycles); a block whose wait gives up leaves with the error flag set after
+// waiting (bounded) for the copy it started; the other blocks leave at their next grid barrier.
+struct __align__(16) F32Stage {
+  float4 J[6][kChunkObs];                    // plane groups 0..5 of the chunk's observations
+  alignas(16) uint8_t rec[kChunkRecMax];     // the chunk record
+  alignas(16) float vi[kChunkObs * 6 + 8];   // V^-1 rows of its landmarks (range rounded out)
+  unsigned long long mbar;
 };
-static_assert(offsetof(F32Pipe, rec) % 16 == 0 && offsetof(F32Pipe, tc) % 16 == 0 &&
-                  offsetof(F32Pipe, vi) % 16 == 0 && offsetof(F32Pipe, sg) % 16 == 0 &&
-                  offsetof(F32Pipe, sv) % 16 == 0 &&
-                  offsetof(F32Pipe, desc) % 16 == 0 && offsetof(F32Pipe, mbJ) % 8 == 0,
+static_assert(offsetof(F32Stage, rec) % 16 == 0 && offsetof(F32Stage, vi) % 16 == 0 &&
+                  offsetof(F32Stage, mbar) % 8 == 0 && kChunkRecMax % 16 == 0,
               "bulk-copy destinations must be 16-byte aligned");
-static_assert((kJStage * 4) % 16 == 0 && kTileRecMax % 16 == 0, "16-byte rows");
-static_assert(kCamScratchBytes <= sizeof(float) * kTileObs * 9, "phase B scratch fits in sg");
+
+struct StagedSmem {
+  GroupSmem<float> g;
+  F32Stage s;
+};
+
+// Bound on a wait for this block's own copies (about 4 s at 2 GHz).
+constexpr long long kCopyWaitCycles = 1LL << 33;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
 __device__ __forceinline__ void mbar_init(unsigned long long* mb) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mb)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 __device__ __forceinline__ void mbar_arm(unsigned long long* mb, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mb)),
@@ -396,10 +382,6 @@ __device__ __forceinline__ bool mbar_try(unsigned long long* mb, unsigned parity
       : "memory");
   return ok != 0;
 }
-// Bound on a wait for this block's own copies (about 4 s at 2 GHz).  Independent of the grid
-// barrier limit: a copy that was started is always waited for.
-constexpr long long kCopyWaitCycles = 1LL << 33;
-
 // Bounded wait for the phase with the given parity; false after `timeout` cycles.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* mb, unsigned parity,
                                           long long timeout) {
@@ -416,228 +398,201 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       "l"(src), "r"(bytes), "r"(smem_u32(mb))
       : "memory");
 }
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Warp 0: bulk copies of the 24 Jacobian planes of the tile {o0, n} into sJ, one plane per lane
-// (lane 0 arms the barrier first).
-__device__ __forceinline__ void issue_J(F32Pipe& S, const float* __restrict__ J, size_t pad,
-                                        int o0, int n, int lane) {
-  const int a0 = o0 & ~3, e = (o0 + n + 3) & ~3;
-  const unsigned bytes = (unsigned)(e - a0) * 4u;
-  if (lane == 0) mbar_arm(&S.mbJ, n > 0 ? 24u * bytes : 0u);
-  __syncwarp();
-  if (n > 0 && lane < 24) bulk_g2s(&S.sJ[lane][0], J + (size_t)lane * pad + a0, bytes, &S.mbJ);
-}
-
-// Thread 0: bulk copy of a tile's index record into ring slot r.
-__device__ __forceinline__ void issue_rec(F32Pipe& S, const uint8_t* __restrict__ recs, int r,
-                                          const int4 (&d)[2]) {
-  const unsigned bytes = (unsigned)tile_rec_layout(d[0].w, d[1].y, d[0].y).bytes;
-  mbar_arm(&S.mbR[r], bytes);
-  bulk_g2s(&S.rec[r][0], recs + (size_t)d[1].z * 16, bytes, &S.mbR[r]);
+// One thread: bulk copies of the chunk with descriptor {d0, d1} into the stage (the stage's
+// previous contents have been read by every thread: the caller is past a block barrier that
+// follows the last read).
+__device__ __forceinline__ void f32_issue(F32Stage& S, const SerTopo& sp, const int4& d0,
+                                          const int4& d1, const float* __restrict__ J, size_t pad,
+                                          const float* __restrict__ Vinv) {
+  const int o0 = d0.x, n = d0.y, L0 = d0.z, nl = d0.w;
+  const unsigned jb = (unsigned)n * 16u;
+  const unsigned rb = (unsigned)chunk_rec_layout(n, nl, d1.x).bytes;
+  const size_t v0 = ((size_t)L0 * 6) & ~(size_t)3, v1 = ((size_t)(L0 + nl) * 6 + 3) & ~(size_t)3;
+  const unsigned vb = (unsigned)(v1 - v0) * 4u;
+  // the stage was last read through the generic proxy; order those reads before the copies
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_arm(&S.mbar, 6u * jb + rb + vb);
+  const float4* G = reinterpret_cast<const float4*>(J);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) bulk_g2s(&S.J[q][0], G + (size_t)q * pad + o0, jb, &S.mbar);
+  bulk_g2s(S.rec, sp.rec + (size_t)d1.y * 16, rb, &S.mbar);
+  bulk_g2s(S.vi, Vinv + v0, vb, &S.mbar);
 }
 
-__global__ void __launch_bounds__(kTileObs, 3) series_persistent_f32_kernel(
-    Topology tp, CamRounds cr, const int4* __restrict__ list, const int* __restrict__ n_list_p,
-    const float* __restrict__ J, const float* __restrict__ Vinv, const double* __restrict__ Uinv,
-    double* __restrict__ x, float* __restrict__ t_cam, float* __restrict__ partial,
-    double* __restrict__ cam_norm, SeriesState* __restrict__ st, SeriesGlobal* __restrict__ sgl,
-    GridSync* __restrict__ gs, int m_max, double eps, long long timeout,
-    long long* __restrict__ trace) {
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
-  F32Pipe& S = *reinterpret_cast<F32Pipe*>(dyn_smem);
-  __shared__ int s_last, s_ok, s_done, s_running, s_fail;
-  __shared__ int s_tk[4];  // tickets of the tiles in desc[] (>= n_list: none)
-  __shared__ unsigned s_gen;
+// The inputs of an active thread from the staged chunk.
+__device__ __forceinline__ void f32_load_staged(const F32Stage& S, const int4& d0,
+                                                const ChunkRecLayout& L, F32Obs& x) {
+  const int tid = threadIdx.x;
+  float all[24];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) unpack16(S.J[q][tid], all + 4 * q);
+#pragma unroll
+  for (int p = 0; p < 18; ++p) x.jp[p] = all[p];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) x.jl[p] = all[18 + p];
+  x.code = reinterpret_cast<const uint32_t*>(S.rec + L.code)[tid];
+  const int lm = (int)(x.code >> 16) & 0xff;
+  const uint16_t* sseg = reinterpret_cast<const uint16_t*>(S.rec + L.sseg);
+  x.a = sseg[lm];
+  x.b = sseg[lm + 1];
+  f32_vinv(x, S.vi + (((size_t)d0.z * 6) & 3) + (size_t)lm * 6);
+}
+
+// The issuing thread of the staged kernel: the first lane of the last warp, whose share of a
+// chunk's slot sums is the smallest (chunk slots are ordered longest first).
+constexpr int kIssuer = kChunkObs - 32;
+
+// Ticket of the next group whose problem still runs (n_groups: none).
+__device__ __forceinline__ int claim_group(const SerTopo& sp, const SeriesState* st,
+                                           const SeriesGlobal* sgl, GridSync* gs) {
+  int g = ld_volatile(&sgl->all_done) ? sp.n_groups : (int)atomicAdd(&gs->tile_next, 1u);
+  while (g < sp.n_groups && ld_volatile(&st[__ldg(sp.group + 2 * g + 1).y].done))
+    g = ld_volatile(&sgl->all_done) ? sp.n_groups : (int)atomicAdd(&gs->tile_next, 1u);
+  return g < sp.n_groups ? g : sp.n_groups;
+}
+
+// Phase A of one term with staged chunks.  Returns false (in every thread) if a copy wait gave
+// up; thread 0 has then waited (bounded) for the copy it had started.
+__device__ __forceinline__ bool groups_staged(const Topology& tp, const SerTopo& sp,
+                                              const float* __restrict__ J,
+                                              const float* __restrict__ Vinv,
+                                              const float* __restrict__ t_cam,
+                                              float* __restrict__ partial, StagedSmem& sm,
+                                              unsigned& par, const SeriesState* st,
+                                              const SeriesGlobal* sgl, GridSync* gs,
+                                              int* s_group) {
   const int tid = threadIdx.x;
   const size_t pad = (size_t)tp.n_obs_pad;
-  double* scratch = reinterpret_cast<double*>(&S.sg[0][0]);  // phase B reuses sg
+  // The issuing thread walks the block's stream of chunks one chunk ahead of the copies in
+  // flight: pend is the next chunk to copy (-1: none), with its descriptor already loaded so that
+  // issuing waits on no load, and pend_end the end of its group's chunk range.  When the walk
+  // leaves a group it claims the next one (a ticket taken about a chunk before the group
+  // starts, so that blocks reserve no more work than they are about to run) and queues it for
+  // the group loop (at most two groups ahead of the current one).
+  int pend = -1, pend_end = 0, qa = sp.n_groups, qb = sp.n_groups;
+  int4 pd0 = make_int4(0, 0, 0, 0), pd1 = pd0;
+  auto fetch = [&](int c) {
+    pend = c;
+    if (c >= 0) {
+      pd0 = __ldg(sp.chunk + 2 * c);
+      pd1 = __ldg(sp.chunk + 2 * c + 1);
+    }
+  };
+  // the chunk after pend in the stream
+  auto advance = [&]() {
+    if (pend + 1 < pend_end) {
+      fetch(pend + 1);
+      return;
+    }
+    const int g2 = claim_group(sp, st, sgl, gs);
+    if (g2 >= sp.n_groups) {
+      fetch(-1);
+      return;
+    }
+    if (qa >= sp.n_groups) qa = g2;
+    else qb = g2;
+    const int4 ge = __ldg(sp.group + 2 * g2);
+    pend_end = ge.x + ge.y;
+    fetch(ge.x);
+  };
+  if (tid == kIssuer) {
+    const int g = claim_group(sp, st, sgl, gs);
+    *s_group = g;
+    if (g < sp.n_groups) {
+      const int4 gd = __ldg(sp.group + 2 * g);
+      pend_end = gd.x + gd.y;
+      fetch(gd.x);
+      f32_issue(sm.s, sp, pd0, pd1, J, pad, Vinv);
+      advance();
+    }
+  }
+  __syncthreads();
+  int g = *s_group;
+  while (g < sp.n_groups) {
+    const int4 gd = __ldg(sp.group + 2 * g);
+    const int c0 = gd.x, nc = gd.y, s0 = gd.z, ns_g = gd.w;
+    for (int i = tid; i < ns_g * 3; i += kChunkObs) {
+      const int s = i / 3, q = i - 3 * s;
+      sm.g.acc[s][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const int cam = __ldg(sp.gslot_cam + s0 + s);
+      sm.g.tc[s][q] = __ldcg(reinterpret_cast<const float4*>(t_cam + (size_t)cam * kTStride) + q);
+    }
+    __syncthreads();
+    for (int c = c0; c < c0 + nc; ++c) {
+      const unsigned wait_par = par;
+      const bool ok = mbar_wait(&sm.s.mbar, wait_par, kCopyWaitCycles);
+      par ^= 1u;
+      const int4 d0 = __ldg(sp.chunk + 2 * c), d1 = __ldg(sp.chunk + 2 * c + 1);
+      const int n = d0.y, ns = d1.x;
+      const ChunkRecLayout L = chunk_rec_layout(n, d0.w, ns);
+      const bool active = tid < n;
+      F32Obs x;
+      if (active) f32_load_staged(sm.s, d0, L, x);
+      else f32_clear(x);
+      x.cl = tid < ns ? reinterpret_cast<const uint32_t*>(sm.s.rec + L.clist)[tid] : 0u;
+      bool issued = false;
+      const bool all_ok = chunk_f32_core<kModeSeries>(x, active, n, ns, c & 1, 0.f, 0.f, 0.f, ok,
+                                                      sm.g, [&] {
+        if (tid == kIssuer && pend >= 0) {
+          f32_issue(sm.s, sp, pd0, pd1, J, pad, Vinv);
+          issued = true;
+        }
+      });
+      if (!all_ok) {
+        if (tid == kIssuer) mbar_wait(&sm.s.mbar, wait_par, kCopyWaitCycles);
+        return false;
+      }
+      // the walk's next step (descriptor loads, at a group's end a ticket) after the chunk's
+      // slot sums, where the issuing warp (the last, with the shortest slots) has slack
+      if (issued) advance();
+    }
+    __syncthreads();
+    for (int i = tid; i < ns_g * 9; i += kChunkObs) {
+      const int s = i / 9, k = i - 9 * s;
+      partial[(size_t)__ldg(sp.gslot_row + s0 + s) * 9 + k] =
+          reinterpret_cast<const float*>(sm.g.acc[s])[k];
+    }
+    if (tid == kIssuer) {
+      // the next group: the oldest one the walk claimed (its first chunk is in flight)
+      *s_group = qa;
+      qa = qb;
+      qb = sp.n_groups;
+    }
+    __syncthreads();
+    g = *s_group;
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kChunkObs, 3) series_staged_kernel(
+    Topology tp, SerTopo sp, CamRounds cr, const float* __restrict__ J,
+    const float* __restrict__ Vinv, const double* __restrict__ Uinv, double* __restrict__ x,
+    float* __restrict__ t_cam, float* __restrict__ partial, double* __restrict__ cam_norm,
+    SeriesState* __restrict__ st, SeriesGlobal* __restrict__ sgl, GridSync* __restrict__ gs,
+    int m_max, double eps, long long timeout, long long* __restrict__ trace) {
+  extern __shared__ __align__(16) unsigned char staged_smem[];
+  StagedSmem& sm = *reinterpret_cast<StagedSmem*>(staged_smem);
+  __shared__ int s_group, s_last, s_ok, s_done, s_running;
+  __shared__ unsigned s_gen;
+  static_assert(kCamScratchBytes <= sizeof(sm.g.sg), "phase B scratch fits in sg");
+  const int tid = threadIdx.x;
+  double* scratch = reinterpret_cast<double*>(&sm.g.sg[0][0]);  // phase B reuses sg
 
   if (tid == 0) {
-    s_done = ld_volatile(&sgl->all_done);
-    s_fail = 0;
-    mbar_init(&S.mbJ);
-    for (int r = 0; r < 3; ++r) mbar_init(&S.mbR[r]);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_done = ld_volatile(&sgl->all_done);  // every x(0) = 0: nothing to do
+    mbar_init(&sm.s.mbar);
   }
   __syncthreads();
   if (s_done) return;
-  const int n_list = *n_list_p;
   __shared__ RoundCache rc;
   round_cache(tp, cr, x, rc);
-  unsigned parJ = 0u, parR = 0u;  // phase parity of mbJ and of mbR[0..2] (bit r)
-  unsigned pend = 0u;  // armed barriers not yet waited for (bit r: mbR[r], bit 3: mbJ)
-  const bool tracer = blockIdx.x == gridDim.x - 1 && tid == 0 && trace != nullptr;
-
+  unsigned par = 0u;  // parity of the stage's next mbarrier phase
+  const bool tracer = blockIdx.x == 0 && tid == 0 && trace != nullptr;
   for (int i = 1; i <= m_max; ++i) {
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 0] = global_ns();
-    // ---- phase A, prologue: claim three tiles, fetch their descriptors, start the first
-    // two records and the first Jacobians
-    int tk_next = n_list;  // thread 0: ticket claimed for the slot after the last filled one
-    int stop_seen = 0;     // thread 0: the all-stopped flag as of the previous claim
-    if (tid < 32) {
-      if (tid == 0) {
-        int t0 = n_list;
-        if (!ld_volatile(&sgl->all_done)) t0 = (int)atomicAdd(&gs->tile_next, 3u);
-        for (int q = 0; q < 3; ++q) {
-          const int tk = t0 + q < n_list ? t0 + q : n_list;
-          s_tk[q] = tk;
-          if (tk < n_list) {
-            cp_async16(&S.desc[q][0], list + 2 * (size_t)tk);
-            cp_async16(&S.desc[q][1], list + 2 * (size_t)tk + 1);
-          }
-        }
-        cp_async_wait_all();
-        if (t0 + 2 < n_list) tk_next = (int)atomicAdd(&gs->tile_next, 1u);
-        if (s_tk[0] < n_list) {
-          issue_rec(S, tp.tile_rec, 0, S.desc[0]);
-          pend |= 9u;
-        }
-        if (s_tk[1] < n_list) {
-          issue_rec(S, tp.tile_rec, 1, S.desc[1]);
-          pend |= 2u;
-        }
-      }
-      __syncwarp();
-      if (s_tk[0] < n_list) issue_J(S, J, pad, S.desc[0][0].z, S.desc[0][0].w, tid);
-    }
-    __syncthreads();
-    if (s_tk[0] < n_list) {
-      // t rows and V^-1 of the first tile
-      const bool ok = mbar_wait(&S.mbR[0], parR & 1u, kCopyWaitCycles);
-      if (ok) {
-        parR ^= 1u;
-        pend &= ~1u;
-      } else {
-        s_fail = 1;
-      }
-      const int4 d0 = S.desc[0][0], d1 = S.desc[0][1];
-      const TileRecLayout g = tile_rec_layout(d0.w, d1.y, d0.y);
-      const int* scam = reinterpret_cast<const int*>(&S.rec[0][g.scam]);
-      if (ok && tid < d1.y) {  // the record's slot cameras are valid only once it has arrived
-        const float* src = t_cam + (size_t)scam[tid] * kTStride;
-        cp_async16(&S.tc[0][tid][0], src);
-        cp_async16(&S.tc[0][tid][4], src + 4);
-        cp_async16(&S.tc[0][tid][8], src + 8);
-      }
-      if (tid < d0.y) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) cp_async4(&S.vi[0][tid][k], Vinv + (size_t)(d0.x + tid) * 6 + k);
-      }
-      cp_async_commit();
-    }
-    // ---- phase A, steady state: tile k uses desc[k % 4], rec[k % 3], tc / vi[k % 2]
-    for (int k = 0;; ++k) {
-      const int dk = k & 3, rk = k % 3, bk = k & 1;
-      if (s_tk[dk] >= n_list || s_fail) break;
-      if (mbar_wait(&S.mbJ, parJ, kCopyWaitCycles)) {
-        parJ ^= 1u;
-        pend &= ~8u;
-      } else {
-        s_fail = 1;
-      }
-      cp_async_wait_all();
-      __syncthreads();
-      if (s_fail) break;
-      const int4 d0 = S.desc[dk][0], d1 = S.desc[dk][1];
-      const int nl = d0.y, o0 = d0.z, n = d0.w, ns = d1.y;
-      const TileRecLayout g = tile_rec_layout(n, ns, nl);
-      const uint8_t* rec = S.rec[rk];
-      const bool active = tid < n;
-      float jp[18], jl[6];
-      int meta = 0, lm = 0;
-      if (active) {
-        const int sh = (o0 & 3) + tid;
-#pragma unroll
-        for (int p = 0; p < 18; ++p) jp[p] = S.sJ[p][sh];
-#pragma unroll
-        for (int p = 0; p < 6; ++p) jl[p] = S.sJ[18 + p][sh];
-        meta = reinterpret_cast<const uint16_t*>(rec + g.meta)[tid];
-        lm = rec[g.olm + tid];
-      }
-      const int k1 = (k + 1) & 3, k2 = (k + 2) & 3, k3 = (k + 3) & 3;
-      // after the core's first barrier every thread holds its J in registers and is past the
-      // start of this tile: refill sJ, the record ring and the descriptor ring for the tiles
-      // ahead, and fetch the next tile's t rows and V^-1 once its record has arrived
-      auto ahead = [&]() {
-        if (tid < 32) {
-          if (s_tk[k1] < n_list) {
-            issue_J(S, J, pad, S.desc[k1][0].z, S.desc[k1][0].w, tid);
-            if (tid == 0) pend |= 8u;
-          }
-          if (tid == 0) {
-            if (s_tk[k2] < n_list) {
-              issue_rec(S, tp.tile_rec, (k + 2) % 3, S.desc[k2]);
-              pend |= 1u << ((k + 2) % 3);
-            }
-            // the ticket claimed one tile ago (at or past n_list: none) and the all-stopped
-            // flag read then: neither round trip is waited for in the tile that starts it
-            const int tk = tk_next;
-            s_tk[k3] = tk;
-            tk_next = n_list;
-            if (tk < n_list) {
-              cp_async16(&S.desc[k3][0], list + 2 * (size_t)tk);
-              cp_async16(&S.desc[k3][1], list + 2 * (size_t)tk + 1);
-              if (!stop_seen) tk_next = (int)atomicAdd(&gs->tile_next, 1u);
-            }
-            stop_seen = ld_volatile(&sgl->all_done);
-          }
-        }
-        if (s_tk[k1] >= n_list) {
-          cp_async_commit();
-          return;
-        }
-        const int r1 = (k + 1) % 3;
-        const bool ok = mbar_wait(&S.mbR[r1], (parR >> r1) & 1u, kCopyWaitCycles);
-        if (ok) {
-          parR ^= 1u << r1;
-          pend &= ~(1u << r1);
-        } else {
-          s_fail = 1;
-        }
-        const int4 e0 = S.desc[k1][0], e1 = S.desc[k1][1];
-        const TileRecLayout h = tile_rec_layout(e0.w, e1.y, e0.y);
-        const int* scam1 = reinterpret_cast<const int*>(&S.rec[r1][h.scam]);
-        if (ok && tid < e1.y) {
-          const float* src = t_cam + (size_t)scam1[tid] * kTStride;
-          cp_async16(&S.tc[bk ^ 1][tid][0], src);
-          cp_async16(&S.tc[bk ^ 1][tid][4], src + 4);
-          cp_async16(&S.tc[bk ^ 1][tid][8], src + 8);
-        }
-        if (tid < e0.y) {
-#pragma unroll
-          for (int q = 0; q < 6; ++q)
-            cp_async4(&S.vi[bk ^ 1][tid][q], Vinv + (size_t)(e0.x + tid) * 6 + q);
-        }
-        cp_async_commit();
-      };
-      f32_tile_core<kModeSeries, false>(active, n, ns, lm, meta, jp, jl, &S.tc[bk][0][0],
-                                        kTStride, &S.vi[bk][0][0], 6,
-                                        reinterpret_cast<const uint16_t*>(rec + g.sseg),
-                                        reinterpret_cast<const uint16_t*>(rec + g.sbeg),
-                                        reinterpret_cast<const int*>(rec + g.srow), S.sv, S.sg,
-                                        partial, ahead);
-    }
-    cp_async_wait_all();
-    __syncthreads();
-    if (s_fail) {
-      // let the bulk copies this block started finish (each wait bounded) before it leaves
-      if (tid == 0) {
-        atomicExch(&gs->error, 1);
-        if (pend & 8u) mbar_wait(&S.mbJ, parJ, kCopyWaitCycles);
-        for (int r = 0; r < 3; ++r)
-          if (pend & (1u << r)) mbar_wait(&S.mbR[r], (parR >> r) & 1u, kCopyWaitCycles);
-      }
-      __syncthreads();
+    if (!stop_block() && !groups_staged(tp, sp, J, Vinv, t_cam, partial, sm, par, st, sgl, gs, &s_group)) {
+      if (tid == 0) atomicExch(&gs->error, 1);
       return;
     }
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 1] = global_ns();
@@ -646,7 +601,6 @@ __global__ void __launch_bounds__(kTileObs, 3) series_persistent_f32_kernel(
     if (tid == 0) s_done = ld_volatile(&sgl->all_done);
     __syncthreads();
     if (s_done) break;
-    // ---- phase B: cameras
     camera_phase<float>(tp, cr, rc, partial, Uinv, x, t_cam, cam_norm, st, scratch);
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 3] = global_ns();
     if (!term_end_barrier(tp, gs, cam_norm, st, sgl, i, eps, timeout, &s_last, &s_gen, &s_ok,
@@ -657,59 +611,71 @@ __global__ void __launch_bounds__(kTileObs, 3) series_persistent_f32_kernel(
   round_writeback(rc, x);
 }
 
-int persistent_blocks_per_sm(bool f32) {
+int staged_blocks_per_sm() {
+  if (cudaFuncSetAttribute(series_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(StagedSmem)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   int nb = 0;
-  if (f32)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, series_persistent_kernel<float>, kTileObs, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, series_persistent_kernel<double>, kTileObs, 0);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, series_staged_kernel, kChunkObs,
+                                                    sizeof(StagedSmem)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
   return nb;
 }
 
-int pipelined_blocks_per_sm() {
-  if (cudaFuncSetAttribute(series_persistent_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(F32Pipe)) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, series_persistent_f32_kernel, kTileObs,
-                                                    sizeof(F32Pipe)) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return nb;
+cudaError_t launch_series_staged(const Topology& tp, const SerTopo& sp, const CamRounds& cr,
+                                 int grid, const float* J, const float* Vinv, const double* Uinv,
+                                 double* x, float* t_cam, float* partial, double* cam_norm,
+                                 SeriesState* st, SeriesGlobal* sgl, GridSync* gs, int m_max,
+                                 double eps, long long timeout, long long* trace,
+                                 cudaStream_t s) {
+  void* args[] = {(void*)&tp, (void*)&sp, (void*)&cr, (void*)&J, (void*)&Vinv, (void*)&Uinv,
+                  (void*)&x, (void*)&t_cam, (void*)&partial, (void*)&cam_norm, (void*)&st,
+                  (void*)&sgl, (void*)&gs, (void*)&m_max, (void*)&eps, (void*)&timeout,
+                  (void*)&trace};
+  return cudaLaunchCooperativeKernel((const void*)series_staged_kernel, dim3(grid),
+                                     dim3(kChunkObs), args, sizeof(StagedSmem), s);
 }
 
 template <typename T>
-cudaError_t launch_series_persistent(const Topology& tp, const CamRounds& cr, int grid, const T* J, const T* Vinv,
-                                     const double* Uinv, double* x, T* t_cam, T* partial,
-                                     double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
-                                     GridSync* gs, int m_max, double eps, long long timeout,
-                                     long long* trace, cudaStream_t s) {
-  void* args[] = {(void*)&tp, (void*)&cr, (void*)&J, (void*)&Vinv, (void*)&Uinv, (void*)&x,
-                  (void*)&t_cam, (void*)&partial, (void*)&cam_norm, (void*)&st, (void*)&sgl,
-                  (void*)&gs, (void*)&m_max, (void*)&eps, (void*)&timeout, (void*)&trace};
+int blocks_per_sm_of() {
+  if (cudaFuncSetAttribute(series_persistent_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(GroupSmem<T>)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, series_persistent_kernel<T>, kChunkObs,
+                                                    sizeof(GroupSmem<T>)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
+int persistent_blocks_per_sm(bool f32) {
+  return f32 ? blocks_per_sm_of<float>() : blocks_per_sm_of<double>();
+}
+
+template <typename T>
+cudaError_t launch_series_persistent(const Topology& tp, const SerTopo& sp, const CamRounds& cr,
+                                     int grid, const T* J, const T* Vinv, const double* Uinv,
+                                     double* x, T* t_cam, T* partial, double* cam_norm,
+                                     SeriesState* st, SeriesGlobal* sgl, GridSync* gs, int m_max,
+                                     double eps, long long timeout, long long* trace,
+                                     cudaStream_t s) {
+  void* args[] = {(void*)&tp, (void*)&sp, (void*)&cr, (void*)&J, (void*)&Vinv, (void*)&Uinv,
+                  (void*)&x, (void*)&t_cam, (void*)&partial, (void*)&cam_norm, (void*)&st,
+                  (void*)&sgl, (void*)&gs, (void*)&m_max, (void*)&eps, (void*)&timeout,
+                  (void*)&trace};
   return cudaLaunchCooperativeKernel((const void*)series_persistent_kernel<T>, dim3(grid),
-                                     dim3(kTileObs), args, 0, s);
+                                     dim3(kChunkObs), args, sizeof(GroupSmem<T>), s);
 }
 
-cudaError_t launch_series_pipelined(const Topology& tp, const CamRounds& cr, int grid,
-                                    const int4* list,
-                                    const int* n_list, const float* J, const float* Vinv,
-                                    const double* Uinv, double* x, float* t_cam, float* partial,
-                                    double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
-                                    GridSync* gs, int m_max, double eps, long long timeout,
-                                    long long* trace, cudaStream_t s) {
-  void* args[] = {(void*)&tp, (void*)&cr, (void*)&list, (void*)&n_list, (void*)&J, (void*)&Vinv,
-                  (void*)&Uinv, (void*)&x, (void*)&t_cam, (void*)&partial, (void*)&cam_norm,
-                  (void*)&st, (void*)&sgl, (void*)&gs, (void*)&m_max, (void*)&eps,
-                  (void*)&timeout, (void*)&trace};
-  return cudaLaunchCooperativeKernel((const void*)series_persistent_f32_kernel, dim3(grid),
-                                     dim3(kTileObs), args, sizeof(F32Pipe), s);
-}
-
-template cudaError_t launch_series_persistent<double>(const Topology&, const CamRounds&, int, const double*, const double*, const double*, double*, double*, double*, double*, SeriesState*, SeriesGlobal*, GridSync*, int, double, long long, long long*, cudaStream_t);
-template cudaError_t launch_series_persistent<float>(const Topology&, const CamRounds&, int, const float*, const float*, const double*, double*, float*, float*, double*, SeriesState*, SeriesGlobal*, GridSync*, int, double, long long, long long*, cudaStream_t);
+template cudaError_t launch_series_persistent<double>(const Topology&, const SerTopo&, const CamRounds&, int, const double*, const double*, const double*, double*, double*, double*, double*, SeriesState*, SeriesGlobal*, GridSync*, int, double, long long, long long*, cudaStream_t);
+template cudaError_t launch_series_persistent<float>(const Topology&, const SerTopo&, const CamRounds&, int, const float*, const float*, const double*, double*, float*, float*, double*, SeriesState*, SeriesGlobal*, GridSync*, int, double, long long, long long*, cudaStream_t);
 
 }  // namespace poba

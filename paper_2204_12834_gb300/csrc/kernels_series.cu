@@ -1,12 +1,12 @@
 // Per-term power-series kernels of libpoba (sm_103a), Sec. 4.3, and the LM helper kernels.
 //
-// One series term is two launches: tile_matvec_kernel (the tile body of series_body.cuh over all
-// tiles) and camera_step_kernel (the camera body over all cameras, then the stop rule of eq.
-// `qcriterion` in the last block to finish, which raises `done` so that later launches return at
-// once).  These launches are what the captured-graph path replays; the persistent kernel in
-// kernels_persistent.cu runs the same bodies in one launch.  Back-substitution (Sec. 4.2)
-// reuses the first half of the tile body and also accumulates the model decrease
-// 1/2||r||^2 - 1/2||r + J_p dx_p + J_l dx_l||^2.
+// One series term is two launches: series_group_kernel (the group body of series_body.cuh, one
+// block per group of the series schedule) and camera_step_kernel (the camera body over all
+// cameras, then the stop rule of eq. `qcriterion` in the last block to finish, which raises
+// `done` so that later launches return at once).  These launches are what the captured-graph
+// path replays; the persistent kernel in kernels_persistent.cu runs the same bodies in one
+// launch.  Back-substitution (Sec. 4.2) runs over the tile schedule and also accumulates the
+// model decrease 1/2||r||^2 - 1/2||r + J_p dx_p + J_l dx_l||^2.
 #include <cfloat>
 #include <cmath>
 
@@ -16,34 +16,48 @@
 
 namespace poba {
 
+// One block per group of the series schedule (the per-term forms; the persistent kernel runs
+// the same group body).  Groups of problems whose series has stopped return at once.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kTileObs) tile_matvec_kernel(
-    Topology tp, const T* __restrict__ J, const T* __restrict__ t_cam,
+__global__ void __launch_bounds__(kChunkObs) series_group_kernel(
+    Topology tp, SerTopo sp, const T* __restrict__ J, const T* __restrict__ t_cam,
     const double* __restrict__ b_l, const T* __restrict__ Vinv, T* __restrict__ partial,
     const SeriesState* __restrict__ st, const SeriesGlobal* __restrict__ sgl) {
-  __shared__ TileSmem<T> sm;
-  // every problem stopped, or this tile's problem stopped in an earlier term (uniform per block)
+  extern __shared__ __align__(16) unsigned char group_smem[];
+  GroupSmem<T>& sm = *reinterpret_cast<GroupSmem<T>*>(group_smem);
   if (MODE == kModeSeries && sgl->all_done) return;
-  if (st[tp.tile_prob[blockIdx.x]].done) return;
-  if constexpr (sizeof(T) == 4)
-    tile_matvec_body_f32<MODE>(tp, blockIdx.x, J, t_cam, b_l, Vinv, partial, sm);
-  else
-    tile_matvec_body<T, MODE>(tp, blockIdx.x, J, t_cam, b_l, Vinv, partial, sm);
+  if (st[__ldg(sp.group + 2 * blockIdx.x + 1).y].done) return;
+  group_body<T, MODE>(tp, sp, blockIdx.x, J, t_cam, b_l, Vinv, partial, sm);
 }
 
 template <typename T>
-void launch_tile_rhs(const Topology& tp, const T* J, const double* b_l, const T* Vinv, T* partial,
-                     const SeriesState* st, cudaStream_t s) {
-  tile_matvec_kernel<T, kModeRhs><<<tp.n_tiles, kTileObs, 0, s>>>(tp, J, nullptr, b_l, Vinv,
-                                                                  partial, st, nullptr);
+cudaError_t series_group_kernels_init() {
+  const int bytes = (int)sizeof(GroupSmem<T>);
+  cudaError_t e = cudaFuncSetAttribute(series_group_kernel<T, kModeSeries>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(series_group_kernel<T, kModeRhs>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+template cudaError_t series_group_kernels_init<float>();
+template cudaError_t series_group_kernels_init<double>();
+
+template <typename T>
+void launch_tile_rhs(const Topology& tp, const SerTopo& sp, const T* J, const double* b_l,
+                     const T* Vinv, T* partial, const SeriesState* st, cudaStream_t s) {
+  if (sp.n_groups == 0) return;
+  series_group_kernel<T, kModeRhs><<<sp.n_groups, kChunkObs, sizeof(GroupSmem<T>), s>>>(
+      tp, sp, J, nullptr, b_l, Vinv, partial, st, nullptr);
 }
 
 template <typename T>
-void launch_tile_series(const Topology& tp, const T* J, const T* t_cam, const T* Vinv,
-                        T* partial, const SeriesState* st, const SeriesGlobal* sgl,
+void launch_tile_series(const Topology& tp, const SerTopo& sp, const T* J, const T* t_cam,
+                        const T* Vinv, T* partial, const SeriesState* st, const SeriesGlobal* sgl,
                         cudaStream_t s) {
-  tile_matvec_kernel<T, kModeSeries><<<tp.n_tiles, kTileObs, 0, s>>>(tp, J, t_cam, nullptr, Vinv,
-                                                                     partial, st, sgl);
+  if (sp.n_groups == 0) return;
+  series_group_kernel<T, kModeSeries><<<sp.n_groups, kChunkObs, sizeof(GroupSmem<T>), s>>>(
+      tp, sp, J, t_cam, nullptr, Vinv, partial, st, sgl);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -127,10 +141,10 @@ void launch_tile_backsub(const Topology& tp, const T* J, const T* r, const doubl
   tile_backsub_kernel<T><<<tp.n_tiles, kTileObs, 0, s>>>(tp, J, r, x, b_l, Vinv, dx_l, block_pred);
 }
 
-template void launch_tile_rhs<double>(const Topology&, const double*, const double*, const double*, double*, const SeriesState*, cudaStream_t);
-template void launch_tile_rhs<float>(const Topology&, const float*, const double*, const float*, float*, const SeriesState*, cudaStream_t);
-template void launch_tile_series<double>(const Topology&, const double*, const double*, const double*, double*, const SeriesState*, const SeriesGlobal*, cudaStream_t);
-template void launch_tile_series<float>(const Topology&, const float*, const float*, const float*, float*, const SeriesState*, const SeriesGlobal*, cudaStream_t);
+template void launch_tile_rhs<double>(const Topology&, const SerTopo&, const double*, const double*, const double*, double*, const SeriesState*, cudaStream_t);
+template void launch_tile_rhs<float>(const Topology&, const SerTopo&, const float*, const double*, const float*, float*, const SeriesState*, cudaStream_t);
+template void launch_tile_series<double>(const Topology&, const SerTopo&, const double*, const double*, const double*, double*, const SeriesState*, const SeriesGlobal*, cudaStream_t);
+template void launch_tile_series<float>(const Topology&, const SerTopo&, const float*, const float*, const float*, float*, const SeriesState*, const SeriesGlobal*, cudaStream_t);
 template void launch_tile_backsub<double>(const Topology&, const double*, const double*, const double*, const double*, const double*, double*, double*, cudaStream_t);
 template void launch_tile_backsub<float>(const Topology&, const float*, const float*, const double*, const double*, const float*, double*, double*, cudaStream_t);
 
@@ -143,7 +157,8 @@ int camera_blocks(const Topology& tp) { return (tp.n_cams + kCamBlock - 1) / kCa
 // takes kCamBlock cameras (9 warps), so that the last block has warps for its many problems.
 template <typename PT, int MODE, int CS>
 __global__ void __launch_bounds__(CS * 9) camera_step_kernel(
-    Topology tp, const PT* __restrict__ partial, const double* __restrict__ b_p,
+    Topology tp, const int32_t* __restrict__ cam_ptr, const PT* __restrict__ partial,
+    const double* __restrict__ b_p,
     const double* __restrict__ Uinv, double* __restrict__ x, PT* __restrict__ t_cam,
     double* __restrict__ cam_norm, SeriesState* __restrict__ st, SeriesGlobal* __restrict__ sgl,
     int iter, double eps) {
@@ -152,8 +167,8 @@ __global__ void __launch_bounds__(CS * 9) camera_step_kernel(
   __shared__ int is_last, s_running;
   if (MODE == kModeSeries && sgl->all_done) return;
   const int tid = threadIdx.x;
-  camera_body<PT, MODE>(tp, blockIdx.x * CS, CS, partial, b_p, Uinv, x, t_cam, st, cam_norm, ys,
-                        y2);
+  camera_body<PT, MODE>(tp, cam_ptr, blockIdx.x * CS, CS, partial, b_p, Uinv, x, t_cam, st,
+                        cam_norm, ys, y2);
   if (tid == 0) {
     __threadfence();
     const unsigned ticket = atomicAdd(&sgl->counter, 1u);
@@ -167,37 +182,40 @@ __global__ void __launch_bounds__(CS * 9) camera_step_kernel(
 }
 
 template <typename PT, int MODE>
-void launch_camera_step(const Topology& tp, const PT* partial, const double* b_p,
-                        const double* Uinv, double* x, PT* t_cam, double* cam_norm,
-                        SeriesState* st, SeriesGlobal* sgl, int iter, double eps, cudaStream_t s) {
+void launch_camera_step(const Topology& tp, const SerTopo& sp, const PT* partial,
+                        const double* b_p, const double* Uinv, double* x, PT* t_cam,
+                        double* cam_norm, SeriesState* st, SeriesGlobal* sgl, int iter, double eps,
+                        cudaStream_t s) {
   constexpr int kSmall = 8;
   if (tp.n_probs <= 2)
     camera_step_kernel<PT, MODE, kSmall><<<(tp.n_cams + kSmall - 1) / kSmall, kSmall * 9, 0, s>>>(
-        tp, partial, b_p, Uinv, x, t_cam, cam_norm, st, sgl, iter, eps);
+        tp, sp.cam_ptr, partial, b_p, Uinv, x, t_cam, cam_norm, st, sgl, iter, eps);
   else
     camera_step_kernel<PT, MODE, kCamBlock><<<camera_blocks(tp), kCamBlock * 9, 0, s>>>(
-        tp, partial, b_p, Uinv, x, t_cam, cam_norm, st, sgl, iter, eps);
+        tp, sp.cam_ptr, partial, b_p, Uinv, x, t_cam, cam_norm, st, sgl, iter, eps);
 }
 
 template <typename PT>
-void launch_camera_rhs(const Topology& tp, const PT* partial, const double* b_p, const double* Uinv,
-                       double* x, PT* t_cam, double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
-                       cudaStream_t s) {
-  launch_camera_step<PT, kModeRhs>(tp, partial, b_p, Uinv, x, t_cam, cam_norm, st, sgl, 0, 0.0, s);
+void launch_camera_rhs(const Topology& tp, const SerTopo& sp, const PT* partial, const double* b_p,
+                       const double* Uinv, double* x, PT* t_cam, double* cam_norm,
+                       SeriesState* st, SeriesGlobal* sgl, cudaStream_t s) {
+  launch_camera_step<PT, kModeRhs>(tp, sp, partial, b_p, Uinv, x, t_cam, cam_norm, st, sgl, 0,
+                                   0.0, s);
 }
 
 template <typename PT>
-void launch_camera_series(const Topology& tp, const PT* partial, const double* Uinv, double* x,
-                          PT* t_cam, double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
-                          int iter, double eps, cudaStream_t s) {
-  launch_camera_step<PT, kModeSeries>(tp, partial, nullptr, Uinv, x, t_cam, cam_norm, st, sgl,
-                                      iter, eps, s);
+void launch_camera_series(const Topology& tp, const SerTopo& sp, const PT* partial,
+                          const double* Uinv, double* x, PT* t_cam, double* cam_norm,
+                          SeriesState* st, SeriesGlobal* sgl, int iter, double eps,
+                          cudaStream_t s) {
+  launch_camera_step<PT, kModeSeries>(tp, sp, partial, nullptr, Uinv, x, t_cam, cam_norm, st,
+                                      sgl, iter, eps, s);
 }
 
-template void launch_camera_rhs<double>(const Topology&, const double*, const double*, const double*, double*, double*, double*, SeriesState*, SeriesGlobal*, cudaStream_t);
-template void launch_camera_rhs<float>(const Topology&, const float*, const double*, const double*, double*, float*, double*, SeriesState*, SeriesGlobal*, cudaStream_t);
-template void launch_camera_series<double>(const Topology&, const double*, const double*, double*, double*, double*, SeriesState*, SeriesGlobal*, int, double, cudaStream_t);
-template void launch_camera_series<float>(const Topology&, const float*, const double*, double*, float*, double*, SeriesState*, SeriesGlobal*, int, double, cudaStream_t);
+template void launch_camera_rhs<double>(const Topology&, const SerTopo&, const double*, const double*, const double*, double*, double*, double*, SeriesState*, SeriesGlobal*, cudaStream_t);
+template void launch_camera_rhs<float>(const Topology&, const SerTopo&, const float*, const double*, const double*, double*, float*, double*, SeriesState*, SeriesGlobal*, cudaStream_t);
+template void launch_camera_series<double>(const Topology&, const SerTopo&, const double*, const double*, double*, double*, double*, SeriesState*, SeriesGlobal*, int, double, cudaStream_t);
+template void launch_camera_series<float>(const Topology&, const SerTopo&, const float*, const double*, double*, float*, double*, SeriesState*, SeriesGlobal*, int, double, cudaStream_t);
 
 // ---------------------------------------------------------------------------------------
 __global__ void series_reset_kernel(SeriesState* st, SeriesGlobal* sgl, const LmRecord* rec,
@@ -219,64 +237,6 @@ __global__ void series_reset_kernel(SeriesState* st, SeriesGlobal* sgl, const Lm
 void launch_series_reset(SeriesState* st, SeriesGlobal* sgl, const LmRecord* rec, int n_probs,
                          cudaStream_t s) {
   series_reset_kernel<<<(n_probs + 127) / 128, 128, 0, s>>>(st, sgl, rec, n_probs);
-}
-
-// Active tile list of a batch: an exclusive scan of the tile counts of the problems still
-// taking part (one block, problems in chunks of blockDim), then a copy of their descriptors.
-__global__ void __launch_bounds__(1024) active_tiles_scan_kernel(Topology tp,
-                                                                  const SeriesState* st,
-                                                                  int32_t* list_off,
-                                                                  SeriesGlobal* sgl) {
-  __shared__ int s_warp[32];
-  __shared__ int s_base;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (threadIdx.x == 0) s_base = 0;
-  __syncthreads();
-  for (int p0 = 0; p0 < tp.n_probs; p0 += blockDim.x) {
-    const int p = p0 + threadIdx.x;
-    const int c = (p < tp.n_probs && !st[p].done) ? tp.tile_off[p + 1] - tp.tile_off[p] : 0;
-    int v = c;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, v, off);
-      if (lane >= off) v += y;
-    }
-    if (lane == 31) s_warp[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-      int w = lane < nw ? s_warp[lane] : 0;
-#pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, w, off);
-        if (lane >= off) w += y;
-      }
-      s_warp[lane] = w;
-    }
-    __syncthreads();
-    const int excl = s_base + (warp > 0 ? s_warp[warp - 1] : 0) + v - c;
-    if (p < tp.n_probs) list_off[p] = excl;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) s_base = excl + c;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) sgl->n_list = s_base;
-}
-
-__global__ void active_tiles_fill_kernel(Topology tp, const SeriesState* st,
-                                         const int32_t* list_off, int4* list) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= tp.n_tiles) return;
-  const int p = tp.tile_prob[t];
-  if (st[p].done) return;
-  const int k = list_off[p] + (t - tp.tile_off[p]);
-  list[2 * (size_t)k] = tp.tile_desc[2 * (size_t)t];
-  list[2 * (size_t)k + 1] = tp.tile_desc[2 * (size_t)t + 1];
-}
-
-void launch_active_tiles(const Topology& tp, const SeriesState* st, int32_t* list_off,
-                         int4* list, SeriesGlobal* sgl, cudaStream_t s) {
-  active_tiles_scan_kernel<<<1, 1024, 0, s>>>(tp, st, list_off, sgl);
-  active_tiles_fill_kernel<<<(tp.n_tiles + 255) / 256, 256, 0, s>>>(tp, st, list_off, list);
 }
 
 // ---------------------------------------------------------------------------------------

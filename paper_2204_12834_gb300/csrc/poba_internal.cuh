@@ -18,11 +18,12 @@
 //   kTStride elements), which a tile gathers through its slots' cameras.  A tile holds at most
 //   kTileSlots slots.
 //
-//   Jacobians and residuals are structure-of-arrays planes of length n_obs_pad in the
-//   handle's bulk precision T:
-//     J[p * n_obs_pad + o], p = 0..17: J_p row-major (row i, col j at p = 9 i + j)
-//                           p = 18..23: J_l row-major (row i, col j at p = 18 + 3 i + j)
-//     r[i * n_obs_pad + o], i = 0, 1
+//   Jacobians are 24 planes p (p = 0..17: J_p row-major, row i, col j at p = 9 i + j;
+//   p = 18..23: J_l row-major at p = 18 + 3 i + j) in the handle's bulk precision T, stored in
+//   16-byte plane groups: the V = 16 / sizeof(T) planes V q .. V q + V - 1 of observation o are
+//   contiguous at J[(q * n_obs_pad + o) * V] (jidx below), so a thread reads its observation's 24
+//   values with 6 (float) or 12 (double) 16-byte loads, and one load instruction of a warp covers
+//   512 contiguous bytes.  Residuals are planes of length n_obs_pad: r[i * n_obs_pad + o].
 //   obs_meta[o] (uint16) = (position of o in the tile's camera-sorted order) | slot << 8.
 #pragma once
 
@@ -106,12 +107,76 @@ __host__ __device__ constexpr TileRecLayout tile_rec_layout(int n, int ns, int n
 }
 constexpr int kTileRecMax = tile_rec_layout(kTileObs, kTileSlots, kTileLms).bytes;
 
+// Jacobian plane groups (see the layout note above): elements of T per 16-byte group and the
+// index of plane p of observation o.
+template <typename T>
+__host__ __device__ constexpr int jgroup() { return (int)(16 / sizeof(T)); }
+template <typename T>
+__host__ __device__ __forceinline__ size_t jidx(int p, size_t o, size_t pad) {
+  return ((size_t)(p / jgroup<T>()) * pad + o) * jgroup<T>() + (size_t)(p % jgroup<T>());
+}
+
 // Returns an empty string on success, else a description of why the inputs are rejected.
 // cam_off / lm_off ([n_probs + 1]) split cameras and landmarks into independent problems; every
 // observation must join a camera and a landmark of the same problem.  NULL means one problem.
 std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_idx,
                            const int32_t* lm_idx, int n_probs, const int32_t* cam_off,
                            const int32_t* lm_off, Schedule* out);
+
+// ---------------------------------------------------------------------------------------
+// Series schedule (host, rebuilt when the group size changes).  The power-series kernels do
+// not use the tiles above: each problem's observed landmarks are cut into groups of
+// consecutive landmarks holding about `target` observations (boundaries at whole landmarks,
+// balanced by observation count; a group also ends before it would touch more than
+// kGroupSlots distinct cameras; optionally each group's last eighth is cut into smaller
+// groups), and each group into chunks of at most kChunkObs observations of whole landmarks.  One block runs one group: its chunks in order, with one accumulator row
+// per distinct camera of the group (a group slot), written once per group as a partial row.
+// A camera's partial rows (one per group that touches it) are contiguous, groups in landmark
+// order (cam_ptr), and summed by the camera kernels in chunks of cam_chunk_rows rows.
+//
+// Chunk record (16-byte aligned, chunk_rec_layout):
+//   code[n]      uint32 per observation: position in the chunk's camera-sorted order (bits
+//                0-7) | group slot of its camera (8-15) | landmark within the chunk (16-23);
+//   sseg[nl + 1] uint16 landmark offsets within the chunk;
+//   clist[ns]    uint32 per distinct camera of the chunk (a chunk slot): its group slot
+//                (bits 0-7) | its first camera-sorted position (8-15) | its number of rows
+//                (16-24); longest first (ties in camera order), so that the lanes that sum
+//                one warp's slots have similar work.
+constexpr int kChunkObs = 256;
+constexpr int kGroupSlots = 256;
+
+struct ChunkRecLayout {
+  int code, sseg, clist, bytes;
+};
+__host__ __device__ constexpr ChunkRecLayout chunk_rec_layout(int n, int nl, int ns) {
+  return ChunkRecLayout{0, 4 * ((n + 3) & ~3), 4 * ((n + 3) & ~3) + 2 * ((nl + 1 + 7) & ~7),
+                        4 * ((n + 3) & ~3) + 2 * ((nl + 1 + 7) & ~7) + 4 * ((ns + 3) & ~3)};
+}
+constexpr int kChunkRecMax = chunk_rec_layout(kChunkObs, kChunkObs, kChunkObs).bytes;
+
+struct SerSchedule {
+  int target = 0;  // observations per group the partition aimed at
+  int tail = 0;    // pieces the last eighth of each group is cut into (0: none)
+  int n_groups = 0, n_chunks = 0, n_gslots = 0, max_group_slots = 0;
+  // [n_groups][8] in ticket order (decreasing observation count): chunk0, n_chunks, gslot0,
+  // n_gslots, n_obs, problem, 0, 0
+  std::vector<int32_t> group;
+  // [n_chunks][8] (landmark order): o0, n, L0, nl, ns, record offset / 16, group, 0
+  std::vector<int32_t> chunk;
+  std::vector<uint8_t> rec;         // chunk records
+  std::vector<int32_t> gslot_cam;   // [n_gslots] camera of each group slot
+  std::vector<int32_t> gslot_row;   // [n_gslots] its camera-major partial row
+  std::vector<int32_t> cam_ptr;     // [n_cams + 1] partial rows of each camera
+};
+
+// Builds the series schedule of S for a target group size (observations, >= 1).  tail > 0: the
+// last eighth of the observations of each group (of at least two chunks) becomes `tail`
+// smaller groups, which the ticket order (largest first) hands out last, so that blocks that
+// finish their large group early take them and the phase ends more evenly.
+std::string build_series_schedule(const Schedule& S, int target, int tail, SerSchedule* out);
+// The automatic group size for G blocks that run groups: one group of n_obs / G observations
+// per block (at least one chunk's worth).
+int series_auto_target(int64_t n_obs, int G);
 
 // Camera schedule of the persistent camera phase.  Items are the chunks of every camera's slot
 // rows (cam_chunks per camera, in camera order): camera c owns items [cam_item[c],
@@ -126,7 +191,7 @@ struct CamSchedule {
 struct CamRoundList {
   std::vector<int32_t> round_cam, round_item, block_round;
 };
-void build_cam_schedule(const Schedule& S, CamSchedule* out);
+void build_cam_schedule(const std::vector<int32_t>& cam_ptr, int n_cams, CamSchedule* out);
 // Rounds sized for a grid of G blocks: as few items per round as spread the items over the grid.
 void build_cam_rounds(const CamSchedule& cs, int n_cams, int G, CamRoundList* out);
 
@@ -162,6 +227,17 @@ struct Topology {
   const int32_t* tile_prob; // [n_tiles]
   const int32_t* cam_off;   // [n_probs + 1]
   const int32_t* tile_off;  // [n_probs + 1]
+};
+
+// Device view of the series schedule (SerSchedule), passed to the series kernels by value.
+struct SerTopo {
+  int n_groups, n_chunks, n_gslots;
+  const int4* group;         // [n_groups][2]: {chunk0, n_chunks, gslot0, n_gslots}, {n_obs, problem, 0, 0}
+  const int4* chunk;         // [n_chunks][2]: {o0, n, L0, nl}, {ns, record offset / 16, group, 0}
+  const uint8_t* rec;        // chunk records (chunk_rec_layout)
+  const int32_t* gslot_cam;  // [n_gslots]
+  const int32_t* gslot_row;  // [n_gslots] camera-major partial row
+  const int32_t* cam_ptr;    // [n_cams + 1] partial rows of each camera
 };
 
 // Per-camera values prepared once per state: rotation R (row-major), the matrix G with
@@ -256,13 +332,19 @@ void launch_tile_cost(const Topology& tp, const double* prep, const double* lms,
                       const double* dx_l, const double2* obs, const double* sqrt_w,
                       double* tile_cost, cudaStream_t s);
 
+// Series kernels over the series schedule sp (one block per group): b~'s tile part
+// W V^-1 b_l (RHS) or W V^-1 W^T t (series) as partial rows, then the camera kernels.
+// series_group_kernels_init raises the kernels' dynamic shared-memory limit (once per process).
 template <typename T>
-void launch_tile_rhs(const Topology& tp, const T* J, const double* b_l, const T* Vinv,
-                     T* partial, const SeriesState* st, cudaStream_t s);
+cudaError_t series_group_kernels_init();
 
 template <typename T>
-void launch_tile_series(const Topology& tp, const T* J, const T* t_cam, const T* Vinv,
-                        T* partial, const SeriesState* st, const SeriesGlobal* sgl,
+void launch_tile_rhs(const Topology& tp, const SerTopo& sp, const T* J, const double* b_l,
+                     const T* Vinv, T* partial, const SeriesState* st, cudaStream_t s);
+
+template <typename T>
+void launch_tile_series(const Topology& tp, const SerTopo& sp, const T* J, const T* t_cam,
+                        const T* Vinv, T* partial, const SeriesState* st, const SeriesGlobal* sgl,
                         cudaStream_t s);
 
 template <typename T>
@@ -270,19 +352,20 @@ void launch_tile_backsub(const Topology& tp, const T* J, const T* r, const doubl
                          const double* b_l, const T* Vinv, double* dx_l,
                          double* block_pred, cudaStream_t s);
 
-// The camera kernels write the new term t into each of the camera's camera-major slot rows
-// (t_cam), which the next tile kernel gathers through slot_row, and a (||t_c||^2, ||x_c||^2)
-// pair per camera (cam_norm); the last block to finish reduces the pairs per problem and
-// applies the stop rule of each problem.
+// The camera kernels sum each camera's partial rows (sp.cam_ptr), write the new term t into the
+// camera's row of t_cam, which the next group kernel gathers, and a (||t_c||^2, ||x_c||^2) pair
+// per camera (cam_norm); the last block to finish reduces the pairs per problem and applies the
+// stop rule of each problem.
 template <typename PT>
-void launch_camera_rhs(const Topology& tp, const PT* partial, const double* b_p,
+void launch_camera_rhs(const Topology& tp, const SerTopo& sp, const PT* partial, const double* b_p,
                        const double* Uinv, double* x, PT* t_cam, double* cam_norm,
                        SeriesState* st, SeriesGlobal* sgl, cudaStream_t s);
 
 template <typename PT>
-void launch_camera_series(const Topology& tp, const PT* partial, const double* Uinv, double* x,
-                          PT* t_cam, double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
-                          int iter, double eps, cudaStream_t s);
+void launch_camera_series(const Topology& tp, const SerTopo& sp, const PT* partial,
+                          const double* Uinv, double* x, PT* t_cam, double* cam_norm,
+                          SeriesState* st, SeriesGlobal* sgl, int iter, double eps,
+                          cudaStream_t s);
 
 int camera_blocks(const Topology& tp);
 
@@ -326,11 +409,12 @@ void launch_invert_camera_blocks(const Topology& tp, const double* A45, const do
                                  int damping_mode, double* out81, int32_t* not_spd,
                                  cudaStream_t s);
 template <typename PT>
-void launch_schur_camera(const Topology& tp, const PT* partial, const double* U45, double lam,
-                         int mode, const double* p, double* q, cudaStream_t s);
+void launch_schur_camera(const Topology& tp, const SerTopo& sp, const PT* partial,
+                         const double* U45, double lam, int mode, const double* p, double* q,
+                         cudaStream_t s);
 template <typename PT>
-void launch_schur_rhs_camera(const Topology& tp, const PT* partial, const double* b_p,
-                             double* out, cudaStream_t s);
+void launch_schur_rhs_camera(const Topology& tp, const SerTopo& sp, const PT* partial,
+                             const double* b_p, double* out, cudaStream_t s);
 template <typename PT>
 void launch_stage_term(int n_cams, const double* p, PT* t_cam, cudaStream_t s);
 void launch_dot(int n, const double* a, const double* b, double* part, double* out,
@@ -357,35 +441,29 @@ void launch_obs_gradient(const Topology& tp, const T* J, const T* r, const doubl
 // Fixed-order sum of n doubles into *out = scale * sum (one block).
 void launch_reduce_sum(const double* in, int n, double* out, double scale, cudaStream_t s);
 
-// Persistent series kernel (cooperative launch): up to m_max terms and the stop rule.  The last
-// block records %globaltimer at 5 points of each of the first kTraceTerms terms (start, end of
-// the tile phase, after the first barrier, end of the camera phase, after the second barrier).
+// Persistent series kernel (cooperative launch): up to m_max terms and the stop rule.  Blocks
+// take groups of the series schedule by ticket (sp.group is in ticket order), except the
+// grid's last block, which applies the stop rule.  Block 0 records %globaltimer at 5 points of
+// each of the first kTraceTerms terms (start, end of its group phase, after the first barrier,
+// end of the camera phase, after the second barrier).
 constexpr int kTraceTerms = 64;
 constexpr int kTracePoints = 5;
-int persistent_blocks_per_sm(bool f32);
-
-// FP32-bulk persistent kernel with the software-pipelined tile phase (bulk copies of each
-// tile's Jacobians and index record, issued ahead).  Needs every tile to hold at most
-// kTileSlots slots.  Tiles come from `list` (descriptor pairs as tile_desc), *n_list of them.
-int pipelined_blocks_per_sm();  // 0: the kernel cannot be launched on this device
-cudaError_t launch_series_pipelined(const Topology& tp, const CamRounds& cr, int grid,
-                                    const int4* list,
-                                    const int* n_list, const float* J, const float* Vinv,
-                                    const double* Uinv, double* x, float* t_cam, float* partial,
-                                    double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
-                                    GridSync* gs, int m_max, double eps, long long timeout,
-                                    long long* trace, cudaStream_t s);
-
-// Batches: the descriptors of the tiles of every problem still taking part (st[p].done == 0),
-// in tile order, into list; their number into sgl->n_list.  list_off: [n_probs] scratch.
-void launch_active_tiles(const Topology& tp, const SeriesState* st, int32_t* list_off,
-                         int4* list, SeriesGlobal* sgl, cudaStream_t s);
+int persistent_blocks_per_sm(bool f32);  // 0: the kernel cannot be launched on this device
+// FP32-bulk persistent kernel with chunks staged in shared memory by bulk copies issued one
+// chunk ahead (series_exec 4); the same sums as every other form.
+int staged_blocks_per_sm();  // 0: the kernel cannot be launched on this device
+cudaError_t launch_series_staged(const Topology& tp, const SerTopo& sp, const CamRounds& cr,
+                                 int grid, const float* J, const float* Vinv, const double* Uinv,
+                                 double* x, float* t_cam, float* partial, double* cam_norm,
+                                 SeriesState* st, SeriesGlobal* sgl, GridSync* gs, int m_max,
+                                 double eps, long long timeout, long long* trace,
+                                 cudaStream_t s);
 template <typename T>
-cudaError_t launch_series_persistent(const Topology& tp, const CamRounds& cr, int grid, const T* J,
-                                     const T* Vinv,
-                                     const double* Uinv, double* x, T* t_cam, T* partial,
-                                     double* cam_norm, SeriesState* st, SeriesGlobal* sgl,
-                                     GridSync* gs, int m_max, double eps, long long timeout,
-                                     long long* trace, cudaStream_t s);
+cudaError_t launch_series_persistent(const Topology& tp, const SerTopo& sp, const CamRounds& cr,
+                                     int grid, const T* J, const T* Vinv, const double* Uinv,
+                                     double* x, T* t_cam, T* partial, double* cam_norm,
+                                     SeriesState* st, SeriesGlobal* sgl, GridSync* gs, int m_max,
+                                     double eps, long long timeout, long long* trace,
+                                     cudaStream_t s);
 
 }  // namespace poba

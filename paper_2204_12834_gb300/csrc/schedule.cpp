@@ -7,6 +7,7 @@
 // whose sums are later combined per camera in a fixed order.
 #include <algorithm>
 #include <climits>
+#include <cstring>
 #include <numeric>
 #include <string>
 
@@ -219,11 +220,169 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
   return "";
 }
 
-void build_cam_schedule(const Schedule& S, CamSchedule* cs) {
-  cs->cam_item.assign(S.n_cams + 1, 0);
+std::string build_series_schedule(const Schedule& S, int target, int tail, SerSchedule* Q) {
+  if (target < 1) return "the group size must be >= 1";
+  if (tail < 0 || tail > 64) return "the tail split must be in [0, 64]";
+  Q->target = target;
+  Q->tail = tail;
+  std::vector<int32_t> gnat;   // groups in landmark order: [8] each (see SerSchedule::group)
+  std::vector<int32_t> gcams;  // the groups' distinct cameras, ascending, concatenated
+  Q->chunk.clear();
+  Q->rec.clear();
+  std::vector<int32_t> stamp(S.n_cams, -1);  // range that last counted the camera
+  std::vector<int32_t> gslot_of(S.n_cams, -1);
+  std::vector<int32_t> local;
+  std::vector<std::pair<int, int>> ranges;   // one problem's groups as landmark ranges
+  int n_groups = 0, rid = 0;
+  for (int p = 0; p < S.n_probs; ++p) {
+    // the problem's observed landmarks (unobserved ones sort last within their problem)
+    const int l0 = S.lm_off_int[p];
+    int l1 = S.lm_off_int[p + 1];
+    while (l1 > l0 && S.lm_seg[l1] == S.lm_seg[l1 - 1]) --l1;
+    const int64_t o_beg = S.lm_seg[l0], n_p = (int64_t)S.lm_seg[l1] - o_beg;
+    if (n_p == 0) continue;
+    const int64_t ng = (n_p + target - 1) / target;
+    int64_t k_next = 1;  // index of the next balanced boundary
+    ranges.clear();
+    for (int l = l0; l < l1;) {
+      // one range: landmarks [l, le), ending at the balanced boundary k_next * n_p / ng
+      // (observations from the problem's start) or before its cameras would exceed kGroupSlots
+      const int r = rid++;
+      int le = l, ncam = 0;
+      while (le < l1) {
+        const int a = S.lm_seg[le], b = S.lm_seg[le + 1];
+        int fresh = 0;
+        for (int o = a; o < b; ++o) fresh += stamp[S.cam_of[o]] != r;
+        if (le > l && ncam + fresh > kGroupSlots) break;
+        for (int o = a; o < b; ++o) {
+          if (stamp[S.cam_of[o]] != r) {
+            stamp[S.cam_of[o]] = r;
+            ++ncam;
+          }
+        }
+        ++le;
+        const int64_t done = (int64_t)S.lm_seg[le] - o_beg;
+        if (done * ng >= k_next * n_p) {
+          while (k_next < ng && done * ng >= k_next * n_p) ++k_next;
+          break;
+        }
+      }
+      // tail split: the range's last eighth of observations becomes `tail` small ranges
+      const int64_t n_r = (int64_t)S.lm_seg[le] - S.lm_seg[l];
+      if (tail > 0 && n_r >= 2 * kChunkObs) {
+        const int64_t head_end = S.lm_seg[l] + n_r - n_r / 8;
+        int lh = l + 1;
+        while (lh < le && S.lm_seg[lh] < head_end) ++lh;
+        ranges.push_back({l, lh});
+        const int64_t t0 = S.lm_seg[lh], n_t = (int64_t)S.lm_seg[le] - t0;
+        int lt = lh;
+        for (int k = 1; k <= tail && lt < le; ++k) {
+          int lte = lt + 1;
+          while (lte < le && ((int64_t)S.lm_seg[lte] - t0) * tail < k * n_t) ++lte;
+          if (k == tail) lte = le;
+          ranges.push_back({lt, lte});
+          lt = lte;
+        }
+      } else {
+        ranges.push_back({l, le});
+      }
+      l = le;
+    }
+    for (const auto& rg : ranges) {
+      const int l = rg.first, le = rg.second;
+      const int g = n_groups++;
+      // the group's distinct cameras, ascending, are its slots
+      const int gs0 = (int)gcams.size();
+      for (int o = S.lm_seg[l]; o < S.lm_seg[le]; ++o) {
+        const int c = S.cam_of[o];
+        if (gslot_of[c] != -2 - g) {
+          gslot_of[c] = -2 - g;
+          gcams.push_back(c);
+        }
+      }
+      std::sort(gcams.begin() + gs0, gcams.end());
+      const int ns_g = (int)gcams.size() - gs0;
+      for (int s = 0; s < ns_g; ++s) gslot_of[gcams[gs0 + s]] = s;
+      // chunks: whole landmarks, at most kChunkObs observations
+      const int c0 = (int)(Q->chunk.size() / 8);
+      int lc = l;
+      while (lc < le) {
+        int lce = lc;
+        while (lce < le && S.lm_seg[lce + 1] - S.lm_seg[lc] <= kChunkObs) ++lce;
+        if (lce == lc) return "a landmark has more observations than a chunk holds";
+        const int o0 = S.lm_seg[lc], n = S.lm_seg[lce] - o0, nl = lce - lc;
+        local.resize(n);
+        for (int i = 0; i < n; ++i) local[i] = i;
+        std::stable_sort(local.begin(), local.end(), [&](int32_t x, int32_t y) {
+          return S.cam_of[o0 + x] < S.cam_of[o0 + y];
+        });
+        std::vector<uint32_t> code(n), clist;
+        int prev = -1;
+        for (int q = 0; q < n; ++q) {
+          const int i = local[q], cam = S.cam_of[o0 + i];
+          if (cam != prev) {
+            clist.push_back((uint32_t)gslot_of[cam] | ((uint32_t)q << 8));
+            prev = cam;
+          }
+          clist.back() += 1u << 16;  // one more row
+          code[i] = (uint32_t)q | ((uint32_t)gslot_of[cam] << 8) |
+                    ((uint32_t)(S.lm_of[o0 + i] - lc) << 16);
+        }
+        std::stable_sort(clist.begin(), clist.end(),
+                         [](uint32_t x, uint32_t y) { return (x >> 16) > (y >> 16); });
+        const int ns = (int)clist.size();
+        const ChunkRecLayout L = chunk_rec_layout(n, nl, ns);
+        const size_t off = Q->rec.size();
+        if (off / 16 > (size_t)INT32_MAX) return "too many chunks for the chunk records";
+        Q->rec.resize(off + L.bytes, 0);
+        uint8_t* base = Q->rec.data() + off;
+        std::memcpy(base + L.code, code.data(), 4 * (size_t)n);
+        uint16_t* sseg = reinterpret_cast<uint16_t*>(base + L.sseg);
+        for (int j = 0; j <= nl; ++j) sseg[j] = (uint16_t)(S.lm_seg[lc + j] - o0);
+        std::memcpy(base + L.clist, clist.data(), 4 * (size_t)ns);
+        const int32_t d[8] = {o0, n, lc, nl, ns, (int32_t)(off / 16), g, 0};
+        Q->chunk.insert(Q->chunk.end(), d, d + 8);
+        lc = lce;
+      }
+      const int nc = (int)(Q->chunk.size() / 8) - c0;
+      const int32_t gd[8] = {c0, nc, gs0, ns_g, S.lm_seg[le] - S.lm_seg[l], p, 0, 0};
+      gnat.insert(gnat.end(), gd, gd + 8);
+    }
+  }
+  Q->n_groups = n_groups;
+  Q->n_chunks = (int)(Q->chunk.size() / 8);
+  Q->n_gslots = (int)gcams.size();
+  Q->gslot_cam = gcams;
+  Q->max_group_slots = 0;
+  for (int g = 0; g < n_groups; ++g) Q->max_group_slots = std::max(Q->max_group_slots, gnat[8 * g + 3]);
+  // camera-major rows: camera c's rows are its group slots in landmark (group) order
+  Q->cam_ptr.assign(S.n_cams + 1, 0);
+  for (int c : gcams) Q->cam_ptr[c + 1]++;
+  for (int c = 0; c < S.n_cams; ++c) Q->cam_ptr[c + 1] += Q->cam_ptr[c];
+  std::vector<int32_t> fill(Q->cam_ptr.begin(), Q->cam_ptr.end() - 1);
+  Q->gslot_row.assign(Q->n_gslots, 0);
+  for (int s = 0; s < Q->n_gslots; ++s) Q->gslot_row[s] = fill[gcams[s]]++;
+  // ticket order: decreasing observation count (longest first), ties in landmark order
+  std::vector<int32_t> ord(n_groups);
+  for (int g = 0; g < n_groups; ++g) ord[g] = g;
+  std::stable_sort(ord.begin(), ord.end(),
+                   [&](int32_t x, int32_t y) { return gnat[8 * x + 4] > gnat[8 * y + 4]; });
+  Q->group.assign((size_t)n_groups * 8, 0);
+  for (int i = 0; i < n_groups; ++i)
+    std::memcpy(&Q->group[(size_t)i * 8], &gnat[(size_t)ord[i] * 8], 8 * sizeof(int32_t));
+  return "";
+}
+
+int series_auto_target(int64_t n_obs, int G) {
+  const int64_t t = G > 0 ? (n_obs + G - 1) / G : n_obs;
+  return (int)std::min<int64_t>(std::max<int64_t>(t, kChunkObs), INT32_MAX);
+}
+
+void build_cam_schedule(const std::vector<int32_t>& cam_ptr, int n_cams, CamSchedule* cs) {
+  cs->cam_item.assign(n_cams + 1, 0);
   cs->item_q.clear();
-  for (int c = 0; c < S.n_cams; ++c) {
-    const int r0 = S.cam_slot_ptr[c], r1 = S.cam_slot_ptr[c + 1];
+  for (int c = 0; c < n_cams; ++c) {
+    const int r0 = cam_ptr[c], r1 = cam_ptr[c + 1];
     const int k = cam_chunks(r1 - r0), C = cam_chunk_rows(r1 - r0);
     for (int j = 0; j < k; ++j) {
       cs->item_q.push_back(std::min(r0 + j * C, r1));

@@ -2,21 +2,26 @@
 // persistent series kernel.  Data written by other blocks of the same launch (t_cam, partial,
 // x) is read with __ldcg (L2), since L1 is not coherent across SMs within a launch.
 //
-// With P = U^-1 W V^-1 W^T, W = J_p^T J_l, a term t_i = P t_{i-1} is applied matrix-free:
-//   tile body (per tile of whole landmarks, one observation per thread):
-//     u_o = J_p,o t_c(o)                       (t staged per slot in shared memory)
-//     z_l = V_l^-1 sum_{o in l} J_l,o^T u_o    (landmark-segmented sum in shared memory)
+// With P = U^-1 W V^-1 W^T, W = J_p^T J_l, a term t_i = P t_{i-1} is applied matrix-free over
+// the series schedule (SerSchedule): a block runs one group of consecutive landmarks, chunk by
+// chunk (one observation per thread):
+//     u_o = J_p,o t_c(o)                       (t staged per group slot in shared memory)
+//     z_l = V_l^-1 sum_{o in l} J_l,o^T u_o    (landmark-segmented sum)
 //     g_o = J_p,o^T (J_l,o z_l(o))             (J still in registers: one J read per term)
-//     partial[row(slot)] = sum_{o in slot} g_o (per-tile camera sums, fixed order)
-//   camera body (9 threads per camera):
+//     acc[slot(o)] += sum_{o in slot} g_o      (per chunk slot, then across the group's chunks)
+//   and writes one partial row per group slot; then the camera body (9 threads per camera):
 //     y_c = sum of the camera's partial rows; t_i = U_c^-1 y_c; x += t_i; t_cam[c] = t_i.
 // With z_l = V_l^-1 b_l (RHS mode) the same bodies form b~ = b_p - W V^-1 b_l and
 // x(0) = -U^-1 b~ (Sec. 4.2 and eq. `x_approx` with m = 0).
+//
+// Every sum has a fixed order that depends only on the schedule, whichever block runs a group,
+// so all execution forms give bitwise-equal results.
 #pragma once
 
 #include <cstddef>
 #include <cstdint>
 
+#include "jacobian_io.cuh"
 #include "poba_internal.cuh"
 #include "tile_common.cuh"
 
@@ -24,18 +29,7 @@ namespace poba {
 
 enum { kModeSeries = 0, kModeRhs = 1 };
 
-// FP32 tiles whose slots hold fewer rows than this on average sum each (slot, component) in one
-// thread; longer slots are split over a warp.
-constexpr int kShortSlotRows = 6;
-
-template <typename T>
-__device__ __forceinline__ void load_J(const T* __restrict__ J, size_t pad, int o, T (&jp)[18],
-                                       T (&jl)[6]) {
-#pragma unroll
-  for (int p = 0; p < 18; ++p) jp[p] = J[p * pad + o];
-#pragma unroll
-  for (int p = 0; p < 6; ++p) jl[p] = J[(18 + p) * pad + o];
-}
+constexpr unsigned kFull = 0xffffffffu;
 
 // z = Vinv s with Vinv stored as [00 01 02 11 12 22].
 template <typename T>
@@ -46,7 +40,8 @@ __device__ __forceinline__ void apply_vinv(const T* __restrict__ vi, const T (&s
   z[2] = v2 * s[0] + v4 * s[1] + v5 * s[2];
 }
 
-// Tile header: {L0, nl, o0, n} and {S0, ns}.
+// Tile header of the tile schedule (back-substitution, linearisation): {L0, nl, o0, n} and
+// {S0, ns}.
 struct TileHdr {
   int L0, nl, o0, n, S0, ns;
 };
@@ -56,287 +51,486 @@ __device__ __forceinline__ TileHdr load_tile(const Topology& tp, int tile) {
   return TileHdr{a.x, a.y, a.z, a.w, b.x, b.y};
 }
 
-// 16-byte aligned: the persistent kernel reuses sg as a double array in its camera phase.
-template <typename T>
-struct __align__(16) TileSmem {
-  T tcam[kTileObs][9];
-  T sv[kTileObs][3];
-  T sg[kTileObs][9];
-  uint16_t sbeg[kTileObs];
-  int srow[kTileObs];
-  int sseg[kTileLms + 1];
+// ---------------------------------------------------------------------------------------
+// Shared memory of a group.  The camera phase of the persistent kernel reuses sg as scratch.
+template <typename T> struct GroupSmem;
+
+template <> struct __align__(16) GroupSmem<float> {
+  float4 tc[kGroupSlots][3];   // current term of each group slot's camera (9 of 12 used)
+  float4 acc[kGroupSlots][3];  // the group slots' sums
+  float4 sg[kChunkObs][3];     // a chunk's g rows at their camera-sorted positions
+  float tail[kChunkObs / 32][4];  // per warp: the scan value at its last lane
+  float head[kChunkObs / 32][4];  // per warp: the scan value at the end of its first segment
+  uint32_t clist[2][kChunkObs];   // chunk slots, alternating buffers (filled before the
+                                  // barrier that ends the previous chunk's slot sums' reads)
 };
-static_assert(offsetof(TileSmem<float>, sg) % 8 == 0, "sg is reused as double storage");
-static_assert(offsetof(TileSmem<double>, sg) % 8 == 0, "sg is reused as double storage");
 
-// One tile of one term (blockDim.x == kTileObs; every thread must call it).
-template <typename T, int MODE>
-__device__ __forceinline__ void tile_matvec_body(const Topology& tp, int tile,
-                                                 const T* __restrict__ J,
-                                                 const T* __restrict__ t_cam,
-                                                 const double* __restrict__ b_l,
-                                                 const T* __restrict__ Vinv,
-                                                 T* __restrict__ partial, TileSmem<T>& sm) {
+template <> struct __align__(16) GroupSmem<double> {
+  double2 tc[kGroupSlots][5];  // 9 of 10 used
+  double acc[kGroupSlots][9];
+  double2 sg[kChunkObs][5];    // g rows at their camera-sorted positions
+  double sv[kChunkObs][3];     // each observation's landmark contribution J_l^T J_p t
+  double sz[kChunkObs][3];     // z of each landmark of the chunk
+};
+
+// Lanes of a chunk's slot sums.  Each of `items` sums (chunk slots are ordered longest first,
+// so items are too) runs over `split` lanes, a power of two: the largest s <= 8 with
+// items * s <= kChunkObs for every item, and, with the lanes left over, 2 s for the first
+// items.  The plan depends on the item count alone, so every sum has a fixed order.
+struct SumPlan {
+  int s, up;    // base split; items 0 .. up-1 run over 2 s lanes
+  int lanes;    // lanes in use
+};
+__device__ __forceinline__ SumPlan sum_plan(int items) {
+  const int s = items * 8 <= kChunkObs ? 8 : items * 4 <= kChunkObs ? 4
+              : items * 2 <= kChunkObs ? 2 : 1;
+  int up = 0;
+  if (s < 16 && items * s < kChunkObs) up = min(items, (kChunkObs - items * s) / s);
+  return SumPlan{s, up, items * s + up * s};
+}
+// Lane idx of the plan: its item, its part (0 .. split-1) and the item's split.
+__device__ __forceinline__ void sum_lane(const SumPlan& P, int idx, int& item, int& part,
+                                         int& split) {
+  const int s2 = 2 * P.s;
+  if (idx < P.up * s2) {
+    item = idx / s2;
+    part = idx - item * s2;
+    split = s2;
+  } else {
+    const int l = idx - P.up * s2;
+    item = P.up + l / P.s;
+    part = l - (item - P.up) * P.s;
+    split = P.s;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// FP32-bulk chunk.  Landmark sums: a segmented inclusive scan of v over each warp's lanes
+// (shuffles, log2 of the longest segment piece in the warp steps), then, for landmarks that
+// cross a warp boundary, the pieces of the warps they span added in warp order (per-warp tail
+// and head values in shared memory).  Every observation of a landmark ends with the same sum
+// and forms z itself.  Camera sums: g goes to the observation's camera-sorted position; each
+// (chunk slot, 4-component quarter) is summed over its rows (split over lanes by sum_plan) and
+// added to the group slot's accumulator.  Two block barriers per chunk.
+//
+// A chunk's inputs reach the threads in one of two ways with the same arithmetic afterwards:
+// direct loads from global memory (f32_load_direct), or from a copy of the chunk staged in
+// shared memory by bulk asynchronous copies issued one chunk ahead (f32_load_staged).
+
+// One observation thread's inputs.
+struct F32Obs {
+  float jp[18], jl[6], vi[6];
+  uint32_t code;
+  int a, b;      // the landmark's segment in the chunk (an inactive lane: [tid, tid + 1))
+  uint32_t cl;   // chunk slot tid (threads tid < ns)
+};
+
+__device__ __forceinline__ void f32_clear(F32Obs& x) {
+#pragma unroll
+  for (int k = 0; k < 18; ++k) x.jp[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) x.jl[k] = x.vi[k] = 0.f;
+  x.code = 0;
+  x.a = threadIdx.x;
+  x.b = threadIdx.x + 1;
+}
+
+// Sum of rows [beg + part, end) step `split` of column q of sg, in row order; the loads go out
+// four at a time ahead of the adds, which stay in row order.
+__device__ __forceinline__ float4 sg_rows_sum(const float4 (*sg)[3], int beg, int end, int split,
+                                              int q) {
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+  int r = beg;
+  for (; r + 3 * split < end; r += 4 * split) {
+    const float4 v0 = sg[r][q], v1 = sg[r + split][q], v2 = sg[r + 2 * split][q],
+                 v3 = sg[r + 3 * split][q];
+    s.x += v0.x; s.y += v0.y; s.z += v0.z; s.w += v0.w;
+    s.x += v1.x; s.y += v1.y; s.z += v1.z; s.w += v1.w;
+    s.x += v2.x; s.y += v2.y; s.z += v2.z; s.w += v2.w;
+    s.x += v3.x; s.y += v3.y; s.z += v3.z; s.w += v3.w;
+  }
+  for (; r < end; r += split) {
+    const float4 v = sg[r][q];
+    s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+  }
+  return s;
+}
+
+__device__ __forceinline__ void f32_vinv(F32Obs& x, const float* __restrict__ row) {
+  const float2* v2 = reinterpret_cast<const float2*>(row);
+  const float2 x0 = v2[0], x1 = v2[1], x2 = v2[2];
+  x.vi[0] = x0.x; x.vi[1] = x0.y; x.vi[2] = x1.x; x.vi[3] = x1.y; x.vi[4] = x2.x; x.vi[5] = x2.y;
+}
+
+// Chunk c's inputs from global memory (active threads).
+__device__ __forceinline__ void f32_load_direct(const Topology& tp, const int4& d0,
+                                                const uint8_t* __restrict__ rec,
+                                                const ChunkRecLayout& L,
+                                                const float* __restrict__ J,
+                                                const float* __restrict__ Vinv, F32Obs& x) {
   const int tid = threadIdx.x;
-  const TileHdr th = load_tile(tp, tile);
-  const int o0 = th.o0, n = th.n, ns = th.ns, nl = th.nl;
-  const bool active = tid < n;
-  const size_t pad = (size_t)tp.n_obs_pad;
-  // issue every independent load of the tile before the first barrier
-  T jp[18], jl[6];
-  int meta = 0;
-  if (active) {
-    const int o = o0 + tid;
-    meta = tp.obs_meta[o];
-    load_J(J, pad, o, jp, jl);
-  }
-  T vi[6];
-  double bl[3] = {0.0, 0.0, 0.0};
-  if (tid < nl) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k) vi[k] = Vinv[(size_t)(th.L0 + tid) * 6 + k];
-    if (MODE == kModeRhs) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) bl[k] = b_l[(size_t)(th.L0 + tid) * 3 + k];
-    }
-  }
-  for (int i = tid; i < ns; i += blockDim.x) {
-    sm.sbeg[i] = tp.slot_beg[th.S0 + i];
-    sm.srow[i] = tp.slot_row[th.S0 + i];
-  }
-  for (int i = tid; i <= nl; i += blockDim.x) sm.sseg[i] = tp.lm_seg[th.L0 + i] - o0;
-  __syncthreads();
+  load_J(J, (size_t)tp.n_obs_pad, d0.x + tid, x.jp, x.jl);
+  x.code = __ldg(reinterpret_cast<const uint32_t*>(rec + L.code) + tid);
+  const int lm = (int)(x.code >> 16) & 0xff;
+  const uint16_t* sseg = reinterpret_cast<const uint16_t*>(rec + L.sseg);
+  x.a = __ldg(sseg + lm);
+  x.b = __ldg(sseg + lm + 1);
+  const float2* v2 = reinterpret_cast<const float2*>(Vinv + (size_t)(d0.z + lm) * 6);
+  const float2 x0 = __ldg(v2), x1 = __ldg(v2 + 1), x2 = __ldg(v2 + 2);
+  x.vi[0] = x0.x; x.vi[1] = x0.y; x.vi[2] = x1.x; x.vi[3] = x1.y; x.vi[4] = x2.x; x.vi[5] = x2.y;
+}
+
+// The chunk's computation once each thread holds its inputs (x; RHS mode: (s0, s1, s2) = the
+// landmark's b_l).  Threads tid < ns hold chunk slot tid in x.cl, which goes to the shared
+// buffer `par` (consecutive chunks of a group alternate 0 and 1).  `ok` is this thread's view of
+// whether its inputs are valid (a staged copy that arrived); the barrier after the landmark
+// scan reduces it over the block, and if any thread's inputs are invalid every thread returns
+// false there, before the hook and before anything is written outside the block's scratch.
+// hook() runs right after that barrier (every thread of the block has its inputs in registers
+// and has copied the slot list).  Every thread of the block must call it.
+template <int MODE, typename Hook>
+__device__ __forceinline__ bool chunk_f32_core(const F32Obs& x, bool active, int n, int ns,
+                                               int par, float s0, float s1, float s2, bool ok,
+                                               GroupSmem<float>& sm, Hook&& hook) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int a = x.a, b = x.b;
+  uint32_t* cl = sm.clist[par];
+  if (tid < ns) cl[tid] = x.cl;
+  const int wb0 = warp * 32;
+  const int sb = min(b, wb0 + 32) - wb0;
+  float e0 = 0.f, e1 = 0.f, e2 = 0.f;
   if (MODE == kModeSeries) {
-    // the current term of each slot's camera
-    for (int i = tid; i < ns * 9; i += blockDim.x) {
-      const int s = i / 9, k = i - s * 9;
-      sm.tcam[s][k] = __ldcg(t_cam + (size_t)tp.slot_cam[th.S0 + s] * kTStride + k);
-    }
-  }
-  __syncthreads();
-
-  if (MODE == kModeSeries && active) {
-    const T* tc = sm.tcam[meta >> 8];
-    T u0 = (T)0, u1 = (T)0;
+    // phase 1: u = J_p t, v = J_l^T u
+    if (active) {
+      const int gs = (int)(x.code >> 8) & 0xff;
+      const float4 ta = sm.tc[gs][0], tb = sm.tc[gs][1], tq = sm.tc[gs][2];
+      const float t[9] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w, tq.x};
+      float u0 = 0.f, u1 = 0.f;
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
-      u0 += jp[j] * tc[j];
-      u1 += jp[9 + j] * tc[j];
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) sm.sv[tid][k] = jl[k] * u0 + jl[3 + k] * u1;
-  }
-  __syncthreads();
-  // landmark phase: z_l = V_l^-1 (sum of W^T t contributions, or b_l), written back per obs
-  if (tid < nl) {
-    const int a = sm.sseg[tid], b = sm.sseg[tid + 1];
-    T s3[3];
-    if (MODE == kModeSeries) {
-      s3[0] = s3[1] = s3[2] = (T)0;
-      for (int q = a; q < b; ++q) {
-        s3[0] += sm.sv[q][0];
-        s3[1] += sm.sv[q][1];
-        s3[2] += sm.sv[q][2];
+      for (int j = 0; j < 9; ++j) {
+        u0 += x.jp[j] * t[j];
+        u1 += x.jp[9 + j] * t[j];
       }
-    } else {
-      s3[0] = (T)bl[0];
-      s3[1] = (T)bl[1];
-      s3[2] = (T)bl[2];
+      s0 = x.jl[0] * u0 + x.jl[3] * u1;
+      s1 = x.jl[1] * u0 + x.jl[4] * u1;
+      s2 = x.jl[2] * u0 + x.jl[5] * u1;
     }
-    T z[3];
-    z[0] = vi[0] * s3[0] + vi[1] * s3[1] + vi[2] * s3[2];
-    z[1] = vi[1] * s3[0] + vi[3] * s3[1] + vi[4] * s3[2];
-    z[2] = vi[2] * s3[0] + vi[4] * s3[1] + vi[5] * s3[2];
-    for (int q = a; q < b; ++q) {
-      sm.sv[q][0] = z[0];
-      sm.sv[q][1] = z[1];
-      sm.sv[q][2] = z[2];
+    // phase 2: segmented scan over the warp's lanes [sa, sb) of each segment
+    const int sa = max(a, wb0) - wb0;
+    const int span = (int)__reduce_max_sync(kFull, (unsigned)(sb - sa));
+    for (int d = 1; d < span; d <<= 1) {
+      const float y0 = __shfl_up_sync(kFull, s0, d);
+      const float y1 = __shfl_up_sync(kFull, s1, d);
+      const float y2 = __shfl_up_sync(kFull, s2, d);
+      if (lane - d >= sa) {
+        s0 += y0;
+        s1 += y1;
+        s2 += y2;
+      }
     }
-  }
-  __syncthreads();
-  // W z scatter: g_o = J_p^T (J_l z), staged at the camera-sorted position
-  if (active) {
-    const T z0 = sm.sv[tid][0], z1 = sm.sv[tid][1], z2 = sm.sv[tid][2];
-    const T w0 = jl[0] * z0 + jl[1] * z1 + jl[2] * z2;
-    const T w1 = jl[3] * z0 + jl[4] * z1 + jl[5] * z2;
-    T* g = sm.sg[meta & 0xff];
-#pragma unroll
-    for (int j = 0; j < 9; ++j) g[j] = jp[j] * w0 + jp[9 + j] * w1;
-  }
-  __syncthreads();
-  slot_sums<T, T>(sm.sg, ns, n, sm.sbeg, sm.srow, partial, 9);
-}
-
-// Phases 1-3 of the FP32-bulk tile (below), shared by the per-term tile kernel and the
-// pipelined persistent kernel so that both compute the same sums in the same order.  The caller
-// stages: tcam[slot * tstride .. + 9) = current term of the slot's camera; V^-1 of tile landmark l at
-// vinv[l * vstride .. + 6) (RHS mode: b_l at + 6 .. + 9); sseg[l] = tile-relative segment
-// offsets (nl + 1 entries); sbeg[s] = first camera-sorted position of slot s; srow[s] = its
-// camera-major row.  lm = the observation's landmark within the tile, meta = pos | slot << 8.
-// kShared: the caller's staging shares storage (landmark marks in sv, V^-1 in sg), which costs
-// two more barriers; otherwise sv, sg, tcam and vinv must be separate.  hook() runs after the
-// barrier that follows the v writes (every thread has passed the start of the tile).  Every
-// thread of the block must call it.
-template <int MODE, bool kShared, typename SegT, typename BegT, typename Hook>
-__device__ __forceinline__ void f32_tile_core(bool active, int n, int ns, int lm, int meta,
-                                              const float (&jp)[18], const float (&jl)[6],
-                                              const float* tcam, int tstride, const float* vinv,
-                                              int vstride, const SegT* sseg, const BegT* sbeg,
-                                              const int* srow, float (*sv)[3], float (*sg)[9],
-                                              float* __restrict__ partial, Hook&& hook) {
-  const int tid = threadIdx.x;
-  // phase 1: u = J_p t, v = J_l^T u
-  float u0 = 0.f, u1 = 0.f;
-  if (MODE == kModeSeries && active) {
-    const float* tc = tcam + (size_t)(meta >> 8) * tstride;
-#pragma unroll
-    for (int j = 0; j < 9; ++j) {
-      u0 += jp[j] * tc[j];
-      u1 += jp[9 + j] * tc[j];
+    if (lane == 31) {
+      sm.tail[warp][0] = s0;
+      sm.tail[warp][1] = s1;
+      sm.tail[warp][2] = s2;
     }
+    if (a < wb0 && lane == sb - 1) {
+      sm.head[warp][0] = s0;
+      sm.head[warp][1] = s1;
+      sm.head[warp][2] = s2;
+    }
+    e0 = __shfl_sync(kFull, s0, sb - 1);
+    e1 = __shfl_sync(kFull, s1, sb - 1);
+    e2 = __shfl_sync(kFull, s2, sb - 1);
   }
-  if (kShared) __syncthreads();  // sv still holds the landmark marks read before the call
-  if (MODE == kModeSeries && active) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) sv[tid][k] = jl[k] * u0 + jl[3 + k] * u1;
-  }
-  __syncthreads();
+  // every thread holds its inputs and has finished the previous chunk's slot sums (which read
+  // sg and the slot list)
+  if (__syncthreads_or(!ok)) return false;
   hook();
-  // phase 2: each observation thread sums its landmark's v in segment order, applies V^-1 and
-  // forms J_l z
-  if (active) {
-    float s3[3];
-    const float* vl = vinv + (size_t)lm * vstride;
-    if (MODE == kModeSeries) {
-      s3[0] = s3[1] = s3[2] = 0.f;
-      const int a = sseg[lm], b = sseg[lm + 1];
-      for (int q = a; q < b; ++q) {
-        s3[0] += sv[q][0];
-        s3[1] += sv[q][1];
-        s3[2] += sv[q][2];
+  if (MODE == kModeSeries) {
+    if (a < wb0 || b > wb0 + 32) {
+      // the landmark spans warps wa..wz: tails of wa..wz-1, then the head of wz
+      const int wa = min(a >> 5, kChunkObs / 32 - 1), wz = min((b - 1) >> 5, kChunkObs / 32 - 1);
+      s0 = s1 = s2 = 0.f;
+      for (int w = wa; w < wz; ++w) {
+        s0 += sm.tail[w][0];
+        s1 += sm.tail[w][1];
+        s2 += sm.tail[w][2];
       }
+      s0 += sm.head[wz][0];
+      s1 += sm.head[wz][1];
+      s2 += sm.head[wz][2];
     } else {
-      s3[0] = vl[6];
-      s3[1] = vl[7];
-      s3[2] = vl[8];
+      s0 = e0;
+      s1 = e1;
+      s2 = e2;
     }
-    const float z0 = vl[0] * s3[0] + vl[1] * s3[1] + vl[2] * s3[2];
-    const float z1 = vl[1] * s3[0] + vl[3] * s3[1] + vl[4] * s3[2];
-    const float z2 = vl[2] * s3[0] + vl[4] * s3[1] + vl[5] * s3[2];
-    u0 = jl[0] * z0 + jl[1] * z1 + jl[2] * z2;
-    u1 = jl[3] * z0 + jl[4] * z1 + jl[5] * z2;
   }
-  if (kShared) __syncthreads();  // the V^-1 staging shares sg with the scatter below
+  // z = V^-1 s, then g = J_p^T (J_l z) at the camera-sorted position
   if (active) {
-    float* g = sg[meta & 0xff];
+    const float z0 = x.vi[0] * s0 + x.vi[1] * s1 + x.vi[2] * s2;
+    const float z1 = x.vi[1] * s0 + x.vi[3] * s1 + x.vi[4] * s2;
+    const float z2 = x.vi[2] * s0 + x.vi[4] * s1 + x.vi[5] * s2;
+    const float w0 = x.jl[0] * z0 + x.jl[1] * z1 + x.jl[2] * z2;
+    const float w1 = x.jl[3] * z0 + x.jl[4] * z1 + x.jl[5] * z2;
+    float g[9];
 #pragma unroll
-    for (int j = 0; j < 9; ++j) g[j] = jp[j] * u0 + jp[9 + j] * u1;
+    for (int j = 0; j < 9; ++j) g[j] = x.jp[j] * w0 + x.jp[9 + j] * w1;
+    float4* row = sm.sg[x.code & 0xff];
+    row[0] = make_float4(g[0], g[1], g[2], g[3]);
+    row[1] = make_float4(g[4], g[5], g[6], g[7]);
+    row[2] = make_float4(g[8], 0.f, 0.f, 0.f);
   }
   __syncthreads();
-  // phase 3, chosen by the tile's shape (the same choice in every form):
-  //  * short slots (fewer than kShortSlotRows rows on average): one thread per (slot, component)
-  //    sums the slot's rows in row order;
-  //  * otherwise one warp per slot: lane 3 k + c sums component k over the c-th third of the
-  //    slot's rows in row order, and the three thirds are added in chunk order.
-  if (n < kShortSlotRows * ns) {
-    for (int k = tid; k < ns * 9; k += blockDim.x) {
-      const int sl = k / 9, kc = k - 9 * sl;
-      const int beg = sbeg[sl], end = (sl + 1 < ns) ? (int)sbeg[sl + 1] : n;
-      float acc = 0.f;
-      for (int q = beg; q < end; ++q) acc += sg[q][kc];
-      partial[(size_t)srow[sl] * 9 + kc] = acc;
+  // phase 3: chunk slot j (longest first), quarter q: its rows in row order over `split`
+  // lanes (sum_plan), combined by a fixed shuffle tree, added to the group slot
+  const int items = ns * 3;
+  const SumPlan P = sum_plan(items);
+  const int bound = (P.lanes + 31) & ~31;
+  for (int idx = tid; idx < bound; idx += kChunkObs) {
+    int item, part, split;
+    sum_lane(P, idx, item, part, split);
+    const bool act = idx < P.lanes;
+    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+    int gs = 0, q = 0;
+    if (act) {
+      const int j = item / 3;
+      q = item - 3 * j;
+      const uint32_t e = cl[j];
+      gs = (int)(e & 0xff);
+      const int beg = (int)(e >> 8) & 0xff, end = beg + (int)(e >> 16);
+      sum = sg_rows_sum(sm.sg, beg + part, end, split, q);
     }
-    return;
-  }
-  const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-  const int kc = lane / 3, cc = lane - 3 * kc;
-  for (int sl = warp; sl < ns; sl += nw) {
-    const int beg = sbeg[sl], end = (sl + 1 < ns) ? (int)sbeg[sl + 1] : n;
-    const int chunk = (end - beg + 2) / 3;
-    float acc = 0.f;
-    if (lane < 27) {
-      const int q0 = beg + cc * chunk, q1 = min(q0 + chunk, end);
-      for (int q = q0; q < q1; ++q) acc += sg[q][kc];
+    for (int off = P.s; off > 0; off >>= 1) {  // levels of the largest split (2 s)
+      const float ax = __shfl_down_sync(kFull, sum.x, off);
+      const float ay = __shfl_down_sync(kFull, sum.y, off);
+      const float az = __shfl_down_sync(kFull, sum.z, off);
+      const float aw = __shfl_down_sync(kFull, sum.w, off);
+      if (off < split) {
+        sum.x += ax;
+        sum.y += ay;
+        sum.z += az;
+        sum.w += aw;
+      }
     }
-    const float a1 = __shfl_down_sync(0xffffffffu, acc, 1);
-    const float a2 = __shfl_down_sync(0xffffffffu, acc, 2);
-    if (lane < 27 && cc == 0) partial[(size_t)srow[sl] * 9 + kc] = (acc + a1) + a2;
+    if (act && part == 0) {
+      float4 acc = sm.acc[gs][q];
+      acc.x += sum.x;
+      acc.y += sum.y;
+      acc.z += sum.z;
+      acc.w += sum.w;
+      sm.acc[gs][q] = acc;
+    }
   }
+  (void)n;
+  return true;
 }
 
-// FP32-bulk tile body (blockDim.x == kTileObs; every thread must call it).  The same sums as
-// tile_matvec_body, arranged for float arithmetic, where redundant FMAs are cheap and barriers
-// are not:
-//   phase 0  J and the observation code into registers; slot threads stage their slot's
-//            first position, camera-major row and current term row; landmark threads stage
-//            their segment, V^-1 and (RHS) b_l and mark their observations' landmark;
-//   phase 1  u = J_p t, v = J_l^T u per observation;
-//   phase 2  every observation thread sums its own landmark's v in segment order and applies
-//            V^-1 (the same sum and the same z in every thread of the landmark), then scatters
-//            g = J_p^T (J_l z) to its camera-sorted position;
-//   phase 3  tiles of short slots: one thread per (slot, component) sums the slot's rows in
-//            order; otherwise one warp per slot: 27 lanes, one per (component, third of the
-//            slot's rows), sum their rows in order, the thirds are added in order; either way
-//            the sum is written to the slot's camera-major row.
+// One chunk with direct loads.  Every thread of the block must call it.
 template <int MODE>
-__device__ __forceinline__ void tile_matvec_body_f32(const Topology& tp, int tile,
-                                                     const float* __restrict__ J,
-                                                     const float* __restrict__ t_cam,
-                                                     const double* __restrict__ b_l,
-                                                     const float* __restrict__ Vinv,
-                                                     float* __restrict__ partial,
-                                                     TileSmem<float>& sm) {
-  const int tid = threadIdx.x;
-  const TileHdr th = load_tile(tp, tile);
-  const int o0 = th.o0, n = th.n, ns = th.ns, nl = th.nl;
-  const bool active = tid < n;
-  const size_t pad = (size_t)tp.n_obs_pad;
-  float jp[18], jl[6];
-  int meta = 0;
+__device__ __forceinline__ void chunk_f32(const Topology& tp, const SerTopo& sp, int c,
+                                          const float* __restrict__ J,
+                                          const double* __restrict__ b_l,
+                                          const float* __restrict__ Vinv, GroupSmem<float>& sm) {
+  const int4 d0 = __ldg(sp.chunk + 2 * c), d1 = __ldg(sp.chunk + 2 * c + 1);
+  const int n = d0.y, ns = d1.x;
+  const uint8_t* rec = sp.rec + (size_t)d1.y * 16;
+  const ChunkRecLayout L = chunk_rec_layout(n, d0.w, ns);
+  const bool active = threadIdx.x < n;
+  F32Obs x;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+  const uint32_t cl =
+      threadIdx.x < ns ? __ldg(reinterpret_cast<const uint32_t*>(rec + L.clist) + threadIdx.x) : 0u;
   if (active) {
-    const int o = o0 + tid;
-    meta = tp.obs_meta[o];
-    load_J(J, pad, o, jp, jl);
+    f32_load_direct(tp, d0, rec, L, J, Vinv, x);
+    if (MODE == kModeRhs) {
+      const double* bl = b_l + (size_t)(d0.z + ((x.code >> 16) & 0xff)) * 3;
+      s0 = (float)__ldg(bl);
+      s1 = (float)__ldg(bl + 1);
+      s2 = (float)__ldg(bl + 2);
+    }
+  } else {
+    f32_clear(x);
   }
-  // shared arrays reused here: sbeg / srow per slot, sseg per landmark, tcam per slot,
-  // sv per observation (first the landmark index of each observation, then v);
-  // sg[l][0..5] = V^-1 of landmark l and sg[l][6..8] = b_l (RHS) until phase 2 ends
-  for (int i = tid; i < ns; i += blockDim.x) {
-    const int r = tp.slot_row[th.S0 + i];
-    sm.sbeg[i] = tp.slot_beg[th.S0 + i];
-    sm.srow[i] = r;
-    if (MODE == kModeSeries) {
-      const int c = tp.slot_cam[th.S0 + i];
+  x.cl = cl;
+  chunk_f32_core<MODE>(x, active, n, ns, c & 1, s0, s1, s2, true, sm, [] {});
+}
+
+// ---------------------------------------------------------------------------------------
+// FP64 chunk.  FP64 instructions are the bound here (GB300 runs a warp's FP64 instruction over
+// 16 cycles of its FP64 pipe), so the landmark sums use one thread per landmark, which adds
+// each contribution once (a scan would add log2 of the track length times), and z is formed
+// once per landmark.  Three block barriers per chunk.  Every thread must call it.
+template <int MODE>
+__device__ __forceinline__ void chunk_f64(const Topology& tp, const SerTopo& sp, int c,
+                                          const double* __restrict__ J,
+                                          const double* __restrict__ b_l,
+                                          const double* __restrict__ Vinv, GroupSmem<double>& sm) {
+  const int tid = threadIdx.x;
+  const int4 d0 = __ldg(sp.chunk + 2 * c), d1 = __ldg(sp.chunk + 2 * c + 1);
+  const int o0 = d0.x, n = d0.y, L0 = d0.z, nl = d0.w, ns = d1.x;
+  const uint8_t* rec = sp.rec + (size_t)d1.y * 16;
+  const ChunkRecLayout L = chunk_rec_layout(n, nl, ns);
+  const bool active = tid < n;
+  double (*sv)[3] = sm.sv;
+  double jp[18], jl[6];
+  uint32_t code = 0;
+  if (active) {
+    load_J(J, (size_t)tp.n_obs_pad, o0 + tid, jp, jl);
+    code = __ldg(reinterpret_cast<const uint32_t*>(rec + L.code) + tid);
+  }
+  double vi[6], sl[3] = {0.0, 0.0, 0.0};
+  int a = 0, b = 0;
+  if (tid < nl) {
+    const uint16_t* sseg = reinterpret_cast<const uint16_t*>(rec + L.sseg);
+    a = __ldg(sseg + tid);
+    b = __ldg(sseg + tid + 1);
+    const double2* v2 = reinterpret_cast<const double2*>(Vinv + (size_t)(L0 + tid) * 6);
+    const double2 x0 = __ldg(v2), x1 = __ldg(v2 + 1), x2 = __ldg(v2 + 2);
+    vi[0] = x0.x; vi[1] = x0.y; vi[2] = x1.x; vi[3] = x1.y; vi[4] = x2.x; vi[5] = x2.y;
+    if (MODE == kModeRhs) {
+      const double* bl = b_l + (size_t)(L0 + tid) * 3;
+      sl[0] = __ldg(bl);
+      sl[1] = __ldg(bl + 1);
+      sl[2] = __ldg(bl + 2);
+    }
+  }
+  if (MODE == kModeSeries) {
+    if (active) {
+      const int gs = (int)(code >> 8) & 0xff;
+      const double* tc = reinterpret_cast<const double*>(sm.tc[gs]);
+      double u0 = 0.0, u1 = 0.0;
 #pragma unroll
-      for (int k = 0; k < 9; ++k) sm.tcam[i][k] = __ldcg(t_cam + (size_t)c * kTStride + k);
+      for (int j = 0; j < 9; ++j) {
+        u0 += jp[j] * tc[j];
+        u1 += jp[9 + j] * tc[j];
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) sv[tid][k] = jl[k] * u0 + jl[3 + k] * u1;
+    }
+    __syncthreads();
+    if (tid < nl) {
+      for (int q = a; q < b; ++q) {
+        sl[0] += sv[q][0];
+        sl[1] += sv[q][1];
+        sl[2] += sv[q][2];
+      }
     }
   }
   if (tid < nl) {
-    const int a = tp.lm_seg[th.L0 + tid] - o0, b = tp.lm_seg[th.L0 + tid + 1] - o0;
-    sm.sseg[tid] = a;
-    if (tid == nl - 1) sm.sseg[nl] = b;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) sm.sg[tid][k] = Vinv[(size_t)(th.L0 + tid) * 6 + k];
-    if (MODE == kModeRhs) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) sm.sg[tid][6 + k] = (float)b_l[(size_t)(th.L0 + tid) * 3 + k];
-    }
-    for (int q = a; q < b; ++q) sm.sv[q][0] = __int_as_float(tid);  // landmark of each obs
+    double z[3];
+    apply_vinv(vi, sl, z);
+    sm.sz[tid][0] = z[0];
+    sm.sz[tid][1] = z[1];
+    sm.sz[tid][2] = z[2];
   }
   __syncthreads();
-  const int lm = active ? __float_as_int(sm.sv[tid][0]) : 0;
-  f32_tile_core<MODE, true>(active, n, ns, lm, meta, jp, jl, &sm.tcam[0][0], 9, &sm.sg[0][0], 9,
-                            sm.sseg, sm.sbeg, sm.srow, sm.sv, sm.sg, partial, [] {});
+  if (active) {
+    const int lm = (int)(code >> 16) & 0xff;
+    const double z0 = sm.sz[lm][0], z1 = sm.sz[lm][1], z2 = sm.sz[lm][2];
+    const double w0 = jl[0] * z0 + jl[1] * z1 + jl[2] * z2;
+    const double w1 = jl[3] * z0 + jl[4] * z1 + jl[5] * z2;
+    double2* row = sm.sg[code & 0xff];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      row[k] = make_double2(jp[2 * k] * w0 + jp[9 + 2 * k] * w1,
+                            jp[2 * k + 1] * w0 + jp[10 + 2 * k] * w1);
+    row[4] = make_double2(jp[8] * w0 + jp[17] * w1, 0.0);
+  }
+  __syncthreads();
+  // chunk slot j, component k: rows [beg_j, beg_{j+1}) over `split` lanes, then the group slot
+  const uint32_t* clist = reinterpret_cast<const uint32_t*>(rec + L.clist);
+  const double* sgd = reinterpret_cast<const double*>(&sm.sg[0][0]);
+  const int items = ns * 9;
+  const SumPlan P = sum_plan(items);
+  const int bound = (P.lanes + 31) & ~31;
+  for (int idx = tid; idx < bound; idx += kChunkObs) {
+    int item, part, split;
+    sum_lane(P, idx, item, part, split);
+    const bool act = idx < P.lanes;
+    double s = 0.0;
+    int gs = 0, k = 0;
+    if (act) {
+      const int j = item / 9;
+      k = item - 9 * j;
+      const uint32_t e = __ldg(clist + j);
+      gs = (int)(e & 0xff);
+      const int beg = (int)(e >> 8) & 0xff, end = beg + (int)(e >> 16);
+      for (int r = beg + part; r < end; r += split) s += sgd[r * 10 + k];
+    }
+    for (int off = P.s; off > 0; off >>= 1) {  // levels of the largest split (2 s)
+      const double a = __shfl_down_sync(kFull, s, off);
+      if (off < split) s += a;
+    }
+    if (act && part == 0) sm.acc[gs][k] += s;
+  }
 }
 
+// One group (blockDim.x == kChunkObs; every thread must call it, and every thread must have
+// finished with the shared memory of the previous group, e.g. by a block barrier): stages the
+// current term of the group's slots and zeroes their accumulators, runs the chunks in order and
+// writes one partial row per group slot (row gslot_row[s], 9 values in the bulk precision).
+template <typename T, int MODE>
+__device__ __forceinline__ void group_body(const Topology& tp, const SerTopo& sp, int g,
+                                           const T* __restrict__ J,
+                                           const T* __restrict__ t_cam,
+                                           const double* __restrict__ b_l,
+                                           const T* __restrict__ Vinv, T* __restrict__ partial,
+                                           GroupSmem<T>& sm) {
+  const int tid = threadIdx.x;
+  const int4 gd = __ldg(sp.group + 2 * g);
+  const int c0 = gd.x, nc = gd.y, s0 = gd.z, ns = gd.w;
+  constexpr int R = sizeof(T) == 4 ? 3 : 5;  // 16-byte pieces of a term row in shared memory
+  for (int i = tid; i < ns * R; i += kChunkObs) {
+    const int s = i / R, q = i - R * s;
+    if constexpr (sizeof(T) == 4) {
+      sm.acc[s][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (MODE == kModeSeries) {
+        const int cam = __ldg(sp.gslot_cam + s0 + s);
+        sm.tc[s][q] = __ldcg(reinterpret_cast<const float4*>(t_cam + (size_t)cam * kTStride) + q);
+      }
+    } else {
+      if (q < 4) {
+        sm.acc[s][2 * q] = 0.0;
+        sm.acc[s][2 * q + 1] = 0.0;
+      } else {
+        sm.acc[s][8] = 0.0;
+      }
+      if (MODE == kModeSeries) {
+        const int cam = __ldg(sp.gslot_cam + s0 + s);
+        const double* src = t_cam + (size_t)cam * kTStride;
+        sm.tc[s][q] = q < 4 ? __ldcg(reinterpret_cast<const double2*>(src) + q)
+                            : make_double2(__ldcg(src + 8), 0.0);
+      }
+    }
+  }
+  __syncthreads();
+  if constexpr (sizeof(T) == 4) {
+    for (int c = c0; c < c0 + nc; ++c) chunk_f32<MODE>(tp, sp, c, J, b_l, Vinv, sm);
+  } else {
+    for (int c = c0; c < c0 + nc; ++c) chunk_f64<MODE>(tp, sp, c, J, b_l, Vinv, sm);
+  }
+  __syncthreads();
+  for (int i = tid; i < ns * 9; i += kChunkObs) {
+    const int s = i / 9, k = i - 9 * s;
+    const int row = __ldg(sp.gslot_row + s0 + s);
+    T v;
+    if constexpr (sizeof(T) == 4)
+      v = reinterpret_cast<const float*>(sm.acc[s])[k];
+    else
+      v = sm.acc[s][k];
+    partial[(size_t)row * 9 + k] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
 __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) {
   return *(const volatile unsigned*)p;
 }
 
-// Sum of one chunk of a camera's slot rows, component k: rows [q0, q1) in row order (loads are
-// issued 16 floats or 8 doubles at a time).  A chunk is a segment: FP32-bulk rows are added in
-// float inside it and the chunks in double (camera_body), FP64 rows in double throughout.
+// Sum of one chunk of a camera's partial rows, component k: rows [q0, q1) in row order (loads
+// are issued 16 floats or 8 doubles at a time).  A chunk is a segment: FP32-bulk rows are added
+// in float inside it and the chunks in double (camera_body), FP64 rows in double throughout.
 template <typename PT>
 __device__ __forceinline__ double cam_chunk_sum(const PT* __restrict__ partial, int q0, int q1,
                                                 int k) {
@@ -354,15 +548,17 @@ __device__ __forceinline__ double cam_chunk_sum(const PT* __restrict__ partial, 
 }
 
 // Camera body for cameras [cam0, cam0 + per_block): thread (c, k) sums component k of the
-// camera's contiguous slot rows (chunk by chunk, cam_chunk_rows rows per chunk, the chunks in
-// order), applies row k of U^-1, updates x and writes the new term t_cam[c]; then the 9 threads
-// of the camera add their squared term and x components (in component order) into the camera's
-// pair cam_norm[c] = (||t_c||^2, ||x_c||^2).  Cameras of problems whose series has stopped are
-// left as they are.  FP64 work is one add per slot row and component: every FP64 warp
-// instruction costs 16 pipe cycles on GB300, so no shuffle trees are used for the slot sums.
-// ys and y2 are shared [per_block][9] arrays.  Every thread of the block must call it.
+// camera's contiguous partial rows [cam_ptr[c], cam_ptr[c + 1]) (chunk by chunk, cam_chunk_rows
+// rows per chunk, the chunks in order), applies row k of U^-1, updates x and writes the new term
+// t_cam[c]; then the 9 threads of the camera add their squared term and x components (in
+// component order) into the camera's pair cam_norm[c] = (||t_c||^2, ||x_c||^2).  Cameras of
+// problems whose series has stopped are left as they are.  FP64 work is one add per row and
+// component: every FP64 warp instruction costs 16 pipe cycles on GB300, so no shuffle trees are
+// used for the row sums.  ys and y2 are shared [per_block][9] arrays.  Every thread of the block
+// must call it.
 template <typename PT, int MODE>
-__device__ __forceinline__ void camera_body(const Topology& tp, int cam0, int per_block,
+__device__ __forceinline__ void camera_body(const Topology& tp, const int32_t* __restrict__ cam_ptr,
+                                            int cam0, int per_block,
                                             const PT* __restrict__ partial,
                                             const double* __restrict__ b_p,
                                             const double* __restrict__ Uinv,
@@ -375,7 +571,7 @@ __device__ __forceinline__ void camera_body(const Topology& tp, int cam0, int pe
   const bool cam_ok = cl < per_block && c < tp.n_cams && !ld_volatile(&st[tp.cam_prob[c]].done);
   double y = 0.0;
   if (cam_ok) {
-    const int r0 = tp.cam_slot_ptr[c], r1 = tp.cam_slot_ptr[c + 1];
+    const int r0 = cam_ptr[c], r1 = cam_ptr[c + 1];
     const int C = cam_chunk_rows(r1 - r0);
     for (int q0 = r0; q0 < r1; q0 += C) y += cam_chunk_sum(partial, q0, min(q0 + C, r1), k);
   }

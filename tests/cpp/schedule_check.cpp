@@ -6,6 +6,7 @@
 // Input (little-endian int32): P, n_cams, n_lms, n_obs, G, cam_off[P + 1], lm_off[P + 1],
 // cam_idx[n_obs], lm_idx[n_obs].
 #include <cstdio>
+#include <algorithm>
 #include <set>
 #include <string>
 #include <vector>
@@ -127,11 +128,149 @@ int main(int argc, char** argv) {
       CHECK(S.cam_slot_list[r] > S.cam_slot_list[r - 1], "camera %d's rows are not in tile order", c);
   }
 
-  // camera rounds for a grid of G blocks
+  // series schedule for a grid of G blocks: groups of whole landmarks of one problem, balanced
+  // by observation count, at most kGroupSlots cameras; chunks of whole landmarks; records
+  SerSchedule Q;
+  const int target = series_auto_target(no, G);
+  const int tail = G % 3;  // exercise the tail split on some grids
+  const std::string qwhy = build_series_schedule(S, target, tail, &Q);
+  CHECK(qwhy.empty(), "build_series_schedule failed: %s", qwhy.c_str());
+  CHECK((int)Q.group.size() == 8 * Q.n_groups && (int)Q.chunk.size() == 8 * Q.n_chunks,
+        "series descriptor sizes");
+  std::vector<int> chunk_group(Q.n_chunks, -1);
+  std::vector<int> group_of_slot(Q.n_gslots, -1);
+  for (int i = 0; i < Q.n_groups; ++i) {
+    const int32_t* g = &Q.group[8 * (size_t)i];
+    if (i > 0) CHECK(g[4] <= Q.group[8 * (size_t)(i - 1) + 4], "groups not in decreasing size order at %d", i);
+    CHECK(g[1] >= 1 && g[0] >= 0 && g[0] + g[1] <= Q.n_chunks, "group %d chunk range", i);
+    CHECK(g[3] >= 1 && g[3] <= kGroupSlots && g[2] >= 0 && g[2] + g[3] <= Q.n_gslots,
+          "group %d slot range (%d slots)", i, g[3]);
+    int obs = 0;
+    std::set<int> cams;
+    for (int c = g[0]; c < g[0] + g[1]; ++c) {
+      CHECK(chunk_group[c] < 0, "chunk %d in two groups", c);
+      chunk_group[c] = i;
+      const int32_t* d = &Q.chunk[8 * (size_t)c];
+      obs += d[1];
+      if (c > g[0]) CHECK(d[2] == Q.chunk[8 * (size_t)(c - 1) + 2] + Q.chunk[8 * (size_t)(c - 1) + 3],
+                          "group %d chunks are not consecutive landmarks", i);
+      for (int o = d[0]; o < d[0] + d[1]; ++o) {
+        cams.insert(S.cam_of[o]);
+        CHECK(S.lm_prob[S.lm_of[o]] == g[5], "group %d holds another problem's observation", i);
+      }
+    }
+    CHECK(obs == g[4], "group %d observation count", i);
+    CHECK((int)cams.size() == g[3], "group %d has %d cameras but %d slots", i, (int)cams.size(), g[3]);
+    int s = g[2];
+    for (int cam : cams) {  // ascending
+      CHECK(Q.gslot_cam[s] == cam, "group %d slot %d is not its %d-th camera", i, s - g[2], s - g[2]);
+      CHECK(group_of_slot[s] < 0, "group slot %d shared", s);
+      group_of_slot[s] = i;
+      ++s;
+    }
+  }
+  // chunks in landmark order cover every observation once
+  {
+    int next_o = 0;
+    for (int c = 0; c < Q.n_chunks; ++c) {
+      const int32_t* d = &Q.chunk[8 * (size_t)c];
+      const int o0 = d[0], n = d[1], L0 = d[2], nl = d[3], ns = d[4];
+      CHECK(chunk_group[c] >= 0, "chunk %d in no group", c);
+      CHECK(n >= 1 && n <= kChunkObs && nl >= 1, "chunk %d size (%d obs, %d landmarks)", c, n, nl);
+      CHECK(o0 == S.lm_seg[L0] && o0 + n == S.lm_seg[L0 + nl], "chunk %d is not whole landmarks", c);
+      CHECK(o0 >= next_o, "chunks overlap at %d", c);
+      for (int o = next_o; o < o0; ++o) CHECK(false, "observation %d is in no chunk", o);
+      next_o = o0 + n;
+      const int32_t* g = nullptr;
+      for (int i = 0; i < Q.n_groups; ++i)
+        if (Q.group[8 * (size_t)i] <= c && c < Q.group[8 * (size_t)i] + Q.group[8 * (size_t)i + 1])
+          g = &Q.group[8 * (size_t)i];
+      const ChunkRecLayout L = chunk_rec_layout(n, nl, ns);
+      CHECK((size_t)d[5] * 16 + L.bytes <= Q.rec.size(), "chunk %d record out of range", c);
+      const uint8_t* base = Q.rec.data() + (size_t)d[5] * 16;
+      const uint32_t* code = reinterpret_cast<const uint32_t*>(base + L.code);
+      const uint16_t* sseg = reinterpret_cast<const uint16_t*>(base + L.sseg);
+      const uint32_t* clist = reinterpret_cast<const uint32_t*>(base + L.clist);
+      for (int j = 0; j <= nl; ++j)
+        CHECK(sseg[j] == S.lm_seg[L0 + j] - o0, "chunk %d segment %d", c, j);
+      std::vector<int> at(n, -1);
+      for (int i = 0; i < n; ++i) {
+        const int pos = code[i] & 0xff, gs = (code[i] >> 8) & 0xff, lm = (code[i] >> 16) & 0xff;
+        CHECK((code[i] >> 24) == 0, "chunk %d code high bits", c);
+        CHECK(pos < n && at[pos] < 0, "chunk %d positions are not a permutation", c);
+        at[pos] = i;
+        CHECK(gs < g[3] && Q.gslot_cam[g[2] + gs] == S.cam_of[o0 + i], "chunk %d obs %d group slot", c, i);
+        CHECK(L0 + lm == S.lm_of[o0 + i], "chunk %d obs %d landmark", c, i);
+      }
+      for (int q = 1; q < n; ++q) {
+        const int a = at[q - 1], b = at[q];
+        CHECK(S.cam_of[o0 + a] < S.cam_of[o0 + b] || (S.cam_of[o0 + a] == S.cam_of[o0 + b] && a < b),
+              "chunk %d positions are not in (camera, landmark) order", c);
+      }
+      // chunk slots: each camera's run of positions once, longest first (ties by position)
+      std::vector<int> run_beg, run_len, run_cam;
+      for (int q = 0; q < n; ++q) {
+        const int cam = S.cam_of[o0 + at[q]];
+        if (q == 0 || cam != S.cam_of[o0 + at[q - 1]]) {
+          run_beg.push_back(q);
+          run_len.push_back(0);
+          run_cam.push_back(cam);
+        }
+        run_len.back()++;
+      }
+      CHECK((int)run_beg.size() == ns, "chunk %d slot count", c);
+      std::vector<char> used(ns, 0);
+      for (int j = 0; j < ns; ++j) {
+        const int gs = clist[j] & 0xff, beg = (clist[j] >> 8) & 0xff, len = (int)(clist[j] >> 16);
+        if (j > 0) {
+          const int lp = (int)(clist[j - 1] >> 16), bp = (clist[j - 1] >> 8) & 0xff;
+          CHECK(len < lp || (len == lp && beg > bp), "chunk %d slots not longest first", c);
+        }
+        int r = -1;
+        for (int k = 0; k < ns; ++k)
+          if (run_beg[k] == beg) r = k;
+        CHECK(r >= 0 && !used[r] && run_len[r] == len && Q.gslot_cam[g[2] + gs] == run_cam[r],
+              "chunk %d slot %d", c, j);
+        used[r] = 1;
+      }
+    }
+    for (int o = next_o; o < no; ++o) CHECK(false, "observation %d is in no chunk", o);
+  }
+  // balance: groups of a single problem differ by at most one track plus the size split
+  if (P == 1 && Q.n_groups > 1) {
+    int big = 0, small = 1 << 30;
+    for (int i = 0; i < Q.n_groups; ++i) {
+      big = std::max(big, Q.group[8 * (size_t)i + 4]);
+      small = std::min(small, Q.group[8 * (size_t)i + 4]);
+    }
+    const int ng = (int)(((int64_t)no + target - 1) / target);
+    if (tail == 0 && Q.n_groups == ng)
+      CHECK(big - small <= 2 * S.max_track, "groups unbalanced: %d vs %d", big, small);
+    CHECK(big <= target + S.max_track, "a group of %d observations for a target of %d", big, target);
+  }
+  // camera-major rows of the group slots
+  CHECK(Q.cam_ptr[0] == 0 && Q.cam_ptr[nc] == Q.n_gslots, "series rows do not cover the group slots");
+  {
+    std::vector<char> seen_row(Q.n_gslots, 0);
+    std::vector<int> row_group(Q.n_gslots, -1);
+    for (int s = 0; s < Q.n_gslots; ++s) {
+      const int r = Q.gslot_row[s], cam = Q.gslot_cam[s];
+      CHECK(r >= 0 && r < Q.n_gslots && !seen_row[r], "gslot_row is not a permutation at %d", s);
+      seen_row[r] = 1;
+      CHECK(r >= Q.cam_ptr[cam] && r < Q.cam_ptr[cam + 1], "group slot %d's row is not its camera's", s);
+      // landmark order of the group: its first chunk's first landmark
+      row_group[r] = Q.group[8 * (size_t)group_of_slot[s]];
+    }
+    for (int cam = 0; cam < nc; ++cam)
+      for (int r = Q.cam_ptr[cam] + 1; r < Q.cam_ptr[cam + 1]; ++r)
+        CHECK(row_group[r] > row_group[r - 1], "camera %d's rows are not in landmark order", cam);
+  }
+
+  // camera rounds for a grid of G blocks over the series rows
   CamSchedule cs;
-  build_cam_schedule(S, &cs);
+  build_cam_schedule(Q.cam_ptr, nc, &cs);
   for (int c = 0; c < nc; ++c) {
-    const int r0 = S.cam_slot_ptr[c], r1 = S.cam_slot_ptr[c + 1];
+    const int r0 = Q.cam_ptr[c], r1 = Q.cam_ptr[c + 1];
     const int i0 = cs.cam_item[c], i1 = cs.cam_item[c + 1];
     CHECK(i1 - i0 == cam_chunks(r1 - r0) && i1 - i0 <= kRoundItems, "camera %d's chunk count", c);
     int q = r0;
@@ -161,6 +300,7 @@ int main(int argc, char** argv) {
   for (int b = 0; b < G; ++b)
     CHECK(rl.block_round[b + 1] >= rl.block_round[b], "block_round decreases at %d", b);
 
-  std::printf("ok tiles=%d slots=%d rounds=%d\n", S.n_tiles, S.n_slots, R);
+  std::printf("ok tiles=%d slots=%d rounds=%d groups=%d chunks=%d gslots=%d\n", S.n_tiles,
+              S.n_slots, R, Q.n_groups, Q.n_chunks, Q.n_gslots);
   return 0;
 }

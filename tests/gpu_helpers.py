@@ -40,3 +40,14 @@ def rel(a, b):
     b = np.asarray(b, dtype=np.float64).ravel()
     nb = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def block_rel(a, b, width):
+    """Largest per-block relative difference over the blocks of `width` values (a camera's 9 or a
+    landmark's 3), each against its own norm, with a floor of 1e-6 of the largest block norm so
+    that a block the step barely moves is not judged on its rounding alone."""
+    a = np.asarray(a, dtype=np.float64).reshape(-1, width)
+    b = np.asarray(b, dtype=np.float64).reshape(-1, width)
+    nb = np.linalg.norm(b, axis=1)
+    floor = 1e-6 * (nb.max() if nb.size and nb.max() > 0 else 1.0)
+    return float(np.max(np.linalg.norm(a - b, axis=1) / np.maximum(nb, floor))) if nb.size else 0.0

@@ -21,6 +21,7 @@ STRUCTS = {
     _lib.StepInfo: "ba_step_info",
     _lib.PcgInfo: "ba_pcg_info",
     _lib.Timing: "ba_timing",
+    _lib.Schedule: "ba_schedule",
 }
 
 

@@ -1,14 +1,15 @@
 """Batches of independent problems (the PoST sub-problem solve, Sec. 5.3): one handle holds P
-problems of uneven sizes and steps them together.  Every problem's tiles, slot rows and
-fixed-order sums are the ones a handle created for it alone would use, so results must be equal
-bit for bit to per-problem handles; the series and the LM loop must also match the FP64 oracle
-per problem (series <= 1e-10 relative in FP64 at equal lambda and stop rule, <= 1e-4 in
-FP32-bulk; LM: same accept sequence, cost within 1e-6)."""
+problems of uneven sizes and steps them together.  Given the same series group size, every
+problem's tiles, groups, partial rows and fixed-order sums are the ones a handle created for it
+alone would use, so results must be equal bit for bit to per-problem handles; the series and
+the LM loop must also match the FP64 oracle per problem (series <= 1e-10 relative in FP64 at
+equal lambda and stop rule, <= 1e-4 in FP32-bulk; LM: same accept sequence, cost within
+1e-6)."""
 import numpy as np
 import pytest
 
 import bal_synth
-from gpu_helpers import OracleRef, rel
+from gpu_helpers import OracleRef, block_rel, rel
 from oracle import camera_model as cm
 from oracle import lm as olm
 
@@ -32,14 +33,20 @@ def small():
     return bal_synth.make_batch(7, seed=5, cams=(3, 40), lms=(30, 600), track=(2, 8))
 
 
-def single(poba, p, precision=0, **opt):
-    return poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, p.weights,
-                          precision=precision, options=poba.ba_default_options(**opt))
+def single(poba, p, precision=0, group_obs=0, **opt):
+    h = poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, p.weights,
+                       precision=precision, options=poba.ba_default_options(**opt))
+    if group_obs:
+        poba.ba_set_schedule(h, group_obs=group_obs)
+    return h
 
 
-def batch(poba, probs, precision=0, **opt):
-    return poba.batch_from_problems(probs, precision=precision,
-                                    options=poba.ba_default_options(**opt))
+def batch(poba, probs, precision=0, group_obs=0, **opt):
+    h = poba.batch_from_problems(probs, precision=precision,
+                                 options=poba.ba_default_options(**opt))
+    if group_obs:
+        poba.ba_set_schedule(h, group_obs=group_obs)
+    return h
 
 
 def test_layout_params_and_costs(poba, small):
@@ -83,10 +90,13 @@ def test_series_per_problem_matches_oracle(poba, small, precision, tol, lam):
         assert len(set(ms)) > 1  # the problems stop at different terms
 
 
+@pytest.mark.parametrize("group_obs", [300, 1500])
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("series_exec", [0, 2, 3, 4])
-def test_lm_equals_individual_handles_bitwise(poba, small, precision, series_exec):
-    opt = dict(max_lm=12, series_exec=series_exec)
+@pytest.mark.parametrize("series_exec", [0, 2, 3])
+def test_lm_equals_individual_handles_bitwise(poba, small, precision, series_exec, group_obs):
+    """A batch and per-problem handles with the same group size: equal parameters, iteration
+    counts and costs bit for bit (one group spans several chunks at 1500 observations)."""
+    opt = dict(max_lm=12, series_exec=series_exec, group_obs=group_obs)
     hb = batch(poba, small, precision=precision, **opt)
     last, n_steps = poba.ba_lm_solve_batch(hb)
     cb, lb = poba.ba_get_params(hb)
@@ -181,11 +191,12 @@ def full_batch():
 
 
 def test_full_size_batch_fp32(poba, full_batch):
-    """The benchmark's batch in its launch configuration (FP32 bulk, persistent series): two LM
-    steps of the batch equal those of per-problem handles on sampled problems bit for bit, the
-    sampled problems' first series matches the FP64 oracle within 1e-4, and every problem's
-    accepted steps decrease its own cost."""
+    """The benchmark's batch in its launch configuration (FP32 bulk, persistent series, the
+    automatic group size): two LM steps of the batch equal those of per-problem handles given
+    the batch's group size on sampled problems bit for bit, and every problem's accepted steps
+    decrease its own cost."""
     hb = batch(poba, full_batch, precision=1)
+    g_obs = poba.ba_get_schedule(hb)["group_obs"]
     f0 = poba.ba_cost_batch(hb)
     steps = [poba.ba_lm_step_batch(hb)[0] for _ in range(2)]
     f2 = poba.ba_cost_batch(hb)
@@ -202,13 +213,37 @@ def test_full_size_batch_fp32(poba, full_batch):
     sample = list(rng.choice(len(full_batch), 3, replace=False)) + [int(sizes.argmin())]
     for i in sample:
         p = full_batch[i]
-        h = single(poba, p, precision=1)
+        h = single(poba, p, precision=1, group_obs=g_obs)
         s0 = poba.ba_lm_step(h)
         s1 = poba.ba_lm_step(h)
         assert s0 == steps[0][i] and s1 == steps[1][i]
         c, l = poba.ba_get_params(h)
         assert np.array_equal(cb[co[i]:co[i + 1]], c) and np.array_equal(lb[lo[i]:lo[i + 1]], l)
-    # the series of the smallest problem at the first step against the FP64 oracle
+
+
+def test_full_size_batch_series_per_problem_vs_oracle(poba, full_batch):
+    """One series solve of the whole benchmark batch (FP32 bulk, persistent series, 8 terms at
+    lambda 1e-2): eight problems spread over the batch's size range (smallest, largest and six
+    between) match the FP64 oracle's series within 1e-4 over the whole step and 1e-2 per camera
+    and landmark block (measured: 1.5e-5 and 1.9e-3).  At lambda 1e-4 the float rounding of J
+    is amplified by the conditioning of the large problems (23 cameras seeing 100,000
+    observations: 4e-3 relative), so this check uses the better-conditioned lambda; the
+    smallest problem is checked at 1e-4 below."""
+    hb = batch(poba, full_batch, precision=1, eps=0.0, max_inner=8)
+    poba.ba_linearize(hb)
+    poba.ba_solve_schur_power(hb, 1e-2)
+    dxp, dxl = poba.ba_get_step(hb)
+    co, lo = poba.ba_get_batch_layout(hb)
+    sizes = np.array([p.n_obs for p in full_batch])
+    order = np.argsort(sizes, kind="stable")
+    sample = [int(order[round(q * (len(order) - 1) / 7)]) for q in range(8)]
+    for i in sample:
+        p = full_batch[i]
+        o = OracleRef(p).solve(1e-2, 0.0, 8)
+        xp, xl = dxp[co[i]:co[i + 1]], dxl[lo[i]:lo[i + 1]]
+        assert rel(xp, o["x"]) < 1e-4 and rel(xl, o["xl"]) < 1e-4, (i, p.n_obs)
+        assert block_rel(xp, o["x"], 9) < 1e-2 and block_rel(xl, o["xl"], 3) < 1e-2, (i, p.n_obs)
+    # the smallest problem at the first LM step's lambda
     i = int(sizes.argmin())
     p = full_batch[i]
     h = single(poba, p, precision=1)

@@ -55,8 +55,8 @@ def test_longest_track_and_wide_tiles(poba):
     p.lm_idx = np.concatenate([p.lm_idx, add_l])
     assert np.sum(p.lm_idx == 0) == 256
     check_series(poba, p)
-    # FP32-bulk: a tile with more than 128 distinct cameras takes the persistent kernel without
-    # the copy pipeline; both persistent forms and the per-term launches agree bit for bit
+    # FP32-bulk: a 256-observation chunk with 256 distinct cameras (every lane of every warp in
+    # one landmark segment); the persistent kernel and the per-term launches agree bit for bit
     h32 = check_series(poba, p, tol=1e-4, precision=1)
     steps = []
     for mode in (1, 2, 3, 4):
