@@ -154,6 +154,21 @@ ba_status ba_solve_schur_power(ba_handle* h, double lambda, ba_series_info* info
  * (non-finite cost at the current state), BA_ERR_TIMEOUT, BA_ERR_CUDA. */
 ba_status ba_lm_step(ba_handle* h, ba_step_info* info);
 
+/* LM steps as one CUDA graph (no counterpart in the paper).  With step graphs on (the default)
+ * the first LM step captures the device part of a step -- the linearisation, gated on a device
+ * flag that the previous step's decision raises when a step was accepted; damping and
+ * inversion; b~, x(0), the series in the handle's form (the persistent kernel included) and the
+ * back-substitution; the trial cost, the decision and the update; the copies of the step's
+ * records to pinned host memory -- and every step replays it: one graph launch, then one
+ * synchronisation to read the records.  The capture is redone when the options, the schedule,
+ * the timing switch or the barrier limit change.  Results equal the step-by-step launches bit
+ * for bit.  If the device cannot capture a form, the handle turns graphs off and launches the
+ * kernels one by one.  ba_get_step_graph: *enabled (may be NULL) the switch,
+ * *kernels_per_step (may be NULL) the kernel launches one replay makes (0: nothing captured
+ * yet). */
+ba_status ba_set_step_graph(ba_handle* h, int32_t enable);
+ba_status ba_get_step_graph(ba_handle* h, int32_t* enabled, int32_t* kernels_per_step);
+
 /* Run ba_lm_step until convergence (func_tol) or max_lm iterations.  trace may be NULL or
  * hold max_lm entries; *n_steps (may be NULL) receives the number of iterations run. */
 ba_status ba_lm_solve(ba_handle* h, ba_step_info* trace, int32_t* n_steps);

@@ -28,7 +28,8 @@ __all__ = ["PobaError", "Handle", "ba_default_options", "ba_create", "ba_set_opt
            "ba_get_series_trace", "ba_set_barrier_timeout", "ba_create_batch",
            "ba_get_batch_layout", "ba_get_series_state", "ba_lm_step_batch", "ba_lm_solve_batch",
            "ba_cost_batch", "batch_from_problems", "ba_autotune", "ba_adjoint",
-           "ba_solve_schur_pcg", "ba_get_schedule", "ba_set_schedule"]
+           "ba_solve_schur_pcg", "ba_get_schedule", "ba_set_schedule", "ba_set_step_graph",
+           "ba_get_step_graph"]
 
 BA_NOALLOC_MAX_CAMS = 4096
 
@@ -380,6 +381,18 @@ def ba_autotune(h: Handle, trials: int = 3) -> dict:
     e, k = C.c_int32(), C.c_int32()
     _check(library().ba_autotune(h.ptr, int(trials), C.byref(e), C.byref(k)), "ba_autotune")
     return {"exec": e.value, "blocks_per_sm": k.value}
+
+
+def ba_set_step_graph(h: Handle, enable: bool = True):
+    """LM steps replay one captured CUDA graph (the default) or launch kernel by kernel."""
+    _check(library().ba_set_step_graph(h.ptr, 1 if enable else 0), "ba_set_step_graph")
+
+
+def ba_get_step_graph(h: Handle) -> dict:
+    """{"enabled": bool, "kernels_per_step": int (0 before the first captured step)}."""
+    e, k = C.c_int32(), C.c_int32()
+    _check(library().ba_get_step_graph(h.ptr, C.byref(e), C.byref(k)), "ba_get_step_graph")
+    return {"enabled": bool(e.value), "kernels_per_step": k.value}
 
 
 def ba_get_schedule(h: Handle) -> dict:

@@ -95,6 +95,8 @@ SIGNATURES = {
     "ba_cost_batch": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ba_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "ba_get_schedule": (C.c_int, [C.c_void_p, C.POINTER(Schedule)]),
+    "ba_set_step_graph": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ba_get_step_graph": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "ba_set_schedule": (C.c_int, [C.c_void_p, C.POINTER(Schedule)]),
     "ba_adjoint": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_void_p, C.c_int32, C.POINTER(SeriesInfo)]),

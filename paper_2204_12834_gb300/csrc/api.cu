@@ -113,6 +113,7 @@ struct ba_handle {
   LmRecord* rec = nullptr;        // [n_probs]
   int32_t* not_spd = nullptr;
   int32_t* io_bad = nullptr;      // [2] non-finite flags of ba_set_params
+  int32_t* relin = nullptr;       // 1: the next captured LM step linearises (set on the device)
   int n_probs = 1;
   std::vector<int32_t> cam_off_h, lm_off_h;  // caller numbering of the problems' cameras / landmarks
 
@@ -123,9 +124,18 @@ struct ba_handle {
   LmRecord* h_rec = nullptr;     // [n_probs]
   int32_t* h_flag = nullptr;
   int32_t* h_io = nullptr;       // [2]
+  int32_t* h_relin = nullptr;    // host value written to relin before a captured step
   double* h_scalar = nullptr;
 
   bool linearized = false;
+  // LM steps as one captured CUDA graph (linearisation gated on the device flag relin, the
+  // solve, the evaluation and decision, the copies of the records to pinned host memory)
+  bool step_graph = true;
+  bool relin_synced = false;      // relin equals !linearized
+  cudaGraphExec_t step_exec = nullptr;
+  int step_kernels = 0;           // kernel nodes of the step graph
+  int step_mode = 0;              // the series form captured in it
+  std::vector<double> step_key;   // the configuration it was captured for
   bool cost_valid = false;
   bool have_step = false;
   bool last_solve_lm = false;  // the last solve was an LM step (per-problem lambdas)
@@ -161,6 +171,7 @@ struct ba_handle {
   // kernel timing: event pairs per class; series classes have one pair per term
   bool timing = false;
   bool capturing = false;
+  bool capturing_step = false;    // capturing an LM step (the series runs as per-term launches)
   int timing_terms = -1;
   std::vector<cudaEvent_t> ev;  // layout: see ev_index()
   double t_ms[BA_TIMING_CLASSES] = {0};
@@ -381,6 +392,7 @@ ba_status run_series_body(ba_handle* h, bool use_active) {
   int mode = h->opts.series_exec == 2 ? h->auto_exec : h->opts.series_exec;
   if (mode == 4 && h->stage_k <= 0) mode = 3;
   if (mode == 3 && h->plain_k <= 0) mode = 1;
+  if (mode == 1 && h->capturing_step) mode = 0;  // the step graph holds the per-term launches
   h->last_exec = mode;
   if (mode >= 3) {
     ba_status st = h->f32() ? seq_series_persistent<float>(h, s, use_active, mode == 4)
@@ -479,6 +491,7 @@ ba_status ba_destroy(ba_handle* h) {
   if (!h) return BA_OK;
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->step_exec) cudaGraphExecDestroy(h->step_exec);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->arena) cudaFree(h->arena);
   if (h->ser_arena) cudaFree(h->ser_arena);
@@ -490,6 +503,7 @@ ba_status ba_destroy(ba_handle* h) {
   if (h->h_gs) cudaFreeHost(h->h_gs);
   if (h->h_flag) cudaFreeHost(h->h_flag);
   if (h->h_io) cudaFreeHost(h->h_io);
+  if (h->h_relin) cudaFreeHost(h->h_relin);
   if (h->h_scalar) cudaFreeHost(h->h_scalar);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -573,6 +587,10 @@ ba_status rebuild_series(ba_handle* h, int group_obs, int tail) {
   if (h->graph_exec) {
     cudaGraphExecDestroy(h->graph_exec);
     h->graph_exec = nullptr;
+  }
+  if (h->step_exec) {
+    cudaGraphExecDestroy(h->step_exec);
+    h->step_exec = nullptr;
   }
   h->ser_arena = arena;
   h->ser_bytes = total;
@@ -798,6 +816,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   items.push_back({(void**)&h->rec, sizeof(LmRecord) * P});
   items.push_back({(void**)&h->not_spd, sizeof(int32_t) * P});
   items.push_back({(void**)&h->io_bad, sizeof(int32_t) * 2});
+  items.push_back({(void**)&h->relin, sizeof(int32_t)});
   size_t total = 0;
   for (auto& it : items) total = align_up(total, 256) + it.bytes;
   total = align_up(total, 256);
@@ -830,6 +849,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
       (e = cudaMallocHost(&h->h_gs, sizeof(GridSync))) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_flag, sizeof(int32_t) * P)) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_io, sizeof(int32_t) * 2)) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_relin, sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_scalar, sizeof(double) * 4)) != cudaSuccess)
     return bail(fail_cuda(e, "cudaMallocHost"));
 
@@ -971,27 +991,43 @@ void fill_step_info(const LmRecord& R, const SeriesState& S, ba_step_info* info)
   info->not_spd = R.not_spd;
 }
 
-// One LM iteration of every problem of the handle whose record is active; batch: a problem that
-// converges becomes inactive.  Reads the records and series states back (one synchronisation).
-ba_status lm_iteration(ba_handle* h, bool batch) {
+// The device part of one LM iteration of every problem whose record is active (batch: a
+// problem that converges becomes inactive), ending with the copies of the records, the series
+// states and the grid-barrier state to pinned host memory.  gated: the linearisation is gated
+// on the device flag relin, which the step clears and the decision raises when a step was
+// accepted (the captured form); else it runs when the host says the state moved.
+ba_status seq_lm_step(ba_handle* h, bool batch, bool gated) {
   cudaStream_t s = h->stream;
   const size_t P = (size_t)h->n_probs;
-  if (!h->cost_valid) {
-    seq_cost(h, rec_field(h->rec, offsetof(LmRecord, cost)), kRecStride);
-    h->cost_valid = true;
-  }
-  if (!h->linearized) {
+  if (gated) {
+    tmark(h, kTLin, 0, 0);
+    launch_cam_prepare(h->cams, nullptr, h->n_c, h->prep, nullptr, s, h->prep32, h->relin);
+    if (h->f32()) {
+      launch_linearize<float>(h->tp, h->prep32, h->lms, h->obs32, h->sqrt_w32, (float*)h->J,
+                              (float*)h->r, h->V, h->b_l, (float*)h->partial, h->block_cost, s,
+                              h->relin);
+      launch_lin_camera_reduce<float>(h->tp, (const float*)h->partial, h->U45, h->b_p, s,
+                                      h->relin);
+    } else {
+      launch_linearize<double>(h->tp, h->prep, h->lms, h->obs, h->sqrt_w, (double*)h->J,
+                               (double*)h->r, h->V, h->b_l, (double*)h->partial, h->block_cost,
+                               s, h->relin);
+      launch_lin_camera_reduce<double>(h->tp, (const double*)h->partial, h->U45, h->b_p, s,
+                                       h->relin);
+    }
+    tmark(h, kTLin, 0, 1);
+    h->launches += 3;
+    CK(cudaMemsetAsync(h->relin, 0, sizeof(int32_t), s));
+  } else if (!h->linearized) {
     seq_linearize(h);
-    h->linearized = true;
   }
-  h->last_solve_lm = true;
   ba_status st = run_solve(h, rec_field(h->rec, offsetof(LmRecord, lambda)), kRecStride, true);
   if (st != BA_OK) return st;
   tmark(h, kTEval, 0, 0);
   launch_cam_prepare(h->cams, h->x, h->n_c, h->prep_trial, h->cams_trial, s);
   launch_tile_cost(h->tp, h->prep_trial, h->lms, h->dx_l, h->obs, h->sqrt_w, h->tile_cost, s);
   launch_lm_decide(h->tp, h->tile_cost, h->block_pred, h->not_spd, h->rec, h->opts.func_tol,
-                   batch ? 1 : 0, s);
+                   batch ? 1 : 0, s, gated ? h->relin : nullptr);
   launch_apply_step(h->tp, h->rec, h->cams, h->cams_trial, h->lms, h->dx_l, s);
   tmark(h, kTEval, 0, 1);
   h->launches += 4;
@@ -1000,13 +1036,111 @@ ba_status lm_iteration(ba_handle* h, bool batch) {
   CK(cudaMemcpyAsync(h->h_rec, h->rec, sizeof(LmRecord) * P, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(SeriesState) * P, cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h->h_gs, h->gs, sizeof(GridSync), cudaMemcpyDeviceToHost, s));
+  return BA_OK;
+}
+
+// The configuration a captured LM step depends on (besides the series schedule, whose rebuild
+// drops the graph).
+std::vector<double> step_key(const ba_handle* h, bool batch) {
+  const ba_options& o = h->opts;
+  return {o.lambda0, o.func_tol, o.eps, (double)o.max_inner, (double)o.damping_mode,
+          (double)o.series_exec, (double)batch, (double)h->timing, (double)h->auto_exec,
+          (double)h->plain_k, (double)h->stage_k, (double)h->barrier_timeout};
+}
+
+// Captures the device part of an LM step as a graph (once per configuration).  False: the
+// capture failed (the step runs eagerly from then on).
+bool capture_lm_step(ba_handle* h, bool batch) {
+  const std::vector<double> key = step_key(h, batch);
+  if (h->step_exec && key == h->step_key) return true;
+  if (h->step_exec) {
+    cudaGraphExecDestroy(h->step_exec);
+    h->step_exec = nullptr;
+  }
+  if (h->timing && ensure_events(h) != BA_OK) return false;
+  cudaStream_t s = h->stream;
+  const uint64_t launches = h->launches;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  h->capturing = true;
+  h->capturing_step = true;
+  const ba_status st = seq_lm_step(h, batch, true);
+  h->capturing = false;
+  h->capturing_step = false;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  h->launches = launches;
+  for (int c = 0; c < BA_TIMING_CLASSES; ++c) h->pending[c] = false;
+  if (st != BA_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    g_last_error.clear();
+    return false;
+  }
+  size_t nn = 0;
+  cudaGraphGetNodes(g, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  cudaGraphGetNodes(g, nodes.data(), &nn);
+  int kernels = 0;
+  for (cudaGraphNode_t n : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(n, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+  }
+  e = cudaGraphInstantiate(&h->step_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->step_exec = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  h->step_kernels = kernels;
+  h->step_mode = h->last_exec;
+  h->step_key = key;
+  return true;
+}
+
+// One LM iteration of every problem of the handle whose record is active; batch: a problem that
+// converges becomes inactive.  With step graphs on (the default), the device part is one
+// replay of the captured step; otherwise the same kernels launch one by one.  Reads the
+// records and series states back (one synchronisation).
+ba_status lm_iteration(ba_handle* h, bool batch) {
+  cudaStream_t s = h->stream;
+  const size_t P = (size_t)h->n_probs;
+  if (!h->cost_valid) {
+    seq_cost(h, rec_field(h->rec, offsetof(LmRecord, cost)), kRecStride);
+    h->cost_valid = true;
+  }
+  h->last_solve_lm = true;
+  const bool was_linearized = h->linearized;
+  bool graph = h->step_graph && capture_lm_step(h, batch);
+  if (h->step_graph && !graph) h->step_graph = false;  // capture unsupported: stay eager
+  if (graph) {
+    if (!h->relin_synced) {
+      *h->h_relin = h->linearized ? 0 : 1;
+      CK(cudaMemcpyAsync(h->relin, h->h_relin, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaGraphLaunch(h->step_exec, s));
+    h->launches += (uint64_t)h->step_kernels;
+    h->last_exec = h->step_mode;
+    if (h->timing) {
+      h->pending[kTLin] = !was_linearized;
+      h->pending[kTDamp] = h->pending[kTRhs] = h->pending[kTBack] = h->pending[kTEval] = true;
+    }
+  } else {
+    ba_status st = seq_lm_step(h, batch, false);
+    if (st != BA_OK) return st;
+  }
   CK(cudaStreamSynchronize(s));
   collect_timing(h, max_terms(h), true);
   if (h->last_exec >= 3 && h->h_gs->error)
     return fail(BA_ERR_TIMEOUT, "a grid barrier of the persistent series kernel timed out");
   // one linearisation covers every problem: it is stale once any problem moved
+  h->linearized = true;
   for (size_t p = 0; p < P; ++p)
     if (h->h_rec[p].accepted) h->linearized = false;
+  h->relin_synced = graph;  // the captured decision set relin = any step accepted
   return BA_OK;
 }
 
@@ -1057,6 +1191,7 @@ ba_status ba_linearize(ba_handle* h, double* cost_out) {
   ba_status st = check_launch(h, "linearize kernels");
   if (st != BA_OK) return st;
   h->linearized = true;
+  h->relin_synced = false;
   if (cost_out) {
     launch_reduce_sum(h->block_cost, h->tp.n_tiles, h->scalars + 1, 1.0, h->stream);
     h->launches += 1;
@@ -1122,6 +1257,7 @@ ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* 
     ba_status st = check_launch(h, "linearize kernels");
     if (st != BA_OK) return st;
     h->linearized = true;
+    h->relin_synced = false;
   }
   // a candidate: execution form, blocks per SM, group size
   struct Cand {
@@ -1216,6 +1352,19 @@ ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* 
   return BA_OK;
 }
 
+ba_status ba_set_step_graph(ba_handle* h, int32_t enable) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  h->step_graph = enable != 0;
+  return BA_OK;
+}
+
+ba_status ba_get_step_graph(ba_handle* h, int32_t* enabled, int32_t* kernels_per_step) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  if (enabled) *enabled = h->step_graph ? 1 : 0;
+  if (kernels_per_step) *kernels_per_step = h->step_exec ? h->step_kernels : 0;
+  return BA_OK;
+}
+
 ba_status ba_get_schedule(ba_handle* h, ba_schedule* out) {
   if (!h || !out) return fail(BA_ERR_INVALID_ARG, "NULL argument");
   out->group_obs = h->ser.target;
@@ -1266,6 +1415,7 @@ ba_status ba_adjoint(ba_handle* h, double lambda, const double* g_cams, const do
     ba_status st = check_launch(h, "linearize kernels");
     if (st != BA_OK) return st;
     h->linearized = true;
+    h->relin_synced = false;
   }
   // the incoming gradient: device inputs are read in place, host inputs are staged in the
   // step buffers (which the solve overwrites)
@@ -1671,6 +1821,7 @@ ba_status ba_set_params(ba_handle* h, const double* cams, const double* lms, int
   if (lms) launch_gather_rows3(l_src, h->lm_order_dev, h->n_l, h->lms, s);
   h->launches += (cams ? 1 : 0) + (lms ? 2 : 0);
   h->linearized = false;
+  h->relin_synced = false;
   h->cost_valid = false;
   return check_launch(h, "state input");
 }

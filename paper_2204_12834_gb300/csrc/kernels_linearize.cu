@@ -24,9 +24,10 @@ namespace poba {
 // ---------------------------------------------------------------------------------------
 __global__ void cam_prepare_kernel(const double* __restrict__ cams, const double* __restrict__ dx_p,
                                    int n_cams, double* __restrict__ prep,
-                                   double* __restrict__ cams_out, float* __restrict__ prep32) {
+                                   double* __restrict__ cams_out, float* __restrict__ prep32,
+                                   const int32_t* __restrict__ gate) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_cams) return;
+  if (c >= n_cams || (gate && *gate == 0)) return;
   double p[9];
 #pragma unroll
   for (int j = 0; j < 9; ++j) p[j] = cams[c * 9 + j] + (dx_p ? dx_p[c * 9 + j] : 0.0);
@@ -83,10 +84,10 @@ __global__ void cam_prepare_kernel(const double* __restrict__ cams, const double
 }
 
 void launch_cam_prepare(const double* cams, const double* dx_p, int n_cams, double* prep,
-                        double* cams_out, cudaStream_t s, float* prep32) {
+                        double* cams_out, cudaStream_t s, float* prep32, const int32_t* gate) {
   // one warp per block: the FP64 rotation work (sin, cos, sqrt) spreads over many SMs
   int threads = 32, blocks = (n_cams + threads - 1) / threads;
-  cam_prepare_kernel<<<blocks, threads, 0, s>>>(cams, dx_p, n_cams, prep, cams_out, prep32);
+  cam_prepare_kernel<<<blocks, threads, 0, s>>>(cams, dx_p, n_cams, prep, cams_out, prep32, gate);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
     Topology tp, const T* __restrict__ prep, const double* __restrict__ lms,
     const vec2<T>* __restrict__ obs, const T* __restrict__ sqrt_w, T* __restrict__ J,
     T* __restrict__ r, double* __restrict__ V, double* __restrict__ b_l, T* __restrict__ partial,
-    double* __restrict__ block_cost) {
+    double* __restrict__ block_cost, const int32_t* __restrict__ gate) {
   // sj: J_p and r of each observation at its camera-sorted position; s9: the landmark
   // contributions.  In FP64 the two share storage (the static limit is 48 KB), with a barrier
   // between the landmark sums and the staging.
@@ -188,6 +189,7 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
   __shared__ int srow[kTileObs];
   __shared__ double sred[kTileObs];
 
+  if (gate && *gate == 0) return;  // the state did not change: the linearisation is current
   const int tile = blockIdx.x, tid = threadIdx.x;
   const int L0 = tp.tile_lm0[tile], L1 = tp.tile_lm0[tile + 1];
   const int o0 = tp.lm_seg[L0], n = tp.lm_seg[L1] - o0;
@@ -273,30 +275,31 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
 template <typename T>
 void launch_linearize(const Topology& tp, const T* prep, const double* lms, const vec2<T>* obs,
                       const T* sqrt_w, T* J, T* r, double* V, double* b_l, T* partial,
-                      double* block_cost, cudaStream_t s) {
+                      double* block_cost, cudaStream_t s, const int32_t* gate) {
   if (sqrt_w)
     linearize_kernel<T, true><<<tp.n_tiles, kTileObs, 0, s>>>(tp, prep, lms, obs, sqrt_w, J, r, V,
-                                                             b_l, partial, block_cost);
+                                                             b_l, partial, block_cost, gate);
   else
     linearize_kernel<T, false><<<tp.n_tiles, kTileObs, 0, s>>>(tp, prep, lms, obs, sqrt_w, J, r,
-                                                              V, b_l, partial, block_cost);
+                                                              V, b_l, partial, block_cost, gate);
 }
 template void launch_linearize<double>(const Topology&, const double*, const double*,
                                        const double2*, const double*, double*, double*, double*,
-                                       double*, double*, double*, cudaStream_t);
+                                       double*, double*, double*, cudaStream_t, const int32_t*);
 template void launch_linearize<float>(const Topology&, const float*, const double*,
                                       const float2*, const float*, float*, float*, double*,
-                                      double*, float*, double*, cudaStream_t);
+                                      double*, float*, double*, cudaStream_t, const int32_t*);
 
 // ---------------------------------------------------------------------------------------
 // Per camera: U (45 packed) and b_p (9) summed over the camera's slots in slot order.
 template <typename PT>
 __global__ void lin_camera_reduce_kernel(Topology tp, const PT* __restrict__ partial,
-                                         double* __restrict__ U45, double* __restrict__ b_p) {
+                                         double* __restrict__ U45, double* __restrict__ b_p,
+                                         const int32_t* __restrict__ gate) {
   const int per = kLinVals;
   const int c = blockIdx.x * 4 + threadIdx.x / per;
   const int k = threadIdx.x % per;
-  if (c >= tp.n_cams) return;
+  if (c >= tp.n_cams || (gate && *gate == 0)) return;
   // the camera's slot rows are contiguous (camera-major)
   const int r0 = tp.cam_slot_ptr[c], r1 = tp.cam_slot_ptr[c + 1];
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
@@ -315,12 +318,12 @@ __global__ void lin_camera_reduce_kernel(Topology tp, const PT* __restrict__ par
 
 template <typename PT>
 void launch_lin_camera_reduce(const Topology& tp, const PT* partial, double* U45, double* b_p,
-                              cudaStream_t s) {
+                              cudaStream_t s, const int32_t* gate) {
   const int blocks = (tp.n_cams + 3) / 4;
-  lin_camera_reduce_kernel<PT><<<blocks, 4 * kLinVals, 0, s>>>(tp, partial, U45, b_p);
+  lin_camera_reduce_kernel<PT><<<blocks, 4 * kLinVals, 0, s>>>(tp, partial, U45, b_p, gate);
 }
-template void launch_lin_camera_reduce<double>(const Topology&, const double*, double*, double*, cudaStream_t);
-template void launch_lin_camera_reduce<float>(const Topology&, const float*, double*, double*, cudaStream_t);
+template void launch_lin_camera_reduce<double>(const Topology&, const double*, double*, double*, cudaStream_t, const int32_t*);
+template void launch_lin_camera_reduce<float>(const Topology&, const float*, double*, double*, cudaStream_t, const int32_t*);
 
 // ---------------------------------------------------------------------------------------
 // Damping (reading of D: D^T D = diag(J^T J) clamped to [1e-6, 1e32], or D = I) and block

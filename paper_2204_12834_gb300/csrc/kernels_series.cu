@@ -329,7 +329,7 @@ constexpr double kLambdaMin = 1e-10, kLambdaMax = 1e32;
 
 __global__ void __launch_bounds__(kReduceThreads) lm_decide_kernel(
     Topology tp, const double* tile_cost, const double* tile_pred, const int32_t* not_spd,
-    LmRecord* rec_all, double func_tol, int deactivate) {
+    LmRecord* rec_all, double func_tol, int deactivate, int32_t* relin) {
   __shared__ double sred[kReduceThreads / 32];
   const int p = blockIdx.x;
   LmRecord* rec = rec_all + p;
@@ -370,6 +370,7 @@ __global__ void __launch_bounds__(kReduceThreads) lm_decide_kernel(
   rec->model_decrease = pred;
   rec->gain_ratio = rho;
   rec->accepted = accepted;
+  if (accepted && relin) *relin = 1;
   rec->not_spd = bad;
   rec->converged = (accepted && actual / F < func_tol) ? 1 : 0;
   rec->nonfinite = (bad || isfinite(F_new)) ? 0 : 1;
@@ -380,9 +381,9 @@ __global__ void __launch_bounds__(kReduceThreads) lm_decide_kernel(
 
 void launch_lm_decide(const Topology& tp, const double* tile_cost, const double* tile_pred,
                       const int32_t* not_spd, LmRecord* rec, double func_tol, int deactivate,
-                      cudaStream_t s) {
+                      cudaStream_t s, int32_t* relin) {
   lm_decide_kernel<<<tp.n_probs, kReduceThreads, 0, s>>>(tp, tile_cost, tile_pred, not_spd, rec,
-                                                         func_tol, deactivate);
+                                                         func_tol, deactivate, relin);
 }
 
 // x <- x + dx for the problems whose step was accepted (cameras already summed in cams_trial).

@@ -298,8 +298,11 @@ void set_last_error(const std::string& msg);
 // ---------------------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files).  All take the stream last.
 // prep32 (optional): a float copy of the records for the FP32-bulk linearisation.
+// gate (optional, device): the kernels return at once when *gate == 0 (a captured LM step skips
+// the linearisation when the last step was rejected; the flag is set on the device).
 void launch_cam_prepare(const double* cams, const double* dx_p, int n_cams, double* prep,
-                        double* cams_out, cudaStream_t s, float* prep32 = nullptr);
+                        double* cams_out, cudaStream_t s, float* prep32 = nullptr,
+                        const int32_t* gate = nullptr);
 
 // Pair type of the observations in a precision: double2 / float2.
 template <typename T> struct Vec2Of;
@@ -313,11 +316,11 @@ template <typename T> using vec2 = typename Vec2Of<T>::type;
 template <typename T>
 void launch_linearize(const Topology& tp, const T* prep, const double* lms, const vec2<T>* obs,
                       const T* sqrt_w, T* J, T* r, double* V, double* b_l, T* partial,
-                      double* block_cost, cudaStream_t s);
+                      double* block_cost, cudaStream_t s, const int32_t* gate = nullptr);
 
 template <typename PT>
 void launch_lin_camera_reduce(const Topology& tp, const PT* partial, double* U45, double* b_p,
-                              cudaStream_t s);
+                              cudaStream_t s, const int32_t* gate = nullptr);
 
 // lambda of problem p is lam[p * lam_stride] (lam_stride 0: one lambda for all problems);
 // not_spd[p] is set to 1 when a damped block of problem p fails its Cholesky factorisation (the
@@ -381,9 +384,11 @@ void launch_reduce_tiles(const Topology& tp, const double* tile_vals, double* ou
 // update; inactive problems are left as they are.  A problem whose damped blocks were not
 // positive definite (not_spd[p]) has no step: it is rejected.  deactivate: a converged problem
 // becomes inactive.
+// relin (optional, device): set to 1 when any problem's step was accepted (the state moved,
+// so the next step linearises).
 void launch_lm_decide(const Topology& tp, const double* tile_cost, const double* tile_pred,
                       const int32_t* not_spd, LmRecord* rec, double func_tol, int deactivate,
-                      cudaStream_t s);
+                      cudaStream_t s, int32_t* relin = nullptr);
 
 void launch_apply_step(const Topology& tp, const LmRecord* rec, double* cams,
                        const double* cams_trial, double* lms, const double* dx_l,

@@ -252,3 +252,37 @@ def test_full_size_batch_series_per_problem_vs_oracle(poba, full_batch):
     dxp, dxl = poba.ba_get_step(h)
     o = OracleRef(p).solve(1e-4, 0.0, info["inner_iters"])
     assert rel(dxp, o["x"]) < 1e-4 and rel(dxl, o["xl"]) < 1e-4
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("series_exec", [0, 1, 3, 4])
+def test_step_graph_equals_eager_bitwise(poba, precision, series_exec):
+    """A batch's LM steps replayed as one captured graph each (the linearisation gated on the
+    device flag that the previous step's decision raises) equal the kernel-by-kernel steps bit
+    for bit, through accepted and rejected steps; one replay launches the captured kernels."""
+    # far from the solution (20 % perturbation) with a tiny initial damping: the first trial
+    # steps overshoot and are rejected, so the device-side gate must skip relinearising
+    rng = np.random.default_rng(11)
+    probs = [bal_synth.make_problem(int(rng.integers(4, 30)), int(rng.integers(40, 400)),
+                                    track=("uniform", 2, 6), visibility="clustered",
+                                    sigma_init=0.2, seed=int(rng.integers(1 << 30)))
+             for _ in range(5)]
+    out = []
+    for graph in (True, False):
+        hb = batch(poba, probs, precision=precision, max_lm=12, series_exec=series_exec,
+                   lambda0=1e-9)
+        poba.ba_set_step_graph(hb, graph)
+        steps = []
+        for _ in range(8):
+            n0 = poba.ba_kernel_launches(hb)
+            infos, active = poba.ba_lm_step_batch(hb)
+            steps.append([(s["accepted"], repr(s["cost_after"]), s["lam"], s["inner"]) for s in infos])
+            if graph and len(steps) > 1:
+                k = poba.ba_get_step_graph(hb)["kernels_per_step"]
+                assert k > 0 and poba.ba_kernel_launches(hb) - n0 == k
+        assert poba.ba_get_step_graph(hb)["enabled"] == graph
+        out.append((steps, poba.ba_get_params(hb)))
+    (sg, (cg, lg)), (se, (ce, le)) = out
+    assert sg == se
+    assert np.array_equal(cg, ce) and np.array_equal(lg, le)
+    assert any(not a for st in sg for a, *_ in st) and any(a for st in sg for a, *_ in st)
