@@ -41,7 +41,11 @@ import bal_synth  # noqa: E402
 WORKLOAD = "clustered_1200c_160000l"
 METRIC = "LM iterations/s (power-series Schur PoBA, BAL camera model)"
 L2_FLUSH_BYTES = 512 << 20
-FP64_PEAK_TFLOPS_DERIVED = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk/SM x 2 x max clock
+# FP64 FMA issue rate of one GB300 SM per clock; ba_probe_fp64_fma (bench.py --fp64-probe)
+# measures the device rate that backs it
+FP64_FMA_PER_CLK_PER_SM = 2
+DEFAULT_MAX_SM_MHZ = 2070.0
+REFERENCE_BUDGET_S = 240.0
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -50,6 +54,27 @@ STANDS_IN_FOR = {
     "clustered_1200c_160000l": "BAL Ladybug-1197",
     "powerlaw_10000c_1000000l": "BAL Venice-1778",
 }
+
+
+def fp64_peak_tflops(sms: int, max_mhz) -> float:
+    """Derived FP64 FMA peak: SMs x FMA/clk/SM x 2 FLOP x maximum SM clock (the sampled
+    clocks.max.sm, else GB300's 2070 MHz)."""
+    return sms * FP64_FMA_PER_CLK_PER_SM * 2 * float(max_mhz or DEFAULT_MAX_SM_MHZ) * 1e6 / 1e12
+
+
+def headline_config(workload: str, p, world: int) -> dict:
+    """The `config` of the headline line; both arms print the same one."""
+    return {"workload": workload, "n_cams": p.n_cams, "n_lms": p.n_lms, "n_obs": p.n_obs,
+            "role": ("headline: the plain vs FP32-bulk PoBA problem (1,200 cameras, 160,000 "
+                     "landmarks, ~560,000 observations, 3-4 per landmark, clustered visibility), "
+                     "the workload on which the metric's time to 1% cost and the FP32-vs-FP64 "
+                     "error are defined; `value` is its FP64 LM iterations/s, `fp32_bulk` the "
+                     "FP32-bulk form; the 10,000-camera power-law problem is under `large`"),
+            "visibility": "clustered window 8, tracks U{3,4}",
+            "series": {"eps": 0.01, "max_inner": 20},
+            "lm": {"lambda0": 1e-4, "func_tol": 1e-6, "max_lm": 50, "restart_from_x0": True},
+            "l2": "GPU arm: flushed before every timed step (512 MiB write)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
 def data_note(workload: str) -> str:
@@ -82,6 +107,9 @@ def parse_args(argv=None):
                     help=argparse.SUPPRESS)
     ap.add_argument("--cpu-sync-dir", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-sync-n", type=int, default=1, help=argparse.SUPPRESS)
+    ap.add_argument("--fp64-probe", action="store_true",
+                    help="only measure the device's FP64 FMA rate (ba_probe_fp64_fma) with the "
+                         "SM clocks sampled during it, and print one JSON line")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run only this many untimed LM steps (for ncu captures)")
     ap.add_argument("--profile-precision", choices=["fp64", "fp32"], default="fp64")
@@ -448,6 +476,16 @@ def run_poba(args):
 
     # roofline of the dominant kernel class
     hbm_peak, hbm_kind, _, _ = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    l2_bytes = getattr(props, "L2_cache_size", 0) or (126 << 20)
+    max_mhz = float(clk.get("sm_max_mhz") or DEFAULT_MAX_SM_MHZ)
+    peak64 = fp64_peak_tflops(sms, max_mhz)
+    pr = max((poba.ba_probe_fp64_fma(4, 1 << 16, stream) for _ in range(3)),
+             key=lambda d: d["flops_per_s"])
+    probe = {"tflops": pr["flops_per_s"] / 1e12, "ms": pr["ms"],
+             "what": "ba_probe_fp64_fma: 4 blocks/SM x 256 threads x 8 independent FMA chains, "
+                     "best of 3 launches (untimed clocks; see bench.py --fp64-probe)"}
 
     def roofline(name):
         """Dominant kernel: the series (one term = tile phase and camera phase, plus the two
@@ -464,10 +502,15 @@ def run_poba(args):
         avg_s = (ms_t + ms_c) / 1e3 / max(cnt, 1)
         form = r["tuned"]["exec"]
         prec = "double" if name == "fp64" else "float"
-        kernel = {1: f"series_group_kernel<{prec}, 0> + camera_step_kernel<{prec}, 0> "
-                     "(replayed CUDA graph, one pair of launches per term)",
+        pair = (f"series_group_kernel<{prec}, 0> + camera_step_kernel<{prec}, 0> (one pair of "
+                "launches per term")
+        kernel = {0: pair + ")",
+                  1: pair + ", inside the captured LM-step graph)",
                   3: f"series_persistent_kernel<{prec}> (one series term: group phase, camera "
-                     "phase, two grid barriers)"}[form]
+                     "phase, two grid barriers)",
+                  4: "series_staged_kernel (persistent; each chunk's inputs staged in shared "
+                     "memory by bulk copies one chunk ahead; one term: group phase, camera "
+                     "phase, two grid barriers)"}.get(form, f"series form {form}")
         traffic = profiled_traffic(name, form)
         common = {"kernel": kernel, "series_form": r["tuned"], "schedule": sched,
                   "traffic": traffic, "algorithmic_bytes_per_term": nb,
@@ -476,16 +519,25 @@ def run_poba(args):
                   "dominant_class": cls}
         if name == "fp64":
             ach = nf / avg_s / 1e12
-            return {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS_DERIVED,
-                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS_DERIVED,
-                    "peak_kind": "derived FP64 FMA rate (152 SM x 2 FMA/clk x 2.07 GHz)",
-                    "achieved_gbs": nb / avg_s / 1e9, **common}
+            return {"bound": "alu", "achieved": ach, "peak": peak64, "unit": "TFLOP/s",
+                    "frac": ach / peak64,
+                    "peak_kind": (f"derived FP64 FMA rate ({sms} SMs x {FP64_FMA_PER_CLK_PER_SM} "
+                                  f"FMA/clk x 2 FLOP x {max_mhz:.0f} MHz max SM clock)"),
+                    "fp64_probe": probe, "achieved_gbs": nb / avg_s / 1e9, **common}
         ach = nb / avg_s / 1e9
-        return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+        line = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                 "frac": ach / hbm_peak,
                 "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)" if hbm_kind == "measured"
                 else "fallback 6800 GB/s",
                 "achieved_tflops": nf / avg_s / 1e12, **common}
+        if nb <= l2_bytes:
+            # the float Jacobians of this problem fit in L2: after the first term of a solve
+            # the series reads them from L2, so HBM does not bound it
+            line["bound"] = "l2-resident"
+            line["peak_kind"] += (f"; for comparison only: the term's {nb / 1e6:.0f} MB fit the "
+                                  f"{l2_bytes / 1e6:.0f} MB L2, so DRAM is not its bound (the "
+                                  "HBM-bound case is `large`)")
+        return line
 
     batched = None if args.no_batch else batched_section(args, poba, torch, stream, dev,
                                                            max_over_ranks, barrier)
@@ -527,12 +579,7 @@ def run_poba(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": data_note(args.workload),
-        "config": {"workload": args.workload, "n_cams": p.n_cams, "n_lms": p.n_lms,
-                   "n_obs": p.n_obs, "visibility": "clustered window 8, tracks U{3,4}",
-                   "series": {"eps": 0.01, "max_inner": 20}, "lm": {"lambda0": 1e-4,
-                   "func_tol": 1e-6, "max_lm": 50, "restart_from_x0": True},
-                   "l2": "flushed before every timed step (512 MiB write)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": headline_config(args.workload, p, world),
         "roofline": roof64,
         "clocks": clk,
         "gpu_launches": int(r64["launches"]),
@@ -793,7 +840,10 @@ def batched_section(args, poba, torch, stream, dev, max_over_ranks, barrier):
                 n_not_spd)
 
     solve()  # warm-up solve
-    tuned = poba.ba_autotune(hb, trials=2)  # picks the series execution form (untimed)
+    tuned = poba.ba_autotune(hb, trials=2)  # picks the series schedule and form (untimed)
+    schedule = poba.ba_get_schedule(hb)
+    solve()  # captures the LM-step graph for the tuned schedule (untimed)
+    graph = poba.ba_get_step_graph(hb)
     launches0 = poba.ba_kernel_launches(hb)
     barrier()
     runs = [solve() for _ in range(max(1, args.batch_solves))]
@@ -826,6 +876,12 @@ def batched_section(args, poba, torch, stream, dev, max_over_ranks, barrier):
         "converged": runs[-1][4],
         "not_spd_iterations": runs[-1][5],
         "series_form": tuned,
+        "schedule": schedule,
+        "step_graph": {"enabled": graph["enabled"], "kernels_per_step": graph["kernels_per_step"],
+                       "host_calls_per_step": ("one cudaGraphLaunch (the whole LM step: "
+                                               "linearisation gated on the device, series, "
+                                               "decision, record copies) + one stream sync"
+                                               if graph["enabled"] else "eager launches")},
         "fp64_batch": {"problems_per_s": P / (r64[0] / 1e3), "batch_solve_ms": r64[0],
                        "p50_solve_ms": float(np.percentile(r64[2], 50)),
                        "p99_solve_ms": float(np.percentile(r64[2], 99)),
@@ -968,9 +1024,21 @@ def cpu_baseline(args) -> dict:
     return line
 
 
+def oracle_lm_iterations(p, n: int, solver: str = "power") -> int:
+    """n LM iterations of the oracle's own loop (oracle.lm.lm_solve) from x0, restarting from x0
+    after convergence or 50 iterations, as the library arm does.  Within a solve the
+    linearisation is kept across rejected steps (lm_solve rebuilds it only after an accepted
+    one).  Returns the iterations run (n)."""
+    from oracle import lm as olm
+    done = 0
+    while done < n:
+        _, _, hist = olm.lm_solve(p, olm.Options(max_lm=min(50, n - done)), solver=solver)
+        done += len(hist)
+    return done
+
+
 def cpu_baseline_worker(args):
     import resource
-    from oracle import lm as olm
     p = bal_synth.preset(args.workload)
     if args.cpu_sync_dir:
         # start together: announce readiness, then wait (bounded) for the others
@@ -981,17 +1049,13 @@ def cpu_baseline_worker(args):
             time.sleep(0.01)
     start = time.time()
     t0 = time.perf_counter()
-    n = 0
-    # one LM iteration at a time, until the time budget is used (at least one iteration)
-    cams, lms = p.cams0, p.lms0
-    lam, nu = 1e-4, 2.0
-    while True:
-        cams, lms, hist = olm.lm_solve(p, olm.Options(max_lm=1, lambda0=lam),
-                                       solver=args.cpu_solver, cams=cams, lms=lms)
-        lam, nu = olm.lambda_update(lam, nu, hist[-1]["accepted"], hist[-1]["rho"])
-        n += 1
-        if time.perf_counter() - t0 > args.cpu_seconds:
-            break
+    # one iteration sizes the sample, then as many more as fit the time budget (a new solve
+    # from x0; each solve keeps its linearisation across rejected steps)
+    n = oracle_lm_iterations(p, 1, args.cpu_solver)
+    t1 = time.perf_counter() - t0
+    more = int(max(0.0, args.cpu_seconds - t1) // max(t1, 1e-9))
+    if more:
+        n += oracle_lm_iterations(p, more, args.cpu_solver)
     seconds = time.perf_counter() - t0
     rss = resource.getrusage(resource.RUSAGE_SELF).ru_maxrss * 1024  # KiB on Linux
     print(json.dumps({"iters": n, "seconds": seconds, "start": start, "end": start + seconds,
@@ -999,47 +1063,81 @@ def cpu_baseline_worker(args):
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle timed on the host cores (the paper ships no code)."""
+    """Reference arm: the FP64 CPU oracle's LM loop timed on the host cores (the paper ships no
+    code): W untimed warm-up iterations, then K timed ones (fewer only if K iterations would
+    exceed REFERENCE_BUDGET_S at the warm-up's pace; the line says so), on the same workload and
+    with the same config as the library arm."""
     rank, world, local = dist_env()
     if rank != 0:
         return
-    from oracle import lm as olm
     p = bal_synth.preset(args.workload)
-    cams, lms = p.cams0, p.lms0
-    lam, nu = 1e-4, 2.0
-    warm = min(args.warmup, 1)
-    for _ in range(warm):
-        olm.lm_solve(p, olm.Options(max_lm=1, lambda0=lam), cams=cams, lms=lms)
-    budget = 120.0
+    warm = max(0, args.warmup)
+    tw = time.perf_counter()
+    if warm:
+        oracle_lm_iterations(p, warm)
+    per = (time.perf_counter() - tw) / warm if warm else None
+    steps = max(1, args.steps)
+    if per and per * steps > REFERENCE_BUDGET_S:
+        steps = max(1, int(REFERENCE_BUDGET_S // per))
     t0 = time.perf_counter()
-    n = 0
-    while n < args.steps:
-        cams, lms, hist = olm.lm_solve(p, olm.Options(max_lm=1, lambda0=lam), cams=cams, lms=lms)
-        lam, nu = olm.lambda_update(lam, nu, hist[-1]["accepted"], hist[-1]["rho"])
-        n += 1
-        if time.perf_counter() - t0 > budget:
-            break
+    n = oracle_lm_iterations(p, steps)
     dt = time.perf_counter() - t0
     v = n / dt
-    sample = (f"{n} of {args.steps} requested oracle LM iterations (120 s cap) on the full "
-              f"{args.workload} problem, numpy/scipy FP64")
-    cores = 1
+    capped = "" if n == args.steps else f" (of {args.steps} requested: {REFERENCE_BUDGET_S:.0f} s cap)"
+    sample = (f"{n} oracle LM iterations{capped} after {warm} warm-up iterations, on the full "
+              f"{args.workload} problem from x0 (oracle.lm.lm_solve: linearisation kept across "
+              f"rejected steps, restart after convergence or 50 iterations), numpy/scipy FP64, "
+              f"1 thread")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "LM iterations/s",
         "n_gpus": world, "steps": n, "warmup": warm, "ms_per_step": 1e3 * dt / n,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": data_note(args.workload),
-        "config": {"workload": args.workload, "n_cams": p.n_cams, "n_lms": p.n_lms, "n_obs": p.n_obs},
-        "cpu_baseline": {"value": v, "unit": "LM iterations/s", "cores": cores, "kind": "oracle",
+        "config": headline_config(args.workload, p, world),
+        "cpu_baseline": {"value": v, "unit": "LM iterations/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "LM iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def run_fp64_probe(args):
+    """The FP64 FMA rate of the device (ba_probe_fp64_fma, 5 launches of each residency) with
+    the SM clocks sampled while it runs: per launch TFLOP/s and the FMA/clk/SM it implies at the
+    median sampled clock."""
+    import torch
+    import paper_2204_12834_gb300 as poba
+    from paper_2204_12834_gb300 import build as pbuild
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pbuild.build()
+    poba.library()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clocks = ClockSampler(local)
+    clocks.start()
+    rows = []
+    for bps in (1, 2, 4, 8):
+        for _ in range(5):
+            r = poba.ba_probe_fp64_fma(bps, 1 << 16, stream)
+            rows.append({"blocks_per_sm": bps, "tflops": r["flops_per_s"] / 1e12, "ms": r["ms"]})
+    clk = clocks.stop()
+    mhz = clk.get("sm_mhz") or DEFAULT_MAX_SM_MHZ
+    best = max(rows, key=lambda d: d["tflops"])
+    print(json.dumps({
+        "probe": "ba_probe_fp64_fma", "sms": sms, "threads_per_block": 256, "fma_chains": 8,
+        "iters": 1 << 16, "launches": rows, "best_tflops": best["tflops"],
+        "fma_per_clk_per_sm_at_median_clock": best["tflops"] * 1e12 / (2 * sms * mhz * 1e6),
+        "derived_peak_tflops": fp64_peak_tflops(sms, clk.get("sm_max_mhz")), "clocks": clk}),
+        flush=True)
 
 
 def main(argv=None):
     args = parse_args(argv)
     if args.cpu_baseline_worker:
         return cpu_baseline_worker(args)
+    if args.fp64_probe:
+        return run_fp64_probe(args)
     if args.impl == "reference":
         if os.environ.get("POBA_REFERENCE_CHILD") != "1":
             # pin BLAS / OpenMP to one thread so the reported core count is exact

@@ -240,8 +240,9 @@ ba_status ba_get_timing(ba_handle* h, ba_timing* out);
  * (camera rotation records and per-block sums) is one fixed device array of
  * BA_NOALLOC_MAX_CAMS * 25 + 2048 doubles (about 816 KiB) that every GPU using the library
  * holds until the process exits.  n_cams above BA_NOALLOC_MAX_CAMS is rejected with
- * BA_ERR_INVALID_ARG.  The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream capture.  All calls
+ * BA_ERR_INVALID_ARG.  Each call looks up the array's address in the current device's context
+ * (the first call on a device loads the module, so make it outside any stream capture); a
+ * context that was reset between calls is therefore safe.  All calls
  * share the one array and it keeps the last call's contents; every entry a call reads is
  * written earlier in the same call.  Calls that overlap on the GPU (other streams, other host
  * threads) race on the array: order them.  An out-of-range index makes *cost_out NaN. */
@@ -408,6 +409,17 @@ ba_status ba_get_series_trace(ba_handle* h, int64_t* ns, int32_t capacity, int32
  * persistent series kernel waits at a barrier before it gives up (default 2^33, several
  * seconds).  Values < 1 restore the default. */
 ba_status ba_set_barrier_timeout(ba_handle* h, int64_t cycles);
+
+/* Device rate probe (diagnostics; the paper has no counterpart).  Measures the FP64 fused
+ * multiply-add rate of the current device, the ceiling of the float64 series and
+ * linearisation kernels: one launch of blocks_per_sm x (number of SMs) blocks of 256 threads,
+ * each thread running 8 independent FMA chains for `iters` iterations, after one shorter
+ * untimed launch, timed with CUDA events on cuda_stream (NULL: the legacy default stream).
+ * *flops_per_s = 2 x FMAs / time; *ms_out (may be NULL) the timed launch in ms.  Synchronises
+ * the stream.  Errors: BA_ERR_INVALID_ARG (blocks_per_sm outside [1, 8], iters < 1, NULL
+ * flops_per_s), BA_ERR_CUDA. */
+ba_status ba_probe_fp64_fma(int32_t blocks_per_sm, int32_t iters, void* cuda_stream,
+                            double* flops_per_s, double* ms_out);
 
 /* Static string for a status code. */
 const char* ba_status_string(ba_status s);

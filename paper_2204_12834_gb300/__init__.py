@@ -29,7 +29,7 @@ __all__ = ["PobaError", "Handle", "ba_default_options", "ba_create", "ba_set_opt
            "ba_get_batch_layout", "ba_get_series_state", "ba_lm_step_batch", "ba_lm_solve_batch",
            "ba_cost_batch", "batch_from_problems", "ba_autotune", "ba_adjoint",
            "ba_solve_schur_pcg", "ba_get_schedule", "ba_set_schedule", "ba_set_step_graph",
-           "ba_get_step_graph"]
+           "ba_get_step_graph", "ba_probe_fp64_fma"]
 
 BA_NOALLOC_MAX_CAMS = 4096
 
@@ -362,8 +362,19 @@ def ba_cost_noalloc(cams, lms, obs, cam_idx, lm_idx, cost_out, weights=None, str
                                      *args, st), "ba_cost_noalloc")
 
 
+def ba_probe_fp64_fma(blocks_per_sm: int = 4, iters: int = 1 << 16, stream=None) -> dict:
+    """The device's FP64 FMA rate (see poba.h): {"flops_per_s", "ms"} of one timed launch."""
+    st = None
+    if stream is not None:
+        st = int(getattr(stream, "cuda_stream", stream)) or None
+    f, ms = C.c_double(), C.c_double()
+    _check(library().ba_probe_fp64_fma(int(blocks_per_sm), int(iters), st, C.byref(f),
+                                       C.byref(ms)), "ba_probe_fp64_fma")
+    return {"flops_per_s": f.value, "ms": ms.value}
+
+
 def ba_get_series_trace(h: Handle):
-    """[terms, 5] ns timeline of the last block in the last persistent series solve (see poba.h)."""
+    """[terms, 5] ns timeline of block 0 in the last persistent series solve (see poba.h)."""
     buf = np.zeros(64 * 5, dtype=np.int64)
     n = C.c_int32()
     _check(library().ba_get_series_trace(h.ptr, buf.ctypes.data, buf.size, C.byref(n)),

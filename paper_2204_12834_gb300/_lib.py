@@ -85,6 +85,8 @@ SIGNATURES = {
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p]),
     "ba_set_barrier_timeout": (C.c_int, [C.c_void_p, C.c_int64]),
+    "ba_probe_fp64_fma": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double)]),
     "ba_get_series_trace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     "ba_create_batch": (C.c_int, [C.POINTER(ProblemDesc), C.c_int32, C.POINTER(Options),
                                   C.POINTER(C.c_void_p)]),

@@ -18,7 +18,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpoba.so")
 SOURCES = ["schedule.cpp", "kernels_linearize.cu", "kernels_series.cu", "kernels_persistent.cu",
            "kernels_adjoint.cu", "kernels_pcg.cu",
-           "api.cu", "noalloc.cu"]
+           "api.cu", "noalloc.cu", "probe.cu"]
 HEADERS = [os.path.join(CSRC, "poba_internal.cuh"), os.path.join(CSRC, "tile_common.cuh"),
            os.path.join(CSRC, "jacobian_io.cuh"),
            os.path.join(CSRC, "series_body.cuh"),

@@ -9,7 +9,6 @@
 // that loads the library holds that array until the process exits.
 #include <cmath>
 #include <cstdint>
-#include <mutex>
 #include <string>
 
 #include "../../include/poba.h"
@@ -38,7 +37,9 @@ __global__ void __launch_bounds__(kNoAllocThreads) cost_noalloc_kernel(
     const double* __restrict__ weights, double* __restrict__ block_sums) {
   __shared__ double sred[kNoAllocThreads / 32];
   double acc = 0.0;
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n_obs; o += gridDim.x * blockDim.x) {
+  // 64-bit index: n_obs may come within one grid's stride of INT_MAX
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n_obs; o += stride) {
     const int c = cam_idx[o], l = lm_idx[o];
     if (c < 0 || c >= n_cams || l < 0 || l >= n_lms) {
       acc += NAN;
@@ -63,10 +64,6 @@ __global__ void __launch_bounds__(kNoAllocThreads) cost_noalloc_kernel(
 }
 
 namespace {
-std::mutex g_noalloc_mutex;
-constexpr int kMaxDevices = 64;
-double* g_noalloc_addr[kMaxDevices] = {nullptr};
-
 ba_status reject(ba_status s, const std::string& why) {
   set_last_error(why);
   return s;
@@ -95,35 +92,24 @@ ba_status ba_cost_noalloc(int32_t n_cams, int32_t n_lms, int32_t n_obs, const do
     return reject(BA_ERR_INVALID_ARG, "ba_cost_noalloc: obs must be 16-byte aligned");
   cudaStream_t s = (cudaStream_t)cuda_stream;
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  // The scratch array's address in the current device's context, looked up on every call (no
+  // cache: a context that was reset and re-created holds the array at a new address).
+  void* ptr = nullptr;
+  const cudaError_t ea = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (ea != cudaSuccess || !ptr) {
     cudaGetLastError();
-    return reject(BA_ERR_CUDA, "ba_cost_noalloc: no usable current device");
+    return reject(BA_ERR_CUDA, std::string("ba_cost_noalloc: cudaGetSymbolAddress: ") +
+                                   cudaGetErrorString(ea));
   }
-  double* scratch = nullptr;
-  {
-    // Once per device, with that device current: the device address of the scratch array.
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-      void* ptr = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-      if (e != cudaSuccess || !ptr) {
-        cudaGetLastError();
-        return reject(BA_ERR_CUDA, std::string("ba_cost_noalloc: cudaGetSymbolAddress: ") +
-                                       cudaGetErrorString(e));
-      }
-      g_noalloc_addr[dev] = (double*)ptr;
-    }
-    scratch = g_noalloc_addr[dev];
-  }
+  double* scratch = (double*)ptr;
   double* prep = scratch;
   double* block_sums = scratch + kNoAllocPrepDoubles;
 
   // Every scratch entry the kernels read is written earlier in the same call (camera records
   // for all n_cams cameras, one partial per launched block), so nothing needs clearing.
   launch_cam_prepare(cams, nullptr, n_cams, prep, nullptr, s);
-  int blocks = (n_obs + kNoAllocThreads - 1) / kNoAllocThreads;
-  blocks = blocks < 1 ? 1 : (blocks > kNoAllocMaxBlocks ? kNoAllocMaxBlocks : blocks);
+  const int64_t want = ((int64_t)n_obs + kNoAllocThreads - 1) / kNoAllocThreads;
+  const int blocks = want < 1 ? 1 : (want > kNoAllocMaxBlocks ? kNoAllocMaxBlocks : (int)want);
   cost_noalloc_kernel<<<blocks, kNoAllocThreads, 0, s>>>(n_cams, n_lms, n_obs, prep, lms,
                                                          (const double2*)obs, cam_idx, lm_idx,
                                                          weights, block_sums);

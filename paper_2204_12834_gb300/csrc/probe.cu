@@ -1,0 +1,82 @@
+// Device rate probe (ba_probe_fp64_fma): the FP64 fused multiply-add issue rate of the current
+// device, the ceiling of the float64 series and linearisation kernels, which are bound by
+// FP64 arithmetic rather than memory.  Each thread runs eight independent FMA chains
+// a <- a * m + c with |m| < 1, so the values stay finite and the compiler can neither fold nor
+// drop the chains (a result that is never equal to the seed is stored conditionally).
+#include <cstdint>
+#include <string>
+
+#include "../../include/poba.h"
+#include "poba_internal.cuh"
+
+namespace poba {
+
+constexpr int kProbeThreads = 256;
+constexpr int kProbeChains = 8;
+
+static __device__ double g_probe_sink;
+
+__global__ void __launch_bounds__(kProbeThreads) fp64_fma_probe_kernel(int iters, double seed) {
+  double a[kProbeChains];
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) a[k] = seed + 1e-3 * (threadIdx.x + k);
+  const double m = 0.99999999, c = 1e-9;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = fma(a[k], m, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) s += a[k];
+  if (s == seed) g_probe_sink = s;  // never true for these values
+}
+
+}  // namespace poba
+
+extern "C" {
+
+ba_status ba_probe_fp64_fma(int32_t blocks_per_sm, int32_t iters, void* cuda_stream,
+                            double* flops_per_s, double* ms_out) {
+  using namespace poba;
+  if (blocks_per_sm < 1 || blocks_per_sm > 8 || iters < 1 || !flops_per_s) {
+    set_last_error("ba_probe_fp64_fma: need 1 <= blocks_per_sm <= 8, iters >= 1, flops_per_s");
+    return BA_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("ba_probe_fp64_fma: no usable current device");
+    return BA_ERR_CUDA;
+  }
+  const int blocks = sms * blocks_per_sm;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    set_last_error("ba_probe_fp64_fma: cudaEventCreate failed");
+    return BA_ERR_CUDA;
+  }
+  // one untimed launch (clocks ramp, module loaded), then the timed one
+  fp64_fma_probe_kernel<<<blocks, kProbeThreads, 0, s>>>(iters / 4 + 1, 1.0);
+  cudaEventRecord(e0, s);
+  fp64_fma_probe_kernel<<<blocks, kProbeThreads, 0, s>>>(iters, 1.0);
+  cudaEventRecord(e1, s);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error(std::string("ba_probe_fp64_fma: ") + cudaGetErrorString(e));
+    return BA_ERR_CUDA;
+  }
+  const double fma = (double)blocks * kProbeThreads * kProbeChains * (double)iters;
+  *flops_per_s = 2.0 * fma / (ms * 1e-3);
+  if (ms_out) *ms_out = ms;
+  return BA_OK;
+}
+
+}  // extern "C"

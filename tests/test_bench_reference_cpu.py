@@ -32,10 +32,17 @@ def test_reference_arm_prints_one_contract_line():
                 "cpu_baseline", "e2e"):
         assert key in d, key
     assert d["value"] > 0 and d["steps"] == 3 and d["higher_is_better"] is True
+    assert d["warmup"] == 3  # --warmup is honoured in full
     assert d["unit"] == "LM iterations/s" and d["dtype"] == "f64"
     assert d["config"]["workload"] == "uniform_16c_1000l"
     assert d["config"]["n_cams"] == 16 and d["config"]["n_lms"] == 1000
     assert "no BAL counterpart" in d["data"]
+    # the same config dict as the library arm's line (built by the same function)
+    sys.path.insert(0, ROOT)
+    import bal_synth
+    import bench
+    assert d["config"] == json.loads(json.dumps(bench.headline_config(
+        "uniform_16c_1000l", bal_synth.preset("uniform_16c_1000l"), 1)))
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
     e2e = d["e2e"]
@@ -55,3 +62,18 @@ def test_data_note_names_the_stand_in():
     assert "Ladybug-1197" in bench.data_note("clustered_1200c_160000l")
     assert "Venice-1778" in bench.data_note("powerlaw_10000c_1000000l")
     assert "synthetic" in bench.data_note("weighted_200c_20000l")
+
+
+def test_oracle_lm_iterations_restart_and_count():
+    """The reference arm's step loop runs exactly n oracle LM iterations, restarting from x0
+    after a solve converges (so n may exceed one solve's length)."""
+    sys.path.insert(0, ROOT)
+    import bal_synth
+    import bench
+    from oracle import lm as olm
+    p = bal_synth.preset("uniform_16c_1000l")
+    _, _, hist = olm.lm_solve(p)
+    one = len(hist)
+    assert one < 50  # this small problem converges
+    n = one + 3
+    assert bench.oracle_lm_iterations(p, n) == n

@@ -164,3 +164,31 @@ def test_adjoint_weighted_200c_20000l(poba):
                                         m_max=40)
     assert info["inner_iters"] == m == 40
     assert rel(d_obs, o_obs) < 1e-10 and rel(d_w, o_w) < 1e-10
+
+
+def test_autograd_backward_restores_options_and_flags_truncation(poba, monkeypatch):
+    """The backward applies adjoint_options to its own solve only: the handle gets the forward's
+    options back afterwards.  A series cut at its term cap (2 terms, eps 1e-14) raises a
+    RuntimeWarning and leaves its state in BundleAdjustment.last_adjoint_info."""
+    import torch
+    from paper_2204_12834_gb300 import autograd as ag
+    p = bal_synth.make_problem(12, 300, track=("uniform", 3, 5), weighted=True, seed=306)
+    dev = torch.device("cuda")
+    obs = torch.tensor(p.obs, device=dev, requires_grad=True)
+    fwd = poba.ba_default_options(max_lm=10, eps=0.02)
+    adj = poba.ba_default_options(eps=1e-14, max_inner=2)
+    calls = []
+    real = ag.ba_set_options
+    monkeypatch.setattr(ag, "ba_set_options",
+                        lambda h, o: (calls.append((o.eps, o.max_inner, o.max_lm)), real(h, o)))
+    cams, lms = ag.bundle_adjust(obs, torch.tensor(p.cams0, device=dev),
+                                 torch.tensor(p.lms0, device=dev),
+                                 torch.tensor(p.cam_idx, device=dev),
+                                 torch.tensor(p.lm_idx, device=dev),
+                                 options=fwd, adjoint_lambda=1e-3, adjoint_options=adj)
+    with pytest.warns(RuntimeWarning, match="truncated"):
+        (cams.sum() + lms.sum()).backward()
+    assert calls == [(1e-14, 2, adj.max_lm), (0.02, fwd.max_inner, 10)]
+    info = ag.BundleAdjustment.last_adjoint_info
+    assert info["inner_iters"] == 2 and not info["stopped"]
+    assert torch.isfinite(obs.grad).all()
