@@ -510,7 +510,10 @@ def run_poba(args):
                      "phase, two grid barriers)",
                   4: "series_staged_kernel (persistent; each chunk's inputs staged in shared "
                      "memory by bulk copies one chunk ahead; one term: group phase, camera "
-                     "phase, two grid barriers)"}.get(form, f"series form {form}")
+                     "phase, two grid barriers)",
+                  5: f"series_dataflow_kernel<{prec}> (persistent, no grid barriers: groups of "
+                     "term i start once their cameras' term i-1 updates are published; one term "
+                     "= the time of the whole launch / terms)"}.get(form, f"series form {form}")
         traffic = profiled_traffic(name, form)
         common = {"kernel": kernel, "series_form": r["tuned"], "schedule": sched,
                   "traffic": traffic, "algorithmic_bytes_per_term": nb,

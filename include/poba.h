@@ -80,12 +80,18 @@ typedef struct {
                            replayed as a captured CUDA graph, 3 one persistent cooperative kernel
                            for all terms with bounded grid barriers, 4 (BA_FP32_BULK; else as 3)
                            the persistent kernel with each chunk's inputs staged in shared
-                           memory by bulk asynchronous copies issued one chunk ahead, 2
+                           memory by bulk asynchronous copies issued one chunk ahead, 5 one
+                           persistent cooperative kernel without grid barriers: blocks take
+                           (term, group) tickets, a group starts once the previous term's
+                           update of its cameras is published, and the block that completes a
+                           camera's rows of a term runs that camera's update (and the block
+                           that completes a problem's cameras its stop rule), so blocks run
+                           ahead into the next term instead of waiting for the slowest group, 2
                            (default) the handle's schedule (ba_set_schedule / ba_autotune; at
                            creation 3 at the largest residency, 4 blocks per SM in BA_FP32_BULK,
                            3 in BA_FP64).  A device that cannot run a persistent form falls back
-                           (4 to 3, 3 to 1: all blocks must be co-resident).  All forms give
-                           bitwise-equal results for the handle's series schedule. */
+                           (4 and 5 to 3, 3 to 1: all blocks must be co-resident).  All forms
+                           give bitwise-equal results for the handle's series schedule. */
 } ba_options;
 
 typedef struct {
@@ -339,15 +345,16 @@ ba_status ba_solve_schur_pcg(ba_handle* h, double lambda, int32_t precond, int32
  *                  out largest first), so that the blocks that finish early even out the end of
  *                  the phase; 0: no split (the default at creation);
  *   series_exec    the form series_exec 2 runs: 1 (graph of per-term launches), 3 (persistent
- *                  kernel) or 4 (persistent kernel with staged chunks, BA_FP32_BULK);
+ *                  kernel), 4 (persistent kernel with staged chunks, BA_FP32_BULK) or 5
+ *                  (dataflow persistent kernel);
  *   blocks_per_sm  the persistent kernel's residency (1 .. its occupancy limit on the device:
- *                  on GB300 4 for form 3 in BA_FP32_BULK, 3 in BA_FP64, 3 for form 4);
+ *                  on GB300 4 for forms 3 and 5 in BA_FP32_BULK, 3 in BA_FP64, 3 for form 4);
  *   n_groups, n_chunks, n_group_slots (ba_get_schedule only): the resulting schedule; the
  *                  camera step sums n_group_slots partial rows of 9 values per term.
  * ba_set_schedule rebuilds the schedule on the host when the group size changes (it waits for
  * the handle's stream and replaces the schedule's device allocation).  Errors:
- * BA_ERR_INVALID_ARG (negative group_obs, tail_parts outside [0, 64], a form other than 1, 3 or
- * 4, form 4 in BA_FP64, a residency out of range),
+ * BA_ERR_INVALID_ARG (negative group_obs, tail_parts outside [0, 64], a form other than 1, 3, 4
+ * or 5, form 4 in BA_FP64, a residency out of range),
  * BA_ERR_OOM, BA_ERR_CUDA. */
 typedef struct {
   int32_t group_obs;
@@ -362,12 +369,13 @@ ba_status ba_set_schedule(ba_handle* h, const ba_schedule* in);
 /* Autotuner of the series schedule (no counterpart in the paper; the schedule choice of the
  * batched form).  On the handle's current linearisation (linearising first if needed) it times
  * `trials` series solves (damp, invert, max_inner terms, back-substitution; after one warm-up)
- * at lambda0 for: each persistent form (3, and 4 in BA_FP32_BULK) at each residency the device
- * allows with one group per block (group_obs = n_obs / (grid - 1)) and a tail split of 2; at the
- * fastest of those, tail splits of 0 and 4 and half the group size; and the replayed CUDA graph
- * of per-term launches on the fastest schedule.  The fastest becomes the handle's schedule
- * (ba_get_schedule reports it) and the form series_exec 2 runs.  Overwrites the last step (as
- * ba_solve_schur_power does).  *exec_out (may be NULL) receives the chosen form (1, 3 or 4),
+ * at lambda0 for: each persistent form (3, 5, and 4 in BA_FP32_BULK) at each residency the
+ * device allows with one group per block (group_obs = n_obs / (the blocks that run groups))
+ * and no tail split; at the fastest of those, tail splits of 0 and 4 and half the group size;
+ * and the replayed CUDA graph of per-term launches on the fastest schedule.  The fastest
+ * becomes the handle's schedule (ba_get_schedule reports it) and the form series_exec 2 runs.
+ * Overwrites the last step (as ba_solve_schur_power does).  *exec_out (may be NULL) receives
+ * the chosen form (1, 3, 4 or 5),
  * *blocks_per_sm_out (may be NULL) its blocks per SM (0 for the graph).  Synchronises.
  * Errors: BA_ERR_INVALID_ARG (trials < 1), and those of ba_solve_schur_power. */
 ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* blocks_per_sm_out);
@@ -399,10 +407,13 @@ ba_status ba_adjoint(ba_handle* h, double lambda, const double* g_cams, const do
 ba_status ba_destroy(ba_handle* h);
 
 /* Phase timeline of the last persistent series solve: for each executed term (at most 64),
- * five %globaltimer readings in ns taken by the grid's first block (a block that always has
- * group and camera work) -- term start, end of its group phase, release of the first grid
- * barrier, end of its camera phase, release of the second barrier.  Copies min(capacity,
- * 5 * terms) values; *n_terms receives the terms. */
+ * five %globaltimer readings in ns taken by the grid's first block.  Forms 3 and 4 (a block
+ * that always has group and camera work): term start, end of its group phase, release of the
+ * first grid barrier, end of its camera phase, release of the second barrier.  Form 5 (block 0's
+ * first group of the term; 0 where block 0 ran no group of that term): its claim, the end of
+ * its group body, the end of its row counting, the end of its camera updates, the end of its
+ * step (stop rule included).  Copies min(capacity, 5 * terms) values; *n_terms receives the
+ * terms. */
 ba_status ba_get_series_trace(ba_handle* h, int64_t* ns, int32_t capacity, int32_t* n_terms);
 
 /* Test hook for the bounded grid barriers: the limit, in GPU clock cycles, that a block of the

@@ -155,6 +155,9 @@ struct ba_handle {
   SerTopo sp{};
   void* ser_arena = nullptr;
   size_t ser_bytes = 0;
+  FlowState flow{};           // dataflow kernel state (inside ser_arena), zeroed per launch
+  void* flow_base = nullptr;
+  size_t flow_bytes = 0;
   void* ser_partial = nullptr;           // [n_gslots][9] partial rows (bulk precision)
   int group_obs = 0;                     // requested group size (0: automatic)
   // persistent kernel: grid = blocks per SM x SMs
@@ -162,8 +165,9 @@ struct ba_handle {
   int plain_max = 0;                     // occupancy limit (0: kernel unavailable)
   int plain_k = 0;                       // blocks per SM in use
   int stage_max = 0, stage_k = 0;        // FP32 staged persistent kernel: limit, in use
+  int flow_max = 0, flow_k = 0;          // dataflow persistent kernel: limit, in use
   CamRounds plain_rounds[4]{};           // per blocks-per-SM setting (1..4; any persistent form)
-  int auto_exec = 1;                     // form used for series_exec 2: 1, 3 or 4
+  int auto_exec = 1;                     // form used for series_exec 2: 1, 3, 4 or 5
   long long barrier_timeout = 1LL << 33;  // clock cycles a block waits at a grid barrier
   int last_exec = -1;                    // execution form of the last solve (1, 0, 3 or 4)
   uint64_t launches = 0;
@@ -190,7 +194,7 @@ bool valid_options(const ba_options& o, std::string* why) {
   if (o.max_lm < 0 || o.max_lm > 100000) { *why = "max_lm out of range"; return false; }
   if (o.max_inner < 0 || o.max_inner > 10000) { *why = "max_inner out of range [0, 10000]"; return false; }
   if (o.damping_mode != 0 && o.damping_mode != 1) { *why = "damping_mode must be 0 or 1"; return false; }
-  if (o.series_exec < 0 || o.series_exec > 4) { *why = "series_exec must be in [0, 4]"; return false; }
+  if (o.series_exec < 0 || o.series_exec > 5) { *why = "series_exec must be in [0, 5]"; return false; }
   return true;
 }
 
@@ -342,7 +346,8 @@ int series_body_kernels(const ba_handle* h) {
 }
 
 template <typename T>
-ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active, bool staged) {
+ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active, int form) {
+  const bool staged = form == 4, flow = form == 5;
   const Topology& tp = h->tp;
   const SerTopo& sp = h->sp;
   const T* J = (const T*)h->J;
@@ -356,6 +361,10 @@ ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active, b
   tmark(h, kTRhs, 0, 1);
   h->launches += 3 + (sp.n_groups > 0 ? 1 : 0);  // reset, the RHS kernels, back-substitution
   CK(cudaMemsetAsync(h->gs, 0, sizeof(GridSync), s));
+  if (flow) {
+    CK(cudaMemsetAsync(h->flow_base, 0, h->flow_bytes, s));
+    CK(cudaMemsetAsync(h->trace, 0, sizeof(long long) * kTraceTerms * kTracePoints, s));
+  }
   if (h->opts.max_inner > 0) {
     tmark(h, kTTile, 1, 0);
     if constexpr (sizeof(T) == 4) {
@@ -366,7 +375,12 @@ ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active, b
                                 h->barrier_timeout, h->trace, s));
       }
     }
-    if (!staged) {
+    if (flow) {
+      CK(launch_series_dataflow<T>(tp, sp, h->flow, h->flow_k * h->sms, J, Vi, h->Uinv, h->x,
+                                   (T*)h->t_cam, part, h->cam_norm, h->st, h->sgl, h->gs,
+                                   h->opts.max_inner, h->opts.eps, h->barrier_timeout, h->trace,
+                                   s));
+    } else if (!staged) {
       CK(launch_series_persistent<T>(tp, sp, h->plain_rounds[h->plain_k - 1],
                                      h->plain_k * h->sms, J, Vi, h->Uinv, h->x, (T*)h->t_cam,
                                      part, h->cam_norm, h->st, h->sgl, h->gs, h->opts.max_inner,
@@ -390,13 +404,16 @@ ba_status run_series_body(ba_handle* h, bool use_active) {
   // execution form: 0 per-term launches, 1 graph replay, 3 persistent, 4 persistent with staged
   // chunks (FP32 bulk); series_exec 2 takes the handle's schedule (default or ba_autotune)
   int mode = h->opts.series_exec == 2 ? h->auto_exec : h->opts.series_exec;
+  // the dataflow kernel numbers its tickets (term, group) in 32 bits
+  if (mode == 5 && (h->flow_k <= 0 || (int64_t)h->opts.max_inner * h->sp.n_groups >= (1LL << 31)))
+    mode = 3;
   if (mode == 4 && h->stage_k <= 0) mode = 3;
   if (mode == 3 && h->plain_k <= 0) mode = 1;
   if (mode == 1 && h->capturing_step) mode = 0;  // the step graph holds the per-term launches
   h->last_exec = mode;
   if (mode >= 3) {
-    ba_status st = h->f32() ? seq_series_persistent<float>(h, s, use_active, mode == 4)
-                            : seq_series_persistent<double>(h, s, use_active, false);
+    ba_status st = h->f32() ? seq_series_persistent<float>(h, s, use_active, mode)
+                            : seq_series_persistent<double>(h, s, use_active, mode == 4 ? 3 : mode);
     if (st == BA_OK) h->pending[kTRhs] = h->pending[kTBack] = h->timing;
     return st;
   }
@@ -538,9 +555,12 @@ ba_status rebuild_series(ba_handle* h, int group_obs, int tail) {
   const size_t bulk = h->f32() ? sizeof(float) : sizeof(double);
   struct Item { void** ptr; const void* src; size_t bytes; };
   int32_t *d_group = nullptr, *d_chunk = nullptr, *d_gcam = nullptr, *d_grow = nullptr,
-          *d_cptr = nullptr, *d_item = nullptr, *d_q = nullptr, *d_rl[4][3] = {};
+          *d_cptr = nullptr, *d_item = nullptr, *d_q = nullptr, *d_rl[4][3] = {},
+          *d_pnc = nullptr;
   uint8_t* d_rec = nullptr;
   void* d_part = nullptr;
+  void* d_flow = nullptr;
+  const size_t flow_bytes = flow_state_bytes(h->n_c, h->n_probs);
   auto nz = [](size_t b) { return b > 0 ? b : (size_t)16; };
   std::vector<Item> items = {
       {(void**)&d_group, Q.group.data(), sizeof(int32_t) * Q.group.size()},
@@ -549,7 +569,9 @@ ba_status rebuild_series(ba_handle* h, int group_obs, int tail) {
       {(void**)&d_gcam, Q.gslot_cam.data(), sizeof(int32_t) * Q.gslot_cam.size()},
       {(void**)&d_grow, Q.gslot_row.data(), sizeof(int32_t) * Q.gslot_row.size()},
       {(void**)&d_cptr, Q.cam_ptr.data(), sizeof(int32_t) * Q.cam_ptr.size()},
+      {(void**)&d_pnc, Q.prob_ncam.data(), sizeof(int32_t) * Q.prob_ncam.size()},
       {&d_part, nullptr, bulk * 9 * (size_t)Q.n_gslots},
+      {&d_flow, nullptr, flow_bytes},
       {(void**)&d_item, cs.cam_item.data(), sizeof(int32_t) * cs.cam_item.size()},
       {(void**)&d_q, cs.item_q.data(), sizeof(int32_t) * cs.item_q.size()},
   };
@@ -597,7 +619,22 @@ ba_status rebuild_series(ba_handle* h, int group_obs, int tail) {
   h->ser_partial = d_part;
   h->group_obs = group_obs;
   h->sp = SerTopo{Q.n_groups, Q.n_chunks, Q.n_gslots, (const int4*)d_group, (const int4*)d_chunk,
-                  d_rec, d_gcam, d_grow, d_cptr};
+                  d_rec, d_gcam, d_grow, d_cptr, d_pnc};
+  {
+    // flow state: cam_norm_b first (16-byte pairs), then the counters
+    char* f = (char*)d_flow;
+    h->flow.cam_norm_b = (double*)f;
+    f += (size_t)h->n_c * 16;
+    h->flow.cam_cnt = (unsigned*)f;
+    f += (size_t)h->n_c * 4;
+    h->flow.cam_epoch = (int*)f;
+    f += (size_t)h->n_c * 4;
+    h->flow.pcnt = (unsigned*)f;
+    f += (size_t)h->n_probs * 8;
+    h->flow.prob_dec = (int*)f;
+    h->flow_base = d_flow;
+    h->flow_bytes = flow_bytes;
+  }
   for (int k = 0; k < 4; ++k) h->plain_rounds[k] = CamRounds{d_item, d_q, d_rl[k][0], d_rl[k][1], d_rl[k][2]};
   h->ser = std::move(Q);
   return BA_OK;
@@ -733,6 +770,11 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
       const int st = staged_blocks_per_sm();
       h->stage_max = st < 3 ? st : 3;
       h->stage_k = h->stage_max;
+    }
+    if (coop) {
+      const int fl = h->f32() ? dataflow_blocks_per_sm<float>() : dataflow_blocks_per_sm<double>();
+      h->flow_max = fl > 0 ? (fl < cap ? fl : cap) : 0;
+      h->flow_k = h->flow_max;
     }
     // default form: the persistent kernel at its largest residency; ba_autotune measures the
     // forms instead
@@ -1045,7 +1087,8 @@ std::vector<double> step_key(const ba_handle* h, bool batch) {
   const ba_options& o = h->opts;
   return {o.lambda0, o.func_tol, o.eps, (double)o.max_inner, (double)o.damping_mode,
           (double)o.series_exec, (double)batch, (double)h->timing, (double)h->auto_exec,
-          (double)h->plain_k, (double)h->stage_k, (double)h->barrier_timeout};
+          (double)h->plain_k, (double)h->stage_k, (double)h->flow_k,
+          (double)h->barrier_timeout};
 }
 
 // Captures the device part of an LM step as a graph (once per configuration).  False: the
@@ -1265,7 +1308,8 @@ ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* 
   };
   const ba_options saved = h->opts;
   const bool saved_timing = h->timing;
-  const int saved_k = h->plain_k, saved_sk = h->stage_k, saved_target = h->ser.target,
+  const int saved_k = h->plain_k, saved_sk = h->stage_k, saved_fk = h->flow_k,
+            saved_target = h->ser.target,
             saved_req = h->group_obs, saved_tail = h->ser.tail;
   h->opts.eps = 0.0;  // every candidate runs max_inner terms
   h->timing = false;
@@ -1287,6 +1331,7 @@ ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* 
     h->opts.series_exec = c.exec;
     if (c.exec == 3) h->plain_k = c.k;
     if (c.exec == 4) h->stage_k = c.k;
+    if (c.exec == 5) h->flow_k = c.k;
     st = run_solve(h, h->scalars + 0, 0, false);  // warm-up (and graph capture)
     if (st != BA_OK) return;
     cudaEventRecord(e0, h->stream);
@@ -1321,6 +1366,8 @@ ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* 
     trial({3, k, series_auto_target(h->n_o, k * h->sms - 1), kDefaultTail});
   for (int k = 1; k <= h->stage_max; ++k)
     trial({4, k, series_auto_target(h->n_o, k * h->sms - 1), kDefaultTail});
+  for (int k = 1; k <= h->flow_max; ++k)
+    trial({5, k, series_auto_target(h->n_o, k * h->sms), kDefaultTail});
   if (best.exec >= 3) {
     const Cand b = best;
     trial({b.exec, b.k, b.target, 0});
@@ -1334,6 +1381,7 @@ ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* 
   h->timing = saved_timing;
   h->plain_k = saved_k;
   h->stage_k = saved_sk;
+  h->flow_k = saved_fk;
   if (st != BA_OK) {
     if (h->ser.target != saved_target || h->ser.tail != saved_tail)
       rebuild_series(h, saved_req, saved_tail);
@@ -1347,6 +1395,7 @@ ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* 
   h->auto_exec = best.exec;
   if (best.exec == 3) h->plain_k = best.k;
   if (best.exec == 4) h->stage_k = best.k;
+  if (best.exec == 5) h->flow_k = best.k;
   if (exec_out) *exec_out = best.exec;
   if (bps_out) *bps_out = best.exec >= 3 ? best.k : 0;
   return BA_OK;
@@ -1370,7 +1419,7 @@ ba_status ba_get_schedule(ba_handle* h, ba_schedule* out) {
   out->group_obs = h->ser.target;
   out->tail_parts = h->ser.tail;
   out->series_exec = h->auto_exec;
-  out->blocks_per_sm = h->auto_exec == 4 ? h->stage_k : h->plain_k;
+  out->blocks_per_sm = h->auto_exec == 4 ? h->stage_k : h->auto_exec == 5 ? h->flow_k : h->plain_k;
   out->n_groups = h->ser.n_groups;
   out->n_chunks = h->ser.n_chunks;
   out->n_group_slots = h->ser.n_gslots;
@@ -1382,11 +1431,15 @@ ba_status ba_set_schedule(ba_handle* h, const ba_schedule* in) {
   if (in->group_obs < 0) return fail(BA_ERR_INVALID_ARG, "group_obs must be >= 0");
   if (in->tail_parts < 0 || in->tail_parts > 64)
     return fail(BA_ERR_INVALID_ARG, "tail_parts must be in [0, 64]");
-  if (in->series_exec != 1 && in->series_exec != 3 && in->series_exec != 4)
-    return fail(BA_ERR_INVALID_ARG, "series_exec must be 1, 3 or 4");
+  if (in->series_exec != 1 && in->series_exec != 3 && in->series_exec != 4 &&
+      in->series_exec != 5)
+    return fail(BA_ERR_INVALID_ARG, "series_exec must be 1, 3, 4 or 5");
   if (in->series_exec == 4 && h->stage_max <= 0)
     return fail(BA_ERR_INVALID_ARG, "series_exec 4 needs BA_FP32_BULK and the staged kernel");
-  const int kmax = in->series_exec == 4 ? h->stage_max : h->plain_max;
+  if (in->series_exec == 5 && h->flow_max <= 0)
+    return fail(BA_ERR_INVALID_ARG, "series_exec 5 needs the dataflow kernel (cooperative launch)");
+  const int kmax = in->series_exec == 4 ? h->stage_max : in->series_exec == 5 ? h->flow_max
+                                                                              : h->plain_max;
   if (in->series_exec >= 3 && (in->blocks_per_sm < 1 || in->blocks_per_sm > kmax))
     return fail(BA_ERR_INVALID_ARG, "blocks_per_sm must be in [1, " + std::to_string(kmax) +
                                         "] (the persistent kernel's residency on this device)");
@@ -1399,6 +1452,7 @@ ba_status ba_set_schedule(ba_handle* h, const ba_schedule* in) {
   h->auto_exec = in->series_exec;
   if (in->series_exec == 3) h->plain_k = in->blocks_per_sm;
   if (in->series_exec == 4) h->stage_k = in->blocks_per_sm;
+  if (in->series_exec == 5) h->flow_k = in->blocks_per_sm;
   return BA_OK;
 }
 

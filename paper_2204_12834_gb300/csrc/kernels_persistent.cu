@@ -253,13 +253,13 @@ __device__ __forceinline__ bool term_end_barrier(const Topology& tp, GridSync* g
                                                  const double* cam_norm, SeriesState* st,
                                                  SeriesGlobal* sgl, int i, double eps,
                                                  long long timeout, int* s_last, unsigned* s_gen,
-                                                 int* s_ok, int* s_running) {
+                                                 int* s_ok, int* s_running, double* red) {
   unsigned target;
   const bool last = barrier_arrive(gs, gridDim.x, &target, s_last, s_gen);
   if (!stop_block()) return last || barrier_wait(gs, target, timeout, s_ok);
   if (!last && !barrier_wait(gs, target, timeout, s_ok)) return false;
   __threadfence();
-  problems_stop_rule(tp, cam_norm, st, sgl, i, eps, s_running);
+  problems_stop_rule(tp, cam_norm, st, sgl, i, eps, s_running, red);
   return true;
 }
 
@@ -324,12 +324,282 @@ __global__ void __launch_bounds__(kChunkObs, sizeof(T) == 4 ? 4 : 3) series_pers
     camera_phase<T>(tp, cr, rc, partial, Uinv, x, t_cam, cam_norm, st, scratch);
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 3] = global_ns();
     if (!term_end_barrier(tp, gs, cam_norm, st, sgl, i, eps, timeout, &s_last, &s_gen, &s_ok,
-                          &s_running))
+                          &s_running, scratch))
       return;
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 4] = global_ns();
   }
   round_writeback(rc, x);
 }
+
+// ---------------------------------------------------------------------------------------
+// Dataflow persistent kernel (series_exec 5): the same group and camera arithmetic with no grid
+// barrier.  Tickets run over (term, group) pairs -- ticket u is group u mod G of term
+// u / G + 1, groups in their longest-first order -- so a block that finishes early goes on to
+// the next term's groups while others still run this term's.  What a barrier ordered before
+// is ordered per camera and per problem:
+//   * a group of term i starts once the term i - 1 update of each of its slots' cameras is
+//     published (cam_epoch[c] >= i - 1), so it reads t_{i-1} and overwrites partial rows that
+//     have been consumed;
+//   * after writing its partial rows a group counts them per camera (cam_cnt); the block whose
+//     count completes camera c's rows of term i runs c's camera update (the camera body's sums
+//     in the same order: chunk sums of the rows, U^-1, x += t, t_cam, norm pair) and publishes
+//     cam_epoch[c] = i;
+//   * a term-i camera update waits for the problem's term i - 1 stop decision (prob_dec) and
+//     leaves x alone if the rule fired there, so x stays at the term where the rule fired;
+//   * the block whose update completes a problem's cameras of term i (pcnt, by term parity)
+//     applies the problem's stop rule for term i (the same norm sums as every other form, from
+//     the term's norm-pair buffer: cam_norm for even terms, cam_norm_b for odd ones) and
+//     publishes prob_dec = i.
+// Every wait depends only on work of earlier tickets, which blocks of this co-resident grid hold,
+// so the kernel cannot deadlock.  Waits are bounded as in the barrier forms (error flag).
+// The trace records, for block 0's first group of each term: its claim, the end of its group
+// body, the end of its slot counting, the end of its camera updates and the end of its step.
+
+// Wait until *flag >= want or the problem is done (*done != 0), bounded.  1: the flag is set,
+// 0: the problem's rule has fired (the waiting work belongs to a term past its last one and is
+// moot), -1: the wait timed out or another block failed.
+__device__ __forceinline__ int flow_wait(const int* flag, int want, const int* done, GridSync* gs,
+                                         long long timeout) {
+  const long long t0 = clock64();
+  unsigned sleep_ns = 32;
+  for (unsigned it = 0;; ++it) {
+    if (ld_volatile(flag) >= want) {
+      __threadfence();
+      return 1;
+    }
+    if (ld_volatile(done)) {
+      __threadfence();
+      return 0;
+    }
+    if (clock64() - t0 > timeout) {
+      atomicExch(&gs->error, 1);
+      return -1;
+    }
+    if ((it & 15u) == 15u && ld_volatile(&gs->error)) return -1;
+    __nanosleep(sleep_ns);
+    if (sleep_ns < 256) sleep_ns <<= 1;
+  }
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Camera updates of term i for the cameras own[0 .. n_own) (every thread of the block): 28
+// cameras at a time, thread (camera, k) as in camera_body; each pass publishes its cameras'
+// epochs.  norm_out: the term's norm pairs.
+template <typename T>
+__device__ __forceinline__ void flow_cameras(const SerTopo& sp, const int* own, int n_own, int i,
+                                             int* cam_epoch, const T* __restrict__ partial,
+                                             const double* __restrict__ Uinv,
+                                             double* __restrict__ x, T* __restrict__ t_cam,
+                                             double* __restrict__ norm_out, double* scratch) {
+  double (*ys)[9] = reinterpret_cast<double (*)[9]>(scratch);
+  double (*y2)[9] = ys + kRoundItems;
+  const int cl = threadIdx.x / 9, k = threadIdx.x - 9 * cl;
+  for (int base = 0; base < n_own; base += kRoundItems) {
+    const bool cam = cl < kRoundItems && base + cl < n_own;
+    int c = 0;
+    double y = 0.0, xo = 0.0;
+    if (cam) {
+      c = own[base + cl];
+      prefetch_uinv_row(Uinv, c, k);
+      xo = __ldcg(x + (size_t)c * 9 + k);
+      const int r0 = __ldg(sp.cam_ptr + c), r1 = __ldg(sp.cam_ptr + c + 1);
+      const int C = cam_chunk_rows(r1 - r0);
+      for (int q0 = r0; q0 < r1; q0 += C) y += cam_chunk_sum(partial, q0, min(q0 + C, r1), k);
+      ys[cl][k] = y;
+    }
+    __syncthreads();
+    double v = 0.0, xv = 0.0;
+    if (cam) {
+      const double* ui = Uinv + (size_t)c * 81 + k * 9;
+#pragma unroll
+      for (int j = 0; j < 9; ++j) v += __ldg(ui + j) * ys[cl][j];
+      xv = xo + v;
+      x[(size_t)c * 9 + k] = xv;
+      t_cam[(size_t)c * kTStride + k] = (T)v;
+    }
+    __syncthreads();
+    if (cam) {
+      ys[cl][k] = v * v;
+      y2[cl][k] = xv * xv;
+    }
+    __syncthreads();
+    if (cam && k == 0) {
+      double a = 0.0, b = 0.0;
+#pragma unroll
+      for (int j = 0; j < 9; ++j) {
+        a += ys[cl][j];
+        b += y2[cl][j];
+      }
+      norm_out[2 * c + 0] = a;
+      norm_out[2 * c + 1] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      for (int j = base; j < n_own && j < base + kRoundItems; ++j) st_release(cam_epoch + own[j], i);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kChunkObs, sizeof(T) == 4 ? 4 : 3) series_dataflow_kernel(
+    Topology tp, SerTopo sp, FlowState fs, const T* __restrict__ J, const T* __restrict__ Vinv,
+    const double* __restrict__ Uinv, double* __restrict__ x, T* __restrict__ t_cam,
+    T* __restrict__ partial, double* __restrict__ cam_norm, SeriesState* __restrict__ st,
+    SeriesGlobal* __restrict__ sgl, GridSync* __restrict__ gs, int m_max, double eps,
+    long long timeout, long long* __restrict__ trace) {
+  extern __shared__ __align__(16) unsigned char group_smem[];
+  GroupSmem<T>& sm = *reinterpret_cast<GroupSmem<T>*>(group_smem);
+  __shared__ int s_ticket, s_n_own, s_run, s_last;
+  __shared__ int s_own[kGroupSlots];
+  static_assert(2 * kRoundItems * 9 * 8 <= sizeof(sm.sg) && 2 * kNormLanes * 8 <= sizeof(sm.sg),
+                "camera and stop-rule scratch fit in sg");
+  const int tid = threadIdx.x;
+  double* scratch = reinterpret_cast<double*>(&sm.sg[0][0]);
+  const unsigned G = (unsigned)sp.n_groups;
+  const unsigned total = (unsigned)m_max * G;
+  const bool tracer = blockIdx.x == 0 && tid == 0 && trace != nullptr;
+  int traced = 0;  // last term block 0 has traced
+  for (;;) {
+    // ---- claim the next ticket of a problem that is still running
+    if (tid == 0) {
+      int t = -1;
+      while (!ld_volatile(&sgl->all_done) && !ld_volatile(&gs->error)) {
+        const unsigned u = atomicAdd(&gs->tile_next, 1u);
+        if (u >= total) break;
+        // a problem decided done at an earlier term has no more groups to run (no group of a
+        // term at or before its last decision can still be unclaimed)
+        if (ld_volatile(&st[__ldg(sp.group + 2 * (u % G) + 1).y].done)) continue;
+        t = (int)u;
+        break;
+      }
+      s_ticket = t;
+    }
+    __syncthreads();
+    const int t = s_ticket;
+    if (t < 0) break;
+    const int i = t / (int)G + 1, g = t % (int)G;
+    const bool tr = tracer && i > traced && i <= kTraceTerms;
+    if (tr) trace[(i - 1) * kTracePoints + 0] = global_ns();
+    const int4 gd = __ldg(sp.group + 2 * g);
+    const int s0 = gd.z, ns = gd.w, p = __ldg(sp.group + 2 * g + 1).y;
+    // ---- the term i - 1 updates of the group's cameras (or the problem's rule has fired:
+    // then the group is moot)
+    int w = 1;
+    if (i > 1 && tid < ns)
+      w = flow_wait(fs.cam_epoch + __ldg(sp.gslot_cam + s0 + tid), i - 1, &st[p].done, gs, timeout);
+    if (__syncthreads_or(w < 0)) return;
+    if (__syncthreads_or(w == 0)) continue;  // (the claim barrier follows)
+    group_body<T, kModeSeries>(tp, sp, g, J, t_cam, nullptr, Vinv, partial, sm);
+    if (tr) trace[(i - 1) * kTracePoints + 1] = global_ns();
+    // ---- count the group's rows per camera; the last one of a camera's term owns its update
+    if (tid == 0) s_n_own = 0;
+    __syncthreads();  // also: every partial row of the group is written
+    if (tid < ns) {
+      const int c = __ldg(sp.gslot_cam + s0 + tid);
+      const unsigned rows = (unsigned)(__ldg(sp.cam_ptr + c + 1) - __ldg(sp.cam_ptr + c));
+      __threadfence();
+      const unsigned cnt = atomicAdd(fs.cam_cnt + c, 1u) + 1u;
+      if (cnt == (unsigned)i * rows) {
+        __threadfence();
+        s_own[atomicAdd(&s_n_own, 1)] = c;
+      }
+    }
+    __syncthreads();
+    if (tr) trace[(i - 1) * kTracePoints + 2] = trace[(i - 1) * kTracePoints + 3] = global_ns();
+    const int n_own = s_n_own;
+    if (n_own > 0) {
+      // the problem's term i - 1 decision: x moves only while the problem runs
+      if (tid == 0) {
+        const int r = flow_wait(fs.prob_dec + p, i - 1, &st[p].done, gs, timeout);
+        s_run = r < 0 ? -1 : (r == 0 || ld_volatile(&st[p].done)) ? 0 : 1;
+      }
+      __syncthreads();
+      const int run = s_run;
+      if (run < 0) return;
+      double* norm_out = (i & 1) ? fs.cam_norm_b : cam_norm;
+      if (run) {
+        flow_cameras<T>(sp, s_own, n_own, i, fs.cam_epoch, partial, Uinv, x, t_cam, norm_out,
+                        scratch);
+      } else if (tid == 0) {
+        for (int j = 0; j < n_own; ++j) st_release(fs.cam_epoch + s_own[j], i);
+      }
+      if (tid == 0) {
+        int last = 0;
+        if (run) {
+          const unsigned want = (unsigned)((i + 1) / 2) * (unsigned)__ldg(sp.prob_ncam + p);
+          last = atomicAdd(fs.pcnt + 2 * p + (i & 1), (unsigned)n_own) + (unsigned)n_own == want;
+        }
+        s_last = last;
+        if (last) __threadfence();
+      }
+      if (tr) trace[(i - 1) * kTracePoints + 3] = global_ns();
+      __syncthreads();
+      if (s_last) {
+        // this block completed problem p's cameras of term i: its stop rule (the decision of
+        // term i - 1 is in place: every term-i update waited for it)
+        const int c0 = tp.cam_off[p], c1 = tp.cam_off[p + 1];
+        double a = 0.0, b = 0.0;
+        if (c1 - c0 >= kBlockNormCams) {
+          block_norm_sums(norm_out, c0, c1, scratch, a, b);
+        } else if (tid < 32) {
+          warp_norm_sums(norm_out, c0, c1, a, b);
+        }
+        if (tid == 0) {
+          series_stop_rule(&st[p], i, a, b, eps);
+          const bool stop = st[p].done != 0;
+          __threadfence();
+          if (stop && atomicSub(&sgl->n_running, 1) == 1) atomicExch(&sgl->all_done, 1);
+          st_release(fs.prob_dec + p, i);
+        }
+      }
+    }
+    if (tr) {
+      trace[(i - 1) * kTracePoints + 4] = global_ns();
+      traced = i;
+    }
+    __syncthreads();  // every thread is done with this group's shared memory
+  }
+}
+
+template <typename T>
+int dataflow_blocks_per_sm() {
+  if (cudaFuncSetAttribute(series_dataflow_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(GroupSmem<T>)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, series_dataflow_kernel<T>, kChunkObs,
+                                                    sizeof(GroupSmem<T>)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb;
+}
+
+template <typename T>
+cudaError_t launch_series_dataflow(const Topology& tp, const SerTopo& sp, const FlowState& fs,
+                                   int grid, const T* J, const T* Vinv, const double* Uinv,
+                                   double* x, T* t_cam, T* partial, double* cam_norm,
+                                   SeriesState* st, SeriesGlobal* sgl, GridSync* gs, int m_max,
+                                   double eps, long long timeout, long long* trace,
+                                   cudaStream_t s) {
+  void* args[] = {(void*)&tp, (void*)&sp, (void*)&fs, (void*)&J, (void*)&Vinv, (void*)&Uinv,
+                  (void*)&x, (void*)&t_cam, (void*)&partial, (void*)&cam_norm, (void*)&st,
+                  (void*)&sgl, (void*)&gs, (void*)&m_max, (void*)&eps, (void*)&timeout,
+                  (void*)&trace};
+  return cudaLaunchCooperativeKernel((const void*)series_dataflow_kernel<T>, dim3(grid),
+                                     dim3(kChunkObs), args, sizeof(GroupSmem<T>), s);
+}
+
+template int dataflow_blocks_per_sm<double>();
+template int dataflow_blocks_per_sm<float>();
+template cudaError_t launch_series_dataflow<double>(const Topology&, const SerTopo&, const FlowState&, int, const double*, const double*, const double*, double*, double*, double*, double*, SeriesState*, SeriesGlobal*, GridSync*, int, double, long long, long long*, cudaStream_t);
+template cudaError_t launch_series_dataflow<float>(const Topology&, const SerTopo&, const FlowState&, int, const float*, const float*, const double*, double*, float*, float*, double*, SeriesState*, SeriesGlobal*, GridSync*, int, double, long long, long long*, cudaStream_t);
 
 // ---------------------------------------------------------------------------------------
 // FP32-bulk persistent kernel with staged chunks (series_exec 4).  The arithmetic is the group
@@ -604,7 +874,7 @@ __global__ void __launch_bounds__(kChunkObs, 3) series_staged_kernel(
     camera_phase<float>(tp, cr, rc, partial, Uinv, x, t_cam, cam_norm, st, scratch);
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 3] = global_ns();
     if (!term_end_barrier(tp, gs, cam_norm, st, sgl, i, eps, timeout, &s_last, &s_gen, &s_ok,
-                          &s_running))
+                          &s_running, scratch))
       return;
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 4] = global_ns();
   }

@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(CS * 9) camera_step_kernel(
   __shared__ double ys[CS][9];
   __shared__ double y2[CS][9];
   __shared__ int is_last, s_running;
+  __shared__ double red[2 * kNormLanes];
   if (MODE == kModeSeries && sgl->all_done) return;
   const int tid = threadIdx.x;
   camera_body<PT, MODE>(tp, cam_ptr, blockIdx.x * CS, CS, partial, b_p, Uinv, x, t_cam, st,
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(CS * 9) camera_step_kernel(
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  problems_stop_rule(tp, cam_norm, st, sgl, iter, eps, &s_running);
+  problems_stop_rule(tp, cam_norm, st, sgl, iter, eps, &s_running, red);
   if (tid == 0) sgl->counter = 0u;
 }
 

@@ -167,6 +167,7 @@ struct SerSchedule {
   std::vector<int32_t> gslot_cam;   // [n_gslots] camera of each group slot
   std::vector<int32_t> gslot_row;   // [n_gslots] its camera-major partial row
   std::vector<int32_t> cam_ptr;     // [n_cams + 1] partial rows of each camera
+  std::vector<int32_t> prob_ncam;   // [n_probs] cameras of each problem with a partial row
 };
 
 // Builds the series schedule of S for a target group size (observations, >= 1).  tail > 0: the
@@ -238,7 +239,20 @@ struct SerTopo {
   const int32_t* gslot_cam;  // [n_gslots]
   const int32_t* gslot_row;  // [n_gslots] camera-major partial row
   const int32_t* cam_ptr;    // [n_cams + 1] partial rows of each camera
+  const int32_t* prob_ncam;  // [n_probs] cameras of each problem with at least one partial row
 };
+
+// Per-launch state of the dataflow series kernel (series_exec 5), zeroed before each launch.
+struct FlowState {
+  unsigned* cam_cnt;   // [n_cams] group slots of camera c completed in this launch (all terms)
+  int* cam_epoch;      // [n_cams] last term whose update of camera c is published
+  unsigned* pcnt;      // [n_probs][2] camera updates completed, by term parity
+  int* prob_dec;       // [n_probs] last term whose stop rule has been applied
+  double* cam_norm_b;  // [n_cams][2] norm pairs of odd terms (even terms use cam_norm)
+};
+constexpr size_t flow_state_bytes(int n_cams, int n_probs) {
+  return (size_t)n_cams * (4 + 4 + 16) + (size_t)n_probs * (8 + 4) + 64;
+}
 
 // Per-camera values prepared once per state: rotation R (row-major), the matrix G with
 // dP/dw = -[Y]x G (Y = R X and G = left Jacobian of SO(3) on the regular branch; Y = X and
@@ -262,7 +276,7 @@ struct SeriesGlobal {
   int32_t all_done;    // every problem has stopped (later terms return at once)
   uint32_t counter;    // last-block ticket of the per-term camera kernel
   int32_t n_list;      // tiles in the active tile list (batches)
-  int32_t pad;
+  int32_t n_running;   // problems still running after the last stop-rule pass
 };
 
 // Grid-barrier state of the persistent series kernel (zeroed before each launch).
@@ -463,6 +477,17 @@ cudaError_t launch_series_staged(const Topology& tp, const SerTopo& sp, const Ca
                                  SeriesState* st, SeriesGlobal* sgl, GridSync* gs, int m_max,
                                  double eps, long long timeout, long long* trace,
                                  cudaStream_t s);
+// Dataflow persistent kernel (series_exec 5): no grid barriers; per-camera counters and
+// published term numbers order the work (see kernels_persistent.cu).
+template <typename T>
+int dataflow_blocks_per_sm();  // 0: the kernel cannot be launched on this device
+template <typename T>
+cudaError_t launch_series_dataflow(const Topology& tp, const SerTopo& sp, const FlowState& fs,
+                                   int grid, const T* J, const T* Vinv, const double* Uinv,
+                                   double* x, T* t_cam, T* partial, double* cam_norm,
+                                   SeriesState* st, SeriesGlobal* sgl, GridSync* gs, int m_max,
+                                   double eps, long long timeout, long long* trace,
+                                   cudaStream_t s);
 template <typename T>
 cudaError_t launch_series_persistent(const Topology& tp, const SerTopo& sp, const CamRounds& cr,
                                      int grid, const T* J, const T* Vinv, const double* Uinv,

@@ -359,6 +359,10 @@ std::string build_series_schedule(const Schedule& S, int target, int tail, SerSc
   Q->cam_ptr.assign(S.n_cams + 1, 0);
   for (int c : gcams) Q->cam_ptr[c + 1]++;
   for (int c = 0; c < S.n_cams; ++c) Q->cam_ptr[c + 1] += Q->cam_ptr[c];
+  Q->prob_ncam.assign(S.n_probs, 0);
+  for (int p = 0; p < S.n_probs; ++p)
+    for (int c = S.cam_off[p]; c < S.cam_off[p + 1]; ++c)
+      Q->prob_ncam[p] += Q->cam_ptr[c + 1] > Q->cam_ptr[c] ? 1 : 0;
   std::vector<int32_t> fill(Q->cam_ptr.begin(), Q->cam_ptr.end() - 1);
   Q->gslot_row.assign(Q->n_gslots, 0);
   for (int s = 0; s < Q->n_gslots; ++s) Q->gslot_row[s] = fill[gcams[s]]++;

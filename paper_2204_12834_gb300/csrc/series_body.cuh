@@ -639,42 +639,106 @@ __device__ __forceinline__ void series_stop_rule(SeriesState* st, int iter, doub
   }
 }
 
-// Every problem still running: sum its cameras' norm pairs (one warp per problem, lanes strided
-// over the cameras, then a fixed shuffle tree) and apply its stop rule for term `iter`; raise
-// all_done when no problem is left.  Every thread of one block (at least one full warp) must
-// call it.
+// Sum of the camera norm pairs (||t_c||^2, ||x_c||^2) of cameras [c0, c1), the two sums of the
+// stop rule.  The order depends only on the camera count, so every execution form gets the same
+// bits: a problem with fewer than kBlockNormCams cameras is summed by one warp (lane j adds
+// cameras c0 + j, c0 + j + 32, ... in order, then a fixed shuffle tree); a larger one over
+// kNormLanes virtual lanes (lane v adds cameras c0 + v, c0 + v + kNormLanes, ... in order; the
+// block's threads run the lanes whatever the block size), whose sums warp 0 combines: lane j
+// adds virtual lanes j, j + 32, ..., j + kNormLanes - 32 in order, then the same shuffle tree.
+// Loads go out eight at a time.
+constexpr int kBlockNormCams = 2048;
+constexpr int kNormLanes = 256;
+
+__device__ __forceinline__ void strided_norm_sum(const double2* __restrict__ cn, int c, int c1,
+                                                 int stride, double& a, double& b) {
+  for (int cb = c; cb < c1; cb += stride * 8) {
+    double2 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      v[j] = cb + stride * j < c1 ? __ldcg(cn + cb + stride * j) : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      a += v[j].x;
+      b += v[j].y;
+    }
+  }
+}
+
+__device__ __forceinline__ void warp_tree(double& a, double& b) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, off);
+    b += __shfl_down_sync(0xffffffffu, b, off);
+  }
+}
+
+// One warp (all 32 lanes), a problem below kBlockNormCams cameras; the sums land in lane 0.
+__device__ __forceinline__ void warp_norm_sums(const double* __restrict__ cam_norm, int c0, int c1,
+                                               double& a, double& b) {
+  const int lane = threadIdx.x & 31;
+  a = 0.0;
+  b = 0.0;
+  strided_norm_sum(reinterpret_cast<const double2*>(cam_norm), c0 + lane, c1, 32, a, b);
+  warp_tree(a, b);
+}
+
+// Every thread of the block (at least one full warp), a problem of at least kBlockNormCams
+// cameras; red: 2 kNormLanes doubles of shared scratch.  The sums land in thread 0.
+__device__ __forceinline__ void block_norm_sums(const double* __restrict__ cam_norm, int c0, int c1,
+                                                double* red, double& a, double& b) {
+  const double2* cn = reinterpret_cast<const double2*>(cam_norm);
+  for (int v = threadIdx.x; v < kNormLanes; v += blockDim.x) {
+    double va = 0.0, vb = 0.0;
+    strided_norm_sum(cn, c0 + v, c1, kNormLanes, va, vb);
+    red[2 * v] = va;
+    red[2 * v + 1] = vb;
+  }
+  __syncthreads();
+  a = 0.0;
+  b = 0.0;
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int j = 0; j < kNormLanes / 32; ++j) {
+      a += red[2 * (threadIdx.x + 32 * j)];
+      b += red[2 * (threadIdx.x + 32 * j) + 1];
+    }
+    warp_tree(a, b);
+  }
+  __syncthreads();
+}
+
+// Every problem still running: sum its cameras' norm pairs and apply its stop rule for term
+// `iter`; raise all_done when no problem is left and record the running count.  Problems below
+// kBlockNormCams cameras take one warp each (several at once), larger ones the whole block in
+// turn.  Every thread of one block (at least one full warp) must call it; red as for
+// block_norm_sums.
 __device__ __forceinline__ void problems_stop_rule(const Topology& tp,
                                                    const double* __restrict__ cam_norm,
                                                    SeriesState* st, SeriesGlobal* sgl, int iter,
-                                                   double eps, int* s_running) {
-  // only full warps take problems (the shuffles below use every lane of a warp)
+                                                   double eps, int* s_running, double* red) {
+  // only full warps take problems (the shuffles use every lane of a warp)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   if (threadIdx.x == 0) *s_running = 0;
   __syncthreads();
   for (int p = warp; warp < nw && p < tp.n_probs; p += nw) {
-    if (ld_volatile(&st[p].done)) continue;  // warp-uniform
-    // lane j adds the pairs of cameras j, j + 32, j + 64, ... in that order; the loads go out
-    // eight at a time so that the sum waits for one round trip per eight cameras
-    double a = 0.0, b = 0.0;
-    const int c1 = tp.cam_off[p + 1];
-    const double2* cn = reinterpret_cast<const double2*>(cam_norm);
-    for (int cb = tp.cam_off[p] + lane; cb < c1; cb += 32 * 8) {
-      double2 v[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        v[j] = cb + 32 * j < c1 ? __ldcg(cn + cb + 32 * j) : make_double2(0.0, 0.0);
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        a += v[j].x;
-        b += v[j].y;
-      }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      a += __shfl_down_sync(0xffffffffu, a, off);
-      b += __shfl_down_sync(0xffffffffu, b, off);
-    }
+    const int c0 = tp.cam_off[p], c1 = tp.cam_off[p + 1];
+    if (c1 - c0 >= kBlockNormCams || ld_volatile(&st[p].done)) continue;  // warp-uniform
+    double a, b;
+    warp_norm_sums(cam_norm, c0, c1, a, b);
     if (lane == 0) {
+      series_stop_rule(&st[p], iter, a, b, eps);
+      if (!st[p].done) atomicAdd(s_running, 1);
+    }
+  }
+  for (int p = 0; p < tp.n_probs; ++p) {
+    const int c0 = tp.cam_off[p], c1 = tp.cam_off[p + 1];
+    if (c1 - c0 < kBlockNormCams) continue;  // block-uniform
+    __syncthreads();
+    if (ld_volatile(&st[p].done)) continue;  // the same value in every thread (after the barrier)
+    double a, b;
+    block_norm_sums(cam_norm, c0, c1, red, a, b);
+    if (threadIdx.x == 0) {
       series_stop_rule(&st[p], iter, a, b, eps);
       if (!st[p].done) atomicAdd(s_running, 1);
     }
@@ -682,6 +746,7 @@ __device__ __forceinline__ void problems_stop_rule(const Topology& tp,
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
+    sgl->n_running = *s_running;
     if (*s_running == 0) sgl->all_done = 1;
   }
   __syncthreads();

@@ -92,7 +92,7 @@ def test_series_per_problem_matches_oracle(poba, small, precision, tol, lam):
 
 @pytest.mark.parametrize("group_obs", [300, 1500])
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("series_exec", [0, 2, 3])
+@pytest.mark.parametrize("series_exec", [0, 2, 3, 5])
 def test_lm_equals_individual_handles_bitwise(poba, small, precision, series_exec, group_obs):
     """A batch and per-problem handles with the same group size: equal parameters, iteration
     counts and costs bit for bit (one group spans several chunks at 1500 observations)."""
@@ -255,7 +255,7 @@ def test_full_size_batch_series_per_problem_vs_oracle(poba, full_batch):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("series_exec", [0, 1, 3, 4])
+@pytest.mark.parametrize("series_exec", [0, 1, 3, 4, 5])
 def test_step_graph_equals_eager_bitwise(poba, precision, series_exec):
     """A batch's LM steps replayed as one captured graph each (the linearisation gated on the
     device flag that the previous step's decision raises) equal the kernel-by-kernel steps bit

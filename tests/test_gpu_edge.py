@@ -59,7 +59,7 @@ def test_longest_track_and_wide_tiles(poba):
     # one landmark segment); the persistent kernel and the per-term launches agree bit for bit
     h32 = check_series(poba, p, tol=1e-4, precision=1)
     steps = []
-    for mode in (1, 2, 3, 4):
+    for mode in (1, 2, 3, 4, 5):
         h = poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, precision=1,
                            options=poba.ba_default_options(eps=0.0, max_inner=6, series_exec=mode))
         poba.ba_linearize(h)
@@ -172,7 +172,7 @@ def test_nonfinite_state_is_reported(poba):
     assert np.isfinite(poba.ba_cost(h))
 
 
-@pytest.mark.parametrize("precision,mode", [(0, 3), (1, 3), (1, 4)])
+@pytest.mark.parametrize("precision,mode", [(0, 3), (1, 3), (1, 4), (0, 5), (1, 5)])
 def test_grid_barrier_timeout_is_reported_and_recoverable(poba, precision, mode):
     """A grid-barrier wait of the persistent series kernel that runs out (limit of one clock
     cycle) makes the solve return BA_ERR_TIMEOUT; the context stays usable and the next solve

@@ -81,11 +81,11 @@ def test_full_series_fp64_and_fp32(poba, problem, oracle_ref, eps, m):
 
 def test_fp32_persistent_forms_agree_bitwise(poba, problem):
     """FP32-bulk at full size: the persistent kernel (3), its staged-chunk form (4), the
-    replayed graph of per-term launches (1) and the handle's choice (2) give the same step bit
+    dataflow form (5), the replayed graph of per-term launches (1) and the handle's choice (2) give the same step bit
     for bit, with the stop rule on."""
     p = problem
     out = []
-    for mode in (2, 3, 4, 1):
+    for mode in (2, 3, 4, 5, 1):
         h = poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, precision=1,
                            options=poba.ba_default_options(series_exec=mode))
         poba.ba_linearize(h)

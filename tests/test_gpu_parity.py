@@ -175,11 +175,11 @@ def test_solve_is_deterministic(poba, case):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_series_exec_modes_agree_bitwise(poba, case, precision, group_obs):
     """Per-kernel launches, the captured graph, the persistent kernel (series_exec 3), the
-    persistent kernel with staged chunks (4; FP64 runs it as 3) and the handle's own choice give
-    the same step for one series schedule."""
+    persistent kernel with staged chunks (4; FP64 runs it as 3), the dataflow persistent kernel
+    (5) and the handle's own choice give the same step for one series schedule."""
     name, p, ref = case
     res = []
-    for mode in (0, 1, 2, 3, 4):
+    for mode in (0, 1, 2, 3, 4, 5):
         h = make(poba, p, precision=precision, eps=0.01, max_inner=12, series_exec=mode,
                  group_obs=group_obs)
         poba.ba_linearize(h)
@@ -200,7 +200,7 @@ def test_autotune_keeps_results(poba, case):
         poba.ba_linearize(h)
         choice = poba.ba_autotune(h, trials=2)
         sched = poba.ba_get_schedule(h)
-        assert choice["exec"] in (1, 3, 4) and (choice["exec"] != 4 or precision == 1)
+        assert choice["exec"] in (1, 3, 4, 5) and (choice["exec"] != 4 or precision == 1)
         assert sched["series_exec"] == choice["exec"] and sched["group_obs"] >= 256
         assert sched["n_groups"] >= 1 and sched["n_group_slots"] >= 1
         assert poba.ba_default_options().eps == 0.01
