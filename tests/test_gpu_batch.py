@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import bal_synth
-from gpu_helpers import OracleRef, block_rel, rel
+from gpu_helpers import OracleRef, block_rel, check_step_blocks, rel
 from oracle import camera_model as cm
 from oracle import lm as olm
 
@@ -84,6 +84,7 @@ def test_series_per_problem_matches_oracle(poba, small, precision, tol, lam):
         assert states[i]["lam"] == lam
         assert rel(dxp[co[i]:co[i + 1]], o["x"]) < tol
         assert rel(dxl[lo[i]:lo[i + 1]], o["xl"]) < tol
+        check_step_blocks(dxp[co[i]:co[i + 1]], dxl[lo[i]:lo[i + 1]], o["x"], o["xl"], precision)
         ms.append(states[i]["inner_iters"])
     assert info["inner_iters"] == max(ms)
     if precision == 0:

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import bal_synth
-from gpu_helpers import OracleRef, rel
+from gpu_helpers import OracleRef, check_step_blocks, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -28,6 +28,7 @@ def check_series(poba, p, lam=1e-3, m=6, tol=1e-10, precision=0):
     o = ref.solve(lam, 0.0, m)
     assert rel(dxp, o["x"]) < tol
     assert rel(dxl, o["xl"]) < tol
+    check_step_blocks(dxp, dxl, o["x"], o["xl"], precision)
     return h
 
 
@@ -108,6 +109,7 @@ def test_device_inputs_and_stream(poba):
     o = OracleRef(p).solve(1e-3, 0.0, 5)
     assert rel(out_p.cpu().numpy(), o["x"]) < 1e-10
     assert rel(out_l.cpu().numpy(), o["xl"]) < 1e-10
+    check_step_blocks(out_p.cpu().numpy(), out_l.cpu().numpy(), o["x"], o["xl"], 0)
 
 
 def test_not_spd_is_reported(poba):

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import bal_synth
-from gpu_helpers import OracleRef, rel
+from gpu_helpers import OracleRef, check_step_blocks, rel
 from oracle import camera_model as cm
 from oracle import lm as olm
 
@@ -77,6 +77,7 @@ def test_full_series_fp64_and_fp32(poba, problem, oracle_ref, eps, m):
             assert info["inner_iters"] == o["m"]
         assert rel(dxp, o["x"]) < tol, (prec, rel(dxp, o["x"]))
         assert rel(dxl, o["xl"]) < tol, (prec, rel(dxl, o["xl"]))
+        check_step_blocks(dxp, dxl, o["x"], o["xl"], prec)
 
 
 def test_fp32_persistent_forms_agree_bitwise(poba, problem):

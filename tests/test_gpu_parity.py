@@ -8,20 +8,13 @@ import numpy as np
 import pytest
 
 import bal_synth
-from gpu_helpers import OracleRef, block_rel, rel
+from gpu_helpers import FP32_BLOCK_TOL, FP64_BLOCK_TOL, OracleRef, block_rel, rel
 
 pytestmark = pytest.mark.gpu
 
 FP64_SERIES_TOL = 1e-10
 FP32_SERIES_TOL = 1e-4
 LIN_TOL = 1e-12
-# per camera / landmark block (gpu_helpers.block_rel): an error confined to a few weakly
-# observed blocks must not hide under the whole-vector norm.  Measured on these cases: FP64 at
-# most 4e-11 (bound 1e-8); FP32 bulk at most 1.1e-2 at lambda = 1e-4 (a two-view landmark,
-# where float rounding of J is amplified by the conditioning of the series) and 9e-4 at
-# lambda = 1e-2 (bound 5e-2)
-FP64_BLOCK_TOL = 1e-8
-FP32_BLOCK_TOL = 5e-2
 
 # series group sizes (observations per group; ba_set_schedule): the automatic size (one group
 # per block, on these problems a single chunk), groups of a few chunks, and one group per
