@@ -116,6 +116,13 @@ def _track_lengths(rng, n_l, spec):
         p = ks.astype(np.float64) ** (-alpha)
         p /= p.sum()
         return rng.choice(ks, size=n_l, p=p)
+    if kind == "long":
+        # ("long", kmin, kmax, (k_0, k_1, ...)): landmarks 0, 1, ... get the listed track
+        # lengths (long tracks), the others U{kmin..kmax}
+        lo, hi, long = spec[1], spec[2], np.asarray(spec[3], dtype=np.int64)
+        k = rng.integers(lo, hi + 1, size=n_l)
+        k[:long.size] = long[:n_l]
+        return k
     raise ValueError(f"unknown track-length spec {spec}")
 
 
@@ -124,7 +131,8 @@ def make_problem(n_cams: int, n_lms: int, track=("uniform", 2, 6), visibility="u
                  weighted: bool = False, name: str = "custom", shuffle: bool = True) -> Problem:
     """Draw one problem.
 
-    track: ("uniform", kmin, kmax) or ("powerlaw", alpha, kmin, kmax) track-length law.
+    track: ("uniform", kmin, kmax) or ("powerlaw", alpha, kmin, kmax) track-length law, or
+    ("long", kmin, kmax, lengths): the first landmarks get the listed lengths, the rest uniform.
     visibility: "uniform" (k distinct cameras out of all) or "clustered" (k distinct cameras in
     [c, c + width) mod n_cams, width = max(window, 2 k) for power-law tracks, else window).
     """

@@ -90,8 +90,10 @@ typedef struct {
                            (default) the handle's schedule (ba_set_schedule / ba_autotune; at
                            creation 3 at the largest residency, 4 blocks per SM in BA_FP32_BULK,
                            3 in BA_FP64).  A device that cannot run a persistent form falls back
-                           (4 and 5 to 3, 3 to 1: all blocks must be co-resident).  All forms
-                           give bitwise-equal results for the handle's series schedule. */
+                           (4 and 5 to 3, 3 to 1: all blocks must be co-resident), and so do
+                           forms 4 and 5 on a problem with tracks of more than 256 observations.
+                           All forms give bitwise-equal results for the handle's series
+                           schedule. */
 } ba_options;
 
 typedef struct {
@@ -124,8 +126,12 @@ ba_status ba_default_options(ba_options* opts);
 /* Create a problem handle (Sec. 4: state x = (x_p, x_l), residuals r(x)).  Copies and
  * validates the inputs (sizes, index ranges, finiteness, weights > 0), sorts observations by
  * landmark, orders landmarks for camera locality and builds the tile schedule, then allocates
- * all device memory once.  opts may be NULL for the defaults.  Errors: BA_ERR_INVALID_ARG (bad
- * sizes, NULL pointers, out-of-range index, a landmark with more than 256 observations),
+ * all device memory once.  A landmark with more than 256 observations (a long track) is split
+ * into near-equal pieces of at most 256 observations, which the kernels treat as landmarks
+ * holding copies of its state; the landmark-side sums (V, b_l, the series' J_l^T J_p t and the
+ * back-substitution's) are added over the pieces in piece order, so the results are those of
+ * the unsplit problem.  opts may be NULL for the defaults.  Errors: BA_ERR_INVALID_ARG (bad
+ * sizes, NULL pointers, out-of-range index),
  * BA_ERR_NONFINITE (non-finite input), BA_ERR_OOM, BA_ERR_CUDA.  *out is NULL on error. */
 ba_status ba_create(const ba_problem_desc* desc, const ba_options* opts, ba_handle** out);
 

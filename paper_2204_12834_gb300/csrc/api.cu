@@ -48,6 +48,7 @@ void poba::set_last_error(const std::string& msg) { g_last_error = msg; }
 
 struct ba_handle {
   int n_c = 0, n_l = 0, n_o = 0, n_o_pad = 0;
+  int n_li = 0;  // internal landmarks: n_l plus the extra pieces of long tracks
   int precision = BA_FP64;
   bool weighted = false;
   ba_options opts{};
@@ -293,6 +294,10 @@ void collect_timing(ba_handle* h, int terms_run, bool series_ran) {
 
 // ---- kernel sequences ------------------------------------------------------------------
 
+// Extra kernel of a step for the long tracks of a handle (their block and back-substitution
+// kernels), 0 without long tracks.
+int long_kernels(const ba_handle* h) { return h->tp.n_long > 0 ? 1 : 0; }
+
 void seq_linearize(ba_handle* h) {
   cudaStream_t s = h->stream;
   tmark(h, kTLin, 0, 0);
@@ -306,8 +311,9 @@ void seq_linearize(ba_handle* h) {
                              (double*)h->r, h->V, h->b_l, (double*)h->partial, h->block_cost, s);
     launch_lin_camera_reduce<double>(h->tp, (const double*)h->partial, h->U45, h->b_p, s);
   }
+  launch_long_track_blocks(h->tp, h->V, h->b_l, s);
   tmark(h, kTLin, 0, 1);
-  h->launches += 3;
+  h->launches += 3 + long_kernels(h);
 }
 
 // series reset, b~ / x(0), max_inner terms, back-substitution with model decrease
@@ -342,7 +348,7 @@ void seq_series_body(ba_handle* h, cudaStream_t s, bool use_active) {
 // schedule has no group).
 int series_body_kernels(const ba_handle* h) {
   const int group = h->sp.n_groups > 0 ? 1 : 0;
-  return 3 + group + (1 + group) * h->opts.max_inner;
+  return 3 + group + long_kernels(h) + (1 + group) * h->opts.max_inner;
 }
 
 template <typename T>
@@ -359,7 +365,8 @@ ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active, i
   launch_camera_rhs<T>(tp, sp, part, h->rhs_p, h->Uinv, h->x, (T*)h->t_cam, h->cam_norm, h->st,
                        h->sgl, s);
   tmark(h, kTRhs, 0, 1);
-  h->launches += 3 + (sp.n_groups > 0 ? 1 : 0);  // reset, the RHS kernels, back-substitution
+  // reset, the RHS kernels, back-substitution (and that of the long tracks)
+  h->launches += 3 + (sp.n_groups > 0 ? 1 : 0) + long_kernels(h);
   CK(cudaMemsetAsync(h->gs, 0, sizeof(GridSync), s));
   if (flow) {
     CK(cudaMemsetAsync(h->flow_base, 0, h->flow_bytes, s));
@@ -405,9 +412,11 @@ ba_status run_series_body(ba_handle* h, bool use_active) {
   // chunks (FP32 bulk); series_exec 2 takes the handle's schedule (default or ba_autotune)
   int mode = h->opts.series_exec == 2 ? h->auto_exec : h->opts.series_exec;
   // the dataflow kernel numbers its tickets (term, group) in 32 bits
-  if (mode == 5 && (h->flow_k <= 0 || (int64_t)h->opts.max_inner * h->sp.n_groups >= (1LL << 31)))
+  // (the staged and dataflow kernels take groups of whole landmarks only: no long tracks)
+  if (mode == 5 && (h->flow_k <= 0 || h->tp.n_long > 0 ||
+                    (int64_t)h->opts.max_inner * h->sp.n_groups >= (1LL << 31)))
     mode = 3;
-  if (mode == 4 && h->stage_k <= 0) mode = 3;
+  if (mode == 4 && (h->stage_k <= 0 || h->tp.n_long > 0)) mode = 3;
   if (mode == 3 && h->plain_k <= 0) mode = 1;
   if (mode == 1 && h->capturing_step) mode = 0;  // the step graph holds the per-term launches
   h->last_exec = mode;
@@ -751,6 +760,8 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
     return fail(BA_ERR_INVALID_ARG, why);
   }
   const Schedule& S = h->sched;
+  const int nli = S.n_lms_int;  // internal landmark arrays (a long track has several pieces)
+  h->n_li = nli;
   std::vector<int32_t> tile_prob(S.n_tiles);
   for (int t = 0; t < S.n_tiles; ++t) tile_prob[t] = S.lm_prob[S.tile_lm0[t]];
 
@@ -796,7 +807,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   uint16_t *d_meta, *d_slot_beg;
   const size_t slots = (size_t)(S.n_slots > 0 ? S.n_slots : 1);
   const size_t P = (size_t)n_probs;
-  items.push_back({(void**)&d_lm_seg, sizeof(int32_t) * (nl + 1)});
+  items.push_back({(void**)&d_lm_seg, sizeof(int32_t) * (nli + 1)});
   items.push_back({(void**)&d_cam_of, sizeof(int32_t) * (no > 0 ? no : 1)});
   items.push_back({(void**)&d_lm_of, sizeof(int32_t) * (no > 0 ? no : 1)});
   items.push_back({(void**)&d_meta, sizeof(uint16_t) * (no > 0 ? no : 1)});
@@ -809,7 +820,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   items.push_back({(void**)&d_cam_slot_list, sizeof(int32_t) * slots});
   items.push_back({(void**)&d_slot_row, sizeof(int32_t) * slots});
   items.push_back({(void**)&d_cam_prob, sizeof(int32_t) * nc});
-  items.push_back({(void**)&d_lm_prob, sizeof(int32_t) * nl});
+  items.push_back({(void**)&d_lm_prob, sizeof(int32_t) * nli});
   items.push_back({(void**)&d_tile_prob, sizeof(int32_t) * S.n_tiles});
   items.push_back({(void**)&d_cam_off, sizeof(int32_t) * (P + 1)});
   items.push_back({(void**)&d_tile_off, sizeof(int32_t) * (P + 1)});
@@ -817,7 +828,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   if (h->weighted) items.push_back({(void**)&h->sqrt_w, sizeof(double) * (no > 0 ? no : 1)});
   items.push_back({(void**)&h->cams, sizeof(double) * nc * 9});
   items.push_back({(void**)&h->cams_trial, sizeof(double) * nc * 9});
-  items.push_back({(void**)&h->lms, sizeof(double) * nl * 3});
+  items.push_back({(void**)&h->lms, sizeof(double) * nli * 3});
   items.push_back({(void**)&h->prep, sizeof(double) * nc * kCamPrep});
   if (h->f32()) {
     items.push_back({(void**)&h->prep32, sizeof(float) * nc * kCamPrep});
@@ -831,18 +842,23 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   items.push_back({&h->t_cam, bulk * kTStride * nc});
   items.push_back({(void**)&h->U45, sizeof(double) * nc * 45});
   items.push_back({(void**)&h->b_p, sizeof(double) * nc * 9});
-  items.push_back({(void**)&h->V, sizeof(double) * nl * 6});
-  items.push_back({(void**)&h->b_l, sizeof(double) * nl * 3});
+  items.push_back({(void**)&h->V, sizeof(double) * nli * 6});
+  items.push_back({(void**)&h->b_l, sizeof(double) * nli * 3});
   items.push_back({(void**)&h->adj_p, sizeof(double) * nc * 9});
-  items.push_back({(void**)&h->adj_l, sizeof(double) * nl * 3});
+  items.push_back({(void**)&h->adj_l, sizeof(double) * nli * 3});
   items.push_back({(void**)&h->obs_caller, sizeof(int32_t) * (no > 0 ? no : 1)});
-  items.push_back({(void**)&h->lm_order_dev, sizeof(int32_t) * nl});
+  items.push_back({(void**)&h->lm_order_dev, sizeof(int32_t) * nli});
+  int32_t *d_long = nullptr, *d_lm_long = nullptr;
+  if (S.n_long > 0) {
+    items.push_back({(void**)&d_long, sizeof(int32_t) * 3 * S.n_long});
+    items.push_back({(void**)&d_lm_long, sizeof(int32_t) * nli});
+  }
   items.push_back({(void**)&h->Uinv, sizeof(double) * nc * 81});
-  items.push_back({(void**)&h->Vinv, sizeof(double) * nl * 6});
+  items.push_back({(void**)&h->Vinv, sizeof(double) * nli * 6});
   // (4 floats of slack: the staged kernel copies V^-1 ranges rounded out to 16 bytes)
-  if (h->f32()) items.push_back({(void**)&h->Vinv_f, sizeof(float) * ((size_t)nl * 6 + 4)});
+  if (h->f32()) items.push_back({(void**)&h->Vinv_f, sizeof(float) * ((size_t)nli * 6 + 4)});
   items.push_back({(void**)&h->x, sizeof(double) * nc * 9});
-  items.push_back({(void**)&h->dx_l, sizeof(double) * nl * 3});
+  items.push_back({(void**)&h->dx_l, sizeof(double) * nli * 3});
   items.push_back({(void**)&h->cam_norm, sizeof(double) * 2 * nc});
   items.push_back({(void**)&h->block_cost, sizeof(double) * S.n_tiles});
   items.push_back({(void**)&h->tile_cost, sizeof(double) * S.n_tiles});
@@ -907,12 +923,12 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   }
   std::vector<int32_t> obs_caller((size_t)no);
   for (int k = 0; k < no; ++k) obs_caller[k] = (int32_t)S.obs_order[k];
-  std::vector<double> lms_i((size_t)nl * 3);
-  for (int i = 0; i < nl; ++i)
+  std::vector<double> lms_i((size_t)nli * 3);
+  for (int i = 0; i < nli; ++i)
     for (int k = 0; k < 3; ++k) lms_i[i * 3 + k] = lms[(size_t)S.lm_order[i] * 3 + k];
   struct Up { void* dst; const void* src; size_t bytes; };
   std::vector<Up> ups = {
-      {d_lm_seg, S.lm_seg.data(), sizeof(int32_t) * (nl + 1)},
+      {d_lm_seg, S.lm_seg.data(), sizeof(int32_t) * (nli + 1)},
       {d_cam_of, S.cam_of.data(), sizeof(int32_t) * no},
       {d_lm_of, S.lm_of.data(), sizeof(int32_t) * no},
       {d_meta, S.obs_meta.data(), sizeof(uint16_t) * no},
@@ -925,17 +941,25 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
       {d_cam_slot_list, S.cam_slot_list.data(), sizeof(int32_t) * S.n_slots},
       {d_slot_row, S.slot_row.data(), sizeof(int32_t) * S.n_slots},
       {d_cam_prob, S.cam_prob.data(), sizeof(int32_t) * nc},
-      {d_lm_prob, S.lm_prob.data(), sizeof(int32_t) * nl},
+      {d_lm_prob, S.lm_prob.data(), sizeof(int32_t) * nli},
       {d_tile_prob, tile_prob.data(), sizeof(int32_t) * S.n_tiles},
       {d_cam_off, S.cam_off.data(), sizeof(int32_t) * (P + 1)},
       {d_tile_off, S.tile_off.data(), sizeof(int32_t) * (P + 1)},
       {d_tile_rec, S.tile_rec.data(), S.tile_rec.size()},
       {h->obs, obs_s.data(), sizeof(double) * 2 * no},
       {h->obs_caller, obs_caller.data(), sizeof(int32_t) * no},
-      {h->lm_order_dev, S.lm_order.data(), sizeof(int32_t) * nl},
+      {h->lm_order_dev, S.lm_order.data(), sizeof(int32_t) * nli},
       {h->cams, cams.data(), sizeof(double) * nc * 9},
-      {h->lms, lms_i.data(), sizeof(double) * nl * 3},
+      {h->lms, lms_i.data(), sizeof(double) * nli * 3},
   };
+  std::vector<int32_t> long_tab;
+  if (S.n_long > 0) {
+    long_tab.insert(long_tab.end(), S.long_first.begin(), S.long_first.end());
+    long_tab.insert(long_tab.end(), S.long_np.begin(), S.long_np.end());
+    long_tab.insert(long_tab.end(), S.long_tile0.begin(), S.long_tile0.end());
+    ups.push_back({d_long, long_tab.data(), sizeof(int32_t) * long_tab.size()});
+    ups.push_back({d_lm_long, S.lm_long.data(), sizeof(int32_t) * nli});
+  }
   if (h->weighted) ups.push_back({h->sqrt_w, sw_s.data(), sizeof(double) * no});
   // FP32 bulk: the observations and weights in float, rounded once here as the kernels would
   std::vector<float> obs32_s, sw32_s;
@@ -969,7 +993,12 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
 
   Topology& tp = h->tp;
   tp.n_cams = nc;
-  tp.n_lms = nl;
+  tp.n_lms = nli;
+  tp.n_long = S.n_long;
+  tp.long_first = d_long;
+  tp.long_np = d_long ? d_long + S.n_long : nullptr;
+  tp.long_tile0 = d_long ? d_long + 2 * S.n_long : nullptr;
+  tp.lm_long = d_lm_long;
   tp.n_obs = no;
   tp.n_obs_pad = h->n_o_pad;
   tp.n_tiles = S.n_tiles;
@@ -1057,8 +1086,9 @@ ba_status seq_lm_step(ba_handle* h, bool batch, bool gated) {
       launch_lin_camera_reduce<double>(h->tp, (const double*)h->partial, h->U45, h->b_p, s,
                                        h->relin);
     }
+    launch_long_track_blocks(h->tp, h->V, h->b_l, s, h->relin);
     tmark(h, kTLin, 0, 1);
-    h->launches += 3;
+    h->launches += 3 + long_kernels(h);
     CK(cudaMemsetAsync(h->relin, 0, sizeof(int32_t), s));
   } else if (!h->linearized) {
     seq_linearize(h);
@@ -1364,9 +1394,9 @@ ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* 
   // launches replayed as a graph on the best schedule
   for (int k = 1; k <= h->plain_max; ++k)
     trial({3, k, series_auto_target(h->n_o, k * h->sms - 1), kDefaultTail});
-  for (int k = 1; k <= h->stage_max; ++k)
+  for (int k = 1; k <= h->stage_max && h->tp.n_long == 0; ++k)
     trial({4, k, series_auto_target(h->n_o, k * h->sms - 1), kDefaultTail});
-  for (int k = 1; k <= h->flow_max; ++k)
+  for (int k = 1; k <= h->flow_max && h->tp.n_long == 0; ++k)
     trial({5, k, series_auto_target(h->n_o, k * h->sms), kDefaultTail});
   if (best.exec >= 3) {
     const Cand b = best;
@@ -1438,6 +1468,8 @@ ba_status ba_set_schedule(ba_handle* h, const ba_schedule* in) {
     return fail(BA_ERR_INVALID_ARG, "series_exec 4 needs BA_FP32_BULK and the staged kernel");
   if (in->series_exec == 5 && h->flow_max <= 0)
     return fail(BA_ERR_INVALID_ARG, "series_exec 5 needs the dataflow kernel (cooperative launch)");
+  if ((in->series_exec == 4 || in->series_exec == 5) && h->tp.n_long > 0)
+    return fail(BA_ERR_INVALID_ARG, "series_exec 4 and 5 take no tracks of more than 256 observations");
   const int kmax = in->series_exec == 4 ? h->stage_max : in->series_exec == 5 ? h->flow_max
                                                                               : h->plain_max;
   if (in->series_exec >= 3 && (in->blocks_per_sm < 1 || in->blocks_per_sm > kmax))
@@ -1481,7 +1513,7 @@ ba_status ba_adjoint(ba_handle* h, double lambda, const double* g_cams, const do
     gp = h->x;
     gl = h->dx_l;
   }
-  launch_adjoint_rhs(h->n_c, h->n_l, h->lm_order_dev, gp, gl, h->adj_p, h->adj_l, s);
+  launch_adjoint_rhs(h->n_c, h->n_li, h->lm_order_dev, gp, gl, h->adj_p, h->adj_l, s);
   launch_set_scalar(h->scalars + 0, lambda, s);
   h->launches += 2;
   h->solve_lambda = lambda;
@@ -1621,7 +1653,7 @@ ba_status precondition(ba_handle* h, int precond, int m, const double* r, double
     return BA_OK;
   }
   launch_negate(h->n_c * 9, r, h->adj_p, s);
-  CK(cudaMemsetAsync(h->adj_l, 0, sizeof(double) * (size_t)h->n_l * 3, s));
+  CK(cudaMemsetAsync(h->adj_l, 0, sizeof(double) * (size_t)h->n_li * 3, s));
   const ba_options saved = h->opts;
   h->opts.eps = 0.0;
   h->opts.max_inner = m;
@@ -1688,7 +1720,7 @@ ba_status pcg_solve(ba_handle* h, double lambda, int precond, int m, double rtol
   const T* Vi = h->f32() ? (const T*)(const void*)h->Vinv_f : (const T*)(const void*)h->Vinv;
   launch_tile_backsub<T>(h->tp, (const T*)h->J, (const T*)h->r, h->x, h->b_l, Vi, h->dx_l,
                          h->block_pred, s);
-  h->launches += 1;
+  h->launches += 1 + long_kernels(h);
   CK(cudaMemcpyAsync(h->h_flag, h->not_spd, sizeof(int32_t) * h->n_probs, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   st = check_launch(h, "PCG back-substitution");
@@ -1830,7 +1862,8 @@ ba_status state_out(ba_handle* h, const double* cams_dev, const double* lms_dev,
   const cudaMemcpyKind kind = ptr_kind == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (cams) CK(cudaMemcpyAsync(cams, cams_dev, sizeof(double) * (size_t)h->n_c * 9, kind, s));
   if (lms) {
-    launch_scatter_rows3(lms_dev, h->lm_order_dev, h->n_l, h->adj_l, s);
+    // every piece of a long track holds the same values: its copies land on one caller row
+    launch_scatter_rows3(lms_dev, h->lm_order_dev, h->n_li, h->adj_l, s);
     h->launches += 1;
     CK(cudaMemcpyAsync(lms, h->adj_l, sizeof(double) * (size_t)h->n_l * 3, kind, s));
   }
@@ -1872,7 +1905,7 @@ ba_status ba_set_params(ba_handle* h, const double* cams, const double* lms, int
   if (h->h_io[0]) return fail(BA_ERR_NONFINITE, "non-finite camera parameter");
   if (h->h_io[1]) return fail(BA_ERR_NONFINITE, "non-finite landmark");
   if (cams) CK(cudaMemcpyAsync(h->cams, c_src, sizeof(double) * nc9, cudaMemcpyDeviceToDevice, s));
-  if (lms) launch_gather_rows3(l_src, h->lm_order_dev, h->n_l, h->lms, s);
+  if (lms) launch_gather_rows3(l_src, h->lm_order_dev, h->n_li, h->lms, s);
   h->launches += (cams ? 1 : 0) + (lms ? 2 : 0);
   h->linearized = false;
   h->relin_synced = false;
@@ -1945,19 +1978,19 @@ ba_status ba_get_blocks(ba_handle* h, double* U, double* V, double* b_p, double*
     if ((st = copy_out(b_p, b.data(), sizeof(double) * b.size(), ptr_kind)) != BA_OK) return st;
   }
   if (V) {
-    std::vector<double> v6((size_t)nl * 6), v((size_t)nl * 9);
+    std::vector<double> v6((size_t)h->n_li * 6), v((size_t)nl * 9);
     CK(cudaMemcpy(v6.data(), h->V, sizeof(double) * v6.size(), cudaMemcpyDeviceToHost));
     static const int map[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
-    for (int i = 0; i < nl; ++i) {
+    for (int i = 0; i < h->n_li; ++i) {
       const size_t c = (size_t)h->sched.lm_order[i];
       for (int k = 0; k < 9; ++k) v[c * 9 + k] = v6[(size_t)i * 6 + map[k]];
     }
     if ((st = copy_out(V, v.data(), sizeof(double) * v.size(), ptr_kind)) != BA_OK) return st;
   }
   if (b_l) {
-    std::vector<double> bi((size_t)nl * 3), bo((size_t)nl * 3);
+    std::vector<double> bi((size_t)h->n_li * 3), bo((size_t)nl * 3);
     CK(cudaMemcpy(bi.data(), h->b_l, sizeof(double) * bi.size(), cudaMemcpyDeviceToHost));
-    for (int i = 0; i < nl; ++i)
+    for (int i = 0; i < h->n_li; ++i)
       for (int k = 0; k < 3; ++k) bo[(size_t)h->sched.lm_order[i] * 3 + k] = bi[(size_t)i * 3 + k];
     if ((st = copy_out(b_l, bo.data(), sizeof(double) * bo.size(), ptr_kind)) != BA_OK) return st;
   }

@@ -322,6 +322,39 @@ void launch_lin_camera_reduce(const Topology& tp, const PT* partial, double* U45
   const int blocks = (tp.n_cams + 3) / 4;
   lin_camera_reduce_kernel<PT><<<blocks, 4 * kLinVals, 0, s>>>(tp, partial, U45, b_p, gate);
 }
+// Long tracks: the linearisation kernel leaves each piece's own sums in V and b_l; the track's
+// V = sum J_l^T J_l and b_l = sum J_l^T r are the sums over its pieces, added in piece order (in
+// double) and written back to every piece.  One thread per long track.
+__global__ void long_track_blocks_kernel(Topology tp, double* __restrict__ V,
+                                         double* __restrict__ b_l,
+                                         const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= tp.n_long) return;
+  const int l0 = tp.long_first[j], np = tp.long_np[j];
+  double acc[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k] = 0.0;
+  for (int q = 0; q < np; ++q) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] += V[(size_t)(l0 + q) * 6 + k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[6 + k] += b_l[(size_t)(l0 + q) * 3 + k];
+  }
+  for (int q = 0; q < np; ++q) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) V[(size_t)(l0 + q) * 6 + k] = acc[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) b_l[(size_t)(l0 + q) * 3 + k] = acc[6 + k];
+  }
+}
+
+void launch_long_track_blocks(const Topology& tp, double* V, double* b_l, cudaStream_t s,
+                              const int32_t* gate) {
+  if (tp.n_long <= 0) return;
+  long_track_blocks_kernel<<<(tp.n_long + 127) / 128, 128, 0, s>>>(tp, V, b_l, gate);
+}
+
 template void launch_lin_camera_reduce<double>(const Topology&, const double*, double*, double*, cudaStream_t, const int32_t*);
 template void launch_lin_camera_reduce<float>(const Topology&, const float*, double*, double*, cudaStream_t, const int32_t*);
 

@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(kTileObs) tile_backsub_kernel(
   const int tile = blockIdx.x, tid = threadIdx.x;
   const TileHdr th = load_tile(tp, tile);
   const int L0 = th.L0, L1 = th.L0 + th.nl, o0 = th.o0, n = th.n, S0 = th.S0, ns = th.ns;
+  if (tp.n_long > 0 && tp.lm_long[L0] >= 0) return;  // a piece of a long track (below)
   for (int i = tid; i < ns * 9; i += blockDim.x) {
     const int s = i / 9, k = i - s * 9;
     tcam[s][k] = (T)x[(size_t)tp.slot_cam[S0 + s] * 9 + k];
@@ -134,11 +135,95 @@ __global__ void __launch_bounds__(kTileObs) tile_backsub_kernel(
   if (tid == 0) block_pred[tile] = tot;
 }
 
+// Back-substitution of a long track (one block per track): dx_l = -V^-1 (b_l + sum over
+// every observation of J_l^T J_p x_c), each piece's sum in a fixed order (block_sum_tile, in
+// double) and the pieces added in order; every piece receives dx_l.  Then each piece's model
+// decrease terms (as in the tile kernel) are summed into block_pred of the piece's tile.
+template <typename T>
+__global__ void __launch_bounds__(kTileObs) long_backsub_kernel(
+    Topology tp, const T* __restrict__ J, const T* __restrict__ r, const double* __restrict__ x,
+    const double* __restrict__ b_l, const T* __restrict__ Vinv, double* __restrict__ dx_l,
+    double* __restrict__ block_pred) {
+  __shared__ double sbuf[kTileObs];
+  __shared__ double zs[3];
+  const int j = blockIdx.x, tid = threadIdx.x;
+  const int l0 = tp.long_first[j], np = tp.long_np[j], t0 = tp.long_tile0[j];
+  const size_t pad = (size_t)tp.n_obs_pad;
+  auto obs_u = [&](int o, T (&jp)[18], T (&jl)[6], T& u0, T& u1) {
+    const int c = tp.cam_of[o];
+    load_J(J, pad, o, jp, jl);
+    u0 = (T)0;
+    u1 = (T)0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const T xk = (T)x[(size_t)c * 9 + k];
+      u0 += jp[k] * xk;
+      u1 += jp[9 + k] * xk;
+    }
+  };
+  double S0 = 0.0, S1 = 0.0, S2 = 0.0;
+  for (int q = 0; q < np; ++q) {
+    const int o0 = tp.lm_seg[l0 + q], n = tp.lm_seg[l0 + q + 1] - o0;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+    if (tid < n) {
+      T jp[18], jl[6], u0, u1;
+      obs_u(o0 + tid, jp, jl, u0, u1);
+      v0 = (double)(jl[0] * u0 + jl[3] * u1);
+      v1 = (double)(jl[1] * u0 + jl[4] * u1);
+      v2 = (double)(jl[2] * u0 + jl[5] * u1);
+    }
+    const double a0 = block_sum_tile(v0, sbuf);
+    __syncthreads();
+    const double a1 = block_sum_tile(v1, sbuf);
+    __syncthreads();
+    const double a2 = block_sum_tile(v2, sbuf);
+    __syncthreads();
+    S0 += a0;
+    S1 += a1;
+    S2 += a2;
+  }
+  if (tid == 0) {
+    const double s0 = b_l[(size_t)l0 * 3 + 0] + S0, s1 = b_l[(size_t)l0 * 3 + 1] + S1,
+                 s2 = b_l[(size_t)l0 * 3 + 2] + S2;
+    const T* vi = Vinv + (size_t)l0 * 6;
+    const double w0 = (double)vi[0], w1 = (double)vi[1], w2 = (double)vi[2];
+    const double w3 = (double)vi[3], w4 = (double)vi[4], w5 = (double)vi[5];
+    zs[0] = -(w0 * s0 + w1 * s1 + w2 * s2);
+    zs[1] = -(w1 * s0 + w3 * s1 + w4 * s2);
+    zs[2] = -(w2 * s0 + w4 * s1 + w5 * s2);
+  }
+  __syncthreads();
+  for (int q = tid; q < np; q += blockDim.x) {
+    dx_l[(size_t)(l0 + q) * 3 + 0] = zs[0];
+    dx_l[(size_t)(l0 + q) * 3 + 1] = zs[1];
+    dx_l[(size_t)(l0 + q) * 3 + 2] = zs[2];
+  }
+  const T z0 = (T)zs[0], z1 = (T)zs[1], z2 = (T)zs[2];
+  for (int q = 0; q < np; ++q) {
+    const int o0 = tp.lm_seg[l0 + q], n = tp.lm_seg[l0 + q + 1] - o0;
+    double pred = 0.0;
+    if (tid < n) {
+      const int o = o0 + tid;
+      T jp[18], jl[6], u0, u1;
+      obs_u(o, jp, jl, u0, u1);
+      const double r0 = (double)r[o], r1 = (double)r[pad + o];
+      const double q0 = r0 + (double)u0 + (double)(jl[0] * z0 + jl[1] * z1 + jl[2] * z2);
+      const double q1 = r1 + (double)u1 + (double)(jl[3] * z0 + jl[4] * z1 + jl[5] * z2);
+      pred = (r0 * r0 + r1 * r1) - (q0 * q0 + q1 * q1);
+    }
+    const double tot = block_sum_tile(pred, sbuf);
+    if (tid == 0) block_pred[t0 + q] = tot;
+    __syncthreads();
+  }
+}
+
 template <typename T>
 void launch_tile_backsub(const Topology& tp, const T* J, const T* r, const double* x,
                          const double* b_l, const T* Vinv, double* dx_l, double* block_pred,
                          cudaStream_t s) {
   tile_backsub_kernel<T><<<tp.n_tiles, kTileObs, 0, s>>>(tp, J, r, x, b_l, Vinv, dx_l, block_pred);
+  if (tp.n_long > 0)
+    long_backsub_kernel<T><<<tp.n_long, kTileObs, 0, s>>>(tp, J, r, x, b_l, Vinv, dx_l, block_pred);
 }
 
 template void launch_tile_rhs<double>(const Topology&, const SerTopo&, const double*, const double*, const double*, double*, const SeriesState*, cudaStream_t);

@@ -64,10 +64,19 @@ constexpr int kReduceThreads = 256;
 struct Schedule {
   int n_cams = 0, n_lms = 0, n_obs = 0, n_probs = 1;
   int n_tiles = 0, n_slots = 0, max_slots_per_tile = 0, max_track = 0;
+  // Internal landmarks: a landmark with more than kTileObs observations (a long track) is
+  // split into near-equal pieces of at most kTileObs observations in camera order, each an
+  // internal landmark with its own tile and a copy of the landmark's state; its landmark-side
+  // sums are combined over the pieces in piece order.  n_lms_int counts internal landmarks.
+  int n_lms_int = 0, n_long = 0;
+  std::vector<int32_t> long_first;   // [n_long] first piece (internal landmark) of each long track
+  std::vector<int32_t> long_np;      // [n_long] its pieces
+  std::vector<int32_t> long_tile0;   // [n_long] the tile of its first piece (one tile per piece)
+  std::vector<int32_t> lm_long;      // [n_lms_int] long track of each internal landmark, or -1
   std::vector<int32_t> lm_order;     // internal landmark -> caller landmark
-  std::vector<int32_t> lm_rank;      // caller landmark -> internal landmark
+  std::vector<int32_t> lm_rank;      // caller landmark -> (first) internal landmark
   std::vector<int64_t> obs_order;    // sorted observation -> caller observation
-  std::vector<int32_t> lm_seg;       // [n_lms + 1] observation offsets per internal landmark
+  std::vector<int32_t> lm_seg;       // [n_lms_int + 1] observation offsets per internal landmark
   std::vector<int32_t> cam_of;       // [n_obs] camera of each sorted observation
   std::vector<int32_t> lm_of;        // [n_obs] internal landmark of each sorted observation
   std::vector<uint16_t> obs_meta;    // [n_obs] pos | slot << 8
@@ -87,7 +96,7 @@ struct Schedule {
   std::vector<int32_t> lm_off_int;   // [n_probs + 1] internal landmark ranges
   std::vector<int32_t> tile_off;     // [n_probs + 1] tile ranges
   std::vector<int32_t> cam_prob;     // [n_cams]
-  std::vector<int32_t> lm_prob;      // [n_lms] problem of each internal landmark
+  std::vector<int32_t> lm_prob;      // [n_lms_int] problem of each internal landmark
 };
 
 // Per-tile record, one contiguous 16-byte aligned block per tile, so that one bulk copy brings
@@ -221,6 +230,13 @@ struct Topology {
   const int32_t* cam_slot_ptr;
   const int32_t* cam_slot_list;
   const int32_t* slot_row;  // partial sums are stored camera-major: row slot_row[slot]
+  // long tracks (Schedule): their pieces, the tile of the first piece, the track of each
+  // internal landmark (-1: none)
+  int n_long;
+  const int32_t* long_first;
+  const int32_t* long_np;
+  const int32_t* long_tile0;
+  const int32_t* lm_long;
   // independent problems (P = 1 for a single problem)
   int n_probs;
   const int32_t* cam_prob;  // [n_cams]
@@ -339,6 +355,9 @@ void launch_lin_camera_reduce(const Topology& tp, const PT* partial, double* U45
 // lambda of problem p is lam[p * lam_stride] (lam_stride 0: one lambda for all problems);
 // not_spd[p] is set to 1 when a damped block of problem p fails its Cholesky factorisation (the
 // failed pivot is replaced by 1 so that the inverse stays finite).
+// Long tracks: V and b_l summed over each track's pieces and written back to every piece.
+void launch_long_track_blocks(const Topology& tp, double* V, double* b_l, cudaStream_t s,
+                              const int32_t* gate = nullptr);
 void launch_damp_invert(const Topology& tp, const double* U45, const double* V,
                         const double* lambda, int lam_stride, int damping_mode, double* Uinv,
                         double* Vinv, float* Vinv_f, int32_t* not_spd, cudaStream_t s);

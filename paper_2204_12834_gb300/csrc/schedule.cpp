@@ -61,33 +61,60 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
   }
   int max_track = 0;
   for (int l = 0; l < n_lms; ++l) max_track = std::max(max_track, count[l]);
-  if (max_track > kTileObs)
-    return "a landmark has " + std::to_string(max_track) + " observations; at most " +
-           std::to_string(kTileObs) + " are supported";
   S->max_track = max_track;
 
-  // Internal landmark order: by problem, then smallest observing camera (unobserved landmarks
-  // last within their problem), then caller index.
-  S->lm_order.resize(n_lms);
-  std::iota(S->lm_order.begin(), S->lm_order.end(), 0);
-  std::stable_sort(S->lm_order.begin(), S->lm_order.end(), [&](int32_t a, int32_t b) {
+  // Landmark order: by problem, then smallest observing camera (unobserved landmarks last
+  // within their problem), then caller index.
+  std::vector<int32_t> order(n_lms);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
     if (lprob[a] != lprob[b]) return lprob[a] < lprob[b];
     return key[a] < key[b];
   });
-  S->lm_prob.resize(n_lms);
-  S->lm_off_int.assign(n_probs + 1, 0);
+  // Internal landmarks: the landmarks in that order, a long track as its pieces.
+  std::vector<int32_t> first(n_lms);  // first internal landmark of each caller landmark
+  int n_int = 0;
+  S->long_first.clear();
+  S->long_np.clear();
   for (int i = 0; i < n_lms; ++i) {
-    S->lm_prob[i] = lprob[S->lm_order[i]];
-    S->lm_off_int[S->lm_prob[i] + 1]++;
+    const int l = order[i], k = count[l];
+    first[l] = n_int;
+    const int np = k > kTileObs ? (k + kTileObs - 1) / kTileObs : 1;
+    if (np > 1) {
+      S->long_first.push_back(n_int);
+      S->long_np.push_back(np);
+    }
+    n_int += np;
+  }
+  S->n_lms_int = n_int;
+  S->n_long = (int)S->long_first.size();
+  S->lm_order.resize(n_int);
+  S->lm_prob.resize(n_int);
+  S->lm_long.assign(n_int, -1);
+  S->lm_seg.assign(n_int + 1, 0);
+  S->lm_off_int.assign(n_probs + 1, 0);
+  for (int i = 0, j = 0; i < n_lms; ++i) {
+    const int l = order[i], k = count[l];
+    const int np = k > kTileObs ? (k + kTileObs - 1) / kTileObs : 1;
+    for (int q = 0; q < np; ++q) {
+      const int e = first[l] + q;
+      S->lm_order[e] = l;
+      S->lm_prob[e] = lprob[l];
+      // piece q of np: near-equal sizes, the larger ones first
+      S->lm_seg[e + 1] = S->lm_seg[e] + k / np + (q < k % np ? 1 : 0);
+      S->lm_off_int[lprob[l] + 1]++;
+    }
+    if (np > 1) {
+      for (int q = 0; q < np; ++q) S->lm_long[first[l] + q] = j;
+      ++j;
+    }
   }
   for (int p = 0; p < n_probs; ++p) S->lm_off_int[p + 1] += S->lm_off_int[p];
   S->lm_rank.assign(n_lms, 0);
-  for (int i = 0; i < n_lms; ++i) S->lm_rank[S->lm_order[i]] = i;
+  for (int l = 0; l < n_lms; ++l) S->lm_rank[l] = first[l];
 
-  S->lm_seg.assign(n_lms + 1, 0);
-  for (int i = 0; i < n_lms; ++i) S->lm_seg[i + 1] = S->lm_seg[i] + count[S->lm_order[i]];
-
-  // Observations sorted by (internal landmark, camera, caller index).
+  // Observations sorted by (landmark in internal order, camera, caller index); a long track's
+  // observations go to its pieces in that order.
   S->obs_order.resize(n_obs);
   std::iota(S->obs_order.begin(), S->obs_order.end(), (int64_t)0);
   std::sort(S->obs_order.begin(), S->obs_order.end(), [&](int64_t a, int64_t b) {
@@ -98,10 +125,11 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
   });
   S->cam_of.resize(n_obs);
   S->lm_of.resize(n_obs);
-  for (int o = 0; o < n_obs; ++o) {
-    S->cam_of[o] = cam_idx[S->obs_order[o]];
-    S->lm_of[o] = S->lm_rank[lm_idx[S->obs_order[o]]];
-  }
+  for (int e = 0; e < n_int; ++e)
+    for (int o = S->lm_seg[e]; o < S->lm_seg[e + 1]; ++o) {
+      S->cam_of[o] = cam_idx[S->obs_order[o]];
+      S->lm_of[o] = e;
+    }
 
   // Tiles: greedy packing of whole landmarks of one problem, at most kTileObs observations,
   // kTileLms landmarks and kTileSlots distinct cameras per tile.
@@ -110,13 +138,15 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
   {
     int tile_obs = 0, tile_lms = 0, tile_cams = 0, tile_id = 0;
     std::vector<int32_t> stamp(n_cams, -1);  // tile that last counted the camera
-    for (int i = 0; i < n_lms; ++i) {
+    for (int i = 0; i < n_int; ++i) {
       const int k = S->lm_seg[i + 1] - S->lm_seg[i];
       int fresh = 0;  // cameras of landmark i not yet in the tile (a track has distinct cameras)
       for (int o = S->lm_seg[i]; o < S->lm_seg[i + 1]; ++o) fresh += stamp[S->cam_of[o]] != tile_id;
       const bool new_prob = i > 0 && S->lm_prob[i] != S->lm_prob[i - 1];
-      if (tile_lms > 0 && (new_prob || tile_obs + k > kTileObs || tile_lms + 1 > kTileLms ||
-                           tile_cams + fresh > kTileSlots)) {
+      // a piece of a long track has a tile of its own
+      const bool piece = S->lm_long[i] >= 0 || (i > 0 && S->lm_long[i - 1] >= 0);
+      if (tile_lms > 0 && (new_prob || piece || tile_obs + k > kTileObs ||
+                           tile_lms + 1 > kTileLms || tile_cams + fresh > kTileSlots)) {
         S->tile_lm0.push_back(i);
         tile_obs = 0;
         tile_lms = 0;
@@ -129,9 +159,14 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
       tile_lms += 1;
       tile_cams += fresh;
     }
-    S->tile_lm0.push_back(n_lms);
+    S->tile_lm0.push_back(n_int);
   }
   S->n_tiles = (int)S->tile_lm0.size() - 1;
+  S->long_tile0.assign(S->n_long, 0);
+  for (int t = 0; t < S->n_tiles; ++t) {
+    const int j = S->lm_long[S->tile_lm0[t]];
+    if (j >= 0 && S->tile_lm0[t] == S->long_first[j]) S->long_tile0[j] = t;
+  }
   S->tile_off.assign(n_probs + 1, 0);
   for (int t = 0; t < S->n_tiles; ++t) S->tile_off[S->lm_prob[S->tile_lm0[t]] + 1]++;
   for (int p = 0; p < n_probs; ++p) S->tile_off[p + 1] += S->tile_off[p];
@@ -232,8 +267,13 @@ std::string build_series_schedule(const Schedule& S, int target, int tail, SerSc
   std::vector<int32_t> stamp(S.n_cams, -1);  // range that last counted the camera
   std::vector<int32_t> gslot_of(S.n_cams, -1);
   std::vector<int32_t> local;
-  std::vector<std::pair<int, int>> ranges;   // one problem's groups as landmark ranges
+  struct Range {
+    int l, le;
+    bool long_track;  // the pieces of one long track (a long group)
+  };
+  std::vector<Range> ranges;  // one problem's groups as landmark ranges
   int n_groups = 0, rid = 0;
+  int next_tag = -2;  // marks of gslot_of while a slot set is collected (slots are >= 0)
   for (int p = 0; p < S.n_probs; ++p) {
     // the problem's observed landmarks (unobserved ones sort last within their problem)
     const int l0 = S.lm_off_int[p];
@@ -245,11 +285,22 @@ std::string build_series_schedule(const Schedule& S, int target, int tail, SerSc
     int64_t k_next = 1;  // index of the next balanced boundary
     ranges.clear();
     for (int l = l0; l < l1;) {
+      if (S.lm_long[l] >= 0) {
+        // a long track: its pieces form one group of their own
+        const int le = l + S.long_np[S.lm_long[l]];
+        ranges.push_back({l, le, true});
+        const int64_t done = (int64_t)S.lm_seg[le] - o_beg;
+        while (k_next < ng && done * ng >= k_next * n_p) ++k_next;
+        l = le;
+        continue;
+      }
       // one range: landmarks [l, le), ending at the balanced boundary k_next * n_p / ng
-      // (observations from the problem's start) or before its cameras would exceed kGroupSlots
+      // (observations from the problem's start), before a long track, or before its cameras
+      // would exceed kGroupSlots
       const int r = rid++;
       int le = l, ncam = 0;
       while (le < l1) {
+        if (S.lm_long[le] >= 0) break;
         const int a = S.lm_seg[le], b = S.lm_seg[le + 1];
         int fresh = 0;
         for (int o = a; o < b; ++o) fresh += stamp[S.cam_of[o]] != r;
@@ -273,44 +324,56 @@ std::string build_series_schedule(const Schedule& S, int target, int tail, SerSc
         const int64_t head_end = S.lm_seg[l] + n_r - n_r / 8;
         int lh = l + 1;
         while (lh < le && S.lm_seg[lh] < head_end) ++lh;
-        ranges.push_back({l, lh});
+        ranges.push_back({l, lh, false});
         const int64_t t0 = S.lm_seg[lh], n_t = (int64_t)S.lm_seg[le] - t0;
         int lt = lh;
         for (int k = 1; k <= tail && lt < le; ++k) {
           int lte = lt + 1;
           while (lte < le && ((int64_t)S.lm_seg[lte] - t0) * tail < k * n_t) ++lte;
           if (k == tail) lte = le;
-          ranges.push_back({lt, lte});
+          ranges.push_back({lt, lte, false});
           lt = lte;
         }
       } else {
-        ranges.push_back({l, le});
+        ranges.push_back({l, le, false});
       }
       l = le;
     }
     for (const auto& rg : ranges) {
-      const int l = rg.first, le = rg.second;
+      const int l = rg.l, le = rg.le;
       const int g = n_groups++;
-      // the group's distinct cameras, ascending, are its slots
       const int gs0 = (int)gcams.size();
-      for (int o = S.lm_seg[l]; o < S.lm_seg[le]; ++o) {
-        const int c = S.cam_of[o];
-        if (gslot_of[c] != -2 - g) {
-          gslot_of[c] = -2 - g;
-          gcams.push_back(c);
+      // The group's distinct cameras, ascending, are its slots.  A long group's chunks (one
+      // piece each) have slots of their own instead: each chunk's distinct cameras, ascending,
+      // from slot base d[7] on (code and clist hold chunk-relative slots).
+      auto add_slots = [&](int oa, int ob, int tag) {
+        const int s0 = (int)gcams.size();
+        for (int o = oa; o < ob; ++o) {
+          const int c = S.cam_of[o];
+          if (gslot_of[c] != tag) {
+            gslot_of[c] = tag;
+            gcams.push_back(c);
+          }
         }
-      }
-      std::sort(gcams.begin() + gs0, gcams.end());
-      const int ns_g = (int)gcams.size() - gs0;
-      for (int s = 0; s < ns_g; ++s) gslot_of[gcams[gs0 + s]] = s;
-      // chunks: whole landmarks, at most kChunkObs observations
+        std::sort(gcams.begin() + s0, gcams.end());
+        for (int s = s0; s < (int)gcams.size(); ++s) gslot_of[gcams[s]] = s - s0;
+        return s0 - gs0;
+      };
+      if (!rg.long_track) add_slots(S.lm_seg[l], S.lm_seg[le], next_tag--);
+      // chunks: whole landmarks, at most kChunkObs observations (a long group: one piece each)
       const int c0 = (int)(Q->chunk.size() / 8);
       int lc = l;
       while (lc < le) {
         int lce = lc;
-        while (lce < le && S.lm_seg[lce + 1] - S.lm_seg[lc] <= kChunkObs) ++lce;
+        if (rg.long_track)
+          lce = lc + 1;
+        else
+          while (lce < le && S.lm_seg[lce + 1] - S.lm_seg[lc] <= kChunkObs) ++lce;
         if (lce == lc) return "a landmark has more observations than a chunk holds";
         const int o0 = S.lm_seg[lc], n = S.lm_seg[lce] - o0, nl = lce - lc;
+        const int sbase = rg.long_track
+                              ? add_slots(o0, o0 + n, next_tag--)
+                              : 0;
         local.resize(n);
         for (int i = 0; i < n; ++i) local[i] = i;
         std::stable_sort(local.begin(), local.end(), [&](int32_t x, int32_t y) {
@@ -340,12 +403,14 @@ std::string build_series_schedule(const Schedule& S, int target, int tail, SerSc
         uint16_t* sseg = reinterpret_cast<uint16_t*>(base + L.sseg);
         for (int j = 0; j <= nl; ++j) sseg[j] = (uint16_t)(S.lm_seg[lc + j] - o0);
         std::memcpy(base + L.clist, clist.data(), 4 * (size_t)ns);
-        const int32_t d[8] = {o0, n, lc, nl, ns, (int32_t)(off / 16), g, 0};
+        const int32_t d[8] = {o0, n, lc, nl, ns, (int32_t)(off / 16), g, sbase};
         Q->chunk.insert(Q->chunk.end(), d, d + 8);
         lc = lce;
       }
       const int nc = (int)(Q->chunk.size() / 8) - c0;
-      const int32_t gd[8] = {c0, nc, gs0, ns_g, S.lm_seg[le] - S.lm_seg[l], p, 0, 0};
+      const int ns_g = (int)gcams.size() - gs0;
+      const int32_t gd[8] = {c0, nc, gs0, ns_g, S.lm_seg[le] - S.lm_seg[l], p,
+                             rg.long_track ? 1 : 0, 0};
       gnat.insert(gnat.end(), gd, gd + 8);
     }
   }

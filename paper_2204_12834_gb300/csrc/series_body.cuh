@@ -465,6 +465,107 @@ __device__ __forceinline__ void chunk_f64(const Topology& tp, const SerTopo& sp,
   }
 }
 
+// The group of a long track (more than kChunkObs observations; its pieces are the group's
+// chunks, one internal landmark each, every piece holding the track's V^-1 and b_l).  Series
+// mode, pass A: per piece, thread o forms v_o = J_l,o^T J_p,o t_c(o) and the block sums the
+// piece's v in a fixed order (block_sum_tile, in double); the piece sums are added in piece
+// order (in double); z = V^-1 of that sum.  RHS mode: z = V^-1 b_l.  Pass B, per piece: g_o =
+// J_p,o^T (J_l,o z) at its camera-sorted position, then thread (slot, k) sums its slot's rows
+// in order and writes the piece's own partial row for that slot (a long group keeps no
+// accumulator across its chunks).  J is read twice in series mode.  Every thread must call it.
+template <typename T, int MODE>
+__device__ __noinline__ void long_group_body(const Topology& tp, const SerTopo& sp, int g,
+                                             const T* __restrict__ J,
+                                             const T* __restrict__ t_cam,
+                                             const double* __restrict__ b_l,
+                                             const T* __restrict__ Vinv, T* __restrict__ partial,
+                                             GroupSmem<T>& sm) {
+  const int tid = threadIdx.x;
+  const int4 gd = __ldg(sp.group + 2 * g);
+  const int c0 = gd.x, nc = gd.y, s0 = gd.z;
+  double* sbuf = reinterpret_cast<double*>(&sm.acc[0][0]);  // kChunkObs doubles
+  T (*rows)[9] = reinterpret_cast<T (*)[9]>(&sm.sg[0][0]);  // kChunkObs rows
+  __shared__ double zs[3];
+  const size_t pad = (size_t)tp.n_obs_pad;
+  const int L = __ldg(sp.chunk + 2 * c0).z;  // the first piece (all pieces hold the same V^-1)
+  double S0 = 0.0, S1 = 0.0, S2 = 0.0;
+  if (MODE == kModeSeries) {
+    for (int c = c0; c < c0 + nc; ++c) {
+      const int4 d0 = __ldg(sp.chunk + 2 * c), d1 = __ldg(sp.chunk + 2 * c + 1);
+      const int o0 = d0.x, n = d0.y, sbase = d1.w;
+      const uint8_t* rec = sp.rec + (size_t)d1.y * 16;
+      double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+      if (tid < n) {
+        T jp[18], jl[6];
+        load_J(J, pad, o0 + tid, jp, jl);
+        const uint32_t code = __ldg(reinterpret_cast<const uint32_t*>(rec) + tid);
+        const int cam = __ldg(sp.gslot_cam + s0 + sbase + (int)((code >> 8) & 0xff));
+        const T* tc = t_cam + (size_t)cam * kTStride;
+        T u0 = (T)0, u1 = (T)0;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+          const T tj = __ldcg(tc + j);
+          u0 += jp[j] * tj;
+          u1 += jp[9 + j] * tj;
+        }
+        v0 = (double)(jl[0] * u0 + jl[3] * u1);
+        v1 = (double)(jl[1] * u0 + jl[4] * u1);
+        v2 = (double)(jl[2] * u0 + jl[5] * u1);
+      }
+      const double a0 = block_sum_tile(v0, sbuf);
+      __syncthreads();
+      const double a1 = block_sum_tile(v1, sbuf);
+      __syncthreads();
+      const double a2 = block_sum_tile(v2, sbuf);
+      __syncthreads();
+      S0 += a0;
+      S1 += a1;
+      S2 += a2;
+    }
+  } else if (tid == 0) {
+    S0 = b_l[(size_t)L * 3 + 0];
+    S1 = b_l[(size_t)L * 3 + 1];
+    S2 = b_l[(size_t)L * 3 + 2];
+  }
+  if (tid == 0) {
+    const T* vi = Vinv + (size_t)L * 6;
+    const double w0 = (double)vi[0], w1 = (double)vi[1], w2 = (double)vi[2];
+    const double w3 = (double)vi[3], w4 = (double)vi[4], w5 = (double)vi[5];
+    zs[0] = w0 * S0 + w1 * S1 + w2 * S2;
+    zs[1] = w1 * S0 + w3 * S1 + w4 * S2;
+    zs[2] = w2 * S0 + w4 * S1 + w5 * S2;
+  }
+  __syncthreads();
+  const T z0 = (T)zs[0], z1 = (T)zs[1], z2 = (T)zs[2];
+  for (int c = c0; c < c0 + nc; ++c) {
+    const int4 d0 = __ldg(sp.chunk + 2 * c), d1 = __ldg(sp.chunk + 2 * c + 1);
+    const int o0 = d0.x, n = d0.y, ns = d1.x, sbase = d1.w;
+    const uint8_t* rec = sp.rec + (size_t)d1.y * 16;
+    const ChunkRecLayout RL = chunk_rec_layout(n, 1, ns);
+    if (tid < n) {
+      T jp[18], jl[6];
+      load_J(J, pad, o0 + tid, jp, jl);
+      const uint32_t code = __ldg(reinterpret_cast<const uint32_t*>(rec + RL.code) + tid);
+      const T w0 = jl[0] * z0 + jl[1] * z1 + jl[2] * z2;
+      const T w1 = jl[3] * z0 + jl[4] * z1 + jl[5] * z2;
+      T* row = rows[code & 0xff];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) row[k] = jp[k] * w0 + jp[9 + k] * w1;
+    }
+    __syncthreads();
+    const uint32_t* clist = reinterpret_cast<const uint32_t*>(rec + RL.clist);
+    for (int i = tid; i < ns * 9; i += blockDim.x) {
+      const int j = i / 9, k = i - 9 * j;
+      const uint32_t e = __ldg(clist + j);
+      const int gs = (int)(e & 0xff), beg = (int)(e >> 8) & 0xff, len = (int)(e >> 16);
+      T acc = (T)0;
+      for (int r = beg; r < beg + len; ++r) acc += rows[r][k];
+      partial[(size_t)__ldg(sp.gslot_row + s0 + sbase + gs) * 9 + k] = acc;
+    }
+    __syncthreads();
+  }
+}
+
 // One group (blockDim.x == kChunkObs; every thread must call it, and every thread must have
 // finished with the shared memory of the previous group, e.g. by a block barrier): stages the
 // current term of the group's slots and zeroes their accumulators, runs the chunks in order and
@@ -477,6 +578,10 @@ __device__ __forceinline__ void group_body(const Topology& tp, const SerTopo& sp
                                            const T* __restrict__ Vinv, T* __restrict__ partial,
                                            GroupSmem<T>& sm) {
   const int tid = threadIdx.x;
+  if (__ldg(sp.group + 2 * g + 1).z) {
+    long_group_body<T, MODE>(tp, sp, g, J, t_cam, b_l, Vinv, partial, sm);
+    return;
+  }
   const int4 gd = __ldg(sp.group + 2 * g);
   const int c0 = gd.x, nc = gd.y, s0 = gd.z, ns = gd.w;
   constexpr int R = sizeof(T) == 4 ? 3 : 5;  // 16-byte pieces of a term row in shared memory

@@ -45,6 +45,7 @@ int main(int argc, char** argv) {
                                          P > 1 ? lm_off.data() : nullptr, &S);
   CHECK(why.empty(), "build_schedule rejected the input: %s", why.c_str());
 
+  const int nli = S.n_lms_int;  // internal landmarks: long tracks count once per piece
   // observations: a permutation of the caller's, sorted by (internal landmark, camera)
   std::vector<char> seen(no, 0);
   for (int o = 0; o < no; ++o) {
@@ -52,20 +53,59 @@ int main(int argc, char** argv) {
     CHECK(q >= 0 && q < no && !seen[q], "obs_order is not a permutation at %d", o);
     seen[q] = 1;
     CHECK(S.cam_of[o] == cam[q], "cam_of[%d] is not the caller's camera", o);
-    CHECK(S.lm_of[o] == S.lm_rank[lm[q]], "lm_of[%d] is not the internal landmark", o);
+    CHECK(S.lm_of[o] >= 0 && S.lm_of[o] < nli && S.lm_order[S.lm_of[o]] == lm[q] &&
+              S.lm_of[o] >= S.lm_rank[lm[q]],
+          "lm_of[%d] is not (a piece of) the internal landmark", o);
     if (o > 0) {
       CHECK(S.lm_of[o] > S.lm_of[o - 1] ||
                 (S.lm_of[o] == S.lm_of[o - 1] && S.cam_of[o] >= S.cam_of[o - 1]),
             "observations %d, %d out of (landmark, camera) order", o - 1, o);
     }
   }
-  for (int l = 0; l < nl; ++l)
+  for (int l = 0; l < nli; ++l)
     for (int o = S.lm_seg[l]; o < S.lm_seg[l + 1]; ++o)
       CHECK(S.lm_of[o] == l, "lm_seg of landmark %d holds observation %d of another", l, o);
-  CHECK(S.lm_seg[0] == 0 && S.lm_seg[nl] == no, "lm_seg does not cover the observations");
+  CHECK(S.lm_seg[0] == 0 && S.lm_seg[nli] == no, "lm_seg does not cover the observations");
+
+  // long tracks: a landmark of more than kTileObs observations is split into consecutive pieces
+  // of near-equal size (at most kTileObs), in camera order, each alone in its tile
+  {
+    std::vector<int> cnt(nl, 0);
+    for (int o = 0; o < no; ++o) cnt[lm[o]]++;
+    int n_long = 0, extra = 0;
+    for (int l = 0; l < nl; ++l)
+      if (cnt[l] > kTileObs) {
+        ++n_long;
+        extra += (cnt[l] + kTileObs - 1) / kTileObs - 1;
+      }
+    CHECK(S.n_long == n_long && nli == nl + extra, "%d long tracks, %d internal landmarks", S.n_long,
+          nli);
+    std::vector<int> long_of(nli, -1);
+    for (int j = 0; j < S.n_long; ++j) {
+      const int e0 = S.long_first[j], np = S.long_np[j], l = S.lm_order[e0];
+      CHECK(np >= 2 && np == (cnt[l] + kTileObs - 1) / kTileObs, "long track %d has %d pieces", j, np);
+      CHECK(S.lm_rank[l] == e0, "long track %d: the caller's landmark maps to its first piece", j);
+      CHECK(S.lm_seg[e0 + np] - S.lm_seg[e0] == cnt[l], "long track %d observation count", j);
+      int lo = 1 << 30, hi = 0;
+      for (int q = 0; q < np; ++q) {
+        const int e = e0 + q, k = S.lm_seg[e + 1] - S.lm_seg[e], t = S.long_tile0[j] + q;
+        CHECK(S.lm_order[e] == l && S.lm_long[e] == j, "long track %d piece %d", j, q);
+        CHECK(t < S.n_tiles && S.tile_lm0[t] == e && S.tile_lm0[t + 1] == e + 1,
+              "long track %d piece %d is not alone in tile %d", j, q, t);
+        long_of[e] = j;
+        lo = std::min(lo, k);
+        hi = std::max(hi, k);
+      }
+      CHECK(hi <= kTileObs && hi - lo <= 1, "long track %d pieces of %d .. %d observations", j, lo, hi);
+    }
+    for (int e = 0; e < nli; ++e) {
+      CHECK(S.lm_long[e] == long_of[e], "lm_long[%d]", e);
+      CHECK(S.lm_seg[e + 1] - S.lm_seg[e] <= kTileObs, "landmark %d exceeds a tile", e);
+    }
+  }
 
   // tiles: whole landmarks of one problem within the caps; slots = the tile's cameras ascending
-  CHECK(S.tile_lm0.front() == 0 && S.tile_lm0.back() == nl, "tiles do not cover the landmarks");
+  CHECK(S.tile_lm0.front() == 0 && S.tile_lm0.back() == nli, "tiles do not cover the landmarks");
   std::vector<int> slot_count_of_cam(nc, 0);
   for (int t = 0; t < S.n_tiles; ++t) {
     const int L0 = S.tile_lm0[t], L1 = S.tile_lm0[t + 1];
@@ -139,14 +179,17 @@ int main(int argc, char** argv) {
         "series descriptor sizes");
   std::vector<int> chunk_group(Q.n_chunks, -1);
   std::vector<int> group_of_slot(Q.n_gslots, -1);
+  std::vector<int> slot_key(Q.n_gslots, -1);  // landmark order: the chunk its rows start in
   for (int i = 0; i < Q.n_groups; ++i) {
     const int32_t* g = &Q.group[8 * (size_t)i];
     if (i > 0) CHECK(g[4] <= Q.group[8 * (size_t)(i - 1) + 4], "groups not in decreasing size order at %d", i);
     CHECK(g[1] >= 1 && g[0] >= 0 && g[0] + g[1] <= Q.n_chunks, "group %d chunk range", i);
-    CHECK(g[3] >= 1 && g[3] <= kGroupSlots && g[2] >= 0 && g[2] + g[3] <= Q.n_gslots,
+    const bool lg = g[6] != 0;  // a long track's group: its pieces, one chunk each
+    CHECK(g[3] >= 1 && (lg || g[3] <= kGroupSlots) && g[2] >= 0 && g[2] + g[3] <= Q.n_gslots,
           "group %d slot range (%d slots)", i, g[3]);
     int obs = 0;
     std::set<int> cams;
+    int s = g[2];
     for (int c = g[0]; c < g[0] + g[1]; ++c) {
       CHECK(chunk_group[c] < 0, "chunk %d in two groups", c);
       chunk_group[c] = i;
@@ -158,16 +201,42 @@ int main(int argc, char** argv) {
         cams.insert(S.cam_of[o]);
         CHECK(S.lm_prob[S.lm_of[o]] == g[5], "group %d holds another problem's observation", i);
       }
+      for (int l = d[2]; l < d[2] + d[3]; ++l) {
+        const int j = S.lm_long[l];
+        CHECK(lg == (j >= 0), "group %d: a piece of a long track in a plain group, or the reverse", i);
+        if (lg) {
+          CHECK(d[3] == 1 && l == S.long_first[j] + (c - g[0]) && g[1] == S.long_np[j],
+                "long group %d chunk %d is not piece %d of its track", i, c, c - g[0]);
+        }
+      }
+      if (lg) {
+        // the chunk's slots: its cameras, ascending, from slot base d[7]
+        std::set<int> cc;
+        for (int o = d[0]; o < d[0] + d[1]; ++o) cc.insert(S.cam_of[o]);
+        CHECK(g[2] + d[7] == s, "long group %d chunk %d slot base", i, c);
+        for (int cam : cc) {
+          CHECK(Q.gslot_cam[s] == cam, "long group %d chunk %d slot is not its camera", i, c);
+          CHECK(group_of_slot[s] < 0, "group slot %d shared", s);
+          group_of_slot[s] = i;
+          slot_key[s] = c;
+          ++s;
+        }
+      } else {
+        CHECK(d[7] == 0, "chunk %d of plain group %d has a slot base", c, i);
+      }
     }
     CHECK(obs == g[4], "group %d observation count", i);
-    CHECK((int)cams.size() == g[3], "group %d has %d cameras but %d slots", i, (int)cams.size(), g[3]);
-    int s = g[2];
-    for (int cam : cams) {  // ascending
-      CHECK(Q.gslot_cam[s] == cam, "group %d slot %d is not its %d-th camera", i, s - g[2], s - g[2]);
-      CHECK(group_of_slot[s] < 0, "group slot %d shared", s);
-      group_of_slot[s] = i;
-      ++s;
+    if (!lg) {
+      CHECK((int)cams.size() == g[3], "group %d has %d cameras but %d slots", i, (int)cams.size(), g[3]);
+      for (int cam : cams) {  // ascending
+        CHECK(Q.gslot_cam[s] == cam, "group %d slot %d is not its %d-th camera", i, s - g[2], s - g[2]);
+        CHECK(group_of_slot[s] < 0, "group slot %d shared", s);
+        group_of_slot[s] = i;
+        slot_key[s] = g[0];
+        ++s;
+      }
     }
+    CHECK(s == g[2] + g[3], "group %d slot count", i);
   }
   // chunks in landmark order cover every observation once
   {
@@ -199,7 +268,8 @@ int main(int argc, char** argv) {
         CHECK((code[i] >> 24) == 0, "chunk %d code high bits", c);
         CHECK(pos < n && at[pos] < 0, "chunk %d positions are not a permutation", c);
         at[pos] = i;
-        CHECK(gs < g[3] && Q.gslot_cam[g[2] + gs] == S.cam_of[o0 + i], "chunk %d obs %d group slot", c, i);
+        CHECK(d[7] + gs < g[3] && Q.gslot_cam[g[2] + d[7] + gs] == S.cam_of[o0 + i],
+              "chunk %d obs %d group slot", c, i);
         CHECK(L0 + lm == S.lm_of[o0 + i], "chunk %d obs %d landmark", c, i);
       }
       for (int q = 1; q < n; ++q) {
@@ -229,7 +299,7 @@ int main(int argc, char** argv) {
         int r = -1;
         for (int k = 0; k < ns; ++k)
           if (run_beg[k] == beg) r = k;
-        CHECK(r >= 0 && !used[r] && run_len[r] == len && Q.gslot_cam[g[2] + gs] == run_cam[r],
+        CHECK(r >= 0 && !used[r] && run_len[r] == len && Q.gslot_cam[g[2] + d[7] + gs] == run_cam[r],
               "chunk %d slot %d", c, j);
         used[r] = 1;
       }
@@ -237,7 +307,7 @@ int main(int argc, char** argv) {
     for (int o = next_o; o < no; ++o) CHECK(false, "observation %d is in no chunk", o);
   }
   // balance: groups of a single problem differ by at most one track plus the size split
-  if (P == 1 && Q.n_groups > 1) {
+  if (P == 1 && Q.n_groups > 1 && S.n_long == 0) {
     int big = 0, small = 1 << 30;
     for (int i = 0; i < Q.n_groups; ++i) {
       big = std::max(big, Q.group[8 * (size_t)i + 4]);
@@ -258,8 +328,8 @@ int main(int argc, char** argv) {
       CHECK(r >= 0 && r < Q.n_gslots && !seen_row[r], "gslot_row is not a permutation at %d", s);
       seen_row[r] = 1;
       CHECK(r >= Q.cam_ptr[cam] && r < Q.cam_ptr[cam + 1], "group slot %d's row is not its camera's", s);
-      // landmark order of the group: its first chunk's first landmark
-      row_group[r] = Q.group[8 * (size_t)group_of_slot[s]];
+      // landmark order: the group's first chunk (a long group's slot: its chunk)
+      row_group[r] = slot_key[s];
     }
     for (int cam = 0; cam < nc; ++cam)
       for (int r = Q.cam_ptr[cam] + 1; r < Q.cam_ptr[cam + 1]; ++r)

@@ -59,7 +59,7 @@ def _desc(n_c=3, n_l=4, n_o=6, seed=0):
 
 
 @pytest.mark.parametrize("case", ["bad_cam_index", "bad_lm_index", "zero_cams", "nan_obs",
-                                  "neg_weight", "long_track", "bad_precision"])
+                                  "neg_weight", "bad_precision"])
 def test_create_rejects_bad_inputs_before_touching_the_gpu(lib, case):
     import paper_2204_12834_gb300 as poba
     cams, lms, obs, ci, li = _desc()
@@ -78,11 +78,6 @@ def test_create_rejects_bad_inputs_before_touching_the_gpu(lib, case):
     elif case == "neg_weight":
         w = np.ones(obs.shape[0])
         w[3] = -1.0
-    elif case == "long_track":
-        n = 300
-        obs = np.zeros((n, 2))
-        ci = np.zeros(n, np.int32)
-        li = np.zeros(n, np.int32)
     elif case == "bad_precision":
         prec = 7
     with pytest.raises(poba.PobaError) as e:

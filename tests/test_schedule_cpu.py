@@ -118,3 +118,23 @@ def test_full_size_schedules(checker, tmp_path, workload):
         out = run(checker, tmp_path, [p], grid=grid)
         slots = int(out.split("slots=")[1].split()[0])
     assert bench.schedule_slots(p) == slots
+
+
+@pytest.mark.parametrize("lengths", [(257,), (300, 700, 2000), (512, 513, 256, 1024)])
+def test_schedule_with_long_tracks(checker, tmp_path, lengths):
+    """Tracks of more than 256 observations: split into near-equal pieces of at most 256 (in
+    camera order), each alone in its tile, the pieces of a track forming one series group of
+    one chunk per piece; the other landmarks are scheduled as usual."""
+    p = bal_synth.make_problem(2100, 3000, track=("long", 2, 6, lengths), seed=89)
+    assert sorted(np.bincount(p.lm_idx)[:len(lengths)]) == sorted(lengths)
+    for grid in (456, 40):
+        out = run(checker, tmp_path, [p], grid=grid)
+        assert out.startswith("ok")
+
+
+def test_batch_schedule_with_long_tracks(checker, tmp_path):
+    """A batch whose problems hold long tracks (and one that holds none)."""
+    problems = [bal_synth.make_problem(600, 400, track=("long", 2, 5, (300,)), seed=90),
+                bal_synth.make_problem(40, 300, track=("uniform", 2, 5), seed=91),
+                bal_synth.make_problem(900, 200, track=("long", 2, 5, (800, 260)), seed=92)]
+    run(checker, tmp_path, problems, grid=152)
