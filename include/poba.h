@@ -44,8 +44,10 @@ typedef enum {
   BA_ERR_NOT_SPD = 4,        /* a damped U or V block had a non-positive Cholesky pivot */
   BA_ERR_NONFINITE = 5,      /* non-finite input, residual, cost or step */
   BA_ERR_NOT_LINEARIZED = 6, /* a solve was requested before ba_linearize */
-  BA_ERR_TIMEOUT = 7         /* a bounded device-side wait gave up (a grid barrier of the
+  BA_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up (a grid barrier of the
                                 persistent series kernel waited longer than its limit) */
+  BA_ERR_CHECK = 8           /* debug builds (libpoba_checks.so): a device-side index check or
+                                a buffer guard failed (message in ba_last_error) */
 } ba_status;
 
 typedef enum {
@@ -437,6 +439,19 @@ ba_status ba_set_barrier_timeout(ba_handle* h, int64_t cycles);
  * flops_per_s), BA_ERR_CUDA. */
 ba_status ba_probe_fp64_fma(int32_t blocks_per_sm, int32_t iters, void* cuda_stream,
                             double* flops_per_s, double* ms_out);
+
+/* Debug checks.  The library built with -DPOBA_CHECKS (libpoba_checks.so) checks every camera,
+ * landmark, slot, position and segment index its kernels read from the schedule before using
+ * it (a bad index is recorded and replaced by an in-range one, so the kernel completes; no
+ * trap), and guards every sub-buffer of a handle's device allocations with 256 bytes of 0xA5.
+ * Each call that synchronises the handle's stream verifies both and returns BA_ERR_CHECK on a
+ * failure.  ba_debug_checks verifies them now: *enabled = 1 in that build (0 in the release
+ * build, where the other outputs are 0); *site = the first failed check (0: none; 100 + i: the
+ * guard of sub-buffer i of the main allocation, 1100 + i: of the series schedule's), *count =
+ * failed checks, *index = the offending index (or byte offset).  The record is then cleared.
+ * Any output may be NULL.  Synchronises. */
+ba_status ba_debug_checks(ba_handle* h, int32_t* enabled, uint32_t* site, uint32_t* count,
+                          int64_t* index);
 
 /* Static string for a status code. */
 const char* ba_status_string(ba_status s);

@@ -29,7 +29,7 @@ __all__ = ["PobaError", "Handle", "ba_default_options", "ba_create", "ba_set_opt
            "ba_get_batch_layout", "ba_get_series_state", "ba_lm_step_batch", "ba_lm_solve_batch",
            "ba_cost_batch", "batch_from_problems", "ba_autotune", "ba_adjoint",
            "ba_solve_schur_pcg", "ba_get_schedule", "ba_set_schedule", "ba_set_step_graph",
-           "ba_get_step_graph", "ba_probe_fp64_fma"]
+           "ba_get_step_graph", "ba_probe_fp64_fma", "ba_debug_checks"]
 
 BA_NOALLOC_MAX_CAMS = 4096
 
@@ -360,6 +360,15 @@ def ba_cost_noalloc(cams, lms, obs, cam_idx, lm_idx, cost_out, weights=None, str
         st = int(getattr(stream, "cuda_stream", stream)) or None
     _check(library().ba_cost_noalloc(int(cams.shape[0]), int(lms.shape[0]), int(obs.shape[0]),
                                      *args, st), "ba_cost_noalloc")
+
+
+def ba_debug_checks(h: Handle) -> dict:
+    """The debug build's check record and buffer guards (see poba.h): {"enabled", "site",
+    "count", "index"}; the record is cleared."""
+    e, site, cnt, idx = C.c_int32(), C.c_uint32(), C.c_uint32(), C.c_int64()
+    _check(library().ba_debug_checks(h.ptr, C.byref(e), C.byref(site), C.byref(cnt), C.byref(idx)),
+           "ba_debug_checks")
+    return {"enabled": bool(e.value), "site": site.value, "count": cnt.value, "index": idx.value}
 
 
 def ba_probe_fp64_fma(blocks_per_sm: int = 4, iters: int = 1 << 16, stream=None) -> dict:

@@ -6,11 +6,12 @@ import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libpoba.so")
+CHECKS_LIB_PATH = os.path.join(_PKG, "libpoba_checks.so")
 
 BA_OK = 0
 STATUS_NAMES = {0: "BA_OK", 1: "BA_ERR_INVALID_ARG", 2: "BA_ERR_CUDA", 3: "BA_ERR_OOM",
                 4: "BA_ERR_NOT_SPD", 5: "BA_ERR_NONFINITE", 6: "BA_ERR_NOT_LINEARIZED",
-                7: "BA_ERR_TIMEOUT"}
+                7: "BA_ERR_TIMEOUT", 8: "BA_ERR_CHECK"}
 BA_FP64 = 0
 BA_FP32_BULK = 1
 
@@ -85,6 +86,8 @@ SIGNATURES = {
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_void_p]),
     "ba_set_barrier_timeout": (C.c_int, [C.c_void_p, C.c_int64]),
+    "ba_debug_checks": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_uint32),
+                                  C.POINTER(C.c_uint32), C.POINTER(C.c_int64)]),
     "ba_probe_fp64_fma": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]),
     "ba_get_series_trace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
@@ -118,7 +121,8 @@ def load(path: str | None = None) -> C.CDLL:
     global _lib
     if _lib is not None and path is None:
         return _lib
-    p = path or LIB_PATH
+    # POBA_CHECKS=1 selects the debug build with device-side index checks and buffer guards
+    p = path or (CHECKS_LIB_PATH if os.environ.get("POBA_CHECKS") == "1" else LIB_PATH)
     if not os.path.exists(p):
         raise ImportError(f"libpoba.so not found at {p}; build it with "
                           "`python -m paper_2204_12834_gb300.build` (needs nvcc)")

@@ -16,10 +16,14 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpoba.so")
+# the debug build: device-side index checks and buffer guards (csrc/checks.cuh)
+BUILD_CHECKS = os.path.join(PKG, "_build_checks")
+LIB_CHECKS = os.path.join(PKG, "libpoba_checks.so")
 SOURCES = ["schedule.cpp", "kernels_linearize.cu", "kernels_series.cu", "kernels_persistent.cu",
            "kernels_adjoint.cu", "kernels_pcg.cu",
            "api.cu", "noalloc.cu", "probe.cu"]
 HEADERS = [os.path.join(CSRC, "poba_internal.cuh"), os.path.join(CSRC, "tile_common.cuh"),
+           os.path.join(CSRC, "checks.cuh"),
            os.path.join(CSRC, "jacobian_io.cuh"),
            os.path.join(CSRC, "series_body.cuh"),
            os.path.join(ROOT, "include", "poba.h")]
@@ -42,11 +46,12 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(p) > t for p in [src] + HEADERS)
 
 
-def _compile(src_name: str, extra: list[str], verbose: bool) -> str:
+def _compile(src_name: str, extra: list[str], verbose: bool, build_dir: str = BUILD,
+             defines: list[str] | None = None) -> str:
     src = os.path.join(CSRC, src_name)
-    obj = os.path.join(BUILD, src_name.rsplit(".", 1)[0] + ".o")
+    obj = os.path.join(build_dir, src_name.rsplit(".", 1)[0] + ".o")
     if _stale(obj, src) or extra:
-        cmd = [nvcc(), "-c", src, "-o", obj] + FLAGS + extra
+        cmd = [nvcc(), "-c", src, "-o", obj] + FLAGS + (defines or []) + extra
         if verbose:
             print(" ".join(cmd), flush=True)
         res = subprocess.run(cmd, capture_output=True, text=True)
@@ -57,26 +62,31 @@ def _compile(src_name: str, extra: list[str], verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link libpoba.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          checks: bool = False) -> str:
+    """Compile and link libpoba.so (checks: the debug build libpoba_checks.so, compiled with
+    -DPOBA_CHECKS); returns its path."""
+    build_dir, lib_path = (BUILD_CHECKS, LIB_CHECKS) if checks else (BUILD, LIB)
+    defines = ["-DPOBA_CHECKS"] if checks else []
+    os.makedirs(build_dir, exist_ok=True)
     if force:
-        for f in os.listdir(BUILD):
+        for f in os.listdir(build_dir):
             if f.endswith(".o"):
-                os.remove(os.path.join(BUILD, f))
+                os.remove(os.path.join(build_dir, f))
     extra = ["-Xptxas", "-v"] if ptxas_info else []
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra, verbose), SOURCES))
-    if force or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        tmp = LIB + ".tmp"
-        cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]
+        objs = list(ex.map(lambda s: _compile(s, extra, verbose, build_dir, defines), SOURCES))
+    out = lib_path
+    if force or not os.path.exists(out) or any(os.path.getmtime(o) > os.path.getmtime(out) for o in objs):
+        tmp = out + ".tmp"
+        cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-ldl"]
         if verbose:
             print(" ".join(cmd), flush=True)
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"nvcc link failed:\n{res.stdout}\n{res.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/poba.h"
 #include "poba_internal.cuh"
 
@@ -156,6 +158,11 @@ struct ba_handle {
   SerTopo sp{};
   void* ser_arena = nullptr;
   size_t ser_bytes = 0;
+  CheckRecord* chk = nullptr;  // debug-build check record (main arena)
+  // debug builds: offsets of the guard bytes after each sub-buffer of the main (0) and series (1)
+  // allocations, on the device
+  uint64_t* canary_dev[2] = {nullptr, nullptr};
+  int canary_n[2] = {0, 0};
   FlowState flow{};           // dataflow kernel state (inside ser_arena), zeroed per launch
   void* flow_base = nullptr;
   size_t flow_bytes = 0;
@@ -215,10 +222,67 @@ ba_status copy_out(void* dst, const void* src, size_t bytes, int ptr_kind) {
   return BA_OK;
 }
 
+ba_status debug_verify(ba_handle* h);
+
+// NVTX range over a scope (host side: the calls that launch a kernel class, and each LM
+// iteration), for profilers that filter by range; free when no tool is attached.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+
 ba_status check_launch(ba_handle* h, const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail_cuda(e, what);
-  return BA_OK;
+  return debug_verify(h);
+}
+
+// Debug builds (checks.cuh): guard bytes after each sub-buffer of an allocation.  layout:
+// returns the bytes a sub-buffer of `bytes` takes (its guard included); fill: writes the guard
+// bytes at the given offsets and uploads the offsets for the check kernel.
+size_t guarded(size_t bytes) { return bytes + (kChecks ? kCanaryBytes : 0); }
+
+cudaError_t install_canaries(ba_handle* h, int which, void* base,
+                             const std::vector<uint64_t>& offs) {
+  if (!kChecks) return cudaSuccess;
+  for (uint64_t o : offs) {
+    cudaError_t e = cudaMemset((char*)base + o, kCanaryByte, kCanaryBytes);
+    if (e != cudaSuccess) return e;
+  }
+  if (h->canary_dev[which]) cudaFree(h->canary_dev[which]);
+  h->canary_dev[which] = nullptr;
+  h->canary_n[which] = (int)offs.size();
+  if (offs.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&h->canary_dev[which], sizeof(uint64_t) * offs.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->canary_dev[which], offs.data(), sizeof(uint64_t) * offs.size(),
+                   cudaMemcpyHostToDevice);
+  return e;
+}
+
+// Debug builds: after the handle's stream drains, the guard bytes of both allocations and the
+// device check record; the first failure becomes BA_ERR_CHECK (the record is then cleared, so
+// the handle stays usable).  Release builds, and while a graph is being captured: BA_OK.
+ba_status debug_verify(ba_handle* h) {
+  if (!kChecks || h->capturing || !h->chk) return BA_OK;
+  cudaStream_t s = h->stream;
+  if (h->canary_n[0] > 0)
+    launch_canary_check((const uint8_t*)h->arena, h->canary_dev[0], h->canary_n[0], kChkCanary,
+                        h->chk, s);
+  if (h->canary_n[1] > 0 && h->ser_arena)
+    launch_canary_check((const uint8_t*)h->ser_arena, h->canary_dev[1], h->canary_n[1],
+                        kChkCanary + 1000, h->chk, s);
+  CheckRecord r{};
+  cudaError_t e = cudaMemcpyAsync(&r, h->chk, sizeof(r), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail_cuda(e, "device check record");
+  if (r.site == kChkNone) return BA_OK;
+  cudaMemsetAsync(h->chk, 0, sizeof(CheckRecord), s);
+  return fail(BA_ERR_CHECK, "device check " + std::to_string(r.site) + " failed: index " +
+                                std::to_string(r.index) + " for bound " + std::to_string(r.bound) +
+                                " (" + std::to_string(r.count) + " failed checks)");
 }
 
 // ---- kernel timing --------------------------------------------------------------------
@@ -299,6 +363,7 @@ void collect_timing(ba_handle* h, int terms_run, bool series_ran) {
 int long_kernels(const ba_handle* h) { return h->tp.n_long > 0 ? 1 : 0; }
 
 void seq_linearize(ba_handle* h) {
+  Range range("poba.linearize");
   cudaStream_t s = h->stream;
   tmark(h, kTLin, 0, 0);
   launch_cam_prepare(h->cams, nullptr, h->n_c, h->prep, nullptr, s, h->prep32);
@@ -403,6 +468,7 @@ ba_status seq_series_persistent(ba_handle* h, cudaStream_t s, bool use_active, i
 }
 
 ba_status run_series_body(ba_handle* h, bool use_active) {
+  Range range("poba.series");
   cudaStream_t s = h->stream;
   if (h->timing) {
     ba_status st = ensure_events(h);
@@ -471,6 +537,7 @@ ba_status run_series_body(ba_handle* h, bool use_active) {
 // lambda of problem p at lam_dev[p * lam_stride]; use_active: problems whose LM record is
 // inactive take no part.
 ba_status run_solve(ba_handle* h, const double* lam_dev, int lam_stride, bool use_active) {
+  Range range("poba.solve");
   CK(cudaMemsetAsync(h->not_spd, 0, sizeof(int32_t) * h->n_probs, h->stream));
   if (h->timing) {
     ba_status st = ensure_events(h);
@@ -521,6 +588,8 @@ ba_status ba_destroy(ba_handle* h) {
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   if (h->arena) cudaFree(h->arena);
   if (h->ser_arena) cudaFree(h->ser_arena);
+  for (uint64_t* c : h->canary_dev)
+    if (c) cudaFree(c);
   if (h->grad_out) cudaFree(h->grad_out);
   if (h->pcg) cudaFree(h->pcg);
   if (h->h_st) cudaFreeHost(h->h_st);
@@ -591,7 +660,7 @@ ba_status rebuild_series(ba_handle* h, int group_obs, int tail) {
     items.push_back({(void**)&d_rl[k][2], rl[k].block_round.data(), sizeof(int32_t) * rl[k].block_round.size()});
   }
   size_t total = 0;
-  for (auto& it : items) total = align_up(total, 256) + nz(it.bytes);
+  for (auto& it : items) total = align_up(total, 256) + guarded(nz(it.bytes));
   total = align_up(total, 256);
   void* arena = nullptr;
   cudaError_t e = cudaMalloc(&arena, total);
@@ -600,16 +669,22 @@ ba_status rebuild_series(ba_handle* h, int group_obs, int tail) {
     return fail(BA_ERR_OOM, "cudaMalloc(series schedule) failed");
   }
   size_t off = 0;
+  std::vector<uint64_t> guards;
   for (auto& it : items) {
     off = align_up(off, 256);
     *it.ptr = (char*)arena + off;
     off += nz(it.bytes);
+    if (kChecks) {
+      guards.push_back(off);
+      off += kCanaryBytes;
+    }
   }
   // the old schedule may still be in use by queued work of the handle's stream
   e = cudaStreamSynchronize(h->stream);
   if (e == cudaSuccess) e = cudaMemset(arena, 0, total);
   for (auto& it : items)
     if (e == cudaSuccess && it.src && it.bytes) e = cudaMemcpy(*it.ptr, it.src, it.bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = install_canaries(h, 1, arena, guards);
   if (e != cudaSuccess) {
     cudaFree(arena);
     return fail_cuda(e, "uploading the series schedule");
@@ -875,8 +950,9 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   items.push_back({(void**)&h->not_spd, sizeof(int32_t) * P});
   items.push_back({(void**)&h->io_bad, sizeof(int32_t) * 2});
   items.push_back({(void**)&h->relin, sizeof(int32_t)});
+  items.push_back({(void**)&h->chk, sizeof(CheckRecord)});
   size_t total = 0;
-  for (auto& it : items) total = align_up(total, 256) + it.bytes;
+  for (auto& it : items) total = align_up(total, 256) + guarded(it.bytes);
   total = align_up(total, 256);
 
   auto bail = [&](ba_status s) { ba_destroy(h); return s; };
@@ -891,16 +967,23 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   e = cudaMalloc(&h->arena, total);
   if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMalloc(arena)"));
   h->arena_bytes = total;
+  std::vector<uint64_t> guards;
   {
     size_t off = 0;
     for (auto& it : items) {
       off = align_up(off, 256);
       *it.ptr = (char*)h->arena + off;
       off += it.bytes;
+      if (kChecks) {
+        guards.push_back(off);
+        off += kCanaryBytes;
+      }
     }
   }
   e = cudaMemset(h->arena, 0, total);
   if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMemset(arena)"));
+  e = install_canaries(h, 0, h->arena, guards);
+  if (e != cudaSuccess) return bail(fail_cuda(e, "guard bytes"));
   if ((e = cudaMallocHost(&h->h_st, sizeof(SeriesState) * P)) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_sgl, sizeof(SeriesGlobal))) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_rec, sizeof(LmRecord) * P)) != cudaSuccess ||
@@ -999,6 +1082,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   tp.long_np = d_long ? d_long + S.n_long : nullptr;
   tp.long_tile0 = d_long ? d_long + 2 * S.n_long : nullptr;
   tp.lm_long = d_lm_long;
+  tp.chk = h->chk;
   tp.n_obs = no;
   tp.n_obs_pad = h->n_o_pad;
   tp.n_tiles = S.n_tiles;
@@ -1095,6 +1179,7 @@ ba_status seq_lm_step(ba_handle* h, bool batch, bool gated) {
   }
   ba_status st = run_solve(h, rec_field(h->rec, offsetof(LmRecord, lambda)), kRecStride, true);
   if (st != BA_OK) return st;
+  Range eval_range("poba.evaluate");
   tmark(h, kTEval, 0, 0);
   launch_cam_prepare(h->cams, h->x, h->n_c, h->prep_trial, h->cams_trial, s);
   launch_tile_cost(h->tp, h->prep_trial, h->lms, h->dx_l, h->obs, h->sqrt_w, h->tile_cost, s);
@@ -1179,6 +1264,7 @@ bool capture_lm_step(ba_handle* h, bool batch) {
 // replay of the captured step; otherwise the same kernels launch one by one.  Reads the
 // records and series states back (one synchronisation).
 ba_status lm_iteration(ba_handle* h, bool batch) {
+  Range range(batch ? "poba.lm_iteration_batch" : "poba.lm_iteration");
   cudaStream_t s = h->stream;
   const size_t P = (size_t)h->n_probs;
   if (!h->cost_valid) {
@@ -1214,7 +1300,7 @@ ba_status lm_iteration(ba_handle* h, bool batch) {
   for (size_t p = 0; p < P; ++p)
     if (h->h_rec[p].accepted) h->linearized = false;
   h->relin_synced = graph;  // the captured decision set relin = any step accepted
-  return BA_OK;
+  return debug_verify(h);
 }
 
 // Status of an LM iteration after its records were read: a non-finite cost at the current state
@@ -1323,6 +1409,7 @@ ba_status ba_solve_schur_power(ba_handle* h, double lambda, ba_series_info* info
 }
 
 ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* bps_out) {
+  Range range("poba.autotune");
   if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
   if (trials < 1) return fail(BA_ERR_INVALID_ARG, "trials must be >= 1");
   if (!h->linearized) {
@@ -1490,6 +1577,7 @@ ba_status ba_set_schedule(ba_handle* h, const ba_schedule* in) {
 
 ba_status ba_adjoint(ba_handle* h, double lambda, const double* g_cams, const double* g_lms,
                      double* d_obs, double* d_weights, int32_t ptr_kind, ba_series_info* info) {
+  Range range("poba.adjoint");
   if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
   if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(BA_ERR_INVALID_ARG, "lambda must be finite and > 0");
   if (!g_cams || !g_lms || !d_obs) return fail(BA_ERR_INVALID_ARG, "g_cams / g_lms / d_obs is NULL");
@@ -1743,6 +1831,7 @@ extern "C" {
 
 ba_status ba_solve_schur_pcg(ba_handle* h, double lambda, int32_t precond, int32_t m_precond,
                              double rtol, int32_t max_iter, ba_pcg_info* info) {
+  Range range("poba.pcg");
   if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
   if (!h->linearized) return fail(BA_ERR_NOT_LINEARIZED, "ba_linearize has not been called");
   if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(BA_ERR_INVALID_ARG, "lambda must be finite and > 0");
@@ -1826,6 +1915,7 @@ ba_status ba_lm_solve_batch(ba_handle* h, ba_step_info* infos, int32_t* n_steps)
 }
 
 ba_status ba_cost(ba_handle* h, double* cost_out) {
+  Range range("poba.cost");
   if (!h || !cost_out) return fail(BA_ERR_INVALID_ARG, "NULL argument");
   launch_cam_prepare(h->cams, nullptr, h->n_c, h->prep, nullptr, h->stream);
   launch_tile_cost(h->tp, h->prep, h->lms, nullptr, h->obs, h->sqrt_w, h->tile_cost, h->stream);
@@ -2082,6 +2172,31 @@ ba_status ba_get_timing(ba_handle* h, ba_timing* out) {
   return BA_OK;
 }
 
+ba_status ba_debug_checks(ba_handle* h, int32_t* enabled, uint32_t* site, uint32_t* count,
+                          int64_t* index) {
+  if (!h) return fail(BA_ERR_INVALID_ARG, "handle is NULL");
+  if (enabled) *enabled = kChecks ? 1 : 0;
+  if (site) *site = 0;
+  if (count) *count = 0;
+  if (index) *index = 0;
+  if (!kChecks) return BA_OK;
+  cudaStream_t s = h->stream;
+  if (h->canary_n[0] > 0)
+    launch_canary_check((const uint8_t*)h->arena, h->canary_dev[0], h->canary_n[0], kChkCanary,
+                        h->chk, s);
+  if (h->canary_n[1] > 0 && h->ser_arena)
+    launch_canary_check((const uint8_t*)h->ser_arena, h->canary_dev[1], h->canary_n[1],
+                        kChkCanary + 1000, h->chk, s);
+  CheckRecord r{};
+  CK(cudaMemcpyAsync(&r, h->chk, sizeof(r), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaMemsetAsync(h->chk, 0, sizeof(CheckRecord), s));
+  if (site) *site = r.site;
+  if (count) *count = r.count;
+  if (index) *index = r.index;
+  return BA_OK;
+}
+
 const char* ba_status_string(ba_status s) {
   switch (s) {
     case BA_OK: return "BA_OK";
@@ -2092,6 +2207,7 @@ const char* ba_status_string(ba_status s) {
     case BA_ERR_NONFINITE: return "BA_ERR_NONFINITE";
     case BA_ERR_NOT_LINEARIZED: return "BA_ERR_NOT_LINEARIZED";
     case BA_ERR_TIMEOUT: return "BA_ERR_TIMEOUT";
+    case BA_ERR_CHECK: return "BA_ERR_CHECK";
   }
   return "unknown status";
 }

@@ -195,8 +195,11 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
   const int o0 = tp.lm_seg[L0], n = tp.lm_seg[L1] - o0;
   const int S0 = tp.tile_slot0[tile], ns = tp.tile_slot0[tile + 1] - S0;
   for (int i = tid; i < ns; i += blockDim.x) {
-    sbeg[i] = tp.slot_beg[S0 + i];
-    srow[i] = tp.slot_row[S0 + i];
+    int bg = tp.slot_beg[S0 + i], rw = tp.slot_row[S0 + i];
+    POBA_CHK(tp.chk, bg, n, kChkLinSeg);
+    POBA_CHK(tp.chk, rw, tp.n_slots, kChkLinRow);
+    sbeg[i] = (uint16_t)bg;
+    srow[i] = rw;
   }
 
   T jp[18], jl[6], rr[2];
@@ -205,8 +208,15 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
   const bool active = tid < n;
   if (active) {
     const int o = o0 + tid;
-    const int c = tp.cam_of[o], l = tp.lm_of[o];
+    int c = tp.cam_of[o], l = tp.lm_of[o];
+    POBA_CHK(tp.chk, c, tp.n_cams, kChkLinCam);
+    POBA_CHK(tp.chk, l, tp.n_lms, kChkLinLm);
     pos = tp.obs_meta[o] & 0xff;
+    POBA_CHK(tp.chk, pos, n, kChkLinPos);
+    if (kChecks) {
+      int sl = tp.obs_meta[o] >> 8;
+      POBA_CHK(tp.chk, sl, ns, kChkLinSlot);
+    }
     const T sw = kWeighted ? sqrt_w[o] : (T)1;
     bal_residual_jacobian<T>(prep + (size_t)c * kCamPrep, lms[l * 3 + 0], lms[l * 3 + 1],
                              lms[l * 3 + 2], obs[o], sw, jp, jl, rr);
@@ -301,7 +311,12 @@ __global__ void lin_camera_reduce_kernel(Topology tp, const PT* __restrict__ par
   const int k = threadIdx.x % per;
   if (c >= tp.n_cams || (gate && *gate == 0)) return;
   // the camera's slot rows are contiguous (camera-major)
-  const int r0 = tp.cam_slot_ptr[c], r1 = tp.cam_slot_ptr[c + 1];
+  int r0 = tp.cam_slot_ptr[c], r1 = tp.cam_slot_ptr[c + 1];
+  if (kChecks && (r0 < 0 || r1 < r0 || r1 > tp.n_slots)) {
+    int bad = r1 > tp.n_slots ? r1 : r0;
+    POBA_CHK(tp.chk, bad, 0, kChkCamReduce);
+    r0 = r1 = 0;
+  }
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
   int r = r0;
   for (; r + 4 <= r1; r += 4) {
@@ -511,7 +526,9 @@ __global__ void __launch_bounds__(kTileObs) tile_cost_kernel(
   double e = 0.0;
   if ((int)threadIdx.x < n) {
     const int o = o0 + threadIdx.x;
-    const int c = tp.cam_of[o], l = tp.lm_of[o];
+    int c = tp.cam_of[o], l = tp.lm_of[o];
+    POBA_CHK(tp.chk, c, tp.n_cams, kChkCostCam);
+    POBA_CHK(tp.chk, l, tp.n_lms, kChkCostLm);
     const double* q = prep + (size_t)c * kCamPrep;
     double X0 = lms[l * 3 + 0], X1 = lms[l * 3 + 1], X2 = lms[l * 3 + 2];
     if (dx_l) {

@@ -111,7 +111,8 @@ struct RoundCache {  // in shared memory
 };
 
 __device__ __forceinline__ void round_cache(const Topology& tp, const CamRounds& cr,
-                                            const double* __restrict__ x, RoundCache& rc) {
+                                            const double* __restrict__ x, RoundCache& rc,
+                                            int n_rows) {
   const int it = threadIdx.x / 9, k = threadIdx.x - it * 9;
   const int rd = cr.block_round[blockIdx.x] < cr.block_round[blockIdx.x + 1]
                      ? cr.block_round[blockIdx.x] : -1;
@@ -123,7 +124,11 @@ __device__ __forceinline__ void round_cache(const Topology& tp, const CamRounds&
       rc.nc = nc;
       rc.ni = ni;
     }
-    if (it < ni && k < 2) rc.q[it][k] = cr.item_q[2 * (i0 + it) + k];
+    if (it < ni && k < 2) {
+      int q = cr.item_q[2 * (i0 + it) + k];
+      POBA_CHK(tp.chk, q, n_rows + 1, kChkCamRows);
+      rc.q[it][k] = q;
+    }
     if (it < nc) {
       const int c = c0 + it;
       if (k == 0) rc.cam[it][0] = c;
@@ -178,7 +183,7 @@ __device__ __forceinline__ double round_finish(bool cam, bool run, int c, int ia
 }
 
 template <typename T>
-__device__ __forceinline__ void camera_phase(const Topology& tp, const CamRounds& cr,
+__device__ __forceinline__ void camera_phase(const Topology& tp, const CamRounds& cr, int n_rows,
                                              RoundCache& rc, const T* __restrict__ partial,
                                              const double* __restrict__ Uinv,
                                              double* __restrict__ x, T* __restrict__ t_cam,
@@ -222,7 +227,9 @@ __device__ __forceinline__ void camera_phase(const Topology& tp, const CamRounds
       done = ld_volatile(&st[tp.cam_prob[c]].done);
     }
     if (it < ni) {
-      const int q0 = cr.item_q[2 * (i0 + it)], q1 = cr.item_q[2 * (i0 + it) + 1];
+      int q0 = cr.item_q[2 * (i0 + it)], q1 = cr.item_q[2 * (i0 + it) + 1];
+      POBA_CHK(tp.chk, q0, n_rows + 1, kChkCamRows);
+      POBA_CHK(tp.chk, q1, n_rows + 1, kChkCamRows);
       pc[it][k] = cam_chunk_sum(partial, q0, q1, k);
     }
     __syncthreads();
@@ -295,7 +302,7 @@ __global__ void __launch_bounds__(kChunkObs, sizeof(T) == 4 ? 4 : 3) series_pers
   __syncthreads();
   if (s_done) return;
   __shared__ RoundCache rc;
-  round_cache(tp, cr, x, rc);
+  round_cache(tp, cr, x, rc, sp.n_gslots);
   const bool tracer = blockIdx.x == 0 && tid == 0 && trace != nullptr;
   for (int i = 1; i <= m_max; ++i) {
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 0] = global_ns();
@@ -321,7 +328,7 @@ __global__ void __launch_bounds__(kChunkObs, sizeof(T) == 4 ? 4 : 3) series_pers
     __syncthreads();
     if (s_done) break;  // every problem's rule fired at term i - 1 or earlier
     // ---- phase B: cameras
-    camera_phase<T>(tp, cr, rc, partial, Uinv, x, t_cam, cam_norm, st, scratch);
+    camera_phase<T>(tp, cr, sp.n_gslots, rc, partial, Uinv, x, t_cam, cam_norm, st, scratch);
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 3] = global_ns();
     if (!term_end_barrier(tp, gs, cam_norm, st, sgl, i, eps, timeout, &s_last, &s_gen, &s_ok,
                           &s_running, scratch))
@@ -389,7 +396,8 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // cameras at a time, thread (camera, k) as in camera_body; each pass publishes its cameras'
 // epochs.  norm_out: the term's norm pairs.
 template <typename T>
-__device__ __forceinline__ void flow_cameras(const SerTopo& sp, const int* own, int n_own, int i,
+__device__ __forceinline__ void flow_cameras(const Topology& tp, const SerTopo& sp, const int* own,
+                                             int n_own, int i,
                                              int* cam_epoch, const T* __restrict__ partial,
                                              const double* __restrict__ Uinv,
                                              double* __restrict__ x, T* __restrict__ t_cam,
@@ -405,7 +413,9 @@ __device__ __forceinline__ void flow_cameras(const SerTopo& sp, const int* own, 
       c = own[base + cl];
       prefetch_uinv_row(Uinv, c, k);
       xo = __ldcg(x + (size_t)c * 9 + k);
-      const int r0 = __ldg(sp.cam_ptr + c), r1 = __ldg(sp.cam_ptr + c + 1);
+      int r0 = __ldg(sp.cam_ptr + c), r1 = __ldg(sp.cam_ptr + c + 1);
+      POBA_CHK(tp.chk, r0, sp.n_gslots + 1, kChkCamRows);
+      POBA_CHK(tp.chk, r1, sp.n_gslots + 1, kChkCamRows);
       const int C = cam_chunk_rows(r1 - r0);
       for (int q0 = r0; q0 < r1; q0 += C) y += cam_chunk_sum(partial, q0, min(q0 + C, r1), k);
       ys[cl][k] = y;
@@ -522,7 +532,7 @@ __global__ void __launch_bounds__(kChunkObs, sizeof(T) == 4 ? 4 : 3) series_data
       if (run < 0) return;
       double* norm_out = (i & 1) ? fs.cam_norm_b : cam_norm;
       if (run) {
-        flow_cameras<T>(sp, s_own, n_own, i, fs.cam_epoch, partial, Uinv, x, t_cam, norm_out,
+        flow_cameras<T>(tp, sp, s_own, n_own, i, fs.cam_epoch, partial, Uinv, x, t_cam, norm_out,
                         scratch);
       } else if (tid == 0) {
         for (int j = 0; j < n_own; ++j) st_release(fs.cam_epoch + s_own[j], i);
@@ -691,8 +701,9 @@ __device__ __forceinline__ void f32_issue(F32Stage& S, const SerTopo& sp, const 
 }
 
 // The inputs of an active thread from the staged chunk.
-__device__ __forceinline__ void f32_load_staged(const F32Stage& S, const int4& d0,
-                                                const ChunkRecLayout& L, F32Obs& x) {
+__device__ __forceinline__ void f32_load_staged(const Topology& tp, const F32Stage& S,
+                                                const int4& d0, const ChunkRecLayout& L, F32Obs& x,
+                                                int gns) {
   const int tid = threadIdx.x;
   float all[24];
 #pragma unroll
@@ -701,11 +712,12 @@ __device__ __forceinline__ void f32_load_staged(const F32Stage& S, const int4& d
   for (int p = 0; p < 18; ++p) x.jp[p] = all[p];
 #pragma unroll
   for (int p = 0; p < 6; ++p) x.jl[p] = all[18 + p];
-  x.code = reinterpret_cast<const uint32_t*>(S.rec + L.code)[tid];
+  x.code = chk_code(tp, reinterpret_cast<const uint32_t*>(S.rec + L.code)[tid], d0.y, d0.w, gns);
   const int lm = (int)(x.code >> 16) & 0xff;
   const uint16_t* sseg = reinterpret_cast<const uint16_t*>(S.rec + L.sseg);
   x.a = sseg[lm];
   x.b = sseg[lm + 1];
+  chk_seg(tp, x.a, x.b, d0.y);
   f32_vinv(x, S.vi + (((size_t)d0.z * 6) & 3) + (size_t)lm * 6);
 }
 
@@ -785,7 +797,8 @@ __device__ __forceinline__ bool groups_staged(const Topology& tp, const SerTopo&
     for (int i = tid; i < ns_g * 3; i += kChunkObs) {
       const int s = i / 3, q = i - 3 * s;
       sm.g.acc[s][q] = make_float4(0.f, 0.f, 0.f, 0.f);
-      const int cam = __ldg(sp.gslot_cam + s0 + s);
+      int cam = __ldg(sp.gslot_cam + s0 + s);
+      POBA_CHK(tp.chk, cam, tp.n_cams, kChkSerCam);
       sm.g.tc[s][q] = __ldcg(reinterpret_cast<const float4*>(t_cam + (size_t)cam * kTStride) + q);
     }
     __syncthreads();
@@ -798,9 +811,12 @@ __device__ __forceinline__ bool groups_staged(const Topology& tp, const SerTopo&
       const ChunkRecLayout L = chunk_rec_layout(n, d0.w, ns);
       const bool active = tid < n;
       F32Obs x;
-      if (active) f32_load_staged(sm.s, d0, L, x);
+      const int gns = ns_g;
+      if (active) f32_load_staged(tp, sm.s, d0, L, x, gns);
       else f32_clear(x);
-      x.cl = tid < ns ? reinterpret_cast<const uint32_t*>(sm.s.rec + L.clist)[tid] : 0u;
+      x.cl = tid < ns ? chk_clist(tp, reinterpret_cast<const uint32_t*>(sm.s.rec + L.clist)[tid], n,
+                                  gns)
+                      : 0u;
       bool issued = false;
       const bool all_ok = chunk_f32_core<kModeSeries>(x, active, n, ns, c & 1, 0.f, 0.f, 0.f, ok,
                                                       sm.g, [&] {
@@ -820,8 +836,9 @@ __device__ __forceinline__ bool groups_staged(const Topology& tp, const SerTopo&
     __syncthreads();
     for (int i = tid; i < ns_g * 9; i += kChunkObs) {
       const int s = i / 9, k = i - 9 * s;
-      partial[(size_t)__ldg(sp.gslot_row + s0 + s) * 9 + k] =
-          reinterpret_cast<const float*>(sm.g.acc[s])[k];
+      int row = __ldg(sp.gslot_row + s0 + s);
+      POBA_CHK(tp.chk, row, sp.n_gslots, kChkSerRow);
+      partial[(size_t)row * 9 + k] = reinterpret_cast<const float*>(sm.g.acc[s])[k];
     }
     if (tid == kIssuer) {
       // the next group: the oldest one the walk claimed (its first chunk is in flight)
@@ -856,7 +873,7 @@ __global__ void __launch_bounds__(kChunkObs, 3) series_staged_kernel(
   __syncthreads();
   if (s_done) return;
   __shared__ RoundCache rc;
-  round_cache(tp, cr, x, rc);
+  round_cache(tp, cr, x, rc, sp.n_gslots);
   unsigned par = 0u;  // parity of the stage's next mbarrier phase
   const bool tracer = blockIdx.x == 0 && tid == 0 && trace != nullptr;
   for (int i = 1; i <= m_max; ++i) {
@@ -871,7 +888,7 @@ __global__ void __launch_bounds__(kChunkObs, 3) series_staged_kernel(
     if (tid == 0) s_done = ld_volatile(&sgl->all_done);
     __syncthreads();
     if (s_done) break;
-    camera_phase<float>(tp, cr, rc, partial, Uinv, x, t_cam, cam_norm, st, scratch);
+    camera_phase<float>(tp, cr, sp.n_gslots, rc, partial, Uinv, x, t_cam, cam_norm, st, scratch);
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 3] = global_ns();
     if (!term_end_barrier(tp, gs, cam_norm, st, sgl, i, eps, timeout, &s_last, &s_gen, &s_ok,
                           &s_running, scratch))

@@ -77,7 +77,9 @@ __global__ void __launch_bounds__(kTileObs) tile_backsub_kernel(
   if (tp.n_long > 0 && tp.lm_long[L0] >= 0) return;  // a piece of a long track (below)
   for (int i = tid; i < ns * 9; i += blockDim.x) {
     const int s = i / 9, k = i - s * 9;
-    tcam[s][k] = (T)x[(size_t)tp.slot_cam[S0 + s] * 9 + k];
+    int c = tp.slot_cam[S0 + s];
+    POBA_CHK(tp.chk, c, tp.n_cams, kChkBackCam);
+    tcam[s][k] = (T)x[(size_t)c * 9 + k];
   }
   __syncthreads();
   const bool active = tid < n;
@@ -88,7 +90,9 @@ __global__ void __launch_bounds__(kTileObs) tile_backsub_kernel(
     const int o = o0 + tid;
     const int meta = tp.obs_meta[o];
     load_J(J, pad, o, jp, jl);
-    const T* tc = tcam[meta >> 8];
+    int sl = meta >> 8;
+    POBA_CHK(tp.chk, sl, ns, kChkBackSlot);
+    const T* tc = tcam[sl];
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
       u0 += jp[j] * tc[j];
@@ -100,7 +104,12 @@ __global__ void __launch_bounds__(kTileObs) tile_backsub_kernel(
   __syncthreads();
   if (tid < L1 - L0) {
     const int l = L0 + tid;
-    const int a = tp.lm_seg[l] - o0, b = tp.lm_seg[l + 1] - o0;
+    int a = tp.lm_seg[l] - o0, b = tp.lm_seg[l + 1] - o0;
+    if (kChecks && (a < 0 || b < a || b > n)) {
+      int bad = b > n ? b : a;
+      POBA_CHK(tp.chk, bad, 0, kChkBackSeg);
+      a = b = 0;
+    }
     T s[3] = {(T)b_l[(size_t)l * 3 + 0], (T)b_l[(size_t)l * 3 + 1], (T)b_l[(size_t)l * 3 + 2]};
     for (int q = a; q < b; ++q) {
       s[0] += sv[q][0];
@@ -163,7 +172,9 @@ __global__ void __launch_bounds__(kTileObs) long_backsub_kernel(
   };
   double S0 = 0.0, S1 = 0.0, S2 = 0.0;
   for (int q = 0; q < np; ++q) {
-    const int o0 = tp.lm_seg[l0 + q], n = tp.lm_seg[l0 + q + 1] - o0;
+    const int o0 = tp.lm_seg[l0 + q];
+    int n = tp.lm_seg[l0 + q + 1] - o0;
+    POBA_CHK(tp.chk, n, kTileObs + 1, kChkLongSeg);
     double v0 = 0.0, v1 = 0.0, v2 = 0.0;
     if (tid < n) {
       T jp[18], jl[6], u0, u1;
@@ -215,6 +226,29 @@ __global__ void __launch_bounds__(kTileObs) long_backsub_kernel(
     if (tid == 0) block_pred[t0 + q] = tot;
     __syncthreads();
   }
+}
+
+// Debug builds: guard bytes after the sub-buffers of an allocation (block i checks the
+// kCanaryBytes bytes at offset off[i]); a changed byte records site site0 + i.
+__global__ void __launch_bounds__(kCanaryBytes) canary_check_kernel(
+    const uint8_t* __restrict__ base, const uint64_t* __restrict__ off, int n, unsigned site0,
+    CheckRecord* chk) {
+  const int i = blockIdx.x;
+  if (i >= n) return;
+  const uint64_t at = off[i] + threadIdx.x;
+  const unsigned char v = base[at];
+  if (v != kCanaryByte) {
+    if (atomicCAS(&chk->site, 0u, site0 + (unsigned)i) == 0u) {
+      chk->index = (long long)at;
+      chk->bound = (long long)v;
+    }
+    atomicAdd(&chk->count, 1u);
+  }
+}
+
+void launch_canary_check(const uint8_t* base, const uint64_t* off, int n, unsigned site0,
+                         CheckRecord* chk, cudaStream_t s) {
+  if (n > 0) canary_check_kernel<<<n, kCanaryBytes, 0, s>>>(base, off, n, site0, chk);
 }
 
 template <typename T>

@@ -34,6 +34,8 @@
 
 #include <cuda_runtime.h>
 
+#include "checks.cuh"
+
 namespace poba {
 
 constexpr int kTileObs = 256;   // observations per tile (= threads of the tile kernels)
@@ -237,6 +239,7 @@ struct Topology {
   const int32_t* long_np;
   const int32_t* long_tile0;
   const int32_t* lm_long;
+  CheckRecord* chk;  // debug-build index checks (checks.cuh)
   // independent problems (P = 1 for a single problem)
   int n_probs;
   const int32_t* cam_prob;  // [n_cams]
@@ -355,6 +358,9 @@ void launch_lin_camera_reduce(const Topology& tp, const PT* partial, double* U45
 // lambda of problem p is lam[p * lam_stride] (lam_stride 0: one lambda for all problems);
 // not_spd[p] is set to 1 when a damped block of problem p fails its Cholesky factorisation (the
 // failed pivot is replaced by 1 so that the inverse stays finite).
+// Debug builds: guard bytes of an allocation (checks.cuh).
+void launch_canary_check(const uint8_t* base, const uint64_t* off, int n, unsigned site0,
+                         CheckRecord* chk, cudaStream_t s);
 // Long tracks: V and b_l summed over each track's pieces and written back to every piece.
 void launch_long_track_blocks(const Topology& tp, double* V, double* b_l, cudaStream_t s,
                               const int32_t* gate = nullptr);

@@ -437,8 +437,13 @@ std::string build_series_schedule(const Schedule& S, int target, int tail, SerSc
   std::stable_sort(ord.begin(), ord.end(),
                    [&](int32_t x, int32_t y) { return gnat[8 * x + 4] > gnat[8 * y + 4]; });
   Q->group.assign((size_t)n_groups * 8, 0);
-  for (int i = 0; i < n_groups; ++i)
+  std::vector<int32_t> ticket(n_groups);
+  for (int i = 0; i < n_groups; ++i) {
     std::memcpy(&Q->group[(size_t)i * 8], &gnat[(size_t)ord[i] * 8], 8 * sizeof(int32_t));
+    ticket[ord[i]] = i;
+  }
+  // each chunk names its group by ticket
+  for (int c = 0; c < Q->n_chunks; ++c) Q->chunk[(size_t)c * 8 + 6] = ticket[Q->chunk[(size_t)c * 8 + 6]];
   return "";
 }
 

@@ -117,6 +117,41 @@ __device__ __forceinline__ void sum_lane(const SumPlan& P, int idx, int& item, i
 // direct loads from global memory (f32_load_direct), or from a copy of the chunk staged in
 // shared memory by bulk asynchronous copies issued one chunk ahead (f32_load_staged).
 
+// Debug builds (checks.cuh): a chunk's indices against their bounds -- an observation code
+// (position < n, group slot < gns, the group's slots, landmark < nl), a chunk slot entry (group slot,
+// rows [beg, beg + len) within the chunk) and a landmark segment [a, b) -- with out-of-range
+// fields replaced by in-range ones.  Release builds return the values unchanged.
+__device__ __forceinline__ uint32_t chk_code(const Topology& tp, uint32_t code, int n, int nl,
+                                             int gns) {
+  if (!kChecks) return code;
+  int pos = (int)(code & 0xff), gs = (int)((code >> 8) & 0xff), lm = (int)((code >> 16) & 0xff);
+  POBA_CHK(tp.chk, pos, n, kChkChunkPos);
+  POBA_CHK(tp.chk, gs, gns, kChkChunkSlot);
+  POBA_CHK(tp.chk, lm, nl, kChkChunkLm);
+  return (uint32_t)pos | ((uint32_t)gs << 8) | ((uint32_t)lm << 16);
+}
+__device__ __forceinline__ uint32_t chk_clist(const Topology& tp, uint32_t e, int n, int gns) {
+  if (!kChecks) return e;
+  int gs = (int)(e & 0xff), beg = (int)((e >> 8) & 0xff), len = (int)(e >> 16);
+  POBA_CHK(tp.chk, gs, gns, kChkClistSlot);
+  if (len < 1 || beg + len > n) {
+    int bad = beg + len;
+    POBA_CHK(tp.chk, bad, 0, kChkClistSeg);
+    beg = 0;
+    len = 0;
+  }
+  return (uint32_t)gs | ((uint32_t)beg << 8) | ((uint32_t)len << 16);
+}
+__device__ __forceinline__ void chk_seg(const Topology& tp, int& a, int& b, int n) {
+  if (!kChecks) return;
+  if (a < 0 || b < a || b > n) {
+    int bad = b > n ? b : a;
+    POBA_CHK(tp.chk, bad, 0, kChkChunkSeg);
+    a = 0;
+    b = 0;
+  }
+}
+
 // One observation thread's inputs.
 struct F32Obs {
   float jp[18], jl[6], vi[6];
@@ -167,14 +202,17 @@ __device__ __forceinline__ void f32_load_direct(const Topology& tp, const int4& 
                                                 const uint8_t* __restrict__ rec,
                                                 const ChunkRecLayout& L,
                                                 const float* __restrict__ J,
-                                                const float* __restrict__ Vinv, F32Obs& x) {
+                                                const float* __restrict__ Vinv, F32Obs& x,
+                                                int gns = 0) {
   const int tid = threadIdx.x;
   load_J(J, (size_t)tp.n_obs_pad, d0.x + tid, x.jp, x.jl);
-  x.code = __ldg(reinterpret_cast<const uint32_t*>(rec + L.code) + tid);
+  x.code = chk_code(tp, __ldg(reinterpret_cast<const uint32_t*>(rec + L.code) + tid), d0.y, d0.w,
+                    gns);
   const int lm = (int)(x.code >> 16) & 0xff;
   const uint16_t* sseg = reinterpret_cast<const uint16_t*>(rec + L.sseg);
   x.a = __ldg(sseg + lm);
   x.b = __ldg(sseg + lm + 1);
+  chk_seg(tp, x.a, x.b, d0.y);
   const float2* v2 = reinterpret_cast<const float2*>(Vinv + (size_t)(d0.z + lm) * 6);
   const float2 x0 = __ldg(v2), x1 = __ldg(v2 + 1), x2 = __ldg(v2 + 2);
   x.vi[0] = x0.x; x.vi[1] = x0.y; x.vi[2] = x1.x; x.vi[3] = x1.y; x.vi[4] = x2.x; x.vi[5] = x2.y;
@@ -330,7 +368,8 @@ template <int MODE>
 __device__ __forceinline__ void chunk_f32(const Topology& tp, const SerTopo& sp, int c,
                                           const float* __restrict__ J,
                                           const double* __restrict__ b_l,
-                                          const float* __restrict__ Vinv, GroupSmem<float>& sm) {
+                                          const float* __restrict__ Vinv, GroupSmem<float>& sm,
+                                          int gns) {
   const int4 d0 = __ldg(sp.chunk + 2 * c), d1 = __ldg(sp.chunk + 2 * c + 1);
   const int n = d0.y, ns = d1.x;
   const uint8_t* rec = sp.rec + (size_t)d1.y * 16;
@@ -339,9 +378,12 @@ __device__ __forceinline__ void chunk_f32(const Topology& tp, const SerTopo& sp,
   F32Obs x;
   float s0 = 0.f, s1 = 0.f, s2 = 0.f;
   const uint32_t cl =
-      threadIdx.x < ns ? __ldg(reinterpret_cast<const uint32_t*>(rec + L.clist) + threadIdx.x) : 0u;
+      threadIdx.x < ns
+          ? chk_clist(tp, __ldg(reinterpret_cast<const uint32_t*>(rec + L.clist) + threadIdx.x), n,
+                      gns)
+          : 0u;
   if (active) {
-    f32_load_direct(tp, d0, rec, L, J, Vinv, x);
+    f32_load_direct(tp, d0, rec, L, J, Vinv, x, gns);
     if (MODE == kModeRhs) {
       const double* bl = b_l + (size_t)(d0.z + ((x.code >> 16) & 0xff)) * 3;
       s0 = (float)__ldg(bl);
@@ -364,7 +406,8 @@ template <int MODE>
 __device__ __forceinline__ void chunk_f64(const Topology& tp, const SerTopo& sp, int c,
                                           const double* __restrict__ J,
                                           const double* __restrict__ b_l,
-                                          const double* __restrict__ Vinv, GroupSmem<double>& sm) {
+                                          const double* __restrict__ Vinv, GroupSmem<double>& sm,
+                                          int gns) {
   const int tid = threadIdx.x;
   const int4 d0 = __ldg(sp.chunk + 2 * c), d1 = __ldg(sp.chunk + 2 * c + 1);
   const int o0 = d0.x, n = d0.y, L0 = d0.z, nl = d0.w, ns = d1.x;
@@ -376,7 +419,7 @@ __device__ __forceinline__ void chunk_f64(const Topology& tp, const SerTopo& sp,
   uint32_t code = 0;
   if (active) {
     load_J(J, (size_t)tp.n_obs_pad, o0 + tid, jp, jl);
-    code = __ldg(reinterpret_cast<const uint32_t*>(rec + L.code) + tid);
+    code = chk_code(tp, __ldg(reinterpret_cast<const uint32_t*>(rec + L.code) + tid), n, nl, gns);
   }
   double vi[6], sl[3] = {0.0, 0.0, 0.0};
   int a = 0, b = 0;
@@ -384,6 +427,7 @@ __device__ __forceinline__ void chunk_f64(const Topology& tp, const SerTopo& sp,
     const uint16_t* sseg = reinterpret_cast<const uint16_t*>(rec + L.sseg);
     a = __ldg(sseg + tid);
     b = __ldg(sseg + tid + 1);
+    chk_seg(tp, a, b, n);
     const double2* v2 = reinterpret_cast<const double2*>(Vinv + (size_t)(L0 + tid) * 6);
     const double2 x0 = __ldg(v2), x1 = __ldg(v2 + 1), x2 = __ldg(v2 + 2);
     vi[0] = x0.x; vi[1] = x0.y; vi[2] = x1.x; vi[3] = x1.y; vi[4] = x2.x; vi[5] = x2.y;
@@ -452,7 +496,7 @@ __device__ __forceinline__ void chunk_f64(const Topology& tp, const SerTopo& sp,
     if (act) {
       const int j = item / 9;
       k = item - 9 * j;
-      const uint32_t e = __ldg(clist + j);
+      const uint32_t e = chk_clist(tp, __ldg(clist + j), n, gns);
       gs = (int)(e & 0xff);
       const int beg = (int)(e >> 8) & 0xff, end = beg + (int)(e >> 16);
       for (int r = beg + part; r < end; r += split) s += sgd[r * 10 + k];
@@ -590,7 +634,8 @@ __device__ __forceinline__ void group_body(const Topology& tp, const SerTopo& sp
     if constexpr (sizeof(T) == 4) {
       sm.acc[s][q] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (MODE == kModeSeries) {
-        const int cam = __ldg(sp.gslot_cam + s0 + s);
+        int cam = __ldg(sp.gslot_cam + s0 + s);
+        POBA_CHK(tp.chk, cam, tp.n_cams, kChkSerCam);
         sm.tc[s][q] = __ldcg(reinterpret_cast<const float4*>(t_cam + (size_t)cam * kTStride) + q);
       }
     } else {
@@ -601,7 +646,8 @@ __device__ __forceinline__ void group_body(const Topology& tp, const SerTopo& sp
         sm.acc[s][8] = 0.0;
       }
       if (MODE == kModeSeries) {
-        const int cam = __ldg(sp.gslot_cam + s0 + s);
+        int cam = __ldg(sp.gslot_cam + s0 + s);
+        POBA_CHK(tp.chk, cam, tp.n_cams, kChkSerCam);
         const double* src = t_cam + (size_t)cam * kTStride;
         sm.tc[s][q] = q < 4 ? __ldcg(reinterpret_cast<const double2*>(src) + q)
                             : make_double2(__ldcg(src + 8), 0.0);
@@ -610,14 +656,15 @@ __device__ __forceinline__ void group_body(const Topology& tp, const SerTopo& sp
   }
   __syncthreads();
   if constexpr (sizeof(T) == 4) {
-    for (int c = c0; c < c0 + nc; ++c) chunk_f32<MODE>(tp, sp, c, J, b_l, Vinv, sm);
+    for (int c = c0; c < c0 + nc; ++c) chunk_f32<MODE>(tp, sp, c, J, b_l, Vinv, sm, ns);
   } else {
-    for (int c = c0; c < c0 + nc; ++c) chunk_f64<MODE>(tp, sp, c, J, b_l, Vinv, sm);
+    for (int c = c0; c < c0 + nc; ++c) chunk_f64<MODE>(tp, sp, c, J, b_l, Vinv, sm, ns);
   }
   __syncthreads();
   for (int i = tid; i < ns * 9; i += kChunkObs) {
     const int s = i / 9, k = i - 9 * s;
-    const int row = __ldg(sp.gslot_row + s0 + s);
+    int row = __ldg(sp.gslot_row + s0 + s);
+    POBA_CHK(tp.chk, row, sp.n_gslots, kChkSerRow);
     T v;
     if constexpr (sizeof(T) == 4)
       v = reinterpret_cast<const float*>(sm.acc[s])[k];
@@ -676,7 +723,12 @@ __device__ __forceinline__ void camera_body(const Topology& tp, const int32_t* _
   const bool cam_ok = cl < per_block && c < tp.n_cams && !ld_volatile(&st[tp.cam_prob[c]].done);
   double y = 0.0;
   if (cam_ok) {
-    const int r0 = cam_ptr[c], r1 = cam_ptr[c + 1];
+    int r0 = cam_ptr[c], r1 = cam_ptr[c + 1];
+    if (kChecks && (r0 < 0 || r1 < r0 || r1 > cam_ptr[tp.n_cams])) {
+      int bad = r1;
+      POBA_CHK(tp.chk, bad, 0, kChkCamRows);
+      r0 = r1 = 0;
+    }
     const int C = cam_chunk_rows(r1 - r0);
     for (int q0 = r0; q0 < r1; q0 += C) y += cam_chunk_sum(partial, q0, min(q0 + C, r1), k);
   }

@@ -194,6 +194,7 @@ int main(int argc, char** argv) {
       CHECK(chunk_group[c] < 0, "chunk %d in two groups", c);
       chunk_group[c] = i;
       const int32_t* d = &Q.chunk[8 * (size_t)c];
+      CHECK(d[6] == i, "chunk %d names group %d, not %d", c, d[6], i);
       obs += d[1];
       if (c > g[0]) CHECK(d[2] == Q.chunk[8 * (size_t)(c - 1) + 2] + Q.chunk[8 * (size_t)(c - 1) + 3],
                           "group %d chunks are not consecutive landmarks", i);
