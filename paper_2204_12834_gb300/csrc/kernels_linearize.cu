@@ -179,17 +179,24 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
   // sj: J_p and r of each observation at its camera-sorted position; s9: the landmark
   // contributions.  In FP64 the two share storage (the static limit is 48 KB), with a barrier
   // between the landmark sums and the staging.
+  // sj rows hold 20 values with a stride of 21 (odd), so that the threads of a warp, which
+  // stage rows at scattered positions, hit distinct banks
   constexpr bool kAlias = sizeof(T) == 8;
-  constexpr int kSjBytes = kTileObs * 20 * (int)sizeof(T);
+  constexpr int kSjStride = 21;
+  constexpr int kSjBytes = kTileObs * kSjStride * (int)sizeof(T);
   constexpr int kS9Bytes = kTileObs * 9 * (int)sizeof(T);
   __shared__ __align__(16) unsigned char lin_smem[kAlias ? kSjBytes : kSjBytes + kS9Bytes];
-  T (*sj)[20] = reinterpret_cast<T (*)[20]>(lin_smem);
+  T (*sj)[kSjStride] = reinterpret_cast<T (*)[kSjStride]>(lin_smem);
   T (*s9)[9] = reinterpret_cast<T (*)[9]>(lin_smem + (kAlias ? 0 : kSjBytes));
   __shared__ uint16_t sbeg[kTileObs];
   __shared__ int srow[kTileObs];
   __shared__ double sred[kTileObs];
+  // the pair table in shared memory: the lanes of a warp read different entries, which the
+  // constant cache would serve one address at a time
+  __shared__ uchar4 spairs[kLinVals];
 
   if (gate && *gate == 0) return;  // the state did not change: the linearisation is current
+  if (threadIdx.x < kLinVals) spairs[threadIdx.x] = kLinPairs.v[threadIdx.x];
   const int tile = blockIdx.x, tid = threadIdx.x;
   const int L0 = tp.tile_lm0[tile], L1 = tp.tile_lm0[tile + 1];
   const int o0 = tp.lm_seg[L0], n = tp.lm_seg[L1] - o0;
@@ -267,7 +274,7 @@ __global__ void __launch_bounds__(kTileObs) linearize_kernel(
   for (int pr = tid; pr < ns * kLinVals; pr += blockDim.x) {
     const int sl = pr / kLinVals, e = pr - sl * kLinVals;
     const int beg = sbeg[sl], end = (sl + 1 < ns) ? (int)sbeg[sl + 1] : n;
-    const uchar4 ix = kLinPairs.v[e];
+    const uchar4 ix = spairs[e];
     T acc = (T)0;
     for (int q = beg; q < end; ++q) {
       if constexpr (sizeof(T) == 8)
@@ -301,15 +308,23 @@ template void launch_linearize<float>(const Topology&, const float*, const doubl
                                       double*, float*, double*, cudaStream_t, const int32_t*);
 
 // ---------------------------------------------------------------------------------------
-// Per camera: U (45 packed) and b_p (9) summed over the camera's slots in slot order.
+// Per camera (one block of 4 x kLinVals threads): U (45 packed) and b_p (9) summed over the
+// camera's slot rows: thread (j, k) adds entry k of rows r0 + j, r0 + j + 4, ... (its row class
+// j mod 4, four loads in flight at a time), thread (0, k) also the last (rows mod 4) rows, and
+// the four class sums are combined as (a0 + a1) + (a2 + a3).  FP32 bulk: each thread adds its
+// rows in float over runs of kLinRun rows (a segment of tiles) and the runs in double, so that
+// the float-to-double conversions and double adds, which run on the FP64 pipe, are one per run
+// rather than one per row.
+constexpr int kLinRun = 16;
 template <typename PT>
-__global__ void lin_camera_reduce_kernel(Topology tp, const PT* __restrict__ partial,
-                                         double* __restrict__ U45, double* __restrict__ b_p,
-                                         const int32_t* __restrict__ gate) {
-  const int per = kLinVals;
-  const int c = blockIdx.x * 4 + threadIdx.x / per;
-  const int k = threadIdx.x % per;
-  if (c >= tp.n_cams || (gate && *gate == 0)) return;
+__global__ void __launch_bounds__(4 * kLinVals) lin_camera_reduce_kernel(
+    Topology tp, const PT* __restrict__ partial, double* __restrict__ U45,
+    double* __restrict__ b_p, const int32_t* __restrict__ gate) {
+  constexpr int per = kLinVals;
+  __shared__ double part[4][per];
+  const int c = blockIdx.x;
+  const int j = threadIdx.x / per, k = threadIdx.x - j * per;
+  if (gate && *gate == 0) return;  // (block-uniform)
   // the camera's slot rows are contiguous (camera-major)
   int r0 = tp.cam_slot_ptr[c], r1 = tp.cam_slot_ptr[c + 1];
   if (kChecks && (r0 < 0 || r1 < r0 || r1 > tp.n_slots)) {
@@ -317,25 +332,60 @@ __global__ void lin_camera_reduce_kernel(Topology tp, const PT* __restrict__ par
     POBA_CHK(tp.chk, bad, 0, kChkCamReduce);
     r0 = r1 = 0;
   }
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-  int r = r0;
-  for (; r + 4 <= r1; r += 4) {
-    a0 += (double)partial[(size_t)(r + 0) * per + k];
-    a1 += (double)partial[(size_t)(r + 1) * per + k];
-    a2 += (double)partial[(size_t)(r + 2) * per + k];
-    a3 += (double)partial[(size_t)(r + 3) * per + k];
+  const int rm = r0 + ((r1 - r0) & ~3);  // end of the rows shared round-robin
+  double a = 0.0;
+  int r = r0 + j;
+  if constexpr (sizeof(PT) == 4) {
+    // runs of kLinRun of this thread's rows in float, the runs in double
+    while (r < rm) {
+      float f = 0.f;
+      const int re = min(rm, r + 4 * kLinRun);
+      for (; r + 12 < re; r += 16) {
+        const float v0 = __ldcg(partial + (size_t)r * per + k);
+        const float v1 = __ldcg(partial + (size_t)(r + 4) * per + k);
+        const float v2 = __ldcg(partial + (size_t)(r + 8) * per + k);
+        const float v3 = __ldcg(partial + (size_t)(r + 12) * per + k);
+        f += v0;
+        f += v1;
+        f += v2;
+        f += v3;
+      }
+      for (; r < re; r += 4) f += __ldcg(partial + (size_t)r * per + k);
+      a += (double)f;
+    }
+    if (j == 0) {
+      float f = 0.f;
+      for (r = rm; r < r1; ++r) f += __ldcg(partial + (size_t)r * per + k);
+      a += (double)f;
+    }
+  } else {
+    for (; r + 12 < rm; r += 16) {
+      const PT v0 = __ldcg(partial + (size_t)r * per + k);
+      const PT v1 = __ldcg(partial + (size_t)(r + 4) * per + k);
+      const PT v2 = __ldcg(partial + (size_t)(r + 8) * per + k);
+      const PT v3 = __ldcg(partial + (size_t)(r + 12) * per + k);
+      a += (double)v0;
+      a += (double)v1;
+      a += (double)v2;
+      a += (double)v3;
+    }
+    for (; r < rm; r += 4) a += (double)__ldcg(partial + (size_t)r * per + k);
+    if (j == 0)
+      for (r = rm; r < r1; ++r) a += (double)__ldcg(partial + (size_t)r * per + k);
   }
-  for (; r < r1; ++r) a0 += (double)partial[(size_t)r * per + k];
-  const double acc = (a0 + a1) + (a2 + a3);
-  if (k < 45) U45[(size_t)c * 45 + k] = acc;
-  else b_p[(size_t)c * 9 + (k - 45)] = acc;
+  part[j][k] = a;
+  __syncthreads();
+  if (j == 0) {
+    const double acc = (part[0][k] + part[1][k]) + (part[2][k] + part[3][k]);
+    if (k < 45) U45[(size_t)c * 45 + k] = acc;
+    else b_p[(size_t)c * 9 + (k - 45)] = acc;
+  }
 }
 
 template <typename PT>
 void launch_lin_camera_reduce(const Topology& tp, const PT* partial, double* U45, double* b_p,
                               cudaStream_t s, const int32_t* gate) {
-  const int blocks = (tp.n_cams + 3) / 4;
-  lin_camera_reduce_kernel<PT><<<blocks, 4 * kLinVals, 0, s>>>(tp, partial, U45, b_p, gate);
+  lin_camera_reduce_kernel<PT><<<tp.n_cams, 4 * kLinVals, 0, s>>>(tp, partial, U45, b_p, gate);
 }
 // Long tracks: the linearisation kernel leaves each piece's own sums in V and b_l; the track's
 // V = sum J_l^T J_l and b_l = sum J_l^T r are the sums over its pieces, added in piece order (in
