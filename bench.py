@@ -113,6 +113,9 @@ def parse_args(argv=None):
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run only this many untimed LM steps (for ncu captures)")
     ap.add_argument("--profile-precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--profile-form", type=int, default=0,
+                    help="profile mode: the series form to run (ba_set_schedule series_exec; "
+                         "0 keeps the handle's default)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="profile mode on the 256-problem batch instead of the single problem")
     return ap.parse_args(argv)
@@ -210,9 +213,9 @@ def kernel_source_sha() -> str:
 
 
 def profiled_traffic(precision: str, form: int, workload: str = WORKLOAD):
-    """DRAM bytes per series term of the persistent kernel in the given form (3 plain, 4 with the
-    copy pipeline) on `workload`, from the committed ncu summary, if the kernel source is
-    unchanged since the capture; else None."""
+    """DRAM bytes per series term of the persistent kernel in the given form (3 plain, 4 staged,
+    5 dataflow) on `workload`, from the committed ncu summary, if the kernel source is unchanged
+    since the capture and that form was captured; else None."""
     path = os.path.join(ROOT, "profiles", f"series_persistent_{workload}.json")
     try:
         d = json.load(open(path))
@@ -220,10 +223,11 @@ def profiled_traffic(precision: str, form: int, workload: str = WORKLOAD):
         return None
     if d.get("kernel_source_sha") != kernel_source_sha():
         return None
-    e = d.get(precision, {})
-    if e.get("form") not in (None, form):
-        return None
-    return e.get("dram_bytes_per_term")
+    # an entry per captured form: "<precision>" and "<precision>_form<k>"
+    for e in (d.get(precision, {}), d.get(f"{precision}_form{form}", {})):
+        if e.get("form") == form:
+            return e.get("dram_bytes_per_term")
+    return None
 
 
 def step_stats(ms) -> dict:
@@ -330,10 +334,14 @@ def run_poba(args):
         prec = poba.BA_FP64 if args.profile_precision == "fp64" else poba.BA_FP32_BULK
         if args.profile_batch:
             hb = poba.batch_from_problems(bal_synth.make_batch(256), precision=prec, stream=stream)
+            if args.profile_form:
+                poba.ba_set_schedule(hb, series_exec=args.profile_form)
             for _ in range(args.profile_steps):
                 poba.ba_lm_step_batch(hb)
         else:
             h = make(prec)
+            if args.profile_form:
+                poba.ba_set_schedule(h, series_exec=args.profile_form)
             for _ in range(args.profile_steps):
                 poba.ba_lm_step(h)
         torch.cuda.synchronize()
