@@ -170,6 +170,7 @@ struct ba_handle {
   int group_obs = 0;                     // requested group size (0: automatic)
   // persistent kernel: grid = blocks per SM x SMs
   int sms = 0;
+  int l2_bytes = 0;                      // L2 size of the device
   int plain_max = 0;                     // occupancy limit (0: kernel unavailable)
   int plain_k = 0;                       // blocks per SM in use
   int stage_max = 0, stage_k = 0;        // FP32 staged persistent kernel: limit, in use
@@ -702,8 +703,11 @@ ba_status rebuild_series(ba_handle* h, int group_obs, int tail) {
   h->ser_bytes = total;
   h->ser_partial = d_part;
   h->group_obs = group_obs;
+  // group bodies prefetch their next chunk when the Jacobians take more than half of L2 (each
+  // term then streams much of them from HBM); an L2-resident problem gains nothing from it
+  const size_t j_bytes = (size_t)24 * h->n_o_pad * (h->f32() ? 4 : 8);
   h->sp = SerTopo{Q.n_groups, Q.n_chunks, Q.n_gslots, (const int4*)d_group, (const int4*)d_chunk,
-                  d_rec, d_gcam, d_grow, d_cptr, d_pnc};
+                  d_rec, d_gcam, d_grow, d_cptr, d_pnc, 2 * j_bytes > (size_t)h->l2_bytes ? 1 : 0};
   {
     // flow state: cam_norm_b first (16-byte pairs), then the counters
     char* f = (char*)d_flow;
@@ -846,6 +850,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&h->l2_bytes, cudaDevAttrL2CacheSize, dev);
     const int per_sm = persistent_blocks_per_sm(h->f32());
     h->sms = sms;
     // FP32 bulk: up to 4 blocks of 256 threads per SM, FP64: up to 3

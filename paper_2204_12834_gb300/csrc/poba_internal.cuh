@@ -259,6 +259,7 @@ struct SerTopo {
   const int32_t* gslot_row;  // [n_gslots] camera-major partial row
   const int32_t* cam_ptr;    // [n_cams + 1] partial rows of each camera
   const int32_t* prob_ncam;  // [n_probs] cameras of each problem with at least one partial row
+  int prefetch;              // 1: group bodies prefetch their next chunk to L2
 };
 
 // Per-launch state of the dataflow series kernel (series_exec 5), zeroed before each launch.

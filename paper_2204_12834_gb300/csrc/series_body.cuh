@@ -417,9 +417,11 @@ __device__ __forceinline__ void chunk_f64(const Topology& tp, const SerTopo& sp,
   double (*sv)[3] = sm.sv;
   double jp[18], jl[6];
   uint32_t code = 0;
+  const uint64_t pol = l2_stream_policy();
   if (active) {
-    load_J(J, (size_t)tp.n_obs_pad, o0 + tid, jp, jl);
-    code = chk_code(tp, __ldg(reinterpret_cast<const uint32_t*>(rec + L.code) + tid), n, nl, gns);
+    load_J_stream(J, (size_t)tp.n_obs_pad, o0 + tid, jp, jl, pol);
+    code = chk_code(tp, ldg_stream(reinterpret_cast<const uint32_t*>(rec + L.code) + tid, pol), n,
+                    nl, gns);
   }
   double vi[6], sl[3] = {0.0, 0.0, 0.0};
   int a = 0, b = 0;
@@ -429,7 +431,7 @@ __device__ __forceinline__ void chunk_f64(const Topology& tp, const SerTopo& sp,
     b = __ldg(sseg + tid + 1);
     chk_seg(tp, a, b, n);
     const double2* v2 = reinterpret_cast<const double2*>(Vinv + (size_t)(L0 + tid) * 6);
-    const double2 x0 = __ldg(v2), x1 = __ldg(v2 + 1), x2 = __ldg(v2 + 2);
+    const double2 x0 = ldg_stream(v2, pol), x1 = ldg_stream(v2 + 1, pol), x2 = ldg_stream(v2 + 2, pol);
     vi[0] = x0.x; vi[1] = x0.y; vi[2] = x1.x; vi[3] = x1.y; vi[4] = x2.x; vi[5] = x2.y;
     if (MODE == kModeRhs) {
       const double* bl = b_l + (size_t)(L0 + tid) * 3;
@@ -610,6 +612,48 @@ __device__ __noinline__ void long_group_body(const Topology& tp, const SerTopo& 
   }
 }
 
+// Chunks of a group prefetched to L2 ahead of the one the block runs (when the schedule asks for
+// it: sp.prefetch, set when the Jacobians take more than half of L2, so that a term streams
+// much of them from HBM).
+constexpr int kChunkAhead = 1;
+
+// Chunk c's inputs toward L2 ahead of their use: the Jacobian plane groups of its observations
+// (24 / V contiguous ranges of n 16-byte groups), its record and the V^-1 rows of its landmarks,
+// one bulk prefetch per range, issued by the first lanes of the calling warp (FP64: with the
+// streaming policy of the FP64 chunk's loads).  A range is widened to 16-byte bounds, which stay
+// inside the 256-byte-aligned arena item it belongs to.  A prefetch changes no data, so the
+// chunk's sums are the same with or without it.
+template <typename T>
+__device__ __forceinline__ void prefetch_chunk_l2(const Topology& tp, const SerTopo& sp, int c,
+                                                  const T* __restrict__ J,
+                                                  const T* __restrict__ Vinv, int lane) {
+  constexpr int V = jgroup<T>(), NG = 24 / V;
+  if (lane >= NG + 2) return;
+  const int4 d0 = __ldg(sp.chunk + 2 * c), d1 = __ldg(sp.chunk + 2 * c + 1);
+  const char* p;
+  size_t bytes;
+  if (lane < NG) {
+    p = reinterpret_cast<const char*>(jgroups(J) + (size_t)lane * tp.n_obs_pad + d0.x);
+    bytes = (size_t)d0.y * 16;
+  } else if (lane == NG) {
+    p = reinterpret_cast<const char*>(sp.rec + (size_t)d1.y * 16);
+    bytes = (size_t)chunk_rec_layout(d0.y, d0.w, d1.x).bytes;
+  } else {
+    p = reinterpret_cast<const char*>(Vinv + (size_t)d0.z * 6);
+    bytes = (size_t)d0.w * 6 * sizeof(T);
+  }
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)15;
+  const uintptr_t e = (reinterpret_cast<uintptr_t>(p) + bytes + 15) & ~(uintptr_t)15;
+  if (e <= a) return;
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(a),
+                 "r"((unsigned)(e - a)), "l"(l2_stream_policy())
+                 : "memory");
+  else
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a))
+                 : "memory");
+}
+
 // One group (blockDim.x == kChunkObs; every thread must call it, and every thread must have
 // finished with the shared memory of the previous group, e.g. by a block barrier): stages the
 // current term of the group's slots and zeroes their accumulators, runs the chunks in order and
@@ -628,6 +672,12 @@ __device__ __forceinline__ void group_body(const Topology& tp, const SerTopo& sp
   }
   const int4 gd = __ldg(sp.group + 2 * g);
   const int c0 = gd.x, nc = gd.y, s0 = gd.z, ns = gd.w;
+  // the last warp prefetches the first chunks now (their loads overlap the staging of t) and
+  // chunk c + kChunkAhead while the block runs chunk c
+  const int pw_lane = sp.prefetch ? tid - (kChunkObs - 32) : -1;
+  if (pw_lane >= 0)
+    for (int c = c0; c < c0 + min(nc, kChunkAhead); ++c)
+      prefetch_chunk_l2<T>(tp, sp, c, J, Vinv, pw_lane);
   constexpr int R = sizeof(T) == 4 ? 3 : 5;  // 16-byte pieces of a term row in shared memory
   for (int i = tid; i < ns * R; i += kChunkObs) {
     const int s = i / R, q = i - R * s;
@@ -656,9 +706,17 @@ __device__ __forceinline__ void group_body(const Topology& tp, const SerTopo& sp
   }
   __syncthreads();
   if constexpr (sizeof(T) == 4) {
-    for (int c = c0; c < c0 + nc; ++c) chunk_f32<MODE>(tp, sp, c, J, b_l, Vinv, sm, ns);
+    for (int c = c0; c < c0 + nc; ++c) {
+      if (pw_lane >= 0 && c + kChunkAhead < c0 + nc)
+        prefetch_chunk_l2<T>(tp, sp, c + kChunkAhead, J, Vinv, pw_lane);
+      chunk_f32<MODE>(tp, sp, c, J, b_l, Vinv, sm, ns);
+    }
   } else {
-    for (int c = c0; c < c0 + nc; ++c) chunk_f64<MODE>(tp, sp, c, J, b_l, Vinv, sm, ns);
+    for (int c = c0; c < c0 + nc; ++c) {
+      if (pw_lane >= 0 && c + kChunkAhead < c0 + nc)
+        prefetch_chunk_l2<T>(tp, sp, c + kChunkAhead, J, Vinv, pw_lane);
+      chunk_f64<MODE>(tp, sp, c, J, b_l, Vinv, sm, ns);
+    }
   }
   __syncthreads();
   for (int i = tid; i < ns * 9; i += kChunkObs) {
