@@ -108,6 +108,7 @@ struct RoundCache {  // in shared memory
   int q[kRoundItems][2];          // item rows
   int cam[kRoundItems][4];        // camera, its items (round-relative), problem
   double x[kRoundItems][9];       // the cameras' x
+  int done[kRoundItems];          // the current round's cameras: their problem's done flag
 };
 
 __device__ __forceinline__ void round_cache(const Topology& tp, const CamRounds& cr,
@@ -141,13 +142,17 @@ __device__ __forceinline__ void round_cache(const Topology& tp, const CamRounds&
   __syncthreads();
 }
 
-// Combination, U^-1 and norms of one round (after the chunk sums are in pc).
+// Combination, U^-1 and norms of one round (after the chunk sums are in pc).  The round's
+// cameras are c_first .. c_first + nc - 1 with their done flags in done[]; the norm pairs are
+// summed by the block's first 2 nc threads (a thread per pair entry), so that only the warps
+// holding them issue those FP64 adds.
 template <typename T>
 __device__ __forceinline__ double round_finish(bool cam, bool run, int c, int ia, int ib,
                                                const double* __restrict__ Uinv, double xo,
                                                T* __restrict__ t_cam,
                                                double* __restrict__ cam_norm, double (*pc)[9],
-                                               double (*ys)[9], double (*y2)[9]) {
+                                               double (*ys)[9], double (*y2)[9], int c_first,
+                                               int nc, const int* done) {
   const int it = threadIdx.x / 9, k = threadIdx.x - it * 9;
   double y = 0.0;
   if (run)
@@ -168,15 +173,9 @@ __device__ __forceinline__ double round_finish(bool cam, bool run, int c, int ia
     y2[it][k] = xv * xv;
   }
   __syncthreads();
-  if (run && k == 0) {
-    double a = 0.0, b = 0.0;
-#pragma unroll
-    for (int j = 0; j < 9; ++j) {
-      a += ys[it][j];
-      b += y2[it][j];
-    }
-    cam_norm[2 * c + 0] = a;
-    cam_norm[2 * c + 1] = b;
+  if (threadIdx.x < 2 * nc) {
+    const int cn = threadIdx.x >> 1, e = threadIdx.x & 1;
+    if (!done[cn]) cam_norm[2 * (c_first + cn) + e] = norm_row_sum(e ? y2[cn] : ys[cn]);
   }
   __syncthreads();
   return run ? xv : xo;
@@ -196,20 +195,22 @@ __device__ __forceinline__ void camera_phase(const Topology& tp, const CamRounds
   const int it = tid / 9, k = tid - it * 9;
   if (rc.rd < 0) return;
   {
-    // the cached first round
+    // the cached first round.  The done flags are read by one warp (a lane per camera): every
+    // block reads them at once, and one request per block keeps their L2 line quiet.
     const bool cam = it < rc.nc;
-    int c = 0, done = 1;
+    int c = 0;
+    if (tid < rc.nc) rc.done[tid] = ld_volatile(&st[rc.cam[tid][3]].done);
     if (cam) {
       c = rc.cam[it][0];
       prefetch_uinv_row(Uinv, c, k);
-      done = ld_volatile(&st[rc.cam[it][3]].done);
     }
     if (it < rc.ni) pc[it][k] = cam_chunk_sum(partial, rc.q[it][0], rc.q[it][1], k);
     __syncthreads();
+    const bool done = cam ? rc.done[it] != 0 : true;
     const double xo = cam ? rc.x[it][k] : 0.0;
     const double xv = round_finish<T>(cam, cam && !done, c, cam ? rc.cam[it][1] : 0,
                                       cam ? rc.cam[it][2] : 0, Uinv, xo, t_cam, cam_norm, pc,
-                                      ys, y2);
+                                      ys, y2, rc.cam[0][0], rc.nc, rc.done);
     if (cam) rc.x[it][k] = xv;
   }
   for (int rd = rc.rd + 1; rd < cr.block_round[blockIdx.x + 1]; ++rd) {
@@ -218,13 +219,13 @@ __device__ __forceinline__ void camera_phase(const Topology& tp, const CamRounds
     const int c = c0 + it;
     const bool cam = it < nc;
     double xo = 0.0;
-    int ia = 0, ib = 0, done = 1;
+    int ia = 0, ib = 0;
+    if (tid < nc) rc.done[tid] = ld_volatile(&st[tp.cam_prob[c0 + tid]].done);
     if (cam) {
       prefetch_uinv_row(Uinv, c, k);
       xo = __ldcg(x + (size_t)c * 9 + k);
       ia = cr.cam_item[c] - i0;
       ib = cr.cam_item[c + 1] - i0;
-      done = ld_volatile(&st[tp.cam_prob[c]].done);
     }
     if (it < ni) {
       int q0 = cr.item_q[2 * (i0 + it)], q1 = cr.item_q[2 * (i0 + it) + 1];
@@ -233,9 +234,23 @@ __device__ __forceinline__ void camera_phase(const Topology& tp, const CamRounds
       pc[it][k] = cam_chunk_sum(partial, q0, q1, k);
     }
     __syncthreads();
-    const bool run = cam && !done;
-    const double xv = round_finish<T>(cam, run, c, ia, ib, Uinv, xo, t_cam, cam_norm, pc, ys, y2);
+    const bool run = cam && rc.done[it] == 0;
+    const double xv = round_finish<T>(cam, run, c, ia, ib, Uinv, xo, t_cam, cam_norm, pc, ys, y2,
+                                      c0, nc, rc.done);
     if (run) x[(size_t)c * 9 + k] = xv;
+  }
+}
+
+// The U^-1 blocks of the cameras of this block's rounds toward L2 (one bulk prefetch per round,
+// the cameras of a round being consecutive), issued when the block leaves a group phase so that
+// the camera phase after the barrier finds them there: a group phase streams the Jacobians
+// through L2 and evicts them otherwise.  Thread 0 only.
+__device__ __forceinline__ void prefetch_round_uinv(const CamRounds& cr, const RoundCache& rc,
+                                                    const double* __restrict__ Uinv) {
+  if (threadIdx.x != 0 || rc.rd < 0) return;
+  for (int rd = rc.rd; rd < cr.block_round[blockIdx.x + 1]; ++rd) {
+    const int c0 = cr.round_cam[rd], c1 = cr.round_cam[rd + 1];
+    prefetch_l2(Uinv + (size_t)c0 * 81, (size_t)(c1 - c0) * 81 * sizeof(double), false);
   }
 }
 
@@ -321,6 +336,7 @@ __global__ void __launch_bounds__(kChunkObs, sizeof(T) == 4 ? 4 : 3) series_pers
       if (g >= sp.n_groups) break;
       group_body<T, kModeSeries>(tp, sp, g, J, t_cam, nullptr, Vinv, partial, sm);
     }
+    prefetch_round_uinv(cr, rc, Uinv);
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 1] = global_ns();
     if (!tile_end_barrier(gs, timeout, &s_last, &s_gen, &s_ok)) return;
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 2] = global_ns();
@@ -436,15 +452,10 @@ __device__ __forceinline__ void flow_cameras(const Topology& tp, const SerTopo& 
       y2[cl][k] = xv * xv;
     }
     __syncthreads();
-    if (cam && k == 0) {
-      double a = 0.0, b = 0.0;
-#pragma unroll
-      for (int j = 0; j < 9; ++j) {
-        a += ys[cl][j];
-        b += y2[cl][j];
-      }
-      norm_out[2 * c + 0] = a;
-      norm_out[2 * c + 1] = b;
+    const int nb = min(kRoundItems, n_own - base);
+    if (threadIdx.x < 2 * nb) {
+      const int cn = threadIdx.x >> 1, e = threadIdx.x & 1;
+      norm_out[2 * own[base + cn] + e] = norm_row_sum(e ? y2[cn] : ys[cn]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -882,6 +893,7 @@ __global__ void __launch_bounds__(kChunkObs, 3) series_staged_kernel(
       if (tid == 0) atomicExch(&gs->error, 1);
       return;
     }
+    prefetch_round_uinv(cr, rc, Uinv);
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 1] = global_ns();
     if (!tile_end_barrier(gs, timeout, &s_last, &s_gen, &s_ok)) return;
     if (tracer && i <= kTraceTerms) trace[(i - 1) * kTracePoints + 2] = global_ns();

@@ -612,6 +612,22 @@ __device__ __noinline__ void long_group_body(const Topology& tp, const SerTopo& 
   }
 }
 
+// Bytes [p, p + bytes) toward L2 (one bulk prefetch; stream: with the streaming policy).  The
+// range is widened to 16-byte bounds, which must stay inside the allocation (every arena item
+// starts on a 256-byte boundary, so a range within one item qualifies).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, bool stream) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)15;
+  const uintptr_t e = (reinterpret_cast<uintptr_t>(p) + bytes + 15) & ~(uintptr_t)15;
+  if (e <= a) return;
+  if (stream)
+    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(a),
+                 "r"((unsigned)(e - a)), "l"(l2_stream_policy())
+                 : "memory");
+  else
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a))
+                 : "memory");
+}
+
 // Chunks of a group prefetched to L2 ahead of the one the block runs (when the schedule asks for
 // it: sp.prefetch, set when the Jacobians take more than half of L2, so that a term streams
 // much of them from HBM).
@@ -620,9 +636,8 @@ constexpr int kChunkAhead = 1;
 // Chunk c's inputs toward L2 ahead of their use: the Jacobian plane groups of its observations
 // (24 / V contiguous ranges of n 16-byte groups), its record and the V^-1 rows of its landmarks,
 // one bulk prefetch per range, issued by the first lanes of the calling warp (FP64: with the
-// streaming policy of the FP64 chunk's loads).  A range is widened to 16-byte bounds, which stay
-// inside the 256-byte-aligned arena item it belongs to.  A prefetch changes no data, so the
-// chunk's sums are the same with or without it.
+// streaming policy of the FP64 chunk's loads).  A prefetch changes no data, so the chunk's sums
+// are the same with or without it.
 template <typename T>
 __device__ __forceinline__ void prefetch_chunk_l2(const Topology& tp, const SerTopo& sp, int c,
                                                   const T* __restrict__ J,
@@ -642,16 +657,7 @@ __device__ __forceinline__ void prefetch_chunk_l2(const Topology& tp, const SerT
     p = reinterpret_cast<const char*>(Vinv + (size_t)d0.z * 6);
     bytes = (size_t)d0.w * 6 * sizeof(T);
   }
-  const uintptr_t a = reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)15;
-  const uintptr_t e = (reinterpret_cast<uintptr_t>(p) + bytes + 15) & ~(uintptr_t)15;
-  if (e <= a) return;
-  if constexpr (sizeof(T) == 8)
-    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(a),
-                 "r"((unsigned)(e - a)), "l"(l2_stream_policy())
-                 : "memory");
-  else
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a))
-                 : "memory");
+  prefetch_l2(p, bytes, sizeof(T) == 8);
 }
 
 // One group (blockDim.x == kChunkObs; every thread must call it, and every thread must have
@@ -757,11 +763,22 @@ __device__ __forceinline__ double cam_chunk_sum(const PT* __restrict__ partial, 
   return (double)pc;
 }
 
+// One entry of a camera's norm pair: the sum of its 9 squared components in component order
+// (every camera update path uses this order).  The camera updates run it on a thread per pair
+// entry, packed into the first threads of the block: each FP64 warp instruction costs 16 pipe
+// cycles on GB300, so the fewer warps issue these adds the better.
+__device__ __forceinline__ double norm_row_sum(const double* sq) {
+  double a = 0.0;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) a += sq[j];
+  return a;
+}
+
 // Camera body for cameras [cam0, cam0 + per_block): thread (c, k) sums component k of the
 // camera's contiguous partial rows [cam_ptr[c], cam_ptr[c + 1]) (chunk by chunk, cam_chunk_rows
 // rows per chunk, the chunks in order), applies row k of U^-1, updates x and writes the new term
-// t_cam[c]; then the 9 threads of the camera add their squared term and x components (in
-// component order) into the camera's pair cam_norm[c] = (||t_c||^2, ||x_c||^2).  Cameras of
+// t_cam[c]; then the camera's squared term and x components are added (in component order,
+// norm_row_sum) into its pair cam_norm[c] = (||t_c||^2, ||x_c||^2).  Cameras of
 // problems whose series has stopped are left as they are.  FP64 work is one add per row and
 // component: every FP64 warp instruction costs 16 pipe cycles on GB300, so no shuffle trees are
 // used for the row sums.  ys and y2 are shared [per_block][9] arrays.  Every thread of the block
@@ -813,15 +830,12 @@ __device__ __forceinline__ void camera_body(const Topology& tp, const int32_t* _
     y2[cl][k] = xv * xv;
   }
   __syncthreads();
-  if (cam_ok && k == 0) {
-    double a = 0.0, b = 0.0;
-#pragma unroll
-    for (int j = 0; j < 9; ++j) {
-      a += ys[cl][j];
-      b += y2[cl][j];
-    }
-    cam_norm[2 * c + 0] = a;
-    cam_norm[2 * c + 1] = b;
+  // the norm pairs: the block's first 2 per_block threads, one pair entry each (the done flags
+  // cannot change before every block of the launch has passed here)
+  if (tid < 2 * per_block) {
+    const int cn = tid >> 1, e = tid & 1, cc = cam0 + cn;
+    if (cc < tp.n_cams && !ld_volatile(&st[tp.cam_prob[cc]].done))
+      cam_norm[2 * cc + e] = norm_row_sum(e ? y2[cn] : ys[cn]);
   }
   __syncthreads();
 }
