@@ -93,7 +93,8 @@ typedef struct {
                            creation 3 at the largest residency, 4 blocks per SM in BA_FP32_BULK,
                            3 in BA_FP64).  A device that cannot run a persistent form falls back
                            (4 and 5 to 3, 3 to 1: all blocks must be co-resident), and so do
-                           forms 4 and 5 on a problem with tracks of more than 256 observations.
+                           forms 4 and 5 on a problem with tracks of more than 256 observations
+                           (or, in BA_FP64, a landmark seen by more than 96 cameras).
                            All forms give bitwise-equal results for the handle's series
                            schedule. */
 } ba_options;
@@ -339,8 +340,10 @@ ba_status ba_solve_schur_pcg(ba_handle* h, double lambda, int32_t precond, int32
 /* Series schedule (no counterpart in the paper; the GPU form of the paper's per-landmark memory
  * blocks, Sec. 5 "Efficient storage").  The power-series kernels cut each problem's observed
  * landmarks into groups of consecutive landmarks of about group_obs observations (boundaries
- * at whole landmarks, balanced by observation count, at most 256 distinct cameras per group),
- * and each group into chunks of at most 256 observations.  One thread block runs one group and
+ * at whole landmarks, balanced by observation count, at most 256 distinct cameras per group in
+ * BA_FP32_BULK and 96 in BA_FP64, whose group body also keeps a chunk's J_p in shared memory; a
+ * landmark seen by more cameras than that, like a long track, is a group of its own), and each
+ * group into chunks of at most 256 observations.  One thread block runs one group and
  * keeps one camera-keyed accumulator per distinct camera of the group, written once per group:
  * larger groups mean fewer partial rows for the camera step, smaller ones finer load balance.
  * The sums of a step depend on the group boundaries, so two handles give bitwise-equal results

@@ -168,6 +168,7 @@ struct ba_handle {
   size_t flow_bytes = 0;
   void* ser_partial = nullptr;           // [n_gslots][9] partial rows (bulk precision)
   int group_obs = 0;                     // requested group size (0: automatic)
+  int ser_long = 0;                      // series groups run by the long-group body
   // persistent kernel: grid = blocks per SM x SMs
   int sms = 0;
   int l2_bytes = 0;                      // L2 size of the device
@@ -362,6 +363,9 @@ void collect_timing(ba_handle* h, int terms_run, bool series_ran) {
 // Extra kernel of a step for the long tracks of a handle (their block and back-substitution
 // kernels), 0 without long tracks.
 int long_kernels(const ba_handle* h) { return h->tp.n_long > 0 ? 1 : 0; }
+// The staged and dataflow series kernels take groups of whole landmarks within the slot cap only:
+// none of long tracks' pieces or of landmarks wider than the cap.
+bool has_long_groups(const ba_handle* h) { return h->tp.n_long > 0 || h->ser_long > 0; }
 
 void seq_linearize(ba_handle* h) {
   Range range("poba.linearize");
@@ -479,11 +483,11 @@ ba_status run_series_body(ba_handle* h, bool use_active) {
   // chunks (FP32 bulk); series_exec 2 takes the handle's schedule (default or ba_autotune)
   int mode = h->opts.series_exec == 2 ? h->auto_exec : h->opts.series_exec;
   // the dataflow kernel numbers its tickets (term, group) in 32 bits
-  // (the staged and dataflow kernels take groups of whole landmarks only: no long tracks)
-  if (mode == 5 && (h->flow_k <= 0 || h->tp.n_long > 0 ||
+  // (the staged and dataflow kernels take no long groups: has_long_groups)
+  if (mode == 5 && (h->flow_k <= 0 || has_long_groups(h) ||
                     (int64_t)h->opts.max_inner * h->sp.n_groups >= (1LL << 31)))
     mode = 3;
-  if (mode == 4 && (h->stage_k <= 0 || h->tp.n_long > 0)) mode = 3;
+  if (mode == 4 && (h->stage_k <= 0 || has_long_groups(h))) mode = 3;
   if (mode == 3 && h->plain_k <= 0) mode = 1;
   if (mode == 1 && h->capturing_step) mode = 0;  // the step graph holds the per-term launches
   h->last_exec = mode;
@@ -625,7 +629,8 @@ ba_status rebuild_series(ba_handle* h, int group_obs, int tail) {
   const Schedule& S = h->sched;
   const int target = group_obs > 0 ? group_obs : series_auto_target(h->n_o, auto_workers(h));
   SerSchedule Q;
-  const std::string why = build_series_schedule(S, target, tail, &Q);
+  const std::string why =
+      build_series_schedule(S, target, tail, &Q, h->f32() ? kGroupSlots : kGroupSlotsF64);
   if (!why.empty()) return fail(BA_ERR_INVALID_ARG, why);
   CamSchedule cs;
   build_cam_schedule(Q.cam_ptr, h->n_c, &cs);
@@ -703,6 +708,7 @@ ba_status rebuild_series(ba_handle* h, int group_obs, int tail) {
   h->ser_bytes = total;
   h->ser_partial = d_part;
   h->group_obs = group_obs;
+  h->ser_long = Q.n_long_groups;
   // group bodies prefetch their next chunk when the Jacobians take more than half of L2 (each
   // term then streams much of them from HBM); an L2-resident problem gains nothing from it
   const size_t j_bytes = (size_t)24 * h->n_o_pad * (h->f32() ? 4 : 8);
@@ -1486,9 +1492,9 @@ ba_status ba_autotune(ba_handle* h, int32_t trials, int32_t* exec_out, int32_t* 
   // launches replayed as a graph on the best schedule
   for (int k = 1; k <= h->plain_max; ++k)
     trial({3, k, series_auto_target(h->n_o, k * h->sms - 1), kDefaultTail});
-  for (int k = 1; k <= h->stage_max && h->tp.n_long == 0; ++k)
+  for (int k = 1; k <= h->stage_max && !has_long_groups(h); ++k)
     trial({4, k, series_auto_target(h->n_o, k * h->sms - 1), kDefaultTail});
-  for (int k = 1; k <= h->flow_max && h->tp.n_long == 0; ++k)
+  for (int k = 1; k <= h->flow_max && !has_long_groups(h); ++k)
     trial({5, k, series_auto_target(h->n_o, k * h->sms), kDefaultTail});
   if (best.exec >= 3) {
     const Cand b = best;
@@ -1560,8 +1566,10 @@ ba_status ba_set_schedule(ba_handle* h, const ba_schedule* in) {
     return fail(BA_ERR_INVALID_ARG, "series_exec 4 needs BA_FP32_BULK and the staged kernel");
   if (in->series_exec == 5 && h->flow_max <= 0)
     return fail(BA_ERR_INVALID_ARG, "series_exec 5 needs the dataflow kernel (cooperative launch)");
-  if ((in->series_exec == 4 || in->series_exec == 5) && h->tp.n_long > 0)
-    return fail(BA_ERR_INVALID_ARG, "series_exec 4 and 5 take no tracks of more than 256 observations");
+  if ((in->series_exec == 4 || in->series_exec == 5) && has_long_groups(h))
+    return fail(BA_ERR_INVALID_ARG,
+                "series_exec 4 and 5 take no tracks of more than 256 observations (nor, in FP64, "
+                "landmarks seen by more than 96 cameras)");
   const int kmax = in->series_exec == 4 ? h->stage_max : in->series_exec == 5 ? h->flow_max
                                                                               : h->plain_max;
   if (in->series_exec >= 3 && (in->blocks_per_sm < 1 || in->blocks_per_sm > kmax))

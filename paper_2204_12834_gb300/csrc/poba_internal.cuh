@@ -139,8 +139,9 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
 // not use the tiles above: each problem's observed landmarks are cut into groups of
 // consecutive landmarks holding about `target` observations (boundaries at whole landmarks,
 // balanced by observation count; a group also ends before it would touch more than
-// kGroupSlots distinct cameras; optionally each group's last eighth is cut into smaller
-// groups), and each group into chunks of at most kChunkObs observations of whole landmarks.  One block runs one group: its chunks in order, with one accumulator row
+// kGroupSlots (FP64: kGroupSlotsF64) distinct cameras; optionally each group's last eighth is
+// cut into smaller groups), and each group into chunks of at most kChunkObs observations of
+// whole landmarks.  One block runs one group: its chunks in order, with one accumulator row
 // per distinct camera of the group (a group slot), written once per group as a partial row.
 // A camera's partial rows (one per group that touches it) are contiguous, groups in landmark
 // order (cam_ptr), and summed by the camera kernels in chunks of cam_chunk_rows rows.
@@ -154,7 +155,9 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
 //                (16-24); longest first (ties in camera order), so that the lanes that sum
 //                one warp's slots have similar work.
 constexpr int kChunkObs = 256;
-constexpr int kGroupSlots = 256;
+constexpr int kGroupSlots = 256;     // distinct cameras of an FP32-bulk group (at most)
+constexpr int kGroupSlotsF64 = 96;   // of an FP64 group, whose shared memory also holds a
+                                     // chunk's J_p rows (the FP64 slot sums form J_p^T w)
 
 struct ChunkRecLayout {
   int code, sseg, clist, bytes;
@@ -169,6 +172,7 @@ struct SerSchedule {
   int target = 0;  // observations per group the partition aimed at
   int tail = 0;    // pieces the last eighth of each group is cut into (0: none)
   int n_groups = 0, n_chunks = 0, n_gslots = 0, max_group_slots = 0;
+  int n_long_groups = 0;  // groups run by the long-group body (long tracks, wide landmarks)
   // [n_groups][8] in ticket order (decreasing observation count): chunk0, n_chunks, gslot0,
   // n_gslots, n_obs, problem, 0, 0
   std::vector<int32_t> group;
@@ -185,7 +189,8 @@ struct SerSchedule {
 // last eighth of the observations of each group (of at least two chunks) becomes `tail`
 // smaller groups, which the ticket order (largest first) hands out last, so that blocks that
 // finish their large group early take them and the phase ends more evenly.
-std::string build_series_schedule(const Schedule& S, int target, int tail, SerSchedule* out);
+std::string build_series_schedule(const Schedule& S, int target, int tail, SerSchedule* out,
+                                  int slot_cap = kGroupSlots);
 // The automatic group size for G blocks that run groups: one group of n_obs / G observations
 // per block (at least one chunk's worth).
 int series_auto_target(int64_t n_obs, int G);

@@ -255,8 +255,10 @@ std::string build_schedule(int n_cams, int n_lms, int n_obs, const int32_t* cam_
   return "";
 }
 
-std::string build_series_schedule(const Schedule& S, int target, int tail, SerSchedule* Q) {
+std::string build_series_schedule(const Schedule& S, int target, int tail, SerSchedule* Q,
+                                  int slot_cap) {
   if (target < 1) return "the group size must be >= 1";
+  if (slot_cap < 1 || slot_cap > kGroupSlots) return "the group slot cap must be in [1, 256]";
   if (tail < 0 || tail > 64) return "the tail split must be in [0, 64]";
   Q->target = target;
   Q->tail = tail;
@@ -272,7 +274,22 @@ std::string build_series_schedule(const Schedule& S, int target, int tail, SerSc
     bool long_track;  // the pieces of one long track (a long group)
   };
   std::vector<Range> ranges;  // one problem's groups as landmark ranges
-  int n_groups = 0, rid = 0;
+  // a landmark seen by more than slot_cap cameras (possible when slot_cap < kChunkObs) cannot
+  // share a group's slots: like a long track's pieces it becomes a group of its own, whose chunk
+  // keeps slots of its own (the long-group body), so that every other group stays within the cap
+  std::vector<char> wide(S.n_lms_int, 0);
+  for (int l = 0; l < S.n_lms_int; ++l) {
+    if (S.lm_long[l] >= 0 || S.lm_seg[l + 1] - S.lm_seg[l] <= slot_cap) continue;
+    int ncam = 0;
+    for (int o = S.lm_seg[l]; o < S.lm_seg[l + 1]; ++o)
+      if (stamp[S.cam_of[o]] != l) {
+        stamp[S.cam_of[o]] = l;
+        ++ncam;
+      }
+    wide[l] = ncam > slot_cap;
+  }
+  std::fill(stamp.begin(), stamp.end(), -1);
+  int n_groups = 0, rid = 0, n_long_groups = 0;
   int next_tag = -2;  // marks of gslot_of while a slot set is collected (slots are >= 0)
   for (int p = 0; p < S.n_probs; ++p) {
     // the problem's observed landmarks (unobserved ones sort last within their problem)
@@ -285,9 +302,9 @@ std::string build_series_schedule(const Schedule& S, int target, int tail, SerSc
     int64_t k_next = 1;  // index of the next balanced boundary
     ranges.clear();
     for (int l = l0; l < l1;) {
-      if (S.lm_long[l] >= 0) {
-        // a long track: its pieces form one group of their own
-        const int le = l + S.long_np[S.lm_long[l]];
+      if (S.lm_long[l] >= 0 || wide[l]) {
+        // a long track: its pieces form one group of their own (a wide landmark: one piece)
+        const int le = S.lm_long[l] >= 0 ? l + S.long_np[S.lm_long[l]] : l + 1;
         ranges.push_back({l, le, true});
         const int64_t done = (int64_t)S.lm_seg[le] - o_beg;
         while (k_next < ng && done * ng >= k_next * n_p) ++k_next;
@@ -296,15 +313,15 @@ std::string build_series_schedule(const Schedule& S, int target, int tail, SerSc
       }
       // one range: landmarks [l, le), ending at the balanced boundary k_next * n_p / ng
       // (observations from the problem's start), before a long track, or before its cameras
-      // would exceed kGroupSlots
+      // would exceed slot_cap
       const int r = rid++;
       int le = l, ncam = 0;
       while (le < l1) {
-        if (S.lm_long[le] >= 0) break;
+        if (S.lm_long[le] >= 0 || wide[le]) break;
         const int a = S.lm_seg[le], b = S.lm_seg[le + 1];
         int fresh = 0;
         for (int o = a; o < b; ++o) fresh += stamp[S.cam_of[o]] != r;
-        if (le > l && ncam + fresh > kGroupSlots) break;
+        if (le > l && ncam + fresh > slot_cap) break;
         for (int o = a; o < b; ++o) {
           if (stamp[S.cam_of[o]] != r) {
             stamp[S.cam_of[o]] = r;
@@ -411,10 +428,12 @@ std::string build_series_schedule(const Schedule& S, int target, int tail, SerSc
       const int ns_g = (int)gcams.size() - gs0;
       const int32_t gd[8] = {c0, nc, gs0, ns_g, S.lm_seg[le] - S.lm_seg[l], p,
                              rg.long_track ? 1 : 0, 0};
+      n_long_groups += rg.long_track ? 1 : 0;
       gnat.insert(gnat.end(), gd, gd + 8);
     }
   }
   Q->n_groups = n_groups;
+  Q->n_long_groups = n_long_groups;
   Q->n_chunks = (int)(Q->chunk.size() / 8);
   Q->n_gslots = (int)gcams.size();
   Q->gslot_cam = gcams;

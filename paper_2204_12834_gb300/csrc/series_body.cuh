@@ -65,12 +65,16 @@ template <> struct __align__(16) GroupSmem<float> {
                                   // barrier that ends the previous chunk's slot sums' reads)
 };
 
+// FP64 rows of sg: J_p (18 values) and w = J_l z (2) of the observation at each camera-sorted
+// position; the odd stride spreads a warp's rows over the banks.
+constexpr int kSgF64 = 21;
+
 template <> struct __align__(16) GroupSmem<double> {
-  double2 tc[kGroupSlots][5];  // 9 of 10 used
-  double acc[kGroupSlots][9];
-  double2 sg[kChunkObs][5];    // g rows at their camera-sorted positions
-  double sv[kChunkObs][3];     // each observation's landmark contribution J_l^T J_p t
-  double sz[kChunkObs][3];     // z of each landmark of the chunk
+  double2 tc[kGroupSlotsF64][5];  // 9 of 10 used
+  double acc[kGroupSlotsF64][9];
+  double sg[kChunkObs][kSgF64];   // J_p and w rows at their camera-sorted positions
+  double sv[kChunkObs][3];        // each observation's landmark contribution J_l^T J_p t
+  double sz[kChunkObs][3];        // z of each landmark of the chunk
 };
 
 // Lanes of a chunk's slot sums.  Each of `items` sums (chunk slots are ordered longest first,
@@ -400,8 +404,11 @@ __device__ __forceinline__ void chunk_f32(const Topology& tp, const SerTopo& sp,
 // ---------------------------------------------------------------------------------------
 // FP64 chunk.  FP64 instructions are the bound here (GB300 runs a warp's FP64 instruction over
 // 16 cycles of its FP64 pipe), so the landmark sums use one thread per landmark, which adds
-// each contribution once (a scan would add log2 of the track length times), and z is formed
-// once per landmark.  Three block barriers per chunk.  Every thread must call it.
+// each contribution once (a scan would add log2 of the track length times), z is formed once
+// per landmark, and g = J_p^T w is never formed on its own: each observation leaves J_p and w
+// at its camera-sorted position and the lanes of a slot sum accumulate J_p^T w row by row with
+// two FMAs per row and component (18 FP64 operations per observation where forming g and then
+// adding it took 27).  Three block barriers per chunk.  Every thread must call it.
 template <int MODE>
 __device__ __forceinline__ void chunk_f64(const Topology& tp, const SerTopo& sp, int c,
                                           const double* __restrict__ J,
@@ -475,17 +482,16 @@ __device__ __forceinline__ void chunk_f64(const Topology& tp, const SerTopo& sp,
     const double z0 = sm.sz[lm][0], z1 = sm.sz[lm][1], z2 = sm.sz[lm][2];
     const double w0 = jl[0] * z0 + jl[1] * z1 + jl[2] * z2;
     const double w1 = jl[3] * z0 + jl[4] * z1 + jl[5] * z2;
-    double2* row = sm.sg[code & 0xff];
+    double* row = sm.sg[code & 0xff];
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      row[k] = make_double2(jp[2 * k] * w0 + jp[9 + 2 * k] * w1,
-                            jp[2 * k + 1] * w0 + jp[10 + 2 * k] * w1);
-    row[4] = make_double2(jp[8] * w0 + jp[17] * w1, 0.0);
+    for (int k = 0; k < 18; ++k) row[k] = jp[k];
+    row[18] = w0;
+    row[19] = w1;
   }
   __syncthreads();
-  // chunk slot j, component k: rows [beg_j, beg_{j+1}) over `split` lanes, then the group slot
+  // chunk slot j, component k: sum over rows [beg_j, beg_{j+1}) (over `split` lanes) of
+  // J_p[k] w0 + J_p[9 + k] w1, then the group slot
   const uint32_t* clist = reinterpret_cast<const uint32_t*>(rec + L.clist);
-  const double* sgd = reinterpret_cast<const double*>(&sm.sg[0][0]);
   const int items = ns * 9;
   const SumPlan P = sum_plan(items);
   const int bound = (P.lanes + 31) & ~31;
@@ -501,7 +507,11 @@ __device__ __forceinline__ void chunk_f64(const Topology& tp, const SerTopo& sp,
       const uint32_t e = chk_clist(tp, __ldg(clist + j), n, gns);
       gs = (int)(e & 0xff);
       const int beg = (int)(e >> 8) & 0xff, end = beg + (int)(e >> 16);
-      for (int r = beg + part; r < end; r += split) s += sgd[r * 10 + k];
+      for (int r = beg + part; r < end; r += split) {
+        const double* q = sm.sg[r];
+        s = __fma_rn(q[k], q[18], s);
+        s = __fma_rn(q[9 + k], q[19], s);
+      }
     }
     for (int off = P.s; off > 0; off >>= 1) {  // levels of the largest split (2 s)
       const double a = __shfl_down_sync(kFull, s, off);

@@ -169,11 +169,12 @@ int main(int argc, char** argv) {
   }
 
   // series schedule for a grid of G blocks: groups of whole landmarks of one problem, balanced
-  // by observation count, at most kGroupSlots cameras; chunks of whole landmarks; records
+  // by observation count, at most `cap` cameras; chunks of whole landmarks; records
   SerSchedule Q;
   const int target = series_auto_target(no, G);
   const int tail = G % 3;  // exercise the tail split on some grids
-  const std::string qwhy = build_series_schedule(S, target, tail, &Q);
+  const int cap = G % 2 ? kGroupSlotsF64 : kGroupSlots;  // both precisions' slot caps
+  const std::string qwhy = build_series_schedule(S, target, tail, &Q, cap);
   CHECK(qwhy.empty(), "build_series_schedule failed: %s", qwhy.c_str());
   CHECK((int)Q.group.size() == 8 * Q.n_groups && (int)Q.chunk.size() == 8 * Q.n_chunks,
         "series descriptor sizes");
@@ -185,7 +186,7 @@ int main(int argc, char** argv) {
     if (i > 0) CHECK(g[4] <= Q.group[8 * (size_t)(i - 1) + 4], "groups not in decreasing size order at %d", i);
     CHECK(g[1] >= 1 && g[0] >= 0 && g[0] + g[1] <= Q.n_chunks, "group %d chunk range", i);
     const bool lg = g[6] != 0;  // a long track's group: its pieces, one chunk each
-    CHECK(g[3] >= 1 && (lg || g[3] <= kGroupSlots) && g[2] >= 0 && g[2] + g[3] <= Q.n_gslots,
+    CHECK(g[3] >= 1 && (lg || g[3] <= cap) && g[2] >= 0 && g[2] + g[3] <= Q.n_gslots,
           "group %d slot range (%d slots)", i, g[3]);
     int obs = 0;
     std::set<int> cams;
