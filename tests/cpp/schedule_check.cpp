@@ -179,13 +179,15 @@ int main(int argc, char** argv) {
   CHECK((int)Q.group.size() == 8 * Q.n_groups && (int)Q.chunk.size() == 8 * Q.n_chunks,
         "series descriptor sizes");
   std::vector<int> chunk_group(Q.n_chunks, -1);
+  int n_lg = 0, n_wide = 0;
   std::vector<int> group_of_slot(Q.n_gslots, -1);
   std::vector<int> slot_key(Q.n_gslots, -1);  // landmark order: the chunk its rows start in
   for (int i = 0; i < Q.n_groups; ++i) {
     const int32_t* g = &Q.group[8 * (size_t)i];
     if (i > 0) CHECK(g[4] <= Q.group[8 * (size_t)(i - 1) + 4], "groups not in decreasing size order at %d", i);
     CHECK(g[1] >= 1 && g[0] >= 0 && g[0] + g[1] <= Q.n_chunks, "group %d chunk range", i);
-    const bool lg = g[6] != 0;  // a long track's group: its pieces, one chunk each
+    const bool lg = g[6] != 0;  // a long group: a long track's pieces or one wide landmark
+    n_lg += lg ? 1 : 0;
     CHECK(g[3] >= 1 && (lg || g[3] <= cap) && g[2] >= 0 && g[2] + g[3] <= Q.n_gslots,
           "group %d slot range (%d slots)", i, g[3]);
     int obs = 0;
@@ -205,10 +207,17 @@ int main(int argc, char** argv) {
       }
       for (int l = d[2]; l < d[2] + d[3]; ++l) {
         const int j = S.lm_long[l];
-        CHECK(lg == (j >= 0), "group %d: a piece of a long track in a plain group, or the reverse", i);
-        if (lg) {
+        CHECK(lg || j < 0, "group %d: a piece of a long track in a plain group", i);
+        if (lg && j >= 0) {
           CHECK(d[3] == 1 && l == S.long_first[j] + (c - g[0]) && g[1] == S.long_np[j],
                 "long group %d chunk %d is not piece %d of its track", i, c, c - g[0]);
+        } else if (lg) {
+          // a landmark seen by more cameras than the slot cap: a group of one piece
+          std::set<int> lc;
+          for (int o = S.lm_seg[l]; o < S.lm_seg[l + 1]; ++o) lc.insert(S.cam_of[o]);
+          CHECK(d[3] == 1 && g[1] == 1 && (int)lc.size() > cap,
+                "long group %d is neither a long track nor one landmark wider than the cap", i);
+          ++n_wide;
         }
       }
       if (lg) {
@@ -239,6 +248,18 @@ int main(int argc, char** argv) {
       }
     }
     CHECK(s == g[2] + g[3], "group %d slot count", i);
+  }
+  CHECK(n_lg == Q.n_long_groups, "long group count %d, schedule says %d", n_lg, Q.n_long_groups);
+  {
+    // every landmark wider than the cap (and not a long track) has a group of its own
+    int wide = 0;
+    for (int l = 0; l < S.n_lms_int; ++l) {
+      if (S.lm_long[l] >= 0) continue;
+      std::set<int> lc;
+      for (int o = S.lm_seg[l]; o < S.lm_seg[l + 1]; ++o) lc.insert(S.cam_of[o]);
+      wide += (int)lc.size() > cap ? 1 : 0;
+    }
+    CHECK(wide == n_wide, "%d landmarks wider than the cap, %d wide groups", wide, n_wide);
   }
   // chunks in landmark order cover every observation once
   {
@@ -372,7 +393,8 @@ int main(int argc, char** argv) {
   for (int b = 0; b < G; ++b)
     CHECK(rl.block_round[b + 1] >= rl.block_round[b], "block_round decreases at %d", b);
 
-  std::printf("ok tiles=%d slots=%d rounds=%d groups=%d chunks=%d gslots=%d\n", S.n_tiles,
+  std::printf("ok wide=%d tiles=%d slots=%d rounds=%d groups=%d chunks=%d gslots=%d\n", n_wide,
+              S.n_tiles,
               S.n_slots, R, Q.n_groups, Q.n_chunks, Q.n_gslots);
   return 0;
 }

@@ -70,6 +70,40 @@ def test_longest_track_and_wide_tiles(poba):
         assert np.array_equal(st[0], steps[0][0]) and np.array_equal(st[1], steps[0][1])
 
 
+def test_landmarks_wider_than_the_fp64_group(poba):
+    """FP64 groups hold at most 96 cameras: landmarks seen by 150 and 97 cameras run as groups
+    of their own (the long-group body), one seen by 96 cameras in an ordinary group. FP64 series
+    against the oracle at fixed m and with the stop rule; every form gives the same bits (forms
+    4 and 5 fall back to 3 on such a problem, and ba_set_schedule refuses them)."""
+    rng = np.random.default_rng(6)
+    p = bal_synth.make_problem(200, 600, track=("uniform", 2, 6), seed=113)
+    from oracle import camera_model as cm
+    for lm, k in ((0, 150), (1, 97), (2, 96)):
+        seen = p.cam_idx[p.lm_idx == lm]
+        add_c = np.setdiff1d(np.arange(k), seen)[:k - len(np.unique(seen))].astype(np.int32)
+        add_l = np.full(len(add_c), lm, np.int32)
+        pix = np.stack(cm.project([p.cams_gt[add_c, j] for j in range(9)],
+                                  [p.lms_gt[add_l, j] for j in range(3)]), 1)
+        p.obs = np.vstack([p.obs, pix + rng.normal(0, 1, pix.shape)])
+        p.cam_idx = np.concatenate([p.cam_idx, add_c])
+        p.lm_idx = np.concatenate([p.lm_idx, add_l])
+    check_series(poba, p)
+    check_series(poba, p, lam=1e-2, m=20)
+    steps = []
+    for mode in (0, 1, 2, 3, 4, 5):
+        h = poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, precision=0,
+                           options=poba.ba_default_options(eps=0.01, max_inner=12,
+                                                           series_exec=mode))
+        poba.ba_linearize(h)
+        info = poba.ba_solve_schur_power(h, 1e-3)
+        steps.append((info["inner_iters"], poba.ba_get_step(h)))
+    for st in steps[1:]:
+        assert st[0] == steps[0][0]
+        assert np.array_equal(st[1][0], steps[0][1][0]) and np.array_equal(st[1][1], steps[0][1][1])
+    with pytest.raises(poba.PobaError):
+        poba.ba_set_schedule(h, series_exec=5, blocks_per_sm=1)
+
+
 def test_no_observations(poba):
     p = bal_synth.make_problem(3, 10, seed=105)
     h = poba.ba_create(p.cams0, p.lms0, p.obs[:0], p.cam_idx[:0], p.lm_idx[:0],

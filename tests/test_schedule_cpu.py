@@ -3,7 +3,9 @@ tests/cpp/schedule_check.cpp against the properties the kernels rely on: observa
 (landmark, camera); tiles of whole landmarks of one problem within the observation, landmark
 and camera caps; slots equal to each tile's cameras in ascending order, with positions that
 sort the tile by camera; camera-major rows in tile order; camera chunks that tile each
-camera's rows; rounds of at most 28 cameras and items split over the grid."""
+camera's rows; rounds of at most 28 cameras and items split over the grid; series groups within
+each precision's camera cap (256 FP32 bulk, 96 FP64), landmarks wider than the cap and long
+tracks' pieces in groups of their own."""
 import os
 import shutil
 import subprocess
@@ -89,6 +91,21 @@ def test_schedule_with_a_256_camera_track(checker, tmp_path):
     p.lm_idx = np.concatenate([p.lm_idx, np.zeros(len(extra), dtype=p.lm_idx.dtype)])
     assert np.sum(p.lm_idx == 0) == 256
     run(checker, tmp_path, [p])
+
+
+def test_schedule_with_landmarks_wider_than_the_fp64_cap(checker, tmp_path):
+    """FP64 groups hold at most 96 cameras (odd grids make the checker use that cap): landmarks
+    seen by 256, 150 and 97 cameras each become a group of their own (one chunk with its own
+    slots), one seen by exactly 96 does not; under the FP32-bulk cap of 256 none does."""
+    p = bal_synth.make_problem(256, 300, track=("uniform", 2, 6), seed=93)
+    for lm, k in ((0, 256), (1, 150), (2, 97), (3, 96)):
+        seen = p.cam_idx[p.lm_idx == lm]
+        extra = np.setdiff1d(np.arange(k), seen)[:k - len(np.unique(seen))]
+        p.cam_idx = np.concatenate([p.cam_idx, extra]).astype(p.cam_idx.dtype)
+        p.lm_idx = np.concatenate([p.lm_idx, np.full(len(extra), lm, dtype=p.lm_idx.dtype)])
+        assert len(np.unique(p.cam_idx[p.lm_idx == lm])) == max(k, len(np.unique(seen)))
+    assert run(checker, tmp_path, [p], grid=455).startswith("ok wide=3 ")
+    assert run(checker, tmp_path, [p], grid=456).startswith("ok wide=0 ")
 
 
 def test_schedule_with_a_repeated_observation(checker, tmp_path):
