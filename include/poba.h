@@ -350,7 +350,8 @@ ba_status ba_solve_schur_pcg(ba_handle* h, double lambda, int32_t precond, int32
  * when their group sizes agree (a batch and handles made for its problems alone included).
  *   group_obs      observations per group; 0: automatic, n_obs / (the blocks of the
  *                  persistent kernel at its largest residency that run groups: SMs x residency
- *                  - 1), i.e. one group per block (at least 256);
+ *                  - 1), i.e. one group per block (two per block for a batch, whose problems
+ *                  stop at different terms and steps; at least 256);
  *   tail_parts     each group of at least 512 observations gives its last eighth to
  *                  tail_parts smaller groups, which blocks take after the large ones (groups go
  *                  out largest first), so that the blocks that finish early even out the end of
@@ -381,8 +382,8 @@ ba_status ba_set_schedule(ba_handle* h, const ba_schedule* in);
  * batched form).  On the handle's current linearisation (linearising first if needed) it times
  * `trials` series solves (damp, invert, max_inner terms, back-substitution; after one warm-up)
  * at lambda0 for: each persistent form (3, 5, and 4 in BA_FP32_BULK) at each residency the
- * device allows with one group per block (group_obs = n_obs / (the blocks that run groups))
- * and no tail split; at the fastest of those, tail splits of 0 and 4 and half the group size;
+ * device allows with one group per block (group_obs = n_obs / (the blocks that run groups);
+ * two per block for a batch) and no tail split; at the fastest of those, tail splits of 0 and 4 and half the group size;
  * and the replayed CUDA graph of per-term launches on the fastest schedule.  The fastest
  * becomes the handle's schedule (ba_get_schedule reports it) and the form series_exec 2 runs.
  * Overwrites the last step (as ba_solve_schur_power does).  *exec_out (may be NULL) receives
