@@ -197,7 +197,10 @@ ba_status ba_cost(ba_handle* h, double* cost_out);
 ba_status ba_get_params(ba_handle* h, double* cams, double* lms, int32_t ptr_kind);
 
 /* Overwrite the current state (same layout as ba_get_params); marks the linearisation stale
- * and leaves lambda unchanged.  Errors: BA_ERR_NONFINITE, BA_ERR_INVALID_ARG. */
+ * and leaves lambda unchanged.  A state equal to the current one in every bit (for instance the
+ * state a rejected LM step left, read back with ba_get_params) changes nothing: the
+ * linearisation and the cost at that state stay in place.  Synchronises (the finiteness check).
+ * Errors: BA_ERR_NONFINITE, BA_ERR_INVALID_ARG. */
 ba_status ba_set_params(ba_handle* h, const double* cams, const double* lms, int32_t ptr_kind);
 
 /* Copy the last solve's step dx_p [n_cams][9] and dx_l [n_lms][3] (caller's order).

@@ -115,7 +115,7 @@ struct ba_handle {
   SeriesGlobal* sgl = nullptr;
   LmRecord* rec = nullptr;        // [n_probs]
   int32_t* not_spd = nullptr;
-  int32_t* io_bad = nullptr;      // [2] non-finite flags of ba_set_params
+  int32_t* io_bad = nullptr;      // [3] non-finite flags and the "state differs" flag of ba_set_params
   int32_t* relin = nullptr;       // 1: the next captured LM step linearises (set on the device)
   int n_probs = 1;
   std::vector<int32_t> cam_off_h, lm_off_h;  // caller numbering of the problems' cameras / landmarks
@@ -126,7 +126,7 @@ struct ba_handle {
   GridSync* h_gs = nullptr;
   LmRecord* h_rec = nullptr;     // [n_probs]
   int32_t* h_flag = nullptr;
-  int32_t* h_io = nullptr;       // [2]
+  int32_t* h_io = nullptr;       // [3]
   int32_t* h_relin = nullptr;    // host value written to relin before a captured step
   double* h_scalar = nullptr;
 
@@ -194,6 +194,13 @@ struct ba_handle {
 
   bool f32() const { return precision == BA_FP32_BULK; }
 };
+
+namespace poba {
+// *differ |= 1 if the input state differs from the current one in any bit (kernels_series.cu;
+// order: the internal landmark rows' caller rows, 3 values each; null for cameras).
+void launch_state_differs(const double* src, const double* cur, const int32_t* order, int n,
+                          int32_t* differ, cudaStream_t s);
+}  // namespace poba
 
 namespace {
 
@@ -966,7 +973,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
   items.push_back({(void**)&h->sgl, sizeof(SeriesGlobal)});
   items.push_back({(void**)&h->rec, sizeof(LmRecord) * P});
   items.push_back({(void**)&h->not_spd, sizeof(int32_t) * P});
-  items.push_back({(void**)&h->io_bad, sizeof(int32_t) * 2});
+  items.push_back({(void**)&h->io_bad, sizeof(int32_t) * 3});
   items.push_back({(void**)&h->relin, sizeof(int32_t)});
   items.push_back({(void**)&h->chk, sizeof(CheckRecord)});
   size_t total = 0;
@@ -1007,7 +1014,7 @@ ba_status create_impl(const ba_problem_desc* descs, int n_probs, const ba_option
       (e = cudaMallocHost(&h->h_rec, sizeof(LmRecord) * P)) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_gs, sizeof(GridSync))) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_flag, sizeof(int32_t) * P)) != cudaSuccess ||
-      (e = cudaMallocHost(&h->h_io, sizeof(int32_t) * 2)) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_io, sizeof(int32_t) * 3)) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_relin, sizeof(int32_t))) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_scalar, sizeof(double) * 4)) != cudaSuccess)
     return bail(fail_cuda(e, "cudaMallocHost"));
@@ -2005,18 +2012,24 @@ ba_status ba_set_params(ba_handle* h, const double* cams, const double* lms, int
     c_src = h->adj_p;
     l_src = h->adj_l;
   }
-  CK(cudaMemsetAsync(h->io_bad, 0, sizeof(int32_t) * 2, s));
+  CK(cudaMemsetAsync(h->io_bad, 0, sizeof(int32_t) * 3, s));
   if (cams) launch_check_finite(c_src, (int)nc9, h->io_bad + 0, s);
   if (lms) launch_check_finite(l_src, (int)nl3, h->io_bad + 1, s);
-  CK(cudaMemcpyAsync(h->h_io, h->io_bad, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, s));
+  // a state equal to the current one in every bit (typically the state a rejected LM step
+  // left, read back and passed in again) keeps the linearisation and the cost
+  if (cams) launch_state_differs(c_src, h->cams, nullptr, (int)nc9, h->io_bad + 2, s);
+  if (lms) launch_state_differs(l_src, h->lms, h->lm_order_dev, h->n_li, h->io_bad + 2, s);
+  h->launches += (cams ? 2 : 0) + (lms ? 2 : 0);
+  CK(cudaMemcpyAsync(h->h_io, h->io_bad, sizeof(int32_t) * 3, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   ba_status st = check_launch(h, "state input");
   if (st != BA_OK) return st;
   if (h->h_io[0]) return fail(BA_ERR_NONFINITE, "non-finite camera parameter");
   if (h->h_io[1]) return fail(BA_ERR_NONFINITE, "non-finite landmark");
+  if (!h->h_io[2]) return BA_OK;
   if (cams) CK(cudaMemcpyAsync(h->cams, c_src, sizeof(double) * nc9, cudaMemcpyDeviceToDevice, s));
   if (lms) launch_gather_rows3(l_src, h->lm_order_dev, h->n_li, h->lms, s);
-  h->launches += (cams ? 1 : 0) + (lms ? 2 : 0);
+  h->launches += lms ? 1 : 0;
   h->linearized = false;
   h->relin_synced = false;
   h->cost_valid = false;

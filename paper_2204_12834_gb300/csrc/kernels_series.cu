@@ -378,6 +378,24 @@ __global__ void scatter_rows3_kernel(const double* __restrict__ src, const int32
   if (i < 3 * n) dst[(size_t)order[i / 3] * 3 + i % 3] = src[i];
 }
 
+// *differ |= 1 when src differs from the current state cur in any bit: src[i] against cur[i]
+// (order null), or the caller-order rows src[order[r]] against the internal rows cur[r] (3 values
+// per row, n rows).
+__global__ void state_differs_kernel(const double* __restrict__ src, const double* __restrict__ cur,
+                                     const int32_t* __restrict__ order, int n, int32_t* differ) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = order ? 3 * n : n;
+  if (i >= m) return;
+  const double a = order ? src[(size_t)order[i / 3] * 3 + i % 3] : src[i];
+  if (__double_as_longlong(a) != __double_as_longlong(cur[i])) atomicOr(differ, 1);
+}
+
+void launch_state_differs(const double* src, const double* cur, const int32_t* order, int n,
+                          int32_t* differ, cudaStream_t s) {
+  const int m = order ? 3 * n : n;
+  if (m > 0) state_differs_kernel<<<(m + 255) / 256, 256, 0, s>>>(src, cur, order, n, differ);
+}
+
 void launch_check_finite(const double* src, int n, int32_t* bad, cudaStream_t s) {
   if (n > 0) check_finite_kernel<<<(n + 255) / 256, 256, 0, s>>>(src, n, bad);
 }

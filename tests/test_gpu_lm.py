@@ -103,3 +103,41 @@ def test_lm_solve_entry_point(poba):
     assert trace[-1]["converged"] or len(trace) == 30
     _, _, hist = olm.lm_solve(p, olm.Options(max_lm=30))
     assert len(trace) == len(hist)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_state_round_trip_keeps_the_linearisation(poba, precision):
+    """ba_set_params with the state ba_get_params returned (bit for bit) changes nothing: the
+    linearisation stays in place (no relinearisation after a rejected step), and an LM run that
+    passes its state through the host every step gives the device loop's steps and final state
+    bit for bit.  A state that differs in one bit marks the linearisation stale."""
+    p = bal_synth.make_problem(60, 3000, track=("uniform", 2, 6), visibility="clustered",
+                               seed=131)
+    opt = poba.ba_default_options(func_tol=0.0)
+    h1 = poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, options=opt,
+                        precision=precision)
+    h2 = poba.ba_create(p.cams0, p.lms0, p.obs, p.cam_idx, p.lm_idx, options=opt,
+                        precision=precision)
+    s1, s2 = [], []
+    for _ in range(25):
+        s1.append(poba.ba_lm_step(h1))
+        c, l = poba.ba_get_params(h2)
+        poba.ba_set_params(h2, c, l)
+        s2.append(poba.ba_lm_step(h2))
+    for a, b in zip(s1, s2):
+        assert a["accepted"] == b["accepted"] and a["cost_after"] == b["cost_after"]
+    c1, l1 = poba.ba_get_params(h1)
+    c2, l2 = poba.ba_get_params(h2)
+    assert np.array_equal(c1, c2) and np.array_equal(l1, l2)
+    # the linearisation survives a round trip of the current state
+    poba.ba_linearize(h2)
+    c, l = poba.ba_get_params(h2)
+    poba.ba_set_params(h2, c, l)
+    poba.ba_get_linearization(h2)
+    # and goes stale when one value changes in its last bit
+    l = l.copy()
+    l[5, 1] = np.nextafter(l[5, 1], np.inf)
+    poba.ba_set_params(h2, c, l)
+    with pytest.raises(poba.PobaError) as e:
+        poba.ba_get_linearization(h2)
+    assert e.value.status_name == "BA_ERR_NOT_LINEARIZED"
